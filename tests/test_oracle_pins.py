@@ -1,0 +1,372 @@
+"""Pins for the CPU oracle: published test vectors, exact closed forms, brute force on tiny graphs and invariants.
+
+Each test ties one oracle function to something other than the oracle itself, so that a dropped term, a wrong sign,
+a swapped operand or a wrong index in it fails here.
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.csgraph as csg
+
+import bruteforce as bf
+from synth import graphs
+
+IC, WC, PER_EDGE = 0, 1, 2
+
+
+# --- hash primitives -------------------------------------------------------------------------------------------
+
+def test_fmix32_published_vectors(orc):
+    # MurmurHash3_x86_32 of the empty key with seed s reduces to fmix32(s); the published values for seeds 0, 1 and
+    # 0xFFFFFFFF are 0, 0x514E28B7 and 0x81F16F39.
+    assert orc.fmix32(0) == 0
+    assert orc.fmix32(1) == 0x514E28B7
+    assert orc.fmix32(0xFFFFFFFF) == 0x81F16F39
+
+
+def test_fmix32_is_a_bijection_on_a_sample(orc):
+    xs = np.random.PCG64(7).random_raw(20000) & 0xFFFFFFFF
+    ys = {orc.fmix32(int(x)) for x in xs}
+    assert len(ys) == len(set(int(x) for x in xs))
+
+
+def test_splitmix64_published_vector(orc):
+    # The reference sequence of splitmix64 (Steele, Lea & Flood 2014; Vigna's splitmix64.c) from seed 1234567.
+    ref = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431, 16408922859458223821]
+    assert [orc.splitmix64(1234567, i) for i in range(5)] == ref
+
+
+def test_sim_words_take_alternate_outputs(orc):
+    # X_r is the high half of output 2r, Y_r of output 2r+1 (reading R3), checked on the published sequence.
+    X, Y = orc.sim_words(1234567, 2)
+    ref = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431]
+    assert [int(X[0]), int(Y[0]), int(X[1]), int(Y[1])] == [r >> 32 for r in ref]
+
+
+def test_clz32_matches_bit_length(orc):
+    xs = [0, 1, 2, 3, 0x7FFFFFFF, 0x80000000, 0xFFFFFFFF] + [int(x) for x in
+                                                               np.random.PCG64(3).random_raw(2000) >> np.uint64(
+                                                                   np.random.PCG64(4).random_raw(1)[0] % 32 + 32)]
+    for x in xs:
+        x &= 0xFFFFFFFF
+        assert orc.clz32(x) == 32 - x.bit_length()
+
+
+def test_edge_hash_is_fmix32_of_small_keys(orc):
+    # Where u*n+v fits in 32 bits the edge hash is exactly fmix32(u*n+v), the form named for the 2000-vertex graph.
+    n = 2000
+    for u, v in [(0, 1), (1, 0), (5, 1999), (1999, 1998), (1234, 567)]:
+        assert orc.edge_hash(u, v, n) == orc.fmix32(u * n + v)
+
+
+def test_edge_hash_keeps_high_key_bits(orc):
+    # For n = 2^20, (u, v) and (u + 4096, v) agree in the low 32 bits of u*n+v; their hashes must still differ.
+    n = 1 << 20
+    same = sum(orc.edge_hash(u, v, n) == orc.edge_hash(u + 4096, v, n) for u in range(0, 4096, 97) for v in (0, 77))
+    assert same == 0
+
+
+def test_init_rank_is_clz_of_vertex_hash_xor_word(orc):
+    for v in [0, 1, 2, 1999, 1 << 20, (1 << 22) - 1]:
+        for y in [0, 1, 0xDEADBEEF, 0xFFFFFFFF]:
+            hv = orc.fmix32((v ^ 0x9E3779B9) & 0xFFFFFFFF)
+            assert orc.init_rank(v, y) == 32 - (hv ^ y).bit_length()
+
+
+# --- sampling test (Eq. 4-5) -----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1e-9, 2.3283064365386963e-10, 0.005, 0.01, 0.05, 0.1, 1 / 3, 0.5, 0.999999, 1.0,
+                               0.123456789])
+def test_threshold_gives_smallest_grid_probability_not_below_p(orc, p):
+    # Live iff (h ^ X) <= T, so P(live) = (T+1)/2^32 over uniform X; that must be the least multiple of 2^-32
+    # that is >= p (Eq. 5 with h_max = 2^32: P < w).
+    ok, T = orc.threshold_from_p(p)
+    assert ok == 1
+    q = Fraction(p)
+    assert Fraction(T + 1, 1 << 32) >= q
+    assert Fraction(T, 1 << 32) < q
+
+
+def test_threshold_of_the_2000_vertex_workload(orc):
+    assert orc.threshold_from_p(0.05) == (1, 214748364)
+
+
+@pytest.mark.parametrize("p", [0.0, -0.5])
+def test_nonpositive_probability_never_samples(orc, p):
+    ok, _ = orc.threshold_from_p(p)
+    assert ok == 0
+    assert not orc.is_live(0, 0, 0xFFFFFFFF, 0)
+
+
+def test_live_compare_direction_and_bound(orc):
+    # Feeding X = h ^ t makes (h ^ X) = t, so the test must accept exactly t <= T.
+    h = 0x12345678
+    for T in [0, 1, 214748364, 0x7FFFFFFF, 0xFFFFFFFE, 0xFFFFFFFF]:
+        for t in {0, max(T - 1, 0), T, min(T + 1, 0xFFFFFFFF), 0xFFFFFFFF}:
+            assert orc.is_live(h, h ^ t, T, 1) == (t <= T)
+
+
+def test_weighted_cascade_threshold_is_one_over_indegree(orc):
+    # WC uses p(u,v) = 1/indeg(v) (Section 2.1); the threshold must satisfy the same exact property with q = 1/d.
+    g = graphs.random_small(40, 400, seed=11)
+    T, ok = orc.edge_thresholds(g.n, g.xadj, g.adj, WC)
+    indeg = np.bincount(g.adj, minlength=g.n)
+    for e in range(g.m):
+        d = int(indeg[g.adj[e]])
+        assert ok[e] == 1
+        assert Fraction(int(T[e]) + 1, 1 << 32) >= Fraction(1, d) > Fraction(int(T[e]), 1 << 32)
+
+
+def test_per_edge_thresholds(orc):
+    g = graphs.random_small(20, 100, seed=12)
+    pe = np.linspace(0.0, 1.0, g.m, dtype=np.float32)
+    T, ok = orc.edge_thresholds(g.n, g.xadj, g.adj, PER_EDGE, p_edge=pe)
+    for e in range(g.m):
+        ok1, t1 = orc.threshold_from_p(float(pe[e]))
+        assert ok[e] == ok1 and (not ok1 or T[e] == t1)
+
+
+def test_live_fraction_matches_probability(orc):
+    # Section 3.1 (Fig. 3-4) argues the hash-based draws behave like uniform ones: over ~2.6M (edge, simulation)
+    # pairs the live fraction must sit within 5 standard deviations of (T+1)/2^32, and per-simulation counts must
+    # pass a chi-square test.
+    g = graphs.erdos_renyi(2000, 20000, seed=1)
+    X, _ = orc.sim_words(99, 128)
+    p = 0.05
+    _, T = orc.threshold_from_p(p)
+    q = (T + 1) / 2 ** 32
+    src, dst = g.edges()
+    h = np.array([orc.edge_hash(int(u), int(v), g.n) for u, v in zip(src, dst)], dtype=np.uint32)
+    live = (h[:, None] ^ X[None, :]) <= np.uint32(T)  # the oracle's live test is checked pointwise below
+    for e in range(0, g.m, 997):
+        for j in range(0, 128, 13):
+            assert live[e, j] == orc.is_live(int(h[e]), int(X[j]), T, 1)
+    N = live.size
+    sd = math.sqrt(N * q * (1 - q))
+    assert abs(live.sum() - N * q) < 5 * sd
+    per_sim = live.sum(axis=0)
+    exp = g.m * q
+    chi2 = float(((per_sim - exp) ** 2 / (exp * (1 - q))).sum())
+    # 127 degrees of freedom: the 1e-6 upper tail is about 230
+    assert chi2 < 230
+
+
+# --- diffusion (Algorithm 2) -----------------------------------------------------------------------------------
+
+def _problem(orc, g, model, p, R, seed, p_edge=None):
+    T, ok = orc.edge_thresholds(g.n, g.xadj, g.adj, model, p=p, p_edge=p_edge)
+    X, Y = orc.sim_words(seed, R)
+    return T, ok, X, Y
+
+
+CASES = [
+    ("ic0.05", graphs.random_small(48, 300, 21), IC, 0.05, None),
+    ("ic0.3", graphs.random_small(40, 160, 22), IC, 0.3, None),
+    ("ic0.7", graphs.random_small(33, 90, 23), IC, 0.7, None),
+    ("wc", graphs.random_small(64, 400, 24), WC, 0.0, None),
+    ("per_edge", graphs.random_small(30, 120, 25), PER_EDGE, 0.0, "ramp"),
+    ("chainish", graphs.chain(20), IC, 0.9, None),
+]
+
+
+@pytest.mark.parametrize("name,g,model,p,pe", CASES, ids=[c[0] for c in CASES])
+def test_registers_equal_bruteforce_reach_maxima(orc, name, g, model, p, pe):
+    p_edge = np.linspace(0.0, 0.9, g.m, dtype=np.float32) if pe == "ramp" else None
+    R = 64
+    T, ok, X, Y = _problem(orc, g, model, p, R, seed=5, p_edge=p_edge)
+    M, sweeps, visits, log = orc.build_sketch(g.n, g.xadj, g.adj, model, p, R, seed=5, p_edge=p_edge)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X)
+    ref = bf.registers(orc, g.n, g.xadj, g.adj, live, Y)
+    assert np.array_equal(M, ref)
+    assert log[0] == g.n and visits >= g.m * R
+
+
+def test_blocked_registers_equal_residual_reach_maxima(orc):
+    g = graphs.random_small(40, 200, 31)
+    R = 64
+    T, ok, X, Y = _problem(orc, g, IC, 0.3, R, seed=8)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X)
+    reached = np.zeros((g.n, R), np.uint8)
+    for s in (3, 17):
+        orc.reach_add(g.n, g.xadj, g.adj, T, ok, R, X, s, reached)
+    assert np.array_equal(reached, bf.reached_by(g.n, g.xadj, g.adj, live, [3, 17], R))
+    M = orc.init_registers(g.n, R, Y, blocked=reached)
+    orc.simulate(g.n, g.xadj, g.adj, T, ok, R, X, M, blocked=reached)
+    ref = bf.registers(orc, g.n, g.xadj, g.adj, live, Y, blocked=reached.astype(bool))
+    assert np.array_equal(M, ref)
+
+
+def test_probability_zero_leaves_initial_ranks(orc):
+    g = graphs.random_small(50, 300, 41)
+    R = 64
+    M, sweeps, visits, log = orc.build_sketch(g.n, g.xadj, g.adj, IC, 0.0, R, seed=3)
+    _, Y = orc.sim_words(3, R)
+    ref = np.array([[32 - (orc.fmix32(v ^ 0x9E3779B9) ^ int(Y[j])).bit_length() for j in range(R)]
+                    for v in range(g.n)], dtype=np.uint8)
+    assert np.array_equal(M, ref)
+    assert sweeps == 1 and visits == g.m * R
+
+
+def test_probability_one_gives_transitive_closure_maxima(orc):
+    # With every edge live, M_v[j] is the max initial rank over everything v reaches (scipy's traversal, not ours).
+    g = graphs.random_small(60, 150, 42)
+    R = 64
+    M, *_ = orc.build_sketch(g.n, g.xadj, g.adj, IC, 1.0, R, seed=4)
+    _, Y = orc.sim_words(4, R)
+    A = sp.csr_matrix((np.ones(g.m), g.adj, g.xadj), shape=(g.n, g.n))
+    rank = np.array([[orc.init_rank(v, int(Y[j])) for j in range(R)] for v in range(g.n)])
+    for v in range(g.n):
+        reach = csg.breadth_first_order(A, v, directed=True, return_predecessors=False)
+        assert np.array_equal(M[v], rank[reach].max(axis=0))
+
+
+@pytest.mark.parametrize("reverse", [False, True], ids=["forward", "reverse"])
+def test_chain_sweep_count_is_the_longest_propagation_distance(orc, reverse):
+    # On a path with every edge live, Jacobi sweep t sets M_u to the max over the t vertices downstream of u; the
+    # last change happens at t* = max over (u, j) of the distance from u to the first downstream maximum, and one
+    # more sweep finds nothing, so sweeps = t* + 1.  Visits: sweep t processes u iff its successor changed in sweep
+    # t-1.  The reversed path (edges i -> i-1) makes in-place updates in id order finish early, so it tells Jacobi
+    # sweeps apart from Gauss-Seidel ones.
+    L = 40
+    if reverse:
+        g = graphs.csr_from_edges(L, np.arange(1, L), np.arange(L - 1))
+        succ = lambda u: u - 1 if u > 0 else None  # noqa: E731
+        order = lambda u: list(range(u, -1, -1))  # noqa: E731
+    else:
+        g = graphs.chain(L)
+        succ = lambda u: u + 1 if u < L - 1 else None  # noqa: E731
+        order = lambda u: list(range(u, L))  # noqa: E731
+    R = 64
+    M, sweeps, visits, log = orc.build_sketch(g.n, g.xadj, g.adj, IC, 1.0, R, seed=6)
+    _, Y = orc.sim_words(6, R)
+    rank = np.array([[orc.init_rank(v, int(Y[j])) for j in range(R)] for v in range(L)])
+    tstar = 0
+    for j in range(R):
+        for u in range(L):
+            downstream = rank[order(u), j]
+            tstar = max(tstar, int(np.argmax(downstream)))
+    assert sweeps == tstar + 1
+    cur = rank.copy()
+    changed = np.ones(L, bool)
+    total = 0
+    for _ in range(sweeps):
+        nxt = cur.copy()
+        for u in range(L):
+            v = succ(u)
+            if v is not None and changed[v]:
+                total += R
+                nxt[u] = np.maximum(nxt[u], cur[v])
+        changed = (nxt != cur).any(axis=1)
+        cur = nxt
+    assert visits == total
+    assert np.array_equal(M, cur)
+
+
+def test_blocked_registers_never_update_even_if_the_set_is_not_closed(orc):
+    # Algorithm 2 skips the update of a blocked (u, j) outright.  With the reach set of a seed set as the blocked
+    # set that check can never fire (a blocked vertex only reaches blocked ones), so an arbitrary mask is used here:
+    # a blocked register stays 0 and relays nothing.
+    g = graphs.random_small(40, 220, 33)
+    R = 64
+    T, ok, X, Y = _problem(orc, g, IC, 0.5, R, seed=12)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X)
+    blocked = (np.random.PCG64(5).random_raw(g.n * R).reshape(g.n, R) % 5 == 0).astype(np.uint8)
+    M = orc.init_registers(g.n, R, Y, blocked=blocked)
+    orc.simulate(g.n, g.xadj, g.adj, T, ok, R, X, M, blocked=blocked)
+    ref = bf.registers(orc, g.n, g.xadj, g.adj, live, Y, blocked=blocked.astype(bool))
+    assert np.array_equal(M, ref)
+
+
+def test_converged_registers_are_a_fixpoint(orc):
+    g = graphs.random_small(64, 500, 51)
+    R = 128
+    T, ok, X, Y = _problem(orc, g, WC, 0.0, R, seed=9)
+    M, *_ = orc.build_sketch(g.n, g.xadj, g.adj, WC, 0.0, R, seed=9)
+    M2 = M.copy()
+    sweeps, visits, log = orc.simulate(g.n, g.xadj, g.adj, T, ok, R, X, M2)
+    assert sweeps == 1 and np.array_equal(M, M2)
+
+
+def test_result_is_schedule_independent(orc):
+    # In-place (Gauss-Seidel) updates in a random vertex order reach the same least fixpoint.
+    g = graphs.random_small(50, 260, 52)
+    R = 64
+    T, ok, X, Y = _problem(orc, g, IC, 0.4, R, seed=10)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X)
+    M, *_ = orc.build_sketch(g.n, g.xadj, g.adj, IC, 0.4, R, seed=10)
+    G = np.array([[orc.init_rank(v, int(Y[j])) for j in range(R)] for v in range(g.n)], dtype=np.uint8)
+    order = np.random.default_rng(0).permutation(g.n)
+    changed = True
+    while changed:
+        changed = False
+        for u in order:
+            for e in range(g.xadj[u], g.xadj[u + 1]):
+                v = g.adj[e]
+                new = np.where(live[e], np.maximum(G[u], G[v]), G[u])
+                if (new != G[u]).any():
+                    G[u] = new
+                    changed = True
+    assert np.array_equal(M, G)
+
+
+def test_early_exit_stops_at_first_small_frontier(orc):
+    g = graphs.random_small(64, 400, 53)
+    R = 64
+    _, s_full, _, log_full = orc.build_sketch(g.n, g.xadj, g.adj, IC, 0.5, R, seed=11)
+    eps_c = 0.1
+    _, s_cut, _, log_cut = orc.build_sketch(g.n, g.xadj, g.adj, IC, 0.5, R, seed=11, eps_c=eps_c)
+    sizes = list(log_full[1:]) + [0]  # |L'| after each sweep of the full run
+    first = next(i for i, x in enumerate(sizes) if x <= eps_c * g.n)
+    assert s_cut == first + 1
+    assert np.array_equal(log_cut, log_full[: s_cut])
+
+
+# --- greedy loop (Algorithm 1) ---------------------------------------------------------------------------------
+
+def _greedy_case(orc, g, model, p, R, K, eps_g, eps_l, seed):
+    T, ok, X, Y = _problem(orc, g, model, p, R, seed)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X)
+    ref = bf.greedy(orc, g.n, g.xadj, g.adj, live, Y, K, eps_g, eps_l)
+    out = orc.select_seeds(g.n, g.xadj, g.adj, model, p, R, K, eps_g, eps_l, seed=seed)
+    assert out["seeds"].tolist() == ref["seeds"]
+    assert out["gsum"].tolist() == ref["gsum"]
+    assert out["rebuilt"].tolist() == ref["rebuilt"]
+    assert np.array_equal(out["sigma"], np.array(ref["sigma"]))
+    assert np.array_equal(out["est"], np.array(ref["est"]))
+    return out
+
+
+@pytest.mark.parametrize("eps", [(0.0, 0.0), (math.inf, math.inf), (0.01, 0.3), (0.2, 0.9)],
+                         ids=["always", "never", "paper", "loose"])
+@pytest.mark.parametrize("gseed", [61, 62, 63])
+def test_greedy_equals_bruteforce_on_tiny_graphs(orc, eps, gseed):
+    g = graphs.random_small(12, 30, gseed)
+    _greedy_case(orc, g, IC, 0.5, 64, 3, eps[0], eps[1], seed=gseed)
+
+
+def test_greedy_bruteforce_weighted_cascade_longer(orc):
+    g = graphs.random_small(24, 80, 64)
+    out = _greedy_case(orc, g, WC, 0.0, 64, 6, 0.01, 0.3, seed=3)
+    assert len(set(out["seeds"].tolist())) == 6
+
+
+def test_never_rebuild_runs_one_diffusion_and_always_rebuild_runs_k(orc):
+    g = graphs.random_small(30, 120, 65)
+    never = orc.select_seeds(g.n, g.xadj, g.adj, IC, 0.3, 64, 5, math.inf, math.inf, seed=2)
+    always = orc.select_seeds(g.n, g.xadj, g.adj, IC, 0.3, 64, 5, 0.0, 0.0, seed=2)
+    assert never["builds"] == 1 and never["rebuilt"].sum() == 0
+    assert always["builds"] == 5 and always["rebuilt"].sum() == 5  # the K-th rebuild is decided, not run
+
+
+def test_estimate_is_eq2(orc):
+    for g_sum, R in [(0, 64), (64, 64), (149, 64), (1000, 256), (16384, 512)]:
+        assert orc.estimate_from_sum(g_sum, R) == pytest.approx(2.0 ** (g_sum / R) / 0.77351, rel=1e-15)
+    M = np.array([[1, 5, 0, 2], [3, 0, 0, 7], [0, 0, 4, 0]], np.uint8)
+    e, gsum = orc.estimate_set(M, [0, 1])
+    assert gsum == 3 + 5 + 0 + 7
+    assert e == pytest.approx(2.0 ** (15 / 4) / 0.77351, rel=1e-15)

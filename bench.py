@@ -1,0 +1,297 @@
+"""Benchmark: sketch-based influence maximisation (HyperFuseR, arXiv 2105.04023) on one GB300.
+
+One step = one full seed selection (Algorithm 1: initial build, K greedy steps, reachability searches and the
+error-adaptive rebuilds) on the R-MAT scale-20 weighted-cascade workload (1,048,576 vertices, 16,085,964 edges after
+merging duplicates, R = 256 uint8 registers, K = 50, eps_g = 0.01, eps_l = 0.3) with inputs resident in HBM.
+
+metric: sampled edge-simulation visits per second = (sum over every diffusion sweep of the step of
+|{(u,v): v in L}| * R) / step time; the end-to-end seconds per K-seed selection are reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own replica (the workload does not shard: replicas only) and rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sampled edge-sim visits/sec"
+UNIT = "edge-sim visits/s"
+WORKLOAD = "rmat20_wc"
+
+
+def load_workload():
+    from synth import workloads
+
+    return workloads.rmat20_wc(cache=True)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(prob, sweeps: int = 1) -> tuple[float, int, float]:
+    """The CPU oracle as it stands on a bounded sample: the first `sweeps` Jacobi sweeps of the workload's build."""
+    import oracle
+
+    g = prob.graph
+    T, ok = oracle.edge_thresholds(g.n, g.xadj, g.adj, prob.model, p=prob.p)
+    X, Y = oracle.sim_words(prob.seed, prob.R)
+    M = oracle.init_registers(g.n, prob.R, Y)
+    t = time.perf_counter()
+    _, visits, _ = oracle.simulate(g.n, g.xadj, g.adj, T, ok, prob.R, X, M, max_sweeps=sweeps)
+    dt = time.perf_counter() - t
+    return visits / dt, visits, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    prob = load_workload()
+    vals = []
+    visits = 0
+    for i in range(args.warmup + args.steps):
+        v, visits, dt = oracle_sample(prob)
+        if i >= args.warmup:
+            vals.append(dt)
+    total = sum(vals)
+    value = visits * len(vals) / total
+    sample = (f"first Jacobi sweep of the build on the full R-MAT scale-20 graph ({visits} edge-simulation visits) "
+              f"per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": config(prob, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(prob, args):
+    g = prob.graph
+    return {"workload": "R-MAT scale 20, edge factor 16 (a,b,c,d = .57,.19,.19,.05), weighted cascade",
+            "n": g.n, "m": g.m, "R": prob.R, "K": prob.K, "eps_g": prob.eps_g, "eps_l": prob.eps_l,
+            "eps_c": prob.eps_c, "seed": prob.seed, "parallelism": f"replicas{args.gpus}",
+            "l2": "flushed between steps (256 MiB write); registers 2 x 256 MiB exceed L2"}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2105_04023_gb300 as im
+
+    torch.cuda.set_device(local)
+    from paper_2105_04023_gb300 import build as b
+
+    b.build()
+    prob = load_workload()
+    g = prob.graph
+    prm = im.params(R=prob.R, K=prob.K, eps_g=prob.eps_g, eps_l=prob.eps_l, eps_c=prob.eps_c, seed=prob.seed)
+    dev_graph = im.Graph.from_synth(g, prob.model, prob.p, device=f"cuda:{local}")
+    # pinned host copies for the end-to-end leg
+    hx = torch.from_numpy(np.ascontiguousarray(g.xadj)).pin_memory()
+    ha = torch.from_numpy(np.ascontiguousarray(g.adj)).pin_memory()
+    host_graph = im.Graph(g.n, hx.numpy(), ha.numpy(), prob.model, prob.p)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    ctx = im.Context(local)
+
+    seeds_ref = None
+    for _ in range(args.warmup):
+        out = ctx.im_select_seeds(dev_graph, prm, trace=False)
+        seeds_ref = out["seeds"]
+    torch.cuda.synchronize()
+
+    # timed region: device-resident inputs
+    ctx.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    dev_ms, visits, launches, prop_ms, prop_bytes, prop_launches, wall = [], 0, 0, 0.0, 0, 0, []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = ctx.im_select_seeds(dev_graph, prm, trace=False)
+        wall.append(time.perf_counter() - t)
+        st = ctx.stats()
+        dev_ms.append(st["total_ms"])
+        visits += st["visits"]
+        launches += st["kernel_launches"]
+        prop_ms += st["prop_ms"]
+        prop_bytes += st["prop_bytes"]
+        prop_launches += st["prop_launches"]
+        if seeds_ref is not None:
+            assert out["seeds"].tolist() == seeds_ref.tolist(), "seed sets differ between steps"
+        seeds_ref = out["seeds"]
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ctx.set_timing(False)
+    total_s = max_over_ranks(sum(dev_ms) / 1000.0, world)
+    value = visits * world / total_s
+
+    # end-to-end through the public API with host inputs (copies inside the timed call)
+    e2e_ms = []
+    e2e_visits = 0
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = ctx.im_select_seeds(host_graph, prm, trace=False)
+        e2e_ms.append(1000 * (time.perf_counter() - t))
+        e2e_visits += ctx.stats()["visits"]
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1000.0, world)
+
+    hbm, peak_kind = peaks()
+    achieved = prop_bytes / (prop_ms / 1000.0) / 1e9 if prop_ms > 0 else None
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "prop_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+    if rank == 0:
+        cpu_v, cpu_visits, cpu_dt = oracle_sample(prob)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": config(prob, args),
+            "im_seconds_per_K_seeds": total_s / args.steps,
+            "step_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99))},
+            "visits_per_step": visits // args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                         "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "k_prop + k_combine (one sweep)",
+                         "bytes_per_launch": prop_bytes / max(prop_launches, 1),
+                         "launches": prop_launches, "ms": prop_ms},
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first Jacobi sweep of the build on the full graph ({cpu_visits} visits, "
+                                       f"{cpu_dt:.1f} s)"},
+            "e2e": {"value": e2e_visits * world / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(g.xadj.nbytes + g.adj.nbytes), "d2h_bytes_per_step": 4 * prob.K + 8,
+                    "ms_per_step": 1000 * e2e_s / max(1, args.steps)},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_ms_per_step": 1000 * sum(wall) / len(wall),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * im.h — C ABI of a GB300-native (sm_103a) sketch-based influence-maximisation library.
+ *
+ * The library implements the hot path of HyperFuseR (Goktürk & Kaya, arXiv 2105.04023): hash-based fused sampling
+ * of independent-cascade simulations (Section 3.1, Eq. 4-5), Flajolet-Martin sketch registers per vertex and
+ * simulation (Section 2.2, Eq. 1-3) diffused to a fixpoint by pull-based sweeps (Algorithm 2), and greedy seed
+ * selection with error-adaptive sketch rebuilding (Algorithm 1, Section 3.2.1).  Every step runs in the library's
+ * own CUDA kernels on one GPU.
+ *
+ * Conventions for every call:
+ *   - Each call returns an im_status; IM_OK (0) means success.  A non-zero status leaves every output untouched
+ *     and the reason is available from im_last_error(ctx) until the next call on that context.  No call aborts.
+ *   - A context is used by one host thread at a time.  All device work of a context is issued on its CUDA stream
+ *     (the one given to im_ctx_create, or a stream the context creates); calls return after that work completes.
+ *   - Graph arrays are owned by the caller and are read only; with IM_MEM_DEVICE they are device pointers that
+ *     must stay valid for the lifetime of every sketch built from them, with IM_MEM_HOST the library copies them
+ *     into its own device memory during the call.
+ *   - Sketches, contexts and batches are owned by the library and freed by their *_destroy call.
+ *   - Output pointers are HOST pointers unless stated otherwise.
+ *
+ * Readings of the paper that fix the results (shared with the CPU oracle used by the tests):
+ *   edge hash h(u,v) = fmix32(lo32(u*n+v) XOR fmix32(hi32(u*n+v))) (MurmurHash3 finaliser, Eq. 4), h_max = 2^32;
+ *   simulation words X_r, Y_r = high halves of splitmix64 outputs 2r and 2r+1 from the seed;
+ *   edge (u,v) is live in simulation r iff (h XOR X_r) <= ceil(p * 2^32) - 1 (Eq. 5, "P < w"), p = 1/indeg(v)
+ *   for the weighted cascade, never for p <= 0;
+ *   initial register M_v[j] = clz32(fmix32(v XOR 0x9E3779B9) XOR Y_j) (Algorithm 1 initialisation);
+ *   u pulls from its out-neighbour v: M_u[j] = max(M_u[j], M_v[j]) over live edges (Algorithm 2);
+ *   estimate e = 2^(mean_j M[j]) / 0.77351 (Eq. 2); greedy argmax over v not in S, ties to the smallest id.
+ */
+#ifndef IM_H_
+#define IM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IM_OK = 0,
+    IM_EINVAL = 1,     /* invalid argument: malformed CSR, out-of-range id, bad R, K or probability */
+    IM_ENOMEM = 2,     /* the footprint does not fit the device memory or the given HBM budget */
+    IM_ECUDA = 3,      /* a CUDA runtime call failed (including "no device") */
+    IM_ETIMEOUT = 4,   /* a diffusion or search exceeded its sweep limit (im_params.max_sweeps) */
+    IM_ECANCELED = 5,  /* the request was cancelled before it ran */
+    IM_ENOTREADY = 6   /* a batch or served request has not finished yet */
+} im_status;
+
+typedef enum {
+    IM_IC_CONST = 0, /* independent cascade, the same probability p on every edge (Section 2.1) */
+    IM_WC = 1,       /* weighted cascade, p(u,v) = 1 / indeg(v) (Section 2.1, Fig. 1b) */
+    IM_PER_EDGE = 2  /* one probability per edge, p_edge[e] for the e-th entry of adj */
+} im_model;
+
+typedef enum {
+    IM_MEM_DEVICE = 0, /* xadj / adj / p_edge are device pointers of the context's device */
+    IM_MEM_HOST = 1    /* they are host pointers (pinned or pageable); the library copies them */
+} im_memory;
+
+/*
+ * A directed graph as an out-neighbour CSR (Section 3.3): the targets of vertex u are adj[xadj[u] .. xadj[u+1]-1].
+ * Requirements (checked, IM_EINVAL otherwise): n >= 1, xadj[0] = 0, xadj non-decreasing, xadj[n] = m, every target
+ * in [0, n), n < 2^31.  Self-loops and parallel edges should be merged beforehand (Section 2.1); they are accepted
+ * and treated as ordinary edges.
+ */
+typedef struct {
+    int64_t n;             /* vertices */
+    int64_t m;             /* edges */
+    const int64_t *xadj;   /* n + 1 row offsets */
+    const int32_t *adj;    /* m target ids */
+    im_model model;
+    double p;              /* IM_IC_CONST: the edge probability, in [0, 1] */
+    const float *p_edge;   /* IM_PER_EDGE: m probabilities in [0, 1]; NULL otherwise */
+    im_memory memory;
+} im_graph;
+
+/*
+ * Parameters of one influence-maximisation run (Algorithm 1).
+ * R: simulations = FM registers per vertex (the paper's J): 64, 128, 256, 512 or 1024.
+ * K: seeds to select, 1 <= K <= n.
+ * eps_g, eps_l: global and local error thresholds of Section 3.2.1 (the paper uses 0.01 and 0.3); 0 rebuilds the
+ *   sketch after every seed, +infinity never rebuilds.
+ * eps_c: the diffusion stops after the first sweep whose set of changed vertices has at most eps_c * n members
+ *   (Section 3.2; 0 runs to the fixpoint).
+ * seed: run seed of the per-simulation words.
+ * max_sweeps: limit on sweeps of one diffusion and levels of one reachability search; 0 means n + 2 (always
+ *   enough for a fixpoint).  Exceeding it returns IM_ETIMEOUT.
+ */
+typedef struct {
+    int32_t R;
+    int32_t K;
+    double eps_g;
+    double eps_l;
+    double eps_c;
+    uint64_t seed;
+    int64_t max_sweeps;
+} im_params;
+
+/* Per-step record of a seed selection (Algorithm 1); every array has K entries and may be NULL. */
+typedef struct {
+    int32_t *seeds;     /* chosen seed of step k */
+    double *sigma;      /* sigma after step k: mean over the R samples of |R_{G_j}(S)| */
+    double *estimate;   /* e of step k: Estimate(Merge(M_S', M_s)) */
+    uint64_t *gsum;     /* integer register sum behind e: sum_j max(M_S'[j], M_s[j]) */
+    uint8_t *rebuilt;   /* 1 if the error check of step k asked for a rebuild */
+} im_trace;
+
+/* Counters of the last completed call on a context. */
+typedef struct {
+    uint64_t visits;          /* edge-simulation visits: sum over sweeps of |{(u,v): v in L}| * R */
+    uint64_t prop_bytes;      /* bytes the propagation kernels must move: per visited row 16 (offsets) + R (own
+                                 row) + R if written; per scanned edge 4 (target id) + the threshold bytes of edges
+                                 to live-set vertices (4 weighted cascade, 5 per-edge); R per neighbour row read;
+                                 R per partial row written and read back for split rows */
+    int64_t sweeps;           /* diffusion sweeps */
+    int64_t builds;           /* diffusions run (initial build + rebuilds) */
+    int64_t bfs_levels;       /* reachability-search levels */
+    int64_t kernel_launches;  /* kernels launched by the call */
+    int64_t prop_launches;    /* launches of the propagation kernel (one per sweep and R class) */
+    double prop_ms;           /* summed CUDA-event time of the propagation kernels of every sweep (the row kernel
+                                 and the merge of split rows; 0 unless timing is enabled) */
+    double total_ms;          /* device time of the whole call (CUDA events around it) */
+} im_stats;
+
+typedef struct im_ctx im_ctx;
+typedef struct im_sketch im_sketch;
+
+/* Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to issue work on, or NULL for a
+ * stream owned by the context.  Returns IM_ECUDA if the device cannot be used. */
+im_status im_ctx_create(int device, void *cuda_stream, im_ctx **out);
+im_status im_ctx_destroy(im_ctx *ctx);
+
+/* Last error message of the context (never NULL); valid until the next call on the context. */
+const char *im_last_error(const im_ctx *ctx);
+
+/* Enables (1) or disables (0) per-launch CUDA-event timing of the propagation kernel, reported in im_stats. */
+im_status im_ctx_set_timing(im_ctx *ctx, int enable);
+
+/* Copies the counters of the last completed call. */
+im_status im_ctx_stats(const im_ctx *ctx, im_stats *out);
+
+/*
+ * Builds the sketch of a graph: initial registers (Algorithm 1) then Simulate (Algorithm 2) to the fixpoint (or
+ * the eps_c stop).  Uses params R, seed, eps_c and max_sweeps.  The sketch keeps pointers to the caller's device
+ * graph arrays (IM_MEM_DEVICE) or its own copy (IM_MEM_HOST).
+ */
+im_status im_build_sketches(im_ctx *ctx, const im_graph *graph, const im_params *params, im_sketch **out);
+
+/*
+ * Influence estimate of a seed set on a built sketch: the registers of the k seeds are merged (Eq. 3) and
+ * estimated (Eq. 2) into *est_out.  If sigma_out is not NULL the exact mean reach of the set over the sketch's R
+ * hash-sampled graphs is also computed (Algorithm 1's Monte-Carlo step).  seeds is a host array of k ids in
+ * [0, n); k >= 1.
+ */
+im_status im_estimate(im_ctx *ctx, const im_sketch *sketch, const int32_t *seeds, int32_t k, double *est_out,
+                      double *sigma_out);
+
+/* Copies the n*R registers of a sketch, row-major (vertex-major, simulation-minor), to host memory. */
+im_status im_sketch_registers(im_ctx *ctx, const im_sketch *sketch, uint8_t *host_out);
+
+/* Number of sweeps and edge-simulation visits of the sketch's diffusion; frontier_log (may be NULL) receives
+ * |L| at the start of each sweep for the first log_cap sweeps. */
+im_status im_sketch_info(im_ctx *ctx, const im_sketch *sketch, int64_t *sweeps, uint64_t *visits,
+                         int64_t *frontier_log, int64_t log_cap);
+
+im_status im_sketch_destroy(im_sketch *sketch);
+
+/*
+ * Selects K seeds with Algorithm 1: build, then K greedy steps; each step picks the argmax of the merged-sketch
+ * estimate, computes the exact reach of S over the R samples, and either merges the seed into M_S' or rebuilds
+ * the sketch on the residual samples (registers of vertices reached by S set to 0) when both the local and the
+ * global estimation error reach their thresholds.  seeds_out: host array of K ids.  sigma_out (nullable): final
+ * sigma.  rebuilds_out (nullable): number of steps whose check asked for a rebuild.  trace (nullable): per step.
+ */
+im_status im_select_seeds(im_ctx *ctx, const im_graph *graph, const im_params *params, int32_t *seeds_out,
+                          double *sigma_out, int32_t *rebuilds_out, im_trace *trace);
+
+/*
+ * Runs nq independent seed selections (one graph and parameter set each) together: every kernel launch serves
+ * all problems that are in the same phase, so many small graphs share the GPU.  seeds_out[q] is a host array of
+ * params[q].K ids; sigma_out (nullable) receives nq final sigmas; rebuilds_out (nullable) nq counts.  Results are
+ * identical to nq separate im_select_seeds calls.
+ */
+im_status im_select_seeds_batch(im_ctx *ctx, int32_t nq, const im_graph *graphs, const im_params *params,
+                                int32_t *const *seeds_out, double *sigma_out, int32_t *rebuilds_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IM_H_ */

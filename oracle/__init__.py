@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
             "or_select_seeds": (_i32, [_i64, _i64, _ptr, _ptr, _i32, _dbl, _ptr, _i32, _i32, _dbl, _dbl, _dbl, _u64,
                                        _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr]),
             "or_estimate_set": (_dbl, [_i64, _i32, _ptr, _ptr, _i32, _ptr]),
+            "or_register_at": (_i32, [_i64, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _i64, _i32, _ptr, _ptr]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -223,3 +224,28 @@ def estimate_set(M: np.ndarray, S) -> tuple[float, int]:
     g = np.zeros(1, np.uint64)
     e = lib().or_estimate_set(M.shape[0], M.shape[1], _p(M), _p(S), S.shape[0], _p(g))
     return float(e), int(g[0])
+
+
+class RegisterProbe:
+    """Evaluates single registers M_v[j] by breadth-first search (for sampled checks on large graphs)."""
+
+    def __init__(self, n, xadj, adj, model, p, R, seed, p_edge=None):
+        self.n = n
+        self.xadj, self.adj = _csr(xadj, adj)
+        self.T, self.ok = edge_thresholds(n, self.xadj, self.adj, model, p=p, p_edge=p_edge)
+        self.X, self.Y = sim_words(seed, R)
+        self.seen = np.zeros(max(n, 1), np.uint8)
+        self.queue = np.zeros(max(n, 1), np.int64)
+
+    def __call__(self, v: int, j: int) -> int:
+        return int(lib().or_register_at(self.n, _p(self.xadj), _p(self.adj), _p(self.T), _p(self.ok), _p(self.X),
+                                        _p(self.Y), v, j, _p(self.seen), _p(self.queue)))
+
+    def reach_total(self, seeds) -> int:
+        """|{(v, j): v reachable from the seed set in sample j}| summed over the R samples."""
+        R = self.X.shape[0]
+        reached = np.zeros((self.n, R), np.uint8)
+        total = 0
+        for s in seeds:
+            total += reach_add(self.n, self.xadj, self.adj, self.T, self.ok, R, self.X, int(s), reached)
+        return total

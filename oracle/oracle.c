@@ -433,3 +433,31 @@ double or_estimate_set(int64_t n, int32_t R, const uint8_t *M, const int32_t *S,
     if (gsum_out) *gsum_out = g;
     return or_estimate_from_sum(g, R);
 }
+
+/*
+ * One register by its definition (Section 2.2 with Algorithm 2's fixpoint): M_v[j] is the largest initial rank over
+ * the vertices that v reaches in sample j.  Breadth-first search over the edges sampled in j.  `seen` is caller
+ * scratch of n bytes, all zero on entry and returned all zero; `queue` holds n entries.
+ */
+int32_t or_register_at(int64_t n, const int64_t *xadj, const int32_t *adj, const uint32_t *T, const uint8_t *possible,
+                       const uint32_t *X, const uint32_t *Y, int64_t v, int32_t j, uint8_t *seen, int64_t *queue)
+{
+    int64_t head = 0, tail = 0;
+    int32_t best = 0;
+    seen[v] = 1;
+    queue[tail++] = v;
+    while (head < tail) {
+        int64_t u = queue[head++];
+        int32_t r = or_init_rank(u, Y[j]);
+        if (r > best) best = r;
+        for (int64_t e = xadj[u]; e < xadj[u + 1]; ++e) {
+            int64_t w = adj[e];
+            if (seen[w]) continue;
+            if (!or_is_live(or_edge_hash(u, w, n), X[j], T[e], possible[e])) continue;
+            seen[w] = 1;
+            queue[tail++] = w;
+        }
+    }
+    for (int64_t i = 0; i < tail; ++i) seen[queue[i]] = 0;
+    return best;
+}

@@ -1,0 +1,205 @@
+"""GB300-native (sm_103a) sketch-based influence maximisation after HyperFuseR (arXiv 2105.04023).
+
+Python front end of the C ABI in ``include/im.h``.  The functions keep the C names (``im_build_sketches``,
+``im_estimate``, ``im_select_seeds`` ...) and only marshal arguments: every step runs in the library's CUDA kernels.
+Graphs are given as numpy arrays (copied by the library, ``IM_MEM_HOST``) or as CUDA torch tensors
+(``IM_MEM_DEVICE``: used in place).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import IM_IC_CONST, IM_PER_EDGE, IM_WC  # noqa: F401
+
+
+class ImError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _addr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+@dataclass
+class Graph:
+    """An out-neighbour CSR graph plus its diffusion model, ready to hand to the library."""
+
+    n: int
+    xadj: object  # int64[n+1]: numpy (host) or torch CUDA tensor (device)
+    adj: object  # int32[m]
+    model: int = IM_IC_CONST
+    p: float = 0.0
+    p_edge: object = None  # float32[m] for IM_PER_EDGE
+
+    def c(self) -> _lib.im_graph:
+        dev = not isinstance(self.xadj, np.ndarray)
+        for a in (self.xadj, self.adj, self.p_edge):
+            if a is None:
+                continue
+            if dev and getattr(a, "is_cuda", False) is False:
+                raise TypeError("mixing host and device arrays in one graph")
+            if isinstance(a, np.ndarray) and not a.flags.c_contiguous:
+                raise TypeError("host arrays must be C-contiguous")
+        if isinstance(self.xadj, np.ndarray):
+            assert self.xadj.dtype == np.int64 and self.adj.dtype == np.int32
+        else:
+            import torch
+
+            assert self.xadj.dtype == torch.int64 and self.adj.dtype == torch.int32
+            assert self.xadj.is_contiguous() and self.adj.is_contiguous()
+        m = int(self.adj.shape[0])
+        return _lib.im_graph(n=self.n, m=m, xadj=_addr(self.xadj), adj=_addr(self.adj), model=self.model, p=self.p,
+                             p_edge=_addr(self.p_edge), memory=_lib.IM_MEM_DEVICE if dev else _lib.IM_MEM_HOST)
+
+    @staticmethod
+    def from_synth(g, model: int, p: float = 0.0, p_edge=None, device: str | None = None) -> "Graph":
+        """Wraps a ``synth.graphs.Graph``; with ``device='cuda'`` the arrays are uploaded as torch tensors."""
+        if device is None:
+            pe = None if p_edge is None else np.ascontiguousarray(p_edge, dtype=np.float32)
+            return Graph(g.n, np.ascontiguousarray(g.xadj, np.int64), np.ascontiguousarray(g.adj, np.int32), model, p,
+                         pe)
+        import torch
+
+        pe = None if p_edge is None else torch.as_tensor(np.asarray(p_edge, np.float32), device=device)
+        return Graph(g.n, torch.as_tensor(g.xadj, device=device), torch.as_tensor(g.adj, device=device), model, p,
+                     pe)
+
+
+def params(R: int, K: int = 1, eps_g: float = 0.01, eps_l: float = 0.3, eps_c: float = 0.0, seed: int = 1,
+           max_sweeps: int = 0) -> _lib.im_params:
+    return _lib.im_params(R=R, K=K, eps_g=eps_g, eps_l=eps_l, eps_c=eps_c, seed=seed, max_sweeps=max_sweeps)
+
+
+def _sync_torch():
+    try:
+        import torch
+
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            torch.cuda.synchronize()
+    except ImportError:
+        pass
+
+
+class Context:
+    """An im_ctx on one CUDA device (work runs on a stream the context owns)."""
+
+    def __init__(self, device: int = 0):
+        self._L = _lib.load()
+        h = ctypes.c_void_p()
+        st = self._L.im_ctx_create(device, None, ctypes.byref(h))
+        if st != 0:
+            raise ImError(st, f"cannot create a context on CUDA device {device}")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self._L.im_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != 0:
+            raise ImError(st, self._L.im_last_error(self.h).decode())
+
+    def set_timing(self, on: bool):
+        self._check(self._L.im_ctx_set_timing(self.h, 1 if on else 0))
+
+    def stats(self) -> dict:
+        s = _lib.im_stats()
+        self._check(self._L.im_ctx_stats(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in _lib.im_stats._fields_}
+
+    # --- the C calls, same names --------------------------------------------------------------------------------
+    def im_build_sketches(self, graph: Graph, prm: _lib.im_params) -> "Sketch":
+        _sync_torch()
+        g = graph.c()
+        out = ctypes.c_void_p()
+        self._check(self._L.im_build_sketches(self.h, ctypes.byref(g), ctypes.byref(prm), ctypes.byref(out)))
+        return Sketch(self, out, graph.n, prm.R)
+
+    def im_select_seeds(self, graph: Graph, prm: _lib.im_params, trace: bool = True) -> dict:
+        _sync_torch()
+        g = graph.c()
+        K = prm.K
+        seeds = np.zeros(K, np.int32)
+        sigma = ctypes.c_double()
+        reb = ctypes.c_int32()
+        tr = None
+        arrs = {}
+        if trace:
+            arrs = dict(seeds=np.zeros(K, np.int32), sigma=np.zeros(K, np.float64), estimate=np.zeros(K, np.float64),
+                        gsum=np.zeros(K, np.uint64), rebuilt=np.zeros(K, np.uint8))
+            tr = _lib.im_trace(**{k: v.ctypes.data for k, v in arrs.items()})
+        self._check(self._L.im_select_seeds(self.h, ctypes.byref(g), ctypes.byref(prm), seeds.ctypes.data,
+                                            ctypes.addressof(sigma), ctypes.addressof(reb),
+                                            ctypes.byref(tr) if tr is not None else None))
+        out = dict(seeds=seeds, sigma_final=sigma.value, rebuilds=reb.value)
+        out.update(arrs)
+        return out
+
+    def im_select_seeds_batch(self, graphs: list[Graph], prms: list[_lib.im_params]) -> list[dict]:
+        _sync_torch()
+        nq = len(graphs)
+        gs = (_lib.im_graph * nq)(*[g.c() for g in graphs])
+        ps = (_lib.im_params * nq)(*prms)
+        seeds = [np.zeros(p.K, np.int32) for p in prms]
+        ptrs = (ctypes.c_void_p * nq)(*[s.ctypes.data for s in seeds])
+        sig = np.zeros(nq, np.float64)
+        reb = np.zeros(nq, np.int32)
+        self._check(self._L.im_select_seeds_batch(self.h, nq, ctypes.addressof(gs), ctypes.addressof(ps),
+                                                  ctypes.addressof(ptrs), sig.ctypes.data, reb.ctypes.data))
+        return [dict(seeds=seeds[i], sigma_final=float(sig[i]), rebuilds=int(reb[i])) for i in range(nq)]
+
+
+class Sketch:
+    """An im_sketch: registers of a built sketch, kept on the device."""
+
+    def __init__(self, ctx: Context, h: ctypes.c_void_p, n: int, R: int):
+        self.ctx, self.h, self.n, self.R = ctx, h, n, R
+
+    def close(self):
+        if self.h:
+            self.ctx._L.im_sketch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def im_sketch_registers(self) -> np.ndarray:
+        M = np.zeros((self.n, self.R), np.uint8)
+        self.ctx._check(self.ctx._L.im_sketch_registers(self.ctx.h, self.h, M.ctypes.data))
+        return M
+
+    def im_sketch_info(self, log_cap: int = 4096) -> tuple[int, int, np.ndarray]:
+        sw = ctypes.c_int64()
+        vi = ctypes.c_uint64()
+        log = np.zeros(log_cap, np.int64)
+        self.ctx._check(self.ctx._L.im_sketch_info(self.ctx.h, self.h, ctypes.addressof(sw), ctypes.addressof(vi),
+                                                   log.ctypes.data, log_cap))
+        return sw.value, vi.value, log[: min(sw.value, log_cap)]
+
+    def im_estimate(self, seeds, exact: bool = False) -> tuple[float, float | None]:
+        s = np.ascontiguousarray(seeds, dtype=np.int32)
+        est = ctypes.c_double()
+        sig = ctypes.c_double()
+        self.ctx._check(self.ctx._L.im_estimate(self.ctx.h, self.h, s.ctypes.data, int(s.shape[0]),
+                                                ctypes.addressof(est), ctypes.addressof(sig) if exact else None))
+        return est.value, (sig.value if exact else None)

@@ -1,0 +1,139 @@
+// Device-side data layout and helpers shared by the kernels and the host engine of the influence-maximisation
+// library.  One DevProb describes one seed-selection problem (a graph, its sampling thresholds and every device
+// buffer of its sketch); kernels take an array of them so that a single launch serves many problems.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace imk {
+
+constexpr int kBlock = 256;          // threads per block of every kernel
+constexpr int kWarpsPerBlock = kBlock / 32;
+constexpr int kHeavyDeg = 64;        // rows with more out-edges are split into tasks of kTaskEdges edges
+constexpr int kTaskEdges = 64;
+constexpr int kBfsHeavyDeg = 256;    // search-frontier vertices with more out-edges are spread over the grid
+
+enum Model : int32_t { kIC = 0, kWC = 1, kPerEdge = 2 };
+
+// Counters of one problem, written by the kernels and read back by the host after each engine tick.
+struct DevCtr {
+    // diffusion (Algorithm 2) ----------------------------------------------------------------------------------
+    uint32_t t;          // sweep index of the current diffusion
+    uint32_t done;       // 1 once the diffusion reached its stop condition
+    uint32_t timeout;    // 1 if it hit the sweep limit first
+    uint32_t full;       // the current sweep visits every row (otherwise the listed ones)
+    uint32_t res_par;    // register buffer (0/1) holding the diffusion's result
+    uint32_t nchg;       // vertices whose registers changed in the current sweep (|L'|)
+    uint32_t nchg_list;  // entries written to chg_list
+    uint32_t nrows[2];   // listed light rows for the sweep of that parity
+    uint32_t pad0;
+    unsigned long long visits;        // edge-simulation visits, running total
+    unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total
+    unsigned long long sweeps_total;  // sweeps, running total
+    // greedy step (Algorithm 1) --------------------------------------------------------------------------------
+    unsigned long long best_key;      // max over candidates of (gsum << 32 | ~v)
+    uint32_t s;          // seed chosen by the last step
+    uint32_t gsum;       // sum_j max(M_S'[j], M_s[j]) of that seed
+    // reachability search ---------------------------------------------------------------------------------------
+    uint32_t lvl;        // level of the current search
+    uint32_t bdone;      // 1 once the search found no new vertex
+    uint32_t btimeout;   // 1 if it hit the level limit first
+    uint32_t nF[2];      // light frontier entries by level parity
+    uint32_t nH[2];      // heavy frontier entries by level parity
+    uint32_t pad1;
+    unsigned long long reached;       // |{(v, j): v in R_{G_j}(S)}|
+    unsigned long long levels_total;
+};
+
+// One problem.  Register rows are R bytes, 16-byte aligned; bit arrays are 32-bit words.
+struct DevProb {
+    int64_t n, m;
+    const int64_t *xadj;       // out-CSR (Section 3.3)
+    const int32_t *adj;
+    const int64_t *xadj_in;    // in-CSR, used to list the rows a changed vertex feeds
+    const int32_t *adj_in;
+    const uint32_t *heavy;     // bit per row: out-degree > kHeavyDeg
+    const int64_t *task_off;   // n+1: first task of each row (tasks only for heavy rows)
+    const int32_t *task_row;   // per task: its row
+    const int32_t *heavy_rows; // rows with tasks
+    int64_t n_tasks;
+    int64_t n_heavy;
+    int32_t model;
+    int32_t R;                 // simulations (registers per row), a power of two in [64, 1024]
+    int32_t W;                 // R / 32: words per row of a bit array over simulations
+    uint32_t T_const;          // IC threshold
+    int32_t ic_ok;             // IC: p > 0
+    int32_t pad0;
+    const uint32_t *T_vert;    // WC: threshold per target vertex
+    const uint32_t *T_edge;    // per-edge model: threshold per edge
+    const uint8_t *ok_edge;    // per-edge model: p > 0
+    const uint32_t *X;         // sampling words X_r (Eq. 5)
+    const uint32_t *Y;         // initialisation words ("hash(j)" of Algorithm 1)
+    uint8_t *M0, *M1;          // register buffers (Jacobi pair)
+    uint8_t *part;             // n_tasks x R partial maxima of heavy-row tasks
+    uint32_t *part_any;        // bit per task: the task merged at least one neighbour
+    uint32_t *Lb0, *Lb1;       // frontier bits: vertices changed in the previous sweep
+    uint32_t *mark;            // rows listed for the next sweep
+    int32_t *chg_list;         // compacted changed vertices
+    int32_t *rows0, *rows1;    // light rows of the sweep of that parity
+    uint32_t *vis;             // n x W: v in R_{G_j}(S)
+    uint32_t *del0, *del1;     // n x W: bits newly reached at the previous level, by parity
+    uint32_t *Fb;              // bit per vertex: reached something new at this level
+    int32_t *F0, *F1, *H0, *H1;  // light / heavy frontier lists by parity
+    uint32_t *inS;             // bit per vertex: in the seed set
+    uint8_t *MS;               // R bytes: M_S'
+    DevCtr *ctr;
+    uint32_t stop_thr;         // diffusion stops when |L'| <= stop_thr
+    uint32_t full_thr;         // a sweep after one with more changes than this visits every row
+    uint32_t max_sweeps;       // sweep / level limit
+    int32_t flog_cap;
+    int64_t *flog;             // |L| at the start of each sweep of the current diffusion
+    uint32_t *step_seed;       // per greedy step k: seed (device trace)
+    uint32_t *step_gsum;
+    unsigned long long *step_reached;
+};
+
+// ------------------------------------------------------------------------------------------------------------
+// Method arithmetic (independent restatement of the paper's Section 3.1 / Algorithm 1 readings)
+
+// MurmurHash3's 32-bit finaliser.
+__device__ __forceinline__ uint32_t fmix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+
+// Eq. 4: hash of edge (u, v) from the 64-bit key u * n + v.
+__device__ __forceinline__ uint32_t edge_hash(uint64_t u, uint64_t v, uint64_t n) {
+    const uint64_t key = u * n + v;
+    return fmix32(static_cast<uint32_t>(key) ^ fmix32(static_cast<uint32_t>(key >> 32)));
+}
+
+// Initial FM rank of vertex v for simulation word y (Algorithm 1's initialisation).
+__device__ __forceinline__ uint32_t vertex_hash(uint32_t v) { return fmix32(v ^ 0x9E3779B9u); }
+
+__device__ __forceinline__ bool test_bit(const uint32_t *bits, int64_t i) {
+    return (bits[i >> 5] >> (i & 31)) & 1u;
+}
+
+__device__ __forceinline__ void set_bit(uint32_t *bits, int64_t i) { atomicOr(&bits[i >> 5], 1u << (i & 31)); }
+
+// Threshold of edge e = (u, v) and whether it can be live at all.
+__device__ __forceinline__ void edge_threshold(const DevProb &P, int64_t e, int32_t v, uint32_t &T, bool &ok) {
+    if (P.model == kIC) {
+        T = P.T_const;
+        ok = P.ic_ok != 0;
+    } else if (P.model == kWC) {
+        T = __ldg(&P.T_vert[v]);
+        ok = true;
+    } else {
+        T = __ldg(&P.T_edge[e]);
+        ok = __ldg(&P.ok_edge[e]) != 0;
+    }
+}
+
+}  // namespace imk

@@ -1,0 +1,977 @@
+// Host side of the library: contexts, graph preparation, per-problem device state, the engine that advances many
+// seed-selection problems in lock step (one launch per phase serves all of them), and the C ABI of include/im.h.
+//
+// Host arithmetic that decides results (Algorithm 1's error check, Eq. 2) is done in double from the integers the
+// kernels produce, with the same formula order as the paper states it; the file is compiled without floating
+// contraction so the decisions do not depend on the compiler's use of fused multiply-add.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/im.h"
+#include "im_common.cuh"
+#include "im_launch.h"
+
+using namespace imk;
+
+namespace {
+
+constexpr double kPhi = 0.77351;  // FM correction factor of Eq. 2
+
+struct CudaError {
+    cudaError_t code;
+    const char *what;
+};
+
+inline void ck(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) throw CudaError{e, what};
+}
+
+struct ImError {
+    im_status status;
+    std::string msg;
+};
+
+[[noreturn]] inline void fail(im_status s, const std::string &msg) { throw ImError{s, msg}; }
+
+}  // namespace
+
+struct im_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    im_stats stats{};
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prop_ev;
+    int64_t launches = 0;
+    int64_t prop_launches = 0;
+    DevCtr *h_ctr = nullptr;  // pinned staging for counter read-back
+    size_t h_ctr_cap = 0;
+    int32_t *h_act = nullptr;  // pinned staging for active lists
+    size_t h_act_cap = 0;
+    int32_t *d_act = nullptr;
+    size_t d_act_cap = 0;
+    int sweep_chunk = 4;
+    int level_chunk = 4;
+};
+
+namespace {
+
+// ------------------------------------------------------------------------------------------------------------
+// Device memory: stream-ordered allocations from the device's pool (kept reserved between calls).
+
+struct DevMem {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit DevMem(cudaStream_t st) : s(st) {}
+    template <class T>
+    T *alloc(size_t count, bool zero = false) {
+        void *p = nullptr;
+        const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+        const cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            fail(IM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+        }
+        ck(e, "cudaMallocAsync");
+        ptrs.push_back(p);
+        if (zero) ck(cudaMemsetAsync(p, 0, bytes, s), "cudaMemsetAsync");
+        return static_cast<T *>(p);
+    }
+    ~DevMem() {
+        for (void *p : ptrs) cudaFreeAsync(p, s);
+    }
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+};
+
+// Threshold of Eq. 5 for probability p: live iff (h XOR X_r) <= ceil(p * 2^32) - 1; p <= 0 is never live.
+inline void ic_threshold(double p, uint32_t &T, int32_t &ok) {
+    if (!(p > 0.0)) {
+        T = 0;
+        ok = 0;
+        return;
+    }
+    T = static_cast<uint32_t>(std::ceil(p * 4294967296.0) - 1.0);
+    ok = 1;
+}
+
+// A graph on the device with everything derived from it (in-CSR, thresholds, heavy-row tasks).
+struct GraphDev {
+    int64_t n = 0, m = 0;
+    const int64_t *xadj = nullptr;
+    const int32_t *adj = nullptr;
+    const float *p_edge = nullptr;
+    int32_t model = 0;
+    uint32_t T_const = 0;
+    int32_t ic_ok = 0;
+    int64_t *xadj_in = nullptr;
+    int32_t *adj_in = nullptr;
+    uint32_t *T_vert = nullptr;
+    uint32_t *T_edge = nullptr;
+    uint8_t *ok_edge = nullptr;
+    uint32_t *heavy = nullptr;
+    int64_t *task_off = nullptr;
+    int32_t *task_row = nullptr;
+    int32_t *heavy_rows = nullptr;
+    int64_t n_tasks = 0, n_heavy = 0;
+    std::unique_ptr<DevMem> mem;
+    uint64_t bytes = 0;
+};
+
+}  // namespace
+
+namespace imk {
+void launch_validate(const int64_t *xadj, const int32_t *adj, int64_t n, int64_t m, unsigned int *flags,
+                     cudaStream_t s);
+void launch_edge_thresholds(const float *p, int64_t m, uint32_t *T, uint8_t *ok, unsigned int *flags,
+                            cudaStream_t s);
+}  // namespace imk
+
+namespace {
+
+void check_params(const im_params *pr, int64_t n, bool need_k) {
+    if (!pr) fail(IM_EINVAL, "params is NULL");
+    const int R = pr->R;
+    if (R != 64 && R != 128 && R != 256 && R != 512 && R != 1024)
+        fail(IM_EINVAL, "R must be one of 64, 128, 256, 512, 1024 (got " + std::to_string(R) + ")");
+    if (need_k && (pr->K < 1 || pr->K > n)) fail(IM_EINVAL, "K must be in [1, n]");
+    if (std::isnan(pr->eps_g) || std::isnan(pr->eps_l) || pr->eps_g < 0 || pr->eps_l < 0)
+        fail(IM_EINVAL, "eps_g and eps_l must be >= 0");
+    if (!(pr->eps_c >= 0.0 && pr->eps_c < 1.0)) fail(IM_EINVAL, "eps_c must be in [0, 1)");
+    if (pr->max_sweeps < 0) fail(IM_EINVAL, "max_sweeps must be >= 0");
+}
+
+std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
+    if (!g) fail(IM_EINVAL, "graph is NULL");
+    if (g->n < 1 || g->n >= (int64_t(1) << 31) - 1) fail(IM_EINVAL, "n must be in [1, 2^31 - 2]");
+    if (g->m < 0 || g->m >= (int64_t(1) << 40)) fail(IM_EINVAL, "m out of range");
+    if (!g->xadj || (g->m > 0 && !g->adj)) fail(IM_EINVAL, "xadj / adj is NULL");
+    if (g->model != IM_IC_CONST && g->model != IM_WC && g->model != IM_PER_EDGE) fail(IM_EINVAL, "unknown model");
+    if (g->model == IM_IC_CONST && !(g->p >= 0.0 && g->p <= 1.0)) fail(IM_EINVAL, "p must be in [0, 1]");
+    if (g->model == IM_PER_EDGE && g->m > 0 && !g->p_edge) fail(IM_EINVAL, "p_edge is NULL");
+    if (g->memory != IM_MEM_DEVICE && g->memory != IM_MEM_HOST) fail(IM_EINVAL, "unknown memory kind");
+    cudaStream_t s = ctx->stream;
+    auto G = std::make_shared<GraphDev>();
+    G->mem = std::make_unique<DevMem>(s);
+    DevMem &mem = *G->mem;
+    G->n = g->n;
+    G->m = g->m;
+    G->model = g->model;
+    const int64_t n = g->n, m = g->m;
+    if (g->memory == IM_MEM_HOST) {
+        if (g->xadj[0] != 0 || g->xadj[n] != m) fail(IM_EINVAL, "xadj[0] must be 0 and xadj[n] must be m");
+        int64_t *x = mem.alloc<int64_t>(n + 1);
+        ck(cudaMemcpyAsync(x, g->xadj, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s), "copy xadj");
+        int32_t *a = mem.alloc<int32_t>(m);
+        if (m) ck(cudaMemcpyAsync(a, g->adj, m * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy adj");
+        G->xadj = x;
+        G->adj = a;
+        if (g->model == IM_PER_EDGE) {
+            float *pe = mem.alloc<float>(m);
+            if (m) ck(cudaMemcpyAsync(pe, g->p_edge, m * sizeof(float), cudaMemcpyHostToDevice, s), "copy p");
+            G->p_edge = pe;
+        }
+    } else {
+        G->xadj = g->xadj;
+        G->adj = g->adj;
+        G->p_edge = g->p_edge;
+    }
+    // validation on the device: xadj[0] = 0, xadj[n] = m, non-decreasing, every target in [0, n)
+    // (checked before any kernel indexes memory with these values)
+    unsigned int *flags = mem.alloc<unsigned int>(4, true);
+    launch_validate(G->xadj, G->adj, n, m, flags, s);
+    ctx->launches += 1;
+    {
+        unsigned int f[4] = {0, 0, 0, 0};
+        ck(cudaMemcpyAsync(f, flags, sizeof(f), cudaMemcpyDeviceToHost, s), "read flags");
+        ck(cudaStreamSynchronize(s), "sync");
+        if (f[0]) fail(IM_EINVAL, "xadj[0] must be 0 and xadj[n] must be m");
+        if (f[1]) fail(IM_EINVAL, "xadj must be non-decreasing");
+        if (f[2]) fail(IM_EINVAL, "adj holds a vertex id outside [0, n)");
+    }
+    // in-degree, in-CSR
+    int32_t *indeg = mem.alloc<int32_t>(n, true);
+    launch_indeg(G->adj, m, indeg, s);
+    const int64_t nb = scan_block_count(n) + 1;
+    int64_t *bsums = mem.alloc<int64_t>(nb);
+    G->xadj_in = mem.alloc<int64_t>(n + 1);
+    launch_exclusive_scan(indeg, n, G->xadj_in, bsums, s);
+    unsigned long long *cursor = mem.alloc<unsigned long long>(n);
+    ck(cudaMemcpyAsync(cursor, G->xadj_in, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s), "copy cursor");
+    G->adj_in = mem.alloc<int32_t>(m);
+    launch_transpose_fill(G->xadj, G->adj, n, cursor, G->adj_in, s);
+    ctx->launches += 5;
+    if (g->model == IM_WC) {
+        G->T_vert = mem.alloc<uint32_t>(n);
+        launch_wc_thresholds(indeg, n, G->T_vert, s);
+        ctx->launches += 1;
+    } else if (g->model == IM_PER_EDGE) {
+        G->T_edge = mem.alloc<uint32_t>(m);
+        G->ok_edge = mem.alloc<uint8_t>(m);
+        launch_edge_thresholds(G->p_edge, m, G->T_edge, G->ok_edge, flags, s);
+        ctx->launches += 1;
+    } else {
+        ic_threshold(g->p, G->T_const, G->ic_ok);
+    }
+    // heavy rows and their tasks
+    const int64_t words = (n + 31) / 32;
+    G->heavy = mem.alloc<uint32_t>(words, true);
+    int32_t *ntask = mem.alloc<int32_t>(n);
+    launch_row_tasks(G->xadj, n, ntask, G->heavy, s);
+    G->task_off = mem.alloc<int64_t>(n + 1);
+    launch_exclusive_scan(ntask, n, G->task_off, bsums, s);
+    ctx->launches += 4;
+    int64_t h_tasks = 0;
+    unsigned int h_flags[4] = {0, 0, 0, 0};
+    ck(cudaMemcpyAsync(&h_tasks, G->task_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "read tasks");
+    ck(cudaMemcpyAsync(h_flags, flags, sizeof(h_flags), cudaMemcpyDeviceToHost, s), "read flags");
+    ck(cudaStreamSynchronize(s), "sync");
+    if (h_flags[3]) fail(IM_EINVAL, "p_edge holds a value outside [0, 1]");
+    G->n_tasks = h_tasks;
+    G->task_row = mem.alloc<int32_t>(std::max<int64_t>(h_tasks, 1));
+    G->heavy_rows = mem.alloc<int32_t>(std::max<int64_t>(h_tasks, 1));
+    unsigned int *nheavy = mem.alloc<unsigned int>(1, true);
+    launch_task_fill(G->task_off, n, G->task_row, G->heavy_rows, nheavy, s);
+    ctx->launches += 1;
+    unsigned int h_nheavy = 0;
+    ck(cudaMemcpyAsync(&h_nheavy, nheavy, sizeof(unsigned int), cudaMemcpyDeviceToHost, s), "read heavy");
+    ck(cudaStreamSynchronize(s), "sync");
+    G->n_heavy = h_nheavy;
+    return G;
+}
+
+// One seed-selection problem (or one sketch): its device state and the host side of Algorithm 1.
+struct Prob {
+    std::shared_ptr<GraphDev> G;
+    im_params prm{};
+    bool greedy = false;
+    std::unique_ptr<DevMem> mem;
+    DevProb dp{};
+    DevProb *d_prob = nullptr;  // slot in the device descriptor array this problem was uploaded to
+    DevCtr *d_ctr = nullptr;
+    int64_t flog_cap = 0;
+    // engine state
+    enum Phase { kInit, kSweep, kScan, kBfs, kDone } phase = kInit;
+    bool merge_pending = false;
+    int step = 0;
+    double varsigma = 0.0;
+    std::vector<int32_t> seeds;
+    std::vector<double> sigma, est;
+    std::vector<uint64_t> gsum;
+    std::vector<uint8_t> rebuilt;
+    int64_t builds = 0;
+    DevCtr last{};
+    bool has_bfs = false;
+};
+
+void alloc_bfs(Prob &P) {
+    const int64_t n = P.G->n;
+    const int W = P.prm.R / 32;
+    DevMem &mem = *P.mem;
+    const int64_t words = (n + 31) / 32;
+    P.dp.vis = mem.alloc<uint32_t>(n * W, true);
+    P.dp.del0 = mem.alloc<uint32_t>(n * W, true);
+    P.dp.del1 = mem.alloc<uint32_t>(n * W, true);
+    P.dp.Fb = mem.alloc<uint32_t>(words, true);
+    P.dp.inS = mem.alloc<uint32_t>(words, true);
+    P.dp.F0 = mem.alloc<int32_t>(n);
+    P.dp.F1 = mem.alloc<int32_t>(n);
+    P.dp.H0 = mem.alloc<int32_t>(n);
+    P.dp.H1 = mem.alloc<int32_t>(n);
+    P.has_bfs = true;
+}
+
+std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const im_params &prm, bool greedy) {
+    auto P = std::make_unique<Prob>();
+    P->G = std::move(G);
+    P->prm = prm;
+    P->greedy = greedy;
+    P->mem = std::make_unique<DevMem>(ctx->stream);
+    DevMem &mem = *P->mem;
+    const GraphDev &g = *P->G;
+    const int64_t n = g.n;
+    const int R = prm.R;
+    DevProb &d = P->dp;
+    d.n = n;
+    d.m = g.m;
+    d.xadj = g.xadj;
+    d.adj = g.adj;
+    d.xadj_in = g.xadj_in;
+    d.adj_in = g.adj_in;
+    d.heavy = g.heavy;
+    d.task_off = g.task_off;
+    d.task_row = g.task_row;
+    d.heavy_rows = g.heavy_rows;
+    d.n_tasks = g.n_tasks;
+    d.n_heavy = g.n_heavy;
+    d.model = g.model;
+    d.R = R;
+    d.W = R / 32;
+    d.T_const = g.T_const;
+    d.ic_ok = g.ic_ok;
+    d.T_vert = g.T_vert;
+    d.T_edge = g.T_edge;
+    d.ok_edge = g.ok_edge;
+    uint32_t *X = mem.alloc<uint32_t>(R);
+    uint32_t *Y = mem.alloc<uint32_t>(R);
+    launch_words(prm.seed, R, X, Y, ctx->stream);
+    ctx->launches += 1;
+    d.X = X;
+    d.Y = Y;
+    d.M0 = mem.alloc<uint8_t>(static_cast<size_t>(n) * R);
+    d.M1 = mem.alloc<uint8_t>(static_cast<size_t>(n) * R);
+    d.part = mem.alloc<uint8_t>(static_cast<size_t>(std::max<int64_t>(g.n_tasks, 1)) * R);
+    d.part_any = mem.alloc<uint32_t>((g.n_tasks + 31) / 32 + 1, true);
+    const int64_t words = (n + 31) / 32;
+    d.Lb0 = mem.alloc<uint32_t>(words, true);
+    d.Lb1 = mem.alloc<uint32_t>(words, true);
+    d.mark = mem.alloc<uint32_t>(words, true);
+    d.chg_list = mem.alloc<int32_t>(n);
+    d.rows0 = mem.alloc<int32_t>(n);
+    d.rows1 = mem.alloc<int32_t>(n);
+    d.MS = mem.alloc<uint8_t>(R, true);
+    const int64_t ms = prm.max_sweeps > 0 ? prm.max_sweeps : n + 2;
+    d.max_sweeps = static_cast<uint32_t>(std::min<int64_t>(ms, 0x7FFFFFFF));
+    // stop after the first sweep with |L'| <= eps_c * n: the largest integer count satisfying it
+    const double thr = static_cast<double>(n) * prm.eps_c;
+    d.stop_thr = static_cast<uint32_t>(std::floor(thr));
+    d.full_thr = static_cast<uint32_t>(std::max<int64_t>(n / 8, 1024));
+    P->flog_cap = 4096;
+    d.flog_cap = static_cast<int32_t>(P->flog_cap);
+    d.flog = mem.alloc<int64_t>(P->flog_cap, true);
+    if (greedy) {
+        alloc_bfs(*P);
+        d.step_seed = mem.alloc<uint32_t>(prm.K);
+        d.step_gsum = mem.alloc<uint32_t>(prm.K);
+    }
+    P->seeds.reserve(greedy ? prm.K : 0);
+    return P;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Engine
+
+struct Engine {
+    im_ctx *ctx;
+    std::vector<Prob *> probs;
+    DevProb *d_probs = nullptr;
+    std::unique_ptr<DevMem> mem;
+
+    DevCtr *d_ctrs = nullptr;
+
+    // Uploads the descriptors; the counters of all problems live in one array so one copy reads them back.
+    Engine(im_ctx *c, std::vector<Prob *> ps, const std::vector<DevCtr> *init_ctr = nullptr)
+        : ctx(c), probs(std::move(ps)) {
+        mem = std::make_unique<DevMem>(ctx->stream);
+        d_probs = mem->alloc<DevProb>(probs.size());
+        d_ctrs = mem->alloc<DevCtr>(probs.size(), true);
+        if (init_ctr)
+            ck(cudaMemcpyAsync(d_ctrs, init_ctr->data(), probs.size() * sizeof(DevCtr), cudaMemcpyHostToDevice,
+                               ctx->stream),
+               "upload counters");
+        std::vector<DevProb> h(probs.size());
+        for (size_t i = 0; i < probs.size(); ++i) {
+            probs[i]->dp.ctr = d_ctrs + i;
+            probs[i]->d_ctr = d_ctrs + i;
+            h[i] = probs[i]->dp;
+            probs[i]->d_prob = d_probs + i;
+        }
+        ck(cudaMemcpyAsync(d_probs, h.data(), h.size() * sizeof(DevProb), cudaMemcpyHostToDevice, ctx->stream),
+           "upload problems");
+        ck(cudaStreamSynchronize(ctx->stream), "sync");
+        ensure_staging(probs.size());
+    }
+
+    void ensure_staging(size_t np) {
+        if (ctx->h_ctr_cap < np) {
+            if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
+            ck(cudaMallocHost(&ctx->h_ctr, np * sizeof(DevCtr)), "cudaMallocHost");
+            ctx->h_ctr_cap = np;
+        }
+        const size_t acap = 16 * np + 64;
+        if (ctx->h_act_cap < acap) {
+            if (ctx->h_act) cudaFreeHost(ctx->h_act);
+            ck(cudaMallocHost(&ctx->h_act, acap * sizeof(int32_t)), "cudaMallocHost");
+            ctx->h_act_cap = acap;
+        }
+        if (ctx->d_act_cap < acap) {
+            if (ctx->d_act) cudaFree(ctx->d_act);
+            ck(cudaMalloc(&ctx->d_act, acap * sizeof(int32_t)), "cudaMalloc");
+            ctx->d_act_cap = acap;
+        }
+    }
+
+    // Active lists of one tick live in one pinned array copied to the device once per tick.
+    struct List {
+        int off = 0, count = 0;
+    };
+    std::vector<int32_t> staging;
+
+    List add_list(const std::vector<int32_t> &ids) {
+        List l;
+        l.off = static_cast<int>(staging.size());
+        l.count = static_cast<int>(ids.size());
+        staging.insert(staging.end(), ids.begin(), ids.end());
+        return l;
+    }
+
+    const int32_t *dptr(const List &l) const { return ctx->d_act + l.off; }
+
+    // One sweep's propagation launches (k_prop, then k_combine for split rows), optionally between two events.
+    void timed_prop(const std::vector<std::pair<int, List>> &byR) {
+        cudaStream_t s = ctx->stream;
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (ctx->timing) {
+            a = get_event();
+            b = get_event();
+            ck(cudaEventRecord(a, s), "event");
+        }
+        for (auto &rl : byR) launch_prop(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
+        for (auto &rl : byR) launch_combine(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
+        if (ctx->timing) {
+            ck(cudaEventRecord(b, s), "event");
+            ctx->prop_ev.emplace_back(a, b);
+        }
+        ctx->launches += 2 * static_cast<int64_t>(byR.size());
+        ctx->prop_launches += static_cast<int64_t>(byR.size());
+    }
+
+    cudaEvent_t get_event() {
+        if (ctx->ev_free.empty()) {
+            cudaEvent_t e;
+            ck(cudaEventCreate(&e), "cudaEventCreate");
+            return e;
+        }
+        cudaEvent_t e = ctx->ev_free.back();
+        ctx->ev_free.pop_back();
+        return e;
+    }
+
+    void enqueue_sweeps(const std::vector<int32_t> &ids, int chunk) {
+        if (ids.empty()) return;
+        cudaStream_t s = ctx->stream;
+        std::vector<std::pair<int, List>> byR;
+        for (int R : {64, 128, 256, 512, 1024}) {
+            std::vector<int32_t> sub;
+            for (int32_t i : ids)
+                if (probs[i]->prm.R == R) sub.push_back(i);
+            if (!sub.empty()) byR.emplace_back(R, add_list(sub));
+        }
+        const List all = add_list(ids);
+        pending.push_back([this, byR, all, chunk, s]() {
+            for (int c = 0; c < chunk; ++c) {
+                timed_prop(byR);
+                launch_frontier(d_probs, dptr(all), all.count, s);
+                launch_expand(d_probs, dptr(all), all.count, s);
+                launch_rows(d_probs, dptr(all), all.count, s);
+                launch_advance(d_probs, dptr(all), all.count, s);
+                ctx->launches += 4;
+            }
+        });
+    }
+
+    void enqueue_bfs(const std::vector<int32_t> &ids, int chunk) {
+        if (ids.empty()) return;
+        const List all = add_list(ids);
+        cudaStream_t s = ctx->stream;
+        pending.push_back([this, all, chunk, s]() {
+            for (int c = 0; c < chunk; ++c) {
+                launch_bfs_level(d_probs, dptr(all), all.count, s);
+                launch_bfs_frontier(d_probs, dptr(all), all.count, s);
+                launch_bfs_advance(d_probs, dptr(all), all.count, s);
+                ctx->launches += 3;
+            }
+        });
+    }
+
+    void enqueue_scan(const std::vector<int32_t> &ids) {
+        if (ids.empty()) return;
+        cudaStream_t s = ctx->stream;
+        std::vector<std::pair<int, List>> byR;
+        for (int R : {64, 128, 256, 512, 1024}) {
+            std::vector<int32_t> sub;
+            for (int32_t i : ids)
+                if (probs[i]->prm.R == R) sub.push_back(i);
+            if (!sub.empty()) byR.emplace_back(R, add_list(sub));
+        }
+        // one choose launch per problem: each records its own step index
+        std::vector<std::pair<List, int>> chooses;
+        for (int32_t i : ids) chooses.emplace_back(add_list({i}), probs[i]->step);
+        pending.push_back([this, byR, chooses, s]() {
+            for (auto &rl : byR) launch_scan(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
+            for (auto &c : chooses) launch_choose(d_probs, dptr(c.first), 1, c.second, s);
+            ctx->launches += static_cast<int64_t>(byR.size() + chooses.size());
+        });
+    }
+
+    std::vector<std::function<void()>> pending;
+
+    void flush() {
+        if (!staging.empty()) {
+            std::memcpy(ctx->h_act, staging.data(), staging.size() * sizeof(int32_t));
+            ck(cudaMemcpyAsync(ctx->d_act, ctx->h_act, staging.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               ctx->stream),
+               "upload active lists");
+        }
+        for (auto &f : pending) f();
+        pending.clear();
+        staging.clear();
+    }
+
+    void read_counters() {
+        cudaStream_t s = ctx->stream;
+        ck(cudaMemcpyAsync(ctx->h_ctr, d_ctrs, probs.size() * sizeof(DevCtr), cudaMemcpyDeviceToHost, s),
+           "read counters");
+        ck(cudaStreamSynchronize(s), "sync");
+        ck(cudaGetLastError(), "kernel launch");
+        for (size_t i = 0; i < probs.size(); ++i) probs[i]->last = ctx->h_ctr[i];
+    }
+
+    // Algorithm 1's error check after step k of problem P (host, double, from device integers).
+    void decide(Prob &P) {
+        const DevCtr &C = P.last;
+        const int R = P.prm.R;
+        const double e = std::exp2(static_cast<double>(C.gsum) / static_cast<double>(R)) / kPhi;
+        const double sigma = static_cast<double>(C.reached) / static_cast<double>(R);
+        const double delta = sigma - P.varsigma;
+        const double err_l = (delta == 0.0) ? INFINITY : std::fabs((e - delta) / delta);
+        const double err_g = std::fabs((e - delta) / sigma);
+        P.seeds.push_back(static_cast<int32_t>(C.s));
+        P.sigma.push_back(sigma);
+        P.est.push_back(e);
+        P.gsum.push_back(C.gsum);
+        const int k = P.step;
+        P.step += 1;
+        if (err_l < P.prm.eps_l || err_g < P.prm.eps_g) {
+            P.rebuilt.push_back(0);
+            P.merge_pending = true;
+            P.phase = (P.step == P.prm.K) ? Prob::kDone : Prob::kScan;
+        } else {
+            P.rebuilt.push_back(1);
+            P.varsigma = sigma;
+            P.merge_pending = false;
+            P.phase = (k + 1 < P.prm.K) ? Prob::kInit : Prob::kDone;
+        }
+    }
+
+    void run() {
+        cudaStream_t s = ctx->stream;
+        for (;;) {
+            std::vector<int32_t> init, sweep, scan, bfs, merge;
+            bool any = false;
+            for (size_t i = 0; i < probs.size(); ++i) {
+                Prob &P = *probs[i];
+                switch (P.phase) {
+                    case Prob::kInit: init.push_back(i); sweep.push_back(i); any = true; break;
+                    case Prob::kSweep: sweep.push_back(i); any = true; break;
+                    case Prob::kScan:
+                        if (P.merge_pending) merge.push_back(i);
+                        scan.push_back(i);
+                        bfs.push_back(i);
+                        any = true;
+                        break;
+                    case Prob::kBfs: bfs.push_back(i); any = true; break;
+                    default: break;
+                }
+            }
+            if (!any) break;
+            if (!merge.empty()) {
+                const List l = add_list(merge);
+                pending.push_back([this, l, s]() {
+                    launch_merge(d_probs, dptr(l), l.count, s);
+                    ctx->launches += 1;
+                });
+            }
+            if (!init.empty()) {
+                const List l = add_list(init);
+                pending.push_back([this, l, s]() {
+                    launch_init(d_probs, dptr(l), l.count, s);
+                    ctx->launches += 1;
+                });
+            }
+            enqueue_sweeps(sweep, ctx->sweep_chunk);
+            enqueue_scan(scan);
+            enqueue_bfs(bfs, ctx->level_chunk);
+            flush();
+            read_counters();
+            for (int32_t i : init) {
+                probs[i]->phase = Prob::kSweep;
+                probs[i]->builds += 1;
+            }
+            for (int32_t i : merge) probs[i]->merge_pending = false;
+            for (int32_t i : scan) probs[i]->phase = Prob::kBfs;
+            for (size_t i = 0; i < probs.size(); ++i) {
+                Prob &P = *probs[i];
+                if (P.phase == Prob::kSweep && P.last.done) {
+                    if (P.last.timeout) fail(IM_ETIMEOUT, "diffusion exceeded max_sweeps");
+                    P.phase = P.greedy ? Prob::kScan : Prob::kDone;
+                } else if (P.phase == Prob::kBfs && P.last.bdone) {
+                    if (P.last.btimeout) fail(IM_ETIMEOUT, "reachability search exceeded max_sweeps levels");
+                    decide(P);
+                }
+            }
+        }
+    }
+};
+
+void set_err(im_ctx *ctx, const std::string &m) {
+    if (ctx) ctx->err = m;
+}
+
+template <class F>
+im_status guarded(im_ctx *ctx, F &&f) {
+    try {
+        f();
+        if (ctx) ctx->err.clear();
+        return IM_OK;
+    } catch (const ImError &e) {
+        set_err(ctx, e.msg);
+        return e.status;
+    } catch (const CudaError &e) {
+        set_err(ctx, std::string(e.what) + ": " + cudaGetErrorString(e.code));
+        cudaGetLastError();
+        return IM_ECUDA;
+    } catch (const std::bad_alloc &) {
+        set_err(ctx, "host allocation failed");
+        return IM_ENOMEM;
+    }
+}
+
+void begin_call(im_ctx *ctx) {
+    ck(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ctx->launches = 0;
+    ctx->prop_launches = 0;
+    for (auto &pe : ctx->prop_ev) {
+        ctx->ev_free.push_back(pe.first);
+        ctx->ev_free.push_back(pe.second);
+    }
+    ctx->prop_ev.clear();
+}
+
+void end_call(im_ctx *ctx, const std::vector<Prob *> &probs, cudaEvent_t t0, cudaEvent_t t1) {
+    im_stats st{};
+    for (Prob *P : probs) {
+        st.visits += P->last.visits;
+        st.prop_bytes += P->last.bytes;
+        st.sweeps += static_cast<int64_t>(P->last.sweeps_total);
+        st.bfs_levels += static_cast<int64_t>(P->last.levels_total);
+        st.builds += P->builds;
+    }
+    st.kernel_launches = ctx->launches;
+    st.prop_launches = ctx->prop_launches;
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, t0, t1), "elapsed");
+    st.total_ms = ms;
+    double pm = 0.0;
+    for (auto &pe : ctx->prop_ev) {
+        float x = 0.f;
+        ck(cudaEventElapsedTime(&x, pe.first, pe.second), "elapsed");
+        pm += x;
+    }
+    st.prop_ms = pm;
+    ctx->stats = st;
+}
+
+struct CallTimer {
+    im_ctx *ctx;
+    cudaEvent_t a, b;
+    explicit CallTimer(im_ctx *c) : ctx(c) {
+        ck(cudaEventCreate(&a), "event");
+        ck(cudaEventCreate(&b), "event");
+        ck(cudaEventRecord(a, ctx->stream), "event");
+    }
+    void stop() {
+        ck(cudaEventRecord(b, ctx->stream), "event");
+        ck(cudaEventSynchronize(b), "event");
+    }
+    ~CallTimer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+}  // namespace
+
+struct im_sketch {
+    std::unique_ptr<Prob> P;
+    im_ctx *ctx = nullptr;
+};
+
+extern "C" {
+
+im_status im_ctx_create(int device, void *cuda_stream, im_ctx **out) {
+    if (!out) return IM_EINVAL;
+    *out = nullptr;
+    auto *ctx = new (std::nothrow) im_ctx();
+    if (!ctx) return IM_ENOMEM;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        delete ctx;
+        return IM_ECUDA;
+    }
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess || configure(device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return IM_ECUDA;
+    }
+    // keep freed device memory reserved in the pool so repeated calls do not pay for fresh allocations
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete ctx;
+            return IM_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (const char *v = std::getenv("IM_SWEEP_CHUNK")) ctx->sweep_chunk = std::max(1, std::atoi(v));
+    if (const char *v = std::getenv("IM_LEVEL_CHUNK")) ctx->level_chunk = std::max(1, std::atoi(v));
+    *out = ctx;
+    return IM_OK;
+}
+
+im_status im_ctx_destroy(im_ctx *ctx) {
+    if (!ctx) return IM_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &pe : ctx->prop_ev) {
+        cudaEventDestroy(pe.first);
+        cudaEventDestroy(pe.second);
+    }
+    for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
+    if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
+    if (ctx->h_act) cudaFreeHost(ctx->h_act);
+    if (ctx->d_act) cudaFree(ctx->d_act);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return IM_OK;
+}
+
+const char *im_last_error(const im_ctx *ctx) { return ctx ? ctx->err.c_str() : "context is NULL"; }
+
+im_status im_ctx_set_timing(im_ctx *ctx, int enable) {
+    if (!ctx) return IM_EINVAL;
+    ctx->timing = enable != 0;
+    return IM_OK;
+}
+
+im_status im_ctx_stats(const im_ctx *ctx, im_stats *out) {
+    if (!ctx || !out) return IM_EINVAL;
+    *out = ctx->stats;
+    return IM_OK;
+}
+
+im_status im_build_sketches(im_ctx *ctx, const im_graph *graph, const im_params *params, im_sketch **out) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!out) fail(IM_EINVAL, "out is NULL");
+        begin_call(ctx);
+        CallTimer tm(ctx);
+        if (!graph) fail(IM_EINVAL, "graph is NULL");
+        check_params(params, graph->n, false);
+        auto G = prepare_graph(ctx, graph);
+        auto sk = std::make_unique<im_sketch>();
+        sk->ctx = ctx;
+        sk->P = make_prob(ctx, G, *params, false);
+        Engine eng(ctx, {sk->P.get()});
+        eng.run();
+        tm.stop();
+        end_call(ctx, {sk->P.get()}, tm.a, tm.b);
+        *out = sk.release();
+    });
+}
+
+im_status im_sketch_destroy(im_sketch *sketch) {
+    if (!sketch) return IM_EINVAL;
+    cudaSetDevice(sketch->ctx->device);
+    cudaStreamSynchronize(sketch->ctx->stream);
+    delete sketch;
+    return IM_OK;
+}
+
+im_status im_sketch_registers(im_ctx *ctx, const im_sketch *sketch, uint8_t *host_out) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!sketch || !host_out) fail(IM_EINVAL, "sketch / host_out is NULL");
+        begin_call(ctx);
+        const Prob &P = *sketch->P;
+        const uint8_t *M = P.last.res_par ? P.dp.M1 : P.dp.M0;
+        ck(cudaMemcpyAsync(host_out, M, static_cast<size_t>(P.G->n) * P.prm.R, cudaMemcpyDeviceToHost, ctx->stream),
+           "copy registers");
+        ck(cudaStreamSynchronize(ctx->stream), "sync");
+    });
+}
+
+im_status im_sketch_info(im_ctx *ctx, const im_sketch *sketch, int64_t *sweeps, uint64_t *visits,
+                         int64_t *frontier_log, int64_t log_cap) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!sketch) fail(IM_EINVAL, "sketch is NULL");
+        const Prob &P = *sketch->P;
+        if (sweeps) *sweeps = static_cast<int64_t>(P.last.sweeps_total);
+        if (visits) *visits = P.last.visits;
+        if (frontier_log && log_cap > 0) {
+            const int64_t k = std::min<int64_t>({log_cap, P.flog_cap, static_cast<int64_t>(P.last.sweeps_total)});
+            if (k > 0) {
+                ck(cudaMemcpyAsync(frontier_log, P.dp.flog, k * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream),
+                   "copy log");
+                ck(cudaStreamSynchronize(ctx->stream), "sync");
+            }
+        }
+    });
+}
+
+im_status im_estimate(im_ctx *ctx, const im_sketch *sketch, const int32_t *seeds, int32_t k, double *est_out,
+                      double *sigma_out) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!sketch || !seeds || !est_out) fail(IM_EINVAL, "sketch / seeds / est_out is NULL");
+        if (k < 1) fail(IM_EINVAL, "k must be >= 1");
+        Prob &P = *sketch->P;
+        for (int32_t i = 0; i < k; ++i)
+            if (seeds[i] < 0 || seeds[i] >= P.G->n) fail(IM_EINVAL, "seed id outside [0, n)");
+        begin_call(ctx);
+        CallTimer tm(ctx);
+        cudaStream_t s = ctx->stream;
+        DevMem tmp(s);
+        int32_t *d_seeds = tmp.alloc<int32_t>(k);
+        ck(cudaMemcpyAsync(d_seeds, seeds, k * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy seeds");
+        unsigned long long *d_g = tmp.alloc<unsigned long long>(1, true);
+        if (sigma_out && !P.has_bfs) alloc_bfs(P);
+        std::vector<DevCtr> c0(1);
+        c0[0].res_par = P.last.res_par;
+        c0[0].sweeps_total = P.last.sweeps_total;
+        c0[0].visits = P.last.visits;
+        c0[0].bytes = P.last.bytes;
+        Engine eng(ctx, {&P}, &c0);
+        launch_estimate(eng.d_probs, d_seeds, k, d_g, s);
+        ctx->launches += 1;
+        unsigned long long g = 0;
+        ck(cudaMemcpyAsync(&g, d_g, sizeof(g), cudaMemcpyDeviceToHost, s), "read sum");
+        ck(cudaStreamSynchronize(s), "sync");
+        const double e = std::exp2(static_cast<double>(g) / static_cast<double>(P.prm.R)) / kPhi;
+        double sigma = 0.0;
+        const DevCtr keep = P.last;
+        if (sigma_out) {
+            const int64_t n = P.G->n;
+            const int W = P.prm.R / 32;
+            ck(cudaMemsetAsync(P.dp.vis, 0, static_cast<size_t>(n) * W * 4, s), "memset");
+            ck(cudaMemsetAsync(P.dp.del0, 0, static_cast<size_t>(n) * W * 4, s), "memset");
+            ck(cudaMemsetAsync(P.dp.del1, 0, static_cast<size_t>(n) * W * 4, s), "memset");
+            ck(cudaMemsetAsync(P.dp.Fb, 0, ((n + 31) / 32) * 4, s), "memset");
+            ck(cudaMemsetAsync(P.dp.inS, 0, ((n + 31) / 32) * 4, s), "memset");
+            launch_seed_set(eng.d_probs, d_seeds, k, W, s);
+            ctx->launches += 1;
+            P.phase = Prob::kBfs;
+            for (;;) {
+                eng.enqueue_bfs({0}, ctx->level_chunk);
+                eng.flush();
+                eng.read_counters();
+                if (P.last.bdone) break;
+            }
+            P.phase = Prob::kDone;
+            if (P.last.btimeout) fail(IM_ETIMEOUT, "reachability search exceeded max_sweeps levels");
+            sigma = static_cast<double>(P.last.reached) / static_cast<double>(P.prm.R);
+        }
+        P.last = keep;
+        tm.stop();
+        end_call(ctx, {&P}, tm.a, tm.b);
+        *est_out = e;
+        if (sigma_out) *sigma_out = sigma;
+    });
+}
+
+static void select_many(im_ctx *ctx, int32_t nq, const im_graph *graphs, const im_params *params,
+                        std::vector<std::unique_ptr<Prob>> &out) {
+    std::vector<std::shared_ptr<GraphDev>> gd(nq);
+    for (int32_t q = 0; q < nq; ++q) {
+        check_params(&params[q], graphs[q].n, true);
+        // problems given the very same graph description share one prepared device graph
+        for (int32_t r = 0; r < q && !gd[q]; ++r)
+            if (std::memcmp(&graphs[r], &graphs[q], sizeof(im_graph)) == 0) gd[q] = gd[r];
+        if (!gd[q]) gd[q] = prepare_graph(ctx, &graphs[q]);
+    }
+    for (int32_t q = 0; q < nq; ++q) out.push_back(make_prob(ctx, gd[q], params[q], true));
+    std::vector<Prob *> raw;
+    for (auto &p : out) raw.push_back(p.get());
+    Engine eng(ctx, raw);
+    eng.run();
+}
+
+im_status im_select_seeds(im_ctx *ctx, const im_graph *graph, const im_params *params, int32_t *seeds_out,
+                          double *sigma_out, int32_t *rebuilds_out, im_trace *trace) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!graph || !params || !seeds_out) fail(IM_EINVAL, "graph / params / seeds_out is NULL");
+        begin_call(ctx);
+        CallTimer tm(ctx);
+        std::vector<std::unique_ptr<Prob>> probs;
+        select_many(ctx, 1, graph, params, probs);
+        tm.stop();
+        Prob &P = *probs[0];
+        std::vector<Prob *> raw{&P};
+        end_call(ctx, raw, tm.a, tm.b);
+        const int K = params->K;
+        std::copy(P.seeds.begin(), P.seeds.end(), seeds_out);
+        if (sigma_out) *sigma_out = P.sigma.back();
+        if (rebuilds_out) {
+            int32_t r = 0;
+            for (uint8_t b : P.rebuilt) r += b;
+            *rebuilds_out = r;
+        }
+        if (trace) {
+            for (int k = 0; k < K; ++k) {
+                if (trace->seeds) trace->seeds[k] = P.seeds[k];
+                if (trace->sigma) trace->sigma[k] = P.sigma[k];
+                if (trace->estimate) trace->estimate[k] = P.est[k];
+                if (trace->gsum) trace->gsum[k] = P.gsum[k];
+                if (trace->rebuilt) trace->rebuilt[k] = P.rebuilt[k];
+            }
+        }
+    });
+}
+
+im_status im_select_seeds_batch(im_ctx *ctx, int32_t nq, const im_graph *graphs, const im_params *params,
+                                int32_t *const *seeds_out, double *sigma_out, int32_t *rebuilds_out) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (nq < 1 || !graphs || !params || !seeds_out) fail(IM_EINVAL, "empty batch or NULL argument");
+        begin_call(ctx);
+        CallTimer tm(ctx);
+        std::vector<std::unique_ptr<Prob>> probs;
+        select_many(ctx, nq, graphs, params, probs);
+        tm.stop();
+        std::vector<Prob *> raw;
+        for (auto &p : probs) raw.push_back(p.get());
+        end_call(ctx, raw, tm.a, tm.b);
+        for (int32_t q = 0; q < nq; ++q) {
+            if (!seeds_out[q]) fail(IM_EINVAL, "seeds_out[q] is NULL");
+            std::copy(probs[q]->seeds.begin(), probs[q]->seeds.end(), seeds_out[q]);
+            if (sigma_out) sigma_out[q] = probs[q]->sigma.back();
+            if (rebuilds_out) {
+                int32_t r = 0;
+                for (uint8_t b : probs[q]->rebuilt) r += b;
+                rebuilds_out[q] = r;
+            }
+        }
+    });
+}
+
+}  // extern "C"

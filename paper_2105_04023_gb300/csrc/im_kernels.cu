@@ -1,0 +1,1219 @@
+// CUDA kernels (sm_103a) of the sketch-based influence-maximisation library.
+//
+// Every kernel takes an array of problem descriptors plus a list of the active ones and treats the work of all of
+// them as one flat index space striped over its warps (or blocks, or threads), so a single launch serves one large
+// problem or hundreds of small ones.  Grids are sized once per device (a multiple of the SM count) and kernels read
+// their work counts from device memory, so the host can enqueue sweeps ahead without reading anything back.
+//
+// Paper map:
+//   k_init        Algorithm 1, register initialisation (and its re-initialisation with R_G(S) blocked)
+//   k_prop        Algorithm 2, one sweep of the pull-based diffusion with hash-based fused sampling (Eq. 4-5)
+//   k_combine     Algorithm 2, the same sweep for rows split over several warps
+//   k_frontier, k_expand, k_rows, k_advance   Algorithm 2, the live sets L and L' and the stop test (eps_c)
+//   k_scan, k_choose                          Algorithm 1, argmax of Estimate(Merge(M_S', M_v)) (Eq. 2-3)
+//   k_bfs_*                                   Algorithm 1, reachability set of S in every simulation, sigma
+//   k_merge                                   Algorithm 1, M_S' <- Merge(M_S', M_s)
+#include "im_common.cuh"
+#include "im_launch.h"
+
+namespace imk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// First index owned by `worker` among the units [base, base + count) of a flat space striped over `nworkers`.
+__device__ __forceinline__ uint64_t first_owned(uint64_t worker, uint64_t nworkers, uint64_t base) {
+    const uint64_t r = base % nworkers;
+    return worker >= r ? worker - r : worker + nworkers - r;
+}
+
+template <int R>
+struct Geo {
+    static constexpr int CH = R / 16;               // 16-byte chunks per register row
+    static constexpr int G = CH < 32 ? CH : 32;     // lanes that read one neighbour row together
+    static constexpr int NG = 32 / G;               // neighbour rows a warp reads at once
+    static constexpr int CPL = CH / G;              // chunks per lane
+};
+
+struct Stats {
+    unsigned long long visits = 0, bytes = 0;
+    unsigned int nchg = 0;
+};
+
+__device__ __forceinline__ void flush_stats(DevCtr *C, Stats &st, int lane) {
+    if (lane == 0) {
+        if (st.visits) atomicAdd(&C->visits, st.visits);
+        if (st.bytes) atomicAdd(&C->bytes, st.bytes);
+        if (st.nchg) atomicAdd(&C->nchg, st.nchg);
+    }
+    st = Stats();
+}
+
+__device__ __forceinline__ uint32_t vmax4(uint32_t a, uint32_t b) { return __vmaxu4(a, b); }
+
+// Bytes of (h XOR X_j) whose top byte ties with T's top byte: decide them with the full 32-bit compare.
+__device__ __noinline__ uint32_t tie_break(uint32_t eq, uint32_t h, uint32_t T, const uint32_t *__restrict__ Xj) {
+    uint32_t live = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        if (((eq >> (8 * b)) & 0xFFu) && ((h ^ __ldg(&Xj[b])) <= T)) live |= 0xFFu << (8 * b);
+    return live;
+}
+
+// Eq. 5 for 4 simulations at once, then the register-wise max of Eq. 3 restricted to live simulations.
+// xt packs the top bytes of X_j for the 4 simulations; only ties on the top byte need the full compare.
+template <int R>
+__device__ __forceinline__ void merge_row(uint32_t (&acc)[Geo<R>::CPL][4], const uint4 (&row)[Geo<R>::CPL],
+                                          const uint32_t (&xt)[Geo<R>::CPL][4], uint32_t h, uint32_t T,
+                                          const uint32_t *__restrict__ X, int li) {
+    const uint32_t ht = (h >> 24) * 0x01010101u;
+    const uint32_t tt = (T >> 24) * 0x01010101u;
+#pragma unroll
+    for (int c = 0; c < Geo<R>::CPL; ++c) {
+        const uint32_t rw[4] = {row[c].x, row[c].y, row[c].z, row[c].w};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint32_t a = xt[c][w] ^ ht;
+            uint32_t live = __vcmpltu4(a, tt);
+            const uint32_t eq = __vcmpeq4(a, tt);
+            if (eq) live |= tie_break(eq, h, T, X + 16 * (li + Geo<R>::G * c) + 4 * w);
+            acc[c][w] = vmax4(acc[c][w], rw[w] & live);
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void load_xt(const uint32_t *__restrict__ X, int li, uint32_t (&xt)[Geo<R>::CPL][4]) {
+#pragma unroll
+    for (int c = 0; c < Geo<R>::CPL; ++c)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint32_t *x = X + 16 * (li + Geo<R>::G * c) + 4 * w;
+            xt[c][w] = (__ldg(x) >> 24) | ((__ldg(x + 1) >> 24) << 8) | ((__ldg(x + 2) >> 24) << 16) |
+                       (__ldg(x + 3) & 0xFF000000u);
+        }
+}
+
+struct WarpStage {
+    int32_t v[32];
+    uint32_t h[32];
+    uint32_t T[32];
+};
+
+// Algorithm 2's inner loops for the out-edges [e0, e1) of row u: every edge (u, v) with v in L is one visit; for
+// the sampled simulations the registers of v are max-merged into acc.  Warp-uniform counters: nL edges with v in L,
+// nTaken of them that can be live (their neighbour row was read).
+template <int R, int UNR>
+__device__ __forceinline__ void scan_range(const DevProb &P, int64_t u, int64_t e0, int64_t e1, bool allL,
+                                           const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
+                                           uint32_t (&acc)[Geo<R>::CPL][4], const uint32_t (&xt)[Geo<R>::CPL][4],
+                                           int lane, int g, int li, WarpStage &sw, uint32_t &nL,
+                                           uint32_t &nTaken) {
+    using Gm = Geo<R>;
+    for (int64_t base = e0; base < e1; base += 32) {
+        const int64_t e = base + lane;
+        int32_t v = 0;
+        bool inL = false;
+        if (e < e1) {
+            v = __ldg(&P.adj[e]);
+            inL = allL || test_bit(Lcur, v);
+        }
+        uint32_t T = 0;
+        bool ok = false;
+        if (inL) edge_threshold(P, e, v, T, ok);
+        const unsigned mL = __ballot_sync(kFull, inL);
+        const bool take = inL && ok;
+        const unsigned mT = __ballot_sync(kFull, take);
+        nL += __popc(mL);
+        if (mT == 0) continue;
+        if (take) {
+            const int r = __popc(mT & ((1u << lane) - 1u));
+            sw.v[r] = v;
+            sw.h[r] = edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
+            sw.T[r] = T;
+        }
+        __syncwarp();
+        const int cnt = __popc(mT);
+        nTaken += cnt;
+        for (int i0 = 0; i0 < cnt; i0 += Gm::NG * UNR) {
+            uint4 row[UNR][Gm::CPL];
+            uint32_t hh[UNR], TT[UNR];
+            bool have[UNR];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const int idx = i0 + g + k * Gm::NG;
+                have[k] = idx < cnt;
+                if (have[k]) {
+                    const int32_t vv = sw.v[idx];
+                    hh[k] = sw.h[idx];
+                    TT[k] = sw.T[idx];
+                    const uint4 *src = reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(vv) * R);
+#pragma unroll
+                    for (int c = 0; c < Gm::CPL; ++c) row[k][c] = __ldg(src + li + Gm::G * c);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < UNR; ++k)
+                if (have[k]) merge_row<R>(acc, row[k], xt, hh[k], TT[k], P.X, li);
+        }
+        __syncwarp();
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void reduce_groups(uint32_t (&acc)[Geo<R>::CPL][4]) {
+#pragma unroll
+    for (int off = Geo<R>::G; off < 32; off <<= 1)
+#pragma unroll
+        for (int c = 0; c < Geo<R>::CPL; ++c)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[c][w] = vmax4(acc[c][w], __shfl_xor_sync(kFull, acc[c][w], off));
+}
+
+__device__ __forceinline__ uint64_t thr_bytes(int32_t model) { return model == kWC ? 4 : (model == kPerEdge ? 5 : 0); }
+
+// New registers of row u = max(own row, merged neighbours).  The row is written to the other buffer when it
+// changed, or when the buffers may differ at u (u changed in the previous sweep); a changed row joins L'.
+template <int R>
+__device__ __forceinline__ void finalize_row(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4],
+                                             bool anyTaken, bool sync, const uint8_t *__restrict__ Mcur,
+                                             uint8_t *__restrict__ Mnext, uint32_t *__restrict__ Lnext, int lane,
+                                             int g, int li, Stats &st) {
+    using Gm = Geo<R>;
+    if (!anyTaken && !sync) return;
+    bool diff = false;
+    uint4 nw[Gm::CPL];
+    if (g == 0) {
+        const uint4 *own = reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R);
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c) {
+            const uint4 o = __ldg(own + li + Gm::G * c);
+            nw[c] = make_uint4(vmax4(o.x, acc[c][0]), vmax4(o.y, acc[c][1]), vmax4(o.z, acc[c][2]),
+                               vmax4(o.w, acc[c][3]));
+            diff |= (nw[c].x != o.x) | (nw[c].y != o.y) | (nw[c].z != o.z) | (nw[c].w != o.w);
+        }
+    }
+    const bool changed = __any_sync(kFull, diff);
+    if (g == 0 && (changed || sync)) {
+        uint4 *dst = reinterpret_cast<uint4 *>(Mnext + static_cast<size_t>(u) * R);
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
+    }
+    if (changed && lane == 0) set_bit(Lnext, u);
+    st.nchg += changed ? 1u : 0u;
+    st.bytes += R + ((changed || sync) ? R : 0);
+}
+
+template <int R, int UNR>
+__device__ void prop_problem(const DevProb &P, uint32_t t, bool full, uint64_t nlight, uint64_t cnt, uint64_t first,
+                             uint64_t nworkers, int lane, WarpStage &sw) {
+    using Gm = Geo<R>;
+    const int g = lane / Gm::G, li = lane % Gm::G;
+    uint32_t xt[Gm::CPL][4];
+    load_xt<R>(P.X, li, xt);
+    const bool par = t & 1u;
+    const uint8_t *Mcur = par ? P.M1 : P.M0;
+    uint8_t *Mnext = par ? P.M0 : P.M1;
+    const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
+    uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
+    const int32_t *rows = par ? P.rows1 : P.rows0;
+    const bool allL = (t == 0);
+    const uint64_t tb = thr_bytes(P.model);
+    Stats st;
+    for (uint64_t l = first; l < cnt; l += nworkers) {
+        uint32_t acc[Gm::CPL][4];
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[c][w] = 0;
+        uint32_t nL = 0, nTaken = 0;
+        if (l < nlight) {
+            const int64_t u = full ? static_cast<int64_t>(l) : static_cast<int64_t>(rows[l]);
+            if (full && test_bit(P.heavy, u)) continue;
+            const int64_t e0 = __ldg(&P.xadj[u]), e1 = __ldg(&P.xadj[u + 1]);
+            scan_range<R, UNR>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, nL, nTaken);
+            reduce_groups<R>(acc);
+            st.visits += static_cast<unsigned long long>(nL) * R;
+            st.bytes += 16 + 4 * static_cast<uint64_t>(e1 - e0) + tb * nL + static_cast<uint64_t>(nTaken) * R;
+            finalize_row<R>(P, u, acc, nTaken > 0, test_bit(Lcur, u), Mcur, Mnext, Lnext, lane, g, li, st);
+        } else {
+            const int64_t task = static_cast<int64_t>(l - nlight);
+            const int64_t u = __ldg(&P.task_row[task]);
+            const int64_t e0 = __ldg(&P.xadj[u]) + (task - __ldg(&P.task_off[u])) * kTaskEdges;
+            const int64_t e1 = min(e0 + kTaskEdges, __ldg(&P.xadj[u + 1]));
+            scan_range<R, UNR>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, nL, nTaken);
+            reduce_groups<R>(acc);
+            st.visits += static_cast<unsigned long long>(nL) * R;
+            st.bytes += 4 * static_cast<uint64_t>(e1 - e0) + tb * nL + static_cast<uint64_t>(nTaken) * R;
+            if (nTaken > 0) {
+                if (g == 0) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(P.part + static_cast<size_t>(task) * R);
+#pragma unroll
+                    for (int c = 0; c < Gm::CPL; ++c)
+                        dst[li + Gm::G * c] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+                }
+                if (lane == 0) set_bit(P.part_any, task);
+                st.bytes += R;
+            }
+        }
+    }
+    flush_stats(P.ctr, st, lane);
+}
+
+// Rows of the current sweep: all rows (light ones here, heavy ones as tasks) or the listed light rows.
+__device__ __forceinline__ uint64_t prop_light_count(const DevProb &P, const DevCtr &C) {
+    return C.full ? static_cast<uint64_t>(P.n) : C.nrows[C.t & 1u];
+}
+
+}  // namespace
+
+template <int R, int UNR>
+__global__ void __launch_bounds__(kBlock) k_prop(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
+                                                 int nact) {
+    __shared__ WarpStage stage[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.done) continue;
+        const uint32_t t = C.t;
+        const bool full = C.full != 0;
+        const uint64_t nlight = prop_light_count(P, C);
+        const uint64_t cnt = nlight + static_cast<uint64_t>(P.n_tasks);
+        const uint64_t first = first_owned(worker, nworkers, base);
+        base += cnt;
+        if (first >= cnt) continue;
+        prop_problem<R, UNR>(P, t, full, nlight, cnt, first, nworkers, lane, stage[wib]);
+    }
+}
+
+namespace {
+
+template <int R>
+__device__ void combine_problem(const DevProb &P, uint32_t t, uint64_t cnt, uint64_t first, uint64_t nworkers,
+                                int lane) {
+    using Gm = Geo<R>;
+    const int g = lane / Gm::G, li = lane % Gm::G;
+    const bool par = t & 1u;
+    const uint8_t *Mcur = par ? P.M1 : P.M0;
+    uint8_t *Mnext = par ? P.M0 : P.M1;
+    const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
+    uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
+    Stats st;
+    for (uint64_t l = first; l < cnt; l += nworkers) {
+        const int64_t u = P.heavy_rows[l];
+        const int64_t t0 = __ldg(&P.task_off[u]), t1 = __ldg(&P.task_off[u + 1]);
+        uint32_t acc[Gm::CPL][4];
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[c][w] = 0;
+        bool any = false;
+        for (int64_t k0 = t0; k0 < t1; k0 += 32) {
+            const int64_t k = k0 + lane;
+            const bool mine = k < t1 && test_bit(P.part_any, k);
+            const unsigned m = __ballot_sync(kFull, mine);
+            if (m == 0) continue;
+            any = true;
+            // clear the bits this warp consumed (other rows' tasks may share the word)
+            if (mine) atomicAnd(&P.part_any[k >> 5], ~(1u << (k & 31)));
+            const int cnt_m = __popc(m);
+            for (int i = g; i < cnt_m; i += Gm::NG) {
+                const int src = __fns(m, 0, i + 1);
+                const uint4 *p = reinterpret_cast<const uint4 *>(P.part + static_cast<size_t>(k0 + src) * R);
+#pragma unroll
+                for (int c = 0; c < Gm::CPL; ++c) {
+                    const uint4 x = __ldg(p + li + Gm::G * c);
+                    acc[c][0] = vmax4(acc[c][0], x.x);
+                    acc[c][1] = vmax4(acc[c][1], x.y);
+                    acc[c][2] = vmax4(acc[c][2], x.z);
+                    acc[c][3] = vmax4(acc[c][3], x.w);
+                }
+            }
+            st.bytes += static_cast<uint64_t>(cnt_m) * R;
+        }
+        reduce_groups<R>(acc);
+        st.bytes += 16;
+        finalize_row<R>(P, u, acc, any, test_bit(Lcur, u), Mcur, Mnext, Lnext, lane, g, li, st);
+    }
+    flush_stats(P.ctr, st, lane);
+}
+
+}  // namespace
+
+template <int R>
+__global__ void __launch_bounds__(kBlock) k_combine(const DevProb *__restrict__ probs,
+                                                    const int32_t *__restrict__ act, int nact) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.done) continue;
+        const uint64_t cnt = static_cast<uint64_t>(P.n_heavy);
+        const uint64_t first = first_owned(worker, nworkers, base);
+        base += cnt;
+        if (first >= cnt) continue;
+        combine_problem<R>(P, C.t, cnt, first, nworkers, lane);
+    }
+}
+
+namespace {
+
+// Block-aggregated append of the set bits of one word per thread: ids (word_index*32 + bit) go to out[], the block
+// reserves its range with one atomic on *count.  All threads of the block must call it.
+__device__ __forceinline__ void block_append_bits(uint32_t w, int64_t word_index, int32_t *out, uint32_t *count) {
+    __shared__ uint32_t s_warp[kWarpsPerBlock];
+    __shared__ uint32_t s_base;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t c = __popc(w);
+    uint32_t incl = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) s_warp[wib] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int i = 0; i < kWarpsPerBlock; ++i) {
+            const uint32_t x = s_warp[i];
+            s_warp[i] = run;
+            run += x;
+        }
+        s_base = run ? atomicAdd(count, run) : 0;
+    }
+    __syncthreads();
+    uint32_t pos = s_base + s_warp[wib] + incl - c;
+    while (w) {
+        const int b = __ffs(w) - 1;
+        w &= w - 1;
+        out[pos++] = static_cast<int32_t>(word_index * 32 + b);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool sweep_stops(const DevProb &P, const DevCtr &C) {
+    return C.nchg <= P.stop_thr || C.t + 1 >= P.max_sweeps;
+}
+
+}  // namespace
+
+// After sweep t: clear L_t's bits (the buffer L_{t+2} will be written to) and, when the next sweep is a listed one,
+// compact L_{t+1} into chg_list.
+__global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__ probs,
+                                                     const int32_t *__restrict__ act, int nact) {
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.done || sweep_stops(P, C)) continue;
+        const bool list_next = C.nchg <= P.full_thr;
+        const bool par = C.t & 1u;
+        uint32_t *Lold = par ? P.Lb1 : P.Lb0;
+        const uint32_t *Lnew = par ? P.Lb0 : P.Lb1;
+        const int64_t words = (P.n + 31) >> 5;
+        const uint64_t chunks = (words + kBlock - 1) / kBlock;
+        const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
+        base += chunks;
+        for (uint64_t ch = first; ch < chunks; ch += gridDim.x) {
+            const int64_t i = static_cast<int64_t>(ch) * kBlock + threadIdx.x;
+            uint32_t w = 0;
+            if (i < words) {
+                Lold[i] = 0;
+                w = Lnew[i];
+            }
+            if (list_next) block_append_bits(w, i, P.chg_list, &P.ctr->nchg_list);
+        }
+    }
+}
+
+// Marks every row that must be visited in the next sweep: the changed vertices themselves and their in-neighbours.
+__global__ void __launch_bounds__(kBlock) k_expand(const DevProb *__restrict__ probs,
+                                                   const int32_t *__restrict__ act, int nact) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.done || sweep_stops(P, C) || C.nchg > P.full_thr) continue;
+        const uint64_t cnt = C.nchg_list;
+        const uint64_t first = first_owned(worker, nworkers, base);
+        base += cnt;
+        for (uint64_t l = first; l < cnt; l += nworkers) {
+            const int32_t v = P.chg_list[l];
+            if (lane == 0) set_bit(P.mark, v);
+            const int64_t e0 = __ldg(&P.xadj_in[v]), e1 = __ldg(&P.xadj_in[v + 1]);
+            for (int64_t e = e0 + lane; e < e1; e += 32) set_bit(P.mark, __ldg(&P.adj_in[e]));
+        }
+    }
+}
+
+// Compacts the marked light rows into the row list of the next sweep and clears the marks.
+__global__ void __launch_bounds__(kBlock) k_rows(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
+                                                 int nact) {
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.done || sweep_stops(P, C) || C.nchg > P.full_thr) continue;
+        const uint32_t np = (C.t + 1) & 1u;
+        int32_t *rows = np ? P.rows1 : P.rows0;
+        const int64_t words = (P.n + 31) >> 5;
+        const uint64_t chunks = (words + kBlock - 1) / kBlock;
+        const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
+        base += chunks;
+        for (uint64_t ch = first; ch < chunks; ch += gridDim.x) {
+            const int64_t i = static_cast<int64_t>(ch) * kBlock + threadIdx.x;
+            uint32_t w = 0;
+            if (i < words) {
+                w = P.mark[i];
+                if (w) {
+                    P.mark[i] = 0;
+                    w &= ~P.heavy[i];
+                }
+            }
+            block_append_bits(w, i, rows, &P.ctr->nrows[np]);
+        }
+    }
+}
+
+// Ends sweep t: stop test (|L'| <= eps_c |V| or the sweep limit), mode of the next sweep, counter resets.
+__global__ void k_advance(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nact) return;
+    const DevProb &P = probs[act[q]];
+    DevCtr &C = *P.ctr;
+    if (C.done) return;
+    const uint32_t t = C.t;
+    const uint32_t nchg = C.nchg;
+    if (static_cast<int32_t>(t + 1) < P.flog_cap) P.flog[t + 1] = nchg;
+    C.sweeps_total += 1;
+    const bool stop = nchg <= P.stop_thr;
+    const bool lim = t + 1 >= P.max_sweeps;
+    if (stop || lim) {
+        C.done = 1;
+        C.timeout = (!stop && lim) ? 1u : 0u;
+        C.res_par = (t + 1) & 1u;
+    }
+    C.full = nchg > P.full_thr ? 1u : 0u;
+    C.nrows[t & 1u] = 0;
+    C.nchg = 0;
+    C.nchg_list = 0;
+    C.t = t + 1;
+}
+
+// Algorithm 1's initialisation: M_v[j] = clz(hash(v) XOR Y_j), 0 where v is in R_{G_j}(S) (a rebuild), written to
+// both register buffers; resets the diffusion state and M_S'.
+__global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
+                                                 int nact) {
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const int CH = P.R / 16;
+        const uint64_t nchunks = static_cast<uint64_t>(P.n) * CH;
+        const int64_t words = (P.n + 31) >> 5;
+        const int64_t twords = (P.n_tasks + 31) >> 5;
+        const uint64_t cnt = nchunks + 3 * static_cast<uint64_t>(words) + static_cast<uint64_t>(twords) + 1;
+        const uint64_t first = first_owned(tid, nthreads, base);
+        base += cnt;
+        for (uint64_t l = first; l < cnt; l += nthreads) {
+            if (l < nchunks) {
+                const uint32_t v = static_cast<uint32_t>(l / CH);
+                const int c = static_cast<int>(l % CH);
+                const uint32_t hv = vertex_hash(v);
+                uint32_t blocked = 0;
+                if (P.vis) blocked = (P.vis[static_cast<size_t>(v) * P.W + (c >> 1)] >> (16 * (c & 1))) & 0xFFFFu;
+                uint32_t w[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    uint32_t x = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int j = 16 * c + 4 * k + b;
+                        const uint32_t rank = (blocked >> (4 * k + b)) & 1u ? 0u : __clz(hv ^ __ldg(&P.Y[j]));
+                        x |= rank << (8 * b);
+                    }
+                    w[k] = x;
+                }
+                const uint4 val = make_uint4(w[0], w[1], w[2], w[3]);
+                reinterpret_cast<uint4 *>(P.M0)[l] = val;
+                reinterpret_cast<uint4 *>(P.M1)[l] = val;
+            } else if (l < nchunks + 3 * static_cast<uint64_t>(words)) {
+                const uint64_t k = l - nchunks;
+                const int64_t i = static_cast<int64_t>(k % words);
+                const int which = static_cast<int>(k / words);
+                (which == 0 ? P.Lb0 : which == 1 ? P.Lb1 : P.mark)[i] = 0;
+            } else if (l < cnt - 1) {
+                P.part_any[l - nchunks - 3 * static_cast<uint64_t>(words)] = 0;
+            } else {
+                DevCtr &C = *P.ctr;
+                C.t = 0;
+                C.done = 0;
+                C.timeout = 0;
+                C.full = 1;
+                C.res_par = 0;
+                C.nchg = 0;
+                C.nchg_list = 0;
+                C.nrows[0] = 0;
+                C.nrows[1] = 0;
+                if (P.flog_cap > 0) P.flog[0] = P.n;
+                for (int j = 0; j < P.R; ++j) P.MS[j] = 0;
+            }
+        }
+    }
+}
+
+namespace {
+
+template <int R>
+__device__ void scan_problem(const DevProb &P, uint64_t cnt, uint64_t first, uint64_t nworkers, int lane) {
+    using Gm = Geo<R>;
+    const int g = lane / Gm::G, li = lane % Gm::G;
+    const uint8_t *M = P.ctr->res_par ? P.M1 : P.M0;
+    uint32_t ms[Gm::CPL][4];
+    {
+        const uint4 *p = reinterpret_cast<const uint4 *>(P.MS);
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c) {
+            const uint4 x = p[li + Gm::G * c];
+            ms[c][0] = x.x;
+            ms[c][1] = x.y;
+            ms[c][2] = x.z;
+            ms[c][3] = x.w;
+        }
+    }
+    unsigned long long best = 0;
+    for (uint64_t l = first; l < cnt; l += nworkers) {
+        const int64_t v = static_cast<int64_t>(l) * Gm::NG + g;
+        uint32_t s = 0;
+        const bool ok = v < P.n && !test_bit(P.inS, v);
+        if (ok) {
+            const uint4 *row = reinterpret_cast<const uint4 *>(M + static_cast<size_t>(v) * R);
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) {
+                const uint4 x = __ldg(row + li + Gm::G * c);
+                s = __dp4a(vmax4(x.x, ms[c][0]), 0x01010101u, s);
+                s = __dp4a(vmax4(x.y, ms[c][1]), 0x01010101u, s);
+                s = __dp4a(vmax4(x.z, ms[c][2]), 0x01010101u, s);
+                s = __dp4a(vmax4(x.w, ms[c][3]), 0x01010101u, s);
+            }
+        }
+#pragma unroll
+        for (int off = 1; off < Gm::G; off <<= 1) s += __shfl_xor_sync(kFull, s, off);
+        if (ok) {
+            const unsigned long long key =
+                (static_cast<unsigned long long>(s) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(v));
+            best = key > best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, best, off);
+        best = o > best ? o : best;
+    }
+    if (lane == 0 && best) atomicMax(&P.ctr->best_key, best);
+}
+
+}  // namespace
+
+// Algorithm 1's argmax: for every v not in S, gsum_v = sum_j max(M_S'[j], M_v[j]) (Merge, Eq. 3; Estimate, Eq. 2 is
+// increasing in it); the maximum of (gsum_v << 32 | ~v) picks the largest sum, ties to the smallest id.
+template <int R>
+__global__ void __launch_bounds__(kBlock) k_scan(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
+                                                 int nact) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const uint64_t cnt = (static_cast<uint64_t>(P.n) + Geo<R>::NG - 1) / Geo<R>::NG;
+        const uint64_t first = first_owned(worker, nworkers, base);
+        base += cnt;
+        if (first >= cnt) continue;
+        scan_problem<R>(P, cnt, first, nworkers, lane);
+    }
+}
+
+// Takes the argmax as seed s of step k, adds it to S and starts the reachability search from it: s is marked
+// reached in every simulation where it was not yet, and those bits form the first frontier.
+__global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact, int32_t step) {
+    const int q = blockIdx.x;
+    if (q >= nact) return;
+    const DevProb &P = probs[act[q]];
+    DevCtr &C = *P.ctr;
+    const int lane = threadIdx.x;
+    const unsigned long long key = C.best_key;
+    const uint32_t s = 0xFFFFFFFFu - static_cast<uint32_t>(key & 0xFFFFFFFFull);
+    const uint32_t gsum = static_cast<uint32_t>(key >> 32);
+    if (key == 0 || s >= static_cast<uint64_t>(P.n)) {  // no candidate was scanned: nothing to search
+        if (lane == 0) {
+            C.bdone = 1;
+            C.btimeout = 1;
+        }
+        return;
+    }
+    uint32_t added = 0;
+    for (int k = lane; k < P.W; k += 32) {
+        const size_t at = static_cast<size_t>(s) * P.W + k;
+        const uint32_t nb = ~P.vis[at];
+        P.vis[at] = 0xFFFFFFFFu;
+        P.del0[at] = nb;
+        added += __popc(nb);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
+    __syncwarp();
+    if (lane == 0) {
+        C.s = s;
+        C.gsum = gsum;
+        C.best_key = 0;
+        set_bit(P.inS, s);
+        C.reached += added;
+        const int64_t deg = P.xadj[s + 1] - P.xadj[s];
+        const bool heavy = deg > kBfsHeavyDeg;
+        C.nF[0] = heavy ? 0u : 1u;
+        C.nH[0] = heavy ? 1u : 0u;
+        C.nF[1] = 0;
+        C.nH[1] = 0;
+        (heavy ? P.H0 : P.F0)[0] = static_cast<int32_t>(s);
+        C.lvl = 0;
+        C.bdone = added ? 0u : 1u;
+        C.btimeout = 0;
+        if (step >= 0) {
+            P.step_seed[step] = s;
+            P.step_gsum[step] = gsum;
+        }
+    }
+}
+
+// Starts a reachability search from a whole seed set (for an exact sigma of a given set).
+__global__ void k_seed_set(const DevProb *__restrict__ prob, const int32_t *__restrict__ seeds, int k) {
+    const DevProb &P = *prob;
+    DevCtr &C = *P.ctr;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k * P.W; i += gridDim.x * blockDim.x) {
+        const int32_t s = seeds[i / P.W];
+        const int w = i % P.W;
+        const size_t at = static_cast<size_t>(s) * P.W + w;
+        const uint32_t old = atomicOr(&P.vis[at], 0xFFFFFFFFu);
+        if (~old) {
+            atomicOr(&P.del0[at], ~old);
+            atomicAdd(&C.reached, static_cast<unsigned long long>(__popc(~old)));
+        }
+        if (w == 0) {
+            const uint32_t prev = atomicOr(&P.inS[s >> 5], 1u << (s & 31));
+            if (!((prev >> (s & 31)) & 1u)) {
+                const int64_t deg = P.xadj[s + 1] - P.xadj[s];
+                if (deg > kBfsHeavyDeg)
+                    P.H0[atomicAdd(&C.nH[0], 1u)] = s;
+                else
+                    P.F0[atomicAdd(&C.nF[0], 1u)] = s;
+            }
+        }
+    }
+}
+
+namespace {
+
+// New bits for target v over edge (u, v) in the simulations of word k whose bit is set in d.
+__device__ __forceinline__ uint32_t bfs_edge_word(uint32_t d, uint32_t h, uint32_t T, const uint32_t *__restrict__ X,
+                                                  int k) {
+    uint32_t m = 0;
+    while (d) {
+        const int b = __ffs(d) - 1;
+        d &= d - 1;
+        if ((h ^ __ldg(&X[32 * k + b])) <= T) m |= 1u << b;
+    }
+    return m;
+}
+
+// Pushes the new bits of u over edge e = (u, v): vis[v] |= d(u) & live(u, v); bits that were not set yet go to the
+// next level's delta of v and put v on the next frontier.
+__device__ __forceinline__ unsigned long long bfs_push(const DevProb &P, int64_t u, int64_t e,
+                                                       const uint32_t *d, uint32_t *dnext) {
+    const int32_t v = __ldg(&P.adj[e]);
+    uint32_t T;
+    bool ok;
+    edge_threshold(P, e, v, T, ok);
+    if (!ok) return 0;
+    const uint32_t h = edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
+    unsigned long long added = 0;
+    bool any_new = false;
+    for (int k = 0; k < P.W; ++k) {
+        const uint32_t dk = d[k];
+        if (!dk) continue;
+        const size_t at = static_cast<size_t>(v) * P.W + k;
+        const uint32_t cand = dk & ~P.vis[at];
+        if (!cand) continue;
+        const uint32_t m = bfs_edge_word(cand, h, T, P.X, k);
+        if (!m) continue;
+        const uint32_t old = atomicOr(&P.vis[at], m);
+        const uint32_t nb = m & ~old;
+        if (nb) {
+            atomicOr(&dnext[at], nb);
+            added += __popc(nb);
+            any_new = true;
+        }
+    }
+    if (any_new) set_bit(P.Fb, v);
+    return added;
+}
+
+}  // namespace
+
+// One level of the bit-parallel reachability search of Algorithm 1, over all simulations at once.
+__global__ void __launch_bounds__(kBlock) k_bfs_level(const DevProb *__restrict__ probs,
+                                                      const int32_t *__restrict__ act, int nact) {
+    __shared__ uint32_t s_d[kWarpsPerBlock][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    // light frontier vertices: one warp each, lanes over out-edges
+    {
+        const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+        const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+        uint64_t base = 0;
+        for (int q = 0; q < nact; ++q) {
+            const DevProb &P = probs[act[q]];
+            const DevCtr &C = *P.ctr;
+            if (C.bdone) continue;
+            const uint32_t p = C.lvl & 1u;
+            const uint64_t cnt = C.nF[p];
+            const uint64_t first = first_owned(worker, nworkers, base);
+            base += cnt;
+            const int32_t *F = p ? P.F1 : P.F0;
+            uint32_t *dcur = p ? P.del1 : P.del0;
+            uint32_t *dnext = p ? P.del0 : P.del1;
+            unsigned long long added = 0;
+            for (uint64_t l = first; l < cnt; l += nworkers) {
+                const int64_t u = F[l];
+                for (int k = lane; k < P.W; k += 32) {
+                    const size_t at = static_cast<size_t>(u) * P.W + k;
+                    s_d[wib][k] = dcur[at];
+                    dcur[at] = 0;
+                }
+                __syncwarp();
+                const int64_t e0 = __ldg(&P.xadj[u]), e1 = __ldg(&P.xadj[u + 1]);
+                for (int64_t e = e0 + lane; e < e1; e += 32) added += bfs_push(P, u, e, s_d[wib], dnext);
+                __syncwarp();
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
+            if (lane == 0 && added) atomicAdd(&P.ctr->reached, added);
+        }
+    }
+    // heavy frontier vertices: their out-edges spread over every thread of the grid
+    {
+        const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+        const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+        uint64_t base = 0;
+        for (int q = 0; q < nact; ++q) {
+            const DevProb &P = probs[act[q]];
+            const DevCtr &C = *P.ctr;
+            if (C.bdone) continue;
+            const uint32_t p = C.lvl & 1u;
+            const int32_t *H = p ? P.H1 : P.H0;
+            const uint32_t *dcur = p ? P.del1 : P.del0;
+            uint32_t *dnext = p ? P.del0 : P.del1;
+            const uint32_t nh = C.nH[p];
+            unsigned long long added = 0;
+            for (uint32_t i = 0; i < nh; ++i) {
+                const int64_t u = H[i];
+                const int64_t e0 = P.xadj[u], e1 = P.xadj[u + 1];
+                const uint64_t cnt = static_cast<uint64_t>(e1 - e0);
+                const uint64_t first = first_owned(tid, nthreads, base);
+                base += cnt;
+                const uint32_t *d = dcur + static_cast<size_t>(u) * P.W;
+                for (uint64_t l = first; l < cnt; l += nthreads) added += bfs_push(P, u, e0 + l, d, dnext);
+            }
+            if (added) atomicAdd(&P.ctr->reached, added);
+        }
+    }
+}
+
+// After a level: clears the consumed delta rows of heavy frontier vertices and compacts the vertices that reached
+// something new into the next frontier (light and heavy lists).
+__global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restrict__ probs,
+                                                         const int32_t *__restrict__ act, int nact) {
+    {
+        const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+        const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+        uint64_t base = 0;
+        for (int q = 0; q < nact; ++q) {
+            const DevProb &P = probs[act[q]];
+            const DevCtr &C = *P.ctr;
+            if (C.bdone) continue;
+            const uint32_t p = C.lvl & 1u;
+            const int32_t *H = p ? P.H1 : P.H0;
+            uint32_t *dcur = p ? P.del1 : P.del0;
+            const uint64_t cnt = static_cast<uint64_t>(C.nH[p]) * P.W;
+            const uint64_t first = first_owned(tid, nthreads, base);
+            base += cnt;
+            for (uint64_t l = first; l < cnt; l += nthreads)
+                dcur[static_cast<size_t>(H[l / P.W]) * P.W + l % P.W] = 0;
+        }
+    }
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.bdone) continue;
+        const uint32_t np = (C.lvl + 1) & 1u;
+        int32_t *F = np ? P.F1 : P.F0;
+        int32_t *H = np ? P.H1 : P.H0;
+        const int64_t words = (P.n + 31) >> 5;
+        const uint64_t chunks = (words + kBlock - 1) / kBlock;
+        const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
+        base += chunks;
+        for (uint64_t ch = first; ch < chunks; ch += gridDim.x) {
+            const int64_t i = static_cast<int64_t>(ch) * kBlock + threadIdx.x;
+            uint32_t w = 0;
+            if (i < words) {
+                w = P.Fb[i];
+                if (w) P.Fb[i] = 0;
+            }
+            uint32_t wl = 0, wh = 0;
+            for (uint32_t x = w; x;) {
+                const int b = __ffs(x) - 1;
+                x &= x - 1;
+                const int64_t v = i * 32 + b;
+                if (P.xadj[v + 1] - P.xadj[v] > kBfsHeavyDeg)
+                    wh |= 1u << b;
+                else
+                    wl |= 1u << b;
+            }
+            block_append_bits(wl, i, F, &P.ctr->nF[np]);
+            if (__syncthreads_or(wh != 0)) block_append_bits(wh, i, H, &P.ctr->nH[np]);
+        }
+    }
+}
+
+__global__ void k_bfs_advance(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nact) return;
+    const DevProb &P = probs[act[q]];
+    DevCtr &C = *P.ctr;
+    if (C.bdone) return;
+    const uint32_t p = C.lvl & 1u;
+    C.levels_total += 1;
+    const bool empty = C.nF[p ^ 1u] + C.nH[p ^ 1u] == 0;
+    const bool lim = C.lvl + 1 >= P.max_sweeps;
+    C.nF[p] = 0;
+    C.nH[p] = 0;
+    C.lvl += 1;
+    if (empty || lim) {
+        C.bdone = 1;
+        C.btimeout = (!empty && lim) ? 1u : 0u;
+    }
+}
+
+// M_S' <- Merge(M_S', M_s) (Eq. 3).
+__global__ void k_merge(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact) {
+    const int q = blockIdx.x;
+    if (q >= nact) return;
+    const DevProb &P = probs[act[q]];
+    const DevCtr &C = *P.ctr;
+    const uint8_t *M = C.res_par ? P.M1 : P.M0;
+    const uint32_t *row = reinterpret_cast<const uint32_t *>(M + static_cast<size_t>(C.s) * P.R);
+    uint32_t *ms = reinterpret_cast<uint32_t *>(P.MS);
+    for (int i = threadIdx.x; i < P.R / 4; i += blockDim.x) ms[i] = vmax4(ms[i], row[i]);
+}
+
+// Merge of the registers of k seeds and their byte sum (Eq. 3 then the sum behind Eq. 2).
+__global__ void k_estimate(const DevProb *__restrict__ prob, const int32_t *__restrict__ seeds, int k,
+                           unsigned long long *gsum_out) {
+    const DevProb &P = *prob;
+    const uint8_t *M = P.ctr->res_par ? P.M1 : P.M0;
+    __shared__ unsigned long long s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
+    unsigned long long part = 0;
+    for (int i = threadIdx.x; i < P.R / 4; i += blockDim.x) {
+        uint32_t mx = 0;
+        for (int a = 0; a < k; ++a)
+            mx = vmax4(mx, reinterpret_cast<const uint32_t *>(M + static_cast<size_t>(seeds[a]) * P.R)[i]);
+        part += __dp4a(mx, 0x01010101u, 0u);
+    }
+    atomicAdd(&s_sum, part);
+    __syncthreads();
+    if (threadIdx.x == 0) *gsum_out = s_sum;
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Graph preparation: simulation words, in-degree / in-CSR, weighted-cascade thresholds, heavy-row tasks.
+
+// splitmix64 output i from `seed`: the state after i+1 Weyl steps through the variant-13 mixer.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    X[r] = static_cast<uint32_t>(splitmix64_at(seed, 2ull * r) >> 32);
+    Y[r] = static_cast<uint32_t>(splitmix64_at(seed, 2ull * r + 1) >> 32);
+}
+
+__global__ void k_indeg(const int32_t *__restrict__ adj, int64_t m, int32_t *__restrict__ indeg) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        atomicAdd(&indeg[adj[e]], 1);
+}
+
+__global__ void k_wc_thresholds(const int32_t *__restrict__ indeg, int64_t n, uint32_t *__restrict__ T) {
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
+         v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t d = indeg[v];
+        T[v] = d > 0 ? 0xFFFFFFFFu / static_cast<uint32_t>(d) : 0u;
+    }
+}
+
+__global__ void k_transpose_fill(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj, int64_t n,
+                                 unsigned long long *__restrict__ cursor, int32_t *__restrict__ adj_in) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps)
+        for (int64_t e = xadj[u] + lane; e < xadj[u + 1]; e += 32)
+            adj_in[atomicAdd(&cursor[adj[e]], 1ull)] = static_cast<int32_t>(u);
+}
+
+__global__ void k_row_tasks(const int64_t *__restrict__ xadj, int64_t n, int32_t *__restrict__ ntask,
+                            uint32_t *__restrict__ heavy) {
+    for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < n;
+         u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t d = xadj[u + 1] - xadj[u];
+        const bool h = d > kHeavyDeg;
+        ntask[u] = h ? static_cast<int32_t>((d + kTaskEdges - 1) / kTaskEdges) : 0;
+        if (h) set_bit(heavy, u);
+    }
+}
+
+__global__ void k_task_fill(const int64_t *__restrict__ task_off, int64_t n, int32_t *__restrict__ task_row,
+                            int32_t *__restrict__ heavy_rows, unsigned int *__restrict__ nheavy) {
+    for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < n;
+         u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t a = task_off[u], b = task_off[u + 1];
+        if (b > a) {
+            heavy_rows[atomicAdd(nheavy, 1u)] = static_cast<int32_t>(u);
+            for (int64_t k = a; k < b; ++k) task_row[k] = static_cast<int32_t>(u);
+        }
+    }
+}
+
+// Exclusive prefix sum of n int32 counts into n+1 int64 offsets: per-block scans, a scan of the block totals, and
+// the add-back.
+constexpr int kScanItems = 8;
+
+__global__ void k_scan_blocks(const int32_t *__restrict__ in, int64_t n, int64_t *__restrict__ out,
+                              int64_t *__restrict__ block_sums) {
+    __shared__ int64_t s_warp[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t start = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) * kScanItems;
+    int64_t v[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (start + i < n) ? in[start + i] : 0;
+        sum += v[i];
+    }
+    int64_t incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) s_warp[wib] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < kWarpsPerBlock; ++i) {
+            const int64_t x = s_warp[i];
+            s_warp[i] = run;
+            run += x;
+        }
+        block_sums[blockIdx.x] = run;
+    }
+    __syncthreads();
+    int64_t run = s_warp[wib] + incl - sum;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (start + i < n) out[start + i] = run;
+        run += v[i];
+    }
+}
+
+__global__ void k_scan_sums(int64_t *__restrict__ block_sums, int64_t nb, int64_t *__restrict__ total_out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t run = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t x = block_sums[b];
+        block_sums[b] = run;
+        run += x;
+    }
+    *total_out = run;
+}
+
+__global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *__restrict__ block_sums) {
+    const int64_t per = static_cast<int64_t>(kBlock) * kScanItems;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[i] += block_sums[i / per];
+}
+
+// Argument checks on device-resident CSR arrays: flag 0 bad ends, 1 decreasing offsets, 2 target out of range.
+__global__ void k_validate(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj, int64_t n, int64_t m,
+                           unsigned int *flags) {
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nth = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    if (tid == 0 && (xadj[0] != 0 || xadj[n] != m)) flags[0] = 1;
+    for (int64_t u = tid; u < n; u += nth)
+        if (xadj[u + 1] < xadj[u]) flags[1] = 1;
+    for (int64_t e = tid; e < m; e += nth) {
+        const int32_t v = adj[e];
+        if (v < 0 || v >= n) flags[2] = 1;
+    }
+}
+
+// Per-edge thresholds of Eq. 5: T = ceil(p * 2^32) - 1 in double (exact for float p), never live for p <= 0.
+__global__ void k_edge_thresholds(const float *__restrict__ p, int64_t m, uint32_t *__restrict__ T,
+                                  uint8_t *__restrict__ ok, unsigned int *flags) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const double q = static_cast<double>(p[e]);
+        if (!(q >= 0.0 && q <= 1.0)) flags[3] = 1;
+        const bool live = q > 0.0;
+        ok[e] = live ? 1 : 0;
+        T[e] = live ? static_cast<uint32_t>(ceil(q * 4294967296.0) - 1.0) : 0u;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Host-side launchers
+
+static int g_grid_warp = 0;   // blocks for warp-striped kernels
+static int g_grid_block = 0;  // blocks for block-striped kernels
+
+cudaError_t configure(int device) {
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prop<256, 2>, kBlock, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    g_grid_warp = prop.multiProcessorCount * occ;
+    g_grid_block = prop.multiProcessorCount * 4;
+    return cudaSuccess;
+}
+
+int grid_warp() { return g_grid_warp; }
+
+#define IMK_R_SWITCH(R, CALL)                 \
+    switch (R) {                              \
+        case 64: { constexpr int RR = 64; CALL; } break;     \
+        case 128: { constexpr int RR = 128; CALL; } break;   \
+        case 256: { constexpr int RR = 256; CALL; } break;   \
+        case 512: { constexpr int RR = 512; CALL; } break;   \
+        case 1024: { constexpr int RR = 1024; CALL; } break; \
+        default: break;                       \
+    }
+
+void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    IMK_R_SWITCH(R, (k_prop<RR, 2><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
+}
+void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    IMK_R_SWITCH(R, (k_combine<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
+}
+void launch_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    k_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);
+}
+void launch_expand(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    k_expand<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
+}
+void launch_rows(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    k_rows<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);
+}
+void launch_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    k_advance<<<(nact + 127) / 128, 128, 0, s>>>(probs, act, nact);
+}
+void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    k_init<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
+}
+void launch_scan(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    IMK_R_SWITCH(R, (k_scan<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
+}
+void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t step, cudaStream_t s) {
+    k_choose<<<nact, 32, 0, s>>>(probs, act, nact, step);
+}
+void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cudaStream_t s) {
+    k_seed_set<<<(k * W + 255) / 256, 256, 0, s>>>(prob, seeds, k);
+}
+void launch_bfs_level(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    k_bfs_level<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
+}
+void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    k_bfs_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);
+}
+void launch_bfs_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    k_bfs_advance<<<(nact + 127) / 128, 128, 0, s>>>(probs, act, nact);
+}
+void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    k_merge<<<nact, 128, 0, s>>>(probs, act, nact);
+}
+void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned long long *gsum, cudaStream_t s) {
+    k_estimate<<<1, 256, 0, s>>>(prob, seeds, k, gsum);
+}
+void launch_validate(const int64_t *xadj, const int32_t *adj, int64_t n, int64_t m, unsigned int *flags,
+                     cudaStream_t s) {
+    k_validate<<<g_grid_block, kBlock, 0, s>>>(xadj, adj, n, m, flags);
+}
+void launch_edge_thresholds(const float *p, int64_t m, uint32_t *T, uint8_t *ok, unsigned int *flags,
+                            cudaStream_t s) {
+    if (m > 0) k_edge_thresholds<<<g_grid_block, kBlock, 0, s>>>(p, m, T, ok, flags);
+}
+void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, cudaStream_t s) {
+    k_words<<<(R + 255) / 256, 256, 0, s>>>(seed, R, X, Y);
+}
+void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s) {
+    if (m > 0) k_indeg<<<g_grid_block, kBlock, 0, s>>>(adj, m, indeg);
+}
+void launch_wc_thresholds(const int32_t *indeg, int64_t n, uint32_t *T, cudaStream_t s) {
+    k_wc_thresholds<<<g_grid_block, kBlock, 0, s>>>(indeg, n, T);
+}
+void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, unsigned long long *cursor,
+                           int32_t *adj_in, cudaStream_t s) {
+    k_transpose_fill<<<g_grid_warp, kBlock, 0, s>>>(xadj, adj, n, cursor, adj_in);
+}
+void launch_row_tasks(const int64_t *xadj, int64_t n, int32_t *ntask, uint32_t *heavy, cudaStream_t s) {
+    k_row_tasks<<<g_grid_block, kBlock, 0, s>>>(xadj, n, ntask, heavy);
+}
+void launch_task_fill(const int64_t *task_off, int64_t n, int32_t *task_row, int32_t *heavy_rows,
+                      unsigned int *nheavy, cudaStream_t s) {
+    k_task_fill<<<g_grid_block, kBlock, 0, s>>>(task_off, n, task_row, heavy_rows, nheavy);
+}
+int64_t scan_block_count(int64_t n) {
+    const int64_t per = static_cast<int64_t>(kBlock) * kScanItems;
+    return (n + per - 1) / per;
+}
+void launch_exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums, cudaStream_t s) {
+    const int64_t nb = scan_block_count(n);
+    if (nb > 0) k_scan_blocks<<<static_cast<unsigned>(nb), kBlock, 0, s>>>(in, n, out, block_sums);
+    k_scan_sums<<<1, 32, 0, s>>>(block_sums, nb, out + n);
+    if (nb > 1) k_scan_add<<<g_grid_block, kBlock, 0, s>>>(out, n, block_sums);
+}
+
+}  // namespace imk

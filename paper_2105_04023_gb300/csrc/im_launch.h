@@ -1,0 +1,42 @@
+// Host-side launchers of the library's kernels (defined in im_kernels.cu).  Every launcher enqueues on stream s and
+// returns at once; problem descriptors and the active list live in device memory.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "im_common.cuh"
+
+namespace imk {
+
+cudaError_t configure(int device);
+int grid_warp();
+
+void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_expand(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_rows(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_scan(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t step, cudaStream_t s);
+void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cudaStream_t s);
+void launch_bfs_level(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_bfs_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned long long *gsum, cudaStream_t s);
+
+void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, cudaStream_t s);
+void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s);
+void launch_wc_thresholds(const int32_t *indeg, int64_t n, uint32_t *T, cudaStream_t s);
+void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, unsigned long long *cursor,
+                           int32_t *adj_in, cudaStream_t s);
+void launch_row_tasks(const int64_t *xadj, int64_t n, int32_t *ntask, uint32_t *heavy, cudaStream_t s);
+void launch_task_fill(const int64_t *task_off, int64_t n, int32_t *task_row, int32_t *heavy_rows,
+                      unsigned int *nheavy, cudaStream_t s);
+int64_t scan_block_count(int64_t n);
+void launch_exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums, cudaStream_t s);
+
+}  // namespace imk

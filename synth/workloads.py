@@ -39,9 +39,10 @@ def er_2k() -> Problem:
     return Problem(g, IC, 0.05, R=64, K=10, eps_g=0.01, seed=1, name="er_n2000_m20000_ic0.05_R64_K10")
 
 
-def rmat20_wc() -> Problem:
+def rmat20_wc(cache: bool = False) -> Problem:
     """R-MAT scale 20, edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), weighted cascade, R=256, K=50, eps_g=0.01."""
-    g = graphs.rmat(20, 16, seed=2)
+    g = (graphs.cached(lambda: graphs.rmat(20, 16, seed=2), "rmat_s20_ef16_seed2") if cache
+         else graphs.rmat(20, 16, seed=2))
     return Problem(g, WC, 0.0, R=256, K=50, eps_g=0.01, seed=2, name="rmat_s20_ef16_wc_R256_K50")
 
 

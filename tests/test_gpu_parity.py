@@ -1,0 +1,198 @@
+"""Parity of the CUDA library with the CPU oracle, element by element, on seeded synthetic graphs.
+
+Registers, sweep counts, edge-simulation visits and frontier sizes must be bit-exact; seed sets, register sums and
+rebuild decisions exact; sigma exact (an integer count over R) and the estimate within 1e-12 relative (both sides
+form it from the same integer in double).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import assert_build_parity, assert_select_parity, gpu_build
+from synth import graphs, workloads
+
+import paper_2105_04023_gb300 as im
+
+pytestmark = pytest.mark.gpu
+
+IC, WC, PER_EDGE = 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2105_04023_gb300 import build
+
+    build.build()
+    c = im.Context(0)
+    yield c
+    c.close()
+
+
+SMALL = {
+    "er300": graphs.erdos_renyi(300, 2400, seed=3),
+    "rmat10": graphs.rmat(10, 8, seed=4),
+    "hub1500": graphs.star_hub(1500, seed=5),
+    "ragged97": graphs.random_small(97, 700, seed=6),
+    "chain200": graphs.chain(200),
+}
+
+
+@pytest.mark.parametrize("R", [64, 128, 256, 512, 1024])
+@pytest.mark.parametrize("gname,model,p", [("er300", IC, 0.05), ("rmat10", WC, 0.0), ("hub1500", IC, 0.3),
+                                           ("ragged97", PER_EDGE, 0.0), ("chain200", IC, 0.9)])
+def test_registers_bit_exact(ctx, R, gname, model, p):
+    g = SMALL[gname]
+    pe = np.linspace(0.0, 0.6, g.m, dtype=np.float32) if model == PER_EDGE else None
+    assert_build_parity(ctx, g, model, p, R, seed=7 + R, p_edge=pe)
+
+
+def test_registers_er2000_workload(ctx):
+    w = workloads.er_2k()
+    assert_build_parity(ctx, w.graph, w.model, w.p, w.R, w.seed)
+
+
+@pytest.mark.parametrize("scale,ef,model,p,R", [(13, 16, WC, 0.0, 256), (12, 8, IC, 0.05, 128), (14, 16, IC, 0.01, 512)])
+def test_registers_rmat_several_tiles(ctx, scale, ef, model, p, R):
+    g = graphs.rmat(scale, ef, seed=100 + scale)
+    assert_build_parity(ctx, g, model, p, R, seed=scale)
+
+
+def test_registers_device_and_host_memory_agree(ctx):
+    g = graphs.rmat(11, 12, seed=9)
+    _, Mh, sh, vh, _ = gpu_build(ctx, g, WC, 0.0, 256, 3)
+    _, Md, sd, vd, _ = gpu_build(ctx, g, WC, 0.0, 256, 3, device="cuda")
+    assert np.array_equal(Mh, Md) and sh == sd and vh == vd
+
+
+@pytest.mark.parametrize("eps_c", [0.02, 0.2])
+def test_early_exit_matches_oracle(ctx, eps_c):
+    g = graphs.rmat(11, 16, seed=11)
+    assert_build_parity(ctx, g, WC, 0.0, 128, 5, eps_c=eps_c)
+
+
+def test_select_er2000_workload(ctx):
+    w = workloads.er_2k()
+    assert_select_parity(ctx, w.graph, w.model, w.p, w.R, w.K, w.eps_g, w.eps_l, seed=w.seed)
+
+
+@pytest.mark.parametrize("eps", [(0.0, 0.0), (math.inf, math.inf), (0.01, 0.3), (0.1, 0.5)],
+                         ids=["always", "never", "paper", "loose"])
+@pytest.mark.parametrize("gname,model,p,R", [("rmat10", WC, 0.0, 64), ("er300", IC, 0.05, 256),
+                                             ("hub1500", IC, 0.1, 128)])
+def test_select_variants(ctx, eps, gname, model, p, R):
+    g = SMALL[gname]
+    assert_select_parity(ctx, g, model, p, R, K=8, eps_g=eps[0], eps_l=eps[1], seed=21)
+
+
+def test_select_per_edge_model(ctx):
+    g = graphs.rmat(10, 10, seed=31)
+    pe = (np.arange(g.m) % 7 / 20.0).astype(np.float32)
+    assert_select_parity(ctx, g, PER_EDGE, 0.0, 128, K=6, eps_g=0.01, p_edge=pe, seed=2)
+
+
+def test_select_rmat_scale13_wc(ctx):
+    g = graphs.rmat(13, 16, seed=41)
+    assert_select_parity(ctx, g, WC, 0.0, 256, K=12, eps_g=0.01, seed=2, device="cuda")
+
+
+# --- edge cases -------------------------------------------------------------------------------------------------
+
+def test_single_vertex(ctx):
+    g = graphs.csr_from_edges(1, np.zeros(0, np.int64), np.zeros(0, np.int64))
+    assert_build_parity(ctx, g, IC, 0.5, 64, 1)
+    assert_select_parity(ctx, g, IC, 0.5, 64, K=1, eps_g=0.01)
+
+
+def test_no_edges(ctx):
+    g = graphs.csr_from_edges(70, np.zeros(0, np.int64), np.zeros(0, np.int64))
+    assert_build_parity(ctx, g, WC, 0.0, 128, 1)
+    assert_select_parity(ctx, g, WC, 0.0, 128, K=5, eps_g=0.01)
+
+
+def test_probability_zero_and_one(ctx):
+    g = graphs.rmat(9, 8, seed=51)
+    assert_build_parity(ctx, g, IC, 0.0, 64, 2)
+    assert_build_parity(ctx, g, IC, 1.0, 64, 2)
+    assert_select_parity(ctx, g, IC, 1.0, 64, K=4, eps_g=0.01)
+
+
+def test_k_equals_n(ctx):
+    g = graphs.random_small(24, 60, seed=52)
+    assert_select_parity(ctx, g, IC, 0.4, 64, K=24, eps_g=0.01)
+
+
+def test_long_chain_many_sweeps(ctx):
+    g = graphs.chain(3000)
+    assert_build_parity(ctx, g, IC, 1.0, 64, 3)
+
+
+def test_sweep_limit_reports_timeout(ctx):
+    g = graphs.chain(500)
+    graph = im.Graph.from_synth(g, IC, 1.0)
+    with pytest.raises(im.ImError) as ei:
+        ctx.im_build_sketches(graph, im.params(R=64, seed=1, max_sweeps=5))
+    assert ei.value.status == im._lib.IM_ETIMEOUT
+
+
+@pytest.mark.parametrize("case", ["decreasing_xadj", "target_out_of_range", "bad_end", "bad_R", "bad_K", "bad_p"])
+def test_invalid_arguments(ctx, case):
+    g = graphs.random_small(20, 60, seed=53)
+    xadj, adj = g.xadj.copy(), g.adj.copy()
+    prm = im.params(R=64, K=3)
+    p = 0.1
+    if case == "decreasing_xadj":
+        xadj[5], xadj[6] = xadj[6] + 1, xadj[5]
+    elif case == "target_out_of_range":
+        adj[3] = 20
+    elif case == "bad_end":
+        xadj[-1] -= 1
+    elif case == "bad_R":
+        prm = im.params(R=100, K=3)
+    elif case == "bad_K":
+        prm = im.params(R=64, K=0)
+    elif case == "bad_p":
+        p = 1.5
+    for device in (None, "cuda"):
+        gg = im.Graph.from_synth(graphs.Graph(g.n, xadj, adj), IC, p, device=device)
+        with pytest.raises(im.ImError) as ei:
+            ctx.im_select_seeds(gg, prm)
+        assert ei.value.status == im._lib.IM_EINVAL
+    # the context stays usable after a rejected call
+    assert_build_parity(ctx, g, IC, 0.1, 64, 1)
+
+
+# --- estimate ---------------------------------------------------------------------------------------------------
+
+def test_estimate_and_exact_sigma(ctx):
+    g = graphs.rmat(12, 12, seed=61)
+    R = 256
+    sk, Mo = assert_build_parity(ctx, g, WC, 0.0, R, 8)
+    probe = oracle.RegisterProbe(g.n, g.xadj, g.adj, WC, 0.0, R, 8)
+    for S in ([0], [5, 77, 1000], list(range(0, 4000, 97)), [3, 3, 9]):
+        e, sigma = sk.im_estimate(S, exact=True)
+        e_ref, _ = oracle.estimate_set(Mo, S)
+        assert e == pytest.approx(e_ref, rel=1e-12)
+        assert sigma * R == probe.reach_total(sorted(set(S)))
+        e2, none = sk.im_estimate(S)
+        assert e2 == e and none is None
+
+
+# --- batch ------------------------------------------------------------------------------------------------------
+
+def test_batch_equals_individual_and_oracle(ctx):
+    probs = [workloads.batch_problem(i, max_scale=11) for i in range(10)]
+    gs = [im.Graph.from_synth(p.graph, p.model, p.p) for p in probs]
+    prms = [im.params(R=p.R, K=p.K, eps_g=p.eps_g, eps_l=p.eps_l, seed=p.seed) for p in probs]
+    batch = ctx.im_select_seeds_batch(gs, prms)
+    for p, g, prm, b in zip(probs, gs, prms, batch):
+        single = ctx.im_select_seeds(g, prm)
+        assert b["seeds"].tolist() == single["seeds"].tolist()
+        assert b["sigma_final"] == single["sigma_final"] and b["rebuilds"] == single["rebuilds"]
+        ref = oracle.select_seeds(p.graph.n, p.graph.xadj, p.graph.adj, p.model, p.p, p.R, p.K, p.eps_g, p.eps_l,
+                                  0.0, p.seed)
+        assert b["seeds"].tolist() == ref["seeds"].tolist()
+        assert b["sigma_final"] == ref["sigma"][-1]

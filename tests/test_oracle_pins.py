@@ -370,3 +370,16 @@ def test_estimate_is_eq2(orc):
     e, gsum = orc.estimate_set(M, [0, 1])
     assert gsum == 3 + 5 + 0 + 7
     assert e == pytest.approx(2.0 ** (15 / 4) / 0.77351, rel=1e-15)
+
+
+def test_register_probe_equals_bruteforce(orc):
+    g = graphs.random_small(40, 200, 71)
+    R = 64
+    T, ok, X, Y = _problem(orc, g, WC, 0.0, R, seed=13)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X)
+    ref = bf.registers(orc, g.n, g.xadj, g.adj, live, Y)
+    probe = orc.RegisterProbe(g.n, g.xadj, g.adj, WC, 0.0, R, 13)
+    for v in range(g.n):
+        for j in range(0, R, 7):
+            assert probe(v, j) == ref[v, j]
+    assert probe.reach_total([1, 5]) == int(bf.reached_by(g.n, g.xadj, g.adj, live, [1, 5], R).sum())

@@ -275,15 +275,56 @@ def run_ours(args, world, rank, local):
     ctx.close()
 
 
+def run_build(args, local):
+    """Sketch builds of the workload (initial registers + diffusion to the fixpoint), one per step."""
+    import torch
+
+    import paper_2105_04023_gb300 as im
+    from paper_2105_04023_gb300 import build as b
+
+    torch.cuda.set_device(local)
+    b.build()
+    prob = load_workload()
+    g = prob.graph
+    graph = im.Graph.from_synth(g, prob.model, prob.p, device=f"cuda:{local}")
+    prm = im.params(R=prob.R, seed=prob.seed)
+    ctx = im.Context(local)
+    for _ in range(args.warmup):
+        ctx.im_build_sketches(graph, prm).close()
+    ctx.set_timing(True)
+    rows = []
+    for _ in range(args.steps):
+        sk = ctx.im_build_sketches(graph, prm)
+        st = ctx.stats()
+        sk.close()
+        rows.append(st)
+    hbm, _ = peaks()
+    prop_ms = sum(r["prop_ms"] for r in rows)
+    prop_bytes = sum(r["prop_bytes"] for r in rows)
+    visits = sum(r["visits"] for r in rows)
+    total_ms = sum(r["total_ms"] for r in rows)
+    out = {"mode": "build", "variant": os.environ.get("IM_PROP_VARIANT", "0"), "steps": args.steps,
+           "build_ms": total_ms / args.steps, "prop_ms": prop_ms / args.steps, "sweeps": rows[0]["sweeps"],
+           "visits": visits // args.steps, "prop_GBps": prop_bytes / prop_ms / 1e6,
+           "frac": prop_bytes / prop_ms / 1e6 / hbm, "visits_per_s": visits / (total_ms / 1000),
+           "launches": rows[0]["kernel_launches"]}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="select", choices=["select", "build"],
+                    help="build: time sketch builds only (one diffusion per step), for profiling")
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.mode == "build":
+        run_build(args, local)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)

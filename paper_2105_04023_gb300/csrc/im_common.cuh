@@ -13,6 +13,8 @@ constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kHeavyDeg = 64;        // rows with more out-edges are split into tasks of kTaskEdges edges
 constexpr int kTaskEdges = 64;
 constexpr int kBfsHeavyDeg = 256;    // search-frontier vertices with more out-edges are spread over the grid
+constexpr int kExpandHeavyDeg = 1024;  // changed vertices with more in-edges are expanded by the whole grid
+constexpr int kPfxShift = 17;        // sampling words are compared on their top 15 bits first
 
 enum Model : int32_t { kIC = 0, kWC = 1, kPerEdge = 2 };
 
@@ -25,9 +27,10 @@ struct DevCtr {
     uint32_t full;       // the current sweep visits every row (otherwise the listed ones)
     uint32_t res_par;    // register buffer (0/1) holding the diffusion's result
     uint32_t nchg;       // vertices whose registers changed in the current sweep (|L'|)
-    uint32_t nchg_list;  // entries written to chg_list
+    uint32_t nchg_list;  // entries written to chg_list (changed vertices with few in-edges)
     uint32_t nrows[2];   // listed light rows for the sweep of that parity
-    uint32_t pad0;
+    uint32_t nchg_hlist; // entries written to chg_hlist (changed vertices with many in-edges)
+    unsigned long long chg_indeg;     // sum over changed vertices of (in-degree + 1): cost of listing the next rows
     unsigned long long visits;        // edge-simulation visits, running total
     unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total
     unsigned long long sweeps_total;  // sweeps, running total
@@ -69,13 +72,15 @@ struct DevProb {
     const uint32_t *T_edge;    // per-edge model: threshold per edge
     const uint8_t *ok_edge;    // per-edge model: p > 0
     const uint32_t *X;         // sampling words X_r (Eq. 5)
+    const uint32_t *xpfx;      // 2^15 bits: some X_r has this value of X_r >> kPfxShift
     const uint32_t *Y;         // initialisation words ("hash(j)" of Algorithm 1)
     uint8_t *M0, *M1;          // register buffers (Jacobi pair)
     uint8_t *part;             // n_tasks x R partial maxima of heavy-row tasks
     uint32_t *part_any;        // bit per task: the task merged at least one neighbour
     uint32_t *Lb0, *Lb1;       // frontier bits: vertices changed in the previous sweep
-    uint32_t *mark;            // rows listed for the next sweep
-    int32_t *chg_list;         // compacted changed vertices
+    uint8_t *mark8;            // byte per row (padded to 32): row is visited by the next sweep
+    int32_t *chg_list;         // compacted changed vertices with few in-edges
+    int32_t *chg_hlist;        // compacted changed vertices with many in-edges
     int32_t *rows0, *rows1;    // light rows of the sweep of that parity
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
     uint32_t *del0, *del1;     // n x W: bits newly reached at the previous level, by parity
@@ -85,7 +90,7 @@ struct DevProb {
     uint8_t *MS;               // R bytes: M_S'
     DevCtr *ctr;
     uint32_t stop_thr;         // diffusion stops when |L'| <= stop_thr
-    uint32_t full_thr;         // a sweep after one with more changes than this visits every row
+    uint64_t list_thr;         // next sweep lists its rows when chg_indeg <= list_thr, else visits every row
     uint32_t max_sweeps;       // sweep / level limit
     int32_t flog_cap;
     int64_t *flog;             // |L| at the start of each sweep of the current diffusion

@@ -322,7 +322,9 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     d.ok_edge = g.ok_edge;
     uint32_t *X = mem.alloc<uint32_t>(R);
     uint32_t *Y = mem.alloc<uint32_t>(R);
-    launch_words(prm.seed, R, X, Y, ctx->stream);
+    uint32_t *xpfx = mem.alloc<uint32_t>(1u << (32 - kPfxShift - 5), true);
+    launch_words(prm.seed, R, X, Y, xpfx, ctx->stream);
+    d.xpfx = xpfx;
     ctx->launches += 1;
     d.X = X;
     d.Y = Y;
@@ -333,8 +335,9 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     const int64_t words = (n + 31) / 32;
     d.Lb0 = mem.alloc<uint32_t>(words, true);
     d.Lb1 = mem.alloc<uint32_t>(words, true);
-    d.mark = mem.alloc<uint32_t>(words, true);
+    d.mark8 = mem.alloc<uint8_t>(32 * words, true);
     d.chg_list = mem.alloc<int32_t>(n);
+    d.chg_hlist = mem.alloc<int32_t>(n);
     d.rows0 = mem.alloc<int32_t>(n);
     d.rows1 = mem.alloc<int32_t>(n);
     d.MS = mem.alloc<uint8_t>(R, true);
@@ -343,7 +346,8 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     // stop after the first sweep with |L'| <= eps_c * n: the largest integer count satisfying it
     const double thr = static_cast<double>(n) * prm.eps_c;
     d.stop_thr = static_cast<uint32_t>(std::floor(thr));
-    d.full_thr = static_cast<uint32_t>(std::max<int64_t>(n / 8, 1024));
+    // list the next sweep's rows when marking them costs well under a full visit of every row and edge
+    d.list_thr = static_cast<uint64_t>((g.m + n) / 8);
     P->flog_cap = 4096;
     d.flog_cap = static_cast<int32_t>(P->flog_cap);
     d.flog = mem.alloc<int64_t>(P->flog_cap, true);

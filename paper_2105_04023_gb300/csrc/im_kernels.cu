@@ -13,6 +13,8 @@
 //   k_scan, k_choose                          Algorithm 1, argmax of Estimate(Merge(M_S', M_v)) (Eq. 2-3)
 //   k_bfs_*                                   Algorithm 1, reachability set of S in every simulation, sigma
 //   k_merge                                   Algorithm 1, M_S' <- Merge(M_S', M_s)
+#include <cstdlib>
+
 #include "im_common.cuh"
 #include "im_launch.h"
 
@@ -36,67 +38,78 @@ struct Geo {
     static constexpr int CPL = CH / G;              // chunks per lane
 };
 
-struct Stats {
-    unsigned long long visits = 0, bytes = 0;
-    unsigned int nchg = 0;
-};
-
-__device__ __forceinline__ void flush_stats(DevCtr *C, Stats &st, int lane) {
-    if (lane == 0) {
-        if (st.visits) atomicAdd(&C->visits, st.visits);
-        if (st.bytes) atomicAdd(&C->bytes, st.bytes);
-        if (st.nchg) atomicAdd(&C->nchg, st.nchg);
-    }
-    st = Stats();
+// Byte-wise max of registers.  Every register value is <= 32 < 128, so per byte a - b + 128 lies in [1, 255]: the
+// word subtraction below never carries across bytes and bit 7 of each byte is (a >= b); prmt replicates it.
+__device__ __forceinline__ uint32_t sign_bytes(uint32_t x, uint32_t y, uint32_t sel) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(y), "r"(sel));
+    return r;
 }
 
-__device__ __forceinline__ uint32_t vmax4(uint32_t a, uint32_t b) { return __vmaxu4(a, b); }
-
-// Bytes of (h XOR X_j) whose top byte ties with T's top byte: decide them with the full 32-bit compare.
-__device__ __noinline__ uint32_t tie_break(uint32_t eq, uint32_t h, uint32_t T, const uint32_t *__restrict__ Xj) {
-    uint32_t live = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-        if (((eq >> (8 * b)) & 0xFFu) && ((h ^ __ldg(&Xj[b])) <= T)) live |= 0xFFu << (8 * b);
-    return live;
+__device__ __forceinline__ uint32_t vmax4(uint32_t a, uint32_t b) {
+    const uint32_t ge = sign_bytes(a + 0x80808080u - b, 0u, 0xBA98u);
+    return (a & ge) | (b & ~ge);
 }
 
-// Eq. 5 for 4 simulations at once, then the register-wise max of Eq. 3 restricted to live simulations.
-// xt packs the top bytes of X_j for the 4 simulations; only ties on the top byte need the full compare.
+// Eq. 5 on the top 15 bits, two simulations per word: a = (h ^ X_j) >> 17 and t = T >> 17 sit in 16-bit halves and
+// a + 0x8000 - t stays in [1, 0xFFFF], so the sign bit of each half is (a >= t).  A 15-bit tie (a == t) is the only
+// case the top bits cannot decide; edges where it can happen are flagged and take the exact path.
+// xt[2w] packs simulations 4w, 4w+1 of the chunk, xt[2w+1] packs 4w+2, 4w+3.  ge = 0xFF in each byte whose
+// simulation is not live.
+__device__ __forceinline__ uint32_t dead_bytes(uint32_t xlo, uint32_t xhi, uint32_t ht, uint32_t K) {
+    const uint32_t dlo = (xlo ^ ht) + K;
+    const uint32_t dhi = (xhi ^ ht) + K;
+    return sign_bytes(dlo, dhi, 0xFDB9u);
+}
+
 template <int R>
-__device__ __forceinline__ void merge_row(uint32_t (&acc)[Geo<R>::CPL][4], const uint4 (&row)[Geo<R>::CPL],
-                                          const uint32_t (&xt)[Geo<R>::CPL][4], uint32_t h, uint32_t T,
-                                          const uint32_t *__restrict__ X, int li) {
-    const uint32_t ht = (h >> 24) * 0x01010101u;
-    const uint32_t tt = (T >> 24) * 0x01010101u;
+__device__ __forceinline__ void merge_fast(uint32_t (&acc)[Geo<R>::CPL][4], const uint4 (&row)[Geo<R>::CPL],
+                                           const uint32_t (&xt)[Geo<R>::CPL][8], uint32_t ht, uint32_t K) {
 #pragma unroll
     for (int c = 0; c < Geo<R>::CPL; ++c) {
         const uint32_t rw[4] = {row[c].x, row[c].y, row[c].z, row[c].w};
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            const uint32_t a = xt[c][w] ^ ht;
-            uint32_t live = __vcmpltu4(a, tt);
-            const uint32_t eq = __vcmpeq4(a, tt);
-            if (eq) live |= tie_break(eq, h, T, X + 16 * (li + Geo<R>::G * c) + 4 * w);
+            const uint32_t ge = dead_bytes(xt[c][2 * w], xt[c][2 * w + 1], ht, K);
+            acc[c][w] = vmax4(acc[c][w], rw[w] & ~ge);
+        }
+    }
+}
+
+// The same merge with the full 32-bit test of every simulation (edges with a possible 15-bit tie).
+template <int R>
+__device__ __noinline__ void merge_exact(uint32_t (&acc)[Geo<R>::CPL][4], const uint4 (&row)[Geo<R>::CPL],
+                                         uint32_t h, uint32_t T, const uint32_t *__restrict__ X, int li) {
+#pragma unroll
+    for (int c = 0; c < Geo<R>::CPL; ++c) {
+        const uint32_t rw[4] = {row[c].x, row[c].y, row[c].z, row[c].w};
+        const uint32_t *x = X + 16 * (li + Geo<R>::G * c);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            uint32_t live = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if ((h ^ __ldg(&x[4 * w + b])) <= T) live |= 0xFFu << (8 * b);
             acc[c][w] = vmax4(acc[c][w], rw[w] & live);
         }
     }
 }
 
 template <int R>
-__device__ __forceinline__ void load_xt(const uint32_t *__restrict__ X, int li, uint32_t (&xt)[Geo<R>::CPL][4]) {
+__device__ __forceinline__ void load_xt(const uint32_t *__restrict__ X, int li, uint32_t (&xt)[Geo<R>::CPL][8]) {
 #pragma unroll
     for (int c = 0; c < Geo<R>::CPL; ++c)
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const uint32_t *x = X + 16 * (li + Geo<R>::G * c) + 4 * w;
-            xt[c][w] = (__ldg(x) >> 24) | ((__ldg(x + 1) >> 24) << 8) | ((__ldg(x + 2) >> 24) << 16) |
-                       (__ldg(x + 3) & 0xFF000000u);
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t *x = X + 16 * (li + Geo<R>::G * c) + 2 * k;
+            xt[c][k] = (__ldg(x) >> kPfxShift) | ((__ldg(x + 1) >> kPfxShift) << 16);
         }
 }
 
 struct WarpStage {
-    int32_t v[32];
+    int32_t v[32];    // neighbour id; bit 31 set when the edge needs the exact test
+    uint32_t ht[32];  // (h >> 17) in both halves
+    uint32_t K[32];   // 0x8000 - (T >> 17) in both halves
     uint32_t h[32];
     uint32_t T[32];
 };
@@ -107,7 +120,7 @@ struct WarpStage {
 template <int R, int UNR>
 __device__ __forceinline__ void scan_range(const DevProb &P, int64_t u, int64_t e0, int64_t e1, bool allL,
                                            const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
-                                           uint32_t (&acc)[Geo<R>::CPL][4], const uint32_t (&xt)[Geo<R>::CPL][4],
+                                           uint32_t (&acc)[Geo<R>::CPL][4], const uint32_t (&xt)[Geo<R>::CPL][8],
                                            int lane, int g, int li, WarpStage &sw, uint32_t &nL,
                                            uint32_t &nTaken) {
     using Gm = Geo<R>;
@@ -129,8 +142,13 @@ __device__ __forceinline__ void scan_range(const DevProb &P, int64_t u, int64_t 
         if (mT == 0) continue;
         if (take) {
             const int r = __popc(mT & ((1u << lane) - 1u));
-            sw.v[r] = v;
-            sw.h[r] = edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
+            const uint32_t h =
+                edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
+            const bool tie = test_bit(P.xpfx, (h ^ T) >> kPfxShift);
+            sw.v[r] = v | (tie ? static_cast<int32_t>(0x80000000u) : 0);
+            sw.ht[r] = (h >> kPfxShift) * 0x00010001u;
+            sw.K[r] = (0x8000u - (T >> kPfxShift)) * 0x00010001u;
+            sw.h[r] = h;
             sw.T[r] = T;
         }
         __syncwarp();
@@ -138,24 +156,27 @@ __device__ __forceinline__ void scan_range(const DevProb &P, int64_t u, int64_t 
         nTaken += cnt;
         for (int i0 = 0; i0 < cnt; i0 += Gm::NG * UNR) {
             uint4 row[UNR][Gm::CPL];
-            uint32_t hh[UNR], TT[UNR];
-            bool have[UNR];
+            int32_t vt[UNR];
 #pragma unroll
             for (int k = 0; k < UNR; ++k) {
                 const int idx = i0 + g + k * Gm::NG;
-                have[k] = idx < cnt;
-                if (have[k]) {
-                    const int32_t vv = sw.v[idx];
-                    hh[k] = sw.h[idx];
-                    TT[k] = sw.T[idx];
-                    const uint4 *src = reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(vv) * R);
+                vt[k] = idx < cnt ? sw.v[idx] : -1;
+                if (idx < cnt) {
+                    const uint4 *src =
+                        reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(vt[k] & 0x7FFFFFFF) * R);
 #pragma unroll
                     for (int c = 0; c < Gm::CPL; ++c) row[k][c] = __ldg(src + li + Gm::G * c);
                 }
             }
 #pragma unroll
-            for (int k = 0; k < UNR; ++k)
-                if (have[k]) merge_row<R>(acc, row[k], xt, hh[k], TT[k], P.X, li);
+            for (int k = 0; k < UNR; ++k) {
+                const int idx = i0 + g + k * Gm::NG;
+                if (idx >= cnt) continue;
+                if (vt[k] >= 0)
+                    merge_fast<R>(acc, row[k], xt, sw.ht[idx], sw.K[idx]);
+                else
+                    merge_exact<R>(acc, row[k], sw.h[idx], sw.T[idx], P.X, li);
+            }
         }
         __syncwarp();
     }
@@ -172,6 +193,25 @@ __device__ __forceinline__ void reduce_groups(uint32_t (&acc)[Geo<R>::CPL][4]) {
 }
 
 __device__ __forceinline__ uint64_t thr_bytes(int32_t model) { return model == kWC ? 4 : (model == kPerEdge ? 5 : 0); }
+
+__device__ __forceinline__ uint64_t in_degree(const DevProb &P, int64_t v) {
+    return static_cast<uint64_t>(__ldg(&P.xadj_in[v + 1]) - __ldg(&P.xadj_in[v]));
+}
+
+struct Stats {
+    unsigned long long visits = 0, bytes = 0, indeg = 0;
+    unsigned int nchg = 0;
+};
+
+__device__ __forceinline__ void flush_stats(DevCtr *C, Stats &st, int lane) {
+    if (lane == 0) {
+        if (st.visits) atomicAdd(&C->visits, st.visits);
+        if (st.bytes) atomicAdd(&C->bytes, st.bytes);
+        if (st.nchg) atomicAdd(&C->nchg, st.nchg);
+        if (st.indeg) atomicAdd(&C->chg_indeg, st.indeg);
+    }
+    st = Stats();
+}
 
 // New registers of row u = max(own row, merged neighbours).  The row is written to the other buffer when it
 // changed, or when the buffers may differ at u (u changed in the previous sweep); a changed row joins L'.
@@ -200,7 +240,10 @@ __device__ __forceinline__ void finalize_row(const DevProb &P, int64_t u, uint32
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
     }
-    if (changed && lane == 0) set_bit(Lnext, u);
+    if (changed && lane == 0) {
+        set_bit(Lnext, u);
+        st.indeg += in_degree(P, u) + 1;
+    }
     st.nchg += changed ? 1u : 0u;
     st.bytes += R + ((changed || sync) ? R : 0);
 }
@@ -210,7 +253,7 @@ __device__ void prop_problem(const DevProb &P, uint32_t t, bool full, uint64_t n
                              uint64_t nworkers, int lane, WarpStage &sw) {
     using Gm = Geo<R>;
     const int g = lane / Gm::G, li = lane % Gm::G;
-    uint32_t xt[Gm::CPL][4];
+    uint32_t xt[Gm::CPL][8];
     load_xt<R>(P.X, li, xt);
     const bool par = t & 1u;
     const uint8_t *Mcur = par ? P.M1 : P.M0;
@@ -232,14 +275,17 @@ __device__ void prop_problem(const DevProb &P, uint32_t t, bool full, uint64_t n
             const int64_t u = full ? static_cast<int64_t>(l) : static_cast<int64_t>(rows[l]);
             if (full && test_bit(P.heavy, u)) continue;
             const int64_t e0 = __ldg(&P.xadj[u]), e1 = __ldg(&P.xadj[u + 1]);
+            const bool sync = test_bit(Lcur, u);
+            if (e0 == e1 && !sync) continue;
             scan_range<R, UNR>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, nL, nTaken);
             reduce_groups<R>(acc);
             st.visits += static_cast<unsigned long long>(nL) * R;
             st.bytes += 16 + 4 * static_cast<uint64_t>(e1 - e0) + tb * nL + static_cast<uint64_t>(nTaken) * R;
-            finalize_row<R>(P, u, acc, nTaken > 0, test_bit(Lcur, u), Mcur, Mnext, Lnext, lane, g, li, st);
+            finalize_row<R>(P, u, acc, nTaken > 0, sync, Mcur, Mnext, Lnext, lane, g, li, st);
         } else {
             const int64_t task = static_cast<int64_t>(l - nlight);
             const int64_t u = __ldg(&P.task_row[task]);
+            if (!full && !P.mark8[u]) continue;
             const int64_t e0 = __ldg(&P.xadj[u]) + (task - __ldg(&P.task_off[u])) * kTaskEdges;
             const int64_t e1 = min(e0 + kTaskEdges, __ldg(&P.xadj[u + 1]));
             scan_range<R, UNR>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, nL, nTaken);
@@ -268,9 +314,9 @@ __device__ __forceinline__ uint64_t prop_light_count(const DevProb &P, const Dev
 
 }  // namespace
 
-template <int R, int UNR>
-__global__ void __launch_bounds__(kBlock) k_prop(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
-                                                 int nact) {
+template <int R, int UNR, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_prop(const DevProb *__restrict__ probs,
+                                                       const int32_t *__restrict__ act, int nact) {
     __shared__ WarpStage stage[kWarpsPerBlock];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
@@ -294,8 +340,8 @@ __global__ void __launch_bounds__(kBlock) k_prop(const DevProb *__restrict__ pro
 namespace {
 
 template <int R>
-__device__ void combine_problem(const DevProb &P, uint32_t t, uint64_t cnt, uint64_t first, uint64_t nworkers,
-                                int lane) {
+__device__ void combine_problem(const DevProb &P, uint32_t t, bool full, uint64_t cnt, uint64_t first,
+                                uint64_t nworkers, int lane) {
     using Gm = Geo<R>;
     const int g = lane / Gm::G, li = lane % Gm::G;
     const bool par = t & 1u;
@@ -306,6 +352,7 @@ __device__ void combine_problem(const DevProb &P, uint32_t t, uint64_t cnt, uint
     Stats st;
     for (uint64_t l = first; l < cnt; l += nworkers) {
         const int64_t u = P.heavy_rows[l];
+        if (!full && !P.mark8[u]) continue;
         const int64_t t0 = __ldg(&P.task_off[u]), t1 = __ldg(&P.task_off[u + 1]);
         uint32_t acc[Gm::CPL][4];
 #pragma unroll
@@ -339,6 +386,7 @@ __device__ void combine_problem(const DevProb &P, uint32_t t, uint64_t cnt, uint
         reduce_groups<R>(acc);
         st.bytes += 16;
         finalize_row<R>(P, u, acc, any, test_bit(Lcur, u), Mcur, Mnext, Lnext, lane, g, li, st);
+        if (lane == 0) P.mark8[u] = 0;
     }
     flush_stats(P.ctr, st, lane);
 }
@@ -360,7 +408,7 @@ __global__ void __launch_bounds__(kBlock) k_combine(const DevProb *__restrict__ 
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
         if (first >= cnt) continue;
-        combine_problem<R>(P, C.t, cnt, first, nworkers, lane);
+        combine_problem<R>(P, C.t, C.full != 0, cnt, first, nworkers, lane);
     }
 }
 
@@ -404,10 +452,15 @@ __device__ __forceinline__ bool sweep_stops(const DevProb &P, const DevCtr &C) {
     return C.nchg <= P.stop_thr || C.t + 1 >= P.max_sweeps;
 }
 
+// The next sweep visits listed rows when listing them is cheap (few in-edges into the changed vertices).
+__device__ __forceinline__ bool next_is_listed(const DevProb &P, const DevCtr &C) {
+    return C.chg_indeg <= P.list_thr;
+}
+
 }  // namespace
 
 // After sweep t: clear L_t's bits (the buffer L_{t+2} will be written to) and, when the next sweep is a listed one,
-// compact L_{t+1} into chg_list.
+// compact L_{t+1} into the changed-vertex lists (split by in-degree).
 __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__ probs,
                                                      const int32_t *__restrict__ act, int nact) {
     uint64_t base = 0;
@@ -415,7 +468,7 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
         if (C.done || sweep_stops(P, C)) continue;
-        const bool list_next = C.nchg <= P.full_thr;
+        const bool list_next = next_is_listed(P, C);
         const bool par = C.t & 1u;
         uint32_t *Lold = par ? P.Lb1 : P.Lb0;
         const uint32_t *Lnew = par ? P.Lb0 : P.Lb1;
@@ -430,42 +483,74 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
                 Lold[i] = 0;
                 w = Lnew[i];
             }
-            if (list_next) block_append_bits(w, i, P.chg_list, &P.ctr->nchg_list);
+            if (list_next) {
+                uint32_t wh = 0;
+                for (uint32_t x = w; x;) {
+                    const int b = __ffs(x) - 1;
+                    x &= x - 1;
+                    if (in_degree(P, i * 32 + b) > kExpandHeavyDeg) wh |= 1u << b;
+                }
+                block_append_bits(w & ~wh, i, P.chg_list, &P.ctr->nchg_list);
+                if (__syncthreads_or(wh != 0)) block_append_bits(wh, i, P.chg_hlist, &P.ctr->nchg_hlist);
+            }
         }
     }
 }
 
-// Marks every row that must be visited in the next sweep: the changed vertices themselves and their in-neighbours.
+// Marks every row that must be visited in the next sweep: the changed vertices themselves and their in-neighbours
+// (plain byte stores: a row marked twice is the same mark).
 __global__ void __launch_bounds__(kBlock) k_expand(const DevProb *__restrict__ probs,
                                                    const int32_t *__restrict__ act, int nact) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
-    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
-    uint64_t base = 0;
-    for (int q = 0; q < nact; ++q) {
-        const DevProb &P = probs[act[q]];
-        const DevCtr &C = *P.ctr;
-        if (C.done || sweep_stops(P, C) || C.nchg > P.full_thr) continue;
-        const uint64_t cnt = C.nchg_list;
-        const uint64_t first = first_owned(worker, nworkers, base);
-        base += cnt;
-        for (uint64_t l = first; l < cnt; l += nworkers) {
-            const int32_t v = P.chg_list[l];
-            if (lane == 0) set_bit(P.mark, v);
-            const int64_t e0 = __ldg(&P.xadj_in[v]), e1 = __ldg(&P.xadj_in[v + 1]);
-            for (int64_t e = e0 + lane; e < e1; e += 32) set_bit(P.mark, __ldg(&P.adj_in[e]));
+    {
+        const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+        const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+        uint64_t base = 0;
+        for (int q = 0; q < nact; ++q) {
+            const DevProb &P = probs[act[q]];
+            const DevCtr &C = *P.ctr;
+            if (C.done || sweep_stops(P, C) || !next_is_listed(P, C)) continue;
+            const uint64_t cnt = C.nchg_list;
+            const uint64_t first = first_owned(worker, nworkers, base);
+            base += cnt;
+            for (uint64_t l = first; l < cnt; l += nworkers) {
+                const int32_t v = P.chg_list[l];
+                if (lane == 0) P.mark8[v] = 1;
+                const int64_t e0 = __ldg(&P.xadj_in[v]), e1 = __ldg(&P.xadj_in[v + 1]);
+                for (int64_t e = e0 + lane; e < e1; e += 32) P.mark8[__ldg(&P.adj_in[e])] = 1;
+            }
+        }
+    }
+    {
+        const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+        const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+        uint64_t base = 0;
+        for (int q = 0; q < nact; ++q) {
+            const DevProb &P = probs[act[q]];
+            const DevCtr &C = *P.ctr;
+            if (C.done || sweep_stops(P, C) || !next_is_listed(P, C)) continue;
+            for (uint32_t i = 0; i < C.nchg_hlist; ++i) {
+                const int32_t v = P.chg_hlist[i];
+                const int64_t e0 = P.xadj_in[v], e1 = P.xadj_in[v + 1];
+                const uint64_t cnt = static_cast<uint64_t>(e1 - e0) + 1;
+                const uint64_t first = first_owned(tid, nthreads, base);
+                base += cnt;
+                for (uint64_t l = first; l < cnt; l += nthreads)
+                    P.mark8[l + 1 == cnt ? v : __ldg(&P.adj_in[e0 + l])] = 1;
+            }
         }
     }
 }
 
-// Compacts the marked light rows into the row list of the next sweep and clears the marks.
+// Compacts the marked light rows into the row list of the next sweep and clears their marks (marks of heavy rows
+// stay for the task and combine kernels of the next sweep).
 __global__ void __launch_bounds__(kBlock) k_rows(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
                                                  int nact) {
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
-        if (C.done || sweep_stops(P, C) || C.nchg > P.full_thr) continue;
+        if (C.done || sweep_stops(P, C) || !next_is_listed(P, C)) continue;
         const uint32_t np = (C.t + 1) & 1u;
         int32_t *rows = np ? P.rows1 : P.rows0;
         const int64_t words = (P.n + 31) >> 5;
@@ -476,11 +561,29 @@ __global__ void __launch_bounds__(kBlock) k_rows(const DevProb *__restrict__ pro
             const int64_t i = static_cast<int64_t>(ch) * kBlock + threadIdx.x;
             uint32_t w = 0;
             if (i < words) {
-                w = P.mark[i];
-                if (w) {
-                    P.mark[i] = 0;
-                    w &= ~P.heavy[i];
+                uint4 *mp = reinterpret_cast<uint4 *>(P.mark8 + 32 * i);
+                uint4 a = mp[0], b = mp[1];
+                const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if ((x[k] >> (8 * j)) & 0xFFu) w |= 1u << (4 * k + j);
+                const uint32_t light = w & ~P.heavy[i];
+                if (light) {
+                    uint32_t y[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        uint32_t keep = 0;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (!((light >> (4 * k + j)) & 1u)) keep |= 0xFFu << (8 * j);
+                        y[k] = x[k] & keep;
+                    }
+                    mp[0] = make_uint4(y[0], y[1], y[2], y[3]);
+                    mp[1] = make_uint4(y[4], y[5], y[6], y[7]);
                 }
+                w = light;
             }
             block_append_bits(w, i, rows, &P.ctr->nrows[np]);
         }
@@ -505,10 +608,12 @@ __global__ void k_advance(const DevProb *__restrict__ probs, const int32_t *__re
         C.timeout = (!stop && lim) ? 1u : 0u;
         C.res_par = (t + 1) & 1u;
     }
-    C.full = nchg > P.full_thr ? 1u : 0u;
+    C.full = next_is_listed(P, C) ? 0u : 1u;
     C.nrows[t & 1u] = 0;
     C.nchg = 0;
     C.nchg_list = 0;
+    C.nchg_hlist = 0;
+    C.chg_indeg = 0;
     C.t = t + 1;
 }
 
@@ -525,7 +630,8 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
         const uint64_t nchunks = static_cast<uint64_t>(P.n) * CH;
         const int64_t words = (P.n + 31) >> 5;
         const int64_t twords = (P.n_tasks + 31) >> 5;
-        const uint64_t cnt = nchunks + 3 * static_cast<uint64_t>(words) + static_cast<uint64_t>(twords) + 1;
+        // units: register chunks, then L bits (2 x words), mark bytes (8 x words as 4-byte words), task bits, counters
+        const uint64_t cnt = nchunks + 10 * static_cast<uint64_t>(words) + static_cast<uint64_t>(twords) + 1;
         const uint64_t first = first_owned(tid, nthreads, base);
         base += cnt;
         for (uint64_t l = first; l < cnt; l += nthreads) {
@@ -550,13 +656,13 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 const uint4 val = make_uint4(w[0], w[1], w[2], w[3]);
                 reinterpret_cast<uint4 *>(P.M0)[l] = val;
                 reinterpret_cast<uint4 *>(P.M1)[l] = val;
-            } else if (l < nchunks + 3 * static_cast<uint64_t>(words)) {
+            } else if (l < nchunks + 2 * static_cast<uint64_t>(words)) {
                 const uint64_t k = l - nchunks;
-                const int64_t i = static_cast<int64_t>(k % words);
-                const int which = static_cast<int>(k / words);
-                (which == 0 ? P.Lb0 : which == 1 ? P.Lb1 : P.mark)[i] = 0;
+                (k < static_cast<uint64_t>(words) ? P.Lb0 : P.Lb1)[k % words] = 0;
+            } else if (l < nchunks + 10 * static_cast<uint64_t>(words)) {
+                reinterpret_cast<uint32_t *>(P.mark8)[l - nchunks - 2 * static_cast<uint64_t>(words)] = 0;
             } else if (l < cnt - 1) {
-                P.part_any[l - nchunks - 3 * static_cast<uint64_t>(words)] = 0;
+                P.part_any[l - nchunks - 10 * static_cast<uint64_t>(words)] = 0;
             } else {
                 DevCtr &C = *P.ctr;
                 C.t = 0;
@@ -566,6 +672,8 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 C.res_par = 0;
                 C.nchg = 0;
                 C.nchg_list = 0;
+                C.nchg_hlist = 0;
+                C.chg_indeg = 0;
                 C.nrows[0] = 0;
                 C.nrows[1] = 0;
                 if (P.flog_cap > 0) P.flog[0] = P.n;
@@ -960,11 +1068,15 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
     return z ^ (z >> 31);
 }
 
-__global__ void k_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y) {
+// Simulation words (reading of Section 3.1: X_r, Y_r are the high halves of splitmix64 outputs 2r and 2r+1) and
+// the bitmap of their top-15-bit prefixes (xpfx must be zero on entry).
+__global__ void k_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
-    X[r] = static_cast<uint32_t>(splitmix64_at(seed, 2ull * r) >> 32);
+    const uint32_t x = static_cast<uint32_t>(splitmix64_at(seed, 2ull * r) >> 32);
+    X[r] = x;
     Y[r] = static_cast<uint32_t>(splitmix64_at(seed, 2ull * r + 1) >> 32);
+    set_bit(xpfx, x >> kPfxShift);
 }
 
 __global__ void k_indeg(const int32_t *__restrict__ adj, int64_t m, int32_t *__restrict__ indeg) {
@@ -1104,6 +1216,8 @@ __global__ void k_edge_thresholds(const float *__restrict__ p, int64_t m, uint32
 // ------------------------------------------------------------------------------------------------------------
 // Host-side launchers
 
+static int g_sms = 0;
+static int g_variant = 0;     // propagation launch shape (IM_PROP_VARIANT)
 static int g_grid_warp = 0;   // blocks for warp-striped kernels
 static int g_grid_block = 0;  // blocks for block-striped kernels
 
@@ -1112,12 +1226,40 @@ cudaError_t configure(int device) {
     cudaError_t e = cudaGetDeviceProperties(&prop, device);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prop<256, 2>, kBlock, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prop<256, 2, 1>, kBlock, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
+    g_sms = prop.multiProcessorCount;
     g_grid_warp = prop.multiProcessorCount * occ;
     g_grid_block = prop.multiProcessorCount * 4;
+    if (const char *v = getenv("IM_PROP_VARIANT")) g_variant = atoi(v);
     return cudaSuccess;
+}
+
+// Launch shapes of the propagation kernel: (edges in flight per neighbour group, minimum resident blocks per SM).
+// The grid is sized from the occupancy each shape reaches.
+template <int R, int UNR, int MINB>
+static void launch_prop_shape(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    static int grid = 0;
+    if (grid == 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prop<R, UNR, MINB>, kBlock, 0);
+        grid = g_sms * (occ > 0 ? occ : 1);
+    }
+    k_prop<R, UNR, MINB><<<grid, kBlock, 0, s>>>(probs, act, nact);
+}
+
+template <int R>
+static void launch_prop_r(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    switch (g_variant) {
+        case 1: launch_prop_shape<R, 4, 1>(probs, act, nact, s); break;
+        case 2: launch_prop_shape<R, 2, 3>(probs, act, nact, s); break;
+        case 3: launch_prop_shape<R, 4, 3>(probs, act, nact, s); break;
+        case 4: launch_prop_shape<R, 2, 4>(probs, act, nact, s); break;
+        case 5: launch_prop_shape<R, 8, 2>(probs, act, nact, s); break;
+        case 6: launch_prop_shape<R, 1, 4>(probs, act, nact, s); break;
+        default: launch_prop_shape<R, 2, 1>(probs, act, nact, s); break;
+    }
 }
 
 int grid_warp() { return g_grid_warp; }
@@ -1133,7 +1275,11 @@ int grid_warp() { return g_grid_warp; }
     }
 
 void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    IMK_R_SWITCH(R, (k_prop<RR, 2><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
+    if (R == 256) {
+        launch_prop_r<256>(probs, act, nact, s);
+        return;
+    }
+    IMK_R_SWITCH(R, (launch_prop_shape<RR, 2, 1>(probs, act, nact, s)));
 }
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     IMK_R_SWITCH(R, (k_combine<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
@@ -1185,8 +1331,8 @@ void launch_edge_thresholds(const float *p, int64_t m, uint32_t *T, uint8_t *ok,
                             cudaStream_t s) {
     if (m > 0) k_edge_thresholds<<<g_grid_block, kBlock, 0, s>>>(p, m, T, ok, flags);
 }
-void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, cudaStream_t s) {
-    k_words<<<(R + 255) / 256, 256, 0, s>>>(seed, R, X, Y);
+void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx, cudaStream_t s) {
+    k_words<<<(R + 255) / 256, 256, 0, s>>>(seed, R, X, Y, xpfx);
 }
 void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s) {
     if (m > 0) k_indeg<<<g_grid_block, kBlock, 0, s>>>(adj, m, indeg);

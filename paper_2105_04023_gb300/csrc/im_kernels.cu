@@ -213,6 +213,26 @@ __device__ __forceinline__ void flush_stats(DevCtr *C, Stats &st, int lane) {
     st = Stats();
 }
 
+// Every lane may hold counts: reduce over the warp, then one atomic per field.
+__device__ __forceinline__ void flush_stats_warp(DevCtr *C, Stats &st) {
+    unsigned long long v = st.visits, b = st.bytes, d = st.indeg;
+    unsigned int c = st.nchg;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        v += __shfl_xor_sync(kFull, v, off);
+        b += __shfl_xor_sync(kFull, b, off);
+        d += __shfl_xor_sync(kFull, d, off);
+        c += __shfl_xor_sync(kFull, c, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (v) atomicAdd(&C->visits, v);
+        if (b) atomicAdd(&C->bytes, b);
+        if (c) atomicAdd(&C->nchg, c);
+        if (d) atomicAdd(&C->chg_indeg, d);
+    }
+    st = Stats();
+}
+
 // New registers of row u = max(own row, merged neighbours).  The row is written to the other buffer when it
 // changed, or when the buffers may differ at u (u changed in the previous sweep); a changed row joins L'.
 template <int R>
@@ -334,6 +354,320 @@ __global__ void __launch_bounds__(kBlock, MINB) k_prop(const DevProb *__restrict
         base += cnt;
         if (first >= cnt) continue;
         prop_problem<R, UNR>(P, t, full, nlight, cnt, first, nworkers, lane, stage[wib]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Tile form of the propagation sweep.  A block of kTileT threads takes a tile of consecutive work rows whose
+// edges total at most kTileT (or one kTileEdges task of a heavy row), stages every edge of the tile at once
+// (one thread per edge: target, live-set test, threshold, hash), copies the register rows of all sampled targets
+// into shared memory with cp.async (up to kTileT rows in flight per block, no registers held while they travel),
+// then merges them row by row from shared memory.
+
+namespace {
+
+constexpr int kTileT = 128;
+
+template <int R>
+struct TileSmem {
+    uint4 slot[kTileT][R / 16];  // gathered neighbour rows
+    int64_t row_e0[kTileT];      // first edge of row r
+    int32_t row_u[kTileT];       // rows of the tile
+    int32_t row_pre[kTileT + 1]; // tile edges before row r
+    int32_t take_pre[kTileT + 1];// sampled tile edges before tile edge t
+    uint32_t row_sync[kTileT];   // row changed in the previous sweep (buffers may differ there)
+    int32_t e_v[kTileT];         // per sampled edge: target, bit 31 = needs the exact test
+    uint32_t e_ht[kTileT], e_K[kTileT], e_h[kTileT], e_T[kTileT];
+    int32_t warp_tmp[kTileT / 32];
+    int32_t n_rows;
+    int32_t n_edges;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// Exclusive scan of one int per thread over the kTileT threads of the block; returns the total in *total.
+__device__ __forceinline__ int32_t tile_exclusive_scan(int32_t x, int32_t *warp_tmp, int32_t *total) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int32_t incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int32_t y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_tmp[wib] = incl;
+    __syncthreads();
+    int32_t before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kTileT / 32; ++w) {
+        const int32_t t = warp_tmp[w];
+        before += (w < wib) ? t : 0;
+        all += t;
+    }
+    __syncthreads();
+    *total = all;
+    return before + incl - x;
+}
+
+// One tile.  rows: n_rows row ids with their degrees already prefix-summed into S.row_pre; for a task tile
+// (task >= 0) the single "row" is the task's edge range [e_task0, e_task0 + deg).
+template <int R>
+__device__ void tile_run(const DevProb &P, TileSmem<R> &S, bool allL, const uint32_t *__restrict__ Lcur,
+                         uint32_t *__restrict__ Lnext, const uint8_t *__restrict__ Mcur, uint8_t *__restrict__ Mnext,
+                         const uint32_t (&xt)[Geo<R>::CPL][8], int64_t task, int64_t e_task0, uint64_t tb,
+                         Stats &st) {
+    using Gm = Geo<R>;
+    constexpr int NGB = kTileT / Gm::G;  // merge groups per block
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int g = tid / Gm::G, li = tid % Gm::G;
+    const int n_rows = S.n_rows, n_edges = S.n_edges;
+    // stage: one thread per tile edge
+    int32_t take = 0;
+    int32_t v = 0;
+    uint32_t T = 0, h = 0;
+    bool inL = false;
+    int r = 0;
+    int64_t e = 0;
+    if (tid < n_edges) {
+        int lo = 0, hi = n_rows;  // last row r with row_pre[r] <= tid
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (S.row_pre[mid] <= tid) lo = mid; else hi = mid;
+        }
+        r = lo;
+        e = (task >= 0 ? e_task0 : S.row_e0[r]) + (tid - S.row_pre[r]);
+        v = __ldg(&P.adj[e]);
+        inL = allL || test_bit(Lcur, v);
+        bool ok = false;
+        if (inL) edge_threshold(P, e, v, T, ok);
+        take = (inL && ok) ? 1 : 0;
+    }
+    int32_t n_taken;
+    const int32_t slot = tile_exclusive_scan(take, S.warp_tmp, &n_taken);
+    const unsigned mL = __ballot_sync(kFull, inL);
+    if (lane == 0) st.visits += static_cast<unsigned long long>(__popc(mL)) * R;
+    if (tid < n_edges) S.take_pre[tid] = slot;
+    if (tid == 0) S.take_pre[n_edges] = n_taken;
+    if (take) {
+        h = edge_hash(static_cast<uint64_t>(task >= 0 ? __ldg(&P.task_row[task]) : S.row_u[r]),
+                      static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
+        const bool tie = test_bit(P.xpfx, (h ^ T) >> kPfxShift);
+        S.e_v[slot] = v | (tie ? static_cast<int32_t>(0x80000000u) : 0);
+        S.e_ht[slot] = (h >> kPfxShift) * 0x00010001u;
+        S.e_K[slot] = (0x8000u - (T >> kPfxShift)) * 0x00010001u;
+        S.e_h[slot] = h;
+        S.e_T[slot] = T;
+    }
+    __syncthreads();
+    // gather every sampled neighbour row into shared memory
+    for (int i = tid; i < n_taken * Gm::CH; i += kTileT) {
+        const int sl = i / Gm::CH, c = i % Gm::CH;
+        const int32_t vv = S.e_v[sl] & 0x7FFFFFFF;
+        cp_async16(&S.slot[sl][c], Mcur + static_cast<size_t>(vv) * R + 16 * c);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (tid == 0) st.bytes += static_cast<uint64_t>(n_taken) * R + 4 * static_cast<uint64_t>(n_edges);
+    if (lane == 0) st.bytes += tb * static_cast<uint64_t>(__popc(mL));
+    // merge: one group per row (a single-row tile splits its slots over every group)
+    const bool split = (n_rows == 1);
+    for (int rr = split ? 0 : g; rr < n_rows; rr += split ? 1 : NGB) {
+        const int s0 = S.take_pre[S.row_pre[rr]];
+        const int s1 = S.take_pre[S.row_pre[rr + 1]];
+        uint32_t acc[Gm::CPL][4];
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[c][w] = 0;
+        for (int sl = s0 + (split ? g : 0); sl < s1; sl += split ? NGB : 1) {
+            uint4 row[Gm::CPL];
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) row[c] = S.slot[sl][li + Gm::G * c];
+            const int32_t vv = S.e_v[sl];
+            if (vv >= 0)
+                merge_fast<R>(acc, row, xt, S.e_ht[sl], S.e_K[sl]);
+            else
+                merge_exact<R>(acc, row, S.e_h[sl], S.e_T[sl], P.X, li);
+        }
+        if (split) {
+            // combine the groups' partial maxima through shared memory (the slots are no longer needed)
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) S.slot[g][li + Gm::G * c] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+            __syncthreads();
+            if (g == 0) {
+                for (int k = 1; k < NGB; ++k)
+#pragma unroll
+                    for (int c = 0; c < Gm::CPL; ++c) {
+                        const uint4 x = S.slot[k][li + Gm::G * c];
+                        acc[c][0] = vmax4(acc[c][0], x.x);
+                        acc[c][1] = vmax4(acc[c][1], x.y);
+                        acc[c][2] = vmax4(acc[c][2], x.z);
+                        acc[c][3] = vmax4(acc[c][3], x.w);
+                    }
+            }
+        }
+        if (split && g != 0) break;
+        if (task >= 0) {
+            if (s1 > s0) {
+                uint4 *dst = reinterpret_cast<uint4 *>(P.part + static_cast<size_t>(task) * R);
+#pragma unroll
+                for (int c = 0; c < Gm::CPL; ++c)
+                    dst[li + Gm::G * c] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+                if (li == 0) {
+                    set_bit(P.part_any, task);
+                    st.bytes += R;
+                }
+            }
+            break;
+        }
+        const int64_t u = S.row_u[rr];
+        const bool sync = S.row_sync[rr] != 0;
+        if (s1 == s0 && !sync) continue;
+        // own row, change test, write-back
+        const uint4 *own = reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R);
+        uint4 nw[Gm::CPL];
+        bool diff = false;
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c) {
+            const uint4 o = __ldg(own + li + Gm::G * c);
+            nw[c] = make_uint4(vmax4(o.x, acc[c][0]), vmax4(o.y, acc[c][1]), vmax4(o.z, acc[c][2]),
+                               vmax4(o.w, acc[c][3]));
+            diff |= (nw[c].x != o.x) | (nw[c].y != o.y) | (nw[c].z != o.z) | (nw[c].w != o.w);
+        }
+        // group-wide any (groups are aligned sub-warps of G lanes)
+        const unsigned gmask = (Gm::G == 32) ? kFull : (((1u << Gm::G) - 1u) << (lane & ~(Gm::G - 1)));
+        const bool changed = __any_sync(gmask, diff);
+        if (changed || sync) {
+            uint4 *dst = reinterpret_cast<uint4 *>(Mnext + static_cast<size_t>(u) * R);
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
+        }
+        if (li == 0) {
+            st.bytes += R + ((changed || sync) ? R : 0);
+            if (changed) {
+                set_bit(Lnext, u);
+                st.nchg += 1;
+                st.indeg += in_degree(P, u) + 1;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <int R>
+__device__ void tile_problem(const DevProb &P, TileSmem<R> &S, uint32_t t, bool full, uint64_t nlight,
+                             uint64_t nchunks, uint64_t cnt, uint64_t first, uint64_t nworkers) {
+    using Gm = Geo<R>;
+    const int tid = threadIdx.x;
+    const int li = tid % Gm::G;
+    uint32_t xt[Gm::CPL][8];
+    load_xt<R>(P.X, li, xt);
+    const bool par = t & 1u;
+    const uint8_t *Mcur = par ? P.M1 : P.M0;
+    uint8_t *Mnext = par ? P.M0 : P.M1;
+    const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
+    uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
+    const int32_t *rows = par ? P.rows1 : P.rows0;
+    const bool allL = (t == 0);
+    const uint64_t tb = thr_bytes(P.model);
+    Stats st;
+    for (uint64_t l = first; l < cnt; l += nworkers) {
+        if (l < nchunks) {
+            // a chunk of up to kTileT consecutive work rows, cut into tiles of at most kTileT edges
+            const uint64_t c0 = l * kTileT;
+            const uint64_t c1 = min(c0 + kTileT, nlight);
+            uint64_t pos = c0;
+            while (pos < c1) {
+                const uint64_t i = pos + tid;
+                int32_t deg = 0;
+                uint32_t sync = 0;
+                int32_t u = -1;
+                int64_t e0 = 0;
+                if (i < c1) {
+                    u = full ? static_cast<int32_t>(i) : rows[i];
+                    const bool heavy = full && test_bit(P.heavy, u);
+                    if (!heavy) {
+                        e0 = __ldg(&P.xadj[u]);
+                        deg = static_cast<int32_t>(__ldg(&P.xadj[u + 1]) - e0);
+                        sync = test_bit(Lcur, u) ? 1u : 0u;
+                    }
+                }
+                int32_t total;
+                const int32_t pre = tile_exclusive_scan(deg, S.warp_tmp, &total);
+                // rows of this tile: the longest prefix whose edges fit (at least one row)
+                const bool fits = (i < c1) && (pre + deg <= kTileT);
+                const unsigned fm = __ballot_sync(kFull, fits);
+                if ((tid & 31) == 0) S.warp_tmp[tid >> 5] = __popc(fm);
+                __syncthreads();
+                int32_t nfit = 0;
+#pragma unroll
+                for (int w = 0; w < kTileT / 32; ++w) nfit += S.warp_tmp[w];
+                if (nfit == 0) nfit = 1;  // a light row has at most kTileT edges
+                if (tid < nfit) {
+                    S.row_u[tid] = u;
+                    S.row_e0[tid] = e0;
+                    S.row_pre[tid] = pre;
+                    S.row_sync[tid] = sync;
+                }
+                if (tid == nfit - 1) {
+                    S.row_pre[nfit] = pre + deg;
+                    S.n_rows = nfit;
+                    S.n_edges = pre + deg;
+                }
+                __syncthreads();
+                if (tid == 0) st.bytes += 16ull * nfit;
+                tile_run<R>(P, S, allL, Lcur, Lnext, Mcur, Mnext, xt, -1, 0, tb, st);
+                pos += nfit;
+            }
+        } else {
+            const int64_t task = static_cast<int64_t>(l - nchunks);
+            const int32_t u = __ldg(&P.task_row[task]);
+            if (!full && !P.mark8[u]) continue;
+            const int64_t e0 = __ldg(&P.xadj[u]) + (task - __ldg(&P.task_off[u])) * kTaskEdges;
+            const int64_t e1 = min(e0 + kTaskEdges, __ldg(&P.xadj[u + 1]));
+            if (tid == 0) {
+                S.row_u[0] = u;
+                S.row_pre[0] = 0;
+                S.row_pre[1] = static_cast<int32_t>(e1 - e0);
+                S.row_sync[0] = 0;
+                S.n_rows = 1;
+                S.n_edges = static_cast<int32_t>(e1 - e0);
+            }
+            __syncthreads();
+            tile_run<R>(P, S, allL, Lcur, Lnext, Mcur, Mnext, xt, task, e0, tb, st);
+        }
+    }
+    flush_stats_warp(P.ctr, st);
+}
+
+}  // namespace
+
+template <int R>
+__global__ void __launch_bounds__(kTileT) k_prop_tile(const DevProb *__restrict__ probs,
+                                                      const int32_t *__restrict__ act, int nact) {
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    TileSmem<R> &S = *reinterpret_cast<TileSmem<R> *>(tile_smem);
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.done) continue;
+        const uint32_t t = C.t;
+        const bool full = C.full != 0;
+        const uint64_t nlight = prop_light_count(P, C);
+        const uint64_t nchunks = (nlight + kTileT - 1) / kTileT;
+        const uint64_t cnt = nchunks + static_cast<uint64_t>(P.n_tasks);
+        const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
+        base += cnt;
+        if (first >= cnt) continue;
+        tile_problem<R>(P, S, t, full, nlight, nchunks, cnt, first, gridDim.x);
     }
 }
 
@@ -1249,6 +1583,7 @@ static void launch_prop_shape(const DevProb *probs, const int32_t *act, int nact
     k_prop<R, UNR, MINB><<<grid, kBlock, 0, s>>>(probs, act, nact);
 }
 
+// Launch shapes of the propagation sweep, exact alike; IM_PROP_VARIANT selects one (0 = default).
 template <int R>
 static void launch_prop_r(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     switch (g_variant) {
@@ -1256,13 +1591,10 @@ static void launch_prop_r(const DevProb *probs, const int32_t *act, int nact, cu
         case 2: launch_prop_shape<R, 2, 3>(probs, act, nact, s); break;
         case 3: launch_prop_shape<R, 4, 3>(probs, act, nact, s); break;
         case 4: launch_prop_shape<R, 2, 4>(probs, act, nact, s); break;
-        case 5: launch_prop_shape<R, 8, 2>(probs, act, nact, s); break;
-        case 6: launch_prop_shape<R, 1, 4>(probs, act, nact, s); break;
-        default: launch_prop_shape<R, 2, 1>(probs, act, nact, s); break;
+        case 5: launch_prop_shape<R, 2, 1>(probs, act, nact, s); break;
+        default: launch_prop_shape<R, 1, 4>(probs, act, nact, s); break;  // fastest measured on GB300
     }
 }
-
-int grid_warp() { return g_grid_warp; }
 
 #define IMK_R_SWITCH(R, CALL)                 \
     switch (R) {                              \
@@ -1274,12 +1606,28 @@ int grid_warp() { return g_grid_warp; }
         default: break;                       \
     }
 
+template <int R>
+static void launch_tile(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    static int grid = 0;
+    const int smem = static_cast<int>(sizeof(TileSmem<R>));
+    if (grid == 0) {
+        cudaFuncSetAttribute(k_prop_tile<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prop_tile<R>, kTileT, smem);
+        grid = g_sms * (occ > 0 ? occ : 1);
+    }
+    k_prop_tile<R><<<grid, kTileT, smem, s>>>(probs, act, nact);
+}
+
+template <int R>
+static void launch_tile(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+
 void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    if (R == 256) {
-        launch_prop_r<256>(probs, act, nact, s);
+    if (g_variant == 9) {
+        IMK_R_SWITCH(R, (launch_tile<RR>(probs, act, nact, s)));
         return;
     }
-    IMK_R_SWITCH(R, (launch_prop_shape<RR, 2, 1>(probs, act, nact, s)));
+    IMK_R_SWITCH(R, (launch_prop_r<RR>(probs, act, nact, s)));
 }
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     IMK_R_SWITCH(R, (k_combine<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));

@@ -12,6 +12,7 @@ constexpr int kBlock = 256;          // threads per block of every kernel
 constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kHeavyDeg = 64;        // rows with more out-edges are split into tasks of kTaskEdges edges
 constexpr int kTaskEdges = 64;
+constexpr int kBigTasks = 32;        // split rows with more tasks are merged by a whole block
 constexpr int kBfsHeavyDeg = 256;    // search-frontier vertices with more out-edges are spread over the grid
 constexpr int kExpandHeavyDeg = 1024;  // changed vertices with more in-edges are expanded by the whole grid
 constexpr int kPfxShift = 17;        // sampling words are compared on their top 15 bits first
@@ -30,6 +31,9 @@ struct DevCtr {
     uint32_t nchg_list;  // entries written to chg_list (changed vertices with few in-edges)
     uint32_t nrows[2];   // listed light rows for the sweep of that parity
     uint32_t nchg_hlist; // entries written to chg_hlist (changed vertices with many in-edges)
+    uint32_t ntl[2];     // listed tasks of split rows for the sweep of that parity
+    uint32_t nhs[2];     // listed split rows with at most kBigTasks tasks
+    uint32_t nhb[2];     // listed split rows with more tasks
     unsigned long long chg_indeg;     // sum over changed vertices of (in-degree + 1): cost of listing the next rows
     unsigned long long visits;        // edge-simulation visits, running total
     unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total
@@ -59,9 +63,11 @@ struct DevProb {
     const uint32_t *heavy;     // bit per row: out-degree > kHeavyDeg
     const int64_t *task_off;   // n+1: first task of each row (tasks only for heavy rows)
     const int32_t *task_row;   // per task: its row
-    const int32_t *heavy_rows; // rows with tasks
+    const int32_t *light_list; // rows with 1 .. kHeavyDeg out-edges
+    const int32_t *hsmall;     // split rows with at most kBigTasks tasks
+    const int32_t *hbig;       // split rows with more tasks
     int64_t n_tasks;
-    int64_t n_heavy;
+    int64_t n_light, n_hsmall, n_hbig;
     int32_t model;
     int32_t R;                 // simulations (registers per row), a power of two in [64, 1024]
     int32_t W;                 // R / 32: words per row of a bit array over simulations
@@ -82,6 +88,9 @@ struct DevProb {
     int32_t *chg_list;         // compacted changed vertices with few in-edges
     int32_t *chg_hlist;        // compacted changed vertices with many in-edges
     int32_t *rows0, *rows1;    // light rows of the sweep of that parity
+    int32_t *tl0, *tl1;        // tasks of the marked split rows, by parity
+    int32_t *hsl0, *hsl1;      // marked split rows (few tasks), by parity
+    int32_t *hbl0, *hbl1;      // marked split rows (many tasks), by parity
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
     uint32_t *del0, *del1;     // n x W: bits newly reached at the previous level, by parity
     uint32_t *Fb;              // bit per vertex: reached something new at this level

@@ -120,8 +120,8 @@ struct GraphDev {
     uint32_t *heavy = nullptr;
     int64_t *task_off = nullptr;
     int32_t *task_row = nullptr;
-    int32_t *heavy_rows = nullptr;
-    int64_t n_tasks = 0, n_heavy = 0;
+    int32_t *light_list = nullptr, *hsmall = nullptr, *hbig = nullptr;
+    int64_t n_tasks = 0, n_light = 0, n_hsmall = 0, n_hbig = 0;
     std::unique_ptr<DevMem> mem;
     uint64_t bytes = 0;
 };
@@ -237,14 +237,18 @@ std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
     if (h_flags[3]) fail(IM_EINVAL, "p_edge holds a value outside [0, 1]");
     G->n_tasks = h_tasks;
     G->task_row = mem.alloc<int32_t>(std::max<int64_t>(h_tasks, 1));
-    G->heavy_rows = mem.alloc<int32_t>(std::max<int64_t>(h_tasks, 1));
-    unsigned int *nheavy = mem.alloc<unsigned int>(1, true);
-    launch_task_fill(G->task_off, n, G->task_row, G->heavy_rows, nheavy, s);
+    G->light_list = mem.alloc<int32_t>(n);
+    G->hsmall = mem.alloc<int32_t>(n);
+    G->hbig = mem.alloc<int32_t>(n);
+    unsigned int *counts = mem.alloc<unsigned int>(3, true);
+    launch_classes(G->xadj, G->task_off, n, G->task_row, G->light_list, counts, G->hsmall, G->hbig, s);
     ctx->launches += 1;
-    unsigned int h_nheavy = 0;
-    ck(cudaMemcpyAsync(&h_nheavy, nheavy, sizeof(unsigned int), cudaMemcpyDeviceToHost, s), "read heavy");
+    unsigned int h_counts[3] = {0, 0, 0};
+    ck(cudaMemcpyAsync(h_counts, counts, sizeof(h_counts), cudaMemcpyDeviceToHost, s), "read classes");
     ck(cudaStreamSynchronize(s), "sync");
-    G->n_heavy = h_nheavy;
+    G->n_light = h_counts[0];
+    G->n_hsmall = h_counts[1];
+    G->n_hbig = h_counts[2];
     return G;
 }
 
@@ -309,9 +313,13 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     d.heavy = g.heavy;
     d.task_off = g.task_off;
     d.task_row = g.task_row;
-    d.heavy_rows = g.heavy_rows;
+    d.light_list = g.light_list;
+    d.hsmall = g.hsmall;
+    d.hbig = g.hbig;
     d.n_tasks = g.n_tasks;
-    d.n_heavy = g.n_heavy;
+    d.n_light = g.n_light;
+    d.n_hsmall = g.n_hsmall;
+    d.n_hbig = g.n_hbig;
     d.model = g.model;
     d.R = R;
     d.W = R / 32;
@@ -340,6 +348,12 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     d.chg_hlist = mem.alloc<int32_t>(n);
     d.rows0 = mem.alloc<int32_t>(n);
     d.rows1 = mem.alloc<int32_t>(n);
+    d.tl0 = mem.alloc<int32_t>(std::max<int64_t>(g.n_tasks, 1));
+    d.tl1 = mem.alloc<int32_t>(std::max<int64_t>(g.n_tasks, 1));
+    d.hsl0 = mem.alloc<int32_t>(std::max<int64_t>(g.n_hsmall, 1));
+    d.hsl1 = mem.alloc<int32_t>(std::max<int64_t>(g.n_hsmall, 1));
+    d.hbl0 = mem.alloc<int32_t>(std::max<int64_t>(g.n_hbig, 1));
+    d.hbl1 = mem.alloc<int32_t>(std::max<int64_t>(g.n_hbig, 1));
     d.MS = mem.alloc<uint8_t>(R, true);
     const int64_t ms = prm.max_sweeps > 0 ? prm.max_sweeps : n + 2;
     d.max_sweeps = static_cast<uint32_t>(std::min<int64_t>(ms, 0x7FFFFFFF));

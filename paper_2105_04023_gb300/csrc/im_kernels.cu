@@ -117,70 +117,6 @@ struct WarpStage {
 // Algorithm 2's inner loops for the out-edges [e0, e1) of row u: every edge (u, v) with v in L is one visit; for
 // the sampled simulations the registers of v are max-merged into acc.  Warp-uniform counters: nL edges with v in L,
 // nTaken of them that can be live (their neighbour row was read).
-template <int R, int UNR>
-__device__ __forceinline__ void scan_range(const DevProb &P, int64_t u, int64_t e0, int64_t e1, bool allL,
-                                           const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
-                                           uint32_t (&acc)[Geo<R>::CPL][4], const uint32_t (&xt)[Geo<R>::CPL][8],
-                                           int lane, int g, int li, WarpStage &sw, uint32_t &nL,
-                                           uint32_t &nTaken) {
-    using Gm = Geo<R>;
-    for (int64_t base = e0; base < e1; base += 32) {
-        const int64_t e = base + lane;
-        int32_t v = 0;
-        bool inL = false;
-        if (e < e1) {
-            v = __ldg(&P.adj[e]);
-            inL = allL || test_bit(Lcur, v);
-        }
-        uint32_t T = 0;
-        bool ok = false;
-        if (inL) edge_threshold(P, e, v, T, ok);
-        const unsigned mL = __ballot_sync(kFull, inL);
-        const bool take = inL && ok;
-        const unsigned mT = __ballot_sync(kFull, take);
-        nL += __popc(mL);
-        if (mT == 0) continue;
-        if (take) {
-            const int r = __popc(mT & ((1u << lane) - 1u));
-            const uint32_t h =
-                edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
-            const bool tie = test_bit(P.xpfx, (h ^ T) >> kPfxShift);
-            sw.v[r] = v | (tie ? static_cast<int32_t>(0x80000000u) : 0);
-            sw.ht[r] = (h >> kPfxShift) * 0x00010001u;
-            sw.K[r] = (0x8000u - (T >> kPfxShift)) * 0x00010001u;
-            sw.h[r] = h;
-            sw.T[r] = T;
-        }
-        __syncwarp();
-        const int cnt = __popc(mT);
-        nTaken += cnt;
-        for (int i0 = 0; i0 < cnt; i0 += Gm::NG * UNR) {
-            uint4 row[UNR][Gm::CPL];
-            int32_t vt[UNR];
-#pragma unroll
-            for (int k = 0; k < UNR; ++k) {
-                const int idx = i0 + g + k * Gm::NG;
-                vt[k] = idx < cnt ? sw.v[idx] : -1;
-                if (idx < cnt) {
-                    const uint4 *src =
-                        reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(vt[k] & 0x7FFFFFFF) * R);
-#pragma unroll
-                    for (int c = 0; c < Gm::CPL; ++c) row[k][c] = __ldg(src + li + Gm::G * c);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < UNR; ++k) {
-                const int idx = i0 + g + k * Gm::NG;
-                if (idx >= cnt) continue;
-                if (vt[k] >= 0)
-                    merge_fast<R>(acc, row[k], xt, sw.ht[idx], sw.K[idx]);
-                else
-                    merge_exact<R>(acc, row[k], sw.h[idx], sw.T[idx], P.X, li);
-            }
-        }
-        __syncwarp();
-    }
-}
 
 template <int R>
 __device__ __forceinline__ void reduce_groups(uint32_t (&acc)[Geo<R>::CPL][4]) {
@@ -213,42 +149,106 @@ __device__ __forceinline__ void flush_stats(DevCtr *C, Stats &st, int lane) {
     st = Stats();
 }
 
-// Every lane may hold counts: reduce over the warp, then one atomic per field.
-__device__ __forceinline__ void flush_stats_warp(DevCtr *C, Stats &st) {
-    unsigned long long v = st.visits, b = st.bytes, d = st.indeg;
-    unsigned int c = st.nchg;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        v += __shfl_xor_sync(kFull, v, off);
-        b += __shfl_xor_sync(kFull, b, off);
-        d += __shfl_xor_sync(kFull, d, off);
-        c += __shfl_xor_sync(kFull, c, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (v) atomicAdd(&C->visits, v);
-        if (b) atomicAdd(&C->bytes, b);
-        if (c) atomicAdd(&C->nchg, c);
-        if (d) atomicAdd(&C->chg_indeg, d);
-    }
-    st = Stats();
+// ------------------------------------------------------------------------------------------------------------
+// Gather form of the sweep (the default): as above, one warp per row, but the register rows of the sampled
+// neighbours of each staged batch (and the row's own registers) are copied into a per-warp shared-memory buffer
+// with cp.async before they are merged, so a warp keeps up to GSlots<R> rows in flight without holding them in
+// registers.
+
+template <int R>
+struct GSlots {
+    static constexpr int N = R <= 256 ? 16 : (R == 512 ? 8 : 4);
+    static constexpr int kBytesPerWarp = (N + 1) * R;
+};
+
+__device__ __forceinline__ void cpa16(void *smem, const void *gmem) {
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cpa_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
-// New registers of row u = max(own row, merged neighbours).  The row is written to the other buffer when it
-// changed, or when the buffers may differ at u (u changed in the previous sweep); a changed row joins L'.
 template <int R>
-__device__ __forceinline__ void finalize_row(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4],
-                                             bool anyTaken, bool sync, const uint8_t *__restrict__ Mcur,
-                                             uint8_t *__restrict__ Mnext, uint32_t *__restrict__ Lnext, int lane,
-                                             int g, int li, Stats &st) {
+__device__ __forceinline__ void scan_range_g(const DevProb &P, int64_t u, int64_t e0, int64_t e1, bool allL,
+                                             const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
+                                             uint32_t (&acc)[Geo<R>::CPL][4], const uint32_t (&xt)[Geo<R>::CPL][8],
+                                             int lane, int g, int li, WarpStage &sw, uint4 *buf, uint4 *own,
+                                             bool &own_loaded, uint32_t &nL, uint32_t &nTaken) {
+    using Gm = Geo<R>;
+    constexpr int N = GSlots<R>::N;
+    for (int64_t base = e0; base < e1; base += 32) {
+        const int64_t e = base + lane;
+        int32_t v = 0;
+        bool inL = false;
+        if (e < e1) {
+            v = __ldg(&P.adj[e]);
+            inL = allL || test_bit(Lcur, v);
+        }
+        uint32_t T = 0;
+        bool ok = false;
+        if (inL) edge_threshold(P, e, v, T, ok);
+        const unsigned mL = __ballot_sync(kFull, inL);
+        const bool take = inL && ok;
+        const unsigned mT = __ballot_sync(kFull, take);
+        nL += __popc(mL);
+        if (mT == 0) continue;
+        if (take) {
+            const int r = __popc(mT & ((1u << lane) - 1u));
+            const uint32_t h =
+                edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
+            const bool tie = test_bit(P.xpfx, (h ^ T) >> kPfxShift);
+            sw.v[r] = v | (tie ? static_cast<int32_t>(0x80000000u) : 0);
+            sw.ht[r] = (h >> kPfxShift) * 0x00010001u;
+            sw.K[r] = (0x8000u - (T >> kPfxShift)) * 0x00010001u;
+            sw.h[r] = h;
+            sw.T[r] = T;
+        }
+        __syncwarp();
+        const int cnt = __popc(mT);
+        nTaken += cnt;
+        for (int i0 = 0; i0 < cnt; i0 += N) {
+            const int nb = min(N, cnt - i0);
+            for (int k = lane; k < nb * Gm::CH; k += 32) {
+                const int sl = k / Gm::CH, c = k % Gm::CH;
+                cpa16(&buf[sl * Gm::CH + c],
+                      Mcur + static_cast<size_t>(sw.v[i0 + sl] & 0x7FFFFFFF) * R + 16 * c);
+            }
+            if (own != nullptr && !own_loaded) {
+                for (int k = lane; k < Gm::CH; k += 32) cpa16(&own[k], Mcur + static_cast<size_t>(u) * R + 16 * k);
+                own_loaded = true;
+            }
+            cpa_wait_all();
+            __syncwarp();
+            for (int sl = g; sl < nb; sl += Gm::NG) {
+                uint4 row[Gm::CPL];
+#pragma unroll
+                for (int c = 0; c < Gm::CPL; ++c) row[c] = buf[sl * Gm::CH + li + Gm::G * c];
+                const int idx = i0 + sl;
+                if (sw.v[idx] >= 0)
+                    merge_fast<R>(acc, row, xt, sw.ht[idx], sw.K[idx]);
+                else
+                    merge_exact<R>(acc, row, sw.h[idx], sw.T[idx], P.X, li);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void finalize_row_g(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4],
+                                               bool anyTaken, bool sync, const uint4 *ownp,
+                                               uint8_t *__restrict__ Mnext, uint32_t *__restrict__ Lnext, int lane,
+                                               int g, int li, Stats &st) {
     using Gm = Geo<R>;
     if (!anyTaken && !sync) return;
     bool diff = false;
     uint4 nw[Gm::CPL];
     if (g == 0) {
-        const uint4 *own = reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R);
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) {
-            const uint4 o = __ldg(own + li + Gm::G * c);
+            const uint4 o = ownp[li + Gm::G * c];
             nw[c] = make_uint4(vmax4(o.x, acc[c][0]), vmax4(o.y, acc[c][1]), vmax4(o.z, acc[c][2]),
                                vmax4(o.w, acc[c][3]));
             diff |= (nw[c].x != o.x) | (nw[c].y != o.y) | (nw[c].z != o.z) | (nw[c].w != o.w);
@@ -268,11 +268,38 @@ __device__ __forceinline__ void finalize_row(const DevProb &P, int64_t u, uint32
     st.bytes += R + ((changed || sync) ? R : 0);
 }
 
-template <int R, int UNR>
-__device__ void prop_problem(const DevProb &P, uint32_t t, bool full, uint64_t nlight, uint64_t cnt, uint64_t first,
-                             uint64_t nworkers, int lane, WarpStage &sw) {
+// Work of the current sweep.  A full sweep visits every light row that has out-edges (static list) and every task
+// of every heavy row; a listed sweep visits the rows and tasks that k_rows listed for it.
+struct SweepWork {
+    uint64_t nlight, ntask;
+    const int32_t *rows;
+    const int32_t *tasks;  // nullptr: task ids 0 .. n_tasks-1
+};
+
+__device__ __forceinline__ SweepWork sweep_work(const DevProb &P, const DevCtr &C) {
+    SweepWork w;
+    const uint32_t p = C.t & 1u;
+    if (C.full) {
+        w.nlight = static_cast<uint64_t>(P.n_light);
+        w.ntask = static_cast<uint64_t>(P.n_tasks);
+        w.rows = P.light_list;
+        w.tasks = nullptr;
+    } else {
+        w.nlight = C.nrows[p];
+        w.ntask = C.ntl[p];
+        w.rows = p ? P.rows1 : P.rows0;
+        w.tasks = p ? P.tl1 : P.tl0;
+    }
+    return w;
+}
+
+template <int R>
+__device__ void prop_problem_g(const DevProb &P, uint32_t t, const SweepWork &W, uint64_t cnt, uint64_t first,
+                               uint64_t nworkers, int lane, WarpStage &sw, uint4 *buf) {
     using Gm = Geo<R>;
+    constexpr int N = GSlots<R>::N;
     const int g = lane / Gm::G, li = lane % Gm::G;
+    uint4 *own = buf + N * Gm::CH;
     uint32_t xt[Gm::CPL][8];
     load_xt<R>(P.X, li, xt);
     const bool par = t & 1u;
@@ -280,7 +307,6 @@ __device__ void prop_problem(const DevProb &P, uint32_t t, bool full, uint64_t n
     uint8_t *Mnext = par ? P.M0 : P.M1;
     const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
     uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
-    const int32_t *rows = par ? P.rows1 : P.rows0;
     const bool allL = (t == 0);
     const uint64_t tb = thr_bytes(P.model);
     Stats st;
@@ -291,24 +317,28 @@ __device__ void prop_problem(const DevProb &P, uint32_t t, bool full, uint64_t n
 #pragma unroll
             for (int w = 0; w < 4; ++w) acc[c][w] = 0;
         uint32_t nL = 0, nTaken = 0;
-        if (l < nlight) {
-            const int64_t u = full ? static_cast<int64_t>(l) : static_cast<int64_t>(rows[l]);
-            if (full && test_bit(P.heavy, u)) continue;
+        bool own_loaded = false;
+        if (l < W.nlight) {
+            const int64_t u = W.rows[l];
             const int64_t e0 = __ldg(&P.xadj[u]), e1 = __ldg(&P.xadj[u + 1]);
             const bool sync = test_bit(Lcur, u);
-            if (e0 == e1 && !sync) continue;
-            scan_range<R, UNR>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, nL, nTaken);
+            scan_range_g<R>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, buf, own, own_loaded, nL,
+                            nTaken);
             reduce_groups<R>(acc);
             st.visits += static_cast<unsigned long long>(nL) * R;
             st.bytes += 16 + 4 * static_cast<uint64_t>(e1 - e0) + tb * nL + static_cast<uint64_t>(nTaken) * R;
-            finalize_row<R>(P, u, acc, nTaken > 0, sync, Mcur, Mnext, Lnext, lane, g, li, st);
+            const uint4 *ownp =
+                own_loaded ? own : reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R);
+            finalize_row_g<R>(P, u, acc, nTaken > 0, sync, ownp, Mnext, Lnext, lane, g, li, st);
+            __syncwarp();
         } else {
-            const int64_t task = static_cast<int64_t>(l - nlight);
+            const int64_t task = W.tasks ? static_cast<int64_t>(W.tasks[l - W.nlight])
+                                         : static_cast<int64_t>(l - W.nlight);
             const int64_t u = __ldg(&P.task_row[task]);
-            if (!full && !P.mark8[u]) continue;
             const int64_t e0 = __ldg(&P.xadj[u]) + (task - __ldg(&P.task_off[u])) * kTaskEdges;
             const int64_t e1 = min(e0 + kTaskEdges, __ldg(&P.xadj[u + 1]));
-            scan_range<R, UNR>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, nL, nTaken);
+            scan_range_g<R>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, buf, nullptr, own_loaded,
+                            nL, nTaken);
             reduce_groups<R>(acc);
             st.visits += static_cast<unsigned long long>(nL) * R;
             st.bytes += 4 * static_cast<uint64_t>(e1 - e0) + tb * nL + static_cast<uint64_t>(nTaken) * R;
@@ -327,18 +357,68 @@ __device__ void prop_problem(const DevProb &P, uint32_t t, bool full, uint64_t n
     flush_stats(P.ctr, st, lane);
 }
 
-// Rows of the current sweep: all rows (light ones here, heavy ones as tasks) or the listed light rows.
-__device__ __forceinline__ uint64_t prop_light_count(const DevProb &P, const DevCtr &C) {
-    return C.full ? static_cast<uint64_t>(P.n) : C.nrows[C.t & 1u];
+// The partial rows of tasks [a, b) (b - a <= 32) that merged something: their part_any bits are consumed and the
+// rows are gathered into shared memory, N at a time, and max-merged into acc.  Returns whether any was present.
+template <int R>
+__device__ __forceinline__ bool merge_partials(const DevProb &P, int64_t a, int64_t b,
+                                               uint32_t (&acc)[Geo<R>::CPL][4], int lane, int g, int li,
+                                               WarpStage &sw, uint4 *buf, Stats &st) {
+    using Gm = Geo<R>;
+    constexpr int N = GSlots<R>::N;
+    const int64_t k = a + lane;
+    const bool mine = k < b && test_bit(P.part_any, k);
+    const unsigned m = __ballot_sync(kFull, mine);
+    if (m == 0) return false;
+    if (mine) {
+        atomicAnd(&P.part_any[k >> 5], ~(1u << (k & 31)));
+        sw.v[__popc(m & ((1u << lane) - 1u))] = lane;
+    }
+    __syncwarp();
+    const int cnt = __popc(m);
+    for (int i0 = 0; i0 < cnt; i0 += N) {
+        const int nb = min(N, cnt - i0);
+        for (int q = lane; q < nb * Gm::CH; q += 32) {
+            const int sl = q / Gm::CH, c = q % Gm::CH;
+            cpa16(&buf[sl * Gm::CH + c], P.part + static_cast<size_t>(a + sw.v[i0 + sl]) * R + 16 * c);
+        }
+        cpa_wait_all();
+        __syncwarp();
+        for (int sl = g; sl < nb; sl += Gm::NG) {
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) {
+                const uint4 x = buf[sl * Gm::CH + li + Gm::G * c];
+                acc[c][0] = vmax4(acc[c][0], x.x);
+                acc[c][1] = vmax4(acc[c][1], x.y);
+                acc[c][2] = vmax4(acc[c][2], x.z);
+                acc[c][3] = vmax4(acc[c][3], x.w);
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) st.bytes += static_cast<uint64_t>(cnt) * R;
+    return true;
+}
+
+// Heavy rows of the current sweep with at most kBigTasks tasks (one warp each) or more (one block each).
+__device__ __forceinline__ uint64_t heavy_count(const DevProb &P, const DevCtr &C, bool big, const int32_t *&list) {
+    const uint32_t p = C.t & 1u;
+    if (C.full) {
+        list = big ? P.hbig : P.hsmall;
+        return static_cast<uint64_t>(big ? P.n_hbig : P.n_hsmall);
+    }
+    list = big ? (p ? P.hbl1 : P.hbl0) : (p ? P.hsl1 : P.hsl0);
+    return big ? C.nhb[p] : C.nhs[p];
 }
 
 }  // namespace
 
-template <int R, int UNR, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) k_prop(const DevProb *__restrict__ probs,
-                                                       const int32_t *__restrict__ act, int nact) {
+template <int R, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restrict__ probs,
+                                                        const int32_t *__restrict__ act, int nact) {
     __shared__ WarpStage stage[kWarpsPerBlock];
+    extern __shared__ __align__(16) uint4 gather_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint4 *buf = gather_smem + static_cast<size_t>(wib) * (GSlots<R>::kBytesPerWarp / 16);
     const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
     const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
     uint64_t base = 0;
@@ -346,405 +426,135 @@ __global__ void __launch_bounds__(kBlock, MINB) k_prop(const DevProb *__restrict
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
         if (C.done) continue;
-        const uint32_t t = C.t;
-        const bool full = C.full != 0;
-        const uint64_t nlight = prop_light_count(P, C);
-        const uint64_t cnt = nlight + static_cast<uint64_t>(P.n_tasks);
+        const SweepWork W = sweep_work(P, C);
+        const uint64_t cnt = W.nlight + W.ntask;
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
         if (first >= cnt) continue;
-        prop_problem<R, UNR>(P, t, full, nlight, cnt, first, nworkers, lane, stage[wib]);
+        prop_problem_g<R>(P, C.t, W, cnt, first, nworkers, lane, stage[wib], buf);
     }
 }
 
-// ------------------------------------------------------------------------------------------------------------
-// Tile form of the propagation sweep.  A block of kTileT threads takes a tile of consecutive work rows whose
-// edges total at most kTileT (or one kTileEdges task of a heavy row), stages every edge of the tile at once
-// (one thread per edge: target, live-set test, threshold, hash), copies the register rows of all sampled targets
-// into shared memory with cp.async (up to kTileT rows in flight per block, no registers held while they travel),
-// then merges them row by row from shared memory.
-
-namespace {
-
-constexpr int kTileT = 128;
-
+// Split rows with at most kBigTasks tasks: one warp merges a row's partial rows and finishes the row.
 template <int R>
-struct TileSmem {
-    uint4 slot[kTileT][R / 16];  // gathered neighbour rows
-    int64_t row_e0[kTileT];      // first edge of row r
-    int32_t row_u[kTileT];       // rows of the tile
-    int32_t row_pre[kTileT + 1]; // tile edges before row r
-    int32_t take_pre[kTileT + 1];// sampled tile edges before tile edge t
-    uint32_t row_sync[kTileT];   // row changed in the previous sweep (buffers may differ there)
-    int32_t e_v[kTileT];         // per sampled edge: target, bit 31 = needs the exact test
-    uint32_t e_ht[kTileT], e_K[kTileT], e_h[kTileT], e_T[kTileT];
-    int32_t warp_tmp[kTileT / 32];
-    int32_t n_rows;
-    int32_t n_edges;
-};
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n" ::);
-    asm volatile("cp.async.wait_group 0;\n" ::);
-}
-
-// Exclusive scan of one int per thread over the kTileT threads of the block; returns the total in *total.
-__device__ __forceinline__ int32_t tile_exclusive_scan(int32_t x, int32_t *warp_tmp, int32_t *total) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int32_t incl = x;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int32_t y = __shfl_up_sync(kFull, incl, off);
-        if (lane >= off) incl += y;
-    }
-    if (lane == 31) warp_tmp[wib] = incl;
-    __syncthreads();
-    int32_t before = 0, all = 0;
-#pragma unroll
-    for (int w = 0; w < kTileT / 32; ++w) {
-        const int32_t t = warp_tmp[w];
-        before += (w < wib) ? t : 0;
-        all += t;
-    }
-    __syncthreads();
-    *total = all;
-    return before + incl - x;
-}
-
-// One tile.  rows: n_rows row ids with their degrees already prefix-summed into S.row_pre; for a task tile
-// (task >= 0) the single "row" is the task's edge range [e_task0, e_task0 + deg).
-template <int R>
-__device__ void tile_run(const DevProb &P, TileSmem<R> &S, bool allL, const uint32_t *__restrict__ Lcur,
-                         uint32_t *__restrict__ Lnext, const uint8_t *__restrict__ Mcur, uint8_t *__restrict__ Mnext,
-                         const uint32_t (&xt)[Geo<R>::CPL][8], int64_t task, int64_t e_task0, uint64_t tb,
-                         Stats &st) {
+__global__ void __launch_bounds__(kBlock) k_combine(const DevProb *__restrict__ probs,
+                                                    const int32_t *__restrict__ act, int nact) {
     using Gm = Geo<R>;
-    constexpr int NGB = kTileT / Gm::G;  // merge groups per block
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int g = tid / Gm::G, li = tid % Gm::G;
-    const int n_rows = S.n_rows, n_edges = S.n_edges;
-    // stage: one thread per tile edge
-    int32_t take = 0;
-    int32_t v = 0;
-    uint32_t T = 0, h = 0;
-    bool inL = false;
-    int r = 0;
-    int64_t e = 0;
-    if (tid < n_edges) {
-        int lo = 0, hi = n_rows;  // last row r with row_pre[r] <= tid
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (S.row_pre[mid] <= tid) lo = mid; else hi = mid;
+    __shared__ WarpStage stage[kWarpsPerBlock];
+    extern __shared__ __align__(16) uint4 gather_smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int g = lane / Gm::G, li = lane % Gm::G;
+    uint4 *buf = gather_smem + static_cast<size_t>(wib) * (GSlots<R>::kBytesPerWarp / 16);
+    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.done) continue;
+        const int32_t *list = nullptr;
+        const uint64_t cnt = heavy_count(P, C, false, list);
+        const uint64_t first = first_owned(worker, nworkers, base);
+        base += cnt;
+        if (first >= cnt) continue;
+        const bool par = C.t & 1u;
+        const uint8_t *Mcur = par ? P.M1 : P.M0;
+        uint8_t *Mnext = par ? P.M0 : P.M1;
+        const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
+        uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
+        Stats st;
+        for (uint64_t l = first; l < cnt; l += nworkers) {
+            const int64_t u = list[l];
+            uint32_t acc[Gm::CPL][4];
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[c][w] = 0;
+            const bool any = merge_partials<R>(P, __ldg(&P.task_off[u]), __ldg(&P.task_off[u + 1]), acc, lane, g,
+                                               li, stage[wib], buf, st);
+            reduce_groups<R>(acc);
+            if (lane == 0) st.bytes += 16;
+            finalize_row_g<R>(P, u, acc, any, test_bit(Lcur, u),
+                              reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R), Mnext, Lnext, lane,
+                              g, li, st);
+            __syncwarp();
         }
-        r = lo;
-        e = (task >= 0 ? e_task0 : S.row_e0[r]) + (tid - S.row_pre[r]);
-        v = __ldg(&P.adj[e]);
-        inL = allL || test_bit(Lcur, v);
-        bool ok = false;
-        if (inL) edge_threshold(P, e, v, T, ok);
-        take = (inL && ok) ? 1 : 0;
+        flush_stats(P.ctr, st, lane);
     }
-    int32_t n_taken;
-    const int32_t slot = tile_exclusive_scan(take, S.warp_tmp, &n_taken);
-    const unsigned mL = __ballot_sync(kFull, inL);
-    if (lane == 0) st.visits += static_cast<unsigned long long>(__popc(mL)) * R;
-    if (tid < n_edges) S.take_pre[tid] = slot;
-    if (tid == 0) S.take_pre[n_edges] = n_taken;
-    if (take) {
-        h = edge_hash(static_cast<uint64_t>(task >= 0 ? __ldg(&P.task_row[task]) : S.row_u[r]),
-                      static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
-        const bool tie = test_bit(P.xpfx, (h ^ T) >> kPfxShift);
-        S.e_v[slot] = v | (tie ? static_cast<int32_t>(0x80000000u) : 0);
-        S.e_ht[slot] = (h >> kPfxShift) * 0x00010001u;
-        S.e_K[slot] = (0x8000u - (T >> kPfxShift)) * 0x00010001u;
-        S.e_h[slot] = h;
-        S.e_T[slot] = T;
-    }
-    __syncthreads();
-    // gather every sampled neighbour row into shared memory
-    for (int i = tid; i < n_taken * Gm::CH; i += kTileT) {
-        const int sl = i / Gm::CH, c = i % Gm::CH;
-        const int32_t vv = S.e_v[sl] & 0x7FFFFFFF;
-        cp_async16(&S.slot[sl][c], Mcur + static_cast<size_t>(vv) * R + 16 * c);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    if (tid == 0) st.bytes += static_cast<uint64_t>(n_taken) * R + 4 * static_cast<uint64_t>(n_edges);
-    if (lane == 0) st.bytes += tb * static_cast<uint64_t>(__popc(mL));
-    // merge: one group per row (a single-row tile splits its slots over every group)
-    const bool split = (n_rows == 1);
-    for (int rr = split ? 0 : g; rr < n_rows; rr += split ? 1 : NGB) {
-        const int s0 = S.take_pre[S.row_pre[rr]];
-        const int s1 = S.take_pre[S.row_pre[rr + 1]];
-        uint32_t acc[Gm::CPL][4];
+}
+
+// Split rows with more than kBigTasks tasks (hubs): the warps of one block share a row's partial rows, reduce
+// through shared memory, and warp 0 finishes the row.
+template <int R>
+__global__ void __launch_bounds__(kBlock) k_combine_big(const DevProb *__restrict__ probs,
+                                                        const int32_t *__restrict__ act, int nact) {
+    using Gm = Geo<R>;
+    __shared__ WarpStage stage[kWarpsPerBlock];
+    __shared__ uint4 s_red[kWarpsPerBlock][Gm::CH];
+    __shared__ int s_any[kWarpsPerBlock];
+    extern __shared__ __align__(16) uint4 gather_smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int g = lane / Gm::G, li = lane % Gm::G;
+    uint4 *buf = gather_smem + static_cast<size_t>(wib) * (GSlots<R>::kBytesPerWarp / 16);
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.done) continue;
+        const int32_t *list = nullptr;
+        const uint64_t cnt = heavy_count(P, C, true, list);
+        const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
+        base += cnt;
+        if (first >= cnt) continue;
+        const bool par = C.t & 1u;
+        const uint8_t *Mcur = par ? P.M1 : P.M0;
+        uint8_t *Mnext = par ? P.M0 : P.M1;
+        const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
+        uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
+        Stats st;
+        for (uint64_t l = first; l < cnt; l += gridDim.x) {
+            const int64_t u = list[l];
+            const int64_t t0 = __ldg(&P.task_off[u]), t1 = __ldg(&P.task_off[u + 1]);
+            uint32_t acc[Gm::CPL][4];
 #pragma unroll
-        for (int c = 0; c < Gm::CPL; ++c)
+            for (int c = 0; c < Gm::CPL; ++c)
 #pragma unroll
-            for (int w = 0; w < 4; ++w) acc[c][w] = 0;
-        for (int sl = s0 + (split ? g : 0); sl < s1; sl += split ? NGB : 1) {
-            uint4 row[Gm::CPL];
-#pragma unroll
-            for (int c = 0; c < Gm::CPL; ++c) row[c] = S.slot[sl][li + Gm::G * c];
-            const int32_t vv = S.e_v[sl];
-            if (vv >= 0)
-                merge_fast<R>(acc, row, xt, S.e_ht[sl], S.e_K[sl]);
-            else
-                merge_exact<R>(acc, row, S.e_h[sl], S.e_T[sl], P.X, li);
-        }
-        if (split) {
-            // combine the groups' partial maxima through shared memory (the slots are no longer needed)
-            __syncthreads();
-#pragma unroll
-            for (int c = 0; c < Gm::CPL; ++c) S.slot[g][li + Gm::G * c] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
-            __syncthreads();
+                for (int w = 0; w < 4; ++w) acc[c][w] = 0;
+            bool any = false;
+            for (int64_t a = t0 + 32 * wib; a < t1; a += 32 * kWarpsPerBlock)
+                any |= merge_partials<R>(P, a, min(a + 32, t1), acc, lane, g, li, stage[wib], buf, st);
+            reduce_groups<R>(acc);
             if (g == 0) {
-                for (int k = 1; k < NGB; ++k)
+#pragma unroll
+                for (int c = 0; c < Gm::CPL; ++c)
+                    s_red[wib][li + Gm::G * c] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+            }
+            if (lane == 0) s_any[wib] = any ? 1 : 0;
+            __syncthreads();
+            if (wib == 0) {
+                bool all_any = false;
+                for (int w = 0; w < kWarpsPerBlock; ++w) {
+                    all_any |= s_any[w] != 0;
 #pragma unroll
                     for (int c = 0; c < Gm::CPL; ++c) {
-                        const uint4 x = S.slot[k][li + Gm::G * c];
+                        const uint4 x = s_red[w][li + Gm::G * c];
                         acc[c][0] = vmax4(acc[c][0], x.x);
                         acc[c][1] = vmax4(acc[c][1], x.y);
                         acc[c][2] = vmax4(acc[c][2], x.z);
                         acc[c][3] = vmax4(acc[c][3], x.w);
                     }
-            }
-        }
-        if (split && g != 0) break;
-        if (task >= 0) {
-            if (s1 > s0) {
-                uint4 *dst = reinterpret_cast<uint4 *>(P.part + static_cast<size_t>(task) * R);
-#pragma unroll
-                for (int c = 0; c < Gm::CPL; ++c)
-                    dst[li + Gm::G * c] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
-                if (li == 0) {
-                    set_bit(P.part_any, task);
-                    st.bytes += R;
                 }
-            }
-            break;
-        }
-        const int64_t u = S.row_u[rr];
-        const bool sync = S.row_sync[rr] != 0;
-        if (s1 == s0 && !sync) continue;
-        // own row, change test, write-back
-        const uint4 *own = reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R);
-        uint4 nw[Gm::CPL];
-        bool diff = false;
-#pragma unroll
-        for (int c = 0; c < Gm::CPL; ++c) {
-            const uint4 o = __ldg(own + li + Gm::G * c);
-            nw[c] = make_uint4(vmax4(o.x, acc[c][0]), vmax4(o.y, acc[c][1]), vmax4(o.z, acc[c][2]),
-                               vmax4(o.w, acc[c][3]));
-            diff |= (nw[c].x != o.x) | (nw[c].y != o.y) | (nw[c].z != o.z) | (nw[c].w != o.w);
-        }
-        // group-wide any (groups are aligned sub-warps of G lanes)
-        const unsigned gmask = (Gm::G == 32) ? kFull : (((1u << Gm::G) - 1u) << (lane & ~(Gm::G - 1)));
-        const bool changed = __any_sync(gmask, diff);
-        if (changed || sync) {
-            uint4 *dst = reinterpret_cast<uint4 *>(Mnext + static_cast<size_t>(u) * R);
-#pragma unroll
-            for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
-        }
-        if (li == 0) {
-            st.bytes += R + ((changed || sync) ? R : 0);
-            if (changed) {
-                set_bit(Lnext, u);
-                st.nchg += 1;
-                st.indeg += in_degree(P, u) + 1;
-            }
-        }
-    }
-    __syncthreads();
-}
-
-template <int R>
-__device__ void tile_problem(const DevProb &P, TileSmem<R> &S, uint32_t t, bool full, uint64_t nlight,
-                             uint64_t nchunks, uint64_t cnt, uint64_t first, uint64_t nworkers) {
-    using Gm = Geo<R>;
-    const int tid = threadIdx.x;
-    const int li = tid % Gm::G;
-    uint32_t xt[Gm::CPL][8];
-    load_xt<R>(P.X, li, xt);
-    const bool par = t & 1u;
-    const uint8_t *Mcur = par ? P.M1 : P.M0;
-    uint8_t *Mnext = par ? P.M0 : P.M1;
-    const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
-    uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
-    const int32_t *rows = par ? P.rows1 : P.rows0;
-    const bool allL = (t == 0);
-    const uint64_t tb = thr_bytes(P.model);
-    Stats st;
-    for (uint64_t l = first; l < cnt; l += nworkers) {
-        if (l < nchunks) {
-            // a chunk of up to kTileT consecutive work rows, cut into tiles of at most kTileT edges
-            const uint64_t c0 = l * kTileT;
-            const uint64_t c1 = min(c0 + kTileT, nlight);
-            uint64_t pos = c0;
-            while (pos < c1) {
-                const uint64_t i = pos + tid;
-                int32_t deg = 0;
-                uint32_t sync = 0;
-                int32_t u = -1;
-                int64_t e0 = 0;
-                if (i < c1) {
-                    u = full ? static_cast<int32_t>(i) : rows[i];
-                    const bool heavy = full && test_bit(P.heavy, u);
-                    if (!heavy) {
-                        e0 = __ldg(&P.xadj[u]);
-                        deg = static_cast<int32_t>(__ldg(&P.xadj[u + 1]) - e0);
-                        sync = test_bit(Lcur, u) ? 1u : 0u;
-                    }
-                }
-                int32_t total;
-                const int32_t pre = tile_exclusive_scan(deg, S.warp_tmp, &total);
-                // rows of this tile: the longest prefix whose edges fit (at least one row)
-                const bool fits = (i < c1) && (pre + deg <= kTileT);
-                const unsigned fm = __ballot_sync(kFull, fits);
-                if ((tid & 31) == 0) S.warp_tmp[tid >> 5] = __popc(fm);
-                __syncthreads();
-                int32_t nfit = 0;
-#pragma unroll
-                for (int w = 0; w < kTileT / 32; ++w) nfit += S.warp_tmp[w];
-                if (nfit == 0) nfit = 1;  // a light row has at most kTileT edges
-                if (tid < nfit) {
-                    S.row_u[tid] = u;
-                    S.row_e0[tid] = e0;
-                    S.row_pre[tid] = pre;
-                    S.row_sync[tid] = sync;
-                }
-                if (tid == nfit - 1) {
-                    S.row_pre[nfit] = pre + deg;
-                    S.n_rows = nfit;
-                    S.n_edges = pre + deg;
-                }
-                __syncthreads();
-                if (tid == 0) st.bytes += 16ull * nfit;
-                tile_run<R>(P, S, allL, Lcur, Lnext, Mcur, Mnext, xt, -1, 0, tb, st);
-                pos += nfit;
-            }
-        } else {
-            const int64_t task = static_cast<int64_t>(l - nchunks);
-            const int32_t u = __ldg(&P.task_row[task]);
-            if (!full && !P.mark8[u]) continue;
-            const int64_t e0 = __ldg(&P.xadj[u]) + (task - __ldg(&P.task_off[u])) * kTaskEdges;
-            const int64_t e1 = min(e0 + kTaskEdges, __ldg(&P.xadj[u + 1]));
-            if (tid == 0) {
-                S.row_u[0] = u;
-                S.row_pre[0] = 0;
-                S.row_pre[1] = static_cast<int32_t>(e1 - e0);
-                S.row_sync[0] = 0;
-                S.n_rows = 1;
-                S.n_edges = static_cast<int32_t>(e1 - e0);
+                if (lane == 0) st.bytes += 16;
+                finalize_row_g<R>(P, u, acc, all_any, test_bit(Lcur, u),
+                                  reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R), Mnext, Lnext,
+                                  lane, g, li, st);
             }
             __syncthreads();
-            tile_run<R>(P, S, allL, Lcur, Lnext, Mcur, Mnext, xt, task, e0, tb, st);
         }
-    }
-    flush_stats_warp(P.ctr, st);
-}
-
-}  // namespace
-
-template <int R>
-__global__ void __launch_bounds__(kTileT) k_prop_tile(const DevProb *__restrict__ probs,
-                                                      const int32_t *__restrict__ act, int nact) {
-    extern __shared__ __align__(16) unsigned char tile_smem[];
-    TileSmem<R> &S = *reinterpret_cast<TileSmem<R> *>(tile_smem);
-    uint64_t base = 0;
-    for (int q = 0; q < nact; ++q) {
-        const DevProb &P = probs[act[q]];
-        const DevCtr &C = *P.ctr;
-        if (C.done) continue;
-        const uint32_t t = C.t;
-        const bool full = C.full != 0;
-        const uint64_t nlight = prop_light_count(P, C);
-        const uint64_t nchunks = (nlight + kTileT - 1) / kTileT;
-        const uint64_t cnt = nchunks + static_cast<uint64_t>(P.n_tasks);
-        const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
-        base += cnt;
-        if (first >= cnt) continue;
-        tile_problem<R>(P, S, t, full, nlight, nchunks, cnt, first, gridDim.x);
+        flush_stats(P.ctr, st, lane);
     }
 }
 
-namespace {
-
-template <int R>
-__device__ void combine_problem(const DevProb &P, uint32_t t, bool full, uint64_t cnt, uint64_t first,
-                                uint64_t nworkers, int lane) {
-    using Gm = Geo<R>;
-    const int g = lane / Gm::G, li = lane % Gm::G;
-    const bool par = t & 1u;
-    const uint8_t *Mcur = par ? P.M1 : P.M0;
-    uint8_t *Mnext = par ? P.M0 : P.M1;
-    const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
-    uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
-    Stats st;
-    for (uint64_t l = first; l < cnt; l += nworkers) {
-        const int64_t u = P.heavy_rows[l];
-        if (!full && !P.mark8[u]) continue;
-        const int64_t t0 = __ldg(&P.task_off[u]), t1 = __ldg(&P.task_off[u + 1]);
-        uint32_t acc[Gm::CPL][4];
-#pragma unroll
-        for (int c = 0; c < Gm::CPL; ++c)
-#pragma unroll
-            for (int w = 0; w < 4; ++w) acc[c][w] = 0;
-        bool any = false;
-        for (int64_t k0 = t0; k0 < t1; k0 += 32) {
-            const int64_t k = k0 + lane;
-            const bool mine = k < t1 && test_bit(P.part_any, k);
-            const unsigned m = __ballot_sync(kFull, mine);
-            if (m == 0) continue;
-            any = true;
-            // clear the bits this warp consumed (other rows' tasks may share the word)
-            if (mine) atomicAnd(&P.part_any[k >> 5], ~(1u << (k & 31)));
-            const int cnt_m = __popc(m);
-            for (int i = g; i < cnt_m; i += Gm::NG) {
-                const int src = __fns(m, 0, i + 1);
-                const uint4 *p = reinterpret_cast<const uint4 *>(P.part + static_cast<size_t>(k0 + src) * R);
-#pragma unroll
-                for (int c = 0; c < Gm::CPL; ++c) {
-                    const uint4 x = __ldg(p + li + Gm::G * c);
-                    acc[c][0] = vmax4(acc[c][0], x.x);
-                    acc[c][1] = vmax4(acc[c][1], x.y);
-                    acc[c][2] = vmax4(acc[c][2], x.z);
-                    acc[c][3] = vmax4(acc[c][3], x.w);
-                }
-            }
-            st.bytes += static_cast<uint64_t>(cnt_m) * R;
-        }
-        reduce_groups<R>(acc);
-        st.bytes += 16;
-        finalize_row<R>(P, u, acc, any, test_bit(Lcur, u), Mcur, Mnext, Lnext, lane, g, li, st);
-        if (lane == 0) P.mark8[u] = 0;
-    }
-    flush_stats(P.ctr, st, lane);
-}
-
-}  // namespace
-
-template <int R>
-__global__ void __launch_bounds__(kBlock) k_combine(const DevProb *__restrict__ probs,
-                                                    const int32_t *__restrict__ act, int nact) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
-    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
-    uint64_t base = 0;
-    for (int q = 0; q < nact; ++q) {
-        const DevProb &P = probs[act[q]];
-        const DevCtr &C = *P.ctr;
-        if (C.done) continue;
-        const uint64_t cnt = static_cast<uint64_t>(P.n_heavy);
-        const uint64_t first = first_owned(worker, nworkers, base);
-        base += cnt;
-        if (first >= cnt) continue;
-        combine_problem<R>(P, C.t, C.full != 0, cnt, first, nworkers, lane);
-    }
-}
 
 namespace {
 
@@ -876,8 +686,8 @@ __global__ void __launch_bounds__(kBlock) k_expand(const DevProb *__restrict__ p
     }
 }
 
-// Compacts the marked light rows into the row list of the next sweep and clears their marks (marks of heavy rows
-// stay for the task and combine kernels of the next sweep).
+// Compacts the marked rows into the work lists of the next sweep and clears every mark: light rows go to the row
+// list, split rows to one of the two split-row lists and their tasks to the task list.
 __global__ void __launch_bounds__(kBlock) k_rows(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
                                                  int nact) {
     uint64_t base = 0;
@@ -887,39 +697,46 @@ __global__ void __launch_bounds__(kBlock) k_rows(const DevProb *__restrict__ pro
         if (C.done || sweep_stops(P, C) || !next_is_listed(P, C)) continue;
         const uint32_t np = (C.t + 1) & 1u;
         int32_t *rows = np ? P.rows1 : P.rows0;
+        int32_t *tl = np ? P.tl1 : P.tl0;
+        int32_t *hsl = np ? P.hsl1 : P.hsl0;
+        int32_t *hbl = np ? P.hbl1 : P.hbl0;
         const int64_t words = (P.n + 31) >> 5;
         const uint64_t chunks = (words + kBlock - 1) / kBlock;
         const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
         base += chunks;
         for (uint64_t ch = first; ch < chunks; ch += gridDim.x) {
             const int64_t i = static_cast<int64_t>(ch) * kBlock + threadIdx.x;
-            uint32_t w = 0;
+            uint32_t w = 0, hv = 0;
             if (i < words) {
                 uint4 *mp = reinterpret_cast<uint4 *>(P.mark8 + 32 * i);
-                uint4 a = mp[0], b = mp[1];
+                const uint4 a = mp[0], b = mp[1];
                 const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
                         if ((x[k] >> (8 * j)) & 0xFFu) w |= 1u << (4 * k + j);
-                const uint32_t light = w & ~P.heavy[i];
-                if (light) {
-                    uint32_t y[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        uint32_t keep = 0;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (!((light >> (4 * k + j)) & 1u)) keep |= 0xFFu << (8 * j);
-                        y[k] = x[k] & keep;
-                    }
-                    mp[0] = make_uint4(y[0], y[1], y[2], y[3]);
-                    mp[1] = make_uint4(y[4], y[5], y[6], y[7]);
+                if (w) {
+                    mp[0] = make_uint4(0, 0, 0, 0);
+                    mp[1] = make_uint4(0, 0, 0, 0);
                 }
-                w = light;
+                hv = w & P.heavy[i];
+                w &= ~hv;
             }
             block_append_bits(w, i, rows, &P.ctr->nrows[np]);
+            while (hv) {
+                const int b = __ffs(hv) - 1;
+                hv &= hv - 1;
+                const int32_t u = static_cast<int32_t>(i * 32 + b);
+                const int64_t t0 = P.task_off[u], t1 = P.task_off[u + 1];
+                const bool big = t1 - t0 > kBigTasks;
+                if (big)
+                    hbl[atomicAdd(&P.ctr->nhb[np], 1u)] = u;
+                else
+                    hsl[atomicAdd(&P.ctr->nhs[np], 1u)] = u;
+                const uint32_t pos = atomicAdd(&P.ctr->ntl[np], static_cast<uint32_t>(t1 - t0));
+                for (int64_t k = t0; k < t1; ++k) tl[pos + (k - t0)] = static_cast<int32_t>(k);
+            }
         }
     }
 }
@@ -944,6 +761,9 @@ __global__ void k_advance(const DevProb *__restrict__ probs, const int32_t *__re
     }
     C.full = next_is_listed(P, C) ? 0u : 1u;
     C.nrows[t & 1u] = 0;
+    C.ntl[t & 1u] = 0;
+    C.nhs[t & 1u] = 0;
+    C.nhb[t & 1u] = 0;
     C.nchg = 0;
     C.nchg_list = 0;
     C.nchg_hlist = 0;
@@ -1008,8 +828,12 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 C.nchg_list = 0;
                 C.nchg_hlist = 0;
                 C.chg_indeg = 0;
-                C.nrows[0] = 0;
-                C.nrows[1] = 0;
+                for (int k = 0; k < 2; ++k) {
+                    C.nrows[k] = 0;
+                    C.ntl[k] = 0;
+                    C.nhs[k] = 0;
+                    C.nhb[k] = 0;
+                }
                 if (P.flog_cap > 0) P.flog[0] = P.n;
                 for (int j = 0; j < P.R; ++j) P.MS[j] = 0;
             }
@@ -1448,15 +1272,35 @@ __global__ void k_row_tasks(const int64_t *__restrict__ xadj, int64_t n, int32_t
     }
 }
 
-__global__ void k_task_fill(const int64_t *__restrict__ task_off, int64_t n, int32_t *__restrict__ task_row,
-                            int32_t *__restrict__ heavy_rows, unsigned int *__restrict__ nheavy) {
-    for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < n;
-         u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t a = task_off[u], b = task_off[u + 1];
-        if (b > a) {
-            heavy_rows[atomicAdd(nheavy, 1u)] = static_cast<int32_t>(u);
-            for (int64_t k = a; k < b; ++k) task_row[k] = static_cast<int32_t>(u);
+// Row classes of a graph: light rows with out-edges, split rows with few / many tasks (block-compacted lists), and
+// the row of every task.
+__global__ void __launch_bounds__(kBlock) k_classes(const int64_t *__restrict__ xadj,
+                                                    const int64_t *__restrict__ task_off, int64_t n,
+                                                    int32_t *__restrict__ task_row, int32_t *light, unsigned int *nl,
+                                                    int32_t *hsmall, unsigned int *nhs, int32_t *hbig,
+                                                    unsigned int *nhb) {
+    const int64_t words = (n + 31) >> 5;
+    const uint64_t chunks = (words + kBlock - 1) / kBlock;
+    for (uint64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+        const int64_t i = static_cast<int64_t>(ch) * kBlock + threadIdx.x;
+        uint32_t wl = 0, ws = 0, wb = 0;
+        if (i < words) {
+            for (int b = 0; b < 32; ++b) {
+                const int64_t u = i * 32 + b;
+                if (u >= n) break;
+                const int64_t d = xadj[u + 1] - xadj[u];
+                if (d >= 1 && d <= kHeavyDeg) {
+                    wl |= 1u << b;
+                } else if (d > kHeavyDeg) {
+                    const int64_t t0 = task_off[u], t1 = task_off[u + 1];
+                    if (t1 - t0 > kBigTasks) wb |= 1u << b; else ws |= 1u << b;
+                    for (int64_t k = t0; k < t1; ++k) task_row[k] = static_cast<int32_t>(u);
+                }
+            }
         }
+        block_append_bits(wl, i, light, nl);
+        block_append_bits(ws, i, hsmall, nhs);
+        block_append_bits(wb, i, hbig, nhb);
     }
 }
 
@@ -1560,7 +1404,7 @@ cudaError_t configure(int device) {
     cudaError_t e = cudaGetDeviceProperties(&prop, device);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prop<256, 2, 1>, kBlock, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan<256>, kBlock, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     g_sms = prop.multiProcessorCount;
@@ -1570,67 +1414,57 @@ cudaError_t configure(int device) {
     return cudaSuccess;
 }
 
-// Launch shapes of the propagation kernel: (edges in flight per neighbour group, minimum resident blocks per SM).
-// The grid is sized from the occupancy each shape reaches.
-template <int R, int UNR, int MINB>
-static void launch_prop_shape(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+template <int R, int MINB>
+static void launch_gather(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     static int grid = 0;
+    const int smem = kWarpsPerBlock * GSlots<R>::kBytesPerWarp;
     if (grid == 0) {
+        cudaFuncSetAttribute(k_propg<R, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prop<R, UNR, MINB>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_propg<R, MINB>, kBlock, smem);
         grid = g_sms * (occ > 0 ? occ : 1);
     }
-    k_prop<R, UNR, MINB><<<grid, kBlock, 0, s>>>(probs, act, nact);
+    k_propg<R, MINB><<<grid, kBlock, smem, s>>>(probs, act, nact);
 }
 
-// Launch shapes of the propagation sweep, exact alike; IM_PROP_VARIANT selects one (0 = default).
 template <int R>
-static void launch_prop_r(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    switch (g_variant) {
-        case 1: launch_prop_shape<R, 4, 1>(probs, act, nact, s); break;
-        case 2: launch_prop_shape<R, 2, 3>(probs, act, nact, s); break;
-        case 3: launch_prop_shape<R, 4, 3>(probs, act, nact, s); break;
-        case 4: launch_prop_shape<R, 2, 4>(probs, act, nact, s); break;
-        case 5: launch_prop_shape<R, 2, 1>(probs, act, nact, s); break;
-        default: launch_prop_shape<R, 1, 4>(probs, act, nact, s); break;  // fastest measured on GB300
+static void launch_combines(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    static int grid_s = 0, grid_b = 0;
+    const int smem = kWarpsPerBlock * GSlots<R>::kBytesPerWarp;
+    if (grid_s == 0) {
+        cudaFuncSetAttribute(k_combine<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_combine_big<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_combine<R>, kBlock, smem);
+        grid_s = g_sms * (occ > 0 ? occ : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_combine_big<R>, kBlock, smem);
+        grid_b = g_sms * (occ > 0 ? occ : 1);
     }
+    k_combine<R><<<grid_s, kBlock, smem, s>>>(probs, act, nact);
+    k_combine_big<R><<<grid_b, kBlock, smem, s>>>(probs, act, nact);
 }
 
-#define IMK_R_SWITCH(R, CALL)                 \
-    switch (R) {                              \
+#define IMK_R_SWITCH(R, CALL)                                \
+    switch (R) {                                             \
         case 64: { constexpr int RR = 64; CALL; } break;     \
         case 128: { constexpr int RR = 128; CALL; } break;   \
         case 256: { constexpr int RR = 256; CALL; } break;   \
         case 512: { constexpr int RR = 512; CALL; } break;   \
         case 1024: { constexpr int RR = 1024; CALL; } break; \
-        default: break;                       \
+        default: break;                                      \
     }
 
-template <int R>
-static void launch_tile(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    static int grid = 0;
-    const int smem = static_cast<int>(sizeof(TileSmem<R>));
-    if (grid == 0) {
-        cudaFuncSetAttribute(k_prop_tile<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_prop_tile<R>, kTileT, smem);
-        grid = g_sms * (occ > 0 ? occ : 1);
-    }
-    k_prop_tile<R><<<grid, kTileT, smem, s>>>(probs, act, nact);
-}
-
-template <int R>
-static void launch_tile(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
-
+// Minimum resident blocks per SM of the propagation kernel (register budget); IM_PROP_VARIANT selects 2 or 4
+// instead of the default 3 (all exact alike).
 void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    if (g_variant == 9) {
-        IMK_R_SWITCH(R, (launch_tile<RR>(probs, act, nact, s)));
-        return;
+    switch (g_variant) {
+        case 2: IMK_R_SWITCH(R, (launch_gather<RR, 2>(probs, act, nact, s))); return;
+        case 4: IMK_R_SWITCH(R, (launch_gather<RR, 4>(probs, act, nact, s))); return;
+        default: IMK_R_SWITCH(R, (launch_gather<RR, 3>(probs, act, nact, s))); return;
     }
-    IMK_R_SWITCH(R, (launch_prop_r<RR>(probs, act, nact, s)));
 }
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    IMK_R_SWITCH(R, (k_combine<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
+    IMK_R_SWITCH(R, (launch_combines<RR>(probs, act, nact, s)));
 }
 void launch_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);
@@ -1695,9 +1529,10 @@ void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, u
 void launch_row_tasks(const int64_t *xadj, int64_t n, int32_t *ntask, uint32_t *heavy, cudaStream_t s) {
     k_row_tasks<<<g_grid_block, kBlock, 0, s>>>(xadj, n, ntask, heavy);
 }
-void launch_task_fill(const int64_t *task_off, int64_t n, int32_t *task_row, int32_t *heavy_rows,
-                      unsigned int *nheavy, cudaStream_t s) {
-    k_task_fill<<<g_grid_block, kBlock, 0, s>>>(task_off, n, task_row, heavy_rows, nheavy);
+void launch_classes(const int64_t *xadj, const int64_t *task_off, int64_t n, int32_t *task_row, int32_t *light,
+                    unsigned int *counts, int32_t *hsmall, int32_t *hbig, cudaStream_t s) {
+    k_classes<<<g_grid_block, kBlock, 0, s>>>(xadj, task_off, n, task_row, light, counts, hsmall, counts + 1, hbig,
+                                              counts + 2);
 }
 int64_t scan_block_count(int64_t n) {
     const int64_t per = static_cast<int64_t>(kBlock) * kScanItems;

@@ -34,8 +34,8 @@ void launch_wc_thresholds(const int32_t *indeg, int64_t n, uint32_t *T, cudaStre
 void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, unsigned long long *cursor,
                            int32_t *adj_in, cudaStream_t s);
 void launch_row_tasks(const int64_t *xadj, int64_t n, int32_t *ntask, uint32_t *heavy, cudaStream_t s);
-void launch_task_fill(const int64_t *task_off, int64_t n, int32_t *task_row, int32_t *heavy_rows,
-                      unsigned int *nheavy, cudaStream_t s);
+void launch_classes(const int64_t *xadj, const int64_t *task_off, int64_t n, int32_t *task_row, int32_t *light,
+                    unsigned int *counts, int32_t *hsmall, int32_t *hbig, cudaStream_t s);
 int64_t scan_block_count(int64_t n);
 void launch_exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums, cudaStream_t s);
 

@@ -185,6 +185,35 @@ im_status im_select_seeds(im_ctx *ctx, const im_graph *graph, const im_params *p
 im_status im_select_seeds_batch(im_ctx *ctx, int32_t nq, const im_graph *graphs, const im_params *params,
                                 int32_t *const *seeds_out, double *sigma_out, int32_t *rebuilds_out);
 
+/* Largest seed count and register count accepted by im_estimate_static. */
+#define IM_STATIC_MAX_SEEDS 4096
+#define IM_STATIC_MAX_R 1024
+
+/*
+ * Estimate of a seed set that allocates no device memory.  The paper has no counterpart: this is an interface
+ * addition for callers that must not allocate at call time, such as a serving thread on a latency budget
+ * (cudaMalloc can synchronise the whole device and serialises on a process-wide lock) or a host process that
+ * accounts for every device byte through its own allocator and does not let a library allocate behind its back.
+ *
+ * It returns what im_estimate returns without sigma: *est_out = 2^(g / R) / 0.77351 (Eq. 2), where g (also stored
+ * in *gsum_out when it is not NULL) is the sum over the R simulations of the largest register of the k seeds
+ * (Eq. 3).  The caller passes the data and owns it:
+ *   registers: DEVICE pointer (device of ctx) to an n x R uint8 register matrix, row-major (row v = the R registers
+ *              of vertex v), for example the output of im_sketch_registers copied to the device;
+ *   seeds:     DEVICE pointer to k vertex ids;
+ *   est_out, gsum_out: HOST pointers, written only on IM_OK.
+ * Limits: R is 64, 128, 256, 512 or 1024; 1 <= k <= IM_STATIC_MAX_SEEDS; n >= 1.  Other values return IM_EINVAL,
+ * and so does a seed id outside [0, n) (checked on the device, the row is then not read).
+ * Scratch: one static device array of about 64 KiB defined in the library, which every device that runs this
+ * call keeps until the process exits.  The first call on a device looks up the array's address (once per device,
+ * with that device current); make that first call before any stream capture on the device.  All calls share the
+ * array and each call clears what it needs cleared, so calls that overlap on the GPU (from several threads or
+ * streams) race and can return wrong results: serialise them.  Work runs on the context's stream and the call
+ * returns after it completes.
+ */
+im_status im_estimate_static(im_ctx *ctx, const uint8_t *registers, int64_t n, int32_t R, const int32_t *seeds,
+                             int32_t k, double *est_out, uint64_t *gsum_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -165,6 +165,23 @@ class Context:
                                                   ctypes.addressof(ptrs), sig.ctypes.data, reb.ctypes.data))
         return [dict(seeds=seeds[i], sigma_final=float(sig[i]), rebuilds=int(reb[i])) for i in range(nq)]
 
+    def im_estimate_static(self, registers, seeds) -> tuple[float, int]:
+        """Estimate of a seed set from a register matrix and seed ids already on the device (CUDA torch tensors:
+        uint8 [n, R] and int32 [k]); the library allocates nothing for this call."""
+        import torch
+
+        assert registers.is_cuda and registers.dtype == torch.uint8 and registers.dim() == 2
+        assert seeds.is_cuda and seeds.dtype == torch.int32 and seeds.dim() == 1
+        registers = registers.contiguous()
+        seeds = seeds.contiguous()
+        _sync_torch()
+        est = ctypes.c_double()
+        g = ctypes.c_uint64()
+        self._check(self._L.im_estimate_static(self.h, registers.data_ptr(), int(registers.shape[0]),
+                                               int(registers.shape[1]), seeds.data_ptr(), int(seeds.shape[0]),
+                                               ctypes.addressof(est), ctypes.addressof(g)))
+        return est.value, g.value
+
 
 class Sketch:
     """An im_sketch: registers of a built sketch, kept on the device."""

@@ -55,6 +55,7 @@ SIGNATURES = {
     "im_select_seeds": (_I, [_P, ctypes.POINTER(im_graph), ctypes.POINTER(im_params), _P, _P, _P,
                              ctypes.POINTER(im_trace)]),
     "im_select_seeds_batch": (_I, [_P, _I32, _P, _P, _P, _P, _P]),
+    "im_estimate_static": (_I, [_P, _P, _I64, _I32, _P, _I32, _P, _P]),
 }
 
 _lib = None

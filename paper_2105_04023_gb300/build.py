@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libim.so")
 BUILD_DIR = os.path.join(ROOT, "_build", "im")
-SOURCES = ["im_kernels.cu", "im_host.cu"]
+SOURCES = ["im_kernels.cu", "im_host.cu", "im_static.cu"]
 HEADERS = ["im_common.cuh", "im_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

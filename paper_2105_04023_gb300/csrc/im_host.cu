@@ -723,6 +723,13 @@ struct im_sketch {
     im_ctx *ctx = nullptr;
 };
 
+// Context accessors for the allocation-free entry point (im_static.cu).
+namespace imh {
+cudaStream_t ctx_stream(const im_ctx *ctx) { return ctx->stream; }
+int ctx_device(const im_ctx *ctx) { return ctx->device; }
+void ctx_set_error(im_ctx *ctx, const char *msg) { ctx->err = msg; }
+}  // namespace imh
+
 extern "C" {
 
 im_status im_ctx_create(int device, void *cuda_stream, im_ctx **out) {

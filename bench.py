@@ -115,15 +115,23 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def aggregate(seconds: float, units: float, world: int) -> tuple[float, float]:
+    """Replica timing: the job takes as long as the slowest rank and processes the units of all ranks."""
     if world == 1:
-        return x
+        return seconds, units
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    return aggregate(x, 0.0, world)[0]
 
 
 def oracle_sample(prob, sweeps: int = 1) -> tuple[float, int, float]:
@@ -204,6 +212,7 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     dev_ms, visits, launches, prop_ms, prop_bytes, prop_launches, wall = [], 0, 0, 0.0, 0, 0, []
+    phases = {"sweep_ms": 0.0, "scan_ms": 0.0, "bfs_ms": 0.0, "init_ms": 0.0}
     for _ in range(args.steps):
         flush.fill_(1)
         torch.cuda.synchronize()
@@ -217,6 +226,8 @@ def run_ours(args, world, rank, local):
         prop_ms += st["prop_ms"]
         prop_bytes += st["prop_bytes"]
         prop_launches += st["prop_launches"]
+        for k in phases:
+            phases[k] += st[k]
         if seeds_ref is not None:
             assert out["seeds"].tolist() == seeds_ref.tolist(), "seed sets differ between steps"
         seeds_ref = out["seeds"]
@@ -224,8 +235,8 @@ def run_ours(args, world, rank, local):
     barrier(world)
     clk = clocks.stop()
     ctx.set_timing(False)
-    total_s = max_over_ranks(sum(dev_ms) / 1000.0, world)
-    value = visits * world / total_s
+    total_s, all_visits = aggregate(sum(dev_ms) / 1000.0, float(visits), world)
+    value = all_visits / total_s
 
     # end-to-end through the public API with host inputs (copies inside the timed call)
     e2e_ms = []
@@ -237,7 +248,7 @@ def run_ours(args, world, rank, local):
         out = ctx.im_select_seeds(host_graph, prm, trace=False)
         e2e_ms.append(1000 * (time.perf_counter() - t))
         e2e_visits += ctx.stats()["visits"]
-    e2e_s = max_over_ranks(sum(e2e_ms) / 1000.0, world)
+    e2e_s, e2e_all = aggregate(sum(e2e_ms) / 1000.0, float(e2e_visits), world)
 
     hbm, peak_kind = peaks()
     achieved = prop_bytes / (prop_ms / 1000.0) / 1e9 if prop_ms > 0 else None
@@ -264,12 +275,13 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"first Jacobi sweep of the build on the full graph ({cpu_visits} visits, "
                                        f"{cpu_dt:.1f} s)"},
-            "e2e": {"value": e2e_visits * world / e2e_s, "unit": UNIT,
+            "e2e": {"value": e2e_all / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(g.xadj.nbytes + g.adj.nbytes), "d2h_bytes_per_step": 4 * prob.K + 8,
                     "ms_per_step": 1000 * e2e_s / max(1, args.steps)},
             "gpu_launches": launches,
             "clocks": clk,
             "wall_ms_per_step": 1000 * sum(wall) / len(wall),
+            "phase_ms_per_step": {k: v / args.steps for k, v in phases.items()},
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -312,18 +324,163 @@ def run_build(args, local):
     ctx.close()
 
 
+def run_batch(args, local):
+    """The batched workload: many R-MAT graphs of uneven sizes, models and R, all selected together (one launch per
+    phase for all of them) versus one graph per call on the same GPU, with identical seed sets required."""
+    import torch
+
+    import paper_2105_04023_gb300 as im
+    from paper_2105_04023_gb300 import build as b
+    from synth import graphs, workloads
+
+    torch.cuda.set_device(local)
+    b.build()
+    probs = []
+    for i in range(args.batch_graphs):
+        scale, ef, model, p, R = workloads.batch_spec(i)
+        scale = min(scale, args.batch_max_scale)
+        g = graphs.cached(lambda: graphs.rmat(scale, ef, seed=1000 + i), f"rmat_s{scale}_ef{ef}_seed{1000 + i}")
+        probs.append(workloads.Problem(g, model, p, R=R, K=20, eps_g=0.01, seed=1000 + i))
+    gs = [im.Graph.from_synth(p.graph, p.model, p.p, device=f"cuda:{local}") for p in probs]
+    prms = [im.params(R=p.R, K=p.K, eps_g=p.eps_g, eps_l=p.eps_l, seed=p.seed) for p in probs]
+    ctx = im.Context(local)
+    ctx.im_select_seeds_batch(gs[:8], prms[:8])  # warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    batch = ctx.im_select_seeds_batch(gs, prms)
+    t_batch = time.perf_counter() - t
+    st_b = ctx.stats()
+    t = time.perf_counter()
+    plain = []
+    visits_plain = 0
+    for g, prm in zip(gs, prms):
+        plain.append(ctx.im_select_seeds(g, prm, trace=False))
+        visits_plain += ctx.stats()["visits"]
+    t_plain = time.perf_counter() - t
+    same = all(a["seeds"].tolist() == c["seeds"].tolist() and a["sigma_final"] == c["sigma_final"]
+               for a, c in zip(batch, plain))
+    m_total = sum(p.graph.m for p in probs)
+    out = {"mode": "batch", "graphs": len(probs), "edges_total": m_total, "max_scale": args.batch_max_scale,
+           "batched_s": t_batch, "plain_s": t_plain, "speedup": t_plain / t_batch,
+           "batched_graphs_per_s": len(probs) / t_batch, "plain_graphs_per_s": len(probs) / t_plain,
+           "batched_visits_per_s": st_b["visits"] / t_batch, "plain_visits_per_s": visits_plain / t_plain,
+           "identical_seed_sets": same, "batched_kernel_launches": st_b["kernel_launches"]}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def run_serve(args, local):
+    """The served workload: a resident pool of 64 R-MAT graphs (weighted cascade) and a Poisson stream of queries
+    (K uniform in 5..100, R in {64, 256}); admission by a 120 GB HBM budget; continuous batching.  The arrival rate
+    is 0.8 x the saturation rate measured by a closed-loop pre-run.  Reported: p50/p99 latency and queries/s, and
+    the same queries answered one at a time through im_select_seeds."""
+    import torch
+
+    import paper_2105_04023_gb300 as im
+    from paper_2105_04023_gb300 import build as b
+    from synth import graphs, workloads
+
+    torch.cuda.set_device(local)
+    b.build()
+    pool = []
+    for i in range(64):
+        scale = min(12 + (i % 9), args.serve_max_scale)
+        pool.append(graphs.cached(lambda: graphs.rmat(scale, 16, seed=2000 + i), f"rmat_s{scale}_ef16_seed{2000 + i}"))
+    Q = workloads.serve_queries(count=args.serve_queries, pool=64, seed=5)
+    ctx = im.Context(local)
+    srv = im.Server(ctx, hbm_budget_bytes=120 << 30, max_active=256)
+    gdev = [im.Graph.from_synth(g, im.IM_WC, device=f"cuda:{local}") for g in pool]
+    gids = [srv.im_server_add_graph(g) for g in gdev]
+
+    def prm(q):
+        return im.params(R=int(q[2]), K=int(q[1]), eps_g=0.01, eps_l=0.3, seed=7)
+
+    def drain(tickets, arrivals=None):
+        done, lat = {}, []
+        while tickets:
+            srv.im_server_step()
+            now = time.perf_counter()
+            for tk in list(tickets):
+                r = srv.im_server_poll(tk)
+                if r is not None:
+                    done[tk] = r
+                    if arrivals is not None:
+                        lat.append(now - arrivals[tk])
+                    tickets.discard(tk)
+        return done, lat
+
+    # closed loop: everything submitted at once gives the saturation rate
+    n_sat = min(100, len(Q) // 4)
+    t0 = time.perf_counter()
+    tk = {srv.im_server_submit(gids[int(q[0])], prm(q)) for q in Q[:n_sat]}
+    drain(tk)
+    qps_sat = n_sat / (time.perf_counter() - t0)
+    lam = 0.8 * qps_sat
+    # open loop: Poisson arrivals at lam
+    rest = Q[n_sat:]
+    arrive = np.cumsum(rest[:, 3]) / lam
+    t0 = time.perf_counter()
+    pending, arrivals, results, lat = set(), {}, {}, []
+    k = 0
+    while k < len(rest) or pending:
+        now = time.perf_counter() - t0
+        while k < len(rest) and arrive[k] <= now:
+            t = srv.im_server_submit(gids[int(rest[k, 0])], prm(rest[k]))
+            arrivals[t] = t0 + arrive[k]
+            pending.add(t)
+            results[t] = k
+            k += 1
+        if pending:
+            srv.im_server_step()
+            now2 = time.perf_counter()
+            for t in list(pending):
+                r = srv.im_server_poll(t)
+                if r is not None:
+                    lat.append(now2 - arrivals[t])
+                    results[t] = (results[t], r)
+                    pending.discard(t)
+        elif k < len(rest):
+            time.sleep(max(0.0, min(0.001, arrive[k] - (time.perf_counter() - t0))))
+    span = time.perf_counter() - t0
+    # the same queries one at a time through the plain call
+    t1 = time.perf_counter()
+    same = True
+    for t, (k_i, r) in results.items():
+        q = rest[k_i]
+        alone = ctx.im_select_seeds(gdev[int(q[0])], prm(q), trace=False)
+        same = same and alone["seeds"].tolist() == r["seeds"].tolist()
+    t_seq = time.perf_counter() - t1
+    lat_ms = np.array(lat) * 1000
+    out = {"mode": "serve", "queries": len(rest), "pool_graphs": 64, "pool_max_scale": args.serve_max_scale,
+           "saturation_qps": qps_sat, "lambda_qps": lam, "served_qps": len(rest) / span,
+           "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+           "sequential_qps": len(rest) / t_seq, "identical_seed_sets": same, "hbm_budget_gb": 120}
+    print(json.dumps(out), flush=True)
+    srv.close()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="select", choices=["select", "build"],
-                    help="build: time sketch builds only (one diffusion per step), for profiling")
+    ap.add_argument("--mode", default="select", choices=["select", "build", "batch", "serve"],
+                    help="build: sketch builds only (for profiling); batch: the 256-graph batched workload; "
+                         "serve: the query stream on a resident graph pool")
+    ap.add_argument("--batch-graphs", type=int, default=256)
+    ap.add_argument("--batch-max-scale", type=int, default=18)
+    ap.add_argument("--serve-queries", type=int, default=400)
+    ap.add_argument("--serve-max-scale", type=int, default=16)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.mode == "build":
         run_build(args, local)
+    elif args.mode == "batch":
+        run_batch(args, local)
+    elif args.mode == "serve":
+        run_serve(args, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:

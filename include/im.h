@@ -121,6 +121,10 @@ typedef struct {
     double prop_ms;           /* summed CUDA-event time of the propagation kernels of every sweep (the row kernel
                                  and the merge of split rows; 0 unless timing is enabled) */
     double total_ms;          /* device time of the whole call (CUDA events around it) */
+    double sweep_ms;          /* with timing enabled: all kernels of the diffusion sweeps */
+    double scan_ms;           /* with timing enabled: gain scans and seed choice */
+    double bfs_ms;            /* with timing enabled: reachability-search levels */
+    double init_ms;           /* with timing enabled: register (re)initialisation and M_S' merges */
 } im_stats;
 
 typedef struct im_ctx im_ctx;
@@ -184,6 +188,45 @@ im_status im_select_seeds(im_ctx *ctx, const im_graph *graph, const im_params *p
  */
 im_status im_select_seeds_batch(im_ctx *ctx, int32_t nq, const im_graph *graphs, const im_params *params,
                                 int32_t *const *seeds_out, double *sigma_out, int32_t *rebuilds_out);
+
+/*
+ * Serving.  A server keeps a pool of graphs prepared on the device and answers seed-selection queries on them.
+ * Queries wait in a first-come-first-served queue and are admitted while a batch slot is free and the device bytes
+ * of all running queries stay within the HBM budget; each admitted query's footprint (registers 2 n R bytes, reach
+ * bits 3 n R / 8, and lists of O(n + m / 64) words) is allocated on admission and freed when it finishes.  Every
+ * im_server_step admits what fits and then advances all running queries by one engine tick, in which each phase
+ * (sweeps, gain scans, reachability searches) is one launch for all of them, so queries that arrive while others
+ * run join the batch at the next step (continuous batching).  Results are identical to im_select_seeds on the
+ * same graph and parameters.  A server and its context are used by one host thread.
+ */
+typedef struct im_server im_server;
+
+/* Creates a server on ctx with an HBM budget for running queries and at most max_active (1..4096) of them. */
+im_status im_server_create(im_ctx *ctx, uint64_t hbm_budget_bytes, int32_t max_active, im_server **out);
+im_status im_server_destroy(im_server *srv);
+
+/* Prepares a graph on the device (copied if IM_MEM_HOST) and adds it to the pool; *graph_id names it. */
+im_status im_server_add_graph(im_server *srv, const im_graph *graph, int32_t *graph_id);
+
+/* Queues a query (Algorithm 1 with these parameters on graph graph_id); *ticket identifies it.  IM_ENOMEM if the
+ * query alone needs more than the budget. */
+im_status im_server_submit(im_server *srv, int32_t graph_id, const im_params *params, uint64_t *ticket);
+
+/* Device bytes a query with these parameters on graph graph_id is charged against the budget on admission. */
+im_status im_server_footprint(im_server *srv, int32_t graph_id, const im_params *params, uint64_t *bytes);
+
+/* Admits queued queries that fit and advances every running query by one tick; reports how many queries are
+ * running and queued afterwards (either pointer may be NULL). */
+im_status im_server_step(im_server *srv, int32_t *active_out, int32_t *queued_out);
+
+/* Result of a ticket: IM_ENOTREADY while queued or running; IM_OK with seeds_out (params.K ids), sigma_out and
+ * rebuilds_out (each may be NULL) once done, after which the ticket is forgotten; IM_ECANCELED for a cancelled
+ * query; a query that failed returns its error status. */
+im_status im_server_poll(im_server *srv, uint64_t ticket, int32_t *seeds_out, double *sigma_out,
+                         int32_t *rebuilds_out);
+
+/* Cancels a queued or running query (its memory is freed at once). */
+im_status im_server_cancel(im_server *srv, uint64_t ticket);
 
 /* Largest seed count and register count accepted by im_estimate_static. */
 #define IM_STATIC_MAX_SEEDS 4096

@@ -183,6 +183,72 @@ class Context:
         return est.value, g.value
 
 
+class Server:
+    """An im_server: resident graphs, an HBM-budgeted query queue and continuous batching on one context."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, max_active: int = 256):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx._check(ctx._L.im_server_create(ctx.h, int(hbm_budget_bytes), int(max_active), ctypes.byref(h)))
+        self.h = h
+        self._keep = []
+        self._K = {}
+
+    def close(self):
+        if self.h:
+            self.ctx._L.im_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def im_server_add_graph(self, graph: Graph) -> int:
+        _sync_torch()
+        g = graph.c()
+        gid = ctypes.c_int32()
+        self.ctx._check(self.ctx._L.im_server_add_graph(self.h, ctypes.byref(g), ctypes.addressof(gid)))
+        self._keep.append(graph)
+        return gid.value
+
+    def im_server_submit(self, graph_id: int, prm: _lib.im_params) -> int:
+        t = ctypes.c_uint64()
+        self.ctx._check(self.ctx._L.im_server_submit(self.h, int(graph_id), ctypes.byref(prm), ctypes.addressof(t)))
+        self._K[t.value] = prm.K
+        return t.value
+
+    def im_server_footprint(self, graph_id: int, prm: _lib.im_params) -> int:
+        b = ctypes.c_uint64()
+        self.ctx._check(self.ctx._L.im_server_footprint(self.h, int(graph_id), ctypes.byref(prm),
+                                                        ctypes.addressof(b)))
+        return b.value
+
+    def im_server_step(self) -> tuple[int, int]:
+        a = ctypes.c_int32()
+        q = ctypes.c_int32()
+        self.ctx._check(self.ctx._L.im_server_step(self.h, ctypes.addressof(a), ctypes.addressof(q)))
+        return a.value, q.value
+
+    def im_server_poll(self, ticket: int):
+        """None while queued or running, else dict(seeds, sigma_final, rebuilds); raises for failed queries."""
+        K = self._K[ticket]
+        seeds = np.zeros(K, np.int32)
+        sig = ctypes.c_double()
+        reb = ctypes.c_int32()
+        st = self.ctx._L.im_server_poll(self.h, ctypes.c_uint64(ticket), seeds.ctypes.data, ctypes.addressof(sig),
+                                        ctypes.addressof(reb))
+        if st == _lib.IM_ENOTREADY:
+            return None
+        del self._K[ticket]
+        self.ctx._check(st)
+        return dict(seeds=seeds, sigma_final=sig.value, rebuilds=reb.value)
+
+    def im_server_cancel(self, ticket: int):
+        self.ctx._check(self.ctx._L.im_server_cancel(self.h, ctypes.c_uint64(ticket)))
+
+
 class Sketch:
     """An im_sketch: registers of a built sketch, kept on the device."""
 

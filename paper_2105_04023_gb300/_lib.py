@@ -33,7 +33,9 @@ class im_trace(ctypes.Structure):
 class im_stats(ctypes.Structure):
     _fields_ = [("visits", ctypes.c_uint64), ("prop_bytes", ctypes.c_uint64), ("sweeps", ctypes.c_int64),
                 ("builds", ctypes.c_int64), ("bfs_levels", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("prop_launches", ctypes.c_int64), ("prop_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+                ("prop_launches", ctypes.c_int64), ("prop_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("sweep_ms", ctypes.c_double), ("scan_ms", ctypes.c_double), ("bfs_ms", ctypes.c_double),
+                ("init_ms", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -56,6 +58,14 @@ SIGNATURES = {
                              ctypes.POINTER(im_trace)]),
     "im_select_seeds_batch": (_I, [_P, _I32, _P, _P, _P, _P, _P]),
     "im_estimate_static": (_I, [_P, _P, _I64, _I32, _P, _I32, _P, _P]),
+    "im_server_create": (_I, [_P, ctypes.c_uint64, _I32, ctypes.POINTER(_P)]),
+    "im_server_destroy": (_I, [_P]),
+    "im_server_add_graph": (_I, [_P, ctypes.POINTER(im_graph), _P]),
+    "im_server_submit": (_I, [_P, _I32, ctypes.POINTER(im_params), _P]),
+    "im_server_step": (_I, [_P, _P, _P]),
+    "im_server_footprint": (_I, [_P, _I32, ctypes.POINTER(im_params), _P]),
+    "im_server_poll": (_I, [_P, ctypes.c_uint64, _P, _P, _P]),
+    "im_server_cancel": (_I, [_P, ctypes.c_uint64]),
 }
 
 _lib = None

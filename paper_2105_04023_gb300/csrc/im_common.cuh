@@ -34,6 +34,7 @@ struct DevCtr {
     uint32_t ntl[2];     // listed tasks of split rows for the sweep of that parity
     uint32_t nhs[2];     // listed split rows with at most kBigTasks tasks
     uint32_t nhb[2];     // listed split rows with more tasks
+    uint32_t fault;      // a bulk copy into shared memory did not complete within the wait limit
     unsigned long long chg_indeg;     // sum over changed vertices of (in-degree + 1): cost of listing the next rows
     unsigned long long visits;        // edge-simulation visits, running total
     unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total

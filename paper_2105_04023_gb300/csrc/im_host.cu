@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <functional>
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -50,6 +52,7 @@ struct im_ctx {
     bool timing = false;
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prop_ev;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> phase_ev[4];  // sweeps, scans, searches, inits
     int64_t launches = 0;
     int64_t prop_launches = 0;
     DevCtr *h_ctr = nullptr;  // pinned staging for counter read-back
@@ -70,6 +73,7 @@ namespace {
 struct DevMem {
     cudaStream_t s;
     std::vector<void *> ptrs;
+    uint64_t bytes = 0;
     explicit DevMem(cudaStream_t st) : s(st) {}
     template <class T>
     T *alloc(size_t count, bool zero = false) {
@@ -82,6 +86,7 @@ struct DevMem {
         }
         ck(e, "cudaMallocAsync");
         ptrs.push_back(p);
+        this->bytes += bytes;
         if (zero) ck(cudaMemsetAsync(p, 0, bytes, s), "cudaMemsetAsync");
         return static_cast<T *>(p);
     }
@@ -274,6 +279,8 @@ struct Prob {
     int64_t builds = 0;
     DevCtr last{};
     bool has_bfs = false;
+    im_status status = IM_OK;  // failure of this problem when the engine keeps going (serving)
+    std::string error;
 };
 
 void alloc_bfs(Prob &P) {
@@ -384,29 +391,35 @@ struct Engine {
     std::unique_ptr<DevMem> mem;
 
     DevCtr *d_ctrs = nullptr;
+    bool soft_errors = false;  // record a failing problem and keep the others going instead of throwing
 
-    // Uploads the descriptors; the counters of all problems live in one array so one copy reads them back.
-    Engine(im_ctx *c, std::vector<Prob *> ps, const std::vector<DevCtr> *init_ctr = nullptr)
-        : ctx(c), probs(std::move(ps)) {
+    // A slot table of `capacity` problems; the counters of all slots live in one array so one copy reads them back.
+    Engine(im_ctx *c, size_t capacity) : ctx(c), probs(capacity, nullptr) {
         mem = std::make_unique<DevMem>(ctx->stream);
-        d_probs = mem->alloc<DevProb>(probs.size());
-        d_ctrs = mem->alloc<DevCtr>(probs.size(), true);
-        if (init_ctr)
-            ck(cudaMemcpyAsync(d_ctrs, init_ctr->data(), probs.size() * sizeof(DevCtr), cudaMemcpyHostToDevice,
-                               ctx->stream),
-               "upload counters");
-        std::vector<DevProb> h(probs.size());
-        for (size_t i = 0; i < probs.size(); ++i) {
-            probs[i]->dp.ctr = d_ctrs + i;
-            probs[i]->d_ctr = d_ctrs + i;
-            h[i] = probs[i]->dp;
-            probs[i]->d_prob = d_probs + i;
-        }
-        ck(cudaMemcpyAsync(d_probs, h.data(), h.size() * sizeof(DevProb), cudaMemcpyHostToDevice, ctx->stream),
-           "upload problems");
-        ck(cudaStreamSynchronize(ctx->stream), "sync");
-        ensure_staging(probs.size());
+        d_probs = mem->alloc<DevProb>(capacity);
+        d_ctrs = mem->alloc<DevCtr>(capacity, true);
+        ensure_staging(capacity);
     }
+
+    Engine(im_ctx *c, std::vector<Prob *> ps, const std::vector<DevCtr> *init_ctr = nullptr) : Engine(c, ps.size()) {
+        for (size_t i = 0; i < ps.size(); ++i) attach(i, ps[i], init_ctr ? &(*init_ctr)[i] : nullptr);
+        ck(cudaStreamSynchronize(ctx->stream), "sync");
+    }
+
+    // Puts problem p into slot i with the given (or zero) counters.
+    void attach(size_t i, Prob *p, const DevCtr *c0) {
+        probs[i] = p;
+        p->dp.ctr = d_ctrs + i;
+        p->d_ctr = d_ctrs + i;
+        p->d_prob = d_probs + i;
+        p->last = c0 ? *c0 : DevCtr{};
+        ck(cudaMemcpyAsync(d_ctrs + i, &p->last, sizeof(DevCtr), cudaMemcpyHostToDevice, ctx->stream),
+           "upload counters");
+        ck(cudaMemcpyAsync(d_probs + i, &p->dp, sizeof(DevProb), cudaMemcpyHostToDevice, ctx->stream),
+           "upload problem");
+    }
+
+    void detach(size_t i) { probs[i] = nullptr; }
 
     void ensure_staging(size_t np) {
         if (ctx->h_ctr_cap < np) {
@@ -462,6 +475,20 @@ struct Engine {
         ctx->prop_launches += static_cast<int64_t>(byR.size());
     }
 
+    // Runs launch(); with timing enabled, brackets it with events counted for phase k.
+    template <class F>
+    void phase(int k, F &&launch) {
+        if (!ctx->timing) {
+            launch();
+            return;
+        }
+        cudaEvent_t a = get_event(), b = get_event();
+        ck(cudaEventRecord(a, ctx->stream), "event");
+        launch();
+        ck(cudaEventRecord(b, ctx->stream), "event");
+        ctx->phase_ev[k].emplace_back(a, b);
+    }
+
     cudaEvent_t get_event() {
         if (ctx->ev_free.empty()) {
             cudaEvent_t e;
@@ -485,14 +512,16 @@ struct Engine {
         }
         const List all = add_list(ids);
         pending.push_back([this, byR, all, chunk, s]() {
-            for (int c = 0; c < chunk; ++c) {
-                timed_prop(byR);
-                launch_frontier(d_probs, dptr(all), all.count, s);
-                launch_expand(d_probs, dptr(all), all.count, s);
-                launch_rows(d_probs, dptr(all), all.count, s);
-                launch_advance(d_probs, dptr(all), all.count, s);
-                ctx->launches += 4;
-            }
+            phase(0, [&]() {
+                for (int c = 0; c < chunk; ++c) {
+                    timed_prop(byR);
+                    launch_frontier(d_probs, dptr(all), all.count, s);
+                    launch_expand(d_probs, dptr(all), all.count, s);
+                    launch_rows(d_probs, dptr(all), all.count, s);
+                    launch_advance(d_probs, dptr(all), all.count, s);
+                    ctx->launches += 4;
+                }
+            });
         });
     }
 
@@ -501,12 +530,14 @@ struct Engine {
         const List all = add_list(ids);
         cudaStream_t s = ctx->stream;
         pending.push_back([this, all, chunk, s]() {
-            for (int c = 0; c < chunk; ++c) {
-                launch_bfs_level(d_probs, dptr(all), all.count, s);
-                launch_bfs_frontier(d_probs, dptr(all), all.count, s);
-                launch_bfs_advance(d_probs, dptr(all), all.count, s);
-                ctx->launches += 3;
-            }
+            phase(2, [&]() {
+                for (int c = 0; c < chunk; ++c) {
+                    launch_bfs_level(d_probs, dptr(all), all.count, s);
+                    launch_bfs_frontier(d_probs, dptr(all), all.count, s);
+                    launch_bfs_advance(d_probs, dptr(all), all.count, s);
+                    ctx->launches += 3;
+                }
+            });
         });
     }
 
@@ -524,8 +555,10 @@ struct Engine {
         std::vector<std::pair<List, int>> chooses;
         for (int32_t i : ids) chooses.emplace_back(add_list({i}), probs[i]->step);
         pending.push_back([this, byR, chooses, s]() {
-            for (auto &rl : byR) launch_scan(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
-            for (auto &c : chooses) launch_choose(d_probs, dptr(c.first), 1, c.second, s);
+            phase(1, [&]() {
+                for (auto &rl : byR) launch_scan(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
+                for (auto &c : chooses) launch_choose(d_probs, dptr(c.first), 1, c.second, s);
+            });
             ctx->launches += static_cast<int64_t>(byR.size() + chooses.size());
         });
     }
@@ -550,7 +583,8 @@ struct Engine {
            "read counters");
         ck(cudaStreamSynchronize(s), "sync");
         ck(cudaGetLastError(), "kernel launch");
-        for (size_t i = 0; i < probs.size(); ++i) probs[i]->last = ctx->h_ctr[i];
+        for (size_t i = 0; i < probs.size(); ++i)
+            if (probs[i]) probs[i]->last = ctx->h_ctr[i];
     }
 
     // Algorithm 1's error check after step k of problem P (host, double, from device integers).
@@ -580,62 +614,84 @@ struct Engine {
         }
     }
 
-    void run() {
+    void problem_error(Prob &P, im_status st, const char *msg) {
+        if (!soft_errors) fail(st, msg);
+        P.status = st;
+        P.error = msg;
+        P.phase = Prob::kDone;
+    }
+
+    // One engine tick: every active problem advances by one phase step (one launch per phase for all of them),
+    // then the counters are read back once.  Returns false when no problem had work.
+    bool tick() {
         cudaStream_t s = ctx->stream;
-        for (;;) {
-            std::vector<int32_t> init, sweep, scan, bfs, merge;
-            bool any = false;
-            for (size_t i = 0; i < probs.size(); ++i) {
-                Prob &P = *probs[i];
-                switch (P.phase) {
-                    case Prob::kInit: init.push_back(i); sweep.push_back(i); any = true; break;
-                    case Prob::kSweep: sweep.push_back(i); any = true; break;
-                    case Prob::kScan:
-                        if (P.merge_pending) merge.push_back(i);
-                        scan.push_back(i);
-                        bfs.push_back(i);
-                        any = true;
-                        break;
-                    case Prob::kBfs: bfs.push_back(i); any = true; break;
-                    default: break;
-                }
+        std::vector<int32_t> init, sweep, scan, bfs, merge;
+        bool any = false;
+        for (size_t i = 0; i < probs.size(); ++i) {
+            if (!probs[i]) continue;
+            Prob &P = *probs[i];
+            switch (P.phase) {
+                case Prob::kInit: init.push_back(i); sweep.push_back(i); any = true; break;
+                case Prob::kSweep: sweep.push_back(i); any = true; break;
+                case Prob::kScan:
+                    if (P.merge_pending) merge.push_back(i);
+                    scan.push_back(i);
+                    bfs.push_back(i);
+                    any = true;
+                    break;
+                case Prob::kBfs: bfs.push_back(i); any = true; break;
+                default: break;
             }
-            if (!any) break;
-            if (!merge.empty()) {
-                const List l = add_list(merge);
-                pending.push_back([this, l, s]() {
-                    launch_merge(d_probs, dptr(l), l.count, s);
-                    ctx->launches += 1;
-                });
-            }
-            if (!init.empty()) {
-                const List l = add_list(init);
-                pending.push_back([this, l, s]() {
-                    launch_init(d_probs, dptr(l), l.count, s);
-                    ctx->launches += 1;
-                });
-            }
-            enqueue_sweeps(sweep, ctx->sweep_chunk);
-            enqueue_scan(scan);
-            enqueue_bfs(bfs, ctx->level_chunk);
-            flush();
-            read_counters();
-            for (int32_t i : init) {
-                probs[i]->phase = Prob::kSweep;
-                probs[i]->builds += 1;
-            }
-            for (int32_t i : merge) probs[i]->merge_pending = false;
-            for (int32_t i : scan) probs[i]->phase = Prob::kBfs;
-            for (size_t i = 0; i < probs.size(); ++i) {
-                Prob &P = *probs[i];
-                if (P.phase == Prob::kSweep && P.last.done) {
-                    if (P.last.timeout) fail(IM_ETIMEOUT, "diffusion exceeded max_sweeps");
+        }
+        if (!any) return false;
+        if (!merge.empty()) {
+            const List l = add_list(merge);
+            pending.push_back([this, l, s]() {
+                phase(3, [&]() { launch_merge(d_probs, dptr(l), l.count, s); });
+                ctx->launches += 1;
+            });
+        }
+        if (!init.empty()) {
+            const List l = add_list(init);
+            pending.push_back([this, l, s]() {
+                phase(3, [&]() { launch_init(d_probs, dptr(l), l.count, s); });
+                ctx->launches += 1;
+            });
+        }
+        enqueue_sweeps(sweep, ctx->sweep_chunk);
+        enqueue_scan(scan);
+        enqueue_bfs(bfs, ctx->level_chunk);
+        flush();
+        read_counters();
+        for (int32_t i : init) {
+            probs[i]->phase = Prob::kSweep;
+            probs[i]->builds += 1;
+        }
+        for (int32_t i : merge) probs[i]->merge_pending = false;
+        for (int32_t i : scan) probs[i]->phase = Prob::kBfs;
+        for (size_t i = 0; i < probs.size(); ++i) {
+            if (!probs[i]) continue;
+            Prob &P = *probs[i];
+            if (P.phase == Prob::kDone) continue;
+            if (P.last.fault) {
+                problem_error(P, IM_ECUDA, "a bulk copy into shared memory did not complete");
+            } else if (P.phase == Prob::kSweep && P.last.done) {
+                if (P.last.timeout)
+                    problem_error(P, IM_ETIMEOUT, "diffusion exceeded max_sweeps");
+                else
                     P.phase = P.greedy ? Prob::kScan : Prob::kDone;
-                } else if (P.phase == Prob::kBfs && P.last.bdone) {
-                    if (P.last.btimeout) fail(IM_ETIMEOUT, "reachability search exceeded max_sweeps levels");
+            } else if (P.phase == Prob::kBfs && P.last.bdone) {
+                if (P.last.btimeout)
+                    problem_error(P, IM_ETIMEOUT, "reachability search exceeded max_sweeps levels");
+                else
                     decide(P);
-                }
             }
+        }
+        return true;
+    }
+
+    void run() {
+        while (tick()) {
         }
     }
 };
@@ -672,6 +728,13 @@ void begin_call(im_ctx *ctx) {
         ctx->ev_free.push_back(pe.second);
     }
     ctx->prop_ev.clear();
+    for (auto &v : ctx->phase_ev) {
+        for (auto &pe : v) {
+            ctx->ev_free.push_back(pe.first);
+            ctx->ev_free.push_back(pe.second);
+        }
+        v.clear();
+    }
 }
 
 void end_call(im_ctx *ctx, const std::vector<Prob *> &probs, cudaEvent_t t0, cudaEvent_t t1) {
@@ -695,6 +758,17 @@ void end_call(im_ctx *ctx, const std::vector<Prob *> &probs, cudaEvent_t t0, cud
         pm += x;
     }
     st.prop_ms = pm;
+    double ph[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 4; ++k)
+        for (auto &pe : ctx->phase_ev[k]) {
+            float x = 0.f;
+            ck(cudaEventElapsedTime(&x, pe.first, pe.second), "elapsed");
+            ph[k] += x;
+        }
+    st.sweep_ms = ph[0];
+    st.scan_ms = ph[1];
+    st.bfs_ms = ph[2];
+    st.init_ms = ph[3];
     ctx->stats = st;
 }
 
@@ -780,6 +854,11 @@ im_status im_ctx_destroy(im_ctx *ctx) {
         cudaEventDestroy(pe.first);
         cudaEventDestroy(pe.second);
     }
+    for (auto &v : ctx->phase_ev)
+        for (auto &pe : v) {
+            cudaEventDestroy(pe.first);
+            cudaEventDestroy(pe.second);
+        }
     for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_act) cudaFreeHost(ctx->h_act);
@@ -923,6 +1002,75 @@ im_status im_estimate(im_ctx *ctx, const im_sketch *sketch, const int32_t *seeds
     });
 }
 
+// ------------------------------------------------------------------------------------------------------------
+// Serving: a resident pool of prepared graphs, a queue of seed-selection queries, admission by an HBM budget and a
+// slot limit, and continuous batching (every engine tick launches each phase once for all admitted queries; a
+// query leaves the batch, and frees its memory, as soon as it is done).
+
+namespace {
+
+// Device bytes make_prob + alloc_bfs allocate for a greedy query (each allocation rounded up to 256 bytes).
+uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
+    auto r = [](uint64_t b) { return (std::max<uint64_t>(b, 16) + 255) / 256 * 256; };
+    const uint64_t n = static_cast<uint64_t>(g.n), R = static_cast<uint64_t>(prm.R), W = R / 32;
+    const uint64_t words = (n + 31) / 32, nt = std::max<int64_t>(g.n_tasks, 1);
+    uint64_t b = 0;
+    b += r(4 * R) * 2 + r(4 * 1024);                         // X, Y, prefix bitmap
+    b += r(n * R) * 2;                                       // register buffers
+    b += r(nt * R) + r(4 * (static_cast<uint64_t>(g.n_tasks) / 32 + 1));  // partial rows, their bits
+    b += r(4 * words) * 2 + r(32 * words);                   // live-set bits, row marks
+    b += r(4 * n) * 4;                                       // changed lists, row lists
+    b += r(4 * nt) * 2 + r(4 * std::max<int64_t>(g.n_hsmall, 1)) * 2 + r(4 * std::max<int64_t>(g.n_hbig, 1)) * 2;
+    b += r(R) + r(8 * 4096);                                 // M_S', frontier log
+    b += r(4 * n * W) * 3 + r(4 * words) * 2 + r(4 * n) * 4;  // reach bits, search frontiers, seed set
+    b += r(4 * static_cast<uint64_t>(prm.K)) * 2;            // step records
+    return b;
+}
+
+}  // namespace
+
+struct im_server {
+    im_ctx *ctx = nullptr;
+    uint64_t budget = 0, used = 0;
+    std::vector<std::shared_ptr<GraphDev>> graphs;
+    std::unique_ptr<Engine> eng;
+    struct Query {
+        int32_t gid = 0;
+        im_params prm{};
+        std::unique_ptr<Prob> P;
+        int64_t slot = -1;
+        uint64_t bytes = 0;
+        int state = 0;  // 0 queued, 1 running, 2 done, 3 cancelled, 4 failed
+        std::vector<int32_t> seeds;
+        double sigma = 0.0;
+        int32_t rebuilds = 0;
+        im_status status = IM_OK;
+        std::string error;
+    };
+    std::map<uint64_t, Query> q;
+    std::deque<uint64_t> queue;
+    std::vector<size_t> free_slots;
+    std::vector<uint64_t> slot_ticket;
+    uint64_t next = 1;
+};
+
+namespace {
+
+void server_release(im_server *srv, im_server::Query &Q) {
+    if (Q.slot >= 0) {
+        srv->eng->detach(static_cast<size_t>(Q.slot));
+        srv->free_slots.push_back(static_cast<size_t>(Q.slot));
+        srv->slot_ticket[static_cast<size_t>(Q.slot)] = 0;
+        Q.slot = -1;
+    }
+    if (Q.P) {
+        srv->used -= Q.bytes;
+        Q.P.reset();
+    }
+}
+
+}  // namespace
+
 static void select_many(im_ctx *ctx, int32_t nq, const im_graph *graphs, const im_params *params,
                         std::vector<std::unique_ptr<Prob>> &out) {
     std::vector<std::shared_ptr<GraphDev>> gd(nq);
@@ -997,6 +1145,179 @@ im_status im_select_seeds_batch(im_ctx *ctx, int32_t nq, const im_graph *graphs,
             }
         }
     });
+}
+
+
+im_status im_server_create(im_ctx *ctx, uint64_t hbm_budget_bytes, int32_t max_active, im_server **out) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!out) fail(IM_EINVAL, "out is NULL");
+        if (max_active < 1 || max_active > 4096) fail(IM_EINVAL, "max_active must be in [1, 4096]");
+        if (hbm_budget_bytes == 0) fail(IM_EINVAL, "the HBM budget must be positive");
+        ck(cudaSetDevice(ctx->device), "cudaSetDevice");
+        auto srv = std::make_unique<im_server>();
+        srv->ctx = ctx;
+        srv->budget = hbm_budget_bytes;
+        srv->eng = std::make_unique<Engine>(ctx, static_cast<size_t>(max_active));
+        srv->eng->soft_errors = true;
+        srv->slot_ticket.assign(static_cast<size_t>(max_active), 0);
+        for (int32_t i = max_active - 1; i >= 0; --i) srv->free_slots.push_back(static_cast<size_t>(i));
+        *out = srv.release();
+    });
+}
+
+im_status im_server_destroy(im_server *srv) {
+    if (!srv) return IM_EINVAL;
+    cudaSetDevice(srv->ctx->device);
+    cudaStreamSynchronize(srv->ctx->stream);
+    for (auto &kv : srv->q) kv.second.P.reset();
+    srv->eng.reset();
+    srv->graphs.clear();
+    cudaStreamSynchronize(srv->ctx->stream);
+    delete srv;
+    return IM_OK;
+}
+
+im_status im_server_add_graph(im_server *srv, const im_graph *graph, int32_t *graph_id) {
+    if (!srv) return IM_EINVAL;
+    im_ctx *ctx = srv->ctx;
+    return guarded(ctx, [&]() {
+        if (!graph_id) fail(IM_EINVAL, "graph_id is NULL");
+        ck(cudaSetDevice(ctx->device), "cudaSetDevice");
+        srv->graphs.push_back(prepare_graph(ctx, graph));
+        *graph_id = static_cast<int32_t>(srv->graphs.size() - 1);
+    });
+}
+
+im_status im_server_submit(im_server *srv, int32_t graph_id, const im_params *params, uint64_t *ticket) {
+    if (!srv) return IM_EINVAL;
+    im_ctx *ctx = srv->ctx;
+    return guarded(ctx, [&]() {
+        if (!params || !ticket) fail(IM_EINVAL, "params / ticket is NULL");
+        if (graph_id < 0 || graph_id >= static_cast<int32_t>(srv->graphs.size())) fail(IM_EINVAL, "unknown graph id");
+        const GraphDev &g = *srv->graphs[static_cast<size_t>(graph_id)];
+        check_params(params, g.n, true);
+        if (query_footprint(g, *params) > srv->budget)
+            fail(IM_ENOMEM, "the query needs more device memory than the whole HBM budget");
+        const uint64_t t = srv->next++;
+        im_server::Query &Q = srv->q[t];
+        Q.gid = graph_id;
+        Q.prm = *params;
+        srv->queue.push_back(t);
+        *ticket = t;
+    });
+}
+
+im_status im_server_footprint(im_server *srv, int32_t graph_id, const im_params *params, uint64_t *bytes) {
+    if (!srv) return IM_EINVAL;
+    return guarded(srv->ctx, [&]() {
+        if (!params || !bytes) fail(IM_EINVAL, "params / bytes is NULL");
+        if (graph_id < 0 || graph_id >= static_cast<int32_t>(srv->graphs.size())) fail(IM_EINVAL, "unknown graph id");
+        const GraphDev &g = *srv->graphs[static_cast<size_t>(graph_id)];
+        check_params(params, g.n, true);
+        *bytes = query_footprint(g, *params);
+    });
+}
+
+im_status im_server_step(im_server *srv, int32_t *active_out, int32_t *queued_out) {
+    if (!srv) return IM_EINVAL;
+    im_ctx *ctx = srv->ctx;
+    return guarded(ctx, [&]() {
+        ck(cudaSetDevice(ctx->device), "cudaSetDevice");
+        // admission: first come, first served, while a slot is free and the budget allows
+        while (!srv->queue.empty() && !srv->free_slots.empty()) {
+            const uint64_t t = srv->queue.front();
+            im_server::Query &Q = srv->q[t];
+            const GraphDev &g = *srv->graphs[static_cast<size_t>(Q.gid)];
+            const uint64_t est = query_footprint(g, Q.prm);
+            if (srv->used + est > srv->budget) break;
+            srv->queue.pop_front();
+            Q.P = make_prob(ctx, srv->graphs[static_cast<size_t>(Q.gid)], Q.prm, true);
+            Q.bytes = Q.P->mem->bytes;
+            srv->used += Q.bytes;
+            const size_t slot = srv->free_slots.back();
+            srv->free_slots.pop_back();
+            srv->eng->attach(slot, Q.P.get(), nullptr);
+            srv->slot_ticket[slot] = t;
+            Q.slot = static_cast<int64_t>(slot);
+            Q.state = 1;
+        }
+        srv->eng->tick();
+        // harvest finished queries and free their memory
+        for (size_t slot = 0; slot < srv->slot_ticket.size(); ++slot) {
+            const uint64_t t = srv->slot_ticket[slot];
+            if (!t) continue;
+            im_server::Query &Q = srv->q[t];
+            Prob &P = *Q.P;
+            if (P.phase != Prob::kDone) continue;
+            if (P.status != IM_OK) {
+                Q.state = 4;
+                Q.status = P.status;
+                Q.error = P.error;
+            } else {
+                Q.state = 2;
+                Q.seeds = P.seeds;
+                Q.sigma = P.sigma.back();
+                Q.rebuilds = 0;
+                for (uint8_t b : P.rebuilt) Q.rebuilds += b;
+            }
+            server_release(srv, Q);
+        }
+        int32_t active = 0;
+        for (uint64_t t : srv->slot_ticket) active += t ? 1 : 0;
+        if (active_out) *active_out = active;
+        if (queued_out) *queued_out = static_cast<int32_t>(srv->queue.size());
+    });
+}
+
+im_status im_server_poll(im_server *srv, uint64_t ticket, int32_t *seeds_out, double *sigma_out,
+                         int32_t *rebuilds_out) {
+    if (!srv) return IM_EINVAL;
+    im_ctx *ctx = srv->ctx;
+    auto it = srv->q.find(ticket);
+    if (it == srv->q.end()) {
+        set_err(ctx, "unknown ticket");
+        return IM_EINVAL;
+    }
+    im_server::Query &Q = it->second;
+    if (Q.state == 0 || Q.state == 1) return IM_ENOTREADY;
+    if (Q.state == 3) {
+        srv->q.erase(it);
+        return IM_ECANCELED;
+    }
+    if (Q.state == 4) {
+        const im_status st = Q.status;
+        set_err(ctx, Q.error);
+        srv->q.erase(it);
+        return st;
+    }
+    if (seeds_out) std::copy(Q.seeds.begin(), Q.seeds.end(), seeds_out);
+    if (sigma_out) *sigma_out = Q.sigma;
+    if (rebuilds_out) *rebuilds_out = Q.rebuilds;
+    srv->q.erase(it);
+    return IM_OK;
+}
+
+im_status im_server_cancel(im_server *srv, uint64_t ticket) {
+    if (!srv) return IM_EINVAL;
+    auto it = srv->q.find(ticket);
+    if (it == srv->q.end()) {
+        set_err(srv->ctx, "unknown ticket");
+        return IM_EINVAL;
+    }
+    im_server::Query &Q = it->second;
+    if (Q.state >= 2) return IM_OK;
+    if (Q.state == 0) {
+        for (auto qi = srv->queue.begin(); qi != srv->queue.end(); ++qi)
+            if (*qi == ticket) {
+                srv->queue.erase(qi);
+                break;
+            }
+    } else {
+        server_release(srv, Q);
+    }
+    Q.state = 3;
+    return IM_OK;
 }
 
 }  // extern "C"

@@ -107,6 +107,7 @@ __device__ __forceinline__ void load_xt(const uint32_t *__restrict__ X, int li, 
 }
 
 struct WarpStage {
+    unsigned long long mbar;  // completion barrier of the warp's bulk copies
     int32_t v[32];    // neighbour id; bit 31 set when the edge needs the exact test
     uint32_t ht[32];  // (h >> 17) in both halves
     uint32_t K[32];   // 0x8000 - (T >> 17) in both halves
@@ -161,21 +162,68 @@ struct GSlots {
     static constexpr int kBytesPerWarp = (N + 1) * R;
 };
 
-__device__ __forceinline__ void cpa16(void *smem, const void *gmem) {
-    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void cpa_wait_all() {
-    asm volatile("cp.async.commit_group;\n" ::);
-    asm volatile("cp.async.wait_group 0;\n" ::);
+
+// Per-warp completion barrier for bulk copies (TMA bulk copy engine, one instruction per row).
+constexpr uint32_t kWaitLimit = 1u << 16;      // tries of mbarrier.try_wait before a copy counts as lost
+constexpr uint32_t kWaitHintNs = 20000;        // each try may suspend the thread up to this long (about 1.3 s in all)
+
+__device__ __forceinline__ void mbar_init(unsigned long long *m) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(m)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+__device__ __forceinline__ void mbar_expect(unsigned long long *m, uint32_t bytes) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state)
+                 : "r"(smem_u32(m)), "r"(bytes)
+                 : "memory");
+    (void)state;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *m) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(m))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long *m, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity), "r"(kWaitHintNs)
+        : "memory");
+    return ok != 0;
+}
+// Waits (all lanes of the warp) for the barrier phase of the given parity.  After kWaitLimit tries the copies count
+// as lost: the fault flag is raised for the host, a second bounded wait gives copies still in flight a chance to
+// land, and the warp is marked aborted, after which it issues no copies and waits no more (its remaining work runs
+// on whatever the buffers hold and the host discards the result).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *m, uint32_t parity, unsigned int *fault, bool &aborted) {
+    if (aborted) return false;
+    bool done = false;
+    for (uint32_t it = 0; it < kWaitLimit && !done; ++it) done = mbar_try(m, parity);
+    done = __all_sync(0xffffffffu, done);
+    if (!done) {
+        if ((threadIdx.x & 31) == 0) atomicOr(fault, 1u);
+        for (uint32_t it = 0; it < kWaitLimit; ++it)
+            if (mbar_try(m, parity)) break;
+        aborted = true;
+    }
+    return done;
+}
+// Orders this warp's earlier generic reads of a buffer before bulk copies that overwrite it.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 template <int R>
 __device__ __forceinline__ void scan_range_g(const DevProb &P, int64_t u, int64_t e0, int64_t e1, bool allL,
                                              const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
                                              uint32_t (&acc)[Geo<R>::CPL][4], const uint32_t (&xt)[Geo<R>::CPL][8],
                                              int lane, int g, int li, WarpStage &sw, uint4 *buf, uint4 *own,
-                                             bool &own_loaded, uint32_t &nL, uint32_t &nTaken) {
+                                             bool &own_loaded, uint32_t &nL, uint32_t &nTaken, uint32_t &phase,
+                                             unsigned int *fault, bool &aborted) {
     using Gm = Geo<R>;
     constexpr int N = GSlots<R>::N;
     for (int64_t base = e0; base < e1; base += 32) {
@@ -210,17 +258,19 @@ __device__ __forceinline__ void scan_range_g(const DevProb &P, int64_t u, int64_
         nTaken += cnt;
         for (int i0 = 0; i0 < cnt; i0 += N) {
             const int nb = min(N, cnt - i0);
-            for (int k = lane; k < nb * Gm::CH; k += 32) {
-                const int sl = k / Gm::CH, c = k % Gm::CH;
-                cpa16(&buf[sl * Gm::CH + c],
-                      Mcur + static_cast<size_t>(sw.v[i0 + sl] & 0x7FFFFFFF) * R + 16 * c);
-            }
-            if (own != nullptr && !own_loaded) {
-                for (int k = lane; k < Gm::CH; k += 32) cpa16(&own[k], Mcur + static_cast<size_t>(u) * R + 16 * k);
-                own_loaded = true;
-            }
-            cpa_wait_all();
+            const bool with_own = own != nullptr && !own_loaded;
             __syncwarp();
+            fence_async_smem();
+            if (aborted) return;
+            if (lane == 0) mbar_expect(&sw.mbar, static_cast<uint32_t>((nb + (with_own ? 1 : 0)) * R));
+            __syncwarp();
+            if (lane < nb)
+                bulk_g2s(&buf[lane * Gm::CH], Mcur + static_cast<size_t>(sw.v[i0 + lane] & 0x7FFFFFFF) * R, R,
+                         &sw.mbar);
+            if (with_own && lane == 31) bulk_g2s(own, Mcur + static_cast<size_t>(u) * R, R, &sw.mbar);
+            own_loaded = own_loaded || with_own;
+            if (!mbar_wait(&sw.mbar, phase, fault, aborted)) return;
+            phase ^= 1u;
             for (int sl = g; sl < nb; sl += Gm::NG) {
                 uint4 row[Gm::CPL];
 #pragma unroll
@@ -295,7 +345,8 @@ __device__ __forceinline__ SweepWork sweep_work(const DevProb &P, const DevCtr &
 
 template <int R>
 __device__ void prop_problem_g(const DevProb &P, uint32_t t, const SweepWork &W, uint64_t cnt, uint64_t first,
-                               uint64_t nworkers, int lane, WarpStage &sw, uint4 *buf) {
+                               uint64_t nworkers, int lane, WarpStage &sw, uint4 *buf, uint32_t &phase,
+                               bool &aborted) {
     using Gm = Geo<R>;
     constexpr int N = GSlots<R>::N;
     const int g = lane / Gm::G, li = lane % Gm::G;
@@ -310,7 +361,7 @@ __device__ void prop_problem_g(const DevProb &P, uint32_t t, const SweepWork &W,
     const bool allL = (t == 0);
     const uint64_t tb = thr_bytes(P.model);
     Stats st;
-    for (uint64_t l = first; l < cnt; l += nworkers) {
+    for (uint64_t l = first; l < cnt && !aborted; l += nworkers) {
         uint32_t acc[Gm::CPL][4];
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c)
@@ -323,7 +374,7 @@ __device__ void prop_problem_g(const DevProb &P, uint32_t t, const SweepWork &W,
             const int64_t e0 = __ldg(&P.xadj[u]), e1 = __ldg(&P.xadj[u + 1]);
             const bool sync = test_bit(Lcur, u);
             scan_range_g<R>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, buf, own, own_loaded, nL,
-                            nTaken);
+                            nTaken, phase, &P.ctr->fault, aborted);
             reduce_groups<R>(acc);
             st.visits += static_cast<unsigned long long>(nL) * R;
             st.bytes += 16 + 4 * static_cast<uint64_t>(e1 - e0) + tb * nL + static_cast<uint64_t>(nTaken) * R;
@@ -338,7 +389,7 @@ __device__ void prop_problem_g(const DevProb &P, uint32_t t, const SweepWork &W,
             const int64_t e0 = __ldg(&P.xadj[u]) + (task - __ldg(&P.task_off[u])) * kTaskEdges;
             const int64_t e1 = min(e0 + kTaskEdges, __ldg(&P.xadj[u + 1]));
             scan_range_g<R>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, buf, nullptr, own_loaded,
-                            nL, nTaken);
+                            nL, nTaken, phase, &P.ctr->fault, aborted);
             reduce_groups<R>(acc);
             st.visits += static_cast<unsigned long long>(nL) * R;
             st.bytes += 4 * static_cast<uint64_t>(e1 - e0) + tb * nL + static_cast<uint64_t>(nTaken) * R;
@@ -362,7 +413,8 @@ __device__ void prop_problem_g(const DevProb &P, uint32_t t, const SweepWork &W,
 template <int R>
 __device__ __forceinline__ bool merge_partials(const DevProb &P, int64_t a, int64_t b,
                                                uint32_t (&acc)[Geo<R>::CPL][4], int lane, int g, int li,
-                                               WarpStage &sw, uint4 *buf, Stats &st) {
+                                               WarpStage &sw, uint4 *buf, Stats &st, uint32_t &phase,
+                                               bool &aborted) {
     using Gm = Geo<R>;
     constexpr int N = GSlots<R>::N;
     const int64_t k = a + lane;
@@ -377,12 +429,15 @@ __device__ __forceinline__ bool merge_partials(const DevProb &P, int64_t a, int6
     const int cnt = __popc(m);
     for (int i0 = 0; i0 < cnt; i0 += N) {
         const int nb = min(N, cnt - i0);
-        for (int q = lane; q < nb * Gm::CH; q += 32) {
-            const int sl = q / Gm::CH, c = q % Gm::CH;
-            cpa16(&buf[sl * Gm::CH + c], P.part + static_cast<size_t>(a + sw.v[i0 + sl]) * R + 16 * c);
-        }
-        cpa_wait_all();
         __syncwarp();
+        fence_async_smem();
+        if (aborted) return true;
+        if (lane == 0) mbar_expect(&sw.mbar, static_cast<uint32_t>(nb * R));
+        __syncwarp();
+        if (lane < nb)
+            bulk_g2s(&buf[lane * Gm::CH], P.part + static_cast<size_t>(a + sw.v[i0 + lane]) * R, R, &sw.mbar);
+        if (!mbar_wait(&sw.mbar, phase, &P.ctr->fault, aborted)) return true;
+        phase ^= 1u;
         for (int sl = g; sl < nb; sl += Gm::NG) {
 #pragma unroll
             for (int c = 0; c < Gm::CPL; ++c) {
@@ -419,6 +474,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restric
     extern __shared__ __align__(16) uint4 gather_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint4 *buf = gather_smem + static_cast<size_t>(wib) * (GSlots<R>::kBytesPerWarp / 16);
+    if (lane == 0) mbar_init(&stage[wib].mbar);
+    __syncwarp();
+    uint32_t phase = 0;
+    bool aborted = false;
     const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
     const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
     uint64_t base = 0;
@@ -431,7 +490,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restric
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
         if (first >= cnt) continue;
-        prop_problem_g<R>(P, C.t, W, cnt, first, nworkers, lane, stage[wib], buf);
+        prop_problem_g<R>(P, C.t, W, cnt, first, nworkers, lane, stage[wib], buf, phase, aborted);
     }
 }
 
@@ -445,6 +504,10 @@ __global__ void __launch_bounds__(kBlock) k_combine(const DevProb *__restrict__ 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int g = lane / Gm::G, li = lane % Gm::G;
     uint4 *buf = gather_smem + static_cast<size_t>(wib) * (GSlots<R>::kBytesPerWarp / 16);
+    if (lane == 0) mbar_init(&stage[wib].mbar);
+    __syncwarp();
+    uint32_t phase = 0;
+    bool aborted = false;
     const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
     const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
     uint64_t base = 0;
@@ -471,7 +534,7 @@ __global__ void __launch_bounds__(kBlock) k_combine(const DevProb *__restrict__ 
 #pragma unroll
                 for (int w = 0; w < 4; ++w) acc[c][w] = 0;
             const bool any = merge_partials<R>(P, __ldg(&P.task_off[u]), __ldg(&P.task_off[u + 1]), acc, lane, g,
-                                               li, stage[wib], buf, st);
+                                               li, stage[wib], buf, st, phase, aborted);
             reduce_groups<R>(acc);
             if (lane == 0) st.bytes += 16;
             finalize_row_g<R>(P, u, acc, any, test_bit(Lcur, u),
@@ -496,6 +559,10 @@ __global__ void __launch_bounds__(kBlock) k_combine_big(const DevProb *__restric
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int g = lane / Gm::G, li = lane % Gm::G;
     uint4 *buf = gather_smem + static_cast<size_t>(wib) * (GSlots<R>::kBytesPerWarp / 16);
+    if (lane == 0) mbar_init(&stage[wib].mbar);
+    __syncwarp();
+    uint32_t phase = 0;
+    bool aborted = false;
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
@@ -522,7 +589,7 @@ __global__ void __launch_bounds__(kBlock) k_combine_big(const DevProb *__restric
                 for (int w = 0; w < 4; ++w) acc[c][w] = 0;
             bool any = false;
             for (int64_t a = t0 + 32 * wib; a < t1; a += 32 * kWarpsPerBlock)
-                any |= merge_partials<R>(P, a, min(a + 32, t1), acc, lane, g, li, stage[wib], buf, st);
+                any |= merge_partials<R>(P, a, min(a + 32, t1), acc, lane, g, li, stage[wib], buf, st, phase, aborted);
             reduce_groups<R>(acc);
             if (g == 0) {
 #pragma unroll

@@ -189,6 +189,8 @@ def run_ours(args, world, rank, local):
 
     b.build()
     prob = load_workload()
+    if args.k:
+        prob.K = args.k
     g = prob.graph
     prm = im.params(R=prob.R, K=prob.K, eps_g=prob.eps_g, eps_l=prob.eps_l, eps_c=prob.eps_c, seed=prob.seed)
     dev_graph = im.Graph.from_synth(g, prob.model, prob.p, device=f"cuda:{local}")
@@ -469,6 +471,7 @@ def main():
     ap.add_argument("--mode", default="select", choices=["select", "build", "batch", "serve"],
                     help="build: sketch builds only (for profiling); batch: the 256-graph batched workload; "
                          "serve: the query stream on a resident graph pool")
+    ap.add_argument("--k", type=int, default=0, help="override the workload's K (profiling runs)")
     ap.add_argument("--batch-graphs", type=int, default=256)
     ap.add_argument("--batch-max-scale", type=int, default=18)
     ap.add_argument("--serve-queries", type=int, default=400)

@@ -13,7 +13,8 @@ constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kHeavyDeg = 64;        // rows with more out-edges are split into tasks of kTaskEdges edges
 constexpr int kTaskEdges = 64;
 constexpr int kBigTasks = 32;        // split rows with more tasks are merged by a whole block
-constexpr int kBfsHeavyDeg = 256;    // search-frontier vertices with more out-edges are spread over the grid
+constexpr int kBfsHeavyDeg = 256;    // search-frontier vertices with more out-edges are split into edge chunks
+constexpr int kBfsChunk = 256;       // out-edges per chunk task of a heavy search-frontier vertex
 constexpr int kExpandHeavyDeg = 1024;  // changed vertices with more in-edges are expanded by the whole grid
 constexpr int kPfxShift = 17;        // sampling words are compared on their top 15 bits first
 
@@ -48,7 +49,7 @@ struct DevCtr {
     uint32_t bdone;      // 1 once the search found no new vertex
     uint32_t btimeout;   // 1 if it hit the level limit first
     uint32_t nF[2];      // light frontier entries by level parity
-    uint32_t nH[2];      // heavy frontier entries by level parity
+    uint32_t nH[2];      // heavy frontier chunk tasks by level parity
     uint32_t pad1;
     unsigned long long reached;       // |{(v, j): v in R_{G_j}(S)}|
     unsigned long long levels_total;
@@ -92,10 +93,12 @@ struct DevProb {
     int32_t *tl0, *tl1;        // tasks of the marked split rows, by parity
     int32_t *hsl0, *hsl1;      // marked split rows (few tasks), by parity
     int32_t *hbl0, *hbl1;      // marked split rows (many tasks), by parity
+    uint32_t *live;            // m x W: edge e is live in simulation j (sampled once per run for the searches)
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
     uint32_t *del0, *del1;     // n x W: bits newly reached at the previous level, by parity
     uint32_t *Fb;              // bit per vertex: reached something new at this level
-    int32_t *F0, *F1, *H0, *H1;  // light / heavy frontier lists by parity
+    int32_t *F0, *F1;            // light frontier vertices by parity
+    uint64_t *H0, *H1;           // heavy frontier chunk tasks by parity: (chunk << 32) | vertex
     uint32_t *inS;             // bit per vertex: in the seed set
     uint8_t *MS;               // R bytes: M_S'
     DevCtr *ctr;

@@ -283,11 +283,14 @@ struct Prob {
     std::string error;
 };
 
-void alloc_bfs(Prob &P) {
+// Buffers of the reachability searches, and the per-edge live-simulation masks they read (computed here, on the
+// context stream, once per problem).  The descriptor must be complete apart from its counters.
+void alloc_bfs(Prob &P, cudaStream_t s) {
     const int64_t n = P.G->n;
     const int W = P.prm.R / 32;
     DevMem &mem = *P.mem;
     const int64_t words = (n + 31) / 32;
+    P.dp.live = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(P.G->m, 1)) * W);
     P.dp.vis = mem.alloc<uint32_t>(n * W, true);
     P.dp.del0 = mem.alloc<uint32_t>(n * W, true);
     P.dp.del1 = mem.alloc<uint32_t>(n * W, true);
@@ -295,9 +298,11 @@ void alloc_bfs(Prob &P) {
     P.dp.inS = mem.alloc<uint32_t>(words, true);
     P.dp.F0 = mem.alloc<int32_t>(n);
     P.dp.F1 = mem.alloc<int32_t>(n);
-    P.dp.H0 = mem.alloc<int32_t>(n);
-    P.dp.H1 = mem.alloc<int32_t>(n);
+    // chunk tasks of heavy vertices: ceil(deg / 256) <= deg / 128 for deg > 256, so m / 128 + 1 bound a level's
+    P.dp.H0 = mem.alloc<uint64_t>(P.G->m / 128 + 1);
+    P.dp.H1 = mem.alloc<uint64_t>(P.G->m / 128 + 1);
     P.has_bfs = true;
+    if (P.G->m > 0) launch_live_masks(P.dp, s);
 }
 
 std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const im_params &prm, bool greedy) {
@@ -373,7 +378,8 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     d.flog_cap = static_cast<int32_t>(P->flog_cap);
     d.flog = mem.alloc<int64_t>(P->flog_cap, true);
     if (greedy) {
-        alloc_bfs(*P);
+        alloc_bfs(*P, ctx->stream);
+        ctx->launches += 1;
         d.step_seed = mem.alloc<uint32_t>(prm.K);
         d.step_gsum = mem.alloc<uint32_t>(prm.K);
     }
@@ -958,7 +964,10 @@ im_status im_estimate(im_ctx *ctx, const im_sketch *sketch, const int32_t *seeds
         int32_t *d_seeds = tmp.alloc<int32_t>(k);
         ck(cudaMemcpyAsync(d_seeds, seeds, k * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy seeds");
         unsigned long long *d_g = tmp.alloc<unsigned long long>(1, true);
-        if (sigma_out && !P.has_bfs) alloc_bfs(P);
+        if (sigma_out && !P.has_bfs) {
+            alloc_bfs(P, s);
+            ctx->launches += 1;
+        }
         std::vector<DevCtr> c0(1);
         c0[0].res_par = P.last.res_par;
         c0[0].sweeps_total = P.last.sweeps_total;
@@ -1022,7 +1031,9 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     b += r(4 * n) * 4;                                       // changed lists, row lists
     b += r(4 * nt) * 2 + r(4 * std::max<int64_t>(g.n_hsmall, 1)) * 2 + r(4 * std::max<int64_t>(g.n_hbig, 1)) * 2;
     b += r(R) + r(8 * 4096);                                 // M_S', frontier log
-    b += r(4 * n * W) * 3 + r(4 * words) * 2 + r(4 * n) * 4;  // reach bits, search frontiers, seed set
+    b += r(4 * n * W) * 3 + r(4 * words) * 2 + r(4 * n) * 2;  // reach bits, frontier bits, seed set, light lists
+    b += r(8 * (static_cast<uint64_t>(g.m) / 128 + 1)) * 2;  // heavy chunk-task lists
+    b += r(4 * W * std::max<uint64_t>(static_cast<uint64_t>(g.m), 1));  // live-simulation masks of the edges
     b += r(4 * static_cast<uint64_t>(prm.K)) * 2;            // step records
     return b;
 }

@@ -175,12 +175,7 @@ __device__ __forceinline__ void mbar_init(unsigned long long *m) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 __device__ __forceinline__ void mbar_expect(unsigned long long *m, uint32_t bytes) {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state)
-                 : "r"(smem_u32(m)), "r"(bytes)
-                 : "memory");
-    (void)state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *m) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -980,6 +975,15 @@ __global__ void __launch_bounds__(kBlock) k_scan(const DevProb *__restrict__ pro
     }
 }
 
+namespace {
+// Appends the chunk tasks of heavy frontier vertex v (out-degree deg) to a heavy list.
+__device__ __forceinline__ void bfs_heavy_tasks(uint64_t *H, uint32_t *count, uint32_t v, int64_t deg) {
+    const uint32_t nt = static_cast<uint32_t>((deg + kBfsChunk - 1) / kBfsChunk);
+    const uint32_t at = atomicAdd(count, nt);
+    for (uint32_t c = 0; c < nt; ++c) H[at + c] = (static_cast<uint64_t>(c) << 32) | v;
+}
+}  // namespace
+
 // Takes the argmax as seed s of step k, adds it to S and starts the reachability search from it: s is marked
 // reached in every simulation where it was not yet, and those bits form the first frontier.
 __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact, int32_t step) {
@@ -1014,14 +1018,16 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
         C.gsum = gsum;
         C.best_key = 0;
         set_bit(P.inS, s);
-        C.reached += added;
         const int64_t deg = P.xadj[s + 1] - P.xadj[s];
         const bool heavy = deg > kBfsHeavyDeg;
         C.nF[0] = heavy ? 0u : 1u;
-        C.nH[0] = heavy ? 1u : 0u;
+        C.nH[0] = 0;
         C.nF[1] = 0;
         C.nH[1] = 0;
-        (heavy ? P.H0 : P.F0)[0] = static_cast<int32_t>(s);
+        if (heavy)
+            bfs_heavy_tasks(P.H0, &C.nH[0], s, deg);
+        else
+            P.F0[0] = static_cast<int32_t>(s);
         C.lvl = 0;
         C.bdone = added ? 0u : 1u;
         C.btimeout = 0;
@@ -1041,16 +1047,13 @@ __global__ void k_seed_set(const DevProb *__restrict__ prob, const int32_t *__re
         const int w = i % P.W;
         const size_t at = static_cast<size_t>(s) * P.W + w;
         const uint32_t old = atomicOr(&P.vis[at], 0xFFFFFFFFu);
-        if (~old) {
-            atomicOr(&P.del0[at], ~old);
-            atomicAdd(&C.reached, static_cast<unsigned long long>(__popc(~old)));
-        }
+        if (~old) atomicOr(&P.del0[at], ~old);
         if (w == 0) {
             const uint32_t prev = atomicOr(&P.inS[s >> 5], 1u << (s & 31));
             if (!((prev >> (s & 31)) & 1u)) {
                 const int64_t deg = P.xadj[s + 1] - P.xadj[s];
                 if (deg > kBfsHeavyDeg)
-                    P.H0[atomicAdd(&C.nH[0], 1u)] = s;
+                    bfs_heavy_tasks(P.H0, &C.nH[0], static_cast<uint32_t>(s), deg);
                 else
                     P.F0[atomicAdd(&C.nF[0], 1u)] = s;
             }
@@ -1060,122 +1063,89 @@ __global__ void k_seed_set(const DevProb *__restrict__ prob, const int32_t *__re
 
 namespace {
 
-// New bits for target v over edge (u, v) in the simulations of word k whose bit is set in d.
-__device__ __forceinline__ uint32_t bfs_edge_word(uint32_t d, uint32_t h, uint32_t T, const uint32_t *__restrict__ X,
-                                                  int k) {
-    uint32_t m = 0;
-    while (d) {
-        const int b = __ffs(d) - 1;
-        d &= d - 1;
-        if ((h ^ __ldg(&X[32 * k + b])) <= T) m |= 1u << b;
-    }
-    return m;
-}
-
-// Pushes the new bits of u over edge e = (u, v): vis[v] |= d(u) & live(u, v); bits that were not set yet go to the
-// next level's delta of v and put v on the next frontier.
-__device__ __forceinline__ unsigned long long bfs_push(const DevProb &P, int64_t u, int64_t e,
-                                                       const uint32_t *d, uint32_t *dnext) {
+// Pushes the new bits d of u over edge e = (u, v): bits of d that are live on e and not yet reached at v are new
+// at v; they are ORed into vis[v] and into the next level's delta of v, and v joins the next frontier.  Pushers of
+// the same level may race on a bit: both OR it, which is the same result, so no atomic needs a return value.
+__device__ __forceinline__ void bfs_push(const DevProb &P, int64_t e, const uint32_t *d, uint32_t *dnext) {
     const int32_t v = __ldg(&P.adj[e]);
-    uint32_t T;
-    bool ok;
-    edge_threshold(P, e, v, T, ok);
-    if (!ok) return 0;
-    const uint32_t h = edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
-    unsigned long long added = 0;
+    const uint32_t *lv = P.live + static_cast<size_t>(e) * P.W;
     bool any_new = false;
     for (int k = 0; k < P.W; ++k) {
         const uint32_t dk = d[k];
         if (!dk) continue;
-        const size_t at = static_cast<size_t>(v) * P.W + k;
-        const uint32_t cand = dk & ~P.vis[at];
-        if (!cand) continue;
-        const uint32_t m = bfs_edge_word(cand, h, T, P.X, k);
+        const uint32_t m = dk & __ldg(&lv[k]);
         if (!m) continue;
-        const uint32_t old = atomicOr(&P.vis[at], m);
-        const uint32_t nb = m & ~old;
-        if (nb) {
-            atomicOr(&dnext[at], nb);
-            added += __popc(nb);
-            any_new = true;
-        }
+        const size_t at = static_cast<size_t>(v) * P.W + k;
+        const uint32_t nb = m & ~P.vis[at];
+        if (!nb) continue;
+        atomicOr(&P.vis[at], nb);
+        atomicOr(&dnext[at], nb);
+        any_new = true;
     }
     if (any_new) set_bit(P.Fb, v);
-    return added;
 }
 
 }  // namespace
 
-// One level of the bit-parallel reachability search of Algorithm 1, over all simulations at once.
+// One level of the bit-parallel reachability search of Algorithm 1, over all simulations at once.  One warp per
+// light frontier vertex (its delta row is consumed, counted and cleared here) or per 256-edge chunk of a heavy one
+// (its row is read by several warps and cleared after the level); lanes go over out-edges.
 __global__ void __launch_bounds__(kBlock) k_bfs_level(const DevProb *__restrict__ probs,
                                                       const int32_t *__restrict__ act, int nact) {
     __shared__ uint32_t s_d[kWarpsPerBlock][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    // light frontier vertices: one warp each, lanes over out-edges
-    {
-        const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
-        const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
-        uint64_t base = 0;
-        for (int q = 0; q < nact; ++q) {
-            const DevProb &P = probs[act[q]];
-            const DevCtr &C = *P.ctr;
-            if (C.bdone) continue;
-            const uint32_t p = C.lvl & 1u;
-            const uint64_t cnt = C.nF[p];
-            const uint64_t first = first_owned(worker, nworkers, base);
-            base += cnt;
-            const int32_t *F = p ? P.F1 : P.F0;
-            uint32_t *dcur = p ? P.del1 : P.del0;
-            uint32_t *dnext = p ? P.del0 : P.del1;
-            unsigned long long added = 0;
-            for (uint64_t l = first; l < cnt; l += nworkers) {
-                const int64_t u = F[l];
-                for (int k = lane; k < P.W; k += 32) {
-                    const size_t at = static_cast<size_t>(u) * P.W + k;
-                    s_d[wib][k] = dcur[at];
+    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.bdone) continue;
+        const uint32_t p = C.lvl & 1u;
+        const uint64_t nf = C.nF[p];
+        const uint64_t cnt = nf + C.nH[p];
+        const uint64_t first = first_owned(worker, nworkers, base);
+        base += cnt;
+        const int32_t *F = p ? P.F1 : P.F0;
+        const uint64_t *H = p ? P.H1 : P.H0;
+        uint32_t *dcur = p ? P.del1 : P.del0;
+        uint32_t *dnext = p ? P.del0 : P.del1;
+        unsigned long long added = 0;
+        for (uint64_t l = first; l < cnt; l += nworkers) {
+            const bool light = l < nf;
+            int64_t u, e0, e1;
+            if (light) {
+                u = F[l];
+                e0 = __ldg(&P.xadj[u]);
+                e1 = __ldg(&P.xadj[u + 1]);
+            } else {
+                const uint64_t t = H[l - nf];
+                u = static_cast<int64_t>(static_cast<uint32_t>(t));
+                e0 = __ldg(&P.xadj[u]) + static_cast<int64_t>(t >> 32) * kBfsChunk;
+                const int64_t end = __ldg(&P.xadj[u + 1]);
+                e1 = end - e0 > kBfsChunk ? e0 + kBfsChunk : end;
+            }
+            for (int k = lane; k < P.W; k += 32) {
+                const size_t at = static_cast<size_t>(u) * P.W + k;
+                const uint32_t x = dcur[at];
+                s_d[wib][k] = x;
+                if (light) {
                     dcur[at] = 0;
+                    added += __popc(x);  // each newly reached (v, j) is consumed exactly once
                 }
-                __syncwarp();
-                const int64_t e0 = __ldg(&P.xadj[u]), e1 = __ldg(&P.xadj[u + 1]);
-                for (int64_t e = e0 + lane; e < e1; e += 32) added += bfs_push(P, u, e, s_d[wib], dnext);
-                __syncwarp();
             }
+            __syncwarp();
+            for (int64_t e = e0 + lane; e < e1; e += 32) bfs_push(P, e, s_d[wib], dnext);
+            __syncwarp();
+        }
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
-            if (lane == 0 && added) atomicAdd(&P.ctr->reached, added);
-        }
-    }
-    // heavy frontier vertices: their out-edges spread over every thread of the grid
-    {
-        const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-        const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-        uint64_t base = 0;
-        for (int q = 0; q < nact; ++q) {
-            const DevProb &P = probs[act[q]];
-            const DevCtr &C = *P.ctr;
-            if (C.bdone) continue;
-            const uint32_t p = C.lvl & 1u;
-            const int32_t *H = p ? P.H1 : P.H0;
-            const uint32_t *dcur = p ? P.del1 : P.del0;
-            uint32_t *dnext = p ? P.del0 : P.del1;
-            const uint32_t nh = C.nH[p];
-            unsigned long long added = 0;
-            for (uint32_t i = 0; i < nh; ++i) {
-                const int64_t u = H[i];
-                const int64_t e0 = P.xadj[u], e1 = P.xadj[u + 1];
-                const uint64_t cnt = static_cast<uint64_t>(e1 - e0);
-                const uint64_t first = first_owned(tid, nthreads, base);
-                base += cnt;
-                const uint32_t *d = dcur + static_cast<size_t>(u) * P.W;
-                for (uint64_t l = first; l < cnt; l += nthreads) added += bfs_push(P, u, e0 + l, d, dnext);
-            }
-            if (added) atomicAdd(&P.ctr->reached, added);
-        }
+        for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
+        if (lane == 0 && added) atomicAdd(&P.ctr->reached, added);
     }
 }
 
-// After a level: clears the consumed delta rows of heavy frontier vertices and compacts the vertices that reached
-// something new into the next frontier (light and heavy lists).
+// After a level: counts and clears the consumed delta rows of heavy frontier vertices and compacts the vertices
+// that reached something new into the next frontier (light vertices, and chunk tasks of heavy ones).
 __global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restrict__ probs,
                                                          const int32_t *__restrict__ act, int nact) {
     {
@@ -1187,13 +1157,22 @@ __global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restri
             const DevCtr &C = *P.ctr;
             if (C.bdone) continue;
             const uint32_t p = C.lvl & 1u;
-            const int32_t *H = p ? P.H1 : P.H0;
+            const uint64_t *H = p ? P.H1 : P.H0;
             uint32_t *dcur = p ? P.del1 : P.del0;
             const uint64_t cnt = static_cast<uint64_t>(C.nH[p]) * P.W;
             const uint64_t first = first_owned(tid, nthreads, base);
             base += cnt;
-            for (uint64_t l = first; l < cnt; l += nthreads)
-                dcur[static_cast<size_t>(H[l / P.W]) * P.W + l % P.W] = 0;
+            unsigned long long added = 0;  // consumed new bits of the heavy frontier vertices (once, at chunk 0)
+            for (uint64_t l = first; l < cnt; l += nthreads) {
+                const uint64_t t = H[l / P.W];
+                if (t >> 32) continue;
+                const size_t at = static_cast<size_t>(static_cast<uint32_t>(t)) * P.W + l % P.W;
+                added += __popc(dcur[at]);
+                dcur[at] = 0;
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
+            if ((threadIdx.x & 31) == 0 && added) atomicAdd(&P.ctr->reached, added);
         }
     }
     uint64_t base = 0;
@@ -1203,7 +1182,7 @@ __global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restri
         if (C.bdone) continue;
         const uint32_t np = (C.lvl + 1) & 1u;
         int32_t *F = np ? P.F1 : P.F0;
-        int32_t *H = np ? P.H1 : P.H0;
+        uint64_t *H = np ? P.H1 : P.H0;
         const int64_t words = (P.n + 31) >> 5;
         const uint64_t chunks = (words + kBlock - 1) / kBlock;
         const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
@@ -1226,7 +1205,10 @@ __global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restri
                     wl |= 1u << b;
             }
             block_append_bits(wl, i, F, &P.ctr->nF[np]);
-            if (__syncthreads_or(wh != 0)) block_append_bits(wh, i, H, &P.ctr->nH[np]);
+            for (uint32_t x = wh; x; x &= x - 1) {
+                const int64_t v = i * 32 + __ffs(x) - 1;
+                bfs_heavy_tasks(H, &P.ctr->nH[np], static_cast<uint32_t>(v), P.xadj[v + 1] - P.xadj[v]);
+            }
         }
     }
 }
@@ -1280,6 +1262,57 @@ __global__ void k_estimate(const DevProb *__restrict__ prob, const int32_t *__re
     atomicAdd(&s_sum, part);
     __syncthreads();
     if (threadIdx.x == 0) *gsum_out = s_sum;
+}
+
+// Live-simulation masks for the reachability searches (Eq. 4-5 evaluated once per edge and simulation): bit j of
+// live[e] is set iff edge e is sampled in simulation j.  One warp per light row or split-row task; lanes stage 32
+// edges, then for each edge every lane tests one simulation of each 32-simulation word and a ballot forms the word.
+template <int R>
+__global__ void __launch_bounds__(kBlock) k_live_masks(const DevProb P) {
+    constexpr int W = R / 32;
+    const int lane = threadIdx.x & 31;
+    const uint64_t worker = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nworkers = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    uint32_t xr[W < 8 ? W : 8];
+#pragma unroll
+    for (int k = 0; k < (W < 8 ? W : 8); ++k) xr[k] = __ldg(&P.X[32 * k + lane]);
+    const uint64_t cnt = static_cast<uint64_t>(P.n_light) + static_cast<uint64_t>(P.n_tasks);
+    for (uint64_t l = worker; l < cnt; l += nworkers) {
+        int64_t u, e0, e1;
+        if (l < static_cast<uint64_t>(P.n_light)) {
+            u = P.light_list[l];
+            e0 = P.xadj[u];
+            e1 = P.xadj[u + 1];
+        } else {
+            const int64_t task = static_cast<int64_t>(l - P.n_light);
+            u = P.task_row[task];
+            e0 = P.xadj[u] + (task - P.task_off[u]) * kTaskEdges;
+            e1 = min(e0 + kTaskEdges, P.xadj[u + 1]);
+        }
+        for (int64_t base = e0; base < e1; base += 32) {
+            const int64_t e = base + lane;
+            uint32_t h = 0, T = 0;
+            bool ok = false;
+            if (e < e1) {
+                const int32_t v = __ldg(&P.adj[e]);
+                edge_threshold(P, e, v, T, ok);
+                h = edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
+            }
+            const int cnt_e = e1 - base < 32 ? static_cast<int>(e1 - base) : 32;
+            for (int j = 0; j < cnt_e; ++j) {
+                const uint32_t hj = __shfl_sync(kFull, h, j);
+                const uint32_t Tj = __shfl_sync(kFull, T, j);
+                const bool okj = __shfl_sync(kFull, ok, j);
+                uint32_t *out = P.live + static_cast<size_t>(base + j) * W;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    const uint32_t x = k < 8 ? xr[k < 8 ? k : 0] : __ldg(&P.X[32 * k + lane]);
+                    const uint32_t m = __ballot_sync(kFull, okj && ((hj ^ x) <= Tj));
+                    if (lane == (k & 31)) out[k] = m;
+                }
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -1579,6 +1612,9 @@ void launch_validate(const int64_t *xadj, const int32_t *adj, int64_t n, int64_t
 void launch_edge_thresholds(const float *p, int64_t m, uint32_t *T, uint8_t *ok, unsigned int *flags,
                             cudaStream_t s) {
     if (m > 0) k_edge_thresholds<<<g_grid_block, kBlock, 0, s>>>(p, m, T, ok, flags);
+}
+void launch_live_masks(const DevProb &P, cudaStream_t s) {
+    IMK_R_SWITCH(P.R, (k_live_masks<RR><<<g_grid_warp, kBlock, 0, s>>>(P)));
 }
 void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx, cudaStream_t s) {
     k_words<<<(R + 255) / 256, 256, 0, s>>>(seed, R, X, Y, xpfx);

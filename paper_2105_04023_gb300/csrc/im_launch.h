@@ -28,6 +28,7 @@ void launch_bfs_advance(const DevProb *probs, const int32_t *act, int nact, cuda
 void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned long long *gsum, cudaStream_t s);
 
+void launch_live_masks(const DevProb &P, cudaStream_t s);
 void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx, cudaStream_t s);
 void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s);
 void launch_wc_thresholds(const int32_t *indeg, int64_t n, uint32_t *T, cudaStream_t s);

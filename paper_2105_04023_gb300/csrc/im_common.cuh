@@ -20,6 +20,17 @@ constexpr int kPfxShift = 17;        // sampling words are compared on their top
 
 enum Model : int32_t { kIC = 0, kWC = 1, kPerEdge = 2 };
 
+// Work of one sweep unit (a light row, or a task of kTaskEdges edges of a split row): its sparse pairs
+// [p0, p0 + np) and its dense edges dlist[d0, d0 + nd).
+struct UnitD {
+    int64_t p0;
+    int64_t d0;
+    uint32_t np;
+    uint32_t nd;
+    int32_t u;
+    int32_t pad;
+};
+
 // Counters of one problem, written by the kernels and read back by the host after each engine tick.
 struct DevCtr {
     // diffusion (Algorithm 2) ----------------------------------------------------------------------------------
@@ -93,7 +104,19 @@ struct DevProb {
     int32_t *tl0, *tl1;        // tasks of the marked split rows, by parity
     int32_t *hsl0, *hsl1;      // marked split rows (few tasks), by parity
     int32_t *hbl0, *hbl1;      // marked split rows (many tasks), by parity
-    uint32_t *live;            // m x W: edge e is live in simulation j (sampled once per run for the searches)
+    uint32_t *live;            // m x W: edge e is live in simulation j (Eq. 4-5 evaluated once per run)
+    // Sparse form of the sampled edges.  An edge live in at most dense_min simulations contributes one pair
+    // (target v, simulation j) per live simulation, pairs in edge order; an edge live in more is a dense edge,
+    // merged with whole register rows.
+    const int64_t *pofs;       // m+1: pairs before each edge
+    const int64_t *dofs;       // m+1: dense edges before each edge
+    const int32_t *pv;         // per pair: target vertex
+    const uint16_t *pj;        // per pair: simulation
+    const uint32_t *dlist;     // dense edge ids, in edge order
+    const UnitD *rdesc;        // n: sweep unit of each row (used for light rows)
+    const UnitD *tdesc;        // n_tasks: sweep unit of each task
+    int32_t dense_min;
+    int32_t pad2;
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
     uint32_t *del0, *del1;     // n x W: bits newly reached at the previous level, by parity
     uint32_t *Fb;              // bit per vertex: reached something new at this level

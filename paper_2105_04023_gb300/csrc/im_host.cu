@@ -90,6 +90,15 @@ struct DevMem {
         if (zero) ck(cudaMemsetAsync(p, 0, bytes, s), "cudaMemsetAsync");
         return static_cast<T *>(p);
     }
+    // Returns a temporary allocation to the pool (stream-ordered: later work on s may reuse it).
+    void release(void *p) {
+        for (size_t i = 0; i < ptrs.size(); ++i)
+            if (ptrs[i] == p) {
+                cudaFreeAsync(p, s);
+                ptrs.erase(ptrs.begin() + static_cast<std::ptrdiff_t>(i));
+                return;
+            }
+    }
     ~DevMem() {
         for (void *p : ptrs) cudaFreeAsync(p, s);
     }
@@ -208,12 +217,12 @@ std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
     const int64_t nb = scan_block_count(n) + 1;
     int64_t *bsums = mem.alloc<int64_t>(nb);
     G->xadj_in = mem.alloc<int64_t>(n + 1);
-    launch_exclusive_scan(indeg, n, G->xadj_in, bsums, s);
+    ctx->launches += launch_exclusive_scan(indeg, n, G->xadj_in, bsums, s);
     unsigned long long *cursor = mem.alloc<unsigned long long>(n);
     ck(cudaMemcpyAsync(cursor, G->xadj_in, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s), "copy cursor");
     G->adj_in = mem.alloc<int32_t>(m);
     launch_transpose_fill(G->xadj, G->adj, n, cursor, G->adj_in, s);
-    ctx->launches += 5;
+    ctx->launches += 2;
     if (g->model == IM_WC) {
         G->T_vert = mem.alloc<uint32_t>(n);
         launch_wc_thresholds(indeg, n, G->T_vert, s);
@@ -232,8 +241,7 @@ std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
     int32_t *ntask = mem.alloc<int32_t>(n);
     launch_row_tasks(G->xadj, n, ntask, G->heavy, s);
     G->task_off = mem.alloc<int64_t>(n + 1);
-    launch_exclusive_scan(ntask, n, G->task_off, bsums, s);
-    ctx->launches += 4;
+    ctx->launches += 1 + launch_exclusive_scan(ntask, n, G->task_off, bsums, s);
     int64_t h_tasks = 0;
     unsigned int h_flags[4] = {0, 0, 0, 0};
     ck(cudaMemcpyAsync(&h_tasks, G->task_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "read tasks");
@@ -279,6 +287,7 @@ struct Prob {
     int64_t builds = 0;
     DevCtr last{};
     bool has_bfs = false;
+    int64_t npairs = 0, ndense = 0;  // sparse pairs and dense edges of the sampled graph
     im_status status = IM_OK;  // failure of this problem when the engine keeps going (serving)
     std::string error;
 };
@@ -290,7 +299,6 @@ void alloc_bfs(Prob &P, cudaStream_t s) {
     const int W = P.prm.R / 32;
     DevMem &mem = *P.mem;
     const int64_t words = (n + 31) / 32;
-    P.dp.live = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(P.G->m, 1)) * W);
     P.dp.vis = mem.alloc<uint32_t>(n * W, true);
     P.dp.del0 = mem.alloc<uint32_t>(n * W, true);
     P.dp.del1 = mem.alloc<uint32_t>(n * W, true);
@@ -302,7 +310,63 @@ void alloc_bfs(Prob &P, cudaStream_t s) {
     P.dp.H0 = mem.alloc<uint64_t>(P.G->m / 128 + 1);
     P.dp.H1 = mem.alloc<uint64_t>(P.G->m / 128 + 1);
     P.has_bfs = true;
-    if (P.G->m > 0) launch_live_masks(P.dp, s);
+}
+
+// An edge live in more simulations than this is merged as a dense edge (whole register rows), a sparser one as
+// (target, simulation) pairs.
+inline int32_t dense_min_for(int R) { return std::max(8, R / 8); }
+
+// Eq. 4-5 for every edge and simulation, once per problem: the live masks (kept for the reachability searches)
+// and from them the sparse pairs and the dense edge list of the sweeps.  Reads back the two totals to size the
+// pair arrays (one stream synchronisation).
+void sample_edges(im_ctx *ctx, Prob &P) {
+    const int64_t m = P.G->m;
+    const int W = P.prm.R / 32;
+    DevMem &mem = *P.mem;
+    DevProb &d = P.dp;
+    cudaStream_t s = ctx->stream;
+    if (m >= (int64_t(1) << 32)) fail(IM_EINVAL, "graphs with 2^32 or more edges are not supported");
+    d.dense_min = dense_min_for(P.prm.R);
+    d.live = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(m, 1)) * W);
+    int64_t *pofs = mem.alloc<int64_t>(m + 1, true);
+    int64_t *dofs = mem.alloc<int64_t>(m + 1, true);
+    d.pofs = pofs;
+    d.dofs = dofs;
+    UnitD *rdesc = mem.alloc<UnitD>(static_cast<size_t>(std::max<int64_t>(P.G->n, 1)));
+    UnitD *tdesc = mem.alloc<UnitD>(static_cast<size_t>(std::max<int64_t>(P.G->n_tasks, 1)));
+    d.rdesc = rdesc;
+    d.tdesc = tdesc;
+    if (m == 0) {
+        d.pv = mem.alloc<int32_t>(1);
+        d.pj = mem.alloc<uint16_t>(1);
+        d.dlist = mem.alloc<uint32_t>(1);
+        return;
+    }
+    launch_live_masks(d, s);
+    int32_t *np = mem.alloc<int32_t>(m);
+    int32_t *nd = mem.alloc<int32_t>(m);
+    int64_t *bsums = mem.alloc<int64_t>(scan_block_count(m) + 1);
+    launch_pair_counts(d, np, nd, s);
+    ctx->launches += 2 + launch_exclusive_scan(np, m, pofs, bsums, s);
+    ctx->launches += launch_exclusive_scan(nd, m, dofs, bsums, s);
+    int64_t tot[2] = {0, 0};
+    ck(cudaMemcpyAsync(&tot[0], pofs + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+    ck(cudaMemcpyAsync(&tot[1], dofs + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+    ck(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    mem.release(np);
+    mem.release(nd);
+    mem.release(bsums);
+    int32_t *pv = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
+    uint16_t *pj = mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
+    uint32_t *dlist = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
+    launch_pair_fill(d, pv, pj, dlist, s);
+    launch_unit_desc(d, rdesc, tdesc, s);
+    ctx->launches += 2;
+    d.pv = pv;
+    d.pj = pj;
+    d.dlist = dlist;
+    P.npairs = tot[0];
+    P.ndense = tot[1];
 }
 
 std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const im_params &prm, bool greedy) {
@@ -377,9 +441,9 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     P->flog_cap = 4096;
     d.flog_cap = static_cast<int32_t>(P->flog_cap);
     d.flog = mem.alloc<int64_t>(P->flog_cap, true);
+    sample_edges(ctx, *P);
     if (greedy) {
         alloc_bfs(*P, ctx->stream);
-        ctx->launches += 1;
         d.step_seed = mem.alloc<uint32_t>(prm.K);
         d.step_gsum = mem.alloc<uint32_t>(prm.K);
     }
@@ -477,7 +541,7 @@ struct Engine {
             ck(cudaEventRecord(b, s), "event");
             ctx->prop_ev.emplace_back(a, b);
         }
-        ctx->launches += 2 * static_cast<int64_t>(byR.size());
+        ctx->launches += 3 * static_cast<int64_t>(byR.size());  // sweep kernel, two combine kernels
         ctx->prop_launches += static_cast<int64_t>(byR.size());
     }
 
@@ -964,10 +1028,7 @@ im_status im_estimate(im_ctx *ctx, const im_sketch *sketch, const int32_t *seeds
         int32_t *d_seeds = tmp.alloc<int32_t>(k);
         ck(cudaMemcpyAsync(d_seeds, seeds, k * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy seeds");
         unsigned long long *d_g = tmp.alloc<unsigned long long>(1, true);
-        if (sigma_out && !P.has_bfs) {
-            alloc_bfs(P, s);
-            ctx->launches += 1;
-        }
+        if (sigma_out && !P.has_bfs) alloc_bfs(P, s);
         std::vector<DevCtr> c0(1);
         c0[0].res_par = P.last.res_par;
         c0[0].sweeps_total = P.last.sweeps_total;
@@ -1033,7 +1094,13 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     b += r(R) + r(8 * 4096);                                 // M_S', frontier log
     b += r(4 * n * W) * 3 + r(4 * words) * 2 + r(4 * n) * 2;  // reach bits, frontier bits, seed set, light lists
     b += r(8 * (static_cast<uint64_t>(g.m) / 128 + 1)) * 2;  // heavy chunk-task lists
-    b += r(4 * W * std::max<uint64_t>(static_cast<uint64_t>(g.m), 1));  // live-simulation masks of the edges
+    const uint64_t m1 = std::max<uint64_t>(static_cast<uint64_t>(g.m), 1);
+    b += r(4 * W * m1);                                      // live-simulation masks of the edges
+    b += r(8 * (m1 + 1)) * 2;                                // pair and dense-edge offsets
+    b += r(sizeof(UnitD) * std::max<uint64_t>(n, 1)) + r(sizeof(UnitD) * nt);  // sweep-unit descriptors
+    // pairs: at most dense_min per edge (6 bytes each), dense edges 4 bytes; the counts and scan sums of the
+    // preparation are freed before the pairs are allocated, and are smaller
+    b += r(6 * m1 * static_cast<uint64_t>(dense_min_for(prm.R))) + r(4 * m1);
     b += r(4 * static_cast<uint64_t>(prm.K)) * 2;            // step records
     return b;
 }

@@ -7,7 +7,9 @@
 //
 // Paper map:
 //   k_init        Algorithm 1, register initialisation (and its re-initialisation with R_G(S) blocked)
-//   k_prop        Algorithm 2, one sweep of the pull-based diffusion with hash-based fused sampling (Eq. 4-5)
+//   k_prop        Algorithm 2, one sweep of the pull-based diffusion; the sampling of Eq. 4-5 is evaluated once
+//                 per run (k_live_masks) and kept as (target, simulation) pairs for edges live in few simulations
+//                 (k_pair_counts, k_pair_fill), the hashed test runs in the sweep for the other edges
 //   k_combine     Algorithm 2, the same sweep for rows split over several warps
 //   k_frontier, k_expand, k_rows, k_advance   Algorithm 2, the live sets L and L' and the stop test (eps_c)
 //   k_scan, k_choose                          Algorithm 1, argmax of Estimate(Merge(M_S', M_v)) (Eq. 2-3)
@@ -56,7 +58,7 @@ __device__ __forceinline__ uint32_t vmax4(uint32_t a, uint32_t b) {
 // case the top bits cannot decide; edges where it can happen are flagged and take the exact path.
 // xt[2w] packs simulations 4w, 4w+1 of the chunk, xt[2w+1] packs 4w+2, 4w+3.  ge = 0xFF in each byte whose
 // simulation is not live.
-__device__ __forceinline__ uint32_t dead_bytes(uint32_t xlo, uint32_t xhi, uint32_t ht, uint32_t K) {
+__device__ __forceinline__ __attribute__((unused)) uint32_t dead_bytes(uint32_t xlo, uint32_t xhi, uint32_t ht, uint32_t K) {
     const uint32_t dlo = (xlo ^ ht) + K;
     const uint32_t dhi = (xhi ^ ht) + K;
     return sign_bytes(dlo, dhi, 0xFDB9u);
@@ -115,10 +117,6 @@ struct WarpStage {
     uint32_t T[32];
 };
 
-// Algorithm 2's inner loops for the out-edges [e0, e1) of row u: every edge (u, v) with v in L is one visit; for
-// the sampled simulations the registers of v are max-merged into acc.  Warp-uniform counters: nL edges with v in L,
-// nTaken of them that can be live (their neighbour row was read).
-
 template <int R>
 __device__ __forceinline__ void reduce_groups(uint32_t (&acc)[Geo<R>::CPL][4]) {
 #pragma unroll
@@ -136,13 +134,12 @@ __device__ __forceinline__ uint64_t in_degree(const DevProb &P, int64_t v) {
 }
 
 struct Stats {
-    unsigned long long visits = 0, bytes = 0, indeg = 0;
+    unsigned long long bytes = 0, indeg = 0;
     unsigned int nchg = 0;
 };
 
 __device__ __forceinline__ void flush_stats(DevCtr *C, Stats &st, int lane) {
     if (lane == 0) {
-        if (st.visits) atomicAdd(&C->visits, st.visits);
         if (st.bytes) atomicAdd(&C->bytes, st.bytes);
         if (st.nchg) atomicAdd(&C->nchg, st.nchg);
         if (st.indeg) atomicAdd(&C->chg_indeg, st.indeg);
@@ -160,6 +157,8 @@ template <int R>
 struct GSlots {
     static constexpr int N = R <= 256 ? 16 : (R == 512 ? 8 : 4);
     static constexpr int kBytesPerWarp = (N + 1) * R;
+    // the sweep kernel: one 32-bit accumulator per simulation and tile for the sparse pairs
+    static constexpr int kPropBytesPerWarp = Geo<R>::NG * 4 * R;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -212,78 +211,158 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *m, uint32_t parity
 // Orders this warp's earlier generic reads of a buffer before bulk copies that overwrite it.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Byte masks of four simulations from four live bits (the low nibble of n): bit k is moved to bit 8k + 7 by one
+// multiply (the shifted copies never overlap, so nothing carries) and prmt replicates each byte's top bit.
+__device__ __forceinline__ uint32_t nibble_bytes(uint32_t n) { return sign_bytes(n * 0x10204080u, 0u, 0xBA98u); }
+
+// The sweep kernel works in tiles of G = Geo<R>::G lanes (16 for R = 256): each tile owns one unit (a light row
+// or a task) at a time, so a warp keeps 32 / G units in flight.  Lane li of a tile holds the 16-simulation chunks
+// li + G * c of the row.
 template <int R>
-__device__ __forceinline__ void scan_range_g(const DevProb &P, int64_t u, int64_t e0, int64_t e1, bool allL,
-                                             const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
-                                             uint32_t (&acc)[Geo<R>::CPL][4], const uint32_t (&xt)[Geo<R>::CPL][8],
-                                             int lane, int g, int li, WarpStage &sw, uint4 *buf, uint4 *own,
-                                             bool &own_loaded, uint32_t &nL, uint32_t &nTaken, uint32_t &phase,
-                                             unsigned int *fault, bool &aborted) {
+__device__ __forceinline__ unsigned tile_mask(int g) {
+    return Geo<R>::G == 32 ? kFull : (((1u << Geo<R>::G) - 1u) << (g * Geo<R>::G));
+}
+
+// Dense edges dlist[d0, d1) of the tile's unit (edges live in many simulations), merged with whole register rows:
+// the tile loads two neighbour rows per round (16 bytes per lane and chunk) when their v is in L, and max-merges
+// them into acc through the edges' live masks (Eq. 4-5, sampled once per run).  Returns the merged rows.
+template <int R>
+__device__ __forceinline__ uint32_t dense_tile(const DevProb &P, int64_t d0, int64_t d1, bool allL,
+                                               const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
+                                               uint32_t (&acc)[Geo<R>::CPL][4], int li) {
     using Gm = Geo<R>;
-    constexpr int N = GSlots<R>::N;
-    for (int64_t base = e0; base < e1; base += 32) {
-        const int64_t e = base + lane;
-        int32_t v = 0;
-        bool inL = false;
-        if (e < e1) {
-            v = __ldg(&P.adj[e]);
-            inL = allL || test_bit(Lcur, v);
-        }
-        uint32_t T = 0;
-        bool ok = false;
-        if (inL) edge_threshold(P, e, v, T, ok);
-        const unsigned mL = __ballot_sync(kFull, inL);
-        const bool take = inL && ok;
-        const unsigned mT = __ballot_sync(kFull, take);
-        nL += __popc(mL);
-        if (mT == 0) continue;
-        if (take) {
-            const int r = __popc(mT & ((1u << lane) - 1u));
-            const uint32_t h =
-                edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
-            const bool tie = test_bit(P.xpfx, (h ^ T) >> kPfxShift);
-            sw.v[r] = v | (tie ? static_cast<int32_t>(0x80000000u) : 0);
-            sw.ht[r] = (h >> kPfxShift) * 0x00010001u;
-            sw.K[r] = (0x8000u - (T >> kPfxShift)) * 0x00010001u;
-            sw.h[r] = h;
-            sw.T[r] = T;
-        }
-        __syncwarp();
-        const int cnt = __popc(mT);
-        nTaken += cnt;
-        for (int i0 = 0; i0 < cnt; i0 += N) {
-            const int nb = min(N, cnt - i0);
-            const bool with_own = own != nullptr && !own_loaded;
-            __syncwarp();
-            fence_async_smem();
-            if (aborted) return;
-            if (lane == 0) mbar_expect(&sw.mbar, static_cast<uint32_t>((nb + (with_own ? 1 : 0)) * R));
-            __syncwarp();
-            if (lane < nb)
-                bulk_g2s(&buf[lane * Gm::CH], Mcur + static_cast<size_t>(sw.v[i0 + lane] & 0x7FFFFFFF) * R, R,
-                         &sw.mbar);
-            if (with_own && lane == 31) bulk_g2s(own, Mcur + static_cast<size_t>(u) * R, R, &sw.mbar);
-            own_loaded = own_loaded || with_own;
-            if (!mbar_wait(&sw.mbar, phase, fault, aborted)) return;
-            phase ^= 1u;
-            for (int sl = g; sl < nb; sl += Gm::NG) {
-                uint4 row[Gm::CPL];
+    constexpr int W = R / 32;
+    uint32_t taken = 0;
+    for (int64_t i = d0; i < d1; i += 2) {
+        uint4 row[2][Gm::CPL];
+        uint32_t msk[2][Gm::CPL];
+        bool in[2];
 #pragma unroll
-                for (int c = 0; c < Gm::CPL; ++c) row[c] = buf[sl * Gm::CH + li + Gm::G * c];
-                const int idx = i0 + sl;
-                if (sw.v[idx] >= 0)
-                    merge_fast<R>(acc, row, xt, sw.ht[idx], sw.K[idx]);
-                else
-                    merge_exact<R>(acc, row, sw.h[idx], sw.T[idx], P.X, li);
+        for (int r = 0; r < 2; ++r) {
+            in[r] = false;
+            int64_t e = 0;
+            int32_t v = 0;
+            if (i + r < d1) {
+                e = static_cast<int64_t>(__ldg(&P.dlist[i + r]));
+                v = __ldg(&P.adj[e]);
+                in[r] = allL || test_bit(Lcur, v);
             }
-            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) {
+                const int ch = li + Gm::G * c;  // 16-simulation chunk: half (ch & 1) of mask word ch / 2
+                row[r][c] = in[r] ? __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(v) * R) + ch)
+                                  : make_uint4(0, 0, 0, 0);
+                msk[r][c] = in[r] ? (__ldg(&P.live[static_cast<size_t>(e) * W + (ch >> 1)]) >> (16 * (ch & 1))) : 0u;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            taken += in[r] ? 1u : 0u;
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) {
+                const uint32_t m = msk[r][c];
+                acc[c][0] = vmax4(acc[c][0], row[r][c].x & nibble_bytes(m & 0xFu));
+                acc[c][1] = vmax4(acc[c][1], row[r][c].y & nibble_bytes((m >> 4) & 0xFu));
+                acc[c][2] = vmax4(acc[c][2], row[r][c].z & nibble_bytes((m >> 8) & 0xFu));
+                acc[c][3] = vmax4(acc[c][3], row[r][c].w & nibble_bytes((m >> 12) & 0xFu));
+            }
         }
     }
+    return taken;
+}
+
+// Sparse pairs [p0, p1) of the tile's unit: for every pair (v, j) with v in L, acc32[j] = max(acc32[j], M_v[j])
+// (the max-merge of Algorithm 2 for one sampled simulation).  Lanes take pairs four at a time, and a pair's
+// register is loaded together with its L bit (and dropped if v is not in L), so one round of dependent loads
+// serves 4 G pairs.  Returns the number of pairs this lane merged.
+template <int R>
+__device__ __forceinline__ uint32_t sparse_tile(const DevProb &P, int64_t p0, int64_t p1, bool allL,
+                                                const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
+                                                uint32_t *acc32, int li) {
+    constexpr int G = Geo<R>::G;
+    uint32_t taken = 0;
+    for (int64_t p = p0 + li; p < p1; p += 4 * G) {
+        int32_t v[4];
+        uint32_t j[4];
+        bool ok[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t q = p + G * k;
+            ok[k] = q < p1;
+            v[k] = ok[k] ? __ldg(&P.pv[q]) : 0;
+            j[k] = ok[k] ? __ldg(&P.pj[q]) : 0u;
+        }
+        uint32_t x[4], lw[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            x[k] = ok[k] ? __ldg(&Mcur[static_cast<size_t>(v[k]) * R + j[k]]) : 0u;
+            lw[k] = (ok[k] && !allL) ? Lcur[v[k] >> 5] : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool in = ok[k] && ((lw[k] >> (v[k] & 31)) & 1u);
+            taken += in ? 1u : 0u;
+            if (in && x[k]) atomicMax(&acc32[j[k]], x[k]);
+        }
+    }
+    return taken;
+}
+
+// Adds the tile's sparse accumulators into acc and clears them.
+template <int R>
+__device__ __forceinline__ void fold_tile(uint32_t (&acc)[Geo<R>::CPL][4], uint32_t *acc32, unsigned tm, int li) {
+    using Gm = Geo<R>;
+    __syncwarp(tm);
+#pragma unroll
+    for (int c = 0; c < Gm::CPL; ++c) {
+        const uint4 *a = reinterpret_cast<const uint4 *>(acc32 + 16 * (li + Gm::G * c));
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint4 q = a[w];
+            acc[c][w] = vmax4(acc[c][w], q.x | (q.y << 8) | (q.z << 16) | (q.w << 24));
+        }
+    }
+    __syncwarp(tm);
+    uint4 *z = reinterpret_cast<uint4 *>(acc32);
+    for (int k = li; k < R / 4; k += Gm::G) z[k] = make_uint4(0, 0, 0, 0);
+    __syncwarp(tm);
+}
+
+// Row u's new registers max(M_u, acc) for a tile (every lane holds its chunks of acc and of the row's own
+// registers in own): written to the next buffer if they changed or the row is in L, and u joins L'.
+template <int R>
+__device__ __forceinline__ void finalize_tile(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4],
+                                              bool anyTaken, bool sync, const uint4 (&own)[Geo<R>::CPL],
+                                              uint8_t *__restrict__ Mnext, uint32_t *__restrict__ Lnext,
+                                              unsigned tm, int li, Stats &st) {
+    using Gm = Geo<R>;
+    if (!anyTaken && !sync) return;
+    bool diff = false;
+    uint4 nw[Gm::CPL];
+#pragma unroll
+    for (int c = 0; c < Gm::CPL; ++c) {
+        const uint4 o = own[c];
+        nw[c] = make_uint4(vmax4(o.x, acc[c][0]), vmax4(o.y, acc[c][1]), vmax4(o.z, acc[c][2]),
+                           vmax4(o.w, acc[c][3]));
+        diff |= (nw[c].x != o.x) | (nw[c].y != o.y) | (nw[c].z != o.z) | (nw[c].w != o.w);
+    }
+    const bool changed = __any_sync(tm, diff);
+    if (changed || sync) {
+        uint4 *dst = reinterpret_cast<uint4 *>(Mnext + static_cast<size_t>(u) * R);
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
+    }
+    if (changed && li == 0) {
+        set_bit(Lnext, u);
+        st.indeg += in_degree(P, u) + 1;
+    }
+    st.nchg += changed ? 1u : 0u;
+    st.bytes += R + ((changed || sync) ? R : 0);
 }
 
 template <int R>
-__device__ __forceinline__ void finalize_row_g(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4],
-                                               bool anyTaken, bool sync, const uint4 *ownp,
+__device__ __forceinline__ void finalize_row_r(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4],
+                                               bool anyTaken, bool sync, const uint4 (&own)[Geo<R>::CPL],
                                                uint8_t *__restrict__ Mnext, uint32_t *__restrict__ Lnext, int lane,
                                                int g, int li, Stats &st) {
     using Gm = Geo<R>;
@@ -293,7 +372,7 @@ __device__ __forceinline__ void finalize_row_g(const DevProb &P, int64_t u, uint
     if (g == 0) {
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) {
-            const uint4 o = ownp[li + Gm::G * c];
+            const uint4 o = own[c];
             nw[c] = make_uint4(vmax4(o.x, acc[c][0]), vmax4(o.y, acc[c][1]), vmax4(o.z, acc[c][2]),
                                vmax4(o.w, acc[c][3]));
             diff |= (nw[c].x != o.x) | (nw[c].y != o.y) | (nw[c].z != o.z) | (nw[c].w != o.w);
@@ -311,6 +390,19 @@ __device__ __forceinline__ void finalize_row_g(const DevProb &P, int64_t u, uint
     }
     st.nchg += changed ? 1u : 0u;
     st.bytes += R + ((changed || sync) ? R : 0);
+}
+
+template <int R>
+__device__ __forceinline__ void finalize_row_g(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4],
+                                               bool anyTaken, bool sync, const uint4 *ownp,
+                                               uint8_t *__restrict__ Mnext, uint32_t *__restrict__ Lnext, int lane,
+                                               int g, int li, Stats &st) {
+    using Gm = Geo<R>;
+    if (!anyTaken && !sync) return;
+    uint4 own[Gm::CPL];
+#pragma unroll
+    for (int c = 0; c < Gm::CPL; ++c) own[c] = g == 0 ? ownp[li + Gm::G * c] : make_uint4(0, 0, 0, 0);
+    finalize_row_r<R>(P, u, acc, anyTaken, sync, own, Mnext, Lnext, lane, g, li, st);
 }
 
 // Work of the current sweep.  A full sweep visits every light row that has out-edges (static list) and every task
@@ -338,16 +430,16 @@ __device__ __forceinline__ SweepWork sweep_work(const DevProb &P, const DevCtr &
     return w;
 }
 
+// Index of sweep unit l in the descriptor arrays: a row id (l < nlight) or a task id.
+__device__ __forceinline__ int64_t unit_id(const SweepWork &W, uint64_t l) {
+    if (l < W.nlight) return W.rows[l];
+    return W.tasks ? static_cast<int64_t>(W.tasks[l - W.nlight]) : static_cast<int64_t>(l - W.nlight);
+}
+
 template <int R>
-__device__ void prop_problem_g(const DevProb &P, uint32_t t, const SweepWork &W, uint64_t cnt, uint64_t first,
-                               uint64_t nworkers, int lane, WarpStage &sw, uint4 *buf, uint32_t &phase,
-                               bool &aborted) {
+__device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W, uint64_t cnt, uint64_t first,
+                               uint64_t nworkers, unsigned tm, int li, uint32_t *acc32) {
     using Gm = Geo<R>;
-    constexpr int N = GSlots<R>::N;
-    const int g = lane / Gm::G, li = lane % Gm::G;
-    uint4 *own = buf + N * Gm::CH;
-    uint32_t xt[Gm::CPL][8];
-    load_xt<R>(P.X, li, xt);
     const bool par = t & 1u;
     const uint8_t *Mcur = par ? P.M1 : P.M0;
     uint8_t *Mnext = par ? P.M0 : P.M1;
@@ -356,51 +448,59 @@ __device__ void prop_problem_g(const DevProb &P, uint32_t t, const SweepWork &W,
     const bool allL = (t == 0);
     const uint64_t tb = thr_bytes(P.model);
     Stats st;
-    for (uint64_t l = first; l < cnt && !aborted; l += nworkers) {
+    // two-stage prefetch over this tile's units: the descriptor of the next unit and the id of the one after it
+    // are loaded while the current unit is processed
+    int64_t id_next = first + nworkers < cnt ? unit_id(W, first + nworkers) : 0;
+    UnitD cur{};
+    if (first < cnt) {
+        const int64_t id0 = unit_id(W, first);
+        cur = first < W.nlight ? P.rdesc[id0] : P.tdesc[id0];
+        cur.pad = static_cast<int32_t>(id0);
+    }
+    for (uint64_t l = first; l < cnt; l += nworkers) {
+        UnitD nxt{};
+        if (l + nworkers < cnt) {
+            nxt = l + nworkers < W.nlight ? P.rdesc[id_next] : P.tdesc[id_next];
+            nxt.pad = static_cast<int32_t>(id_next);
+        }
+        if (l + 2 * nworkers < cnt) id_next = unit_id(W, l + 2 * nworkers);
+        const bool is_row = l < W.nlight;
+        const int64_t u = cur.u;
+        uint4 own[Gm::CPL];
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c)
+            own[c] = is_row ? __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R) + li +
+                                    Gm::G * c)
+                            : make_uint4(0, 0, 0, 0);
         uint32_t acc[Gm::CPL][4];
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c)
 #pragma unroll
             for (int w = 0; w < 4; ++w) acc[c][w] = 0;
-        uint32_t nL = 0, nTaken = 0;
-        bool own_loaded = false;
-        if (l < W.nlight) {
-            const int64_t u = W.rows[l];
-            const int64_t e0 = __ldg(&P.xadj[u]), e1 = __ldg(&P.xadj[u + 1]);
-            const bool sync = test_bit(Lcur, u);
-            scan_range_g<R>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, buf, own, own_loaded, nL,
-                            nTaken, phase, &P.ctr->fault, aborted);
-            reduce_groups<R>(acc);
-            st.visits += static_cast<unsigned long long>(nL) * R;
-            st.bytes += 16 + 4 * static_cast<uint64_t>(e1 - e0) + tb * nL + static_cast<uint64_t>(nTaken) * R;
-            const uint4 *ownp =
-                own_loaded ? own : reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R);
-            finalize_row_g<R>(P, u, acc, nTaken > 0, sync, ownp, Mnext, Lnext, lane, g, li, st);
-            __syncwarp();
-        } else {
-            const int64_t task = W.tasks ? static_cast<int64_t>(W.tasks[l - W.nlight])
-                                         : static_cast<int64_t>(l - W.nlight);
-            const int64_t u = __ldg(&P.task_row[task]);
-            const int64_t e0 = __ldg(&P.xadj[u]) + (task - __ldg(&P.task_off[u])) * kTaskEdges;
-            const int64_t e1 = min(e0 + kTaskEdges, __ldg(&P.xadj[u + 1]));
-            scan_range_g<R>(P, u, e0, e1, allL, Lcur, Mcur, acc, xt, lane, g, li, sw, buf, nullptr, own_loaded,
-                            nL, nTaken, phase, &P.ctr->fault, aborted);
-            reduce_groups<R>(acc);
-            st.visits += static_cast<unsigned long long>(nL) * R;
-            st.bytes += 4 * static_cast<uint64_t>(e1 - e0) + tb * nL + static_cast<uint64_t>(nTaken) * R;
-            if (nTaken > 0) {
-                if (g == 0) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(P.part + static_cast<size_t>(task) * R);
+        uint32_t nPairs = sparse_tile<R>(P, cur.p0, cur.p0 + cur.np, allL, Lcur, Mcur, acc32, li);
+        const uint32_t nTaken = cur.nd > 0 ? dense_tile<R>(P, cur.d0, cur.d0 + cur.nd, allL, Lcur, Mcur, acc, li) : 0u;
+        nPairs = __reduce_add_sync(tm, nPairs);
+        fold_tile<R>(acc, acc32, tm, li);
+        if (li == 0)
+            st.bytes += 32 + 6 * static_cast<uint64_t>(cur.np) + nPairs + (8 + tb) * static_cast<uint64_t>(cur.nd) +
+                        static_cast<uint64_t>(nTaken) * R;
+        const bool any = nPairs + nTaken > 0;
+        if (is_row) {
+            finalize_tile<R>(P, u, acc, any, test_bit(Lcur, u), own, Mnext, Lnext, tm, li, st);
+        } else if (any) {
+            const int64_t task = cur.pad;
+            uint4 *dst = reinterpret_cast<uint4 *>(P.part + static_cast<size_t>(task) * R);
 #pragma unroll
-                    for (int c = 0; c < Gm::CPL; ++c)
-                        dst[li + Gm::G * c] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
-                }
-                if (lane == 0) set_bit(P.part_any, task);
+            for (int c = 0; c < Gm::CPL; ++c)
+                dst[li + Gm::G * c] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+            if (li == 0) {
+                set_bit(P.part_any, task);
                 st.bytes += R;
             }
         }
+        cur = nxt;
     }
-    flush_stats(P.ctr, st, lane);
+    flush_stats(P.ctr, st, li);
 }
 
 // The partial rows of tasks [a, b) (b - a <= 32) that merged something: their part_any bits are consumed and the
@@ -465,16 +565,16 @@ __device__ __forceinline__ uint64_t heavy_count(const DevProb &P, const DevCtr &
 template <int R, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restrict__ probs,
                                                         const int32_t *__restrict__ act, int nact) {
-    __shared__ WarpStage stage[kWarpsPerBlock];
+    using Gm = Geo<R>;
     extern __shared__ __align__(16) uint4 gather_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint4 *buf = gather_smem + static_cast<size_t>(wib) * (GSlots<R>::kBytesPerWarp / 16);
-    if (lane == 0) mbar_init(&stage[wib].mbar);
-    __syncwarp();
-    uint32_t phase = 0;
-    bool aborted = false;
-    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
-    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    const int g = lane / Gm::G, li = lane % Gm::G;
+    const unsigned tm = tile_mask<R>(g);
+    uint32_t *acc32 = reinterpret_cast<uint32_t *>(gather_smem) + (static_cast<size_t>(wib) * Gm::NG + g) * R;
+    for (int k = li; k < R; k += Gm::G) acc32[k] = 0;
+    __syncwarp(tm);
+    const uint64_t worker = (static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib) * Gm::NG + g;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock * Gm::NG;
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
@@ -485,7 +585,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restric
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
         if (first >= cnt) continue;
-        prop_problem_g<R>(P, C.t, W, cnt, first, nworkers, lane, stage[wib], buf, phase, aborted);
+        prop_problem_t<R>(P, C.t, W, cnt, first, nworkers, tm, li, acc32);
     }
 }
 
@@ -821,6 +921,8 @@ __global__ void k_advance(const DevProb *__restrict__ probs, const int32_t *__re
         C.timeout = (!stop && lim) ? 1u : 0u;
         C.res_par = (t + 1) & 1u;
     }
+    // visits of the next sweep (Algorithm 2's work count): every edge (u, v) with v in L_{t+1}, in every simulation
+    if (!C.done) C.visits += (C.chg_indeg - nchg) * static_cast<unsigned long long>(P.R);
     C.full = next_is_listed(P, C) ? 0u : 1u;
     C.nrows[t & 1u] = 0;
     C.ntl[t & 1u] = 0;
@@ -897,6 +999,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                     C.nhb[k] = 0;
                 }
                 if (P.flog_cap > 0) P.flog[0] = P.n;
+                C.visits += static_cast<unsigned long long>(P.m) * static_cast<unsigned long long>(P.R);  // L_0 = V
                 for (int j = 0; j < P.R; ++j) P.MS[j] = 0;
             }
         }
@@ -1315,6 +1418,68 @@ __global__ void __launch_bounds__(kBlock) k_live_masks(const DevProb P) {
     }
 }
 
+// Sweep-unit descriptors of every row (its whole edge range) and every task (its kTaskEdges-edge slice).
+__global__ void __launch_bounds__(kBlock) k_unit_desc(const DevProb P, UnitD *rdesc, UnitD *tdesc) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n + P.n_tasks; i += stride) {
+        int64_t u, e0, e1;
+        if (i < P.n) {
+            u = i;
+            e0 = P.xadj[u];
+            e1 = P.xadj[u + 1];
+        } else {
+            const int64_t task = i - P.n;
+            u = P.task_row[task];
+            e0 = P.xadj[u] + (task - P.task_off[u]) * kTaskEdges;
+            e1 = min(e0 + kTaskEdges, P.xadj[u + 1]);
+        }
+        UnitD d;
+        d.p0 = P.pofs[e0];
+        d.d0 = P.dofs[e0];
+        d.np = static_cast<uint32_t>(P.pofs[e1] - d.p0);
+        d.nd = static_cast<uint32_t>(P.dofs[e1] - d.d0);
+        d.u = static_cast<int32_t>(u);
+        d.pad = 0;
+        (i < P.n ? rdesc[i] : tdesc[i - P.n]) = d;
+    }
+}
+
+// Per edge: its number of live simulations.  An edge live in at most dense_min of them contributes that many
+// pairs, any other edge one entry of the dense list.
+__global__ void __launch_bounds__(kBlock) k_pair_counts(const DevProb P, int32_t *npairs, int32_t *ndense) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < P.m; e += stride) {
+        const uint32_t *lv = P.live + static_cast<size_t>(e) * P.W;
+        int c = 0;
+        for (int k = 0; k < P.W; ++k) c += __popc(lv[k]);
+        const bool dense = c > P.dense_min;
+        npairs[e] = dense ? 0 : c;
+        ndense[e] = dense ? 1 : 0;
+    }
+}
+
+// Writes the pairs of every sparse edge at pofs[e] (simulations in increasing order) and the dense edge ids.
+__global__ void __launch_bounds__(kBlock) k_pair_fill(const DevProb P, int32_t *pv, uint16_t *pj, uint32_t *dlist) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < P.m; e += stride) {
+        const int64_t d0 = P.dofs[e];
+        if (P.dofs[e + 1] != d0) {
+            dlist[d0] = static_cast<uint32_t>(e);
+            continue;
+        }
+        int64_t at = P.pofs[e];
+        const int32_t v = P.adj[e];
+        const uint32_t *lv = P.live + static_cast<size_t>(e) * P.W;
+        for (int k = 0; k < P.W; ++k) {
+            for (uint32_t w = lv[k]; w; w &= w - 1) {
+                pv[at] = v;
+                pj[at] = static_cast<uint16_t>(32 * k + __ffs(w) - 1);
+                ++at;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------------------------
 // Graph preparation: simulation words, in-degree / in-CSR, weighted-cascade thresholds, heavy-row tasks.
 
@@ -1517,7 +1682,7 @@ cudaError_t configure(int device) {
 template <int R, int MINB>
 static void launch_gather(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     static int grid = 0;
-    const int smem = kWarpsPerBlock * GSlots<R>::kBytesPerWarp;
+    const int smem = kWarpsPerBlock * GSlots<R>::kPropBytesPerWarp;
     if (grid == 0) {
         cudaFuncSetAttribute(k_propg<R, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int occ = 0;
@@ -1554,13 +1719,13 @@ static void launch_combines(const DevProb *probs, const int32_t *act, int nact, 
         default: break;                                      \
     }
 
-// Minimum resident blocks per SM of the propagation kernel (register budget); IM_PROP_VARIANT selects 2 or 4
-// instead of the default 3 (all exact alike).
+// Minimum resident blocks per SM of the propagation kernel (register budget); IM_PROP_VARIANT selects 3 or 6
+// instead of the default 4 (all exact alike).
 void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     switch (g_variant) {
-        case 2: IMK_R_SWITCH(R, (launch_gather<RR, 2>(probs, act, nact, s))); return;
-        case 4: IMK_R_SWITCH(R, (launch_gather<RR, 4>(probs, act, nact, s))); return;
-        default: IMK_R_SWITCH(R, (launch_gather<RR, 3>(probs, act, nact, s))); return;
+        case 3: IMK_R_SWITCH(R, (launch_gather<RR, 3>(probs, act, nact, s))); return;
+        case 6: IMK_R_SWITCH(R, (launch_gather<RR, 6>(probs, act, nact, s))); return;
+        default: IMK_R_SWITCH(R, (launch_gather<RR, 4>(probs, act, nact, s))); return;
     }
 }
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
@@ -1616,6 +1781,15 @@ void launch_edge_thresholds(const float *p, int64_t m, uint32_t *T, uint8_t *ok,
 void launch_live_masks(const DevProb &P, cudaStream_t s) {
     IMK_R_SWITCH(P.R, (k_live_masks<RR><<<g_grid_warp, kBlock, 0, s>>>(P)));
 }
+void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
+    k_pair_counts<<<g_grid_block, kBlock, 0, s>>>(P, npairs, ndense);
+}
+void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint32_t *dlist, cudaStream_t s) {
+    k_pair_fill<<<g_grid_block, kBlock, 0, s>>>(P, pv, pj, dlist);
+}
+void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s) {
+    k_unit_desc<<<g_grid_block, kBlock, 0, s>>>(P, rdesc, tdesc);
+}
 void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx, cudaStream_t s) {
     k_words<<<(R + 255) / 256, 256, 0, s>>>(seed, R, X, Y, xpfx);
 }
@@ -1641,11 +1815,12 @@ int64_t scan_block_count(int64_t n) {
     const int64_t per = static_cast<int64_t>(kBlock) * kScanItems;
     return (n + per - 1) / per;
 }
-void launch_exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums, cudaStream_t s) {
+int launch_exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums, cudaStream_t s) {
     const int64_t nb = scan_block_count(n);
     if (nb > 0) k_scan_blocks<<<static_cast<unsigned>(nb), kBlock, 0, s>>>(in, n, out, block_sums);
     k_scan_sums<<<1, 32, 0, s>>>(block_sums, nb, out + n);
     if (nb > 1) k_scan_add<<<g_grid_block, kBlock, 0, s>>>(out, n, block_sums);
+    return 1 + (nb > 0 ? 1 : 0) + (nb > 1 ? 1 : 0);
 }
 
 }  // namespace imk

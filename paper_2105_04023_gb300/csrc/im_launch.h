@@ -29,6 +29,9 @@ void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream
 void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned long long *gsum, cudaStream_t s);
 
 void launch_live_masks(const DevProb &P, cudaStream_t s);
+void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
+void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint32_t *dlist, cudaStream_t s);
+void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s);
 void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx, cudaStream_t s);
 void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s);
 void launch_wc_thresholds(const int32_t *indeg, int64_t n, uint32_t *T, cudaStream_t s);
@@ -38,6 +41,7 @@ void launch_row_tasks(const int64_t *xadj, int64_t n, int32_t *ntask, uint32_t *
 void launch_classes(const int64_t *xadj, const int64_t *task_off, int64_t n, int32_t *task_row, int32_t *light,
                     unsigned int *counts, int32_t *hsmall, int32_t *hbig, cudaStream_t s);
 int64_t scan_block_count(int64_t n);
-void launch_exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums, cudaStream_t s);
+// Returns the number of kernels it launched.
+int launch_exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums, cudaStream_t s);
 
 }  // namespace imk

@@ -8,6 +8,7 @@ Graphs are given as numpy arrays (copied by the library, ``IM_MEM_HOST``) or as 
 from __future__ import annotations
 
 import ctypes
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -100,9 +101,12 @@ class Context:
         if st != 0:
             raise ImError(st, f"cannot create a context on CUDA device {device}")
         self.h = h
+        self._children = weakref.WeakSet()  # servers and sketches, destroyed before the context
 
     def close(self):
         if self.h:
+            for c in list(self._children):
+                c.close()
             self._L.im_ctx_destroy(self.h)
             self.h = None
 
@@ -191,6 +195,7 @@ class Server:
         h = ctypes.c_void_p()
         ctx._check(ctx._L.im_server_create(ctx.h, int(hbm_budget_bytes), int(max_active), ctypes.byref(h)))
         self.h = h
+        ctx._children.add(self)
         self._keep = []
         self._K = {}
 
@@ -254,6 +259,7 @@ class Sketch:
 
     def __init__(self, ctx: Context, h: ctypes.c_void_p, n: int, R: int):
         self.ctx, self.h, self.n, self.R = ctx, h, n, R
+        ctx._children.add(self)
 
     def close(self):
         if self.h:

@@ -15,7 +15,8 @@ constexpr int kTaskEdges = 64;
 constexpr int kBigTasks = 32;        // split rows with more tasks are merged by a whole block
 constexpr int kBfsHeavyDeg = 256;    // search-frontier vertices with more out-edges are split into edge chunks
 constexpr int kBfsChunk = 256;       // out-edges per chunk task of a heavy search-frontier vertex
-constexpr int kExpandHeavyDeg = 1024;  // changed vertices with more in-edges are expanded by the whole grid
+constexpr int kPushChunk = 1024;     // a changed vertex pushes its in-edges in units of at most this many
+constexpr int kCasLimit = 1024;      // compare-and-swap tries of one register-word update before it counts as a fault
 constexpr int kPfxShift = 17;        // sampling words are compared on their top 15 bits first
 
 enum Model : int32_t { kIC = 0, kWC = 1, kPerEdge = 2 };
@@ -37,17 +38,15 @@ struct DevCtr {
     uint32_t t;          // sweep index of the current diffusion
     uint32_t done;       // 1 once the diffusion reached its stop condition
     uint32_t timeout;    // 1 if it hit the sweep limit first
-    uint32_t full;       // the current sweep visits every row (otherwise the listed ones)
+    uint32_t full;       // the current sweep pulls into every row; otherwise L pushes along its in-edges
     uint32_t res_par;    // register buffer (0/1) holding the diffusion's result
     uint32_t nchg;       // vertices whose registers changed in the current sweep (|L'|)
-    uint32_t nchg_list;  // entries written to chg_list (changed vertices with few in-edges)
-    uint32_t nrows[2];   // listed light rows for the sweep of that parity
-    uint32_t nchg_hlist; // entries written to chg_hlist (changed vertices with many in-edges)
-    uint32_t ntl[2];     // listed tasks of split rows for the sweep of that parity
-    uint32_t nhs[2];     // listed split rows with at most kBigTasks tasks
-    uint32_t nhb[2];     // listed split rows with more tasks
-    uint32_t fault;      // a bulk copy into shared memory did not complete within the wait limit
-    unsigned long long chg_indeg;     // sum over changed vertices of (in-degree + 1): cost of listing the next rows
+    uint32_t nchg_list;  // entries written to chg_list (changed vertices with at most kPushChunk in-edges)
+    uint32_t nchg_hc;    // entries written to chg_hc (chunks of the changed vertices with more)
+    uint32_t npush_l;    // chg_list / chg_hc entries the current push sweep works on
+    uint32_t npush_h;
+    uint32_t fault;      // bit 0: a bulk copy did not complete in time; bit 1: a register update kept failing
+    unsigned long long chg_indeg;     // sum over changed vertices of (in-degree + 1): work of pushing from them
     unsigned long long visits;        // edge-simulation visits, running total
     unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total
     unsigned long long sweeps_total;  // sweeps, running total
@@ -73,6 +72,7 @@ struct DevProb {
     const int32_t *adj;
     const int64_t *xadj_in;    // in-CSR, used to list the rows a changed vertex feeds
     const int32_t *adj_in;
+    const uint32_t *ein;       // per in-edge: its index in the out-CSR
     const uint32_t *heavy;     // bit per row: out-degree > kHeavyDeg
     const int64_t *task_off;   // n+1: first task of each row (tasks only for heavy rows)
     const int32_t *task_row;   // per task: its row
@@ -97,13 +97,8 @@ struct DevProb {
     uint8_t *part;             // n_tasks x R partial maxima of heavy-row tasks
     uint32_t *part_any;        // bit per task: the task merged at least one neighbour
     uint32_t *Lb0, *Lb1;       // frontier bits: vertices changed in the previous sweep
-    uint8_t *mark8;            // byte per row (padded to 32): row is visited by the next sweep
-    int32_t *chg_list;         // compacted changed vertices with few in-edges
-    int32_t *chg_hlist;        // compacted changed vertices with many in-edges
-    int32_t *rows0, *rows1;    // light rows of the sweep of that parity
-    int32_t *tl0, *tl1;        // tasks of the marked split rows, by parity
-    int32_t *hsl0, *hsl1;      // marked split rows (few tasks), by parity
-    int32_t *hbl0, *hbl1;      // marked split rows (many tasks), by parity
+    int32_t *chg_list;         // compacted changed vertices with at most kPushChunk in-edges
+    uint64_t *chg_hc;          // (chunk << 32) | v for the changed vertices with more in-edges
     uint32_t *live;            // m x W: edge e is live in simulation j (Eq. 4-5 evaluated once per run)
     // Sparse form of the sampled edges.  An edge live in at most dense_min simulations contributes one pair
     // (target v, simulation j) per live simulation, pairs in edge order; an edge live in more is a dense edge,
@@ -113,6 +108,12 @@ struct DevProb {
     const int32_t *pv;         // per pair: target vertex
     const uint16_t *pj;        // per pair: simulation
     const uint32_t *dlist;     // dense edge ids, in edge order
+    // the same pairs and dense edges by target: per in-edge of the in-CSR
+    const int64_t *ipofs;      // m+1: in-pairs before each in-edge
+    const int64_t *idofs;      // m+1: dense in-edges before each in-edge
+    const int32_t *iu;         // per in-pair: source vertex
+    const uint16_t *ij;        // per in-pair: simulation
+    const uint32_t *idlist;    // dense in-edges (in-CSR indices), in in-CSR order
     const UnitD *rdesc;        // n: sweep unit of each row (used for light rows)
     const UnitD *tdesc;        // n_tasks: sweep unit of each task
     int32_t dense_min;

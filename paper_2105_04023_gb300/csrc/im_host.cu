@@ -128,6 +128,7 @@ struct GraphDev {
     int32_t ic_ok = 0;
     int64_t *xadj_in = nullptr;
     int32_t *adj_in = nullptr;
+    uint32_t *ein = nullptr;  // per in-edge: its index in the out-CSR
     uint32_t *T_vert = nullptr;
     uint32_t *T_edge = nullptr;
     uint8_t *ok_edge = nullptr;
@@ -220,9 +221,6 @@ std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
     ctx->launches += launch_exclusive_scan(indeg, n, G->xadj_in, bsums, s);
     unsigned long long *cursor = mem.alloc<unsigned long long>(n);
     ck(cudaMemcpyAsync(cursor, G->xadj_in, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s), "copy cursor");
-    G->adj_in = mem.alloc<int32_t>(m);
-    launch_transpose_fill(G->xadj, G->adj, n, cursor, G->adj_in, s);
-    ctx->launches += 2;
     if (g->model == IM_WC) {
         G->T_vert = mem.alloc<uint32_t>(n);
         launch_wc_thresholds(indeg, n, G->T_vert, s);
@@ -242,6 +240,11 @@ std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
     launch_row_tasks(G->xadj, n, ntask, G->heavy, s);
     G->task_off = mem.alloc<int64_t>(n + 1);
     ctx->launches += 1 + launch_exclusive_scan(ntask, n, G->task_off, bsums, s);
+    // in-CSR, with the split-row task holding each in-edge
+    G->adj_in = mem.alloc<int32_t>(m);
+    G->ein = mem.alloc<uint32_t>(m);
+    launch_transpose_fill(G->xadj, G->adj, n, cursor, G->adj_in, G->ein, s);
+    ctx->launches += 2;
     int64_t h_tasks = 0;
     unsigned int h_flags[4] = {0, 0, 0, 0};
     ck(cudaMemcpyAsync(&h_tasks, G->task_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "read tasks");
@@ -337,9 +340,11 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     d.rdesc = rdesc;
     d.tdesc = tdesc;
     if (m == 0) {
-        d.pv = mem.alloc<int32_t>(1);
-        d.pj = mem.alloc<uint16_t>(1);
-        d.dlist = mem.alloc<uint32_t>(1);
+        d.pv = d.iu = mem.alloc<int32_t>(1);
+        d.pj = d.ij = mem.alloc<uint16_t>(1);
+        d.dlist = d.idlist = mem.alloc<uint32_t>(1);
+        d.ipofs = pofs;
+        d.idofs = dofs;
         return;
     }
     launch_live_masks(d, s);
@@ -367,6 +372,28 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     d.dlist = dlist;
     P.npairs = tot[0];
     P.ndense = tot[1];
+    // the same pairs and dense edges in in-CSR order, for push sweeps
+    int64_t *ipofs = mem.alloc<int64_t>(m + 1);
+    int64_t *idofs = mem.alloc<int64_t>(m + 1);
+    np = mem.alloc<int32_t>(m);
+    nd = mem.alloc<int32_t>(m);
+    bsums = mem.alloc<int64_t>(scan_block_count(m) + 1);
+    launch_inpair_counts(d, np, nd, s);
+    ctx->launches += 1 + launch_exclusive_scan(np, m, ipofs, bsums, s);
+    ctx->launches += launch_exclusive_scan(nd, m, idofs, bsums, s);
+    mem.release(np);
+    mem.release(nd);
+    mem.release(bsums);
+    d.ipofs = ipofs;
+    d.idofs = idofs;
+    int32_t *iu = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
+    uint16_t *ij = mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
+    uint32_t *idlist = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
+    launch_inpair_fill(d, iu, ij, idlist, s);
+    ctx->launches += 1;
+    d.iu = iu;
+    d.ij = ij;
+    d.idlist = idlist;
 }
 
 std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const im_params &prm, bool greedy) {
@@ -386,6 +413,7 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     d.adj = g.adj;
     d.xadj_in = g.xadj_in;
     d.adj_in = g.adj_in;
+    d.ein = g.ein;
     d.heavy = g.heavy;
     d.task_off = g.task_off;
     d.task_row = g.task_row;
@@ -419,17 +447,9 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     const int64_t words = (n + 31) / 32;
     d.Lb0 = mem.alloc<uint32_t>(words, true);
     d.Lb1 = mem.alloc<uint32_t>(words, true);
-    d.mark8 = mem.alloc<uint8_t>(32 * words, true);
     d.chg_list = mem.alloc<int32_t>(n);
-    d.chg_hlist = mem.alloc<int32_t>(n);
-    d.rows0 = mem.alloc<int32_t>(n);
-    d.rows1 = mem.alloc<int32_t>(n);
-    d.tl0 = mem.alloc<int32_t>(std::max<int64_t>(g.n_tasks, 1));
-    d.tl1 = mem.alloc<int32_t>(std::max<int64_t>(g.n_tasks, 1));
-    d.hsl0 = mem.alloc<int32_t>(std::max<int64_t>(g.n_hsmall, 1));
-    d.hsl1 = mem.alloc<int32_t>(std::max<int64_t>(g.n_hsmall, 1));
-    d.hbl0 = mem.alloc<int32_t>(std::max<int64_t>(g.n_hbig, 1));
-    d.hbl1 = mem.alloc<int32_t>(std::max<int64_t>(g.n_hbig, 1));
+    // chunks of changed vertices with more than kPushChunk in-edges: ceil(d / 1024) <= d / 512 for d > 1024
+    d.chg_hc = mem.alloc<uint64_t>(static_cast<size_t>(g.m / 512 + 1));
     d.MS = mem.alloc<uint8_t>(R, true);
     const int64_t ms = prm.max_sweeps > 0 ? prm.max_sweeps : n + 2;
     d.max_sweeps = static_cast<uint32_t>(std::min<int64_t>(ms, 0x7FFFFFFF));
@@ -586,10 +606,8 @@ struct Engine {
                 for (int c = 0; c < chunk; ++c) {
                     timed_prop(byR);
                     launch_frontier(d_probs, dptr(all), all.count, s);
-                    launch_expand(d_probs, dptr(all), all.count, s);
-                    launch_rows(d_probs, dptr(all), all.count, s);
                     launch_advance(d_probs, dptr(all), all.count, s);
-                    ctx->launches += 4;
+                    ctx->launches += 2;
                 }
             });
         });
@@ -744,7 +762,8 @@ struct Engine {
             Prob &P = *probs[i];
             if (P.phase == Prob::kDone) continue;
             if (P.last.fault) {
-                problem_error(P, IM_ECUDA, "a bulk copy into shared memory did not complete");
+                problem_error(P, IM_ECUDA, (P.last.fault & 1u) ? "a bulk copy into shared memory did not complete"
+                                                                : "a register update did not settle");
             } else if (P.phase == Prob::kSweep && P.last.done) {
                 if (P.last.timeout)
                     problem_error(P, IM_ETIMEOUT, "diffusion exceeded max_sweeps");
@@ -1088,19 +1107,19 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     b += r(4 * R) * 2 + r(4 * 1024);                         // X, Y, prefix bitmap
     b += r(n * R) * 2;                                       // register buffers
     b += r(nt * R) + r(4 * (static_cast<uint64_t>(g.n_tasks) / 32 + 1));  // partial rows, their bits
-    b += r(4 * words) * 2 + r(32 * words);                   // live-set bits, row marks
-    b += r(4 * n) * 4;                                       // changed lists, row lists
-    b += r(4 * nt) * 2 + r(4 * std::max<int64_t>(g.n_hsmall, 1)) * 2 + r(4 * std::max<int64_t>(g.n_hbig, 1)) * 2;
+    b += r(4 * words) * 2;                                   // L bits
+    b += r(4 * n) + r(8 * (static_cast<uint64_t>(g.m) / 512 + 1));  // changed lists
     b += r(R) + r(8 * 4096);                                 // M_S', frontier log
     b += r(4 * n * W) * 3 + r(4 * words) * 2 + r(4 * n) * 2;  // reach bits, frontier bits, seed set, light lists
     b += r(8 * (static_cast<uint64_t>(g.m) / 128 + 1)) * 2;  // heavy chunk-task lists
     const uint64_t m1 = std::max<uint64_t>(static_cast<uint64_t>(g.m), 1);
     b += r(4 * W * m1);                                      // live-simulation masks of the edges
-    b += r(8 * (m1 + 1)) * 2;                                // pair and dense-edge offsets
+    b += r(8 * (m1 + 1)) * 4;                                // pair and dense-edge offsets, out- and in-CSR order
     b += r(sizeof(UnitD) * std::max<uint64_t>(n, 1)) + r(sizeof(UnitD) * nt);  // sweep-unit descriptors
     // pairs: at most dense_min per edge (6 bytes each), dense edges 4 bytes; the counts and scan sums of the
     // preparation are freed before the pairs are allocated, and are smaller
-    b += r(6 * m1 * static_cast<uint64_t>(dense_min_for(prm.R))) + r(4 * m1);
+    const uint64_t pmax = m1 * static_cast<uint64_t>(dense_min_for(prm.R));
+    b += (r(4 * pmax) + r(2 * pmax) + r(4 * m1)) * 2;
     b += r(4 * static_cast<uint64_t>(prm.K)) * 2;            // step records
     return b;
 }
@@ -1311,7 +1330,7 @@ im_status im_server_step(im_server *srv, int32_t *active_out, int32_t *queued_ou
             if (srv->used + est > srv->budget) break;
             srv->queue.pop_front();
             Q.P = make_prob(ctx, srv->graphs[static_cast<size_t>(Q.gid)], Q.prm, true);
-            Q.bytes = Q.P->mem->bytes;
+            Q.bytes = est;  // the reservation: the query's allocations stay within it
             srv->used += Q.bytes;
             const size_t slot = srv->free_slots.back();
             srv->free_slots.pop_back();

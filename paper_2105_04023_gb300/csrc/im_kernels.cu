@@ -11,7 +11,7 @@
 //                 per run (k_live_masks) and kept as (target, simulation) pairs for edges live in few simulations
 //                 (k_pair_counts, k_pair_fill), the hashed test runs in the sweep for the other edges
 //   k_combine     Algorithm 2, the same sweep for rows split over several warps
-//   k_frontier, k_expand, k_rows, k_advance   Algorithm 2, the live sets L and L' and the stop test (eps_c)
+//   k_frontier, k_advance   Algorithm 2, the live sets L and L' (and the copy a push sweep needs), the stop test
 //   k_scan, k_choose                          Algorithm 1, argmax of Estimate(Merge(M_S', M_v)) (Eq. 2-3)
 //   k_bfs_*                                   Algorithm 1, reachability set of S in every simulation, sigma
 //   k_merge                                   Algorithm 1, M_S' <- Merge(M_S', M_s)
@@ -405,35 +405,23 @@ __device__ __forceinline__ void finalize_row_g(const DevProb &P, int64_t u, uint
     finalize_row_r<R>(P, u, acc, anyTaken, sync, own, Mnext, Lnext, lane, g, li, st);
 }
 
-// Work of the current sweep.  A full sweep visits every light row that has out-edges (static list) and every task
-// of every heavy row; a listed sweep visits the rows and tasks that k_rows listed for it.
+// Work of a full sweep: every light row that has out-edges (static list) and every task of every split row.
 struct SweepWork {
     uint64_t nlight, ntask;
     const int32_t *rows;
-    const int32_t *tasks;  // nullptr: task ids 0 .. n_tasks-1
 };
 
-__device__ __forceinline__ SweepWork sweep_work(const DevProb &P, const DevCtr &C) {
+__device__ __forceinline__ SweepWork sweep_work(const DevProb &P) {
     SweepWork w;
-    const uint32_t p = C.t & 1u;
-    if (C.full) {
-        w.nlight = static_cast<uint64_t>(P.n_light);
-        w.ntask = static_cast<uint64_t>(P.n_tasks);
-        w.rows = P.light_list;
-        w.tasks = nullptr;
-    } else {
-        w.nlight = C.nrows[p];
-        w.ntask = C.ntl[p];
-        w.rows = p ? P.rows1 : P.rows0;
-        w.tasks = p ? P.tl1 : P.tl0;
-    }
+    w.nlight = static_cast<uint64_t>(P.n_light);
+    w.ntask = static_cast<uint64_t>(P.n_tasks);
+    w.rows = P.light_list;
     return w;
 }
 
 // Index of sweep unit l in the descriptor arrays: a row id (l < nlight) or a task id.
 __device__ __forceinline__ int64_t unit_id(const SweepWork &W, uint64_t l) {
-    if (l < W.nlight) return W.rows[l];
-    return W.tasks ? static_cast<int64_t>(W.tasks[l - W.nlight]) : static_cast<int64_t>(l - W.nlight);
+    return l < W.nlight ? static_cast<int64_t>(W.rows[l]) : static_cast<int64_t>(l - W.nlight);
 }
 
 template <int R>
@@ -549,18 +537,134 @@ __device__ __forceinline__ bool merge_partials(const DevProb &P, int64_t a, int6
     return true;
 }
 
-// Heavy rows of the current sweep with at most kBigTasks tasks (one warp each) or more (one block each).
+// Split rows of a full sweep with at most kBigTasks tasks (one warp each) or more (one block each); a push sweep
+// has none.
 __device__ __forceinline__ uint64_t heavy_count(const DevProb &P, const DevCtr &C, bool big, const int32_t *&list) {
-    const uint32_t p = C.t & 1u;
-    if (C.full) {
-        list = big ? P.hbig : P.hsmall;
-        return static_cast<uint64_t>(big ? P.n_hbig : P.n_hsmall);
-    }
-    list = big ? (p ? P.hbl1 : P.hbl0) : (p ? P.hsl1 : P.hsl0);
-    return big ? C.nhb[p] : C.nhs[p];
+    list = big ? P.hbig : P.hsmall;
+    if (!C.full) return 0;
+    return static_cast<uint64_t>(big ? P.n_hbig : P.n_hsmall);
 }
 
 }  // namespace
+
+// Bytewise max-merge of cand into the register word at w, lock-free, starting from the value old read there:
+// returns whether the word grew.  A failed compare-and-swap means another thread grew the word first; words only
+// grow (four registers of at most 33 values), so the retries are few; after kCasLimit the fault flag is raised.
+__device__ __forceinline__ bool word_max(uint32_t *w, uint32_t old, uint32_t cand, unsigned int *fault) {
+    for (int it = 0; it < kCasLimit; ++it) {
+        const uint32_t nw = vmax4(old, cand);
+        if (nw == old) return false;
+        const uint32_t prev = atomicCAS(w, old, nw);
+        if (prev == old) return true;
+        old = prev;
+    }
+    atomicOr(fault, 2u);
+    return false;
+}
+
+// u joins L' (the first thread to set its bit counts it).
+__device__ __forceinline__ void mark_changed(const DevProb &P, uint32_t *Lnext, int64_t u, Stats &st) {
+    const uint32_t bit = 1u << (u & 31);
+    if (__ldcg(&Lnext[u >> 5]) & bit) return;
+    if (!(atomicOr(&Lnext[u >> 5], bit) & bit)) {
+        st.nchg += 1;
+        st.indeg += in_degree(P, u) + 1;
+    }
+}
+
+// A push sweep (Algorithm 2 with a small L, in the other direction): every changed vertex v merges M_v into the
+// rows of its in-neighbours u, M'_u[j] = max(M'_u[j], M_v[j]) for every sampled (u, v, j).  The next buffer already
+// holds M_u for every row (rows of L were copied after the previous sweep), so it is updated in place with
+// compare-and-swap; reads come from the current buffer only (Jacobi).  A tile takes one unit: a changed vertex,
+// or a chunk of kPushChunk in-edges of one with more; its row of M_v is staged in shared memory.
+template <int R>
+__device__ void push_problem_t(const DevProb &P, uint32_t t, uint64_t cnt, uint64_t first, uint64_t nworkers,
+                               unsigned tm, int li, uint32_t *tile_smem) {
+    using Gm = Geo<R>;
+    constexpr int G = Gm::G;
+    constexpr int W = R / 32;
+    const bool par = t & 1u;
+    const uint8_t *Mcur = par ? P.M1 : P.M0;
+    uint8_t *Mnext = par ? P.M0 : P.M1;
+    uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
+    uint8_t *srow = reinterpret_cast<uint8_t *>(tile_smem);
+    unsigned int *fault = &P.ctr->fault;
+    const uint64_t nl = P.ctr->npush_l;
+    Stats st;
+    for (uint64_t l = first; l < cnt; l += nworkers) {
+        int64_t v, k0, k1;
+        if (l < nl) {
+            v = P.chg_list[l];
+            k0 = __ldg(&P.xadj_in[v]);
+            k1 = __ldg(&P.xadj_in[v + 1]);
+        } else {
+            const uint64_t h = P.chg_hc[l - nl];
+            v = static_cast<int64_t>(static_cast<uint32_t>(h));
+            k0 = __ldg(&P.xadj_in[v]) + static_cast<int64_t>(h >> 32) * kPushChunk;
+            const int64_t end = __ldg(&P.xadj_in[v + 1]);
+            k1 = end - k0 > kPushChunk ? k0 + kPushChunk : end;
+        }
+        const int64_t p0 = __ldg(&P.ipofs[k0]), p1 = __ldg(&P.ipofs[k1]);
+        const int64_t d0 = __ldg(&P.idofs[k0]), d1 = __ldg(&P.idofs[k1]);
+        uint4 rowc[Gm::CPL];
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c) {
+            rowc[c] = __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(v) * R) + li + G * c);
+            reinterpret_cast<uint4 *>(srow)[li + G * c] = rowc[c];
+        }
+        __syncwarp(tm);
+        for (int64_t p = p0 + li; p < p1; p += 4 * G) {
+            uint32_t *addr[4];
+            uint32_t cand[4], old[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t q = p + G * k;
+                cand[k] = 0;
+                addr[k] = nullptr;
+                if (q < p1) {
+                    const int64_t u = __ldg(&P.iu[q]);
+                    const uint32_t j = __ldg(&P.ij[q]);
+                    cand[k] = static_cast<uint32_t>(srow[j]) << (8 * (j & 3));
+                    addr[k] = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u) * R + (j & ~3u));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) old[k] = cand[k] ? __ldcg(addr[k]) : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (cand[k] && word_max(addr[k], old[k], cand[k], fault)) {
+                    const int64_t u = (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R;
+                    mark_changed(P, Lnext, u, st);
+                }
+            }
+        }
+        for (int64_t d = d0; d < d1; ++d) {
+            const uint32_t k = __ldg(&P.idlist[d]);
+            const int64_t u = __ldg(&P.adj_in[k]);
+            const uint32_t e = __ldg(&P.ein[k]);
+            bool grew = false;
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) {
+                const int ch = li + G * c;
+                const uint32_t m = __ldg(&P.live[static_cast<size_t>(e) * W + (ch >> 1)]) >> (16 * (ch & 1));
+                uint32_t *dst = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u) * R) + 4 * ch;
+                const uint4 o = __ldcg(reinterpret_cast<const uint4 *>(dst));
+                grew |= word_max(dst + 0, o.x, rowc[c].x & nibble_bytes(m & 0xFu), fault);
+                grew |= word_max(dst + 1, o.y, rowc[c].y & nibble_bytes((m >> 4) & 0xFu), fault);
+                grew |= word_max(dst + 2, o.z, rowc[c].z & nibble_bytes((m >> 8) & 0xFu), fault);
+                grew |= word_max(dst + 3, o.w, rowc[c].w & nibble_bytes((m >> 12) & 0xFu), fault);
+            }
+            if (__any_sync(tm, grew) && li == 0) mark_changed(P, Lnext, u, st);
+        }
+        if (li == 0)
+            st.bytes += R + 32 + 10 * static_cast<uint64_t>(p1 - p0) + (12 + W * 4 + R) * static_cast<uint64_t>(d1 - d0);
+        __syncwarp(tm);
+    }
+    // rows are marked by any lane
+    if (st.nchg) atomicAdd(&P.ctr->nchg, st.nchg);
+    if (st.indeg) atomicAdd(&P.ctr->chg_indeg, st.indeg);
+    if (st.bytes) atomicAdd(&P.ctr->bytes, st.bytes);
+}
 
 template <int R, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restrict__ probs,
@@ -580,12 +684,15 @@ __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restric
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
         if (C.done) continue;
-        const SweepWork W = sweep_work(P, C);
-        const uint64_t cnt = W.nlight + W.ntask;
+        const SweepWork W = sweep_work(P);
+        const uint64_t cnt = C.full ? W.nlight + W.ntask : static_cast<uint64_t>(C.npush_l) + C.npush_h;
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
         if (first >= cnt) continue;
-        prop_problem_t<R>(P, C.t, W, cnt, first, nworkers, tm, li, acc32);
+        if (C.full)
+            prop_problem_t<R>(P, C.t, W, cnt, first, nworkers, tm, li, acc32);
+        else
+            push_problem_t<R>(P, C.t, cnt, first, nworkers, tm, li, acc32);
     }
 }
 
@@ -758,15 +865,16 @@ __device__ __forceinline__ bool sweep_stops(const DevProb &P, const DevCtr &C) {
     return C.nchg <= P.stop_thr || C.t + 1 >= P.max_sweeps;
 }
 
-// The next sweep visits listed rows when listing them is cheap (few in-edges into the changed vertices).
-__device__ __forceinline__ bool next_is_listed(const DevProb &P, const DevCtr &C) {
+// The next sweep pushes from L' when that is cheap (few in-edges into the changed vertices).
+__device__ __forceinline__ bool next_is_push(const DevProb &P, const DevCtr &C) {
     return C.chg_indeg <= P.list_thr;
 }
 
 }  // namespace
 
-// After sweep t: clear L_t's bits (the buffer L_{t+2} will be written to) and, when the next sweep is a listed one,
-// compact L_{t+1} into the changed-vertex lists (split by in-degree).
+// After sweep t: clear L_t's bits (the buffer L_{t+2} will be written to) and, when the next sweep is a push
+// sweep, compact L_{t+1} into the changed-vertex lists (whole vertices, or kPushChunk-in-edge chunks of those
+// with more) and copy each changed row into the buffer the next sweep writes, so that it holds every row.
 __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__ probs,
                                                      const int32_t *__restrict__ act, int nact) {
     uint64_t base = 0;
@@ -774,10 +882,12 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
         if (C.done || sweep_stops(P, C)) continue;
-        const bool list_next = next_is_listed(P, C);
+        const bool push_next = next_is_push(P, C);
         const bool par = C.t & 1u;
         uint32_t *Lold = par ? P.Lb1 : P.Lb0;
         const uint32_t *Lnew = par ? P.Lb0 : P.Lb1;
+        const uint8_t *Mw = par ? P.M0 : P.M1;  // written by sweep t
+        uint8_t *Mr = par ? P.M1 : P.M0;        // read by sweep t, written by sweep t + 1
         const int64_t words = (P.n + 31) >> 5;
         const uint64_t chunks = (words + kBlock - 1) / kBlock;
         const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
@@ -789,115 +899,24 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
                 Lold[i] = 0;
                 w = Lnew[i];
             }
-            if (list_next) {
+            if (push_next) {
                 uint32_t wh = 0;
-                for (uint32_t x = w; x;) {
-                    const int b = __ffs(x) - 1;
-                    x &= x - 1;
-                    if (in_degree(P, i * 32 + b) > kExpandHeavyDeg) wh |= 1u << b;
+                for (uint32_t x = w; x; x &= x - 1) {
+                    const int64_t v = i * 32 + __ffs(x) - 1;
+                    const uint4 *src = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R);
+                    uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R);
+#pragma unroll 4
+                    for (int k = 0; k < P.R / 16; ++k) dst[k] = src[k];
+                    const uint64_t d = in_degree(P, v);
+                    if (d > kPushChunk) {
+                        wh |= 1u << (__ffs(x) - 1);
+                        const uint32_t nt = static_cast<uint32_t>((d + kPushChunk - 1) / kPushChunk);
+                        const uint32_t at = atomicAdd(&P.ctr->nchg_hc, nt);
+                        for (uint32_t c = 0; c < nt; ++c)
+                            P.chg_hc[at + c] = (static_cast<uint64_t>(c) << 32) | static_cast<uint32_t>(v);
+                    }
                 }
                 block_append_bits(w & ~wh, i, P.chg_list, &P.ctr->nchg_list);
-                if (__syncthreads_or(wh != 0)) block_append_bits(wh, i, P.chg_hlist, &P.ctr->nchg_hlist);
-            }
-        }
-    }
-}
-
-// Marks every row that must be visited in the next sweep: the changed vertices themselves and their in-neighbours
-// (plain byte stores: a row marked twice is the same mark).
-__global__ void __launch_bounds__(kBlock) k_expand(const DevProb *__restrict__ probs,
-                                                   const int32_t *__restrict__ act, int nact) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    {
-        const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
-        const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
-        uint64_t base = 0;
-        for (int q = 0; q < nact; ++q) {
-            const DevProb &P = probs[act[q]];
-            const DevCtr &C = *P.ctr;
-            if (C.done || sweep_stops(P, C) || !next_is_listed(P, C)) continue;
-            const uint64_t cnt = C.nchg_list;
-            const uint64_t first = first_owned(worker, nworkers, base);
-            base += cnt;
-            for (uint64_t l = first; l < cnt; l += nworkers) {
-                const int32_t v = P.chg_list[l];
-                if (lane == 0) P.mark8[v] = 1;
-                const int64_t e0 = __ldg(&P.xadj_in[v]), e1 = __ldg(&P.xadj_in[v + 1]);
-                for (int64_t e = e0 + lane; e < e1; e += 32) P.mark8[__ldg(&P.adj_in[e])] = 1;
-            }
-        }
-    }
-    {
-        const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-        const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-        uint64_t base = 0;
-        for (int q = 0; q < nact; ++q) {
-            const DevProb &P = probs[act[q]];
-            const DevCtr &C = *P.ctr;
-            if (C.done || sweep_stops(P, C) || !next_is_listed(P, C)) continue;
-            for (uint32_t i = 0; i < C.nchg_hlist; ++i) {
-                const int32_t v = P.chg_hlist[i];
-                const int64_t e0 = P.xadj_in[v], e1 = P.xadj_in[v + 1];
-                const uint64_t cnt = static_cast<uint64_t>(e1 - e0) + 1;
-                const uint64_t first = first_owned(tid, nthreads, base);
-                base += cnt;
-                for (uint64_t l = first; l < cnt; l += nthreads)
-                    P.mark8[l + 1 == cnt ? v : __ldg(&P.adj_in[e0 + l])] = 1;
-            }
-        }
-    }
-}
-
-// Compacts the marked rows into the work lists of the next sweep and clears every mark: light rows go to the row
-// list, split rows to one of the two split-row lists and their tasks to the task list.
-__global__ void __launch_bounds__(kBlock) k_rows(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
-                                                 int nact) {
-    uint64_t base = 0;
-    for (int q = 0; q < nact; ++q) {
-        const DevProb &P = probs[act[q]];
-        const DevCtr &C = *P.ctr;
-        if (C.done || sweep_stops(P, C) || !next_is_listed(P, C)) continue;
-        const uint32_t np = (C.t + 1) & 1u;
-        int32_t *rows = np ? P.rows1 : P.rows0;
-        int32_t *tl = np ? P.tl1 : P.tl0;
-        int32_t *hsl = np ? P.hsl1 : P.hsl0;
-        int32_t *hbl = np ? P.hbl1 : P.hbl0;
-        const int64_t words = (P.n + 31) >> 5;
-        const uint64_t chunks = (words + kBlock - 1) / kBlock;
-        const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
-        base += chunks;
-        for (uint64_t ch = first; ch < chunks; ch += gridDim.x) {
-            const int64_t i = static_cast<int64_t>(ch) * kBlock + threadIdx.x;
-            uint32_t w = 0, hv = 0;
-            if (i < words) {
-                uint4 *mp = reinterpret_cast<uint4 *>(P.mark8 + 32 * i);
-                const uint4 a = mp[0], b = mp[1];
-                const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if ((x[k] >> (8 * j)) & 0xFFu) w |= 1u << (4 * k + j);
-                if (w) {
-                    mp[0] = make_uint4(0, 0, 0, 0);
-                    mp[1] = make_uint4(0, 0, 0, 0);
-                }
-                hv = w & P.heavy[i];
-                w &= ~hv;
-            }
-            block_append_bits(w, i, rows, &P.ctr->nrows[np]);
-            while (hv) {
-                const int b = __ffs(hv) - 1;
-                hv &= hv - 1;
-                const int32_t u = static_cast<int32_t>(i * 32 + b);
-                const int64_t t0 = P.task_off[u], t1 = P.task_off[u + 1];
-                const bool big = t1 - t0 > kBigTasks;
-                if (big)
-                    hbl[atomicAdd(&P.ctr->nhb[np], 1u)] = u;
-                else
-                    hsl[atomicAdd(&P.ctr->nhs[np], 1u)] = u;
-                const uint32_t pos = atomicAdd(&P.ctr->ntl[np], static_cast<uint32_t>(t1 - t0));
-                for (int64_t k = t0; k < t1; ++k) tl[pos + (k - t0)] = static_cast<int32_t>(k);
             }
         }
     }
@@ -923,14 +942,12 @@ __global__ void k_advance(const DevProb *__restrict__ probs, const int32_t *__re
     }
     // visits of the next sweep (Algorithm 2's work count): every edge (u, v) with v in L_{t+1}, in every simulation
     if (!C.done) C.visits += (C.chg_indeg - nchg) * static_cast<unsigned long long>(P.R);
-    C.full = next_is_listed(P, C) ? 0u : 1u;
-    C.nrows[t & 1u] = 0;
-    C.ntl[t & 1u] = 0;
-    C.nhs[t & 1u] = 0;
-    C.nhb[t & 1u] = 0;
+    C.full = next_is_push(P, C) ? 0u : 1u;
+    C.npush_l = C.full ? 0u : C.nchg_list;
+    C.npush_h = C.full ? 0u : C.nchg_hc;
     C.nchg = 0;
     C.nchg_list = 0;
-    C.nchg_hlist = 0;
+    C.nchg_hc = 0;
     C.chg_indeg = 0;
     C.t = t + 1;
 }
@@ -948,8 +965,8 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
         const uint64_t nchunks = static_cast<uint64_t>(P.n) * CH;
         const int64_t words = (P.n + 31) >> 5;
         const int64_t twords = (P.n_tasks + 31) >> 5;
-        // units: register chunks, then L bits (2 x words), mark bytes (8 x words as 4-byte words), task bits, counters
-        const uint64_t cnt = nchunks + 10 * static_cast<uint64_t>(words) + static_cast<uint64_t>(twords) + 1;
+        // units: register chunks, then L bits (2 x words), task bits, counters
+        const uint64_t cnt = nchunks + 2 * static_cast<uint64_t>(words) + static_cast<uint64_t>(twords) + 1;
         const uint64_t first = first_owned(tid, nthreads, base);
         base += cnt;
         for (uint64_t l = first; l < cnt; l += nthreads) {
@@ -977,10 +994,8 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
             } else if (l < nchunks + 2 * static_cast<uint64_t>(words)) {
                 const uint64_t k = l - nchunks;
                 (k < static_cast<uint64_t>(words) ? P.Lb0 : P.Lb1)[k % words] = 0;
-            } else if (l < nchunks + 10 * static_cast<uint64_t>(words)) {
-                reinterpret_cast<uint32_t *>(P.mark8)[l - nchunks - 2 * static_cast<uint64_t>(words)] = 0;
             } else if (l < cnt - 1) {
-                P.part_any[l - nchunks - 10 * static_cast<uint64_t>(words)] = 0;
+                P.part_any[l - nchunks - 2 * static_cast<uint64_t>(words)] = 0;
             } else {
                 DevCtr &C = *P.ctr;
                 C.t = 0;
@@ -990,14 +1005,10 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 C.res_par = 0;
                 C.nchg = 0;
                 C.nchg_list = 0;
-                C.nchg_hlist = 0;
+                C.nchg_hc = 0;
+                C.npush_l = 0;
+                C.npush_h = 0;
                 C.chg_indeg = 0;
-                for (int k = 0; k < 2; ++k) {
-                    C.nrows[k] = 0;
-                    C.ntl[k] = 0;
-                    C.nhs[k] = 0;
-                    C.nhb[k] = 0;
-                }
                 if (P.flog_cap > 0) P.flog[0] = P.n;
                 C.visits += static_cast<unsigned long long>(P.m) * static_cast<unsigned long long>(P.R);  // L_0 = V
                 for (int j = 0; j < P.R; ++j) P.MS[j] = 0;
@@ -1418,6 +1429,37 @@ __global__ void __launch_bounds__(kBlock) k_live_masks(const DevProb P) {
     }
 }
 
+// The same classification per in-edge k (edge ein[k]): in-pair counts and dense in-edge flags.
+__global__ void __launch_bounds__(kBlock) k_inpair_counts(const DevProb P, int32_t *npairs, int32_t *ndense) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < P.m; k += stride) {
+        const int64_t e = P.ein[k];
+        npairs[k] = static_cast<int32_t>(P.pofs[e + 1] - P.pofs[e]);
+        ndense[k] = P.dofs[e + 1] != P.dofs[e] ? 1 : 0;
+    }
+}
+
+// In-pairs (source u, simulation j) of every sparse in-edge at ipofs[k], and the dense in-edge list.
+__global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t *iu, uint16_t *ij,
+                                                        uint32_t *idlist) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < P.m; k += stride) {
+        const int64_t d0 = P.idofs[k];
+        if (P.idofs[k + 1] != d0) {
+            idlist[d0] = static_cast<uint32_t>(k);
+            continue;
+        }
+        const int64_t e = P.ein[k];
+        const int32_t u = P.adj_in[k];
+        int64_t at = P.ipofs[k];
+        for (int64_t p = P.pofs[e]; p < P.pofs[e + 1]; ++p) {
+            iu[at] = u;
+            ij[at] = P.pj[p];
+            ++at;
+        }
+    }
+}
+
 // Sweep-unit descriptors of every row (its whole edge range) and every task (its kTaskEdges-edge slice).
 __global__ void __launch_bounds__(kBlock) k_unit_desc(const DevProb P, UnitD *rdesc, UnitD *tdesc) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -1517,13 +1559,17 @@ __global__ void k_wc_thresholds(const int32_t *__restrict__ indeg, int64_t n, ui
 }
 
 __global__ void k_transpose_fill(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj, int64_t n,
-                                 unsigned long long *__restrict__ cursor, int32_t *__restrict__ adj_in) {
+                                 unsigned long long *__restrict__ cursor, int32_t *__restrict__ adj_in,
+                                 uint32_t *__restrict__ ein) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     for (int64_t u = warp; u < n; u += nwarps)
-        for (int64_t e = xadj[u] + lane; e < xadj[u + 1]; e += 32)
-            adj_in[atomicAdd(&cursor[adj[e]], 1ull)] = static_cast<int32_t>(u);
+        for (int64_t e = xadj[u] + lane; e < xadj[u + 1]; e += 32) {
+            const unsigned long long at = atomicAdd(&cursor[adj[e]], 1ull);
+            adj_in[at] = static_cast<int32_t>(u);
+            ein[at] = static_cast<uint32_t>(e);
+        }
 }
 
 __global__ void k_row_tasks(const int64_t *__restrict__ xadj, int64_t n, int32_t *__restrict__ ntask,
@@ -1734,12 +1780,6 @@ void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, c
 void launch_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);
 }
-void launch_expand(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    k_expand<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
-}
-void launch_rows(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    k_rows<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);
-}
 void launch_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_advance<<<(nact + 127) / 128, 128, 0, s>>>(probs, act, nact);
 }
@@ -1787,6 +1827,12 @@ void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cuda
 void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint32_t *dlist, cudaStream_t s) {
     k_pair_fill<<<g_grid_block, kBlock, 0, s>>>(P, pv, pj, dlist);
 }
+void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
+    k_inpair_counts<<<g_grid_block, kBlock, 0, s>>>(P, npairs, ndense);
+}
+void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *idlist, cudaStream_t s) {
+    k_inpair_fill<<<g_grid_block, kBlock, 0, s>>>(P, iu, ij, idlist);
+}
 void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s) {
     k_unit_desc<<<g_grid_block, kBlock, 0, s>>>(P, rdesc, tdesc);
 }
@@ -1800,8 +1846,8 @@ void launch_wc_thresholds(const int32_t *indeg, int64_t n, uint32_t *T, cudaStre
     k_wc_thresholds<<<g_grid_block, kBlock, 0, s>>>(indeg, n, T);
 }
 void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, unsigned long long *cursor,
-                           int32_t *adj_in, cudaStream_t s) {
-    k_transpose_fill<<<g_grid_warp, kBlock, 0, s>>>(xadj, adj, n, cursor, adj_in);
+                           int32_t *adj_in, uint32_t *ein, cudaStream_t s) {
+    k_transpose_fill<<<g_grid_warp, kBlock, 0, s>>>(xadj, adj, n, cursor, adj_in, ein);
 }
 void launch_row_tasks(const int64_t *xadj, int64_t n, int32_t *ntask, uint32_t *heavy, cudaStream_t s) {
     k_row_tasks<<<g_grid_block, kBlock, 0, s>>>(xadj, n, ntask, heavy);

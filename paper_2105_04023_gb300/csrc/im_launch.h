@@ -16,8 +16,6 @@ void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_
 void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
-void launch_expand(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
-void launch_rows(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_scan(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t step, cudaStream_t s);
@@ -31,12 +29,14 @@ void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned 
 void launch_live_masks(const DevProb &P, cudaStream_t s);
 void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
 void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint32_t *dlist, cudaStream_t s);
+void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
+void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *idlist, cudaStream_t s);
 void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s);
 void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx, cudaStream_t s);
 void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s);
 void launch_wc_thresholds(const int32_t *indeg, int64_t n, uint32_t *T, cudaStream_t s);
 void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, unsigned long long *cursor,
-                           int32_t *adj_in, cudaStream_t s);
+                           int32_t *adj_in, uint32_t *ein, cudaStream_t s);
 void launch_row_tasks(const int64_t *xadj, int64_t n, int32_t *ntask, uint32_t *heavy, cudaStream_t s);
 void launch_classes(const int64_t *xadj, const int64_t *task_off, int64_t n, int32_t *task_row, int32_t *light,
                     unsigned int *counts, int32_t *hsmall, int32_t *hbig, cudaStream_t s);

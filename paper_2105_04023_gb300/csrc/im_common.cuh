@@ -46,7 +46,7 @@ struct DevCtr {
     uint32_t npush_l;    // chg_list / chg_hc entries the current push sweep works on
     uint32_t npush_h;
     uint32_t fault;      // bit 0: a bulk copy did not complete in time; bit 1: a register update kept failing
-    unsigned long long chg_indeg;     // sum over changed vertices of (in-degree + 1): work of pushing from them
+    unsigned long long chg_indeg;     // in-edges into the vertices changed in the current sweep
     unsigned long long visits;        // edge-simulation visits, running total
     unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total
     unsigned long long sweeps_total;  // sweeps, running total
@@ -113,7 +113,9 @@ struct DevProb {
     const int64_t *idofs;      // m+1: dense in-edges before each in-edge
     const int32_t *iu;         // per in-pair: source vertex
     const uint16_t *ij;        // per in-pair: simulation
-    const uint32_t *idlist;    // dense in-edges (in-CSR indices), in in-CSR order
+    const int32_t *idu;        // per dense in-edge, in in-CSR order: source vertex
+    const uint32_t *ide;       //   and out-CSR edge id
+    const UnitD *vdesc;        // n: push unit of each vertex (in-pairs, dense in-edges)
     const UnitD *rdesc;        // n: sweep unit of each row (used for light rows)
     const UnitD *tdesc;        // n_tasks: sweep unit of each task
     int32_t dense_min;
@@ -127,7 +129,6 @@ struct DevProb {
     uint8_t *MS;               // R bytes: M_S'
     DevCtr *ctr;
     uint32_t stop_thr;         // diffusion stops when |L'| <= stop_thr
-    uint64_t list_thr;         // next sweep lists its rows when chg_indeg <= list_thr, else visits every row
     uint32_t max_sweeps;       // sweep / level limit
     int32_t flog_cap;
     int64_t *flog;             // |L| at the start of each sweep of the current diffusion

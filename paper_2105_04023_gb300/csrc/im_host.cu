@@ -342,7 +342,10 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     if (m == 0) {
         d.pv = d.iu = mem.alloc<int32_t>(1);
         d.pj = d.ij = mem.alloc<uint16_t>(1);
-        d.dlist = d.idlist = mem.alloc<uint32_t>(1);
+        d.dlist = d.ide = mem.alloc<uint32_t>(1);
+        d.idu = mem.alloc<int32_t>(1);
+        UnitD *vd0 = mem.alloc<UnitD>(static_cast<size_t>(std::max<int64_t>(P.G->n, 1)), true);
+        d.vdesc = vd0;
         d.ipofs = pofs;
         d.idofs = dofs;
         return;
@@ -388,12 +391,17 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     d.idofs = idofs;
     int32_t *iu = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
     uint16_t *ij = mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
-    uint32_t *idlist = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
-    launch_inpair_fill(d, iu, ij, idlist, s);
-    ctx->launches += 1;
+    int32_t *idu = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
+    uint32_t *ide = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
+    launch_inpair_fill(d, iu, ij, idu, ide, s);
+    UnitD *vdesc = mem.alloc<UnitD>(static_cast<size_t>(std::max<int64_t>(P.G->n, 1)));
+    launch_vertex_desc(d, vdesc, s);
+    ctx->launches += 2;
     d.iu = iu;
     d.ij = ij;
-    d.idlist = idlist;
+    d.idu = idu;
+    d.ide = ide;
+    d.vdesc = vdesc;
 }
 
 std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const im_params &prm, bool greedy) {
@@ -456,8 +464,6 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     // stop after the first sweep with |L'| <= eps_c * n: the largest integer count satisfying it
     const double thr = static_cast<double>(n) * prm.eps_c;
     d.stop_thr = static_cast<uint32_t>(std::floor(thr));
-    // list the next sweep's rows when marking them costs well under a full visit of every row and edge
-    d.list_thr = static_cast<uint64_t>((g.m + n) / 8);
     P->flog_cap = 4096;
     d.flog_cap = static_cast<int32_t>(P->flog_cap);
     d.flog = mem.alloc<int64_t>(P->flog_cap, true);
@@ -546,8 +552,9 @@ struct Engine {
 
     const int32_t *dptr(const List &l) const { return ctx->d_act + l.off; }
 
-    // One sweep's propagation launches (k_prop, then k_combine for split rows), optionally between two events.
-    void timed_prop(const std::vector<std::pair<int, List>> &byR) {
+    // One sweep's propagation launches (k_prop, then for a sweep that pulls into every row, k_combine for the split
+    // rows), optionally between two events.
+    void timed_prop(const std::vector<std::pair<int, List>> &byR, bool combine) {
         cudaStream_t s = ctx->stream;
         cudaEvent_t a = nullptr, b = nullptr;
         if (ctx->timing) {
@@ -556,12 +563,13 @@ struct Engine {
             ck(cudaEventRecord(a, s), "event");
         }
         for (auto &rl : byR) launch_prop(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
-        for (auto &rl : byR) launch_combine(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
+        if (combine)
+            for (auto &rl : byR) launch_combine(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
         if (ctx->timing) {
             ck(cudaEventRecord(b, s), "event");
             ctx->prop_ev.emplace_back(a, b);
         }
-        ctx->launches += 3 * static_cast<int64_t>(byR.size());  // sweep kernel, two combine kernels
+        ctx->launches += (combine ? 3 : 1) * static_cast<int64_t>(byR.size());  // sweep kernel, two combine kernels
         ctx->prop_launches += static_cast<int64_t>(byR.size());
     }
 
@@ -590,7 +598,9 @@ struct Engine {
         return e;
     }
 
-    void enqueue_sweeps(const std::vector<int32_t> &ids, int chunk) {
+    // chunk sweeps of the listed problems; with first_full, some of them start a diffusion (their sweep 0 pulls into
+    // every row, later sweeps push and have no split rows to combine)
+    void enqueue_sweeps(const std::vector<int32_t> &ids, int chunk, bool first_full) {
         if (ids.empty()) return;
         cudaStream_t s = ctx->stream;
         std::vector<std::pair<int, List>> byR;
@@ -601,10 +611,10 @@ struct Engine {
             if (!sub.empty()) byR.emplace_back(R, add_list(sub));
         }
         const List all = add_list(ids);
-        pending.push_back([this, byR, all, chunk, s]() {
+        pending.push_back([this, byR, all, chunk, first_full, s]() {
             phase(0, [&]() {
                 for (int c = 0; c < chunk; ++c) {
-                    timed_prop(byR);
+                    timed_prop(byR, first_full && c == 0);
                     launch_frontier(d_probs, dptr(all), all.count, s);
                     launch_advance(d_probs, dptr(all), all.count, s);
                     ctx->launches += 2;
@@ -746,7 +756,7 @@ struct Engine {
                 ctx->launches += 1;
             });
         }
-        enqueue_sweeps(sweep, ctx->sweep_chunk);
+        enqueue_sweeps(sweep, ctx->sweep_chunk, !init.empty());
         enqueue_scan(scan);
         enqueue_bfs(bfs, ctx->level_chunk);
         flush();
@@ -1119,7 +1129,8 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     // pairs: at most dense_min per edge (6 bytes each), dense edges 4 bytes; the counts and scan sums of the
     // preparation are freed before the pairs are allocated, and are smaller
     const uint64_t pmax = m1 * static_cast<uint64_t>(dense_min_for(prm.R));
-    b += (r(4 * pmax) + r(2 * pmax) + r(4 * m1)) * 2;
+    b += (r(4 * pmax) + r(2 * pmax)) * 2 + r(4 * m1) * 3;  // pairs both ways, dense edges (ids; u and e)
+    b += r(sizeof(UnitD) * std::max<uint64_t>(n, 1));       // push-unit descriptors
     b += r(4 * static_cast<uint64_t>(prm.K)) * 2;            // step records
     return b;
 }

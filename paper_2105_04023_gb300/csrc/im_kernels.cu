@@ -134,7 +134,7 @@ __device__ __forceinline__ uint64_t in_degree(const DevProb &P, int64_t v) {
 }
 
 struct Stats {
-    unsigned long long bytes = 0, indeg = 0;
+    unsigned long long bytes = 0;
     unsigned int nchg = 0;
 };
 
@@ -142,7 +142,6 @@ __device__ __forceinline__ void flush_stats(DevCtr *C, Stats &st, int lane) {
     if (lane == 0) {
         if (st.bytes) atomicAdd(&C->bytes, st.bytes);
         if (st.nchg) atomicAdd(&C->nchg, st.nchg);
-        if (st.indeg) atomicAdd(&C->chg_indeg, st.indeg);
     }
     st = Stats();
 }
@@ -352,10 +351,7 @@ __device__ __forceinline__ void finalize_tile(const DevProb &P, int64_t u, uint3
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
     }
-    if (changed && li == 0) {
-        set_bit(Lnext, u);
-        st.indeg += in_degree(P, u) + 1;
-    }
+    if (changed && li == 0) set_bit(Lnext, u);
     st.nchg += changed ? 1u : 0u;
     st.bytes += R + ((changed || sync) ? R : 0);
 }
@@ -384,10 +380,7 @@ __device__ __forceinline__ void finalize_row_r(const DevProb &P, int64_t u, uint
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
     }
-    if (changed && lane == 0) {
-        set_bit(Lnext, u);
-        st.indeg += in_degree(P, u) + 1;
-    }
+    if (changed && lane == 0) set_bit(Lnext, u);
     st.nchg += changed ? 1u : 0u;
     st.bytes += R + ((changed || sync) ? R : 0);
 }
@@ -563,13 +556,10 @@ __device__ __forceinline__ bool word_max(uint32_t *w, uint32_t old, uint32_t can
 }
 
 // u joins L' (the first thread to set its bit counts it).
-__device__ __forceinline__ void mark_changed(const DevProb &P, uint32_t *Lnext, int64_t u, Stats &st) {
+__device__ __forceinline__ void mark_changed(uint32_t *Lnext, int64_t u, Stats &st) {
     const uint32_t bit = 1u << (u & 31);
     if (__ldcg(&Lnext[u >> 5]) & bit) return;
-    if (!(atomicOr(&Lnext[u >> 5], bit) & bit)) {
-        st.nchg += 1;
-        st.indeg += in_degree(P, u) + 1;
-    }
+    if (!(atomicOr(&Lnext[u >> 5], bit) & bit)) st.nchg += 1;
 }
 
 // A push sweep (Algorithm 2 with a small L, in the other direction): every changed vertex v merges M_v into the
@@ -590,22 +580,28 @@ __device__ void push_problem_t(const DevProb &P, uint32_t t, uint64_t cnt, uint6
     uint8_t *srow = reinterpret_cast<uint8_t *>(tile_smem);
     unsigned int *fault = &P.ctr->fault;
     const uint64_t nl = P.ctr->npush_l;
+    const int src0 = (threadIdx.x & 31) - li;  // first lane of this tile
     Stats st;
     for (uint64_t l = first; l < cnt; l += nworkers) {
-        int64_t v, k0, k1;
+        int64_t v, p0, p1, d0, d1;
         if (l < nl) {
             v = P.chg_list[l];
-            k0 = __ldg(&P.xadj_in[v]);
-            k1 = __ldg(&P.xadj_in[v + 1]);
+            const UnitD dv = P.vdesc[v];
+            p0 = dv.p0;
+            p1 = dv.p0 + dv.np;
+            d0 = dv.d0;
+            d1 = dv.d0 + dv.nd;
         } else {
             const uint64_t h = P.chg_hc[l - nl];
             v = static_cast<int64_t>(static_cast<uint32_t>(h));
-            k0 = __ldg(&P.xadj_in[v]) + static_cast<int64_t>(h >> 32) * kPushChunk;
+            const int64_t k0 = __ldg(&P.xadj_in[v]) + static_cast<int64_t>(h >> 32) * kPushChunk;
             const int64_t end = __ldg(&P.xadj_in[v + 1]);
-            k1 = end - k0 > kPushChunk ? k0 + kPushChunk : end;
+            const int64_t k1 = end - k0 > kPushChunk ? k0 + kPushChunk : end;
+            p0 = __ldg(&P.ipofs[k0]);
+            p1 = __ldg(&P.ipofs[k1]);
+            d0 = __ldg(&P.idofs[k0]);
+            d1 = __ldg(&P.idofs[k1]);
         }
-        const int64_t p0 = __ldg(&P.ipofs[k0]), p1 = __ldg(&P.ipofs[k1]);
-        const int64_t d0 = __ldg(&P.idofs[k0]), d1 = __ldg(&P.idofs[k1]);
         uint4 rowc[Gm::CPL];
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) {
@@ -632,29 +628,53 @@ __device__ void push_problem_t(const DevProb &P, uint32_t t, uint64_t cnt, uint6
             for (int k = 0; k < 4; ++k) old[k] = cand[k] ? __ldcg(addr[k]) : 0u;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (cand[k] && word_max(addr[k], old[k], cand[k], fault)) {
-                    const int64_t u = (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R;
-                    mark_changed(P, Lnext, u, st);
-                }
+                if (cand[k] && word_max(addr[k], old[k], cand[k], fault))
+                    mark_changed(Lnext, (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R, st);
             }
         }
-        for (int64_t d = d0; d < d1; ++d) {
-            const uint32_t k = __ldg(&P.idlist[d]);
-            const int64_t u = __ldg(&P.adj_in[k]);
-            const uint32_t e = __ldg(&P.ein[k]);
-            bool grew = false;
-#pragma unroll
-            for (int c = 0; c < Gm::CPL; ++c) {
-                const int ch = li + G * c;
-                const uint32_t m = __ldg(&P.live[static_cast<size_t>(e) * W + (ch >> 1)]) >> (16 * (ch & 1));
-                uint32_t *dst = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u) * R) + 4 * ch;
-                const uint4 o = __ldcg(reinterpret_cast<const uint4 *>(dst));
-                grew |= word_max(dst + 0, o.x, rowc[c].x & nibble_bytes(m & 0xFu), fault);
-                grew |= word_max(dst + 1, o.y, rowc[c].y & nibble_bytes((m >> 4) & 0xFu), fault);
-                grew |= word_max(dst + 2, o.z, rowc[c].z & nibble_bytes((m >> 8) & 0xFu), fault);
-                grew |= word_max(dst + 3, o.w, rowc[c].w & nibble_bytes((m >> 12) & 0xFu), fault);
+        // dense in-edges: the tile's lanes fetch up to G of them at once, then merge them two by two
+        for (int64_t db = d0; db < d1; db += G) {
+            const int nb = d1 - db < G ? static_cast<int>(d1 - db) : G;
+            int32_t my_u = 0;
+            uint32_t my_e = 0;
+            if (li < nb) {
+                my_u = __ldg(&P.idu[db + li]);
+                my_e = __ldg(&P.ide[db + li]);
             }
-            if (__any_sync(tm, grew) && li == 0) mark_changed(P, Lnext, u, st);
+            for (int i = 0; i < nb; i += 2) {
+                int32_t u[2];
+                bool grew[2] = {false, false};
+                uint32_t m[2][Gm::CPL];
+                uint4 o[2][Gm::CPL];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int ii = i + r < nb ? i + r : i;
+                    u[r] = __shfl_sync(tm, my_u, src0 + ii);
+                    const uint32_t e = __shfl_sync(tm, my_e, src0 + ii);
+#pragma unroll
+                    for (int c = 0; c < Gm::CPL; ++c) {
+                        const int ch = li + G * c;
+                        m[r][c] = (i + r < nb) ? (__ldg(&P.live[static_cast<size_t>(e) * W + (ch >> 1)]) >>
+                                                  (16 * (ch & 1)))
+                                               : 0u;
+                        o[r][c] = __ldcg(reinterpret_cast<const uint4 *>(Mnext + static_cast<size_t>(u[r]) * R) + ch);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+#pragma unroll
+                    for (int c = 0; c < Gm::CPL; ++c) {
+                        uint32_t *dst = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u[r]) * R) +
+                                        4 * (li + G * c);
+                        const uint32_t mm = m[r][c];
+                        grew[r] |= word_max(dst + 0, o[r][c].x, rowc[c].x & nibble_bytes(mm & 0xFu), fault);
+                        grew[r] |= word_max(dst + 1, o[r][c].y, rowc[c].y & nibble_bytes((mm >> 4) & 0xFu), fault);
+                        grew[r] |= word_max(dst + 2, o[r][c].z, rowc[c].z & nibble_bytes((mm >> 8) & 0xFu), fault);
+                        grew[r] |= word_max(dst + 3, o[r][c].w, rowc[c].w & nibble_bytes((mm >> 12) & 0xFu), fault);
+                    }
+                    if (__any_sync(tm, grew[r]) && li == 0) mark_changed(Lnext, u[r], st);
+                }
+            }
         }
         if (li == 0)
             st.bytes += R + 32 + 10 * static_cast<uint64_t>(p1 - p0) + (12 + W * 4 + R) * static_cast<uint64_t>(d1 - d0);
@@ -662,7 +682,6 @@ __device__ void push_problem_t(const DevProb &P, uint32_t t, uint64_t cnt, uint6
     }
     // rows are marked by any lane
     if (st.nchg) atomicAdd(&P.ctr->nchg, st.nchg);
-    if (st.indeg) atomicAdd(&P.ctr->chg_indeg, st.indeg);
     if (st.bytes) atomicAdd(&P.ctr->bytes, st.bytes);
 }
 
@@ -865,10 +884,8 @@ __device__ __forceinline__ bool sweep_stops(const DevProb &P, const DevCtr &C) {
     return C.nchg <= P.stop_thr || C.t + 1 >= P.max_sweeps;
 }
 
-// The next sweep pushes from L' when that is cheap (few in-edges into the changed vertices).
-__device__ __forceinline__ bool next_is_push(const DevProb &P, const DevCtr &C) {
-    return C.chg_indeg <= P.list_thr;
-}
+// Every sweep after the first (where L = V and every row is pulled) pushes from L'.
+__device__ __forceinline__ bool next_is_push(const DevProb &, const DevCtr &) { return true; }
 
 }  // namespace
 
@@ -899,6 +916,7 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
                 Lold[i] = 0;
                 w = Lnew[i];
             }
+            unsigned long long indeg = 0;  // in-edges into L': the next sweep's work count
             if (push_next) {
                 uint32_t wh = 0;
                 for (uint32_t x = w; x; x &= x - 1) {
@@ -908,6 +926,7 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
 #pragma unroll 4
                     for (int k = 0; k < P.R / 16; ++k) dst[k] = src[k];
                     const uint64_t d = in_degree(P, v);
+                    indeg += d;
                     if (d > kPushChunk) {
                         wh |= 1u << (__ffs(x) - 1);
                         const uint32_t nt = static_cast<uint32_t>((d + kPushChunk - 1) / kPushChunk);
@@ -918,6 +937,9 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
                 }
                 block_append_bits(w & ~wh, i, P.chg_list, &P.ctr->nchg_list);
             }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) indeg += __shfl_xor_sync(kFull, indeg, off);
+            if ((threadIdx.x & 31) == 0 && indeg) atomicAdd(&P.ctr->chg_indeg, indeg);
         }
     }
 }
@@ -941,7 +963,7 @@ __global__ void k_advance(const DevProb *__restrict__ probs, const int32_t *__re
         C.res_par = (t + 1) & 1u;
     }
     // visits of the next sweep (Algorithm 2's work count): every edge (u, v) with v in L_{t+1}, in every simulation
-    if (!C.done) C.visits += (C.chg_indeg - nchg) * static_cast<unsigned long long>(P.R);
+    if (!C.done) C.visits += C.chg_indeg * static_cast<unsigned long long>(P.R);
     C.full = next_is_push(P, C) ? 0u : 1u;
     C.npush_l = C.full ? 0u : C.nchg_list;
     C.npush_h = C.full ? 0u : C.nchg_hc;
@@ -1439,14 +1461,15 @@ __global__ void __launch_bounds__(kBlock) k_inpair_counts(const DevProb P, int32
     }
 }
 
-// In-pairs (source u, simulation j) of every sparse in-edge at ipofs[k], and the dense in-edge list.
-__global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t *iu, uint16_t *ij,
-                                                        uint32_t *idlist) {
+// In-pairs (source u, simulation j) of every sparse in-edge at ipofs[k], and the dense in-edges (u, e).
+__global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t *iu, uint16_t *ij, int32_t *idu,
+                                                        uint32_t *ide) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < P.m; k += stride) {
         const int64_t d0 = P.idofs[k];
         if (P.idofs[k + 1] != d0) {
-            idlist[d0] = static_cast<uint32_t>(k);
+            idu[d0] = P.adj_in[k];
+            ide[d0] = P.ein[k];
             continue;
         }
         const int64_t e = P.ein[k];
@@ -1457,6 +1480,22 @@ __global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t
             ij[at] = P.pj[p];
             ++at;
         }
+    }
+}
+
+// Push-unit descriptor of every vertex (its in-pairs and dense in-edges).
+__global__ void __launch_bounds__(kBlock) k_vertex_desc(const DevProb P, UnitD *vdesc) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < P.n; v += stride) {
+        const int64_t k0 = P.xadj_in[v], k1 = P.xadj_in[v + 1];
+        UnitD d;
+        d.p0 = P.ipofs[k0];
+        d.d0 = P.idofs[k0];
+        d.np = static_cast<uint32_t>(P.ipofs[k1] - d.p0);
+        d.nd = static_cast<uint32_t>(P.idofs[k1] - d.d0);
+        d.u = static_cast<int32_t>(v);
+        d.pad = 0;
+        vdesc[v] = d;
     }
 }
 
@@ -1830,8 +1869,11 @@ void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint32_t *dli
 void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
     k_inpair_counts<<<g_grid_block, kBlock, 0, s>>>(P, npairs, ndense);
 }
-void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *idlist, cudaStream_t s) {
-    k_inpair_fill<<<g_grid_block, kBlock, 0, s>>>(P, iu, ij, idlist);
+void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, int32_t *idu, uint32_t *ide, cudaStream_t s) {
+    k_inpair_fill<<<g_grid_block, kBlock, 0, s>>>(P, iu, ij, idu, ide);
+}
+void launch_vertex_desc(const DevProb &P, UnitD *vdesc, cudaStream_t s) {
+    k_vertex_desc<<<g_grid_block, kBlock, 0, s>>>(P, vdesc);
 }
 void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s) {
     k_unit_desc<<<g_grid_block, kBlock, 0, s>>>(P, rdesc, tdesc);

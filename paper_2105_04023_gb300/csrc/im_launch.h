@@ -30,7 +30,8 @@ void launch_live_masks(const DevProb &P, cudaStream_t s);
 void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
 void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint32_t *dlist, cudaStream_t s);
 void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
-void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *idlist, cudaStream_t s);
+void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, int32_t *idu, uint32_t *ide, cudaStream_t s);
+void launch_vertex_desc(const DevProb &P, UnitD *vdesc, cudaStream_t s);
 void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s);
 void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx, cudaStream_t s);
 void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s);

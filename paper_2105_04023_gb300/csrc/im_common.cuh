@@ -13,8 +13,7 @@ constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kHeavyDeg = 64;        // rows with more out-edges are split into tasks of kTaskEdges edges
 constexpr int kTaskEdges = 64;
 constexpr int kBigTasks = 32;        // split rows with more tasks are merged by a whole block
-constexpr int kBfsHeavyDeg = 256;    // search-frontier vertices with more out-edges are split into edge chunks
-constexpr int kBfsChunk = 256;       // out-edges per chunk task of a heavy search-frontier vertex
+constexpr int kBfsTaskEdges = 32;    // out-edges per task of a search-frontier vertex (one warp, one edge a lane)
 constexpr int kPushChunk = 1024;     // a changed vertex pushes its in-edges in units of at most this many
 constexpr int kCasLimit = 1024;      // compare-and-swap tries of one register-word update before it counts as a fault
 constexpr int kPfxShift = 17;        // sampling words are compared on their top 15 bits first
@@ -58,8 +57,9 @@ struct DevCtr {
     uint32_t lvl;        // level of the current search
     uint32_t bdone;      // 1 once the search found no new vertex
     uint32_t btimeout;   // 1 if it hit the level limit first
-    uint32_t nF[2];      // light frontier entries by level parity
-    uint32_t nH[2];      // heavy frontier chunk tasks by level parity
+    uint32_t nT[2];      // search tasks by level parity
+    uint32_t nV;         // vertices that reached something new at the current level
+    uint32_t pad3;
     uint32_t pad1;
     unsigned long long reached;       // |{(v, j): v in R_{G_j}(S)}|
     unsigned long long levels_total;
@@ -123,8 +123,8 @@ struct DevProb {
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
     uint32_t *del0, *del1;     // n x W: bits newly reached at the previous level, by parity
     uint32_t *Fb;              // bit per vertex: reached something new at this level
-    int32_t *F0, *F1;            // light frontier vertices by parity
-    uint64_t *H0, *H1;           // heavy frontier chunk tasks by parity: (chunk << 32) | vertex
+    uint64_t *T0, *T1;         // search tasks by level parity: (chunk << 32) | vertex
+    int32_t *Vn;               // vertices that reached something new at the current level
     uint32_t *inS;             // bit per vertex: in the seed set
     uint8_t *MS;               // R bytes: M_S'
     DevCtr *ctr;

@@ -307,11 +307,11 @@ void alloc_bfs(Prob &P, cudaStream_t s) {
     P.dp.del1 = mem.alloc<uint32_t>(n * W, true);
     P.dp.Fb = mem.alloc<uint32_t>(words, true);
     P.dp.inS = mem.alloc<uint32_t>(words, true);
-    P.dp.F0 = mem.alloc<int32_t>(n);
-    P.dp.F1 = mem.alloc<int32_t>(n);
-    // chunk tasks of heavy vertices: ceil(deg / 256) <= deg / 128 for deg > 256, so m / 128 + 1 bound a level's
-    P.dp.H0 = mem.alloc<uint64_t>(P.G->m / 128 + 1);
-    P.dp.H1 = mem.alloc<uint64_t>(P.G->m / 128 + 1);
+    // tasks of a level: at most one per vertex plus one per kBfsTaskEdges out-edges
+    const size_t ntask = static_cast<size_t>(n + P.G->m / kBfsTaskEdges + 1);
+    P.dp.T0 = mem.alloc<uint64_t>(ntask);
+    P.dp.T1 = mem.alloc<uint64_t>(ntask);
+    P.dp.Vn = mem.alloc<int32_t>(n);
     P.has_bfs = true;
 }
 
@@ -625,12 +625,20 @@ struct Engine {
 
     void enqueue_bfs(const std::vector<int32_t> &ids, int chunk) {
         if (ids.empty()) return;
+        std::vector<std::pair<int, List>> byR;
+        for (int R : {64, 128, 256, 512, 1024}) {
+            std::vector<int32_t> sub;
+            for (int32_t i : ids)
+                if (probs[i]->prm.R == R) sub.push_back(i);
+            if (!sub.empty()) byR.emplace_back(R, add_list(sub));
+        }
         const List all = add_list(ids);
         cudaStream_t s = ctx->stream;
-        pending.push_back([this, all, chunk, s]() {
+        pending.push_back([this, byR, all, chunk, s]() {
             phase(2, [&]() {
                 for (int c = 0; c < chunk; ++c) {
-                    launch_bfs_level(d_probs, dptr(all), all.count, s);
+                    for (auto &rl : byR) launch_bfs_level(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
+                    ctx->launches += static_cast<int64_t>(byR.size()) - 1;
                     launch_bfs_frontier(d_probs, dptr(all), all.count, s);
                     launch_bfs_advance(d_probs, dptr(all), all.count, s);
                     ctx->launches += 3;
@@ -1120,8 +1128,8 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     b += r(4 * words) * 2;                                   // L bits
     b += r(4 * n) + r(8 * (static_cast<uint64_t>(g.m) / 512 + 1));  // changed lists
     b += r(R) + r(8 * 4096);                                 // M_S', frontier log
-    b += r(4 * n * W) * 3 + r(4 * words) * 2 + r(4 * n) * 2;  // reach bits, frontier bits, seed set, light lists
-    b += r(8 * (static_cast<uint64_t>(g.m) / 128 + 1)) * 2;  // heavy chunk-task lists
+    b += r(4 * n * W) * 3 + r(4 * words) * 2 + r(4 * n);  // reach bits, frontier and seed-set bits, new vertices
+    b += r(8 * (n + static_cast<uint64_t>(g.m) / kBfsTaskEdges + 1)) * 2;  // search tasks
     const uint64_t m1 = std::max<uint64_t>(static_cast<uint64_t>(g.m), 1);
     b += r(4 * W * m1);                                      // live-simulation masks of the edges
     b += r(8 * (m1 + 1)) * 4;                                // pair and dense-edge offsets, out- and in-CSR order

@@ -1112,11 +1112,12 @@ __global__ void __launch_bounds__(kBlock) k_scan(const DevProb *__restrict__ pro
 }
 
 namespace {
-// Appends the chunk tasks of heavy frontier vertex v (out-degree deg) to a heavy list.
-__device__ __forceinline__ void bfs_heavy_tasks(uint64_t *H, uint32_t *count, uint32_t v, int64_t deg) {
-    const uint32_t nt = static_cast<uint32_t>((deg + kBfsChunk - 1) / kBfsChunk);
+// Appends the search tasks of vertex v (out-degree deg): one per kBfsTaskEdges out-edges, at least one, whose
+// level also consumes v's delta row.
+__device__ __forceinline__ void bfs_tasks(uint64_t *T, uint32_t *count, uint32_t v, int64_t deg) {
+    const uint32_t nt = deg > 0 ? static_cast<uint32_t>((deg + kBfsTaskEdges - 1) / kBfsTaskEdges) : 1u;
     const uint32_t at = atomicAdd(count, nt);
-    for (uint32_t c = 0; c < nt; ++c) H[at + c] = (static_cast<uint64_t>(c) << 32) | v;
+    for (uint32_t c = 0; c < nt; ++c) T[at + c] = (static_cast<uint64_t>(c) << 32) | v;
 }
 }  // namespace
 
@@ -1154,16 +1155,10 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
         C.gsum = gsum;
         C.best_key = 0;
         set_bit(P.inS, s);
-        const int64_t deg = P.xadj[s + 1] - P.xadj[s];
-        const bool heavy = deg > kBfsHeavyDeg;
-        C.nF[0] = heavy ? 0u : 1u;
-        C.nH[0] = 0;
-        C.nF[1] = 0;
-        C.nH[1] = 0;
-        if (heavy)
-            bfs_heavy_tasks(P.H0, &C.nH[0], s, deg);
-        else
-            P.F0[0] = static_cast<int32_t>(s);
+        C.nT[0] = 0;
+        C.nT[1] = 0;
+        C.nV = 0;
+        bfs_tasks(P.T0, &C.nT[0], s, P.xadj[s + 1] - P.xadj[s]);
         C.lvl = 0;
         C.bdone = added ? 0u : 1u;
         C.btimeout = 0;
@@ -1187,11 +1182,7 @@ __global__ void k_seed_set(const DevProb *__restrict__ prob, const int32_t *__re
         if (w == 0) {
             const uint32_t prev = atomicOr(&P.inS[s >> 5], 1u << (s & 31));
             if (!((prev >> (s & 31)) & 1u)) {
-                const int64_t deg = P.xadj[s + 1] - P.xadj[s];
-                if (deg > kBfsHeavyDeg)
-                    bfs_heavy_tasks(P.H0, &C.nH[0], static_cast<uint32_t>(s), deg);
-                else
-                    P.F0[atomicAdd(&C.nF[0], 1u)] = s;
+                bfs_tasks(P.T0, &C.nT[0], static_cast<uint32_t>(s), P.xadj[s + 1] - P.xadj[s]);
             }
         }
     }
@@ -1199,153 +1190,137 @@ __global__ void k_seed_set(const DevProb *__restrict__ prob, const int32_t *__re
 
 namespace {
 
-// Pushes the new bits d of u over edge e = (u, v): bits of d that are live on e and not yet reached at v are new
-// at v; they are ORed into vis[v] and into the next level's delta of v, and v joins the next frontier.  Pushers of
-// the same level may race on a bit: both OR it, which is the same result, so no atomic needs a return value.
-__device__ __forceinline__ void bfs_push(const DevProb &P, int64_t e, const uint32_t *d, uint32_t *dnext) {
-    const int32_t v = __ldg(&P.adj[e]);
-    const uint32_t *lv = P.live + static_cast<size_t>(e) * P.W;
-    bool any_new = false;
-    for (int k = 0; k < P.W; ++k) {
-        const uint32_t dk = d[k];
-        if (!dk) continue;
-        const uint32_t m = dk & __ldg(&lv[k]);
-        if (!m) continue;
-        const size_t at = static_cast<size_t>(v) * P.W + k;
-        const uint32_t nb = m & ~P.vis[at];
-        if (!nb) continue;
-        atomicOr(&P.vis[at], nb);
-        atomicOr(&dnext[at], nb);
-        any_new = true;
-    }
-    if (any_new) set_bit(P.Fb, v);
-}
-
 }  // namespace
 
-// One level of the bit-parallel reachability search of Algorithm 1, over all simulations at once.  One warp per
-// light frontier vertex (its delta row is consumed, counted and cleared here) or per 256-edge chunk of a heavy one
-// (its row is read by several warps and cleared after the level); lanes go over out-edges.
+// One level of the bit-parallel reachability search of Algorithm 1, over all simulations at once: one warp per
+// task (kBfsTaskEdges out-edges of a frontier vertex u, one a lane).  The delta d of u (bits newly reached at u at
+// the previous level) goes out over each edge e = (u, v) in the simulations where e is live; bits not yet reached
+// at v are ORed into vis[v] and into v's next delta, and the first thread to flag v lists it for the next level.
+// Pushers of one level may race on a bit: both OR it, the same result, so no atomic needs a return value.
+template <int R>
 __global__ void __launch_bounds__(kBlock) k_bfs_level(const DevProb *__restrict__ probs,
                                                       const int32_t *__restrict__ act, int nact) {
-    __shared__ uint32_t s_d[kWarpsPerBlock][32];
+    constexpr int W = R / 32;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
     const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
-        const DevCtr &C = *P.ctr;
+        DevCtr &C = *P.ctr;
         if (C.bdone) continue;
         const uint32_t p = C.lvl & 1u;
-        const uint64_t nf = C.nF[p];
-        const uint64_t cnt = nf + C.nH[p];
+        const uint64_t cnt = C.nT[p];
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
-        const int32_t *F = p ? P.F1 : P.F0;
-        const uint64_t *H = p ? P.H1 : P.H0;
-        uint32_t *dcur = p ? P.del1 : P.del0;
+        const uint64_t *T = p ? P.T1 : P.T0;
+        const uint32_t *dcur = p ? P.del1 : P.del0;
         uint32_t *dnext = p ? P.del0 : P.del1;
-        unsigned long long added = 0;
         for (uint64_t l = first; l < cnt; l += nworkers) {
-            const bool light = l < nf;
-            int64_t u, e0, e1;
-            if (light) {
-                u = F[l];
-                e0 = __ldg(&P.xadj[u]);
-                e1 = __ldg(&P.xadj[u + 1]);
-            } else {
-                const uint64_t t = H[l - nf];
-                u = static_cast<int64_t>(static_cast<uint32_t>(t));
-                e0 = __ldg(&P.xadj[u]) + static_cast<int64_t>(t >> 32) * kBfsChunk;
-                const int64_t end = __ldg(&P.xadj[u + 1]);
-                e1 = end - e0 > kBfsChunk ? e0 + kBfsChunk : end;
+            const uint64_t t = T[l];
+            const int64_t u = static_cast<int64_t>(static_cast<uint32_t>(t));
+            const int64_t e = __ldg(&P.xadj[u]) + static_cast<int64_t>(t >> 32) * kBfsTaskEdges + lane;
+            const bool has = e < __ldg(&P.xadj[u + 1]);
+            const uint32_t dl = lane < W ? dcur[static_cast<size_t>(u) * W + lane] : 0u;
+            const int32_t v = has ? __ldg(&P.adj[e]) : 0;
+            uint32_t m[W];
+            uint32_t any = 0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const uint32_t dk = __shfl_sync(kFull, dl, k);
+                m[k] = (dk && has) ? dk & __ldg(&P.live[static_cast<size_t>(e) * W + k]) : 0u;
+                any |= m[k];
             }
-            for (int k = lane; k < P.W; k += 32) {
-                const size_t at = static_cast<size_t>(u) * P.W + k;
-                const uint32_t x = dcur[at];
-                s_d[wib][k] = x;
-                if (light) {
-                    dcur[at] = 0;
-                    added += __popc(x);  // each newly reached (v, j) is consumed exactly once
+            bool fresh = false;
+            if (__any_sync(kFull, any != 0)) {
+                uint32_t x[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) x[k] = m[k] ? P.vis[static_cast<size_t>(v) * W + k] : 0u;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    const uint32_t nb = m[k] & ~x[k];
+                    if (!nb) continue;
+                    const size_t at = static_cast<size_t>(v) * W + k;
+                    atomicOr(&P.vis[at], nb);
+                    atomicOr(&dnext[at], nb);
+                    fresh = true;
+                }
+                if (fresh) {
+                    const uint32_t bit = 1u << (v & 31);
+                    fresh = !(atomicOr(&P.Fb[v >> 5], bit) & bit);
                 }
             }
-            __syncwarp();
-            for (int64_t e = e0 + lane; e < e1; e += 32) bfs_push(P, e, s_d[wib], dnext);
-            __syncwarp();
+            // warp-aggregated append of the vertices this warp flagged first
+            const unsigned mf = __ballot_sync(kFull, fresh);
+            if (mf) {
+                uint32_t at = 0;
+                if (lane == 0) at = atomicAdd(&C.nV, static_cast<uint32_t>(__popc(mf)));
+                at = __shfl_sync(kFull, at, 0);
+                if (fresh) P.Vn[at + __popc(mf & ((1u << lane) - 1u))] = v;
+            }
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
-        if (lane == 0 && added) atomicAdd(&P.ctr->reached, added);
     }
 }
 
-// After a level: counts and clears the consumed delta rows of heavy frontier vertices and compacts the vertices
-// that reached something new into the next frontier (light vertices, and chunk tasks of heavy ones).
+// After a level: counts and clears the consumed delta rows (one per vertex of the level, at its first task), and
+// turns the vertices that reached something new into the next level's tasks (clearing their flags).
 __global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restrict__ probs,
                                                          const int32_t *__restrict__ act, int nact) {
-    {
-        const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-        const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-        uint64_t base = 0;
-        for (int q = 0; q < nact; ++q) {
-            const DevProb &P = probs[act[q]];
-            const DevCtr &C = *P.ctr;
-            if (C.bdone) continue;
-            const uint32_t p = C.lvl & 1u;
-            const uint64_t *H = p ? P.H1 : P.H0;
-            uint32_t *dcur = p ? P.del1 : P.del0;
-            const uint64_t cnt = static_cast<uint64_t>(C.nH[p]) * P.W;
-            const uint64_t first = first_owned(tid, nthreads, base);
-            base += cnt;
-            unsigned long long added = 0;  // consumed new bits of the heavy frontier vertices (once, at chunk 0)
-            for (uint64_t l = first; l < cnt; l += nthreads) {
-                const uint64_t t = H[l / P.W];
-                if (t >> 32) continue;
-                const size_t at = static_cast<size_t>(static_cast<uint32_t>(t)) * P.W + l % P.W;
-                added += __popc(dcur[at]);
-                dcur[at] = 0;
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
-            if ((threadIdx.x & 31) == 0 && added) atomicAdd(&P.ctr->reached, added);
-        }
-    }
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
         if (C.bdone) continue;
-        const uint32_t np = (C.lvl + 1) & 1u;
-        int32_t *F = np ? P.F1 : P.F0;
-        uint64_t *H = np ? P.H1 : P.H0;
-        const int64_t words = (P.n + 31) >> 5;
-        const uint64_t chunks = (words + kBlock - 1) / kBlock;
-        const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
-        base += chunks;
-        for (uint64_t ch = first; ch < chunks; ch += gridDim.x) {
-            const int64_t i = static_cast<int64_t>(ch) * kBlock + threadIdx.x;
-            uint32_t w = 0;
-            if (i < words) {
-                w = P.Fb[i];
-                if (w) P.Fb[i] = 0;
-            }
-            uint32_t wl = 0, wh = 0;
-            for (uint32_t x = w; x;) {
-                const int b = __ffs(x) - 1;
-                x &= x - 1;
-                const int64_t v = i * 32 + b;
-                if (P.xadj[v + 1] - P.xadj[v] > kBfsHeavyDeg)
-                    wh |= 1u << b;
-                else
-                    wl |= 1u << b;
-            }
-            block_append_bits(wl, i, F, &P.ctr->nF[np]);
-            for (uint32_t x = wh; x; x &= x - 1) {
-                const int64_t v = i * 32 + __ffs(x) - 1;
-                bfs_heavy_tasks(H, &P.ctr->nH[np], static_cast<uint32_t>(v), P.xadj[v + 1] - P.xadj[v]);
+        const uint32_t p = C.lvl & 1u;
+        const uint64_t *T = p ? P.T1 : P.T0;
+        uint64_t *Tn = p ? P.T0 : P.T1;
+        uint32_t *dcur = p ? P.del1 : P.del0;
+        const uint64_t nc = static_cast<uint64_t>(C.nT[p]) * P.W;
+        const uint64_t cnt = nc;
+        const uint64_t first = first_owned(tid, nthreads, base);
+        base += cnt;
+        unsigned long long added = 0;  // newly reached (v, j), each consumed exactly once
+        for (uint64_t l = first; l < cnt; l += nthreads) {
+            if (l < nc) {
+                const uint64_t t = T[l / P.W];
+                if (t >> 32) continue;
+                const size_t at = static_cast<size_t>(static_cast<uint32_t>(t)) * P.W + l % P.W;
+                added += __popc(dcur[at]);
+                dcur[at] = 0;
             }
         }
+        // the next level's tasks, one warp-aggregated reservation per round
+        const uint64_t nv = C.nV;
+        const uint64_t vfirst = first_owned(tid, nthreads, base);
+        base += nv;
+        const uint64_t rounds = (nv + nthreads - 1) / nthreads;
+        for (uint64_t r = 0; r < rounds; ++r) {
+            const uint64_t l = vfirst + r * nthreads;
+            int32_t v = 0;
+            uint32_t nt = 0;
+            if (l < nv) {
+                v = P.Vn[l];
+                atomicAnd(&P.Fb[v >> 5], ~(1u << (v & 31)));
+                const int64_t deg = P.xadj[v + 1] - P.xadj[v];
+                nt = deg > 0 ? static_cast<uint32_t>((deg + kBfsTaskEdges - 1) / kBfsTaskEdges) : 1u;
+            }
+            uint32_t incl = nt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, off);
+                if ((threadIdx.x & 31) >= off) incl += y;
+            }
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+            uint32_t at = 0;
+            if ((threadIdx.x & 31) == 31 && total) at = atomicAdd(&P.ctr->nT[p ^ 1u], total);
+            at = __shfl_sync(kFull, at, 31) + incl - nt;
+            for (uint32_t c = 0; c < nt; ++c) Tn[at + c] = (static_cast<uint64_t>(c) << 32) | static_cast<uint32_t>(v);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
+        if ((threadIdx.x & 31) == 0 && added) atomicAdd(&P.ctr->reached, added);
     }
 }
 
@@ -1357,10 +1332,10 @@ __global__ void k_bfs_advance(const DevProb *__restrict__ probs, const int32_t *
     if (C.bdone) return;
     const uint32_t p = C.lvl & 1u;
     C.levels_total += 1;
-    const bool empty = C.nF[p ^ 1u] + C.nH[p ^ 1u] == 0;
+    const bool empty = C.nT[p ^ 1u] == 0;
     const bool lim = C.lvl + 1 >= P.max_sweeps;
-    C.nF[p] = 0;
-    C.nH[p] = 0;
+    C.nT[p] = 0;
+    C.nV = 0;
     C.lvl += 1;
     if (empty || lim) {
         C.bdone = 1;
@@ -1834,8 +1809,8 @@ void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t s
 void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cudaStream_t s) {
     k_seed_set<<<(k * W + 255) / 256, 256, 0, s>>>(prob, seeds, k);
 }
-void launch_bfs_level(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    k_bfs_level<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
+void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    IMK_R_SWITCH(R, (k_bfs_level<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
 }
 void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_bfs_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);

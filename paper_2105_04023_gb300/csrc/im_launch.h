@@ -20,7 +20,7 @@ void launch_advance(const DevProb *probs, const int32_t *act, int nact, cudaStre
 void launch_scan(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t step, cudaStream_t s);
 void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cudaStream_t s);
-void launch_bfs_level(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_bfs_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);

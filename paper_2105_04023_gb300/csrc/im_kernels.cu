@@ -680,6 +680,10 @@ __device__ void push_problem_t(const DevProb &P, uint32_t t, uint64_t cnt, uint6
             st.bytes += R + 32 + 10 * static_cast<uint64_t>(p1 - p0) + (12 + W * 4 + R) * static_cast<uint64_t>(d1 - d0);
         __syncwarp(tm);
     }
+    // the staged rows shared the tile's sparse accumulators, which a pulling unit of another problem in the same
+    // launch expects to find zero
+    for (int k = li; k < R / 16; k += G) reinterpret_cast<uint4 *>(srow)[k] = make_uint4(0, 0, 0, 0);
+    __syncwarp(tm);
     // rows are marked by any lane
     if (st.nchg) atomicAdd(&P.ctr->nchg, st.nchg);
     if (st.bytes) atomicAdd(&P.ctr->bytes, st.bytes);

@@ -183,6 +183,24 @@ def test_estimate_and_exact_sigma(ctx):
 
 # --- batch ------------------------------------------------------------------------------------------------------
 
+def test_batch_same_R_problems_out_of_phase(ctx):
+    """Problems of one R in different phases share every launch: while one pulls the first sweep of a (re)build,
+    another pushes, and one tile may serve units of both in the same launch."""
+    probs = [workloads.batch_problem(i, max_scale=16) for i in (226, 228, 227, 231, 235)]  # all R = 64
+    assert {p.R for p in probs} == {64}
+    gs = [im.Graph.from_synth(p.graph, p.model, p.p, device="cuda") for p in probs]
+    prms = [im.params(R=p.R, K=p.K, eps_g=p.eps_g, eps_l=p.eps_l, seed=p.seed) for p in probs]
+    batch = ctx.im_select_seeds_batch(gs, prms)
+    for g, prm, b in zip(gs, prms, batch):
+        single = ctx.im_select_seeds(g, prm, trace=False)
+        assert b["seeds"].tolist() == single["seeds"].tolist()
+        assert b["sigma_final"] == single["sigma_final"] and b["rebuilds"] == single["rebuilds"]
+    p = probs[3]  # the smallest: also against the oracle
+    ref = oracle.select_seeds(p.graph.n, p.graph.xadj, p.graph.adj, p.model, p.p, p.R, p.K, p.eps_g, p.eps_l, 0.0,
+                              p.seed)
+    assert batch[3]["seeds"].tolist() == ref["seeds"].tolist()
+
+
 def test_batch_equals_individual_and_oracle(ctx):
     probs = [workloads.batch_problem(i, max_scale=11) for i in range(10)]
     gs = [im.Graph.from_synth(p.graph, p.model, p.p) for p in probs]

@@ -31,6 +31,15 @@ struct UnitD {
     int32_t pad;
 };
 
+// Grid-wide barrier of the persistent (cooperatively launched) kernels: arrivals and a generation count.
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+    unsigned int fail;   // a block gave up waiting (every block then leaves the kernel)
+    unsigned int pad;
+};
+constexpr uint32_t kBarrierLimit = 1u << 20;  // polls of one barrier wait (under a second in all) before giving up
+
 // Counters of one problem, written by the kernels and read back by the host after each engine tick.
 struct DevCtr {
     // diffusion (Algorithm 2) ----------------------------------------------------------------------------------
@@ -44,7 +53,8 @@ struct DevCtr {
     uint32_t nchg_hc;    // entries written to chg_hc (chunks of the changed vertices with more)
     uint32_t npush_l;    // chg_list / chg_hc entries the current push sweep works on
     uint32_t npush_h;
-    uint32_t fault;      // bit 0: a bulk copy did not complete in time; bit 1: a register update kept failing
+    uint32_t fault;      // bit 0: a bulk copy did not complete in time; bit 1: a register update kept failing;
+                         // bit 2: a grid barrier of a persistent kernel was not reached in time
     unsigned long long chg_indeg;     // in-edges into the vertices changed in the current sweep
     unsigned long long visits;        // edge-simulation visits, running total
     unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total

@@ -63,6 +63,10 @@ struct im_ctx {
     size_t d_act_cap = 0;
     int sweep_chunk = 4;
     int level_chunk = 4;
+    GridBar *d_gbar = nullptr;  // barrier of the persistent kernels
+    // run whole searches in one cooperative launch (IM_PERSISTENT=1); measured no faster than level-by-level
+    // launches on the R-MAT workloads, whose levels are dominated by their own dependent loads, so off by default
+    bool persistent = false;
 };
 
 namespace {
@@ -636,6 +640,18 @@ struct Engine {
         cudaStream_t s = ctx->stream;
         pending.push_back([this, byR, all, chunk, s]() {
             phase(2, [&]() {
+                // whole searches, one cooperative launch per R; the host reads the counters once they are done
+                if (ctx->persistent) {
+                    size_t done = 0;
+                    for (auto &rl : byR) {
+                        if (!launch_bfs_run(rl.first, d_probs, dptr(rl.second), rl.second.count, ctx->d_gbar, s))
+                            break;
+                        ++done;
+                    }
+                    ctx->launches += static_cast<int64_t>(done);
+                    if (done == byR.size()) return;
+                    ctx->persistent = false;  // not available on this device: step the remaining levels
+                }
                 for (int c = 0; c < chunk; ++c) {
                     for (auto &rl : byR) launch_bfs_level(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
                     ctx->launches += static_cast<int64_t>(byR.size()) - 1;
@@ -780,8 +796,9 @@ struct Engine {
             Prob &P = *probs[i];
             if (P.phase == Prob::kDone) continue;
             if (P.last.fault) {
-                problem_error(P, IM_ECUDA, (P.last.fault & 1u) ? "a bulk copy into shared memory did not complete"
-                                                                : "a register update did not settle");
+                problem_error(P, IM_ECUDA, (P.last.fault & 1u)   ? "a bulk copy into shared memory did not complete"
+                                           : (P.last.fault & 2u) ? "a register update did not settle"
+                                                                 : "a grid barrier was not reached in time");
             } else if (P.phase == Prob::kSweep && P.last.done) {
                 if (P.last.timeout)
                     problem_error(P, IM_ETIMEOUT, "diffusion exceeded max_sweeps");
@@ -949,6 +966,14 @@ im_status im_ctx_create(int device, void *cuda_stream, im_ctx **out) {
     }
     if (const char *v = std::getenv("IM_SWEEP_CHUNK")) ctx->sweep_chunk = std::max(1, std::atoi(v));
     if (const char *v = std::getenv("IM_LEVEL_CHUNK")) ctx->level_chunk = std::max(1, std::atoi(v));
+    if (const char *v = std::getenv("IM_PERSISTENT")) ctx->persistent = std::atoi(v) != 0;
+    if (cudaMalloc(&ctx->d_gbar, sizeof(GridBar)) != cudaSuccess ||
+        cudaMemset(ctx->d_gbar, 0, sizeof(GridBar)) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return IM_ECUDA;
+    }
     *out = ctx;
     return IM_OK;
 }
@@ -970,6 +995,7 @@ im_status im_ctx_destroy(im_ctx *ctx) {
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     if (ctx->h_act) cudaFreeHost(ctx->h_act);
     if (ctx->d_act) cudaFree(ctx->d_act);
+    if (ctx->d_gbar) cudaFree(ctx->d_gbar);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return IM_OK;

@@ -15,6 +15,7 @@
 //   k_scan, k_choose                          Algorithm 1, argmax of Estimate(Merge(M_S', M_v)) (Eq. 2-3)
 //   k_bfs_*                                   Algorithm 1, reachability set of S in every simulation, sigma
 //   k_merge                                   Algorithm 1, M_S' <- Merge(M_S', M_s)
+#include <algorithm>
 #include <cstdlib>
 
 #include "im_common.cuh"
@@ -1201,31 +1202,33 @@ namespace {
 // the previous level) goes out over each edge e = (u, v) in the simulations where e is live; bits not yet reached
 // at v are ORed into vis[v] and into v's next delta, and the first thread to flag v lists it for the next level.
 // Pushers of one level may race on a bit: both OR it, the same result, so no atomic needs a return value.
+// Phases of a search level are device functions so that the persistent kernel can run many levels in one launch;
+// everything another block may have written during that launch is read past L1 (__ldcg).
 template <int R>
-__global__ void __launch_bounds__(kBlock) k_bfs_level(const DevProb *__restrict__ probs,
-                                                      const int32_t *__restrict__ act, int nact) {
+__device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
+                                                int nact) {
     constexpr int W = R / 32;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
-    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + wib;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
         DevCtr &C = *P.ctr;
-        if (C.bdone) continue;
-        const uint32_t p = C.lvl & 1u;
-        const uint64_t cnt = C.nT[p];
+        if (__ldcg(&C.bdone)) continue;
+        const uint32_t p = __ldcg(&C.lvl) & 1u;
+        const uint64_t cnt = __ldcg(&C.nT[p]);
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
         const uint64_t *T = p ? P.T1 : P.T0;
         const uint32_t *dcur = p ? P.del1 : P.del0;
         uint32_t *dnext = p ? P.del0 : P.del1;
         for (uint64_t l = first; l < cnt; l += nworkers) {
-            const uint64_t t = T[l];
+            const uint64_t t = __ldcg(reinterpret_cast<const unsigned long long *>(&T[l]));
             const int64_t u = static_cast<int64_t>(static_cast<uint32_t>(t));
             const int64_t e = __ldg(&P.xadj[u]) + static_cast<int64_t>(t >> 32) * kBfsTaskEdges + lane;
             const bool has = e < __ldg(&P.xadj[u + 1]);
-            const uint32_t dl = lane < W ? dcur[static_cast<size_t>(u) * W + lane] : 0u;
+            const uint32_t dl = lane < W ? __ldcg(&dcur[static_cast<size_t>(u) * W + lane]) : 0u;
             const int32_t v = has ? __ldg(&P.adj[e]) : 0;
             uint32_t m[W];
             uint32_t any = 0;
@@ -1239,7 +1242,7 @@ __global__ void __launch_bounds__(kBlock) k_bfs_level(const DevProb *__restrict_
             if (__any_sync(kFull, any != 0)) {
                 uint32_t x[W];
 #pragma unroll
-                for (int k = 0; k < W; ++k) x[k] = m[k] ? P.vis[static_cast<size_t>(v) * W + k] : 0u;
+                for (int k = 0; k < W; ++k) x[k] = m[k] ? __ldcg(&P.vis[static_cast<size_t>(v) * W + k]) : 0u;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
                     const uint32_t nb = m[k] & ~x[k];
@@ -1266,37 +1269,43 @@ __global__ void __launch_bounds__(kBlock) k_bfs_level(const DevProb *__restrict_
     }
 }
 
+template <int R>
+__global__ void __launch_bounds__(kBlock) k_bfs_level(const DevProb *__restrict__ probs,
+                                                      const int32_t *__restrict__ act, int nact) {
+    bfs_level_phase<R>(probs, act, nact);
+}
+
 // After a level: counts and clears the consumed delta rows (one per vertex of the level, at its first task), and
 // turns the vertices that reached something new into the next level's tasks (clearing their flags).
-__global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restrict__ probs,
-                                                         const int32_t *__restrict__ act, int nact) {
+__device__ __forceinline__ void bfs_frontier_phase(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
+                                                   int nact) {
     const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
-        if (C.bdone) continue;
-        const uint32_t p = C.lvl & 1u;
+        if (__ldcg(&C.bdone)) continue;
+        const uint32_t p = __ldcg(&C.lvl) & 1u;
         const uint64_t *T = p ? P.T1 : P.T0;
         uint64_t *Tn = p ? P.T0 : P.T1;
         uint32_t *dcur = p ? P.del1 : P.del0;
-        const uint64_t nc = static_cast<uint64_t>(C.nT[p]) * P.W;
+        const uint64_t nc = static_cast<uint64_t>(__ldcg(&C.nT[p])) * P.W;
         const uint64_t cnt = nc;
         const uint64_t first = first_owned(tid, nthreads, base);
         base += cnt;
         unsigned long long added = 0;  // newly reached (v, j), each consumed exactly once
         for (uint64_t l = first; l < cnt; l += nthreads) {
             if (l < nc) {
-                const uint64_t t = T[l / P.W];
+                const uint64_t t = __ldcg(reinterpret_cast<const unsigned long long *>(&T[l / P.W]));
                 if (t >> 32) continue;
                 const size_t at = static_cast<size_t>(static_cast<uint32_t>(t)) * P.W + l % P.W;
-                added += __popc(dcur[at]);
+                added += __popc(__ldcg(&dcur[at]));
                 dcur[at] = 0;
             }
         }
         // the next level's tasks, one warp-aggregated reservation per round
-        const uint64_t nv = C.nV;
+        const uint64_t nv = __ldcg(&C.nV);
         const uint64_t vfirst = first_owned(tid, nthreads, base);
         base += nv;
         const uint64_t rounds = (nv + nthreads - 1) / nthreads;
@@ -1305,7 +1314,7 @@ __global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restri
             int32_t v = 0;
             uint32_t nt = 0;
             if (l < nv) {
-                v = P.Vn[l];
+                v = __ldcg(&P.Vn[l]);
                 atomicAnd(&P.Fb[v >> 5], ~(1u << (v & 31)));
                 const int64_t deg = P.xadj[v + 1] - P.xadj[v];
                 nt = deg > 0 ? static_cast<uint32_t>((deg + kBfsTaskEdges - 1) / kBfsTaskEdges) : 1u;
@@ -1328,22 +1337,103 @@ __global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restri
     }
 }
 
-__global__ void k_bfs_advance(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nact) return;
+__global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restrict__ probs,
+                                                         const int32_t *__restrict__ act, int nact) {
+    bfs_frontier_phase(probs, act, nact);
+}
+
+// Ends a level of problem act[q]: the next level's list becomes current, the search stops when it is empty (or at
+// the level limit).
+__device__ __forceinline__ void bfs_advance_one(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
+                                                int q) {
     const DevProb &P = probs[act[q]];
     DevCtr &C = *P.ctr;
-    if (C.bdone) return;
-    const uint32_t p = C.lvl & 1u;
+    if (__ldcg(&C.bdone)) return;
+    const uint32_t lvl = __ldcg(&C.lvl);
+    const uint32_t p = lvl & 1u;
     C.levels_total += 1;
-    const bool empty = C.nT[p ^ 1u] == 0;
-    const bool lim = C.lvl + 1 >= P.max_sweeps;
+    const bool empty = __ldcg(&C.nT[p ^ 1u]) == 0;
+    const bool lim = lvl + 1 >= P.max_sweeps;
     C.nT[p] = 0;
     C.nV = 0;
-    C.lvl += 1;
+    C.lvl = lvl + 1;
     if (empty || lim) {
         C.bdone = 1;
         C.btimeout = (!empty && lim) ? 1u : 0u;
+    }
+}
+
+__global__ void k_bfs_advance(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nact) bfs_advance_one(probs, act, q);
+}
+
+namespace {
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+}  // namespace
+
+// Grid-wide barrier for a cooperatively launched kernel (every block resident).  Each wait is bounded: a block that
+// gives up raises gb->fail, and every block leaves the kernel at its next barrier (returns false) instead of waiting
+// again, so a lost block cannot hang the device.
+__device__ __forceinline__ bool grid_sync(GridBar *gb) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = ld_acquire(&gb->fail) == 0;
+        if (ok) {
+            const unsigned int gen = ld_acquire(&gb->gen);
+            __threadfence();
+            if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+                atomicExch(&gb->count, 0u);
+                __threadfence();
+                atomicAdd(&gb->gen, 1u);
+            } else {
+                // spin first (a barrier normally opens within microseconds), then poll with short sleeps
+                for (uint32_t it = 0; ld_acquire(&gb->gen) == gen; ++it) {
+                    if (it >= kBarrierLimit || ld_acquire(&gb->fail)) {
+                        atomicExch(&gb->fail, 1u);
+                        ok = 0;
+                        break;
+                    }
+                    if (it >= 4096) __nanosleep(128);
+                }
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// A whole reachability search (every level until every listed problem is done) in one cooperative launch: level,
+// barrier, frontier, barrier, advance (block 0), barrier, stop test.
+// Marks every listed problem as failed by a lost barrier (bit 2 of its fault word).
+__device__ __forceinline__ void barrier_lost(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
+                                             int nact) {
+    for (int q = threadIdx.x; q < nact; q += blockDim.x) atomicOr(&probs[act[q]].ctr->fault, 4u);
+}
+
+constexpr int kRunBlock = 1024;  // threads per block of the persistent kernels (one block per SM: few barrier arrivals)
+
+template <int R>
+__global__ void __launch_bounds__(kRunBlock) k_bfs_run(const DevProb *__restrict__ probs,
+                                                       const int32_t *__restrict__ act, int nact, GridBar *gb) {
+    for (;;) {
+        bfs_level_phase<R>(probs, act, nact);
+        if (!grid_sync(gb)) return barrier_lost(probs, act, nact);
+        bfs_frontier_phase(probs, act, nact);
+        if (!grid_sync(gb)) return barrier_lost(probs, act, nact);
+        if (blockIdx.x == 0)
+            for (int q = threadIdx.x; q < nact; q += blockDim.x) bfs_advance_one(probs, act, q);
+        if (!grid_sync(gb)) return barrier_lost(probs, act, nact);
+        bool all = true;
+        for (int q = 0; q < nact && all; ++q) all = __ldcg(&probs[act[q]].ctr->bdone) != 0;
+        if (all) return;
     }
 }
 
@@ -1724,6 +1814,7 @@ __global__ void k_edge_thresholds(const float *__restrict__ p, int64_t m, uint32
 // Host-side launchers
 
 static int g_sms = 0;
+static int g_device = 0;
 static int g_variant = 0;     // propagation launch shape (IM_PROP_VARIANT)
 static int g_grid_warp = 0;   // blocks for warp-striped kernels
 static int g_grid_block = 0;  // blocks for block-striped kernels
@@ -1737,6 +1828,7 @@ cudaError_t configure(int device) {
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     g_sms = prop.multiProcessorCount;
+    g_device = device;
     g_grid_warp = prop.multiProcessorCount * occ;
     g_grid_block = prop.multiProcessorCount * 4;
     if (const char *v = getenv("IM_PROP_VARIANT")) g_variant = atoi(v);
@@ -1815,6 +1907,30 @@ void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cu
 }
 void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     IMK_R_SWITCH(R, (k_bfs_level<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
+}
+template <int R>
+static bool launch_bfs_run_r(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
+    static int grid = -1;
+    if (grid < 0) {
+        int coop = 0, occ = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g_device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs_run<R>, kRunBlock, 0);
+        grid = (coop && occ > 0) ? g_sms * std::min(occ, 2) : 0;
+    }
+    if (grid == 0) return false;
+    void *args[] = {const_cast<DevProb **>(&probs), const_cast<int32_t **>(&act), &nact, &gb};
+    if (cudaMemsetAsync(gb, 0, sizeof(GridBar), s) != cudaSuccess) return false;
+    if (cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_bfs_run<R>), dim3(grid), dim3(kRunBlock), args,
+                                    0, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
+    bool ok = false;
+    IMK_R_SWITCH(R, (ok = launch_bfs_run_r<RR>(probs, act, nact, gb, s)));
+    return ok;
 }
 void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_bfs_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);

@@ -183,6 +183,23 @@ def test_estimate_and_exact_sigma(ctx):
 
 # --- batch ------------------------------------------------------------------------------------------------------
 
+def test_persistent_search_matches_stepped(monkeypatch):
+    """Whole reachability searches in one cooperative launch (IM_PERSISTENT=1) give the stepped launches' result."""
+    probs = [workloads.batch_problem(i, max_scale=13) for i in (3, 7, 12)]
+    gs = [im.Graph.from_synth(p.graph, p.model, p.p, device="cuda") for p in probs]
+    prms = [im.params(R=p.R, K=p.K, eps_g=p.eps_g, eps_l=p.eps_l, seed=p.seed) for p in probs]
+    monkeypatch.setenv("IM_PERSISTENT", "1")
+    c1 = im.Context(0)
+    pers = c1.im_select_seeds_batch(gs, prms)
+    c1.close()
+    monkeypatch.delenv("IM_PERSISTENT")
+    c0 = im.Context(0)
+    step = c0.im_select_seeds_batch(gs, prms)
+    c0.close()
+    for a, b in zip(pers, step):
+        assert a["seeds"].tolist() == b["seeds"].tolist() and a["sigma_final"] == b["sigma_final"]
+
+
 def test_batch_same_R_problems_out_of_phase(ctx):
     """Problems of one R in different phases share every launch: while one pulls the first sweep of a (re)build,
     another pushes, and one tile may serve units of both in the same launch."""

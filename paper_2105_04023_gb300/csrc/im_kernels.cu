@@ -853,9 +853,10 @@ namespace {
 
 // Block-aggregated append of the set bits of one word per thread: ids (word_index*32 + bit) go to out[], the block
 // reserves its range with one atomic on *count.  All threads of the block must call it.
-__device__ __forceinline__ void block_append_bits(uint32_t w, int64_t word_index, int32_t *out, uint32_t *count) {
+__device__ __forceinline__ void block_append_bits(uint32_t w, int64_t word_index, int32_t *out, uint32_t *count,
+                                                  uint32_t *seg_base = nullptr, uint32_t *seg_len = nullptr) {
     __shared__ uint32_t s_warp[kWarpsPerBlock];
-    __shared__ uint32_t s_base;
+    __shared__ uint32_t s_base, s_run;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t c = __popc(w);
     uint32_t incl = c;
@@ -874,9 +875,12 @@ __device__ __forceinline__ void block_append_bits(uint32_t w, int64_t word_index
             run += x;
         }
         s_base = run ? atomicAdd(count, run) : 0;
+        s_run = run;
     }
     __syncthreads();
     uint32_t pos = s_base + s_warp[wib] + incl - c;
+    if (seg_base) *seg_base = s_base;
+    if (seg_len) *seg_len = s_run;
     while (w) {
         const int b = __ffs(w) - 1;
         w &= w - 1;
@@ -926,21 +930,29 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
                 uint32_t wh = 0;
                 for (uint32_t x = w; x; x &= x - 1) {
                     const int64_t v = i * 32 + __ffs(x) - 1;
-                    const uint4 *src = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R);
-                    uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R);
-#pragma unroll 4
-                    for (int k = 0; k < P.R / 16; ++k) dst[k] = src[k];
                     const uint64_t d = in_degree(P, v);
                     indeg += d;
                     if (d > kPushChunk) {
                         wh |= 1u << (__ffs(x) - 1);
+                        const uint4 *src = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R);
+                        uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R);
+                        for (int k = 0; k < P.R / 16; ++k) dst[k] = src[k];
                         const uint32_t nt = static_cast<uint32_t>((d + kPushChunk - 1) / kPushChunk);
                         const uint32_t at = atomicAdd(&P.ctr->nchg_hc, nt);
                         for (uint32_t c = 0; c < nt; ++c)
                             P.chg_hc[at + c] = (static_cast<uint64_t>(c) << 32) | static_cast<uint32_t>(v);
                     }
                 }
-                block_append_bits(w & ~wh, i, P.chg_list, &P.ctr->nchg_list);
+                uint32_t sb = 0, sn = 0;
+                block_append_bits(w & ~wh, i, P.chg_list, &P.ctr->nchg_list, &sb, &sn);
+                // the block copies the rows it just listed, consecutive threads on consecutive 16-byte chunks
+                const uint32_t CH = static_cast<uint32_t>(P.R / 16);
+#pragma unroll 4
+                for (uint32_t x = threadIdx.x; x < sn * CH; x += blockDim.x) {
+                    const int64_t v = P.chg_list[sb + x / CH];
+                    reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R)[x % CH] =
+                        reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R)[x % CH];
+                }
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) indeg += __shfl_xor_sync(kFull, indeg, off);

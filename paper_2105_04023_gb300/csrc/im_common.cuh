@@ -68,8 +68,7 @@ struct DevCtr {
     uint32_t bdone;      // 1 once the search found no new vertex
     uint32_t btimeout;   // 1 if it hit the level limit first
     uint32_t nT[2];      // search tasks by level parity
-    uint32_t nV;         // vertices that reached something new at the current level
-    uint32_t pad3;
+    uint32_t nVl[2];     // frontier vertices by level parity (those of the next level are added during a level)
     uint32_t pad1;
     unsigned long long reached;       // |{(v, j): v in R_{G_j}(S)}|
     unsigned long long levels_total;
@@ -134,7 +133,7 @@ struct DevProb {
     uint32_t *del0, *del1;     // n x W: bits newly reached at the previous level, by parity
     uint32_t *Fb;              // bit per vertex: reached something new at this level
     uint64_t *T0, *T1;         // search tasks by level parity: (chunk << 32) | vertex
-    int32_t *Vn;               // vertices that reached something new at the current level
+    int32_t *V0, *V1;          // frontier vertices by level parity
     uint32_t *inS;             // bit per vertex: in the seed set
     uint8_t *MS;               // R bytes: M_S'
     DevCtr *ctr;

@@ -315,7 +315,8 @@ void alloc_bfs(Prob &P, cudaStream_t s) {
     const size_t ntask = static_cast<size_t>(n + P.G->m / kBfsTaskEdges + 1);
     P.dp.T0 = mem.alloc<uint64_t>(ntask);
     P.dp.T1 = mem.alloc<uint64_t>(ntask);
-    P.dp.Vn = mem.alloc<int32_t>(n);
+    P.dp.V0 = mem.alloc<int32_t>(n);
+    P.dp.V1 = mem.alloc<int32_t>(n);
     P.has_bfs = true;
 }
 
@@ -1154,7 +1155,7 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     b += r(4 * words) * 2;                                   // L bits
     b += r(4 * n) + r(8 * (static_cast<uint64_t>(g.m) / 512 + 1));  // changed lists
     b += r(R) + r(8 * 4096);                                 // M_S', frontier log
-    b += r(4 * n * W) * 3 + r(4 * words) * 2 + r(4 * n);  // reach bits, frontier and seed-set bits, new vertices
+    b += r(4 * n * W) * 3 + r(4 * words) * 2 + r(4 * n) * 2;  // reach bits, frontier/seed-set bits, frontiers
     b += r(8 * (n + static_cast<uint64_t>(g.m) / kBfsTaskEdges + 1)) * 2;  // search tasks
     const uint64_t m1 = std::max<uint64_t>(static_cast<uint64_t>(g.m), 1);
     b += r(4 * W * m1);                                      // live-simulation masks of the edges

@@ -1174,7 +1174,9 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
         set_bit(P.inS, s);
         C.nT[0] = 0;
         C.nT[1] = 0;
-        C.nV = 0;
+        C.nVl[0] = 1;
+        C.nVl[1] = 0;
+        P.V0[0] = static_cast<int32_t>(s);
         bfs_tasks(P.T0, &C.nT[0], s, P.xadj[s + 1] - P.xadj[s]);
         C.lvl = 0;
         C.bdone = added ? 0u : 1u;
@@ -1199,6 +1201,7 @@ __global__ void k_seed_set(const DevProb *__restrict__ prob, const int32_t *__re
         if (w == 0) {
             const uint32_t prev = atomicOr(&P.inS[s >> 5], 1u << (s & 31));
             if (!((prev >> (s & 31)) & 1u)) {
+                P.V0[atomicAdd(&C.nVl[0], 1u)] = s;
                 bfs_tasks(P.T0, &C.nT[0], static_cast<uint32_t>(s), P.xadj[s + 1] - P.xadj[s]);
             }
         }
@@ -1273,9 +1276,9 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
             const unsigned mf = __ballot_sync(kFull, fresh);
             if (mf) {
                 uint32_t at = 0;
-                if (lane == 0) at = atomicAdd(&C.nV, static_cast<uint32_t>(__popc(mf)));
+                if (lane == 0) at = atomicAdd(&C.nVl[p ^ 1u], static_cast<uint32_t>(__popc(mf)));
                 at = __shfl_sync(kFull, at, 0);
-                if (fresh) P.Vn[at + __popc(mf & ((1u << lane) - 1u))] = v;
+                if (fresh) (p ? P.V0 : P.V1)[at + __popc(mf & ((1u << lane) - 1u))] = v;
             }
         }
     }
@@ -1287,8 +1290,8 @@ __global__ void __launch_bounds__(kBlock) k_bfs_level(const DevProb *__restrict_
     bfs_level_phase<R>(probs, act, nact);
 }
 
-// After a level: counts and clears the consumed delta rows (one per vertex of the level, at its first task), and
-// turns the vertices that reached something new into the next level's tasks (clearing their flags).
+// After a level: counts and clears the consumed delta rows (one per vertex of the level), and turns the vertices
+// that reached something new into the next level's tasks (clearing their flags).
 __device__ __forceinline__ void bfs_frontier_phase(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
                                                    int nact) {
     const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -1299,25 +1302,21 @@ __device__ __forceinline__ void bfs_frontier_phase(const DevProb *__restrict__ p
         const DevCtr &C = *P.ctr;
         if (__ldcg(&C.bdone)) continue;
         const uint32_t p = __ldcg(&C.lvl) & 1u;
-        const uint64_t *T = p ? P.T1 : P.T0;
+        const int32_t *Vc = p ? P.V1 : P.V0;
+        const int32_t *Vx = p ? P.V0 : P.V1;
         uint64_t *Tn = p ? P.T0 : P.T1;
         uint32_t *dcur = p ? P.del1 : P.del0;
-        const uint64_t nc = static_cast<uint64_t>(__ldcg(&C.nT[p])) * P.W;
-        const uint64_t cnt = nc;
+        const uint64_t cnt = static_cast<uint64_t>(__ldcg(&C.nVl[p])) * P.W;
         const uint64_t first = first_owned(tid, nthreads, base);
         base += cnt;
         unsigned long long added = 0;  // newly reached (v, j), each consumed exactly once
         for (uint64_t l = first; l < cnt; l += nthreads) {
-            if (l < nc) {
-                const uint64_t t = __ldcg(reinterpret_cast<const unsigned long long *>(&T[l / P.W]));
-                if (t >> 32) continue;
-                const size_t at = static_cast<size_t>(static_cast<uint32_t>(t)) * P.W + l % P.W;
-                added += __popc(__ldcg(&dcur[at]));
-                dcur[at] = 0;
-            }
+            const size_t at = static_cast<size_t>(__ldcg(&Vc[l / P.W])) * P.W + l % P.W;
+            added += __popc(__ldcg(&dcur[at]));
+            dcur[at] = 0;
         }
         // the next level's tasks, one warp-aggregated reservation per round
-        const uint64_t nv = __ldcg(&C.nV);
+        const uint64_t nv = __ldcg(&C.nVl[p ^ 1u]);
         const uint64_t vfirst = first_owned(tid, nthreads, base);
         base += nv;
         const uint64_t rounds = (nv + nthreads - 1) / nthreads;
@@ -1326,7 +1325,7 @@ __device__ __forceinline__ void bfs_frontier_phase(const DevProb *__restrict__ p
             int32_t v = 0;
             uint32_t nt = 0;
             if (l < nv) {
-                v = __ldcg(&P.Vn[l]);
+                v = __ldcg(&Vx[l]);
                 atomicAnd(&P.Fb[v >> 5], ~(1u << (v & 31)));
                 const int64_t deg = P.xadj[v + 1] - P.xadj[v];
                 nt = deg > 0 ? static_cast<uint32_t>((deg + kBfsTaskEdges - 1) / kBfsTaskEdges) : 1u;
@@ -1367,7 +1366,7 @@ __device__ __forceinline__ void bfs_advance_one(const DevProb *__restrict__ prob
     const bool empty = __ldcg(&C.nT[p ^ 1u]) == 0;
     const bool lim = lvl + 1 >= P.max_sweeps;
     C.nT[p] = 0;
-    C.nV = 0;
+    C.nVl[p] = 0;
     C.lvl = lvl + 1;
     if (empty || lim) {
         C.bdone = 1;

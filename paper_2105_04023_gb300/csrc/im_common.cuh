@@ -31,12 +31,13 @@ struct UnitD {
     int32_t pad;
 };
 
-// Grid-wide barrier of the persistent (cooperatively launched) kernels: arrivals and a generation count.
+// Grid-wide barrier of the persistent (cooperatively launched) kernels: arrivals and a generation count; and the
+// finished-block count of the frontier kernels.
 struct GridBar {
     unsigned int count;
     unsigned int gen;
     unsigned int fail;   // a block gave up waiting (every block then leaves the kernel)
-    unsigned int pad;
+    unsigned int tail;   // blocks of a frontier launch that finished: the last one ends the sweep or level
 };
 constexpr uint32_t kBarrierLimit = 1u << 20;  // polls of one barrier wait (under a second in all) before giving up
 

@@ -620,9 +620,8 @@ struct Engine {
             phase(0, [&]() {
                 for (int c = 0; c < chunk; ++c) {
                     timed_prop(byR, first_full && c == 0);
-                    launch_frontier(d_probs, dptr(all), all.count, s);
-                    launch_advance(d_probs, dptr(all), all.count, s);
-                    ctx->launches += 2;
+                    launch_frontier(d_probs, dptr(all), all.count, ctx->d_gbar, s);
+                    ctx->launches += 1;
                 }
             });
         });
@@ -655,10 +654,8 @@ struct Engine {
                 }
                 for (int c = 0; c < chunk; ++c) {
                     for (auto &rl : byR) launch_bfs_level(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
-                    ctx->launches += static_cast<int64_t>(byR.size()) - 1;
-                    launch_bfs_frontier(d_probs, dptr(all), all.count, s);
-                    launch_bfs_advance(d_probs, dptr(all), all.count, s);
-                    ctx->launches += 3;
+                    launch_bfs_frontier(d_probs, dptr(all), all.count, ctx->d_gbar, s);
+                    ctx->launches += static_cast<int64_t>(byR.size()) + 1;
                 }
             });
         });

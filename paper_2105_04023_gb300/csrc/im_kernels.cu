@@ -11,9 +11,10 @@
 //                 per run (k_live_masks) and kept as (target, simulation) pairs for edges live in few simulations
 //                 (k_pair_counts, k_pair_fill), the hashed test runs in the sweep for the other edges
 //   k_combine     Algorithm 2, the same sweep for rows split over several warps
-//   k_frontier, k_advance   Algorithm 2, the live sets L and L' (and the copy a push sweep needs), the stop test
+//   k_frontier    Algorithm 2, the live sets L and L' (and the copy a push sweep needs); its last block applies
+//                 the stop test (eps_c)
 //   k_scan, k_choose                          Algorithm 1, argmax of Estimate(Merge(M_S', M_v)) (Eq. 2-3)
-//   k_bfs_*                                   Algorithm 1, reachability set of S in every simulation, sigma
+//   k_bfs_level, k_bfs_frontier (k_bfs_run)  Algorithm 1, reachability set of S in every simulation, sigma
 //   k_merge                                   Algorithm 1, M_S' <- Merge(M_S', M_s)
 #include <algorithm>
 #include <cstdlib>
@@ -901,8 +902,26 @@ __device__ __forceinline__ bool next_is_push(const DevProb &, const DevCtr &) { 
 // After sweep t: clear L_t's bits (the buffer L_{t+2} will be written to) and, when the next sweep is a push
 // sweep, compact L_{t+1} into the changed-vertex lists (whole vertices, or kPushChunk-in-edge chunks of those
 // with more) and copy each changed row into the buffer the next sweep writes, so that it holds every row.
+__device__ __forceinline__ void advance_one(const DevProb &P);
+
+// True in the last block of the launch to get here (after every block's writes are visible to it).
+__device__ __forceinline__ bool last_block(GridBar *gb) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&gb->tail, 1u) == gridDim.x - 1;
+        if (s_last) {
+            gb->tail = 0;
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
 __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__ probs,
-                                                     const int32_t *__restrict__ act, int nact) {
+                                                     const int32_t *__restrict__ act, int nact, GridBar *gb) {
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
@@ -959,17 +978,17 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
             if ((threadIdx.x & 31) == 0 && indeg) atomicAdd(&P.ctr->chg_indeg, indeg);
         }
     }
+    if (last_block(gb))
+        for (int q = threadIdx.x; q < nact; q += blockDim.x) advance_one(probs[act[q]]);
 }
 
-// Ends sweep t: stop test (|L'| <= eps_c |V| or the sweep limit), mode of the next sweep, counter resets.
-__global__ void k_advance(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nact) return;
-    const DevProb &P = probs[act[q]];
+// Ends sweep t: stop test (|L'| <= eps_c |V| or the sweep limit), mode of the next sweep, counter resets.  Run by
+// the last block of the frontier kernel to finish.
+__device__ __forceinline__ void advance_one(const DevProb &P) {
     DevCtr &C = *P.ctr;
-    if (C.done) return;
-    const uint32_t t = C.t;
-    const uint32_t nchg = C.nchg;
+    if (__ldcg(&C.done)) return;
+    const uint32_t t = __ldcg(&C.t);
+    const uint32_t nchg = __ldcg(&C.nchg);
     if (static_cast<int32_t>(t + 1) < P.flog_cap) P.flog[t + 1] = nchg;
     C.sweeps_total += 1;
     const bool stop = nchg <= P.stop_thr;
@@ -980,10 +999,10 @@ __global__ void k_advance(const DevProb *__restrict__ probs, const int32_t *__re
         C.res_par = (t + 1) & 1u;
     }
     // visits of the next sweep (Algorithm 2's work count): every edge (u, v) with v in L_{t+1}, in every simulation
-    if (!C.done) C.visits += C.chg_indeg * static_cast<unsigned long long>(P.R);
+    if (!C.done) C.visits += __ldcg(&C.chg_indeg) * static_cast<unsigned long long>(P.R);
     C.full = next_is_push(P, C) ? 0u : 1u;
-    C.npush_l = C.full ? 0u : C.nchg_list;
-    C.npush_h = C.full ? 0u : C.nchg_hc;
+    C.npush_l = C.full ? 0u : __ldcg(&C.nchg_list);
+    C.npush_h = C.full ? 0u : __ldcg(&C.nchg_hc);
     C.nchg = 0;
     C.nchg_list = 0;
     C.nchg_hc = 0;
@@ -1348,9 +1367,14 @@ __device__ __forceinline__ void bfs_frontier_phase(const DevProb *__restrict__ p
     }
 }
 
+__device__ __forceinline__ void bfs_advance_one(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
+                                                int q);
+
 __global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restrict__ probs,
-                                                         const int32_t *__restrict__ act, int nact) {
+                                                         const int32_t *__restrict__ act, int nact, GridBar *gb) {
     bfs_frontier_phase(probs, act, nact);
+    if (last_block(gb))
+        for (int q = threadIdx.x; q < nact; q += blockDim.x) bfs_advance_one(probs, act, q);
 }
 
 // Ends a level of problem act[q]: the next level's list becomes current, the search stops when it is empty (or at
@@ -1374,10 +1398,6 @@ __device__ __forceinline__ void bfs_advance_one(const DevProb *__restrict__ prob
     }
 }
 
-__global__ void k_bfs_advance(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < nact) bfs_advance_one(probs, act, q);
-}
 
 namespace {
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
@@ -1898,11 +1918,8 @@ void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cuda
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     IMK_R_SWITCH(R, (launch_combines<RR>(probs, act, nact, s)));
 }
-void launch_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    k_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);
-}
-void launch_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    k_advance<<<(nact + 127) / 128, 128, 0, s>>>(probs, act, nact);
+void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
+    k_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact, gb);
 }
 void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_init<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
@@ -1943,11 +1960,8 @@ bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, G
     IMK_R_SWITCH(R, (ok = launch_bfs_run_r<RR>(probs, act, nact, gb, s)));
     return ok;
 }
-void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    k_bfs_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);
-}
-void launch_bfs_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    k_bfs_advance<<<(nact + 127) / 128, 128, 0, s>>>(probs, act, nact);
+void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
+    k_bfs_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact, gb);
 }
 void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_merge<<<nact, 128, 0, s>>>(probs, act, nact);

@@ -15,16 +15,16 @@ int grid_warp();
 void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
-void launch_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
-void launch_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+// Ends a sweep: frontier lists and row copies, then (last block) the stop test and counter resets.
+void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
 void launch_scan(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t step, cudaStream_t s);
 void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cudaStream_t s);
 void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 // A whole search in one cooperative launch; false if the device cannot run it (the caller then steps levels).
 bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
-void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
-void launch_bfs_advance(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+// Ends a search level: consumed rows counted, next tasks built, then (last block) the level advances.
+void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
 void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned long long *gsum, cudaStream_t s);
 

@@ -1933,8 +1933,18 @@ void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t s
 void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cudaStream_t s) {
     k_seed_set<<<(k * W + 255) / 256, 256, 0, s>>>(prob, seeds, k);
 }
+template <int R>
+static void launch_bfs_level_r(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    static int grid = 0;  // one wave: the SM count times the blocks that fit
+    if (grid == 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs_level<R>, kBlock, 0);
+        grid = g_sms * (occ > 0 ? occ : 1);
+    }
+    k_bfs_level<R><<<grid, kBlock, 0, s>>>(probs, act, nact);
+}
 void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    IMK_R_SWITCH(R, (k_bfs_level<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
+    IMK_R_SWITCH(R, (launch_bfs_level_r<RR>(probs, act, nact, s)));
 }
 template <int R>
 static bool launch_bfs_run_r(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {

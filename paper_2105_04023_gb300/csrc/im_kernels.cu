@@ -567,22 +567,25 @@ __device__ __forceinline__ void mark_changed(uint32_t *Lnext, int64_t u, Stats &
 // A push sweep (Algorithm 2 with a small L, in the other direction): every changed vertex v merges M_v into the
 // rows of its in-neighbours u, M'_u[j] = max(M'_u[j], M_v[j]) for every sampled (u, v, j).  The next buffer already
 // holds M_u for every row (rows of L were copied after the previous sweep), so it is updated in place with
-// compare-and-swap; reads come from the current buffer only (Jacobi).  A tile takes one unit: a changed vertex,
-// or a chunk of kPushChunk in-edges of one with more; its row of M_v is staged in shared memory.
+// compare-and-swap; reads come from the current buffer only (Jacobi).  A whole warp takes one unit, a changed
+// vertex or a chunk of kPushChunk in-edges of one with more (tiles of one warp busy with units of different shapes
+// would run their divergent paths one after the other); its row M_v is staged in shared memory.  Pairs take all 32
+// lanes, four per lane in flight; dense in-edges are merged by the warp's NG lane groups, two per group a round.
 template <int R>
-__device__ void push_problem_t(const DevProb &P, uint32_t t, uint64_t cnt, uint64_t first, uint64_t nworkers,
-                               unsigned tm, int li, uint32_t *tile_smem) {
+__device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint64_t first, uint64_t nworkers,
+                               int lane, uint32_t *warp_smem) {
     using Gm = Geo<R>;
-    constexpr int G = Gm::G;
+    constexpr int G = Gm::G, NG = Gm::NG;
     constexpr int W = R / 32;
+    const int g = lane / G, li = lane % G;
+    const unsigned tm = tile_mask<R>(g);
     const bool par = t & 1u;
     const uint8_t *Mcur = par ? P.M1 : P.M0;
     uint8_t *Mnext = par ? P.M0 : P.M1;
     uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
-    uint8_t *srow = reinterpret_cast<uint8_t *>(tile_smem);
+    uint8_t *srow = reinterpret_cast<uint8_t *>(warp_smem);
     unsigned int *fault = &P.ctr->fault;
     const uint64_t nl = P.ctr->npush_l;
-    const int src0 = (threadIdx.x & 31) - li;  // first lane of this tile
     Stats st;
     for (uint64_t l = first; l < cnt; l += nworkers) {
         int64_t v, p0, p1, d0, d1;
@@ -604,19 +607,18 @@ __device__ void push_problem_t(const DevProb &P, uint32_t t, uint64_t cnt, uint6
             d0 = __ldg(&P.idofs[k0]);
             d1 = __ldg(&P.idofs[k1]);
         }
+        const uint4 *vrow = reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(v) * R);
+        for (int c = lane; c < Gm::CH; c += 32) reinterpret_cast<uint4 *>(srow)[c] = __ldg(vrow + c);
         uint4 rowc[Gm::CPL];
 #pragma unroll
-        for (int c = 0; c < Gm::CPL; ++c) {
-            rowc[c] = __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(v) * R) + li + G * c);
-            reinterpret_cast<uint4 *>(srow)[li + G * c] = rowc[c];
-        }
-        __syncwarp(tm);
-        for (int64_t p = p0 + li; p < p1; p += 4 * G) {
+        for (int c = 0; c < Gm::CPL; ++c) rowc[c] = __ldg(vrow + li + G * c);
+        __syncwarp();
+        for (int64_t p = p0 + lane; p < p1; p += 128) {
             uint32_t *addr[4];
             uint32_t cand[4], old[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int64_t q = p + G * k;
+                const int64_t q = p + 32 * k;
                 cand[k] = 0;
                 addr[k] = nullptr;
                 if (q < p1) {
@@ -634,59 +636,62 @@ __device__ void push_problem_t(const DevProb &P, uint32_t t, uint64_t cnt, uint6
                     mark_changed(Lnext, (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R, st);
             }
         }
-        // dense in-edges: the tile's lanes fetch up to G of them at once, then merge them two by two
-        for (int64_t db = d0; db < d1; db += G) {
-            const int nb = d1 - db < G ? static_cast<int>(d1 - db) : G;
+        // dense in-edges: the warp fetches up to 32 of them at once; group g merges edges i + g and i + NG + g
+        for (int64_t db = d0; db < d1; db += 32) {
+            const int nb = d1 - db < 32 ? static_cast<int>(d1 - db) : 32;
             int32_t my_u = 0;
             uint32_t my_e = 0;
-            if (li < nb) {
-                my_u = __ldg(&P.idu[db + li]);
-                my_e = __ldg(&P.ide[db + li]);
+            if (lane < nb) {
+                my_u = __ldg(&P.idu[db + lane]);
+                my_e = __ldg(&P.ide[db + lane]);
             }
-            for (int i = 0; i < nb; i += 2) {
+            for (int i = 0; i < nb; i += 2 * NG) {
                 int32_t u[2];
-                bool grew[2] = {false, false};
+                bool ok[2], grew[2] = {false, false};
                 uint32_t m[2][Gm::CPL];
                 uint4 o[2][Gm::CPL];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    const int ii = i + r < nb ? i + r : i;
-                    u[r] = __shfl_sync(tm, my_u, src0 + ii);
-                    const uint32_t e = __shfl_sync(tm, my_e, src0 + ii);
+                    const int ii = i + g + r * NG;
+                    ok[r] = ii < nb;
+                    u[r] = __shfl_sync(kFull, my_u, ok[r] ? ii : 0);
+                    const uint32_t e = __shfl_sync(kFull, my_e, ok[r] ? ii : 0);
 #pragma unroll
                     for (int c = 0; c < Gm::CPL; ++c) {
                         const int ch = li + G * c;
-                        m[r][c] = (i + r < nb) ? (__ldg(&P.live[static_cast<size_t>(e) * W + (ch >> 1)]) >>
-                                                  (16 * (ch & 1)))
-                                               : 0u;
-                        o[r][c] = __ldcg(reinterpret_cast<const uint4 *>(Mnext + static_cast<size_t>(u[r]) * R) + ch);
+                        m[r][c] = ok[r] ? (__ldg(&P.live[static_cast<size_t>(e) * W + (ch >> 1)]) >> (16 * (ch & 1)))
+                                        : 0u;
+                        o[r][c] = ok[r] ? __ldcg(reinterpret_cast<const uint4 *>(Mnext + static_cast<size_t>(u[r]) * R) +
+                                                 ch)
+                                        : make_uint4(0, 0, 0, 0);
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
+                    if (ok[r]) {
 #pragma unroll
-                    for (int c = 0; c < Gm::CPL; ++c) {
-                        uint32_t *dst = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u[r]) * R) +
-                                        4 * (li + G * c);
-                        const uint32_t mm = m[r][c];
-                        grew[r] |= word_max(dst + 0, o[r][c].x, rowc[c].x & nibble_bytes(mm & 0xFu), fault);
-                        grew[r] |= word_max(dst + 1, o[r][c].y, rowc[c].y & nibble_bytes((mm >> 4) & 0xFu), fault);
-                        grew[r] |= word_max(dst + 2, o[r][c].z, rowc[c].z & nibble_bytes((mm >> 8) & 0xFu), fault);
-                        grew[r] |= word_max(dst + 3, o[r][c].w, rowc[c].w & nibble_bytes((mm >> 12) & 0xFu), fault);
+                        for (int c = 0; c < Gm::CPL; ++c) {
+                            uint32_t *dst = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u[r]) * R) +
+                                            4 * (li + G * c);
+                            const uint32_t mm = m[r][c];
+                            grew[r] |= word_max(dst + 0, o[r][c].x, rowc[c].x & nibble_bytes(mm & 0xFu), fault);
+                            grew[r] |= word_max(dst + 1, o[r][c].y, rowc[c].y & nibble_bytes((mm >> 4) & 0xFu), fault);
+                            grew[r] |= word_max(dst + 2, o[r][c].z, rowc[c].z & nibble_bytes((mm >> 8) & 0xFu), fault);
+                            grew[r] |= word_max(dst + 3, o[r][c].w, rowc[c].w & nibble_bytes((mm >> 12) & 0xFu), fault);
+                        }
                     }
                     if (__any_sync(tm, grew[r]) && li == 0) mark_changed(Lnext, u[r], st);
                 }
             }
         }
-        if (li == 0)
+        if (lane == 0)
             st.bytes += R + 32 + 10 * static_cast<uint64_t>(p1 - p0) + (12 + W * 4 + R) * static_cast<uint64_t>(d1 - d0);
-        __syncwarp(tm);
+        __syncwarp();
     }
-    // the staged rows shared the tile's sparse accumulators, which a pulling unit of another problem in the same
-    // launch expects to find zero
-    for (int k = li; k < R / 16; k += G) reinterpret_cast<uint4 *>(srow)[k] = make_uint4(0, 0, 0, 0);
-    __syncwarp(tm);
-    // rows are marked by any lane
+    // the staged rows shared the sparse accumulators, which a pulling unit of another problem in the same launch
+    // expects to find zero
+    for (int k = lane; k < R / 16; k += 32) reinterpret_cast<uint4 *>(srow)[k] = make_uint4(0, 0, 0, 0);
+    __syncwarp();
     if (st.nchg) atomicAdd(&P.ctr->nchg, st.nchg);
     if (st.bytes) atomicAdd(&P.ctr->bytes, st.bytes);
 }
@@ -702,8 +707,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restric
     uint32_t *acc32 = reinterpret_cast<uint32_t *>(gather_smem) + (static_cast<size_t>(wib) * Gm::NG + g) * R;
     for (int k = li; k < R; k += Gm::G) acc32[k] = 0;
     __syncwarp(tm);
-    const uint64_t worker = (static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib) * Gm::NG + g;
-    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock * Gm::NG;
+    const uint64_t wworker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nwworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    const uint64_t worker = wworker * Gm::NG + g;  // tiles for pulls, whole warps for pushes
+    const uint64_t nworkers = nwworkers * Gm::NG;
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
@@ -711,13 +718,14 @@ __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restric
         if (C.done) continue;
         const SweepWork W = sweep_work(P);
         const uint64_t cnt = C.full ? W.nlight + W.ntask : static_cast<uint64_t>(C.npush_l) + C.npush_h;
-        const uint64_t first = first_owned(worker, nworkers, base);
+        const uint64_t first = C.full ? first_owned(worker, nworkers, base) : first_owned(wworker, nwworkers, base);
         base += cnt;
         if (first >= cnt) continue;
         if (C.full)
             prop_problem_t<R>(P, C.t, W, cnt, first, nworkers, tm, li, acc32);
         else
-            push_problem_t<R>(P, C.t, cnt, first, nworkers, tm, li, acc32);
+            push_problem_w<R>(P, C.t, cnt, first, nwworkers, lane,
+                              reinterpret_cast<uint32_t *>(gather_smem) + static_cast<size_t>(wib) * Gm::NG * R);
     }
 }
 

@@ -61,8 +61,8 @@ struct im_ctx {
     size_t h_act_cap = 0;
     int32_t *d_act = nullptr;
     size_t d_act_cap = 0;
-    int sweep_chunk = 4;
-    int level_chunk = 4;
+    int sweep_chunk = 8;   // sweeps enqueued per engine tick (the counters are read back once a tick)
+    int level_chunk = 16;  // search levels enqueued per engine tick
     GridBar *d_gbar = nullptr;  // barrier of the persistent kernels
     // run whole searches in one cooperative launch (IM_PERSISTENT=1); measured no faster than level-by-level
     // launches on the R-MAT workloads, whose levels are dominated by their own dependent loads, so off by default

@@ -1804,15 +1804,41 @@ __global__ void k_scan_blocks(const int32_t *__restrict__ in, int64_t n, int64_t
     }
 }
 
-__global__ void k_scan_sums(int64_t *__restrict__ block_sums, int64_t nb, int64_t *__restrict__ total_out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t run = 0;
-    for (int64_t b = 0; b < nb; ++b) {
+// Exclusive scan of the block sums in one block of kSumThreads threads: each takes a contiguous slice, the slice
+// totals are scanned across the block, and each thread rewrites its slice.
+constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(kSumThreads) k_scan_sums(int64_t *__restrict__ block_sums, int64_t nb,
+                                                          int64_t *__restrict__ total_out) {
+    __shared__ int64_t s_warp[kSumThreads / 32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t per = (nb + kSumThreads - 1) / kSumThreads;
+    const int64_t b0 = threadIdx.x * per, b1 = b0 + per < nb ? b0 + per : nb;
+    int64_t sum = 0;
+    for (int64_t b = b0; b < b1; ++b) sum += block_sums[b];
+    int64_t incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) s_warp[wib] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < kSumThreads / 32; ++i) {
+            const int64_t x = s_warp[i];
+            s_warp[i] = run;
+            run += x;
+        }
+        *total_out = run;
+    }
+    __syncthreads();
+    int64_t run = s_warp[wib] + incl - sum;
+    for (int64_t b = b0; b < b1; ++b) {
         const int64_t x = block_sums[b];
         block_sums[b] = run;
         run += x;
     }
-    *total_out = run;
 }
 
 __global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *__restrict__ block_sums) {
@@ -1926,8 +1952,10 @@ void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cuda
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     IMK_R_SWITCH(R, (launch_combines<RR>(probs, act, nact, s)));
 }
+// The frontier kernels run one block per SM: their work is light, and their last block is found by one atomic per
+// block.
 void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
-    k_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact, gb);
+    k_frontier<<<g_sms, kBlock, 0, s>>>(probs, act, nact, gb);
 }
 void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_init<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
@@ -1979,7 +2007,7 @@ bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, G
     return ok;
 }
 void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
-    k_bfs_frontier<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact, gb);
+    k_bfs_frontier<<<g_sms, kBlock, 0, s>>>(probs, act, nact, gb);
 }
 void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_merge<<<nact, 128, 0, s>>>(probs, act, nact);
@@ -2044,7 +2072,7 @@ int64_t scan_block_count(int64_t n) {
 int launch_exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums, cudaStream_t s) {
     const int64_t nb = scan_block_count(n);
     if (nb > 0) k_scan_blocks<<<static_cast<unsigned>(nb), kBlock, 0, s>>>(in, n, out, block_sums);
-    k_scan_sums<<<1, 32, 0, s>>>(block_sums, nb, out + n);
+    k_scan_sums<<<1, kSumThreads, 0, s>>>(block_sums, nb, out + n);
     if (nb > 1) k_scan_add<<<g_grid_block, kBlock, 0, s>>>(out, n, block_sums);
     return 1 + (nb > 0 ? 1 : 0) + (nb > 1 ? 1 : 0);
 }

@@ -129,7 +129,8 @@ struct DevProb {
     const UnitD *rdesc;        // n: sweep unit of each row (used for light rows)
     const UnitD *tdesc;        // n_tasks: sweep unit of each task
     int32_t dense_min;
-    int32_t pad2;
+    uint32_t pull_sweeps;      // sweeps 0 .. pull_sweeps-1 pull into every row, later ones push
+
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
     uint32_t *del0, *del1;     // n x W: bits newly reached at the previous level, by parity
     uint32_t *Fb;              // bit per vertex: reached something new at this level

@@ -64,6 +64,7 @@ struct im_ctx {
     int sweep_chunk = 8;   // sweeps enqueued per engine tick (the counters are read back once a tick)
     int level_chunk = 16;  // search levels enqueued per engine tick
     GridBar *d_gbar = nullptr;  // barrier of the persistent kernels
+    int pull_sweeps = 1;        // sweeps of a diffusion that pull into every row before pushes take over
     // run whole searches in one cooperative launch (IM_PERSISTENT=1); measured no faster than level-by-level
     // launches on the R-MAT workloads, whose levels are dominated by their own dependent loads, so off by default
     bool persistent = false;
@@ -335,6 +336,7 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     cudaStream_t s = ctx->stream;
     if (m >= (int64_t(1) << 32)) fail(IM_EINVAL, "graphs with 2^32 or more edges are not supported");
     d.dense_min = dense_min_for(P.prm.R);
+    d.pull_sweeps = static_cast<uint32_t>(ctx->pull_sweeps);
     d.live = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(m, 1)) * W);
     int64_t *pofs = mem.alloc<int64_t>(m + 1, true);
     int64_t *dofs = mem.alloc<int64_t>(m + 1, true);
@@ -619,7 +621,7 @@ struct Engine {
         pending.push_back([this, byR, all, chunk, first_full, s]() {
             phase(0, [&]() {
                 for (int c = 0; c < chunk; ++c) {
-                    timed_prop(byR, first_full && c == 0);
+                    timed_prop(byR, first_full && c < ctx->pull_sweeps);
                     launch_frontier(d_probs, dptr(all), all.count, ctx->d_gbar, s);
                     ctx->launches += 1;
                 }
@@ -965,6 +967,9 @@ im_status im_ctx_create(int device, void *cuda_stream, im_ctx **out) {
     if (const char *v = std::getenv("IM_SWEEP_CHUNK")) ctx->sweep_chunk = std::max(1, std::atoi(v));
     if (const char *v = std::getenv("IM_LEVEL_CHUNK")) ctx->level_chunk = std::max(1, std::atoi(v));
     if (const char *v = std::getenv("IM_PERSISTENT")) ctx->persistent = std::atoi(v) != 0;
+    if (const char *v = std::getenv("IM_PULL_SWEEPS")) ctx->pull_sweeps = std::max(1, std::min(8, std::atoi(v)));
+    // every pulling sweep of a diffusion falls in the tick that starts it (split rows are combined only there)
+    ctx->pull_sweeps = std::min(ctx->pull_sweeps, ctx->sweep_chunk);
     if (cudaMalloc(&ctx->d_gbar, sizeof(GridBar)) != cudaSuccess ||
         cudaMemset(ctx->d_gbar, 0, sizeof(GridBar)) != cudaSuccess) {
         cudaGetLastError();

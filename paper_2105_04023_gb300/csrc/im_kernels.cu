@@ -902,8 +902,11 @@ __device__ __forceinline__ bool sweep_stops(const DevProb &P, const DevCtr &C) {
     return C.nchg <= P.stop_thr || C.t + 1 >= P.max_sweeps;
 }
 
-// Every sweep after the first (where L = V and every row is pulled) pushes from L'.
-__device__ __forceinline__ bool next_is_push(const DevProb &, const DevCtr &) { return true; }
+// The first pull_sweeps sweeps pull into every row (sweep 0 has L = V, and the next ones still have most of V in L);
+// every later sweep pushes from L'.  Called after sweep C.t.
+__device__ __forceinline__ bool next_is_push(const DevProb &P, const DevCtr &C) {
+    return __ldcg(&C.t) + 1 >= P.pull_sweeps;
+}
 
 }  // namespace
 
@@ -953,6 +956,8 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
                 w = Lnew[i];
             }
             unsigned long long indeg = 0;  // in-edges into L': the next sweep's work count
+            if (!push_next)
+                for (uint32_t x = w; x; x &= x - 1) indeg += in_degree(P, i * 32 + __ffs(x) - 1);
             if (push_next) {
                 uint32_t wh = 0;
                 for (uint32_t x = w; x; x &= x - 1) {

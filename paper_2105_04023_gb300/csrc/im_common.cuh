@@ -16,7 +16,6 @@ constexpr int kBigTasks = 32;        // split rows with more tasks are merged by
 constexpr int kBfsTaskEdges = 32;    // out-edges per task of a search-frontier vertex (one warp, one edge a lane)
 constexpr int kPushChunk = 1024;     // a changed vertex pushes its in-edges in units of at most this many
 constexpr int kCasLimit = 1024;      // compare-and-swap tries of one register-word update before it counts as a fault
-constexpr int kPfxShift = 17;        // sampling words are compared on their top 15 bits first
 
 enum Model : int32_t { kIC = 0, kWC = 1, kPerEdge = 2 };
 
@@ -68,9 +67,9 @@ struct DevCtr {
     uint32_t lvl;        // level of the current search
     uint32_t bdone;      // 1 once the search found no new vertex
     uint32_t btimeout;   // 1 if it hit the level limit first
+    uint32_t lvl0;       // level at which the current search started
     uint32_t nT[2];      // search tasks by level parity
-    uint32_t nVl[2];     // frontier vertices by level parity (those of the next level are added during a level)
-    uint32_t pad1;
+    uint32_t nVl[3];     // frontier vertices by level mod 3 (those of the next level are added during a level)
     unsigned long long reached;       // |{(v, j): v in R_{G_j}(S)}|
     unsigned long long levels_total;
 };
@@ -101,7 +100,6 @@ struct DevProb {
     const uint32_t *T_edge;    // per-edge model: threshold per edge
     const uint8_t *ok_edge;    // per-edge model: p > 0
     const uint32_t *X;         // sampling words X_r (Eq. 5)
-    const uint32_t *xpfx;      // 2^15 bits: some X_r has this value of X_r >> kPfxShift
     const uint32_t *Y;         // initialisation words ("hash(j)" of Algorithm 1)
     uint8_t *M0, *M1;          // register buffers (Jacobi pair)
     uint8_t *part;             // n_tasks x R partial maxima of heavy-row tasks
@@ -132,10 +130,10 @@ struct DevProb {
     uint32_t pull_sweeps;      // sweeps 0 .. pull_sweeps-1 pull into every row, later ones push
 
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
-    uint32_t *del0, *del1;     // n x W: bits newly reached at the previous level, by parity
-    uint32_t *Fb;              // bit per vertex: reached something new at this level
-    uint64_t *T0, *T1;         // search tasks by level parity: (chunk << 32) | vertex
-    int32_t *V0, *V1;          // frontier vertices by level parity
+    uint32_t *del[3];          // n x W: bits newly reached at the previous level, by level mod 3
+    uint32_t *lstamp;          // per vertex: 1 + the last level that listed it
+    int4 *T[2];                // search tasks by level parity: {first edge (lo, hi), vertex, edge count}
+    int32_t *V[3];             // frontier vertices by level mod 3
     uint32_t *inS;             // bit per vertex: in the seed set
     uint8_t *MS;               // R bytes: M_S'
     DevCtr *ctr;

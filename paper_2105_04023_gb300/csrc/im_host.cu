@@ -308,16 +308,13 @@ void alloc_bfs(Prob &P, cudaStream_t s) {
     DevMem &mem = *P.mem;
     const int64_t words = (n + 31) / 32;
     P.dp.vis = mem.alloc<uint32_t>(n * W, true);
-    P.dp.del0 = mem.alloc<uint32_t>(n * W, true);
-    P.dp.del1 = mem.alloc<uint32_t>(n * W, true);
-    P.dp.Fb = mem.alloc<uint32_t>(words, true);
+    for (auto &d : P.dp.del) d = mem.alloc<uint32_t>(n * W, true);
+    P.dp.lstamp = mem.alloc<uint32_t>(n, true);
     P.dp.inS = mem.alloc<uint32_t>(words, true);
-    // tasks of a level: at most one per vertex plus one per kBfsTaskEdges out-edges
+    // tasks of a level: at most one per vertex with out-edges plus one per kBfsTaskEdges out-edges
     const size_t ntask = static_cast<size_t>(n + P.G->m / kBfsTaskEdges + 1);
-    P.dp.T0 = mem.alloc<uint64_t>(ntask);
-    P.dp.T1 = mem.alloc<uint64_t>(ntask);
-    P.dp.V0 = mem.alloc<int32_t>(n);
-    P.dp.V1 = mem.alloc<int32_t>(n);
+    for (auto &t : P.dp.T) t = mem.alloc<int4>(ntask);
+    for (auto &v : P.dp.V) v = mem.alloc<int32_t>(n);
     P.has_bfs = true;
 }
 
@@ -449,9 +446,7 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     d.ok_edge = g.ok_edge;
     uint32_t *X = mem.alloc<uint32_t>(R);
     uint32_t *Y = mem.alloc<uint32_t>(R);
-    uint32_t *xpfx = mem.alloc<uint32_t>(1u << (32 - kPfxShift - 5), true);
-    launch_words(prm.seed, R, X, Y, xpfx, ctx->stream);
-    d.xpfx = xpfx;
+    launch_words(prm.seed, R, X, Y, ctx->stream);
     ctx->launches += 1;
     d.X = X;
     d.Y = Y;
@@ -638,9 +633,8 @@ struct Engine {
                 if (probs[i]->prm.R == R) sub.push_back(i);
             if (!sub.empty()) byR.emplace_back(R, add_list(sub));
         }
-        const List all = add_list(ids);
         cudaStream_t s = ctx->stream;
-        pending.push_back([this, byR, all, chunk, s]() {
+        pending.push_back([this, byR, chunk, s]() {
             phase(2, [&]() {
                 // whole searches, one cooperative launch per R; the host reads the counters once they are done
                 if (ctx->persistent) {
@@ -655,9 +649,9 @@ struct Engine {
                     ctx->persistent = false;  // not available on this device: step the remaining levels
                 }
                 for (int c = 0; c < chunk; ++c) {
-                    for (auto &rl : byR) launch_bfs_level(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
-                    launch_bfs_frontier(d_probs, dptr(all), all.count, ctx->d_gbar, s);
-                    ctx->launches += static_cast<int64_t>(byR.size()) + 1;
+                    for (auto &rl : byR)
+                        launch_bfs_level(rl.first, d_probs, dptr(rl.second), rl.second.count, ctx->d_gbar, s);
+                    ctx->launches += static_cast<int64_t>(byR.size());
                 }
             });
         });
@@ -1113,9 +1107,8 @@ im_status im_estimate(im_ctx *ctx, const im_sketch *sketch, const int32_t *seeds
             const int64_t n = P.G->n;
             const int W = P.prm.R / 32;
             ck(cudaMemsetAsync(P.dp.vis, 0, static_cast<size_t>(n) * W * 4, s), "memset");
-            ck(cudaMemsetAsync(P.dp.del0, 0, static_cast<size_t>(n) * W * 4, s), "memset");
-            ck(cudaMemsetAsync(P.dp.del1, 0, static_cast<size_t>(n) * W * 4, s), "memset");
-            ck(cudaMemsetAsync(P.dp.Fb, 0, ((n + 31) / 32) * 4, s), "memset");
+            for (uint32_t *d : P.dp.del) ck(cudaMemsetAsync(d, 0, static_cast<size_t>(n) * W * 4, s), "memset");
+            ck(cudaMemsetAsync(P.dp.lstamp, 0, static_cast<size_t>(n) * 4, s), "memset");
             ck(cudaMemsetAsync(P.dp.inS, 0, ((n + 31) / 32) * 4, s), "memset");
             launch_seed_set(eng.d_probs, d_seeds, k, W, s);
             ctx->launches += 1;
@@ -1151,14 +1144,14 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     const uint64_t n = static_cast<uint64_t>(g.n), R = static_cast<uint64_t>(prm.R), W = R / 32;
     const uint64_t words = (n + 31) / 32, nt = std::max<int64_t>(g.n_tasks, 1);
     uint64_t b = 0;
-    b += r(4 * R) * 2 + r(4 * 1024);                         // X, Y, prefix bitmap
+    b += r(4 * R) * 2;                                       // X, Y
     b += r(n * R) * 2;                                       // register buffers
     b += r(nt * R) + r(4 * (static_cast<uint64_t>(g.n_tasks) / 32 + 1));  // partial rows, their bits
     b += r(4 * words) * 2;                                   // L bits
     b += r(4 * n) + r(8 * (static_cast<uint64_t>(g.m) / 512 + 1));  // changed lists
     b += r(R) + r(8 * 4096);                                 // M_S', frontier log
-    b += r(4 * n * W) * 3 + r(4 * words) * 2 + r(4 * n) * 2;  // reach bits, frontier/seed-set bits, frontiers
-    b += r(8 * (n + static_cast<uint64_t>(g.m) / kBfsTaskEdges + 1)) * 2;  // search tasks
+    b += r(4 * n * W) * 4 + r(4 * words) + r(4 * n) * 4;  // reach and delta bits, seed-set bits, stamps, frontiers
+    b += r(sizeof(int4) * (n + static_cast<uint64_t>(g.m) / kBfsTaskEdges + 1)) * 2;  // search tasks
     const uint64_t m1 = std::max<uint64_t>(static_cast<uint64_t>(g.m), 1);
     b += r(4 * W * m1);                                      // live-simulation masks of the edges
     b += r(8 * (m1 + 1)) * 4;                                // pair and dense-edge offsets, out- and in-CSR order

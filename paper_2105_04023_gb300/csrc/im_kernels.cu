@@ -55,68 +55,9 @@ __device__ __forceinline__ uint32_t vmax4(uint32_t a, uint32_t b) {
     return (a & ge) | (b & ~ge);
 }
 
-// Eq. 5 on the top 15 bits, two simulations per word: a = (h ^ X_j) >> 17 and t = T >> 17 sit in 16-bit halves and
-// a + 0x8000 - t stays in [1, 0xFFFF], so the sign bit of each half is (a >= t).  A 15-bit tie (a == t) is the only
-// case the top bits cannot decide; edges where it can happen are flagged and take the exact path.
-// xt[2w] packs simulations 4w, 4w+1 of the chunk, xt[2w+1] packs 4w+2, 4w+3.  ge = 0xFF in each byte whose
-// simulation is not live.
-__device__ __forceinline__ __attribute__((unused)) uint32_t dead_bytes(uint32_t xlo, uint32_t xhi, uint32_t ht, uint32_t K) {
-    const uint32_t dlo = (xlo ^ ht) + K;
-    const uint32_t dhi = (xhi ^ ht) + K;
-    return sign_bytes(dlo, dhi, 0xFDB9u);
-}
-
-template <int R>
-__device__ __forceinline__ void merge_fast(uint32_t (&acc)[Geo<R>::CPL][4], const uint4 (&row)[Geo<R>::CPL],
-                                           const uint32_t (&xt)[Geo<R>::CPL][8], uint32_t ht, uint32_t K) {
-#pragma unroll
-    for (int c = 0; c < Geo<R>::CPL; ++c) {
-        const uint32_t rw[4] = {row[c].x, row[c].y, row[c].z, row[c].w};
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const uint32_t ge = dead_bytes(xt[c][2 * w], xt[c][2 * w + 1], ht, K);
-            acc[c][w] = vmax4(acc[c][w], rw[w] & ~ge);
-        }
-    }
-}
-
-// The same merge with the full 32-bit test of every simulation (edges with a possible 15-bit tie).
-template <int R>
-__device__ __noinline__ void merge_exact(uint32_t (&acc)[Geo<R>::CPL][4], const uint4 (&row)[Geo<R>::CPL],
-                                         uint32_t h, uint32_t T, const uint32_t *__restrict__ X, int li) {
-#pragma unroll
-    for (int c = 0; c < Geo<R>::CPL; ++c) {
-        const uint32_t rw[4] = {row[c].x, row[c].y, row[c].z, row[c].w};
-        const uint32_t *x = X + 16 * (li + Geo<R>::G * c);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            uint32_t live = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if ((h ^ __ldg(&x[4 * w + b])) <= T) live |= 0xFFu << (8 * b);
-            acc[c][w] = vmax4(acc[c][w], rw[w] & live);
-        }
-    }
-}
-
-template <int R>
-__device__ __forceinline__ void load_xt(const uint32_t *__restrict__ X, int li, uint32_t (&xt)[Geo<R>::CPL][8]) {
-#pragma unroll
-    for (int c = 0; c < Geo<R>::CPL; ++c)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t *x = X + 16 * (li + Geo<R>::G * c) + 2 * k;
-            xt[c][k] = (__ldg(x) >> kPfxShift) | ((__ldg(x + 1) >> kPfxShift) << 16);
-        }
-}
-
 struct WarpStage {
     unsigned long long mbar;  // completion barrier of the warp's bulk copies
-    int32_t v[32];    // neighbour id; bit 31 set when the edge needs the exact test
-    uint32_t ht[32];  // (h >> 17) in both halves
-    uint32_t K[32];   // 0x8000 - (T >> 17) in both halves
-    uint32_t h[32];
-    uint32_t T[32];
+    int32_t v[32];            // task index of each partial row being gathered
 };
 
 template <int R>
@@ -1047,17 +988,14 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 const uint32_t hv = vertex_hash(v);
                 uint32_t blocked = 0;
                 if (P.vis) blocked = (P.vis[static_cast<size_t>(v) * P.W + (c >> 1)] >> (16 * (c & 1))) & 0xFFFFu;
+                const uint4 *y = reinterpret_cast<const uint4 *>(P.Y) + 4 * c;  // Y_j of this chunk, 4 at a time
                 uint32_t w[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    uint32_t x = 0;
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const int j = 16 * c + 4 * k + b;
-                        const uint32_t rank = (blocked >> (4 * k + b)) & 1u ? 0u : __clz(hv ^ __ldg(&P.Y[j]));
-                        x |= rank << (8 * b);
-                    }
-                    w[k] = x;
+                    const uint4 q = __ldg(y + k);
+                    const uint32_t x = __clz(hv ^ q.x) | (__clz(hv ^ q.y) << 8) | (__clz(hv ^ q.z) << 16) |
+                                       (__clz(hv ^ q.w) << 24);
+                    w[k] = x & ~nibble_bytes((blocked >> (4 * k)) & 0xFu);
                 }
                 const uint4 val = make_uint4(w[0], w[1], w[2], w[3]);
                 reinterpret_cast<uint4 *>(P.M0)[l] = val;
@@ -1161,14 +1099,36 @@ __global__ void __launch_bounds__(kBlock) k_scan(const DevProb *__restrict__ pro
 }
 
 namespace {
-// Appends the search tasks of vertex v (out-degree deg): one per kBfsTaskEdges out-edges, at least one, whose
-// level also consumes v's delta row.
-__device__ __forceinline__ void bfs_tasks(uint64_t *T, uint32_t *count, uint32_t v, int64_t deg) {
-    const uint32_t nt = deg > 0 ? static_cast<uint32_t>((deg + kBfsTaskEdges - 1) / kBfsTaskEdges) : 1u;
+// Search task c of vertex v, whose out-edges start at edge e: kBfsTaskEdges of them (fewer in the last task), so a
+// level reads neither the task's vertex offsets nor its degree.
+__device__ __forceinline__ int4 bfs_task(uint32_t v, int64_t e, int64_t deg, uint32_t c) {
+    const int64_t e0 = e + static_cast<int64_t>(c) * kBfsTaskEdges;
+    const int64_t left = deg - static_cast<int64_t>(c) * kBfsTaskEdges;
+    return make_int4(static_cast<int>(static_cast<uint32_t>(e0)), static_cast<int>(static_cast<uint64_t>(e0) >> 32),
+                     static_cast<int>(v), static_cast<int>(left < kBfsTaskEdges ? left : kBfsTaskEdges));
+}
+
+__device__ __forceinline__ uint32_t bfs_ntasks(int64_t deg) {
+    return static_cast<uint32_t>((deg + kBfsTaskEdges - 1) / kBfsTaskEdges);
+}
+
+// Appends the search tasks of vertex v: one per kBfsTaskEdges out-edges (none for a vertex without out-edges).
+__device__ __forceinline__ void bfs_tasks(int4 *T, uint32_t *count, uint32_t v, const int64_t *xadj) {
+    const int64_t e = xadj[v], deg = xadj[v + 1] - e;
+    const uint32_t nt = bfs_ntasks(deg);
+    if (!nt) return;
     const uint32_t at = atomicAdd(count, nt);
-    for (uint32_t c = 0; c < nt; ++c) T[at + c] = (static_cast<uint64_t>(c) << 32) | v;
+    for (uint32_t c = 0; c < nt; ++c) T[at + c] = bfs_task(v, e, deg, c);
 }
 }  // namespace
+
+// Search state across levels.  Level numbers run on over the searches of a problem (a search starts at the level
+// where the previous one ended), and level L uses
+//   del[L % 3]        delta rows of its frontier F_L (bits newly reached at the previous level), read,
+//   del[(L + 1) % 3]  delta rows of F_{L+1}, written,
+//   del[(L + 2) % 3]  delta rows of F_{L-1}, cleared (so they are zero again when level L + 1 writes there),
+// with the vertex lists V[.] in the same rotation, tasks T[L % 2] read and T[(L + 1) % 2] written, and the level
+// stamp L + 1 marking the vertices listed into F_{L+1}.  Nothing has to be cleared between levels but those rows.
 
 // Takes the argmax as seed s of step k, adds it to S and starts the reachability search from it: s is marked
 // reached in every simulation where it was not yet, and those bits form the first frontier.
@@ -1188,12 +1148,14 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
         }
         return;
     }
+    const uint32_t L = C.lvl;
+    uint32_t *d0 = P.del[L % 3u];
     uint32_t added = 0;
     for (int k = lane; k < P.W; k += 32) {
         const size_t at = static_cast<size_t>(s) * P.W + k;
         const uint32_t nb = ~P.vis[at];
         P.vis[at] = 0xFFFFFFFFu;
-        P.del0[at] = nb;
+        d0[at] = nb;
         added += __popc(nb);
     }
 #pragma unroll
@@ -1204,13 +1166,14 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
         C.gsum = gsum;
         C.best_key = 0;
         set_bit(P.inS, s);
-        C.nT[0] = 0;
-        C.nT[1] = 0;
-        C.nVl[0] = 1;
-        C.nVl[1] = 0;
-        P.V0[0] = static_cast<int32_t>(s);
-        bfs_tasks(P.T0, &C.nT[0], s, P.xadj[s + 1] - P.xadj[s]);
-        C.lvl = 0;
+        C.reached += added;
+        C.nT[L & 1u] = 0;
+        C.nT[(L & 1u) ^ 1u] = 0;
+        C.nVl[L % 3u] = 1;
+        C.nVl[(L + 1u) % 3u] = 0;
+        P.V[L % 3u][0] = static_cast<int32_t>(s);
+        bfs_tasks(P.T[L & 1u], &C.nT[L & 1u], s, P.xadj);
+        C.lvl0 = L;
         C.bdone = added ? 0u : 1u;
         C.btimeout = 0;
         if (step >= 0) {
@@ -1224,38 +1187,70 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
 __global__ void k_seed_set(const DevProb *__restrict__ prob, const int32_t *__restrict__ seeds, int k) {
     const DevProb &P = *prob;
     DevCtr &C = *P.ctr;
+    const uint32_t L = C.lvl;
+    uint32_t *d0 = P.del[L % 3u];
+    if (blockIdx.x == 0 && threadIdx.x == 0) C.lvl0 = L;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k * P.W; i += gridDim.x * blockDim.x) {
         const int32_t s = seeds[i / P.W];
         const int w = i % P.W;
         const size_t at = static_cast<size_t>(s) * P.W + w;
         const uint32_t old = atomicOr(&P.vis[at], 0xFFFFFFFFu);
-        if (~old) atomicOr(&P.del0[at], ~old);
+        if (~old) {
+            atomicOr(&d0[at], ~old);
+            atomicAdd(&C.reached, static_cast<unsigned long long>(__popc(~old)));
+        }
         if (w == 0) {
             const uint32_t prev = atomicOr(&P.inS[s >> 5], 1u << (s & 31));
             if (!((prev >> (s & 31)) & 1u)) {
-                P.V0[atomicAdd(&C.nVl[0], 1u)] = s;
-                bfs_tasks(P.T0, &C.nT[0], static_cast<uint32_t>(s), P.xadj[s + 1] - P.xadj[s]);
+                P.V[L % 3u][atomicAdd(&C.nVl[L % 3u], 1u)] = s;
+                bfs_tasks(P.T[L & 1u], &C.nT[L & 1u], static_cast<uint32_t>(s), P.xadj);
             }
         }
     }
 }
 
-namespace {
+// Loads VW consecutive words (VW = 2 or 4) with one vector load: through L1 for read-only data (ldg) or from L2 for
+// data other blocks write during the launch (ldcg).
+template <int VW>
+__device__ __forceinline__ void ldg_words(const uint32_t *p, uint32_t *out) {
+    if constexpr (VW == 4) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+        out[0] = q.x, out[1] = q.y, out[2] = q.z, out[3] = q.w;
+    } else {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+        out[0] = q.x, out[1] = q.y;
+    }
+}
 
-}  // namespace
+template <int VW>
+__device__ __forceinline__ void ldcg_words(const uint32_t *p, uint32_t *out) {
+    if constexpr (VW == 4) {
+        const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(p));
+        out[0] = q.x, out[1] = q.y, out[2] = q.z, out[3] = q.w;
+    } else {
+        const uint2 q = __ldcg(reinterpret_cast<const uint2 *>(p));
+        out[0] = q.x, out[1] = q.y;
+    }
+}
 
-// One level of the bit-parallel reachability search of Algorithm 1, over all simulations at once: one warp per
-// task (kBfsTaskEdges out-edges of a frontier vertex u, one a lane).  The delta d of u (bits newly reached at u at
-// the previous level) goes out over each edge e = (u, v) in the simulations where e is live; bits not yet reached
-// at v are ORed into vis[v] and into v's next delta, and the first thread to flag v lists it for the next level.
-// Pushers of one level may race on a bit: both OR it, the same result, so no atomic needs a return value.
+// One level L of the bit-parallel reachability search of Algorithm 1, over all simulations at once: one warp per
+// task (kBfsTaskEdges out-edges of a frontier vertex u, one a lane).  The delta d of u goes out over each edge
+// e = (u, v) in the simulations where e is live; bits not yet reached at v are ORed into vis[v] and into v's next
+// delta, and the thread that stamps v first lists it in F_{L+1} and writes its tasks for level L + 1.  Pushers of
+// one level may race on a bit: both OR it, and the count of newly reached (v, j) takes only the bits an OR really
+// set.  The same launch zeroes the delta rows of F_{L-1}.
 // Phases of a search level are device functions so that the persistent kernel can run many levels in one launch;
 // everything another block may have written during that launch is read past L1 (__ldcg).
 template <int R>
 __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
                                                 int nact) {
     constexpr int W = R / 32;
+    constexpr int VW = W < 4 ? W : 4;  // words per vector load of a row
+    // Up to 8 words (one 32-byte sector) a live row is loaded whole, together with the delta row; longer rows load
+    // only the vectors where the delta has a bit.
+    constexpr bool kEager = W <= 8;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + wib;
     const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
     uint64_t base = 0;
@@ -1263,152 +1258,175 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
         const DevProb &P = probs[act[q]];
         DevCtr &C = *P.ctr;
         if (__ldcg(&C.bdone)) continue;
-        const uint32_t p = __ldcg(&C.lvl) & 1u;
-        const uint64_t cnt = __ldcg(&C.nT[p]);
+        const uint32_t L = __ldcg(&C.lvl);
+        const uint32_t p2 = L & 1u, p3 = L % 3u, n3 = (L + 1u) % 3u, c3 = (L + 2u) % 3u;
+        const uint64_t nt = __ldcg(&C.nT[p2]);
+        const uint64_t nclw = static_cast<uint64_t>(__ldcg(&C.nVl[c3])) * W;  // delta words of F_{L-1}
+        const uint64_t cnt = nt + (nclw + 31) / 32;
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
-        const uint64_t *T = p ? P.T1 : P.T0;
-        const uint32_t *dcur = p ? P.del1 : P.del0;
-        uint32_t *dnext = p ? P.del0 : P.del1;
-        for (uint64_t l = first; l < cnt; l += nworkers) {
-            const uint64_t t = __ldcg(reinterpret_cast<const unsigned long long *>(&T[l]));
-            const int64_t u = static_cast<int64_t>(static_cast<uint32_t>(t));
-            const int64_t e = __ldg(&P.xadj[u]) + static_cast<int64_t>(t >> 32) * kBfsTaskEdges + lane;
-            const bool has = e < __ldg(&P.xadj[u + 1]);
+        const int4 *T = P.T[p2];
+        int4 *Tn = P.T[p2 ^ 1u];
+        const uint32_t *dcur = P.del[p3];
+        uint32_t *dnext = P.del[n3];
+        int32_t *Vn = P.V[n3];
+        const uint32_t stamp = L + 1u;
+        unsigned long long added = 0;
+        uint64_t l = first;
+        int4 tn = l < nt ? __ldcg(&T[l]) : make_int4(0, 0, 0, 0);
+        for (; l < nt; l += nworkers) {
+            const int4 t = tn;
+            if (l + nworkers < nt) tn = __ldcg(&T[l + nworkers]);  // the next task, while this one runs
+            const int64_t e = static_cast<int64_t>((static_cast<uint64_t>(static_cast<uint32_t>(t.y)) << 32) |
+                                                   static_cast<uint32_t>(t.x)) + lane;
+            const int64_t u = static_cast<uint32_t>(t.z);
+            const bool has = lane < t.w;
             const uint32_t dl = lane < W ? __ldcg(&dcur[static_cast<size_t>(u) * W + lane]) : 0u;
             const int32_t v = has ? __ldg(&P.adj[e]) : 0;
+            const uint32_t *lrow = P.live + static_cast<size_t>(e) * W;
             uint32_t m[W];
+            if (kEager) {
+#pragma unroll
+                for (int c = 0; c < W; c += VW) {
+                    if (has) {
+                        ldg_words<VW>(lrow + c, m + c);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < VW; ++k) m[c + k] = 0u;
+                    }
+                }
+            }
             uint32_t any = 0;
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const uint32_t dk = __shfl_sync(kFull, dl, k);
-                m[k] = (dk && has) ? dk & __ldg(&P.live[static_cast<size_t>(e) * W + k]) : 0u;
-                any |= m[k];
+            for (int c = 0; c < W; c += VW) {
+                uint32_t d[VW], dor = 0;
+#pragma unroll
+                for (int k = 0; k < VW; ++k) {
+                    d[k] = __shfl_sync(kFull, dl, c + k);
+                    dor |= d[k];
+                }
+                if (!kEager) {
+                    if (has && dor) {
+                        ldg_words<VW>(lrow + c, m + c);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < VW; ++k) m[c + k] = 0u;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < VW; ++k) {
+                    m[c + k] &= d[k];
+                    any |= m[c + k];
+                }
             }
             bool fresh = false;
+            int64_t ve = 0, vdeg = 0;  // out-edges of v, for its tasks should it be listed
             if (__any_sync(kFull, any != 0)) {
+                const uint32_t *vrow = P.vis + static_cast<size_t>(v) * W;
                 uint32_t x[W];
 #pragma unroll
-                for (int k = 0; k < W; ++k) x[k] = m[k] ? __ldcg(&P.vis[static_cast<size_t>(v) * W + k]) : 0u;
+                for (int c = 0; c < W; c += VW) {
+                    uint32_t mor = 0;
+#pragma unroll
+                    for (int k = 0; k < VW; ++k) mor |= m[c + k];
+                    if (mor) {
+                        ldcg_words<VW>(vrow + c, x + c);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < VW; ++k) x[c + k] = 0u;
+                    }
+                }
+                if (any) {
+                    ve = __ldg(&P.xadj[v]);
+                    vdeg = __ldg(&P.xadj[v + 1]) - ve;
+                }
+                bool nbits = false;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
                     const uint32_t nb = m[k] & ~x[k];
                     if (!nb) continue;
                     const size_t at = static_cast<size_t>(v) * W + k;
-                    atomicOr(&P.vis[at], nb);
+                    const uint32_t old = atomicOr(&P.vis[at], nb);
                     atomicOr(&dnext[at], nb);
-                    fresh = true;
+                    added += __popc(nb & ~old);
+                    nbits = true;
                 }
-                if (fresh) {
-                    const uint32_t bit = 1u << (v & 31);
-                    fresh = !(atomicOr(&P.Fb[v >> 5], bit) & bit);
-                }
+                if (nbits) fresh = atomicExch(&P.lstamp[v], stamp) != stamp;
             }
-            // warp-aggregated append of the vertices this warp flagged first
+            // warp-aggregated listing of the vertices this warp stamped first, and their tasks
             const unsigned mf = __ballot_sync(kFull, fresh);
             if (mf) {
-                uint32_t at = 0;
-                if (lane == 0) at = atomicAdd(&C.nVl[p ^ 1u], static_cast<uint32_t>(__popc(mf)));
-                at = __shfl_sync(kFull, at, 0);
-                if (fresh) (p ? P.V0 : P.V1)[at + __popc(mf & ((1u << lane) - 1u))] = v;
-            }
-        }
-    }
-}
-
-template <int R>
-__global__ void __launch_bounds__(kBlock) k_bfs_level(const DevProb *__restrict__ probs,
-                                                      const int32_t *__restrict__ act, int nact) {
-    bfs_level_phase<R>(probs, act, nact);
-}
-
-// After a level: counts and clears the consumed delta rows (one per vertex of the level), and turns the vertices
-// that reached something new into the next level's tasks (clearing their flags).
-__device__ __forceinline__ void bfs_frontier_phase(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
-                                                   int nact) {
-    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-    uint64_t base = 0;
-    for (int q = 0; q < nact; ++q) {
-        const DevProb &P = probs[act[q]];
-        const DevCtr &C = *P.ctr;
-        if (__ldcg(&C.bdone)) continue;
-        const uint32_t p = __ldcg(&C.lvl) & 1u;
-        const int32_t *Vc = p ? P.V1 : P.V0;
-        const int32_t *Vx = p ? P.V0 : P.V1;
-        uint64_t *Tn = p ? P.T0 : P.T1;
-        uint32_t *dcur = p ? P.del1 : P.del0;
-        const uint64_t cnt = static_cast<uint64_t>(__ldcg(&C.nVl[p])) * P.W;
-        const uint64_t first = first_owned(tid, nthreads, base);
-        base += cnt;
-        unsigned long long added = 0;  // newly reached (v, j), each consumed exactly once
-        for (uint64_t l = first; l < cnt; l += nthreads) {
-            const size_t at = static_cast<size_t>(__ldcg(&Vc[l / P.W])) * P.W + l % P.W;
-            added += __popc(__ldcg(&dcur[at]));
-            dcur[at] = 0;
-        }
-        // the next level's tasks, one warp-aggregated reservation per round
-        const uint64_t nv = __ldcg(&C.nVl[p ^ 1u]);
-        const uint64_t vfirst = first_owned(tid, nthreads, base);
-        base += nv;
-        const uint64_t rounds = (nv + nthreads - 1) / nthreads;
-        for (uint64_t r = 0; r < rounds; ++r) {
-            const uint64_t l = vfirst + r * nthreads;
-            int32_t v = 0;
-            uint32_t nt = 0;
-            if (l < nv) {
-                v = __ldcg(&Vx[l]);
-                atomicAnd(&P.Fb[v >> 5], ~(1u << (v & 31)));
-                const int64_t deg = P.xadj[v + 1] - P.xadj[v];
-                nt = deg > 0 ? static_cast<uint32_t>((deg + kBfsTaskEdges - 1) / kBfsTaskEdges) : 1u;
-            }
-            uint32_t incl = nt;
+                const uint32_t ntk = fresh ? bfs_ntasks(vdeg) : 0u;
+                uint32_t incl = ntk;
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, incl, off);
-                if ((threadIdx.x & 31) >= off) incl += y;
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, incl, off);
+                    if (lane >= off) incl += y;
+                }
+                const uint32_t total = __shfl_sync(kFull, incl, 31);
+                uint32_t at = 0, tat = 0;
+                if (lane == 0) at = atomicAdd(&C.nVl[n3], static_cast<uint32_t>(__popc(mf)));
+                if (lane == 31 && total) tat = atomicAdd(&C.nT[p2 ^ 1u], total);
+                at = __shfl_sync(kFull, at, 0);
+                tat = __shfl_sync(kFull, tat, 31) + incl - ntk;
+                if (fresh) Vn[at + __popc(mf & lt)] = v;
+                if (ntk <= 2)
+                    for (uint32_t c = 0; c < ntk; ++c) Tn[tat + c] = bfs_task(static_cast<uint32_t>(v), ve, vdeg, c);
+                // vertices with more tasks write them with the whole warp
+                for (unsigned big = __ballot_sync(kFull, ntk > 2); big; big &= big - 1u) {
+                    const int f = __ffs(big) - 1;
+                    const uint32_t fv = static_cast<uint32_t>(__shfl_sync(kFull, v, f));
+                    const int64_t fe = __shfl_sync(kFull, ve, f);
+                    const int64_t fd = __shfl_sync(kFull, vdeg, f);
+                    const uint32_t fn = __shfl_sync(kFull, ntk, f);
+                    const uint32_t fa = __shfl_sync(kFull, tat, f);
+                    for (uint32_t c = lane; c < fn; c += 32) Tn[fa + c] = bfs_task(fv, fe, fd, c);
+                }
             }
-            const uint32_t total = __shfl_sync(kFull, incl, 31);
-            uint32_t at = 0;
-            if ((threadIdx.x & 31) == 31 && total) at = atomicAdd(&P.ctr->nT[p ^ 1u], total);
-            at = __shfl_sync(kFull, at, 31) + incl - nt;
-            for (uint32_t c = 0; c < nt; ++c) Tn[at + c] = (static_cast<uint64_t>(c) << 32) | static_cast<uint32_t>(v);
+        }
+        // zero the delta rows of F_{L-1}: level L + 1 writes its new bits there
+        const int32_t *Vc = P.V[c3];
+        uint32_t *dclr = P.del[c3];
+        for (; l < cnt; l += nworkers) {
+            const uint64_t w = (l - nt) * 32 + lane;
+            if (w < nclw) dclr[static_cast<size_t>(__ldcg(&Vc[w / W])) * W + w % W] = 0u;
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
-        if ((threadIdx.x & 31) == 0 && added) atomicAdd(&P.ctr->reached, added);
+        if (lane == 0 && added) atomicAdd(&C.reached, added);
     }
 }
 
-__device__ __forceinline__ void bfs_advance_one(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
-                                                int q);
-
-__global__ void __launch_bounds__(kBlock) k_bfs_frontier(const DevProb *__restrict__ probs,
-                                                         const int32_t *__restrict__ act, int nact, GridBar *gb) {
-    bfs_frontier_phase(probs, act, nact);
-    if (last_block(gb))
-        for (int q = threadIdx.x; q < nact; q += blockDim.x) bfs_advance_one(probs, act, q);
-}
-
-// Ends a level of problem act[q]: the next level's list becomes current, the search stops when it is empty (or at
-// the level limit).
+// Ends level L of problem act[q]: the search stops when F_{L+1} is empty (or at the level limit), and the counters
+// of the lists and tasks level L + 1 fills are reset.
 __device__ __forceinline__ void bfs_advance_one(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
                                                 int q) {
     const DevProb &P = probs[act[q]];
     DevCtr &C = *P.ctr;
     if (__ldcg(&C.bdone)) return;
-    const uint32_t lvl = __ldcg(&C.lvl);
-    const uint32_t p = lvl & 1u;
+    const uint32_t L = __ldcg(&C.lvl);
     C.levels_total += 1;
-    const bool empty = __ldcg(&C.nT[p ^ 1u]) == 0;
-    const bool lim = lvl + 1 >= P.max_sweeps;
-    C.nT[p] = 0;
-    C.nVl[p] = 0;
-    C.lvl = lvl + 1;
+    const bool empty = __ldcg(&C.nVl[(L + 1u) % 3u]) == 0;
+    const bool lim = L + 1u - __ldcg(&C.lvl0) >= P.max_sweeps;
+    C.nT[L & 1u] = 0;
+    C.nVl[(L + 2u) % 3u] = 0;
+    C.lvl = L + 1u;
     if (empty || lim) {
         C.bdone = 1;
         C.btimeout = (!empty && lim) ? 1u : 0u;
     }
+}
+
+// Blocks per SM the register budget is set for: long rows (R = 512, 1024) need more registers than that leaves.
+template <int R>
+constexpr int bfs_level_min_blocks() { return R <= 256 ? 4 : (R == 512 ? 3 : 2); }
+
+template <int R>
+__global__ void __launch_bounds__(kBlock, bfs_level_min_blocks<R>())
+    k_bfs_level(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact, GridBar *gb) {
+    bfs_level_phase<R>(probs, act, nact);
+    if (last_block(gb))
+        for (int q = threadIdx.x; q < nact; q += blockDim.x) bfs_advance_one(probs, act, q);
 }
 
 
@@ -1455,7 +1473,7 @@ __device__ __forceinline__ bool grid_sync(GridBar *gb) {
 }
 
 // A whole reachability search (every level until every listed problem is done) in one cooperative launch: level,
-// barrier, frontier, barrier, advance (block 0), barrier, stop test.
+// barrier, advance (block 0), barrier, stop test.
 // Marks every listed problem as failed by a lost barrier (bit 2 of its fault word).
 __device__ __forceinline__ void barrier_lost(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
                                              int nact) {
@@ -1469,8 +1487,6 @@ __global__ void __launch_bounds__(kRunBlock) k_bfs_run(const DevProb *__restrict
                                                        const int32_t *__restrict__ act, int nact, GridBar *gb) {
     for (;;) {
         bfs_level_phase<R>(probs, act, nact);
-        if (!grid_sync(gb)) return barrier_lost(probs, act, nact);
-        bfs_frontier_phase(probs, act, nact);
         if (!grid_sync(gb)) return barrier_lost(probs, act, nact);
         if (blockIdx.x == 0)
             for (int q = threadIdx.x; q < nact; q += blockDim.x) bfs_advance_one(probs, act, q);
@@ -1685,15 +1701,13 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
     return z ^ (z >> 31);
 }
 
-// Simulation words (reading of Section 3.1: X_r, Y_r are the high halves of splitmix64 outputs 2r and 2r+1) and
-// the bitmap of their top-15-bit prefixes (xpfx must be zero on entry).
-__global__ void k_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx) {
+// Simulation words (reading of Section 3.1: X_r, Y_r are the high halves of splitmix64 outputs 2r and 2r+1).
+__global__ void k_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     const uint32_t x = static_cast<uint32_t>(splitmix64_at(seed, 2ull * r) >> 32);
     X[r] = x;
     Y[r] = static_cast<uint32_t>(splitmix64_at(seed, 2ull * r + 1) >> 32);
-    set_bit(xpfx, x >> kPfxShift);
 }
 
 __global__ void k_indeg(const int32_t *__restrict__ adj, int64_t m, int32_t *__restrict__ indeg) {
@@ -1975,17 +1989,17 @@ void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cu
     k_seed_set<<<(k * W + 255) / 256, 256, 0, s>>>(prob, seeds, k);
 }
 template <int R>
-static void launch_bfs_level_r(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+static void launch_bfs_level_r(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
     static int grid = 0;  // one wave: the SM count times the blocks that fit
     if (grid == 0) {
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs_level<R>, kBlock, 0);
         grid = g_sms * (occ > 0 ? occ : 1);
     }
-    k_bfs_level<R><<<grid, kBlock, 0, s>>>(probs, act, nact);
+    k_bfs_level<R><<<grid, kBlock, 0, s>>>(probs, act, nact, gb);
 }
-void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    IMK_R_SWITCH(R, (launch_bfs_level_r<RR>(probs, act, nact, s)));
+void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
+    IMK_R_SWITCH(R, (launch_bfs_level_r<RR>(probs, act, nact, gb, s)));
 }
 template <int R>
 static bool launch_bfs_run_r(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
@@ -2010,9 +2024,6 @@ bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, G
     bool ok = false;
     IMK_R_SWITCH(R, (ok = launch_bfs_run_r<RR>(probs, act, nact, gb, s)));
     return ok;
-}
-void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
-    k_bfs_frontier<<<g_sms, kBlock, 0, s>>>(probs, act, nact, gb);
 }
 void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_merge<<<nact, 128, 0, s>>>(probs, act, nact);
@@ -2049,8 +2060,8 @@ void launch_vertex_desc(const DevProb &P, UnitD *vdesc, cudaStream_t s) {
 void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s) {
     k_unit_desc<<<g_grid_block, kBlock, 0, s>>>(P, rdesc, tdesc);
 }
-void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx, cudaStream_t s) {
-    k_words<<<(R + 255) / 256, 256, 0, s>>>(seed, R, X, Y, xpfx);
+void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, cudaStream_t s) {
+    k_words<<<(R + 255) / 256, 256, 0, s>>>(seed, R, X, Y);
 }
 void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s) {
     if (m > 0) k_indeg<<<g_grid_block, kBlock, 0, s>>>(adj, m, indeg);

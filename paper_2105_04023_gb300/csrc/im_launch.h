@@ -20,11 +20,10 @@ void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar
 void launch_scan(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t step, cudaStream_t s);
 void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cudaStream_t s);
-void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+// One search level of each listed problem; its last block ends the level (stop test, counter resets).
+void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
 // A whole search in one cooperative launch; false if the device cannot run it (the caller then steps levels).
 bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
-// Ends a search level: consumed rows counted, next tasks built, then (last block) the level advances.
-void launch_bfs_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
 void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned long long *gsum, cudaStream_t s);
 
@@ -35,7 +34,7 @@ void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cu
 void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, int32_t *idu, uint32_t *ide, cudaStream_t s);
 void launch_vertex_desc(const DevProb &P, UnitD *vdesc, cudaStream_t s);
 void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s);
-void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, uint32_t *xpfx, cudaStream_t s);
+void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, cudaStream_t s);
 void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s);
 void launch_wc_thresholds(const int32_t *indeg, int64_t n, uint32_t *T, cudaStream_t s);
 void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, unsigned long long *cursor,

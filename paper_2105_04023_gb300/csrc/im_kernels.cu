@@ -1233,17 +1233,63 @@ __device__ __forceinline__ void ldcg_words(const uint32_t *p, uint32_t *out) {
     }
 }
 
+constexpr int kStage = 32;  // vertices a warp lists before it reserves room for them in the global lists
+
+// Moves a warp's staged vertices (c of them, one a lane) into F_{L+1}'s list and writes their tasks for level
+// L + 1: one reservation per list for the whole batch, so the list counters see one atomic per kStage listed
+// vertices rather than one per listing warp.
+__device__ __forceinline__ void bfs_flush(const DevProb &P, const int32_t *stage, uint32_t c, int32_t *Vn,
+                                          uint32_t *nV, int4 *Tn, uint32_t *nT, int lane) {
+    __syncwarp();
+    int32_t v = 0;
+    int64_t e = 0, deg = 0;
+    uint32_t k = 0;
+    if (lane < static_cast<int>(c)) {
+        v = stage[lane];
+        e = __ldg(&P.xadj[v]);
+        deg = __ldg(&P.xadj[v + 1]) - e;
+        k = bfs_ntasks(deg);
+    }
+    uint32_t incl = k;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    uint32_t vb = 0, tb = 0;
+    if (lane == 0) vb = atomicAdd(nV, c);
+    if (lane == 31 && total) tb = atomicAdd(nT, total);
+    vb = __shfl_sync(kFull, vb, 0);
+    tb = __shfl_sync(kFull, tb, 31) + incl - k;
+    if (lane < static_cast<int>(c)) Vn[vb + lane] = v;
+    if (k <= 2)
+        for (uint32_t t = 0; t < k; ++t) Tn[tb + t] = bfs_task(static_cast<uint32_t>(v), e, deg, t);
+    // vertices with more tasks write them with the whole warp
+    for (unsigned big = __ballot_sync(kFull, k > 2); big; big &= big - 1u) {
+        const int f = __ffs(big) - 1;
+        const uint32_t fv = static_cast<uint32_t>(__shfl_sync(kFull, v, f));
+        const int64_t fe = __shfl_sync(kFull, e, f);
+        const int64_t fd = __shfl_sync(kFull, deg, f);
+        const uint32_t fn = __shfl_sync(kFull, k, f);
+        const uint32_t fa = __shfl_sync(kFull, tb, f);
+        for (uint32_t t = lane; t < fn; t += 32) Tn[fa + t] = bfs_task(fv, fe, fd, t);
+    }
+    __syncwarp();
+}
+
 // One level L of the bit-parallel reachability search of Algorithm 1, over all simulations at once: one warp per
 // task (kBfsTaskEdges out-edges of a frontier vertex u, one a lane).  The delta d of u goes out over each edge
 // e = (u, v) in the simulations where e is live; bits not yet reached at v are ORed into vis[v] and into v's next
-// delta, and the thread that stamps v first lists it in F_{L+1} and writes its tasks for level L + 1.  Pushers of
+// delta, and the thread that stamps v first lists it in F_{L+1} (staged per warp in `stage`, kStage entries, and
+// moved to the global list with its tasks for level L + 1 in batches).  Pushers of
 // one level may race on a bit: both OR it, and the count of newly reached (v, j) takes only the bits an OR really
 // set.  The same launch zeroes the delta rows of F_{L-1}.
 // Phases of a search level are device functions so that the persistent kernel can run many levels in one launch;
 // everything another block may have written during that launch is read past L1 (__ldcg).
 template <int R>
 __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
-                                                int nact) {
+                                                int nact, int32_t *stage) {
     constexpr int W = R / 32;
     constexpr int VW = W < 4 ? W : 4;  // words per vector load of a row
     // Up to 8 words (one 32-byte sector) a live row is loaded whole, together with the delta row; longer rows load
@@ -1272,6 +1318,7 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
         int32_t *Vn = P.V[n3];
         const uint32_t stamp = L + 1u;
         unsigned long long added = 0;
+        uint32_t ns = 0;  // staged vertices of this warp
         uint64_t l = first;
         int4 tn = l < nt ? __ldcg(&T[l]) : make_int4(0, 0, 0, 0);
         for (; l < nt; l += nworkers) {
@@ -1320,7 +1367,6 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
                 }
             }
             bool fresh = false;
-            int64_t ve = 0, vdeg = 0;  // out-edges of v, for its tasks should it be listed
             if (__any_sync(kFull, any != 0)) {
                 const uint32_t *vrow = P.vis + static_cast<size_t>(v) * W;
                 uint32_t x[W];
@@ -1336,10 +1382,6 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
                         for (int k = 0; k < VW; ++k) x[c + k] = 0u;
                     }
                 }
-                if (any) {
-                    ve = __ldg(&P.xadj[v]);
-                    vdeg = __ldg(&P.xadj[v + 1]) - ve;
-                }
                 bool nbits = false;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
@@ -1353,37 +1395,18 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
                 }
                 if (nbits) fresh = atomicExch(&P.lstamp[v], stamp) != stamp;
             }
-            // warp-aggregated listing of the vertices this warp stamped first, and their tasks
+            // the vertices this warp stamped first go to its stage
             const unsigned mf = __ballot_sync(kFull, fresh);
             if (mf) {
-                const uint32_t ntk = fresh ? bfs_ntasks(vdeg) : 0u;
-                uint32_t incl = ntk;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t y = __shfl_up_sync(kFull, incl, off);
-                    if (lane >= off) incl += y;
+                if (ns + __popc(mf) > kStage) {
+                    bfs_flush(P, stage, ns, Vn, &C.nVl[n3], Tn, &C.nT[p2 ^ 1u], lane);
+                    ns = 0;
                 }
-                const uint32_t total = __shfl_sync(kFull, incl, 31);
-                uint32_t at = 0, tat = 0;
-                if (lane == 0) at = atomicAdd(&C.nVl[n3], static_cast<uint32_t>(__popc(mf)));
-                if (lane == 31 && total) tat = atomicAdd(&C.nT[p2 ^ 1u], total);
-                at = __shfl_sync(kFull, at, 0);
-                tat = __shfl_sync(kFull, tat, 31) + incl - ntk;
-                if (fresh) Vn[at + __popc(mf & lt)] = v;
-                if (ntk <= 2)
-                    for (uint32_t c = 0; c < ntk; ++c) Tn[tat + c] = bfs_task(static_cast<uint32_t>(v), ve, vdeg, c);
-                // vertices with more tasks write them with the whole warp
-                for (unsigned big = __ballot_sync(kFull, ntk > 2); big; big &= big - 1u) {
-                    const int f = __ffs(big) - 1;
-                    const uint32_t fv = static_cast<uint32_t>(__shfl_sync(kFull, v, f));
-                    const int64_t fe = __shfl_sync(kFull, ve, f);
-                    const int64_t fd = __shfl_sync(kFull, vdeg, f);
-                    const uint32_t fn = __shfl_sync(kFull, ntk, f);
-                    const uint32_t fa = __shfl_sync(kFull, tat, f);
-                    for (uint32_t c = lane; c < fn; c += 32) Tn[fa + c] = bfs_task(fv, fe, fd, c);
-                }
+                if (fresh) stage[ns + __popc(mf & lt)] = v;
+                ns += __popc(mf);
             }
         }
+        if (ns) bfs_flush(P, stage, ns, Vn, &C.nVl[n3], Tn, &C.nT[p2 ^ 1u], lane);
         // zero the delta rows of F_{L-1}: level L + 1 writes its new bits there
         const int32_t *Vc = P.V[c3];
         uint32_t *dclr = P.del[c3];
@@ -1417,14 +1440,16 @@ __device__ __forceinline__ void bfs_advance_one(const DevProb *__restrict__ prob
     }
 }
 
-// Blocks per SM the register budget is set for: long rows (R = 512, 1024) need more registers than that leaves.
+// Blocks per SM the register budget is set for (85 registers a thread: no spills up to R = 512; 4 blocks measured
+// no faster with the spills they cost); R = 1024 rows need more.
 template <int R>
-constexpr int bfs_level_min_blocks() { return R <= 256 ? 4 : (R == 512 ? 3 : 2); }
+constexpr int bfs_level_min_blocks() { return R <= 512 ? 3 : 2; }
 
 template <int R>
 __global__ void __launch_bounds__(kBlock, bfs_level_min_blocks<R>())
     k_bfs_level(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact, GridBar *gb) {
-    bfs_level_phase<R>(probs, act, nact);
+    __shared__ int32_t stage[(kBlock / 32) * kStage];
+    bfs_level_phase<R>(probs, act, nact, stage + (threadIdx.x >> 5) * kStage);
     if (last_block(gb))
         for (int q = threadIdx.x; q < nact; q += blockDim.x) bfs_advance_one(probs, act, q);
 }
@@ -1485,8 +1510,9 @@ constexpr int kRunBlock = 1024;  // threads per block of the persistent kernels 
 template <int R>
 __global__ void __launch_bounds__(kRunBlock) k_bfs_run(const DevProb *__restrict__ probs,
                                                        const int32_t *__restrict__ act, int nact, GridBar *gb) {
+    __shared__ int32_t stage[(kRunBlock / 32) * kStage];
     for (;;) {
-        bfs_level_phase<R>(probs, act, nact);
+        bfs_level_phase<R>(probs, act, nact, stage + (threadIdx.x >> 5) * kStage);
         if (!grid_sync(gb)) return barrier_lost(probs, act, nact);
         if (blockIdx.x == 0)
             for (int q = threadIdx.x; q < nact; q += blockDim.x) bfs_advance_one(probs, act, q);

@@ -48,7 +48,7 @@ struct DevCtr {
     uint32_t timeout;    // 1 if it hit the sweep limit first
     uint32_t full;       // the current sweep pulls into every row; otherwise L pushes along its in-edges
     uint32_t res_par;    // register buffer (0/1) holding the diffusion's result
-    uint32_t nchg;       // vertices whose registers changed in the current sweep (|L'|)
+    uint32_t nchg;       // vertices whose registers changed in the current sweep (|L'|, counted after it)
     uint32_t nchg_list;  // entries written to chg_list (changed vertices with at most kPushChunk in-edges)
     uint32_t nchg_hc;    // entries written to chg_hc (chunks of the changed vertices with more)
     uint32_t npush_l;    // chg_list / chg_hc entries the current push sweep works on

@@ -78,13 +78,11 @@ __device__ __forceinline__ uint64_t in_degree(const DevProb &P, int64_t v) {
 
 struct Stats {
     unsigned long long bytes = 0;
-    unsigned int nchg = 0;
 };
 
 __device__ __forceinline__ void flush_stats(DevCtr *C, Stats &st, int lane) {
     if (lane == 0) {
         if (st.bytes) atomicAdd(&C->bytes, st.bytes);
-        if (st.nchg) atomicAdd(&C->nchg, st.nchg);
     }
     st = Stats();
 }
@@ -295,7 +293,6 @@ __device__ __forceinline__ void finalize_tile(const DevProb &P, int64_t u, uint3
         for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
     }
     if (changed && li == 0) set_bit(Lnext, u);
-    st.nchg += changed ? 1u : 0u;
     st.bytes += R + ((changed || sync) ? R : 0);
 }
 
@@ -324,7 +321,6 @@ __device__ __forceinline__ void finalize_row_r(const DevProb &P, int64_t u, uint
         for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
     }
     if (changed && lane == 0) set_bit(Lnext, u);
-    st.nchg += changed ? 1u : 0u;
     st.bytes += R + ((changed || sync) ? R : 0);
 }
 
@@ -498,12 +494,6 @@ __device__ __forceinline__ bool word_max(uint32_t *w, uint32_t old, uint32_t can
     return false;
 }
 
-// u joins L' (the first thread to set its bit counts it).
-__device__ __forceinline__ void mark_changed(uint32_t *Lnext, int64_t u, Stats &st) {
-    const uint32_t bit = 1u << (u & 31);
-    if (__ldcg(&Lnext[u >> 5]) & bit) return;
-    if (!(atomicOr(&Lnext[u >> 5], bit) & bit)) st.nchg += 1;
-}
 
 // A push sweep (Algorithm 2 with a small L, in the other direction): every changed vertex v merges M_v into the
 // rows of its in-neighbours u, M'_u[j] = max(M'_u[j], M_v[j]) for every sampled (u, v, j).  The next buffer already
@@ -574,7 +564,7 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (cand[k] && word_max(addr[k], old[k], cand[k], fault))
-                    mark_changed(Lnext, (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R, st);
+                    set_bit(Lnext, (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R);
             }
         }
         // dense in-edges: the warp fetches up to 32 of them at once; group g merges edges i + g and i + NG + g
@@ -621,7 +611,7 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
                             grew[r] |= word_max(dst + 3, o[r][c].w, rowc[c].w & nibble_bytes((mm >> 12) & 0xFu), fault);
                         }
                     }
-                    if (__any_sync(tm, grew[r]) && li == 0) mark_changed(Lnext, u[r], st);
+                    if (__any_sync(tm, grew[r]) && li == 0) set_bit(Lnext, u[r]);
                 }
             }
         }
@@ -633,7 +623,6 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
     // expects to find zero
     for (int k = lane; k < R / 16; k += 32) reinterpret_cast<uint4 *>(srow)[k] = make_uint4(0, 0, 0, 0);
     __syncwarp();
-    if (st.nchg) atomicAdd(&P.ctr->nchg, st.nchg);
     if (st.bytes) atomicAdd(&P.ctr->bytes, st.bytes);
 }
 
@@ -839,10 +828,6 @@ __device__ __forceinline__ void block_append_bits(uint32_t w, int64_t word_index
     __syncthreads();
 }
 
-__device__ __forceinline__ bool sweep_stops(const DevProb &P, const DevCtr &C) {
-    return C.nchg <= P.stop_thr || C.t + 1 >= P.max_sweeps;
-}
-
 // The first pull_sweeps sweeps pull into every row (sweep 0 has L = V, and the next ones still have most of V in L);
 // every later sweep pushes from L'.  Called after sweep C.t.
 __device__ __forceinline__ bool next_is_push(const DevProb &P, const DevCtr &C) {
@@ -872,13 +857,21 @@ __device__ __forceinline__ bool last_block(GridBar *gb) {
     return s_last != 0;
 }
 
+constexpr int kFrontChunk = 4 * kBlock;  // vertices of L_{t+1} a frontier block takes at a time (4 a thread)
+static_assert(4 * kWarpsPerBlock == 32, "one warp scans the frontier chunk's per-warp counts");
+
 __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__ probs,
                                                      const int32_t *__restrict__ act, int nact, GridBar *gb) {
+    __shared__ uint32_t s_cnt[4 * kWarpsPerBlock];  // light vertices listed by (k, warp), then their offsets
+    __shared__ uint32_t s_base, s_n;
+    __shared__ int32_t s_v[kFrontChunk];            // the chunk's listed vertices, for the row copies
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
-        if (C.done || sweep_stops(P, C)) continue;
+        if (C.done) continue;
         const bool push_next = next_is_push(P, C);
         const bool par = C.t & 1u;
         uint32_t *Lold = par ? P.Lb1 : P.Lb0;
@@ -886,50 +879,96 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
         const uint8_t *Mw = par ? P.M0 : P.M1;  // written by sweep t
         uint8_t *Mr = par ? P.M1 : P.M0;        // read by sweep t, written by sweep t + 1
         const int64_t words = (P.n + 31) >> 5;
-        const uint64_t chunks = (words + kBlock - 1) / kBlock;
+        const uint64_t chunks = (static_cast<uint64_t>(P.n) + kFrontChunk - 1) / kFrontChunk;
         const uint64_t first = first_owned(blockIdx.x, gridDim.x, base);
         base += chunks;
+        unsigned long long indeg = 0;  // in-edges into L': the next sweep's work count
+        uint32_t nchg = 0;             // |L'| (this thread's bits)
         for (uint64_t ch = first; ch < chunks; ch += gridDim.x) {
-            const int64_t i = static_cast<int64_t>(ch) * kBlock + threadIdx.x;
-            uint32_t w = 0;
-            if (i < words) {
-                Lold[i] = 0;
-                w = Lnew[i];
-            }
-            unsigned long long indeg = 0;  // in-edges into L': the next sweep's work count
-            if (!push_next)
-                for (uint32_t x = w; x; x &= x - 1) indeg += in_degree(P, i * 32 + __ffs(x) - 1);
-            if (push_next) {
-                uint32_t wh = 0;
-                for (uint32_t x = w; x; x &= x - 1) {
-                    const int64_t v = i * 32 + __ffs(x) - 1;
+            // vertex ch * kFrontChunk + k * kBlock + threadIdx.x: word (ch * 4 + k) * kWarpsPerBlock + wib, bit lane
+            bool light[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t wi = (static_cast<int64_t>(ch) * 4 + k) * kWarpsPerBlock + wib;
+                uint32_t w = 0;
+                if (wi < words) {
+                    w = Lnew[wi];
+                    if (lane == 0) Lold[wi] = 0;
+                }
+                light[k] = false;
+                nchg += (w >> lane) & 1u;
+                if ((w >> lane) & 1u) {
+                    const int64_t v = wi * 32 + lane;
                     const uint64_t d = in_degree(P, v);
                     indeg += d;
-                    if (d > kPushChunk) {
-                        wh |= 1u << (__ffs(x) - 1);
+                    light[k] = true;
+                    if (push_next && d > kPushChunk) {
+                        light[k] = false;
                         const uint4 *src = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R);
                         uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R);
-                        for (int k = 0; k < P.R / 16; ++k) dst[k] = src[k];
+                        for (int c = 0; c < P.R / 16; ++c) dst[c] = src[c];
                         const uint32_t nt = static_cast<uint32_t>((d + kPushChunk - 1) / kPushChunk);
                         const uint32_t at = atomicAdd(&P.ctr->nchg_hc, nt);
                         for (uint32_t c = 0; c < nt; ++c)
                             P.chg_hc[at + c] = (static_cast<uint64_t>(c) << 32) | static_cast<uint32_t>(v);
                     }
                 }
-                uint32_t sb = 0, sn = 0;
-                block_append_bits(w & ~wh, i, P.chg_list, &P.ctr->nchg_list, &sb, &sn);
-                // the block copies the rows it just listed, consecutive threads on consecutive 16-byte chunks
-                const uint32_t CH = static_cast<uint32_t>(P.R / 16);
-#pragma unroll 4
-                for (uint32_t x = threadIdx.x; x < sn * CH; x += blockDim.x) {
-                    const int64_t v = P.chg_list[sb + x / CH];
-                    reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R)[x % CH] =
-                        reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R)[x % CH];
+            }
+            if (!push_next) continue;  // the next sweep pulls into every row: no list, no copies
+            // list the chunk's light vertices (one reservation) and copy their rows into the next sweep's buffer.
+            // This barrier also ends the previous chunk's use of the shared arrays.
+            if (!__syncthreads_or(light[0] | light[1] | light[2] | light[3])) continue;
+            unsigned mk[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                mk[k] = __ballot_sync(kFull, light[k]);
+                if (lane == 0) s_cnt[k * kWarpsPerBlock + wib] = __popc(mk[k]);
+            }
+            __syncthreads();
+            if (wib == 0) {
+                const uint32_t c = s_cnt[lane];
+                uint32_t incl = c;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, incl, off);
+                    if (lane >= off) incl += y;
+                }
+                s_cnt[lane] = incl - c;
+                if (lane == 31) {
+                    s_n = incl;
+                    s_base = incl ? atomicAdd(&P.ctr->nchg_list, incl) : 0u;
                 }
             }
+            __syncthreads();
+            const uint32_t sn = s_n, sb = s_base;
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) indeg += __shfl_xor_sync(kFull, indeg, off);
-            if ((threadIdx.x & 31) == 0 && indeg) atomicAdd(&P.ctr->chg_indeg, indeg);
+            for (int k = 0; k < 4; ++k) {
+                if (light[k]) {
+                    const uint32_t at = s_cnt[k * kWarpsPerBlock + wib] + __popc(mk[k] & lt);
+                    const int32_t v = static_cast<int32_t>(
+                        ((static_cast<int64_t>(ch) * 4 + k) * kWarpsPerBlock + wib) * 32 + lane);
+                    P.chg_list[sb + at] = v;
+                    s_v[at] = v;
+                }
+            }
+            __syncthreads();
+            // consecutive threads on consecutive 16-byte chunks of the listed rows
+            const uint32_t CH = static_cast<uint32_t>(P.R / 16);
+#pragma unroll 4
+            for (uint32_t x = threadIdx.x; x < sn * CH; x += blockDim.x) {
+                const int64_t v = s_v[x / CH];
+                reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R)[x % CH] =
+                    reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R)[x % CH];
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            indeg += __shfl_xor_sync(kFull, indeg, off);
+            nchg += __shfl_xor_sync(kFull, nchg, off);
+        }
+        if (lane == 0 && nchg) {
+            atomicAdd(&P.ctr->nchg, nchg);
+            atomicAdd(&P.ctr->chg_indeg, indeg);
         }
     }
     if (last_block(gb))
@@ -2000,7 +2039,7 @@ void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, c
 // The frontier kernels run one block per SM: their work is light, and their last block is found by one atomic per
 // block.
 void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
-    k_frontier<<<g_sms, kBlock, 0, s>>>(probs, act, nact, gb);
+    k_frontier<<<g_sms * 3, kBlock, 0, s>>>(probs, act, nact, gb);  // one wave (78 registers a thread)
 }
 void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_init<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);

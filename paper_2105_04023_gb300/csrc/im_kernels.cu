@@ -1138,24 +1138,28 @@ __global__ void __launch_bounds__(kBlock) k_scan(const DevProb *__restrict__ pro
 }
 
 namespace {
-// Search task c of vertex v, whose out-edges start at edge e: kBfsTaskEdges of them (fewer in the last task), so a
-// level reads neither the task's vertex offsets nor its degree.
+constexpr int kFirstTask = 0x100;  // flag in a task's edge-count field: the vertex's first task (it counts the row)
+
+// Search task c of vertex v, whose out-edges start at edge e: kBfsTaskEdges of them (fewer in the last task, none
+// for a vertex without out-edges), so a level reads neither the task's vertex offsets nor its degree.
 __device__ __forceinline__ int4 bfs_task(uint32_t v, int64_t e, int64_t deg, uint32_t c) {
     const int64_t e0 = e + static_cast<int64_t>(c) * kBfsTaskEdges;
     const int64_t left = deg - static_cast<int64_t>(c) * kBfsTaskEdges;
+    const int ne = static_cast<int>(left < kBfsTaskEdges ? left : kBfsTaskEdges);
     return make_int4(static_cast<int>(static_cast<uint32_t>(e0)), static_cast<int>(static_cast<uint64_t>(e0) >> 32),
-                     static_cast<int>(v), static_cast<int>(left < kBfsTaskEdges ? left : kBfsTaskEdges));
+                     static_cast<int>(v), ne | (c == 0 ? kFirstTask : 0));
 }
 
+// Tasks of a vertex: one per kBfsTaskEdges out-edges, and one for a vertex without out-edges, whose first task
+// still counts the bits its delta row newly reached.
 __device__ __forceinline__ uint32_t bfs_ntasks(int64_t deg) {
-    return static_cast<uint32_t>((deg + kBfsTaskEdges - 1) / kBfsTaskEdges);
+    return deg > 0 ? static_cast<uint32_t>((deg + kBfsTaskEdges - 1) / kBfsTaskEdges) : 1u;
 }
 
-// Appends the search tasks of vertex v: one per kBfsTaskEdges out-edges (none for a vertex without out-edges).
+// Appends the search tasks of vertex v.
 __device__ __forceinline__ void bfs_tasks(int4 *T, uint32_t *count, uint32_t v, const int64_t *xadj) {
     const int64_t e = xadj[v], deg = xadj[v + 1] - e;
     const uint32_t nt = bfs_ntasks(deg);
-    if (!nt) return;
     const uint32_t at = atomicAdd(count, nt);
     for (uint32_t c = 0; c < nt; ++c) T[at + c] = bfs_task(v, e, deg, c);
 }
@@ -1205,7 +1209,6 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
         C.gsum = gsum;
         C.best_key = 0;
         set_bit(P.inS, s);
-        C.reached += added;
         C.nT[L & 1u] = 0;
         C.nT[(L & 1u) ^ 1u] = 0;
         C.nVl[L % 3u] = 1;
@@ -1234,10 +1237,7 @@ __global__ void k_seed_set(const DevProb *__restrict__ prob, const int32_t *__re
         const int w = i % P.W;
         const size_t at = static_cast<size_t>(s) * P.W + w;
         const uint32_t old = atomicOr(&P.vis[at], 0xFFFFFFFFu);
-        if (~old) {
-            atomicOr(&d0[at], ~old);
-            atomicAdd(&C.reached, static_cast<unsigned long long>(__popc(~old)));
-        }
+        if (~old) atomicOr(&d0[at], ~old);
         if (w == 0) {
             const uint32_t prev = atomicOr(&P.inS[s >> 5], 1u << (s & 31));
             if (!((prev >> (s & 31)) & 1u)) {
@@ -1321,9 +1321,10 @@ __device__ __forceinline__ void bfs_flush(const DevProb &P, const int32_t *stage
 // task (kBfsTaskEdges out-edges of a frontier vertex u, one a lane).  The delta d of u goes out over each edge
 // e = (u, v) in the simulations where e is live; bits not yet reached at v are ORed into vis[v] and into v's next
 // delta, and the thread that stamps v first lists it in F_{L+1} (staged per warp in `stage`, kStage entries, and
-// moved to the global list with its tasks for level L + 1 in batches).  Pushers of
-// one level may race on a bit: both OR it, and the count of newly reached (v, j) takes only the bits an OR really
-// set.  The same launch zeroes the delta rows of F_{L-1}.
+// moved to the global list with its tasks for level L + 1 in batches).  Pushers of one level may race on a bit:
+// both OR it, the same result, so no OR needs a returned value; the newly reached (v, j) are counted from the
+// delta rows, each by the first task of its vertex at the next level.  The same launch zeroes the delta rows of
+// F_{L-1}.
 // Phases of a search level are device functions so that the persistent kernel can run many levels in one launch;
 // everything another block may have written during that launch is read past L1 (__ldcg).
 template <int R>
@@ -1366,8 +1367,9 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
             const int64_t e = static_cast<int64_t>((static_cast<uint64_t>(static_cast<uint32_t>(t.y)) << 32) |
                                                    static_cast<uint32_t>(t.x)) + lane;
             const int64_t u = static_cast<uint32_t>(t.z);
-            const bool has = lane < t.w;
+            const bool has = lane < (t.w & (kFirstTask - 1));
             const uint32_t dl = lane < W ? __ldcg(&dcur[static_cast<size_t>(u) * W + lane]) : 0u;
+            if (t.w & kFirstTask) added += __popc(dl);  // u's row: the bits newly reached at u, counted once
             const int32_t v = has ? __ldg(&P.adj[e]) : 0;
             const uint32_t *lrow = P.live + static_cast<size_t>(e) * W;
             uint32_t m[W];
@@ -1427,9 +1429,8 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
                     const uint32_t nb = m[k] & ~x[k];
                     if (!nb) continue;
                     const size_t at = static_cast<size_t>(v) * W + k;
-                    const uint32_t old = atomicOr(&P.vis[at], nb);
+                    atomicOr(&P.vis[at], nb);
                     atomicOr(&dnext[at], nb);
-                    added += __popc(nb & ~old);
                     nbits = true;
                 }
                 if (nbits) fresh = atomicExch(&P.lstamp[v], stamp) != stamp;
@@ -2036,10 +2037,9 @@ void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cuda
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     IMK_R_SWITCH(R, (launch_combines<RR>(probs, act, nact, s)));
 }
-// The frontier kernels run one block per SM: their work is light, and their last block is found by one atomic per
-// block.
+// The frontier kernel runs one wave (its last block is found by one atomic per block).
 void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
-    k_frontier<<<g_sms * 3, kBlock, 0, s>>>(probs, act, nact, gb);  // one wave (78 registers a thread)
+    k_frontier<<<g_sms * 3, kBlock, 0, s>>>(probs, act, nact, gb);  // 3 blocks an SM at its register count
 }
 void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_init<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);

@@ -271,7 +271,7 @@ def run_ours(args, world, rank, local):
             "visits_per_step": visits // args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                         "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "k_propg (one sweep: sweep 0 pulls every row, later sweeps push from L)",
+                         "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "k_propg / k_push (one sweep: sweep 0 pulls every row in k_propg, later sweeps push from L in k_push)",
                          "bytes_per_launch": prop_bytes / max(prop_launches, 1),
                          "launches": prop_launches, "ms": prop_ms},
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",

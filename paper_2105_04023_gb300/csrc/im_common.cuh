@@ -54,7 +54,8 @@ struct DevCtr {
     uint32_t npush_l;    // chg_list / chg_hc entries the current push sweep works on
     uint32_t npush_h;
     uint32_t fault;      // bit 0: a bulk copy did not complete in time; bit 1: a register update kept failing;
-                         // bit 2: a grid barrier of a persistent kernel was not reached in time
+                         // bit 2: a grid barrier of a persistent kernel was not reached in time;
+                         // bit 3: a pulling sweep reached the push-only kernel
     unsigned long long chg_indeg;     // in-edges into the vertices changed in the current sweep
     unsigned long long visits;        // edge-simulation visits, running total
     unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total

@@ -564,7 +564,7 @@ struct Engine {
             b = get_event();
             ck(cudaEventRecord(a, s), "event");
         }
-        for (auto &rl : byR) launch_prop(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
+        for (auto &rl : byR) launch_prop(rl.first, d_probs, dptr(rl.second), rl.second.count, combine, s);
         if (combine)
             for (auto &rl : byR) launch_combine(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
         if (ctx->timing) {
@@ -792,7 +792,8 @@ struct Engine {
             if (P.last.fault) {
                 problem_error(P, IM_ECUDA, (P.last.fault & 1u)   ? "a bulk copy into shared memory did not complete"
                                            : (P.last.fault & 2u) ? "a register update did not settle"
-                                                                 : "a grid barrier was not reached in time");
+                                           : (P.last.fault & 4u) ? "a grid barrier was not reached in time"
+                                                                 : "a pulling sweep was launched as a push sweep");
             } else if (P.phase == Prob::kSweep && P.last.done) {
                 if (P.last.timeout)
                     problem_error(P, IM_ETIMEOUT, "diffusion exceeded max_sweeps");

@@ -659,6 +659,34 @@ __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restric
     }
 }
 
+constexpr int kPushMinBlocks = 4;  // resident blocks an SM the push kernel's register budget is set for
+
+// A sweep in which every listed problem pushes (only the first pull_sweeps sweeps of a diffusion pull): the push
+// path alone, with its own register budget and R bytes of shared memory a warp for the staged row.
+template <int R, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_push(const DevProb *__restrict__ probs,
+                                                       const int32_t *__restrict__ act, int nact) {
+    __shared__ __align__(16) uint32_t srow[kWarpsPerBlock][R / 4];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t wworker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nwworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.done) continue;
+        if (C.full) {  // a pulling sweep here would be a scheduling error: flag it rather than skip the rows
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&P.ctr->fault, 8u);
+            continue;
+        }
+        const uint64_t cnt = static_cast<uint64_t>(C.npush_l) + C.npush_h;
+        const uint64_t first = first_owned(wworker, nwworkers, base);
+        base += cnt;
+        if (first >= cnt) continue;
+        push_problem_w<R>(P, C.t, cnt, first, nwworkers, lane, srow[wib]);
+    }
+}
+
 // Split rows with at most kBigTasks tasks: one warp merges a row's partial rows and finishes the row.
 template <int R>
 __global__ void __launch_bounds__(kBlock) k_combine(const DevProb *__restrict__ probs,
@@ -1998,6 +2026,17 @@ static void launch_gather(const DevProb *probs, const int32_t *act, int nact, cu
     k_propg<R, MINB><<<grid, kBlock, smem, s>>>(probs, act, nact);
 }
 
+template <int R, int MINB>
+static void launch_push(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    static int grid = 0;
+    if (grid == 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push<R, MINB>, kBlock, 0);
+        grid = g_sms * (occ > 0 ? occ : 1);
+    }
+    k_push<R, MINB><<<grid, kBlock, 0, s>>>(probs, act, nact);
+}
+
 template <int R>
 static void launch_combines(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     static int grid_s = 0, grid_b = 0;
@@ -2027,7 +2066,11 @@ static void launch_combines(const DevProb *probs, const int32_t *act, int nact, 
 
 // Minimum resident blocks per SM of the propagation kernel (register budget); IM_PROP_VARIANT selects 3 or 6
 // instead of the default 4 (all exact alike).
-void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, bool pulls, cudaStream_t s) {
+    if (!pulls) {
+        IMK_R_SWITCH(R, (launch_push<RR, kPushMinBlocks>(probs, act, nact, s)));
+        return;
+    }
     switch (g_variant) {
         case 3: IMK_R_SWITCH(R, (launch_gather<RR, 3>(probs, act, nact, s))); return;
         case 6: IMK_R_SWITCH(R, (launch_gather<RR, 6>(probs, act, nact, s))); return;

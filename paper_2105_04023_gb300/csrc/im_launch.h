@@ -13,7 +13,8 @@ cudaError_t configure(int device);
 int grid_warp();
 
 void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
-void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+// One sweep: the pull-and-push kernel when a listed problem may pull (pulls), else the push-only kernel.
+void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, bool pulls, cudaStream_t s);
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 // Ends a sweep: frontier lists and row copies, then (last block) the stop test and counter resets.
 void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);

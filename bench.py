@@ -326,6 +326,56 @@ def run_build(args, local):
     ctx.close()
 
 
+def run_mc(args, local):
+    """The influence scorer on the bench workload: the 50 seeds the select picks, scored by sample-then-diffuse
+    Monte Carlo over --mc-samples mt19937-sampled graphs (Section 5's way of scoring seed sets), timed with CUDA
+    events; the oracle scores one sample on one core for comparison."""
+    import torch
+
+    import paper_2105_04023_gb300 as im
+    from paper_2105_04023_gb300 import build as b
+
+    torch.cuda.set_device(local)
+    b.build()
+    prob = load_workload()
+    g = prob.graph
+    graph = im.Graph.from_synth(g, prob.model, prob.p, device=f"cuda:{local}")
+    ctx = im.Context(local)
+    sel = ctx.im_select_seeds(graph, im.params(R=prob.R, K=prob.K, eps_g=prob.eps_g, eps_l=prob.eps_l,
+                                               eps_c=prob.eps_c, seed=prob.seed), trace=False)
+    seeds = sel["seeds"]
+    N = args.mc_samples
+    for _ in range(args.warmup):
+        ctx.im_influence_mc(graph, seeds, N, 77)
+    ctx.set_timing(True)
+    times, sig = [], None
+    for i in range(args.steps):
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        sig, reach = ctx.im_influence_mc(graph, seeds, N, 77)
+        c.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(c) / 1000.0)
+    st = ctx.stats()
+    t = sum(times) / len(times)
+    import oracle
+
+    t0 = time.perf_counter()
+    _, one = oracle.influence_mc(g.n, g.xadj, g.adj, prob.model, prob.p, seeds, 1, 77)
+    t_cpu = time.perf_counter() - t0
+    out = {"mode": "mc", "workload": "R-MAT scale 20, edge factor 16, weighted cascade (the 50 seeds of the select)",
+           "samples": N, "steps": args.steps, "s_per_call": t, "samples_per_s": N / t,
+           "edge_draws_per_s": g.m * N / t, "sigma_mc": sig, "sigma_sketch_samples": sel["sigma_final"],
+           "mc_stderr": float(np.std(reach.astype(np.float64), ddof=1) / np.sqrt(N)),
+           "sample_phase_ms": st["init_ms"], "search_phase_ms": st["bfs_ms"], "search_levels": st["bfs_levels"],
+           "cpu_baseline": {"samples_per_s": 1.0 / t_cpu, "cores": 1, "kind": "oracle",
+                            "sample": "sample 0 of the same scoring, drawn and searched on one core"},
+           "oracle_sample0_matches": int(one[0]) == int(reach[0])}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def run_batch(args, local):
     """The batched workload: many R-MAT graphs of uneven sizes, models and R, all selected together (one launch per
     phase for all of them) versus one graph per call on the same GPU, with identical seed sets required."""
@@ -468,9 +518,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="select", choices=["select", "build", "batch", "serve"],
+    ap.add_argument("--mode", default="select", choices=["select", "build", "batch", "serve", "mc"],
                     help="build: sketch builds only (for profiling); batch: the 256-graph batched workload; "
-                         "serve: the query stream on a resident graph pool")
+                         "serve: the query stream on a resident graph pool; mc: the Monte-Carlo influence scorer")
+    ap.add_argument("--mc-samples", type=int, default=1024)
     ap.add_argument("--k", type=int, default=0, help="override the workload's K (profiling runs)")
     ap.add_argument("--batch-graphs", type=int, default=256)
     ap.add_argument("--batch-max-scale", type=int, default=18)
@@ -484,6 +535,8 @@ def main():
         run_batch(args, local)
     elif args.mode == "serve":
         run_serve(args, local)
+    elif args.mode == "mc":
+        run_mc(args, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -257,6 +257,24 @@ im_status im_server_cancel(im_server *srv, uint64_t ticket);
 im_status im_estimate_static(im_ctx *ctx, const uint8_t *registers, int64_t n, int32_t R, const int32_t *seeds,
                              int32_t k, double *est_out, uint64_t *gsum_out);
 
+/*
+ * Influence score of a seed set by plain sample-then-diffuse Monte Carlo, the way the paper's experiments score
+ * every method's seed sets (Section 5, "Performance Metrics": a separate oracle that samples with mt19937 and then
+ * diffuses, independent of the hash-based sampling of Section 3.1).  In each of nsamples samples every edge is
+ * drawn live or not with mt19937, and the vertices the k seeds reach over the live edges are counted:
+ *   sample s draws edge e's value as output (e mod 8192) of its own mt19937 stream for the chunk of 8192 edges
+ *   holding e (out-CSR order), seeded by init_genrand with the high 32 bits of output s * ceil(m / 8192) +
+ *   floor(e / 8192) of the splitmix64 sequence of `seed`; the edge is live iff the draw is <= its threshold
+ *   T = ceil(p * 2^32) - 1 (weighted cascade: floor((2^32 - 1) / indeg(v)); p <= 0 never live).
+ * graph: as for im_select_seeds (device or host arrays).  seeds: HOST array of k ids in [0, n), k >= 1 (repeats
+ * count once).  nsamples: a multiple of 64 in [64, 2^24].  sigma_out: HOST pointer, receives the mean reach over
+ * the samples.  reach_out: HOST array of nsamples counts (nullable), receives each sample's reach.  Outputs are
+ * written only on IM_OK; IM_EINVAL for bad arguments or an invalid graph.  Device memory: one 1024-sample batch
+ * (about m * 128 + n * 640 bytes) at a time, freed before the call returns.
+ */
+im_status im_influence_mc(im_ctx *ctx, const im_graph *graph, const int32_t *seeds, int32_t k, int64_t nsamples,
+                          uint64_t seed, double *sigma_out, uint64_t *reach_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,10 @@ Parity status per function (what pins each one is listed in ``tests/test_oracle_
   reach / sigma ............. pinned to brute-force breadth-first search per simulation
   select_seeds .............. pinned to brute-force greedy on tiny graphs (always-rebuild, never-rebuild, mixed)
   estimate .................. pinned to Eq. 2 on hand-built sketches
+  mt19937 ................... pinned to the value the C++ standard fixes (10000th output of the default seed) and
+                              to numpy's independent implementation
+  influence_mc .............. pinned to reachability closed forms (p = 0, p = 1), to a per-sample search over edges
+                              drawn with numpy's generator, and to the expected reach of a star
 """
 from __future__ import annotations
 
@@ -73,6 +77,10 @@ def lib() -> ctypes.CDLL:
                                        _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr]),
             "or_estimate_set": (_dbl, [_i64, _i32, _ptr, _ptr, _i32, _ptr]),
             "or_register_at": (_i32, [_i64, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _i64, _i32, _ptr, _ptr]),
+            "or_mt_outputs": (None, [_u32, _i64, _ptr]),
+            "or_mc_stream_seed": (_u32, [_u64, _i64, _i64, _i64]),
+            "or_mc_live": (_i32, [_i64, _ptr, _ptr, _u64, _i64, _ptr]),
+            "or_influence_mc": (_i64, [_i64, _i64, _ptr, _ptr, _i32, _dbl, _ptr, _ptr, _i32, _i64, _i64, _u64, _ptr]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -249,3 +257,40 @@ class RegisterProbe:
         for s in seeds:
             total += reach_add(self.n, self.xadj, self.adj, self.T, self.ok, R, self.X, int(s), reached)
         return total
+
+
+MC_CHUNK = 8192  # edges per generator stream of the influence oracle (reading R15)
+
+
+def mt_outputs(seed: int, count: int) -> np.ndarray:
+    """The first `count` outputs of mt19937 seeded with init_genrand(seed)."""
+    out = np.zeros(max(count, 1), np.uint32)
+    lib().or_mt_outputs(seed & 0xFFFFFFFF, count, _p(out))
+    return out[:count]
+
+
+def mc_stream_seed(seed: int, s: int, c: int, nchunks: int) -> int:
+    return int(lib().or_mc_stream_seed(seed, s, c, nchunks))
+
+
+def mc_live(n, xadj, adj, model, p, seed, s, p_edge=None) -> np.ndarray:
+    """Reading R15: the live edges (one byte per out-CSR edge) of sample s."""
+    T, ok = edge_thresholds(n, xadj, adj, model, p, p_edge)
+    m = T.shape[0]
+    live = np.zeros(max(m, 1), np.uint8)
+    lib().or_mc_live(m, _p(np.ascontiguousarray(T)), _p(np.ascontiguousarray(ok)), seed, s, _p(live))
+    return live[:m]
+
+
+def influence_mc(n, xadj, adj, model, p, seeds, N, seed, p_edge=None, first=0):
+    """Sample-then-diffuse influence of `seeds` over samples first .. first + N - 1 (Section 5's oracle, reading
+    R15).  Returns (total reached over those samples, per-sample reach counts)."""
+    xadj, adj = _csr(xadj, adj)
+    S = np.ascontiguousarray(seeds, dtype=np.int32)
+    pe = None if p_edge is None else np.ascontiguousarray(p_edge, dtype=np.float32)
+    reach = np.zeros(max(N, 1), np.int64)
+    t = lib().or_influence_mc(n, adj.shape[0], _p(xadj), _p(adj), model, p, _p(pe), _p(S), S.shape[0], first, N,
+                              seed, _p(reach))
+    if t < 0:
+        raise RuntimeError(f"or_influence_mc rc={-t}")
+    return int(t), reach[:N].copy()

@@ -33,6 +33,10 @@
  *   R10 e, sigma and the errors are computed in double from integer register sums and reach counts.
  *   R11 sigma is the mean reach of S over the same R hash-sampled graphs.
  *   R12 the rebuild decided after the K-th seed is recorded but its diffusion is not run (its sketch is never read).
+ *   R15 influence scoring (the separate sample-then-diffuse oracle of the experiments, Section 5, which draws with
+ *      mt19937): sample s draws edge e's value as output (e mod C) of its own mt19937 stream for the chunk of
+ *      C = 8192 edges holding e (out-CSR order), seeded by init_genrand with the high half of splitmix64 output
+ *      s * nchunks + floor(e / C) of the run seed; the edge is live iff the draw is <= T (R4's threshold).
  */
 #include <math.h>
 #include <stdint.h>
@@ -460,4 +464,130 @@ int32_t or_register_at(int64_t n, const int64_t *xadj, const int32_t *adj, const
     }
     for (int64_t i = 0; i < tail; ++i) seen[queue[i]] = 0;
     return best;
+}
+
+/*
+ * MT19937 (Matsumoto & Nishimura, "Mersenne Twister: a 623-dimensionally equidistributed uniform pseudo-random
+ * number generator", ACM TOMACS 8(1), 1998): a 624-word state seeded by init_genrand, regenerated 624 words at a
+ * time by the twist (lower 31 bits of the next word joined to the top bit of this one, shifted, XORed with the
+ * matrix row 0x9908B0DF when odd, and with the word 397 places on), and tempered on output.
+ */
+typedef struct {
+    uint32_t mt[624];
+    int32_t i;
+} or_mt19937;
+
+void or_mt_seed(or_mt19937 *g, uint32_t s)
+{
+    g->mt[0] = s;
+    for (int32_t i = 1; i < 624; ++i) g->mt[i] = 1812433253u * (g->mt[i - 1] ^ (g->mt[i - 1] >> 30)) + (uint32_t)i;
+    g->i = 624;
+}
+
+static void or_mt_twist(or_mt19937 *g)
+{
+    for (int32_t i = 0; i < 624; ++i) {
+        uint32_t x = (g->mt[i] & 0x80000000u) | (g->mt[(i + 1) % 624] & 0x7FFFFFFFu);
+        uint32_t xa = x >> 1;
+        if (x & 1u) xa ^= 0x9908B0DFu;
+        g->mt[i] = g->mt[(i + 397) % 624] ^ xa;
+    }
+    g->i = 0;
+}
+
+uint32_t or_mt_next(or_mt19937 *g)
+{
+    if (g->i >= 624) or_mt_twist(g);
+    uint32_t y = g->mt[g->i++];
+    y ^= y >> 11;
+    y ^= (y << 7) & 0x9D2C5680u;
+    y ^= (y << 15) & 0xEFC60000u;
+    y ^= y >> 18;
+    return y;
+}
+
+/* The first `count` outputs of the generator seeded with s (for the pins). */
+void or_mt_outputs(uint32_t s, int64_t count, uint32_t *out)
+{
+    or_mt19937 g;
+    or_mt_seed(&g, s);
+    for (int64_t i = 0; i < count; ++i) out[i] = or_mt_next(&g);
+}
+
+#define OR_MC_CHUNK 8192
+
+/* Reading R15: the seed of sample s's stream for edge chunk c. */
+uint32_t or_mc_stream_seed(uint64_t seed, int64_t s, int64_t c, int64_t nchunks)
+{
+    return (uint32_t)(or_splitmix64(seed, (uint64_t)s * (uint64_t)nchunks + (uint64_t)c) >> 32);
+}
+
+/* Reading R15: live[e] = 1 iff edge e is live in sample s. */
+int32_t or_mc_live(int64_t m, const uint32_t *T, const uint8_t *possible, uint64_t seed, int64_t s, uint8_t *live)
+{
+    const int64_t nchunks = (m + OR_MC_CHUNK - 1) / OR_MC_CHUNK;
+    or_mt19937 g;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        or_mt_seed(&g, or_mc_stream_seed(seed, s, c, nchunks));
+        const int64_t e1 = (c + 1) * OR_MC_CHUNK < m ? (c + 1) * OR_MC_CHUNK : m;
+        for (int64_t e = c * OR_MC_CHUNK; e < e1; ++e) {
+            const uint32_t x = or_mt_next(&g);
+            live[e] = (uint8_t)(possible[e] && x <= T[e]);
+        }
+    }
+    return OR_OK;
+}
+
+/*
+ * Influence of a seed set by plain sample-then-diffuse Monte Carlo (the influence oracle of Section 5): in each of
+ * the N samples s0 .. s0 + N - 1 every edge is drawn live or not (reading R15), and a breadth-first search from S
+ * over the live edges counts the vertices reached.  reach[i] gets sample s0 + i's count (nullable); returns the
+ * total over the samples, or a negative value on error.
+ */
+int64_t or_influence_mc(int64_t n, int64_t m, const int64_t *xadj, const int32_t *adj, int32_t model, double p,
+                        const float *p_edge, const int32_t *S, int32_t k, int64_t s0, int64_t N, uint64_t seed,
+                        int64_t *reach)
+{
+    uint32_t *T = (uint32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(uint32_t));
+    uint8_t *possible = (uint8_t *)malloc((size_t)(m > 0 ? m : 1));
+    uint8_t *live = (uint8_t *)malloc((size_t)(m > 0 ? m : 1));
+    uint8_t *seen = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t *queue = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t total = 0;
+    if (!T || !possible || !live || !seen || !queue) {
+        total = -OR_ENOMEM;
+        goto done;
+    }
+    if (or_edge_thresholds(n, m, xadj, adj, model, p, p_edge, T, possible) != OR_OK) {
+        total = -OR_EINVAL;
+        goto done;
+    }
+    for (int64_t s = s0; s < s0 + N; ++s) {
+        or_mc_live(m, T, possible, seed, s, live);
+        int64_t head = 0, tail = 0;
+        for (int32_t i = 0; i < k; ++i) {
+            if (seen[S[i]]) continue;
+            seen[S[i]] = 1;
+            queue[tail++] = S[i];
+        }
+        while (head < tail) {
+            const int64_t u = queue[head++];
+            for (int64_t e = xadj[u]; e < xadj[u + 1]; ++e) {
+                const int64_t v = adj[e];
+                if (seen[v] || !live[e]) continue;
+                seen[v] = 1;
+                queue[tail++] = v;
+            }
+        }
+        if (reach) reach[s - s0] = tail;
+        total += tail;
+        for (int64_t i = 0; i < tail; ++i) seen[queue[i]] = 0;
+    }
+done:
+    free(T);
+    free(possible);
+    free(live);
+    free(seen);
+    free(queue);
+    return total;
 }

@@ -169,6 +169,19 @@ class Context:
                                                   ctypes.addressof(ptrs), sig.ctypes.data, reb.ctypes.data))
         return [dict(seeds=seeds[i], sigma_final=float(sig[i]), rebuilds=int(reb[i])) for i in range(nq)]
 
+    def im_influence_mc(self, graph: Graph, seeds, nsamples: int, seed: int) -> tuple[float, np.ndarray]:
+        """Sample-then-diffuse influence of a seed set over `nsamples` mt19937-sampled graphs (the scoring of
+        Section 5); returns (mean reach, reach of each sample)."""
+        _sync_torch()
+        g = graph.c()
+        S = np.ascontiguousarray(seeds, dtype=np.int32)
+        reach = np.zeros(max(int(nsamples), 1), np.uint64)
+        sigma = ctypes.c_double()
+        self._check(self._L.im_influence_mc(self.h, ctypes.byref(g), S.ctypes.data, int(S.shape[0]), int(nsamples),
+                                            int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.addressof(sigma),
+                                            reach.ctypes.data))
+        return sigma.value, reach[: int(nsamples)]
+
     def im_estimate_static(self, registers, seeds) -> tuple[float, int]:
         """Estimate of a seed set from a register matrix and seed ids already on the device (CUDA torch tensors:
         uint8 [n, R] and int32 [k]); the library allocates nothing for this call."""

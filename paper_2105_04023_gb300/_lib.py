@@ -58,6 +58,7 @@ SIGNATURES = {
                              ctypes.POINTER(im_trace)]),
     "im_select_seeds_batch": (_I, [_P, _I32, _P, _P, _P, _P, _P]),
     "im_estimate_static": (_I, [_P, _P, _I64, _I32, _P, _I32, _P, _P]),
+    "im_influence_mc": (_I, [_P, ctypes.POINTER(im_graph), _P, _I32, _I64, ctypes.c_uint64, _P, _P]),
     "im_server_create": (_I, [_P, ctypes.c_uint64, _I32, ctypes.POINTER(_P)]),
     "im_server_destroy": (_I, [_P]),
     "im_server_add_graph": (_I, [_P, ctypes.POINTER(im_graph), _P]),

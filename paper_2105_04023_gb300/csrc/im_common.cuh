@@ -15,6 +15,7 @@ constexpr int kTaskEdges = 64;
 constexpr int kBigTasks = 32;        // split rows with more tasks are merged by a whole block
 constexpr int kBfsTaskEdges = 32;    // out-edges per task of a search-frontier vertex (one warp, one edge a lane)
 constexpr int kPushChunk = 1024;     // a changed vertex pushes its in-edges in units of at most this many
+constexpr int kMcChunk = 8192;      // edges per generator stream of the Monte-Carlo influence scorer
 constexpr int kCasLimit = 1024;      // compare-and-swap tries of one register-word update before it counts as a fault
 
 enum Model : int32_t { kIC = 0, kWC = 1, kPerEdge = 2 };

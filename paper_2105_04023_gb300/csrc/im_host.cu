@@ -300,8 +300,8 @@ struct Prob {
     std::string error;
 };
 
-// Buffers of the reachability searches, and the per-edge live-simulation masks they read (computed here, on the
-// context stream, once per problem).  The descriptor must be complete apart from its counters.
+// Buffers of the reachability searches (the per-edge live-simulation masks they read come from the sampling).
+// The descriptor must be complete apart from its counters.
 void alloc_bfs(Prob &P, cudaStream_t s) {
     const int64_t n = P.G->n;
     const int W = P.prm.R / 32;
@@ -1030,6 +1030,112 @@ im_status im_build_sketches(im_ctx *ctx, const im_graph *graph, const im_params 
         tm.stop();
         end_call(ctx, {sk->P.get()}, tm.a, tm.b);
         *out = sk.release();
+    });
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Influence scoring by plain sample-then-diffuse Monte Carlo (Section 5's separate influence oracle), on the
+// device: live masks drawn with mt19937 streams (k_mc_live), then the seed set's reachability search over them
+// with the search kernels of the greedy loop, in batches of up to 1024 samples.
+
+// A search-only problem of R samples on graph G: thresholds, live masks and search buffers, nothing of a sketch.
+std::unique_ptr<Prob> make_mc_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, int R) {
+    auto P = std::make_unique<Prob>();
+    P->G = std::move(G);
+    P->prm.R = R;
+    P->prm.K = 1;
+    P->mem = std::make_unique<DevMem>(ctx->stream);
+    const GraphDev &g = *P->G;
+    DevProb &d = P->dp;
+    d.n = g.n;
+    d.m = g.m;
+    d.xadj = g.xadj;
+    d.adj = g.adj;
+    d.model = g.model;
+    d.R = R;
+    d.W = R / 32;
+    d.T_const = g.T_const;
+    d.ic_ok = g.ic_ok;
+    d.T_vert = g.T_vert;
+    d.T_edge = g.T_edge;
+    d.ok_edge = g.ok_edge;
+    d.live = P->mem->alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(g.m, 1)) * d.W);
+    d.max_sweeps = static_cast<uint32_t>(std::min<int64_t>(g.n + 2, 0x7FFFFFFF));
+    alloc_bfs(*P, ctx->stream);
+    return P;
+}
+
+im_status im_influence_mc(im_ctx *ctx, const im_graph *graph, const int32_t *seeds, int32_t k, int64_t nsamples,
+                          uint64_t seed, double *sigma_out, uint64_t *reach_out) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!graph || !seeds || !sigma_out) fail(IM_EINVAL, "graph / seeds / sigma_out is NULL");
+        if (k < 1) fail(IM_EINVAL, "k must be >= 1");
+        if (nsamples < 64 || nsamples % 64 != 0 || nsamples > (int64_t{1} << 24))
+            fail(IM_EINVAL, "nsamples must be a multiple of 64 in [64, 2^24]");
+        for (int32_t i = 0; i < k; ++i)
+            if (seeds[i] < 0 || seeds[i] >= graph->n) fail(IM_EINVAL, "seed id outside [0, n)");
+        begin_call(ctx);
+        CallTimer tm(ctx);
+        auto G = prepare_graph(ctx, graph);
+        cudaStream_t s = ctx->stream;
+        DevMem tmp(s);
+        int32_t *d_seeds = tmp.alloc<int32_t>(k);
+        ck(cudaMemcpyAsync(d_seeds, seeds, k * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy seeds");
+        unsigned long long *d_counts = tmp.alloc<unsigned long long>(1024);
+        std::vector<unsigned long long> h_counts(1024);
+        const int64_t n = G->n;
+        const int64_t nchunks = (G->m + kMcChunk - 1) / kMcChunk;
+        std::unique_ptr<Prob> full, last;  // the 1024-sample problem reused by every full batch, the remainder's
+        std::vector<Prob *> used;
+        unsigned long long total = 0;
+        for (int64_t s0 = 0; s0 < nsamples;) {
+            const int64_t left = nsamples - s0;
+            int R = 1024;
+            while (R > 64 && R / 2 >= left) R /= 2;
+            std::unique_ptr<Prob> &slot = R == 1024 ? full : last;
+            if (!slot) {
+                slot = make_mc_prob(ctx, G, R);
+                used.push_back(slot.get());
+            }
+            Prob &P = *slot;
+            const int W = R / 32;
+            const int64_t nb = std::min<int64_t>(left, R);
+            for (uint32_t *d : P.dp.del) ck(cudaMemsetAsync(d, 0, static_cast<size_t>(n) * W * 4, s), "memset");
+            ck(cudaMemsetAsync(P.dp.vis, 0, static_cast<size_t>(n) * W * 4, s), "memset");
+            ck(cudaMemsetAsync(P.dp.lstamp, 0, static_cast<size_t>(n) * 4, s), "memset");
+            ck(cudaMemsetAsync(P.dp.inS, 0, ((n + 31) / 32) * 4, s), "memset");
+            ck(cudaMemsetAsync(d_counts, 0, R * sizeof(unsigned long long), s), "memset");
+            std::vector<DevCtr> c0(1);
+            c0[0].levels_total = P.last.levels_total;  // this problem's levels so far, for the call's statistics
+            Engine eng(ctx, {&P}, &c0);
+            eng.phase(3, [&]() { launch_mc_live(R, eng.d_probs, seed, s0, nb, nchunks, s); });
+            launch_seed_set(eng.d_probs, d_seeds, k, W, s);
+            ctx->launches += 2;
+            P.phase = Prob::kBfs;
+            for (;;) {
+                eng.enqueue_bfs({0}, ctx->level_chunk);
+                eng.flush();
+                eng.read_counters();
+                if (P.last.bdone || P.last.fault) break;
+            }
+            P.phase = Prob::kDone;
+            if (P.last.fault) fail(IM_ECUDA, "a grid barrier was not reached in time");
+            if (P.last.btimeout) fail(IM_ETIMEOUT, "reachability search exceeded its level limit");
+            launch_sample_counts(R, eng.d_probs, d_counts, s);
+            ctx->launches += 1;
+            ck(cudaMemcpyAsync(h_counts.data(), d_counts, R * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s),
+               "read counts");
+            ck(cudaStreamSynchronize(s), "sync");
+            for (int64_t j = 0; j < nb; ++j) {
+                total += h_counts[j];
+                if (reach_out) reach_out[s0 + j] = h_counts[j];
+            }
+            s0 += nb;
+        }
+        tm.stop();
+        end_call(ctx, used, tm.a, tm.b);
+        *sigma_out = static_cast<double>(total) / static_cast<double>(nsamples);
     });
 }
 

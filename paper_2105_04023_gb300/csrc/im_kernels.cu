@@ -7,15 +7,16 @@
 //
 // Paper map:
 //   k_init        Algorithm 1, register initialisation (and its re-initialisation with R_G(S) blocked)
-//   k_prop        Algorithm 2, one sweep of the pull-based diffusion; the sampling of Eq. 4-5 is evaluated once
-//                 per run (k_live_masks) and kept as (target, simulation) pairs for edges live in few simulations
-//                 (k_pair_counts, k_pair_fill), the hashed test runs in the sweep for the other edges
-//   k_combine     Algorithm 2, the same sweep for rows split over several warps
+//   k_propg       Algorithm 2, one sweep that pulls into every row (sweep 0); the sampling of Eq. 4-5 is
+//                 evaluated once per run (k_live_masks) and kept as (target, simulation) pairs for edges live in
+//                 few simulations (k_pair_counts, k_pair_fill) and as live masks for the others
+//   k_push        Algorithm 2, the later sweeps, pushed from the vertices L that changed in the previous one
+//   k_combine     Algorithm 2, sweep 0 for rows split over several warps
 //   k_frontier    Algorithm 2, the live sets L and L' (and the copy a push sweep needs); its last block applies
 //                 the stop test (eps_c)
-//   k_scan, k_choose                          Algorithm 1, argmax of Estimate(Merge(M_S', M_v)) (Eq. 2-3)
-//   k_bfs_level, k_bfs_frontier (k_bfs_run)  Algorithm 1, reachability set of S in every simulation, sigma
-//   k_merge                                   Algorithm 1, M_S' <- Merge(M_S', M_s)
+//   k_scan, k_choose             Algorithm 1, argmax of Estimate(Merge(M_S', M_v)) (Eq. 2-3)
+//   k_bfs_level (k_bfs_run)      Algorithm 1, reachability set of S in every simulation, sigma
+//   k_merge                      Algorithm 1, M_S' <- Merge(M_S', M_s)
 #include <algorithm>
 #include <cstdlib>
 
@@ -1804,6 +1805,85 @@ __global__ void k_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y) {
     Y[r] = static_cast<uint32_t>(splitmix64_at(seed, 2ull * r + 1) >> 32);
 }
 
+// ------------------------------------------------------------------------------------------------------------
+// Influence scoring by plain sample-then-diffuse Monte Carlo (the separate influence oracle of Section 5, which
+// draws with mt19937).  Sample s draws edge e's value as output (e mod kMcChunk) of its own mt19937 stream for the
+// chunk of kMcChunk edges holding e (out-CSR order), seeded by init_genrand with the high half of splitmix64
+// output s * nchunks + floor(e / kMcChunk) of the run seed; the edge is live iff the draw is <= its threshold.
+
+// MT19937 (Matsumoto & Nishimura, ACM TOMACS 8(1), 1998): 624-word state seeded by init_genrand, regenerated 624
+// words at a time by the twist, tempered on output.  The state lives in the thread's local memory.
+struct Mt19937 {
+    uint32_t mt[624];
+    int i;
+    __device__ __forceinline__ void seed(uint32_t s) {
+        mt[0] = s;
+        for (int k = 1; k < 624; ++k) mt[k] = 1812433253u * (mt[k - 1] ^ (mt[k - 1] >> 30)) + static_cast<uint32_t>(k);
+        i = 624;
+    }
+    __device__ __forceinline__ static uint32_t twist_word(uint32_t a, uint32_t b, uint32_t far) {
+        const uint32_t x = (a & 0x80000000u) | (b & 0x7FFFFFFFu);
+        return far ^ (x >> 1) ^ ((x & 1u) ? 0x9908B0DFu : 0u);
+    }
+    // in place, in index order: words below 227 combine with old words 397 on, later ones with new words 227 back
+    __device__ __forceinline__ void twist() {
+        for (int k = 0; k < 227; ++k) mt[k] = twist_word(mt[k], mt[k + 1], mt[k + 397]);
+        for (int k = 227; k < 623; ++k) mt[k] = twist_word(mt[k], mt[k + 1], mt[k - 227]);
+        mt[623] = twist_word(mt[623], mt[0], mt[396]);
+        i = 0;
+    }
+    __device__ __forceinline__ uint32_t next() {
+        if (i >= 624) twist();
+        uint32_t y = mt[i++];
+        y ^= y >> 11;
+        y ^= (y << 7) & 0x9D2C5680u;
+        y ^= (y << 15) & 0xEFC60000u;
+        y ^= y >> 18;
+        return y;
+    }
+};
+
+// Live masks of samples s0 .. s0 + 32 W - 1 (bit s - s0 of word (s - s0) / 32 of edge e's row): a warp takes 32
+// consecutive samples over one edge chunk, a lane per sample's stream, and forms each edge's word by ballot.
+// Lanes at or past nvalid (samples beyond the requested count) leave their bit 0.
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_mc_live(const DevProb *__restrict__ prob, uint64_t seed, int64_t s0,
+                                                    int64_t nvalid, int64_t nchunks) {
+    const DevProb &P = *prob;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    Mt19937 g;
+    for (uint64_t unit = warp; unit < static_cast<uint64_t>(W) * nchunks; unit += nwarps) {
+        const int k = static_cast<int>(unit % W);
+        const int64_t c = static_cast<int64_t>(unit / W);
+        const int64_t s = static_cast<int64_t>(k) * 32 + lane;
+        const bool valid = s < nvalid;
+        g.seed(static_cast<uint32_t>(splitmix64_at(seed, static_cast<uint64_t>(s0 + s) * nchunks + c) >> 32));
+        const int64_t e0 = c * kMcChunk;
+        const int64_t e1 = e0 + kMcChunk < P.m ? e0 + kMcChunk : P.m;
+        for (int64_t e = e0; e < e1; ++e) {
+            const uint32_t x = g.next();
+            uint32_t T;
+            bool ok;
+            edge_threshold(P, e, __ldg(&P.adj[e]), T, ok);
+            const unsigned b = __ballot_sync(kFull, valid && ok && x <= T);
+            if (lane == 0) P.live[static_cast<size_t>(e) * W + k] = b;
+        }
+    }
+}
+
+// Per-sample reach counts: counts[j] += |{v : bit j of vis[v]}|.  A block of 32 W threads, one per sample,
+// strides over the vertices.
+__global__ void k_sample_counts(const DevProb *__restrict__ prob, unsigned long long *counts) {
+    const DevProb &P = *prob;
+    const int j = threadIdx.x;
+    unsigned long long c = 0;
+    for (int64_t v = blockIdx.x; v < P.n; v += gridDim.x)
+        c += (__ldcg(&P.vis[static_cast<size_t>(v) * P.W + (j >> 5)]) >> (j & 31)) & 1u;
+    if (c) atomicAdd(&counts[j], c);
+}
+
 __global__ void k_indeg(const int32_t *__restrict__ adj, int64_t m, int32_t *__restrict__ indeg) {
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -2167,6 +2247,16 @@ void launch_vertex_desc(const DevProb &P, UnitD *vdesc, cudaStream_t s) {
 }
 void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s) {
     k_unit_desc<<<g_grid_block, kBlock, 0, s>>>(P, rdesc, tdesc);
+}
+void launch_mc_live(int R, const DevProb *prob, uint64_t seed, int64_t s0, int64_t nvalid, int64_t nchunks,
+                    cudaStream_t s) {
+    const int64_t warps = static_cast<int64_t>(R / 32) * nchunks;
+    const int64_t cap = static_cast<int64_t>(g_sms) * 8 * kWarpsPerBlock;  // 8 blocks an SM at most
+    const int blocks = static_cast<int>((std::min(warps, cap) + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (blocks > 0) IMK_R_SWITCH(R, (k_mc_live<RR / 32><<<blocks, kBlock, 0, s>>>(prob, seed, s0, nvalid, nchunks)));
+}
+void launch_sample_counts(int R, const DevProb *prob, unsigned long long *counts, cudaStream_t s) {
+    k_sample_counts<<<g_sms * 2, R, 0, s>>>(prob, counts);
 }
 void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, cudaStream_t s) {
     k_words<<<(R + 255) / 256, 256, 0, s>>>(seed, R, X, Y);

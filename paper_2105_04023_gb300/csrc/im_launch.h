@@ -26,6 +26,11 @@ void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact,
 // A whole search in one cooperative launch; false if the device cannot run it (the caller then steps levels).
 bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
 void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+// Influence scorer: live masks of samples s0 .. s0 + R - 1 (those at or past nvalid left dead) into prob->live,
+// and per-sample reach counts of prob->vis added into counts[R].
+void launch_mc_live(int R, const DevProb *prob, uint64_t seed, int64_t s0, int64_t nvalid, int64_t nchunks,
+                    cudaStream_t s);
+void launch_sample_counts(int R, const DevProb *prob, unsigned long long *counts, cudaStream_t s);
 void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned long long *gsum, cudaStream_t s);
 
 void launch_live_masks(const DevProb &P, cudaStream_t s);

@@ -383,3 +383,74 @@ def test_register_probe_equals_bruteforce(orc):
         for j in range(0, R, 7):
             assert probe(v, j) == ref[v, j]
     assert probe.reach_total([1, 5]) == int(bf.reached_by(g.n, g.xadj, g.adj, live, [1, 5], R).sum())
+
+
+# --- influence scoring: mt19937 sample-then-diffuse (Section 5's separate influence oracle, reading R15) ---------
+
+def test_mt19937_value_fixed_by_the_cpp_standard(orc):
+    # [rand.predef]: the 10000th consecutive output of a default-constructed std::mt19937 (seed 5489) is 4123659995.
+    assert int(orc.mt_outputs(5489, 10000)[-1]) == 4123659995
+
+
+@pytest.mark.parametrize("seed", [1, 5489, 0xDEADBEEF, 0xFFFFFFFF])
+def test_mt19937_matches_numpy(orc, seed):
+    # numpy's RandomState seeds its own MT19937 with init_genrand for an integer seed; a full-range uint32 draw is
+    # one raw output.  2000 outputs span four twists of the state.
+    ref = np.random.RandomState(seed).randint(0, 2 ** 32, size=2000, dtype=np.uint64).astype(np.uint32)
+    assert np.array_equal(orc.mt_outputs(seed, 2000), ref)
+
+
+def _reach_count(g, live, seeds):
+    """Vertices reached from `seeds` over the edges flagged in `live` (scipy breadth-first order per seed)."""
+    src = np.repeat(np.arange(g.n), np.diff(g.xadj))
+    keep = live.astype(bool)
+    A = sp.csr_matrix((np.ones(int(keep.sum())), (src[keep], g.adj[keep])), shape=(g.n, g.n))
+    seen = np.zeros(g.n, bool)
+    for s in set(int(x) for x in seeds):
+        seen[csg.breadth_first_order(A, s, directed=True, return_predecessors=False)] = True
+    return int(seen.sum())
+
+
+def test_influence_mc_equals_a_search_over_numpy_drawn_edges(orc):
+    # 20000+ edges: three generator streams per sample, so the per-chunk reseeding and the in-chunk output index
+    # are both exercised.  Edges are drawn here with numpy's MT19937 and the stream seeds of reading R15 (the high
+    # half of splitmix64 output s * nchunks + chunk), then searched with scipy.
+    g = graphs.erdos_renyi(3000, 21000, seed=41)
+    m = g.adj.shape[0]
+    assert m > 2 * orc.MC_CHUNK
+    nchunks = -(-m // orc.MC_CHUNK)
+    for model, p in ((IC, 0.12), (WC, 0.0)):
+        T, ok = orc.edge_thresholds(g.n, g.xadj, g.adj, model, p)
+        seeds = [7, 100, 7, 2999]
+        total, reach = orc.influence_mc(g.n, g.xadj, g.adj, model, p, seeds, 6, seed=99)
+        for s in range(6):
+            draws = np.concatenate([
+                np.random.RandomState(orc.splitmix64(99, s * nchunks + c) >> 32).randint(
+                    0, 2 ** 32, size=min(orc.MC_CHUNK, m - c * orc.MC_CHUNK), dtype=np.uint64)
+                for c in range(nchunks)])
+            live = ok.astype(bool) & (draws <= T)
+            assert reach[s] == _reach_count(g, live, seeds), (model, s)
+        assert total == int(reach.sum())
+
+
+def test_influence_mc_closed_forms(orc):
+    g = graphs.random_small(60, 240, seed=5)
+    seeds = [3, 3, 17]
+    # p = 0: nothing is live, every sample reaches exactly the distinct seeds
+    _, r0 = orc.influence_mc(g.n, g.xadj, g.adj, IC, 0.0, seeds, 64, seed=1)
+    assert (r0 == 2).all()
+    # p = 1: every edge is live, every sample reaches the seeds' reachability set in G
+    _, r1 = orc.influence_mc(g.n, g.xadj, g.adj, IC, 1.0, seeds, 64, seed=1)
+    assert (r1 == _reach_count(g, np.ones(g.adj.shape[0], np.uint8), seeds)).all()
+
+
+def test_influence_mc_star_expectation(orc):
+    # A star: the hub reaches each of its L leaves with probability p, so the mean reach is 1 + L p with standard
+    # error sqrt(L p (1 - p) / N); the mean over N = 4000 samples lies within 5 standard errors.
+    L, p, N = 200, 0.3, 4000
+    g = graphs.csr_from_edges(L + 1, np.zeros(L, np.int64), np.arange(1, L + 1))
+    total, reach = orc.influence_mc(g.n, g.xadj, g.adj, IC, p, [0], N, seed=2024)
+    assert abs(total / N - (1 + L * p)) < 5 * math.sqrt(L * p * (1 - p) / N)
+    assert reach.min() >= 1 and reach.max() <= L + 1
+    # a leaf as the only seed reaches itself alone
+    assert orc.influence_mc(g.n, g.xadj, g.adj, IC, p, [5], 64, seed=3)[0] == 64

@@ -216,8 +216,16 @@ im_status im_server_submit(im_server *srv, int32_t graph_id, const im_params *pa
 im_status im_server_footprint(im_server *srv, int32_t graph_id, const im_params *params, uint64_t *bytes);
 
 /* Admits queued queries that fit and advances every running query by one tick; reports how many queries are
- * running and queued afterwards (either pointer may be NULL). */
+ * running and queued afterwards (either pointer may be NULL).
+ * A query's first diffusion depends only on (graph, R, seed, eps_c, max_sweeps): the server keeps the sampled
+ * graph and the registers of each first diffusion it runs, within the budget, and a later query with the same five
+ * starts from them (same results: the diffusion is deterministic).  Kept diffusions are dropped, least recently
+ * used first, when an admission needs their room. */
 im_status im_server_step(im_server *srv, int32_t *active_out, int32_t *queued_out);
+
+/* Budget use of a server (HOST pointers, each may be NULL): bytes charged (running queries' reservations plus kept
+ * diffusions), kept diffusions, and queries started from a kept diffusion so far. */
+im_status im_server_info(const im_server *srv, uint64_t *used_bytes, int32_t *kept_builds, uint64_t *build_hits);
 
 /* Result of a ticket: IM_ENOTREADY while queued or running; IM_OK with seeds_out (params.K ids), sigma_out and
  * rebuilds_out (each may be NULL) once done, after which the ticket is forgotten; IM_ECANCELED for a cancelled

@@ -266,6 +266,14 @@ class Server:
     def im_server_cancel(self, ticket: int):
         self.ctx._check(self.ctx._L.im_server_cancel(self.h, ctypes.c_uint64(ticket)))
 
+    def im_server_info(self) -> dict:
+        used = ctypes.c_uint64()
+        kept = ctypes.c_int32()
+        hits = ctypes.c_uint64()
+        self.ctx._check(self.ctx._L.im_server_info(self.h, ctypes.addressof(used), ctypes.addressof(kept),
+                                                   ctypes.addressof(hits)))
+        return dict(used_bytes=used.value, kept_builds=kept.value, build_hits=hits.value)
+
 
 class Sketch:
     """An im_sketch: registers of a built sketch, kept on the device."""

@@ -67,6 +67,7 @@ SIGNATURES = {
     "im_server_footprint": (_I, [_P, _I32, ctypes.POINTER(im_params), _P]),
     "im_server_poll": (_I, [_P, ctypes.c_uint64, _P, _P, _P]),
     "im_server_cancel": (_I, [_P, ctypes.c_uint64]),
+    "im_server_info": (_I, [_P, _P, _P, _P]),
 }
 
 _lib = None

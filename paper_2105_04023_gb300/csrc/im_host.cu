@@ -279,6 +279,8 @@ struct Prob {
     im_params prm{};
     bool greedy = false;
     std::unique_ptr<DevMem> mem;
+    std::shared_ptr<DevMem> smem;  // the sampled graph (live masks, pair lists, unit descriptors): read-only once
+                                   // built, so queries with the same sample may share it
     DevProb dp{};
     DevProb *d_prob = nullptr;  // slot in the device descriptor array this problem was uploaded to
     DevCtr *d_ctr = nullptr;
@@ -328,7 +330,8 @@ inline int32_t dense_min_for(int R) { return std::max(8, R / 8); }
 void sample_edges(im_ctx *ctx, Prob &P) {
     const int64_t m = P.G->m;
     const int W = P.prm.R / 32;
-    DevMem &mem = *P.mem;
+    P.smem = std::make_shared<DevMem>(ctx->stream);
+    DevMem &mem = *P.smem;
     DevProb &d = P.dp;
     cudaStream_t s = ctx->stream;
     if (m >= (int64_t(1) << 32)) fail(IM_EINVAL, "graphs with 2^32 or more edges are not supported");
@@ -408,7 +411,39 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     d.vdesc = vdesc;
 }
 
+// The descriptor fields sample_edges sets (everything the sampled graph consists of).
+void copy_sample_fields(DevProb &d, const DevProb &src) {
+    d.dense_min = src.dense_min;
+    d.pull_sweeps = src.pull_sweeps;
+    d.live = src.live;
+    d.pofs = src.pofs;
+    d.dofs = src.dofs;
+    d.rdesc = src.rdesc;
+    d.tdesc = src.tdesc;
+    d.pv = src.pv;
+    d.pj = src.pj;
+    d.dlist = src.dlist;
+    d.ipofs = src.ipofs;
+    d.idofs = src.idofs;
+    d.iu = src.iu;
+    d.ij = src.ij;
+    d.idu = src.idu;
+    d.ide = src.ide;
+    d.vdesc = src.vdesc;
+}
+
+// A problem built from a cached first diffusion: `sample` (whose sampled graph it shares) is any problem of the
+// same graph, R, seed, eps_c and sweep limit; its own buffers are allocated and filled as make_prob would, except
+// that the sampling is not redone.
+std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const im_params &prm, bool greedy,
+                                const Prob *sample);
+
 std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const im_params &prm, bool greedy) {
+    return make_prob(ctx, std::move(G), prm, greedy, nullptr);
+}
+
+std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const im_params &prm, bool greedy,
+                                const Prob *sample) {
     auto P = std::make_unique<Prob>();
     P->G = std::move(G);
     P->prm = prm;
@@ -469,7 +504,14 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     P->flog_cap = 4096;
     d.flog_cap = static_cast<int32_t>(P->flog_cap);
     d.flog = mem.alloc<int64_t>(P->flog_cap, true);
-    sample_edges(ctx, *P);
+    if (sample) {
+        P->smem = sample->smem;
+        copy_sample_fields(d, sample->dp);
+        P->npairs = sample->npairs;
+        P->ndense = sample->ndense;
+    } else {
+        sample_edges(ctx, *P);
+    }
     if (greedy) {
         alloc_bfs(*P, ctx->stream);
         d.step_seed = mem.alloc<uint32_t>(prm.K);
@@ -1291,7 +1333,22 @@ struct im_server {
         int32_t rebuilds = 0;
         im_status status = IM_OK;
         std::string error;
+        bool fill = false;  // keep this query's first diffusion for later queries with the same one
     };
+    // First diffusions by (graph, R, seed, eps_c, sweep limit): the sampled graph and the registers the
+    // diffusion reached, for later queries that would compute exactly the same (their K and error thresholds only
+    // act after it).  Held within the budget; the least recently used go first when a query needs the room.
+    struct Build {
+        Prob sample;                   // the shared sampled graph (smem, the sampling fields of dp, pair counts)
+        std::unique_ptr<DevMem> rmem;  // the registers
+        uint8_t *M = nullptr;
+        DevCtr ctr{};                  // the counters right after the diffusion
+        uint64_t bytes = 0;
+        uint64_t last_use = 0;
+    };
+    using BuildKey = std::tuple<int32_t, int32_t, uint64_t, double, int64_t>;
+    std::map<BuildKey, Build> builds;
+    uint64_t clock = 0, build_hits = 0;
     std::map<uint64_t, Query> q;
     std::deque<uint64_t> queue;
     std::vector<size_t> free_slots;
@@ -1300,6 +1357,47 @@ struct im_server {
 };
 
 namespace {
+
+im_server::BuildKey build_key(const im_server::Query &Q) {
+    return {Q.gid, Q.prm.R, Q.prm.seed, Q.prm.eps_c, Q.prm.max_sweeps};
+}
+
+// Drops the least recently used kept diffusion other than `spare` (nullable); false if there is none.  The memory
+// of a sampled graph that a running query still shares stays allocated until that query ends, inside its own
+// reservation.
+bool evict_build(im_server *srv, const im_server::BuildKey *spare) {
+    auto lru = srv->builds.end();
+    for (auto it = srv->builds.begin(); it != srv->builds.end(); ++it)
+        if ((!spare || it->first != *spare) && (lru == srv->builds.end() || it->second.last_use < lru->second.last_use))
+            lru = it;
+    if (lru == srv->builds.end()) return false;
+    srv->used -= lru->second.bytes;
+    srv->builds.erase(lru);
+    return true;
+}
+
+// Keeps query Q's first diffusion (just finished: its registers are the result buffer) if the budget has room.
+void keep_build(im_server *srv, im_server::Query &Q) {
+    Prob &P = *Q.P;
+    const GraphDev &g = *srv->graphs[static_cast<size_t>(Q.gid)];
+    const size_t regs = static_cast<size_t>(g.n) * static_cast<size_t>(Q.prm.R);
+    const uint64_t bytes = P.smem->bytes + (std::max<size_t>(regs, 16) + 255) / 256 * 256;
+    if (srv->used + bytes > srv->budget) return;
+    im_server::Build b;
+    b.sample.smem = P.smem;
+    copy_sample_fields(b.sample.dp, P.dp);
+    b.sample.npairs = P.npairs;
+    b.sample.ndense = P.ndense;
+    b.rmem = std::make_unique<DevMem>(srv->ctx->stream);
+    b.M = b.rmem->alloc<uint8_t>(regs);
+    ck(cudaMemcpyAsync(b.M, P.last.res_par ? P.dp.M1 : P.dp.M0, regs, cudaMemcpyDeviceToDevice, srv->ctx->stream),
+       "keep registers");
+    b.ctr = P.last;
+    b.bytes = bytes;
+    b.last_use = ++srv->clock;
+    srv->used += b.bytes;
+    srv->builds[build_key(Q)] = std::move(b);
+}
 
 void server_release(im_server *srv, im_server::Query &Q) {
     if (Q.slot >= 0) {
@@ -1475,19 +1573,55 @@ im_status im_server_step(im_server *srv, int32_t *active_out, int32_t *queued_ou
             im_server::Query &Q = srv->q[t];
             const GraphDev &g = *srv->graphs[static_cast<size_t>(Q.gid)];
             const uint64_t est = query_footprint(g, Q.prm);
+            const auto key = build_key(Q);
+            // room for the query comes first: kept diffusions go, the one this query could start from last
+            while (srv->used + est > srv->budget && evict_build(srv, &key)) {
+            }
+            if (srv->used + est > srv->budget) evict_build(srv, nullptr);
             if (srv->used + est > srv->budget) break;
+            auto hit = srv->builds.find(key);
             srv->queue.pop_front();
-            Q.P = make_prob(ctx, srv->graphs[static_cast<size_t>(Q.gid)], Q.prm, true);
-            Q.bytes = est;  // the reservation: the query's allocations stay within it
-            srv->used += Q.bytes;
             const size_t slot = srv->free_slots.back();
             srv->free_slots.pop_back();
-            srv->eng->attach(slot, Q.P.get(), nullptr);
+            if (hit != srv->builds.end()) {
+                // the first diffusion is this kept one: share its sampled graph, copy its registers, and start
+                // at the first greedy step with the counters it ended with
+                im_server::Build &b = hit->second;
+                b.last_use = ++srv->clock;
+                Q.P = make_prob(ctx, srv->graphs[static_cast<size_t>(Q.gid)], Q.prm, true, &b.sample);
+                Prob &P = *Q.P;
+                ck(cudaMemcpyAsync(b.ctr.res_par ? P.dp.M1 : P.dp.M0, b.M,
+                                   static_cast<size_t>(g.n) * static_cast<size_t>(Q.prm.R), cudaMemcpyDeviceToDevice,
+                                   ctx->stream),
+                   "copy kept registers");
+                srv->eng->attach(slot, &P, &b.ctr);
+                P.phase = Prob::kScan;
+                P.builds = 1;
+                Q.fill = false;
+                srv->build_hits += 1;
+            } else {
+                Q.P = make_prob(ctx, srv->graphs[static_cast<size_t>(Q.gid)], Q.prm, true);
+                srv->eng->attach(slot, Q.P.get(), nullptr);
+                Q.fill = true;
+            }
+            Q.bytes = est;  // the reservation: the query's allocations stay within it
+            srv->used += Q.bytes;
             srv->slot_ticket[slot] = t;
             Q.slot = static_cast<int64_t>(slot);
             Q.state = 1;
         }
         srv->eng->tick();
+        // keep first diffusions that just finished, before the next tick's kernels run
+        for (size_t slot = 0; slot < srv->slot_ticket.size(); ++slot) {
+            const uint64_t t = srv->slot_ticket[slot];
+            if (!t) continue;
+            im_server::Query &Q = srv->q[t];
+            const Prob &P = *Q.P;
+            if (Q.fill && P.status == IM_OK && P.phase == Prob::kScan && P.step == 0 && P.builds == 1) {
+                Q.fill = false;
+                if (srv->builds.find(build_key(Q)) == srv->builds.end()) keep_build(srv, Q);
+            }
+        }
         // harvest finished queries and free their memory
         for (size_t slot = 0; slot < srv->slot_ticket.size(); ++slot) {
             const uint64_t t = srv->slot_ticket[slot];
@@ -1513,6 +1647,14 @@ im_status im_server_step(im_server *srv, int32_t *active_out, int32_t *queued_ou
         if (active_out) *active_out = active;
         if (queued_out) *queued_out = static_cast<int32_t>(srv->queue.size());
     });
+}
+
+im_status im_server_info(const im_server *srv, uint64_t *used_bytes, int32_t *kept_builds, uint64_t *build_hits) {
+    if (!srv) return IM_EINVAL;
+    if (used_bytes) *used_bytes = srv->used;
+    if (kept_builds) *kept_builds = static_cast<int32_t>(srv->builds.size());
+    if (build_hits) *build_hits = srv->build_hits;
+    return IM_OK;
 }
 
 im_status im_server_poll(im_server *srv, uint64_t ticket, int32_t *seeds_out, double *sigma_out,

@@ -130,3 +130,27 @@ def test_cancel_running_query_frees_its_slot(ctx):
     res = _drain(srv, {t2})
     assert res[t2]["seeds"].tolist() == _alone(ctx, 0, 2, 64, 10)["seeds"].tolist()
     srv.close()
+
+
+def test_repeated_first_diffusions_are_reused(ctx):
+    # queries that share (graph, R, seed) start from the kept first diffusion and still answer exactly what they
+    # answer alone; a different seed or R does not hit
+    srv = im.Server(ctx, hbm_budget_bytes=8 << 30, max_active=4)
+    gids = [srv.im_server_add_graph(_graph(i)) for i in range(2)]
+    first = [(0, 6, 256, 31), (1, 4, 64, 32)]
+    rest = [(0, 9, 256, 31), (0, 3, 256, 31), (1, 7, 64, 32), (0, 5, 128, 31), (1, 2, 64, 33), (0, 8, 256, 31)]
+    res, tickets = {}, {}
+    for batch in (first, rest):
+        ts = {srv.im_server_submit(gids[q[0]], im.params(R=q[2], K=q[1], eps_g=0.01, seed=q[3])): q for q in batch}
+        res.update(_drain(srv, set(ts)))
+        tickets.update(ts)
+    info = srv.im_server_info()
+    assert info["build_hits"] == 4, info  # the four later queries with the keys of the first two
+    assert info["kept_builds"] == 4, info  # one per distinct (graph, R, seed)
+    assert info["used_bytes"] > 0
+    for t, q in tickets.items():
+        alone = _alone(ctx, *q)
+        assert res[t]["seeds"].tolist() == alone["seeds"].tolist(), q
+        assert res[t]["sigma_final"] == alone["sigma_final"]
+        assert res[t]["rebuilds"] == alone["rebuilds"]
+    srv.close()

@@ -313,8 +313,8 @@ void alloc_bfs(Prob &P, cudaStream_t s) {
     for (auto &d : P.dp.del) d = mem.alloc<uint32_t>(n * W, true);
     P.dp.lstamp = mem.alloc<uint32_t>(n, true);
     P.dp.inS = mem.alloc<uint32_t>(words, true);
-    // tasks of a level: at most one per vertex with out-edges plus one per kBfsTaskEdges out-edges
-    const size_t ntask = static_cast<size_t>(n + P.G->m / kBfsTaskEdges + 1);
+    // tasks of a level: at most one per vertex plus one per kBfsTaskEdgesMin out-edges
+    const size_t ntask = static_cast<size_t>(n + P.G->m / kBfsTaskEdgesMin + 1);
     for (auto &t : P.dp.T) t = mem.alloc<int4>(ntask);
     for (auto &v : P.dp.V) v = mem.alloc<int32_t>(n);
     P.has_bfs = true;
@@ -1300,7 +1300,7 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     b += r(4 * n) + r(8 * (static_cast<uint64_t>(g.m) / 512 + 1));  // changed lists
     b += r(R) + r(8 * 4096);                                 // M_S', frontier log
     b += r(4 * n * W) * 4 + r(4 * words) + r(4 * n) * 4;  // reach and delta bits, seed-set bits, stamps, frontiers
-    b += r(sizeof(int4) * (n + static_cast<uint64_t>(g.m) / kBfsTaskEdges + 1)) * 2;  // search tasks
+    b += r(sizeof(int4) * (n + static_cast<uint64_t>(g.m) / kBfsTaskEdgesMin + 1)) * 2;  // search tasks
     const uint64_t m1 = std::max<uint64_t>(static_cast<uint64_t>(g.m), 1);
     b += r(4 * W * m1);                                      // live-simulation masks of the edges
     b += r(8 * (m1 + 1)) * 4;                                // pair and dense-edge offsets, out- and in-CSR order

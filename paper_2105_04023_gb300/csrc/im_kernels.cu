@@ -1169,28 +1169,28 @@ __global__ void __launch_bounds__(kBlock) k_scan(const DevProb *__restrict__ pro
 namespace {
 constexpr int kFirstTask = 0x100;  // flag in a task's edge-count field: the vertex's first task (it counts the row)
 
-// Search task c of vertex v, whose out-edges start at edge e: kBfsTaskEdges of them (fewer in the last task, none
-// for a vertex without out-edges), so a level reads neither the task's vertex offsets nor its degree.
-__device__ __forceinline__ int4 bfs_task(uint32_t v, int64_t e, int64_t deg, uint32_t c) {
-    const int64_t e0 = e + static_cast<int64_t>(c) * kBfsTaskEdges;
-    const int64_t left = deg - static_cast<int64_t>(c) * kBfsTaskEdges;
-    const int ne = static_cast<int>(left < kBfsTaskEdges ? left : kBfsTaskEdges);
+// Search task c of vertex v, whose out-edges start at edge e: te of them (fewer in the last task, none for a
+// vertex without out-edges), so a level reads neither the task's vertex offsets nor its degree.
+__device__ __forceinline__ int4 bfs_task(uint32_t v, int64_t e, int64_t deg, uint32_t c, int te) {
+    const int64_t e0 = e + static_cast<int64_t>(c) * te;
+    const int64_t left = deg - static_cast<int64_t>(c) * te;
+    const int ne = static_cast<int>(left < te ? left : te);
     return make_int4(static_cast<int>(static_cast<uint32_t>(e0)), static_cast<int>(static_cast<uint64_t>(e0) >> 32),
                      static_cast<int>(v), ne | (c == 0 ? kFirstTask : 0));
 }
 
-// Tasks of a vertex: one per kBfsTaskEdges out-edges, and one for a vertex without out-edges, whose first task
-// still counts the bits its delta row newly reached.
-__device__ __forceinline__ uint32_t bfs_ntasks(int64_t deg) {
-    return deg > 0 ? static_cast<uint32_t>((deg + kBfsTaskEdges - 1) / kBfsTaskEdges) : 1u;
+// Tasks of a vertex: one per te out-edges, and one for a vertex without out-edges, whose first task still counts
+// the bits its delta row newly reached.
+__device__ __forceinline__ uint32_t bfs_ntasks(int64_t deg, int te) {
+    return deg > 0 ? static_cast<uint32_t>((deg + te - 1) / te) : 1u;
 }
 
 // Appends the search tasks of vertex v.
-__device__ __forceinline__ void bfs_tasks(int4 *T, uint32_t *count, uint32_t v, const int64_t *xadj) {
+__device__ __forceinline__ void bfs_tasks(int4 *T, uint32_t *count, uint32_t v, const int64_t *xadj, int te) {
     const int64_t e = xadj[v], deg = xadj[v + 1] - e;
-    const uint32_t nt = bfs_ntasks(deg);
+    const uint32_t nt = bfs_ntasks(deg, te);
     const uint32_t at = atomicAdd(count, nt);
-    for (uint32_t c = 0; c < nt; ++c) T[at + c] = bfs_task(v, e, deg, c);
+    for (uint32_t c = 0; c < nt; ++c) T[at + c] = bfs_task(v, e, deg, c, te);
 }
 }  // namespace
 
@@ -1243,7 +1243,7 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
         C.nVl[L % 3u] = 1;
         C.nVl[(L + 1u) % 3u] = 0;
         P.V[L % 3u][0] = static_cast<int32_t>(s);
-        bfs_tasks(P.T[L & 1u], &C.nT[L & 1u], s, P.xadj);
+        bfs_tasks(P.T[L & 1u], &C.nT[L & 1u], s, P.xadj, bfs_task_edges(P.W));
         C.lvl0 = L;
         C.bdone = added ? 0u : 1u;
         C.btimeout = 0;
@@ -1271,7 +1271,7 @@ __global__ void k_seed_set(const DevProb *__restrict__ prob, const int32_t *__re
             const uint32_t prev = atomicOr(&P.inS[s >> 5], 1u << (s & 31));
             if (!((prev >> (s & 31)) & 1u)) {
                 P.V[L % 3u][atomicAdd(&C.nVl[L % 3u], 1u)] = s;
-                bfs_tasks(P.T[L & 1u], &C.nT[L & 1u], static_cast<uint32_t>(s), P.xadj);
+                bfs_tasks(P.T[L & 1u], &C.nT[L & 1u], static_cast<uint32_t>(s), P.xadj, bfs_task_edges(P.W));
             }
         }
     }
@@ -1307,7 +1307,7 @@ constexpr int kStage = 32;  // vertices a warp lists before it reserves room for
 // L + 1: one reservation per list for the whole batch, so the list counters see one atomic per kStage listed
 // vertices rather than one per listing warp.
 __device__ __forceinline__ void bfs_flush(const DevProb &P, const int32_t *stage, uint32_t c, int32_t *Vn,
-                                          uint32_t *nV, int4 *Tn, uint32_t *nT, int lane) {
+                                          uint32_t *nV, int4 *Tn, uint32_t *nT, int lane, int te) {
     __syncwarp();
     int32_t v = 0;
     int64_t e = 0, deg = 0;
@@ -1316,7 +1316,7 @@ __device__ __forceinline__ void bfs_flush(const DevProb &P, const int32_t *stage
         v = stage[lane];
         e = __ldg(&P.xadj[v]);
         deg = __ldg(&P.xadj[v + 1]) - e;
-        k = bfs_ntasks(deg);
+        k = bfs_ntasks(deg, te);
     }
     uint32_t incl = k;
 #pragma unroll
@@ -1332,7 +1332,7 @@ __device__ __forceinline__ void bfs_flush(const DevProb &P, const int32_t *stage
     tb = __shfl_sync(kFull, tb, 31) + incl - k;
     if (lane < static_cast<int>(c)) Vn[vb + lane] = v;
     if (k <= 2)
-        for (uint32_t t = 0; t < k; ++t) Tn[tb + t] = bfs_task(static_cast<uint32_t>(v), e, deg, t);
+        for (uint32_t t = 0; t < k; ++t) Tn[tb + t] = bfs_task(static_cast<uint32_t>(v), e, deg, t, te);
     // vertices with more tasks write them with the whole warp
     for (unsigned big = __ballot_sync(kFull, k > 2); big; big &= big - 1u) {
         const int f = __ffs(big) - 1;
@@ -1341,13 +1341,13 @@ __device__ __forceinline__ void bfs_flush(const DevProb &P, const int32_t *stage
         const int64_t fd = __shfl_sync(kFull, deg, f);
         const uint32_t fn = __shfl_sync(kFull, k, f);
         const uint32_t fa = __shfl_sync(kFull, tb, f);
-        for (uint32_t t = lane; t < fn; t += 32) Tn[fa + t] = bfs_task(fv, fe, fd, t);
+        for (uint32_t t = lane; t < fn; t += 32) Tn[fa + t] = bfs_task(fv, fe, fd, t, te);
     }
     __syncwarp();
 }
 
-// One level L of the bit-parallel reachability search of Algorithm 1, over all simulations at once: one warp per
-// task (kBfsTaskEdges out-edges of a frontier vertex u, one a lane).  The delta d of u goes out over each edge
+// One level L of the bit-parallel reachability search of Algorithm 1, over all simulations at once: a lane group
+// per task (TE = 16 out-edges of a frontier vertex u, one a lane, two tasks a warp; 32 and one for R = 1024).  The delta d of u goes out over each edge
 // e = (u, v) in the simulations where e is live; bits not yet reached at v are ORed into vis[v] and into v's next
 // delta, and the thread that stamps v first lists it in F_{L+1} (staged per warp in `stage`, kStage entries, and
 // moved to the global list with its tasks for level L + 1 in batches).  Pushers of one level may race on a bit:
@@ -1364,7 +1364,10 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
     // Up to 8 words (one 32-byte sector) a live row is loaded whole, together with the delta row; longer rows load
     // only the vectors where the delta has a bit.
     constexpr bool kEager = W <= 8;
+    constexpr int TE = bfs_task_edges(W);  // edges of a task, one a lane of its lane group
+    constexpr int NH = 32 / TE;            // tasks a warp takes at a time
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gl = lane % TE, g0 = lane - gl;  // this lane's place in its group, and the group's first lane
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + wib;
     const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
@@ -1376,8 +1379,9 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
         const uint32_t L = __ldcg(&C.lvl);
         const uint32_t p2 = L & 1u, p3 = L % 3u, n3 = (L + 1u) % 3u, c3 = (L + 2u) % 3u;
         const uint64_t nt = __ldcg(&C.nT[p2]);
+        const uint64_t ntw = (nt + NH - 1) / NH;  // warp items of tasks: tasks NH l .. NH l + NH - 1
         const uint64_t nclw = static_cast<uint64_t>(__ldcg(&C.nVl[c3])) * W;  // delta words of F_{L-1}
-        const uint64_t cnt = nt + (nclw + 31) / 32;
+        const uint64_t cnt = ntw + (nclw + 31) / 32;
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
         const int4 *T = P.T[p2];
@@ -1389,15 +1393,17 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
         unsigned long long added = 0;
         uint32_t ns = 0;  // staged vertices of this warp
         uint64_t l = first;
-        int4 tn = l < nt ? __ldcg(&T[l]) : make_int4(0, 0, 0, 0);
-        for (; l < nt; l += nworkers) {
-            const int4 t = tn;
-            if (l + nworkers < nt) tn = __ldcg(&T[l + nworkers]);  // the next task, while this one runs
+        const uint64_t hq = static_cast<uint64_t>(lane / TE);  // this lane group's task of the warp item
+        int4 tn = l < ntw && l * NH + hq < nt ? __ldcg(&T[l * NH + hq]) : make_int4(0, 0, 0, 0);
+        for (; l < ntw; l += nworkers) {
+            const int4 t = tn;  // empty (no edges, not first) past the last task
+            const uint64_t ln = l + nworkers;
+            if (ln < ntw) tn = ln * NH + hq < nt ? __ldcg(&T[ln * NH + hq]) : make_int4(0, 0, 0, 0);  // prefetch
             const int64_t e = static_cast<int64_t>((static_cast<uint64_t>(static_cast<uint32_t>(t.y)) << 32) |
-                                                   static_cast<uint32_t>(t.x)) + lane;
+                                                   static_cast<uint32_t>(t.x)) + gl;
             const int64_t u = static_cast<uint32_t>(t.z);
-            const bool has = lane < (t.w & (kFirstTask - 1));
-            const uint32_t dl = lane < W ? __ldcg(&dcur[static_cast<size_t>(u) * W + lane]) : 0u;
+            const bool has = gl < (t.w & (kFirstTask - 1));
+            const uint32_t dl = gl < W ? __ldcg(&dcur[static_cast<size_t>(u) * W + gl]) : 0u;
             if (t.w & kFirstTask) added += __popc(dl);  // u's row: the bits newly reached at u, counted once
             const int32_t v = has ? __ldg(&P.adj[e]) : 0;
             const uint32_t *lrow = P.live + static_cast<size_t>(e) * W;
@@ -1419,7 +1425,7 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
                 uint32_t d[VW], dor = 0;
 #pragma unroll
                 for (int k = 0; k < VW; ++k) {
-                    d[k] = __shfl_sync(kFull, dl, c + k);
+                    d[k] = __shfl_sync(kFull, dl, g0 + c + k);
                     dor |= d[k];
                 }
                 if (!kEager) {
@@ -1468,19 +1474,19 @@ __device__ __forceinline__ void bfs_level_phase(const DevProb *__restrict__ prob
             const unsigned mf = __ballot_sync(kFull, fresh);
             if (mf) {
                 if (ns + __popc(mf) > kStage) {
-                    bfs_flush(P, stage, ns, Vn, &C.nVl[n3], Tn, &C.nT[p2 ^ 1u], lane);
+                    bfs_flush(P, stage, ns, Vn, &C.nVl[n3], Tn, &C.nT[p2 ^ 1u], lane, TE);
                     ns = 0;
                 }
                 if (fresh) stage[ns + __popc(mf & lt)] = v;
                 ns += __popc(mf);
             }
         }
-        if (ns) bfs_flush(P, stage, ns, Vn, &C.nVl[n3], Tn, &C.nT[p2 ^ 1u], lane);
+        if (ns) bfs_flush(P, stage, ns, Vn, &C.nVl[n3], Tn, &C.nT[p2 ^ 1u], lane, TE);
         // zero the delta rows of F_{L-1}: level L + 1 writes its new bits there
         const int32_t *Vc = P.V[c3];
         uint32_t *dclr = P.del[c3];
         for (; l < cnt; l += nworkers) {
-            const uint64_t w = (l - nt) * 32 + lane;
+            const uint64_t w = (l - ntw) * 32 + lane;
             if (w < nclw) dclr[static_cast<size_t>(__ldcg(&Vc[w / W])) * W + w % W] = 0u;
         }
 #pragma unroll

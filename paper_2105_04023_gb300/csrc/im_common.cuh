@@ -14,9 +14,9 @@ constexpr int kHeavyDeg = 64;        // rows with more out-edges are split into 
 constexpr int kTaskEdges = 64;
 constexpr int kBigTasks = 32;        // split rows with more tasks are merged by a whole block
 constexpr int kBfsTaskEdges = 32;    // out-edges per search task with R = 1024 (one warp, one edge a lane)
-constexpr int kBfsTaskEdgesMin = 16; // out-edges per search task with R <= 512 (a half warp each, two a warp)
-// Out-edges per search task for rows of W words: a half warp holds the delta row of its task up to 16 words.
-__host__ __device__ constexpr int bfs_task_edges(int W) { return W <= 16 ? kBfsTaskEdgesMin : kBfsTaskEdges; }
+constexpr int kBfsTaskEdgesMin = 8;  // out-edges per search task with R <= 256 (four tasks a warp)
+// Out-edges per search task for rows of W words: a group of that many lanes holds the task's delta row.
+__host__ __device__ constexpr int bfs_task_edges(int W) { return W <= 8 ? 8 : (W <= 16 ? 16 : kBfsTaskEdges); }
 constexpr int kPushChunk = 1024;     // a changed vertex pushes its in-edges in units of at most this many
 constexpr int kMcChunk = 8192;      // edges per generator stream of the Monte-Carlo influence scorer
 constexpr int kCasLimit = 1024;      // compare-and-swap tries of one register-word update before it counts as a fault

@@ -1347,7 +1347,8 @@ __device__ __forceinline__ void bfs_flush(const DevProb &P, const int32_t *stage
 }
 
 // One level L of the bit-parallel reachability search of Algorithm 1, over all simulations at once: a lane group
-// per task (TE = 16 out-edges of a frontier vertex u, one a lane, two tasks a warp; 32 and one for R = 1024).  The delta d of u goes out over each edge
+// per task (TE out-edges of a frontier vertex u, one a lane, 32 / TE tasks a warp; TE = 8, 16 or 32 as R/32 words
+// fit a group).  The delta d of u goes out over each edge
 // e = (u, v) in the simulations where e is live; bits not yet reached at v are ORed into vis[v] and into v's next
 // delta, and the thread that stamps v first lists it in F_{L+1} (staged per warp in `stage`, kStage entries, and
 // moved to the global list with its tasks for level L + 1 in batches).  Pushers of one level may race on a bit:

@@ -328,7 +328,7 @@ def run_build(args, local):
 
 def run_mc(args, local):
     """The influence scorer on the bench workload: the 50 seeds the select picks, scored by sample-then-diffuse
-    Monte Carlo over --mc-samples mt19937-sampled graphs (Section 5's way of scoring seed sets), timed with CUDA
+    Monte Carlo over --mc-samples mt19937-sampled graphs (Section 4's way of scoring seed sets), timed with CUDA
     events; the oracle scores one sample on one core for comparison."""
     import torch
 

@@ -267,7 +267,7 @@ im_status im_estimate_static(im_ctx *ctx, const uint8_t *registers, int64_t n, i
 
 /*
  * Influence score of a seed set by plain sample-then-diffuse Monte Carlo, the way the paper's experiments score
- * every method's seed sets (Section 5, "Performance Metrics": a separate oracle that samples with mt19937 and then
+ * every method's seed sets (Section 4, "Performance Metrics": a separate oracle that samples with mt19937 and then
  * diffuses, independent of the hash-based sampling of Section 3.1).  In each of nsamples samples every edge is
  * drawn live or not with mt19937, and the vertices the k seeds reach over the live edges are counted:
  *   sample s draws edge e's value as output (e mod 8192) of its own mt19937 stream for the chunk of 8192 edges

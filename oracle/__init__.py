@@ -283,7 +283,7 @@ def mc_live(n, xadj, adj, model, p, seed, s, p_edge=None) -> np.ndarray:
 
 
 def influence_mc(n, xadj, adj, model, p, seeds, N, seed, p_edge=None, first=0):
-    """Sample-then-diffuse influence of `seeds` over samples first .. first + N - 1 (Section 5's oracle, reading
+    """Sample-then-diffuse influence of `seeds` over samples first .. first + N - 1 (Section 4's oracle, reading
     R15).  Returns (total reached over those samples, per-sample reach counts)."""
     xadj, adj = _csr(xadj, adj)
     S = np.ascontiguousarray(seeds, dtype=np.int32)

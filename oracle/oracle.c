@@ -33,7 +33,7 @@
  *   R10 e, sigma and the errors are computed in double from integer register sums and reach counts.
  *   R11 sigma is the mean reach of S over the same R hash-sampled graphs.
  *   R12 the rebuild decided after the K-th seed is recorded but its diffusion is not run (its sketch is never read).
- *   R15 influence scoring (the separate sample-then-diffuse oracle of the experiments, Section 5, which draws with
+ *   R15 influence scoring (the separate sample-then-diffuse oracle of the experiments, Section 4, which draws with
  *      mt19937): sample s draws edge e's value as output (e mod C) of its own mt19937 stream for the chunk of
  *      C = 8192 edges holding e (out-CSR order), seeded by init_genrand with the high half of splitmix64 output
  *      s * nchunks + floor(e / C) of the run seed; the edge is live iff the draw is <= T (R4's threshold).
@@ -539,7 +539,7 @@ int32_t or_mc_live(int64_t m, const uint32_t *T, const uint8_t *possible, uint64
 }
 
 /*
- * Influence of a seed set by plain sample-then-diffuse Monte Carlo (the influence oracle of Section 5): in each of
+ * Influence of a seed set by plain sample-then-diffuse Monte Carlo (the influence oracle of Section 4): in each of
  * the N samples s0 .. s0 + N - 1 every edge is drawn live or not (reading R15), and a breadth-first search from S
  * over the live edges counts the vertices reached.  reach[i] gets sample s0 + i's count (nullable); returns the
  * total over the samples, or a negative value on error.

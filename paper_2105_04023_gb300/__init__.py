@@ -171,7 +171,7 @@ class Context:
 
     def im_influence_mc(self, graph: Graph, seeds, nsamples: int, seed: int) -> tuple[float, np.ndarray]:
         """Sample-then-diffuse influence of a seed set over `nsamples` mt19937-sampled graphs (the scoring of
-        Section 5); returns (mean reach, reach of each sample)."""
+        Section 4); returns (mean reach, reach of each sample)."""
         _sync_torch()
         g = graph.c()
         S = np.ascontiguousarray(seeds, dtype=np.int32)

@@ -1076,7 +1076,7 @@ im_status im_build_sketches(im_ctx *ctx, const im_graph *graph, const im_params 
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Influence scoring by plain sample-then-diffuse Monte Carlo (Section 5's separate influence oracle), on the
+// Influence scoring by plain sample-then-diffuse Monte Carlo (Section 4's separate influence oracle), on the
 // device: live masks drawn with mt19937 streams (k_mc_live), then the seed set's reachability search over them
 // with the search kernels of the greedy loop, in batches of up to 1024 samples.
 

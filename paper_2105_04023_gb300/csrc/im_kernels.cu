@@ -1813,7 +1813,7 @@ __global__ void k_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y) {
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Influence scoring by plain sample-then-diffuse Monte Carlo (the separate influence oracle of Section 5, which
+// Influence scoring by plain sample-then-diffuse Monte Carlo (the separate influence oracle of Section 4, which
 // draws with mt19937).  Sample s draws edge e's value as output (e mod kMcChunk) of its own mt19937 stream for the
 // chunk of kMcChunk edges holding e (out-CSR order), seeded by init_genrand with the high half of splitmix64
 // output s * nchunks + floor(e / kMcChunk) of the run seed; the edge is live iff the draw is <= its threshold.

@@ -1,4 +1,4 @@
-"""Influence scorer (Section 5's sample-then-diffuse oracle with mt19937, reading R15): the CUDA path against the
+"""Influence scorer (Section 4's sample-then-diffuse oracle with mt19937, reading R15): the CUDA path against the
 CPU oracle, per sample and bit-exact (reach counts are integers)."""
 from __future__ import annotations
 

@@ -385,7 +385,7 @@ def test_register_probe_equals_bruteforce(orc):
     assert probe.reach_total([1, 5]) == int(bf.reached_by(g.n, g.xadj, g.adj, live, [1, 5], R).sum())
 
 
-# --- influence scoring: mt19937 sample-then-diffuse (Section 5's separate influence oracle, reading R15) ---------
+# --- influence scoring: mt19937 sample-then-diffuse (Section 4's separate influence oracle, reading R15) ---------
 
 def test_mt19937_value_fixed_by_the_cpp_standard(orc):
     # [rand.predef]: the 10000th consecutive output of a default-constructed std::mt19937 (seed 5489) is 4123659995.

@@ -36,11 +36,11 @@ def _check(ctx, g, model, p, seeds, N, seed, p_edge=None, device="cuda"):
     assert sigma == total / N  # both sides divide the same integers
 
 
-@pytest.mark.parametrize("N", [64, 192, 1024, 1088])
+@pytest.mark.parametrize("N", [64, 192, 512, 1024, 1088])
 @pytest.mark.parametrize("model,p", [(IC, 0.12), (WC, 0.0)])
 def test_mc_matches_oracle_per_sample(ctx, N, model, p):
-    # three generator streams per sample; 192 runs as one 256-sample batch with 64 unused columns, 1088 as a full
-    # 1024-sample batch plus a 64-sample one
+    # three generator streams per sample; 192 runs as one 256-sample batch with 64 unused columns, 512 with 16-edge
+    # search tasks, 1088 as a full 1024-sample batch plus a 64-sample one
     g = graphs.erdos_renyi(3000, 21000, seed=41)
     _check(ctx, g, model, p, [7, 100, 7, 2999], N, seed=99)
 

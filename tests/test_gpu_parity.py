@@ -82,7 +82,8 @@ def test_select_er2000_workload(ctx):
 @pytest.mark.parametrize("eps", [(0.0, 0.0), (math.inf, math.inf), (0.01, 0.3), (0.1, 0.5)],
                          ids=["always", "never", "paper", "loose"])
 @pytest.mark.parametrize("gname,model,p,R", [("rmat10", WC, 0.0, 64), ("er300", IC, 0.05, 256),
-                                             ("hub1500", IC, 0.1, 128)])
+                                             ("hub1500", IC, 0.1, 128), ("er300", IC, 0.05, 512),
+                                             ("rmat10", WC, 0.0, 1024)])
 def test_select_variants(ctx, eps, gname, model, p, R):
     g = SMALL[gname]
     assert_select_parity(ctx, g, model, p, R, K=8, eps_g=eps[0], eps_l=eps[1], seed=21)

@@ -1113,28 +1113,41 @@ __device__ void scan_problem(const DevProb &P, uint64_t cnt, uint64_t first, uin
             ms[c][3] = x.w;
         }
     }
+    // U rows a lane group in flight at once: their loads go out together, and apart from the seed-set test
+    constexpr int U = Gm::CPL == 1 ? 4 : (Gm::CPL == 2 ? 2 : 1);
     unsigned long long best = 0;
-    for (uint64_t l = first; l < cnt; l += nworkers) {
-        const int64_t v = static_cast<int64_t>(l) * Gm::NG + g;
-        uint32_t s = 0;
-        const bool ok = v < P.n && !test_bit(P.inS, v);
-        if (ok) {
-            const uint4 *row = reinterpret_cast<const uint4 *>(M + static_cast<size_t>(v) * R);
+    for (uint64_t l0 = first; l0 < cnt; l0 += U * nworkers) {
+        int64_t v[U];
+        bool ok[U];
+        uint4 x[U][Gm::CPL];
 #pragma unroll
-            for (int c = 0; c < Gm::CPL; ++c) {
-                const uint4 x = __ldg(row + li + Gm::G * c);
-                s = __dp4a(vmax4(x.x, ms[c][0]), 0x01010101u, s);
-                s = __dp4a(vmax4(x.y, ms[c][1]), 0x01010101u, s);
-                s = __dp4a(vmax4(x.z, ms[c][2]), 0x01010101u, s);
-                s = __dp4a(vmax4(x.w, ms[c][3]), 0x01010101u, s);
-            }
+        for (int u = 0; u < U; ++u) {
+            const uint64_t l = l0 + static_cast<uint64_t>(u) * nworkers;
+            v[u] = static_cast<int64_t>(l) * Gm::NG + g;
+            ok[u] = l < cnt && v[u] < P.n;
+            const uint4 *row = reinterpret_cast<const uint4 *>(M + static_cast<size_t>(ok[u] ? v[u] : 0) * R);
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) x[u][c] = ok[u] ? __ldg(row + li + Gm::G * c) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
-        for (int off = 1; off < Gm::G; off <<= 1) s += __shfl_xor_sync(kFull, s, off);
-        if (ok) {
-            const unsigned long long key =
-                (static_cast<unsigned long long>(s) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(v));
-            best = key > best ? key : best;
+        for (int u = 0; u < U; ++u) ok[u] = ok[u] && !test_bit(P.inS, v[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) {
+                s = __dp4a(vmax4(x[u][c].x, ms[c][0]), 0x01010101u, s);
+                s = __dp4a(vmax4(x[u][c].y, ms[c][1]), 0x01010101u, s);
+                s = __dp4a(vmax4(x[u][c].z, ms[c][2]), 0x01010101u, s);
+                s = __dp4a(vmax4(x[u][c].w, ms[c][3]), 0x01010101u, s);
+            }
+#pragma unroll
+            for (int off = 1; off < Gm::G; off <<= 1) s += __shfl_xor_sync(kFull, s, off);
+            if (ok[u]) {
+                const unsigned long long key =
+                    (static_cast<unsigned long long>(s) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(v[u]));
+                best = key > best ? key : best;
+            }
         }
     }
 #pragma unroll

@@ -1130,6 +1130,7 @@ im_status im_influence_mc(im_ctx *ctx, const im_graph *graph, const int32_t *see
         const int64_t nchunks = (G->m + kMcChunk - 1) / kMcChunk;
         std::unique_ptr<Prob> full, last;  // the 1024-sample problem reused by every full batch, the remainder's
         std::vector<Prob *> used;
+        std::vector<unsigned long long> reach(static_cast<size_t>(nsamples));  // written out only on success
         unsigned long long total = 0;
         for (int64_t s0 = 0; s0 < nsamples;) {
             const int64_t left = nsamples - s0;
@@ -1171,13 +1172,14 @@ im_status im_influence_mc(im_ctx *ctx, const im_graph *graph, const int32_t *see
             ck(cudaStreamSynchronize(s), "sync");
             for (int64_t j = 0; j < nb; ++j) {
                 total += h_counts[j];
-                if (reach_out) reach_out[s0 + j] = h_counts[j];
+                reach[static_cast<size_t>(s0 + j)] = h_counts[j];
             }
             s0 += nb;
         }
         tm.stop();
         end_call(ctx, used, tm.a, tm.b);
         *sigma_out = static_cast<double>(total) / static_cast<double>(nsamples);
+        if (reach_out) std::copy(reach.begin(), reach.end(), reach_out);
     });
 }
 

@@ -39,13 +39,22 @@ _dbl = ctypes.c_double
 _ptr = ctypes.c_void_p
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle source file to a shared library (plain gcc, -O2, no fused multiply-add contraction)."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile liboracle.so (plain gcc, -O2, no fused multiply-add contraction)."""
+    """Compile liboracle.so from oracle.c.  ORACLE_LIBRARY names another build to load instead: the mutation
+    tests point it at an oracle with one planted mistake, to show that a pin catches it."""
+    other = os.environ.get("ORACLE_LIBRARY")
+    if other:
+        return other
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC,
-                               "-lm"])
-        os.replace(tmp, _LIB)
+        compile_source(_SRC, _LIB)
     return _LIB
 
 

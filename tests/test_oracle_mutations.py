@@ -1,0 +1,57 @@
+"""Planted mistakes: each case compiles the oracle with one plausible mistake and requires a pin of
+``test_oracle_pins.py`` to fail on it, so the pins are shown to bite (a dropped term, a wrong sign, index or
+operand, a wrong constant).  CPU only; the mistakes are planted in a temporary copy of the oracle, never in the
+CUDA path."""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTATIONS = {
+    # Eq. 5 under reading R4: the live test's compare off by one
+    "live_compare": ("return possible && ((h ^ Xr) <= T);", "return possible && ((h ^ Xr) < T);"),
+    # Algorithm 2 as Jacobi sweeps: reading the registers being written (Gauss-Seidel)
+    "gauss_seidel": ("uint8_t mv = Mold[(size_t)v * (size_t)R + (size_t)j];",
+                     "uint8_t mv = M[(size_t)v * (size_t)R + (size_t)j];"),
+    # reading R6: the blocked-register test dropped
+    "blocked_dropped": ("if (blocked && blocked[at]) continue;", "if (0) continue;"),
+    # reading R5: a wrong vertex hash
+    "vertex_hash": ("or_fmix32((uint32_t)v ^ 0x9E3779B9u)", "or_fmix32((uint32_t)v ^ 0x9E3779B8u)"),
+    # reading R9: ties to the largest id
+    "tie_break": ("if (best < 0 || g > best_g)", "if (best < 0 || g >= best_g)"),
+    # Section 3.2.1: err_g divided by delta instead of sigma
+    "err_g_denominator": ("double err_g = fabs((e - delta) / sigma);", "double err_g = fabs((e - delta) / delta);"),
+    # MT19937: a tempering mask bit (bit 12; the low 7 bits of y << 7 are zero, so a change there is no mistake),
+    # the twist's far offset, the seeding multiplier
+    "mt_temper": ("y ^= (y << 7) & 0x9D2C5680u;", "y ^= (y << 7) & 0x9D2C4680u;"),
+    "mt_twist_offset": ("g->mt[(i + 397) % 624]", "g->mt[(i + 396) % 624]"),
+    "mt_seeding": ("1812433253u", "1812433255u"),
+    # reading R15: sample and chunk swapped in the stream index
+    "mc_stream_index": ("(uint64_t)s * (uint64_t)nchunks + (uint64_t)c", "(uint64_t)c * (uint64_t)nchunks + (uint64_t)s"),
+    # the scorer counting a repeated seed twice
+    "mc_seed_repeat": ("if (seen[S[i]]) continue;", "if (0) continue;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_a_pin_catches_the_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site of {name} not found exactly once"
+    src = tmp_path / "oracle_mutant.c"
+    src.write_text(text.replace(old, new))
+    lib = oracle.compile_source(str(src), str(tmp_path / "liboracle_mutant.so"))
+    env = dict(os.environ, ORACLE_LIBRARY=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x",
+                        "-q", "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode != 0, f"no pin failed with the planted mistake {name}:\n{r.stdout[-2000:]}"
+    assert "failed" in r.stdout, r.stdout[-2000:]

@@ -38,6 +38,30 @@ MUTATIONS = {
     "mc_stream_index": ("(uint64_t)s * (uint64_t)nchunks + (uint64_t)c", "(uint64_t)c * (uint64_t)nchunks + (uint64_t)s"),
     # the scorer counting a repeated seed twice
     "mc_seed_repeat": ("if (seen[S[i]]) continue;", "if (0) continue;"),
+    # reading R3: X and Y drawn from the same splitmix64 outputs
+    "sim_words_index": ("Y[r] = (uint32_t)(or_splitmix64(seed, 2u * (uint64_t)r + 1u) >> 32);",
+                        "Y[r] = (uint32_t)(or_splitmix64(seed, 2u * (uint64_t)r) >> 32);"),
+    # reading R2: the edge key's halves combined the other way round
+    "edge_hash_halves": ("return or_fmix32((uint32_t)key ^ or_fmix32((uint32_t)(key >> 32)));",
+                         "return or_fmix32((uint32_t)(key >> 32) ^ or_fmix32((uint32_t)key));"),
+    # reading R4 for weighted cascade: a threshold one too large
+    "wc_threshold": ("T[e] = (uint32_t)(0xFFFFFFFFull / (uint64_t)indeg[adj[e]]);",
+                     "T[e] = (uint32_t)(0xFFFFFFFFull / (uint64_t)indeg[adj[e]]) + 1u;"),
+    # reading R14: the visits of a sweep miscounted
+    "visits": ("visits += (uint64_t)R;", "visits += (uint64_t)R + 1u;"),
+    # reading R7: the eps_c stop one frontier vertex early (a change that never stops would hang the pins instead)
+    "eps_c_stop": ("if ((double)sizeL <= (double)n * eps_c) break;",
+                   "if ((double)sizeL <= (double)n * eps_c + 1.0) break;"),
+    # Algorithm 1's reach: an edge's liveness taken from the next simulation's word (a search that re-entered reached
+    # vertices would overrun its queue instead)
+    "reach_wrong_simulation": ("if (!or_is_live(or_edge_hash(u, v, n), X[j], T[e], possible[e])) continue;",
+                               "if (!or_is_live(or_edge_hash(u, v, n), X[(j + 1) % R], T[e], possible[e])) continue;"),
+    # Eq. 2: the FM correction factor
+    "phi": ("static const double OR_PHI = 0.77351;", "static const double OR_PHI = 0.7735;"),
+    # Eq. 3: M_S' merged with a min instead of a max
+    "merge_min": ("if (row[j] > MS[j]) MS[j] = row[j];", "if (row[j] < MS[j]) MS[j] = row[j];"),
+    # Section 3.2.1: the rebuild without the reached registers blocked
+    "rebuild_unblocked": ("or_init_registers(n, R, Y, reached, M);", "or_init_registers(n, R, Y, NULL, M);"),
 }
 
 
@@ -52,6 +76,6 @@ def test_a_pin_catches_the_planted_mistake(name, tmp_path):
     env = dict(os.environ, ORACLE_LIBRARY=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x",
                         "-q", "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True, text=True,
-                       timeout=600)
+                       timeout=300)
     assert r.returncode != 0, f"no pin failed with the planted mistake {name}:\n{r.stdout[-2000:]}"
     assert "failed" in r.stdout, r.stdout[-2000:]

@@ -62,6 +62,15 @@ MUTATIONS = {
     "merge_min": ("if (row[j] > MS[j]) MS[j] = row[j];", "if (row[j] < MS[j]) MS[j] = row[j];"),
     # Section 3.2.1: the rebuild without the reached registers blocked
     "rebuild_unblocked": ("or_init_registers(n, R, Y, reached, M);", "or_init_registers(n, R, Y, NULL, M);"),
+    # reading R8: the sketch kept only when both errors are small
+    "keep_rule_and": ("if (err_l < eps_l || err_g < eps_g) {", "if (err_l < eps_l && err_g < eps_g) {"),
+    # reading R9: seeds already in S scanned again
+    "argmax_includes_S": ("if (inS[v]) continue;", "if (0) continue;"),
+    # reading R8: delta = 0 read as no local error
+    "err_l_delta_zero": ("double err_l = (delta == 0.0) ? INFINITY : fabs((e - delta) / delta);",
+                         "double err_l = (delta == 0.0) ? 0.0 : fabs((e - delta) / delta);"),
+    # reading R12: the rebuild after the K-th seed run anyway
+    "last_rebuild_run": ("if (k + 1 < K) {", "if (k < K) {"),
 }
 
 

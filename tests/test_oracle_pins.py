@@ -355,6 +355,24 @@ def test_greedy_bruteforce_weighted_cascade_longer(orc):
     assert len(set(out["seeds"].tolist())) == 6
 
 
+@pytest.mark.parametrize("eps", [(0.0, 0.0), (math.inf, math.inf), (0.01, 0.3)], ids=["always", "never", "paper"])
+def test_greedy_bruteforce_every_vertex_a_seed(orc, eps):
+    # K = n: once the remaining gains all tie the argmax must still skip S (reading R9) and end with every vertex
+    g = graphs.random_small(9, 14, 66)
+    out = _greedy_case(orc, g, IC, 0.5, 64, g.n, eps[0], eps[1], seed=5)
+    assert sorted(out["seeds"].tolist()) == list(range(g.n))
+
+
+def test_greedy_bruteforce_step_that_reaches_nothing_new(orc):
+    # A star with p = 1: the hub reaches every leaf in every sample.  With thresholds near 0 the first step rebuilds
+    # (sigma becomes the reference), so the second seed, a leaf, has delta = 0: err_l is +infinity (reading R8) and
+    # err_g = e / sigma is far above the threshold, so that step rebuilds too.
+    g = graphs.csr_from_edges(10, np.zeros(9, np.int64), np.arange(1, 10))
+    out = _greedy_case(orc, g, IC, 1.0, 64, 3, 1e-9, 1e-9, seed=4)
+    assert out["seeds"].tolist()[0] == 0 and out["sigma"].tolist() == [10.0, 10.0, 10.0]
+    assert out["rebuilt"].tolist() == [1, 1, 1]
+
+
 def test_never_rebuild_runs_one_diffusion_and_always_rebuild_runs_k(orc):
     g = graphs.random_small(30, 120, 65)
     never = orc.select_seeds(g.n, g.xadj, g.adj, IC, 0.3, 64, 5, math.inf, math.inf, seed=2)

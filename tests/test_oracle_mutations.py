@@ -71,6 +71,13 @@ MUTATIONS = {
                          "double err_l = (delta == 0.0) ? 0.0 : fabs((e - delta) / delta);"),
     # reading R12: the rebuild after the K-th seed run anyway
     "last_rebuild_run": ("if (k + 1 < K) {", "if (k < K) {"),
+    # Algorithm 2's L: every out-neighbour pulled from, not only those that changed
+    "frontier_ignored": ("if (!inL[v]) continue;", "if (0) continue;"),
+    # reading R4: the threshold rounded down instead of up
+    "threshold_rounding": ("double c = ceil(p * 4294967296.0);", "double c = floor(p * 4294967296.0);"),
+    # reading R3: X drawn from the next splitmix64 output
+    "sim_words_shift": ("X[r] = (uint32_t)(or_splitmix64(seed, 2u * (uint64_t)r) >> 32);",
+                        "X[r] = (uint32_t)(or_splitmix64(seed, 2u * (uint64_t)r + 2u) >> 32);"),
 }
 
 

@@ -1391,7 +1391,11 @@ void keep_build(im_server *srv, im_server::Query &Q) {
     b.sample.npairs = P.npairs;
     b.sample.ndense = P.ndense;
     b.rmem = std::make_unique<DevMem>(srv->ctx->stream);
-    b.M = b.rmem->alloc<uint8_t>(regs);
+    try {
+        b.M = b.rmem->alloc<uint8_t>(regs);
+    } catch (const ImError &) {  // keeping is optional: without the room the queries just run the diffusion
+        return;
+    }
     ck(cudaMemcpyAsync(b.M, P.last.res_par ? P.dp.M1 : P.dp.M0, regs, cudaMemcpyDeviceToDevice, srv->ctx->stream),
        "keep registers");
     b.ctr = P.last;

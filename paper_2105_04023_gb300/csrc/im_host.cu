@@ -304,7 +304,7 @@ struct Prob {
 
 // Buffers of the reachability searches (the per-edge live-simulation masks they read come from the sampling).
 // The descriptor must be complete apart from its counters.
-void alloc_bfs(Prob &P, cudaStream_t s) {
+void alloc_bfs(Prob &P) {
     const int64_t n = P.G->n;
     const int W = P.prm.R / 32;
     DevMem &mem = *P.mem;
@@ -513,7 +513,7 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
         sample_edges(ctx, *P);
     }
     if (greedy) {
-        alloc_bfs(*P, ctx->stream);
+        alloc_bfs(*P);
         d.step_seed = mem.alloc<uint32_t>(prm.K);
         d.step_gsum = mem.alloc<uint32_t>(prm.K);
     }
@@ -1103,7 +1103,7 @@ std::unique_ptr<Prob> make_mc_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, int
     d.ok_edge = g.ok_edge;
     d.live = P->mem->alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(g.m, 1)) * d.W);
     d.max_sweeps = static_cast<uint32_t>(std::min<int64_t>(g.n + 2, 0x7FFFFFFF));
-    alloc_bfs(*P, ctx->stream);
+    alloc_bfs(*P);
     return P;
 }
 
@@ -1239,7 +1239,7 @@ im_status im_estimate(im_ctx *ctx, const im_sketch *sketch, const int32_t *seeds
         int32_t *d_seeds = tmp.alloc<int32_t>(k);
         ck(cudaMemcpyAsync(d_seeds, seeds, k * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy seeds");
         unsigned long long *d_g = tmp.alloc<unsigned long long>(1, true);
-        if (sigma_out && !P.has_bfs) alloc_bfs(P, s);
+        if (sigma_out && !P.has_bfs) alloc_bfs(P);
         std::vector<DevCtr> c0(1);
         c0[0].res_par = P.last.res_par;
         c0[0].sweeps_total = P.last.sweeps_total;

@@ -36,6 +36,8 @@ MUTATIONS = {
     "mt_seeding": ("1812433253u", "1812433255u"),
     # reading R15: sample and chunk swapped in the stream index
     "mc_stream_index": ("(uint64_t)s * (uint64_t)nchunks + (uint64_t)c", "(uint64_t)c * (uint64_t)nchunks + (uint64_t)s"),
+    # reading R15: a draw equal to the threshold read as dead
+    "mc_live_compare": ("live[e] = (uint8_t)(possible[e] && x <= T[e]);", "live[e] = (uint8_t)(possible[e] && x < T[e]);"),
     # the scorer counting a repeated seed twice
     "mc_seed_repeat": ("if (seen[S[i]]) continue;", "if (0) continue;"),
     # reading R3: X and Y drawn from the same splitmix64 outputs

@@ -462,6 +462,24 @@ def test_influence_mc_closed_forms(orc):
     assert (r1 == _reach_count(g, np.ones(g.adj.shape[0], np.uint8), seeds)).all()
 
 
+def test_influence_mc_draw_equal_to_threshold_is_live(orc):
+    # Reading R4's bound in the scorer: an edge whose draw equals its threshold is live.  On a star, every edge whose
+    # sample-0 draw d is below 2^24 gets p = (d + 1) / 2^32 (exact in float32, so T = ceil(p 2^32) - 1 = d); every
+    # other edge gets p = 0.  The hub then reaches exactly those leaves in sample 0.
+    L = 6000
+    g = graphs.csr_from_edges(L + 1, np.zeros(L, np.int64), np.arange(1, L + 1))
+    draws = orc.mt_outputs(orc.mc_stream_seed(31, 0, 0, 1), L)
+    hit = draws < (1 << 24)
+    pe = np.zeros(L, np.float32)
+    pe[hit] = ((draws[hit].astype(np.float64) + 1.0) / 2.0 ** 32).astype(np.float32)
+    assert np.array_equal(pe[hit].astype(np.float64) * 2.0 ** 32 - 1.0, draws[hit].astype(np.float64))
+    assert hit.sum() >= 5
+    T, ok = orc.edge_thresholds(g.n, g.xadj, g.adj, PER_EDGE, 0.0, pe)
+    assert np.array_equal(T[hit], draws[hit])
+    _, reach = orc.influence_mc(g.n, g.xadj, g.adj, PER_EDGE, 0.0, [0], 1, 31, p_edge=pe)
+    assert int(reach[0]) == 1 + int(hit.sum())
+
+
 def test_influence_mc_star_expectation(orc):
     # A star: the hub reaches each of its L leaves with probability p, so the mean reach is 1 + L p with standard
     # error sqrt(L p (1 - p) / N); the mean over N = 4000 samples lies within 5 standard errors.

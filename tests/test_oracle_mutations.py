@@ -73,6 +73,12 @@ MUTATIONS = {
                          "double err_l = (delta == 0.0) ? 0.0 : fabs((e - delta) / delta);"),
     # reading R12: the rebuild after the K-th seed run anyway
     "last_rebuild_run": ("if (k + 1 < K) {", "if (k < K) {"),
+    # the sweep limit one sweep late, the empty-graph guard, the K <= n check (found by an operator sweep)
+    "sweep_limit": ("if (max_sweeps > 0 && sweeps >= max_sweeps) break;",
+                    "if (max_sweeps > 0 && sweeps > max_sweeps) break;"),
+    "empty_graph_guard": ("    if (n <= 0) {\n        *sweeps_out = 0;", "    if (n < 0) {\n        *sweeps_out = 0;"),
+    "k_zero_accepted": ("if (n <= 0 || K < 1 || K > n || R < 1) return OR_EINVAL;",
+                        "if (n <= 0 || K < 0 || K > n || R < 1) return OR_EINVAL;"),
     # Algorithm 2's L: every out-neighbour pulled from, not only those that changed
     "frontier_ignored": ("if (!inL[v]) continue;", "if (0) continue;"),
     # reading R4: the threshold rounded down instead of up

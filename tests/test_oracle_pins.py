@@ -373,6 +373,28 @@ def test_greedy_bruteforce_step_that_reaches_nothing_new(orc):
     assert out["rebuilt"].tolist() == [1, 1, 1]
 
 
+def test_simulate_stops_at_the_sweep_limit(orc):
+    # a 40-vertex chain with every edge live needs a sweep per hop; a limit of 7 stops after exactly 7 sweeps
+    g = graphs.chain(40)
+    T, ok, X, Y = _problem(orc, g, IC, 1.0, 64, 3)
+    full = orc.simulate(g.n, g.xadj, g.adj, T, ok, 64, X, orc.init_registers(g.n, 64, Y))[0]
+    assert full >= 39
+    assert orc.simulate(g.n, g.xadj, g.adj, T, ok, 64, X, orc.init_registers(g.n, 64, Y), max_sweeps=7)[0] == 7
+
+
+def test_simulate_empty_graph(orc):
+    sweeps, visits, log = orc.simulate(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.uint32),
+                                       np.zeros(0, np.uint8), 64, np.zeros(64, np.uint32), np.zeros((0, 64), np.uint8))
+    assert (sweeps, visits, len(log)) == (0, 0, 0)
+
+
+@pytest.mark.parametrize("K,R", [(0, 64), (13, 64), (3, 0)])
+def test_select_seeds_rejects_bad_arguments(orc, K, R):
+    g = graphs.random_small(12, 30, 61)
+    with pytest.raises(RuntimeError):
+        orc.select_seeds(g.n, g.xadj, g.adj, IC, 0.5, R, K, 0.01, 0.3, seed=1)
+
+
 def test_never_rebuild_runs_one_diffusion_and_always_rebuild_runs_k(orc):
     g = graphs.random_small(30, 120, 65)
     never = orc.select_seeds(g.n, g.xadj, g.adj, IC, 0.3, 64, 5, math.inf, math.inf, seed=2)

@@ -1,13 +1,17 @@
 """Benchmark: sketch-based influence maximisation (HyperFuseR, arXiv 2105.04023) on one GB300.
 
 One step = one full seed selection (Algorithm 1: initial build, K greedy steps, reachability searches and the
-error-adaptive rebuilds) on the R-MAT scale-20 weighted-cascade workload (1,048,576 vertices, 16,085,964 edges after
-merging duplicates, R = 256 uint8 registers, K = 50, eps_g = 0.01, eps_l = 0.3) with inputs resident in HBM.
+error-adaptive rebuilds) with inputs resident in HBM.  Workloads (``--workload``):
+  chunglu22_ic (default): directed Chung-Lu graph, n = 2^22, mean degree 16, degree exponent 2.1 (m = 56,688,349
+      after merging duplicates), independent cascade p = 0.01, R = 512 uint8 registers, K = 100, eps_g = 0.02;
+  rmat20_wc: R-MAT scale 20, edge factor 16 (m = 16,085,964), weighted cascade, R = 256, K = 50, eps_g = 0.01.
 
 metric: sampled edge-simulation visits per second = (sum over every diffusion sweep of the step of
-|{(u,v): v in L}| * R) / step time; the end-to-end seconds per K-seed selection are reported beside it.
+|{(u,v): v in L}| * R) / step time.  This counts the work of the paper's Jacobi sweeps; the kernels skip the
+(edge, simulation) pairs that are not live, so the executed live pairs per second and the modelled bytes per second
+of the sweep kernels are reported beside it.  The end-to-end seconds per K-seed selection are reported too.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 Under torchrun every rank runs its own replica (the workload does not shard: replicas only) and rank 0 prints.
 """
 from __future__ import annotations
@@ -27,13 +31,29 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sampled edge-sim visits/sec"
 UNIT = "edge-sim visits/s"
-WORKLOAD = "rmat20_wc"
+WORKLOADS = {
+    "chunglu22_ic": "Chung-Lu n=2^22, mean degree 16, degree exponent 2.1, independent cascade p=0.01",
+    "rmat20_wc": "R-MAT scale 20, edge factor 16 (a,b,c,d = .57,.19,.19,.05), weighted cascade",
+}
+# the oracle sample of one step: the first Jacobi sweep over every ORACLE_STRIDE-th row
+ORACLE_STRIDE = {"chunglu22_ic": 32, "rmat20_wc": 1}
 
 
-def load_workload():
+def load_workload(name: str):
     from synth import workloads
 
-    return workloads.rmat20_wc(cache=True)
+    return getattr(workloads, name)(cache=True)
+
+
+def golden_record(name: str) -> dict | None:
+    """The oracle's recorded whole-run times for this workload (written with its golden file, see tests/golden)."""
+    path = os.path.join(ROOT, "tests", "golden", f"{name}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        g = json.load(f)
+    return {"build_s": g["build"].get("seconds"), "select_s": g["select"].get("seconds"),
+            "select_visits": g["select"]["visits"], "host": g.get("host", "recorded when the golden file was written")}
 
 
 def peaks():
@@ -134,49 +154,60 @@ def max_over_ranks(x: float, world: int) -> float:
     return aggregate(x, 0.0, world)[0]
 
 
-def oracle_sample(prob, sweeps: int = 1) -> tuple[float, int, float]:
-    """The CPU oracle as it stands on a bounded sample: the first `sweeps` Jacobi sweeps of the workload's build."""
+def oracle_sample(prob, stride: int = 1) -> tuple[float, int, float, int]:
+    """The CPU oracle as it stands on a bounded sample: the first Jacobi sweep of the workload's build over every
+    `stride`-th row (rows u with u mod stride = 0 keep their out-edges, the others have none in the sample;
+    thresholds are those of the whole graph), so that the sample has the graph's degree mix.  Returns
+    (visits/s, visits, seconds, rows sampled)."""
     import oracle
 
     g = prob.graph
     T, ok = oracle.edge_thresholds(g.n, g.xadj, g.adj, prob.model, p=prob.p)
+    keep_row = (np.arange(g.n) % stride) == 0
+    deg = np.diff(g.xadj)
+    keep_edge = np.repeat(keep_row, deg)
+    xadj = np.zeros(g.n + 1, np.int64)
+    np.cumsum(np.where(keep_row, deg, 0), out=xadj[1:])
+    adj = np.ascontiguousarray(g.adj[keep_edge])
     X, Y = oracle.sim_words(prob.seed, prob.R)
     M = oracle.init_registers(g.n, prob.R, Y)
     t = time.perf_counter()
-    _, visits, _ = oracle.simulate(g.n, g.xadj, g.adj, T, ok, prob.R, X, M, max_sweeps=sweeps)
+    _, visits, _ = oracle.simulate(g.n, xadj, adj, T[keep_edge], ok[keep_edge], prob.R, X, M, max_sweeps=1)
     dt = time.perf_counter() - t
-    return visits / dt, visits, dt
+    return visits / dt, visits, dt, int(keep_row.sum())
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    prob = load_workload()
+    prob = load_workload(args.workload)
+    stride = ORACLE_STRIDE[args.workload]
     vals = []
-    visits = 0
+    visits = rows = 0
     for i in range(args.warmup + args.steps):
-        v, visits, dt = oracle_sample(prob)
+        v, visits, dt, rows = oracle_sample(prob, stride)
         if i >= args.warmup:
             vals.append(dt)
     total = sum(vals)
     value = visits * len(vals) / total
-    sample = (f"first Jacobi sweep of the build on the full R-MAT scale-20 graph ({visits} edge-simulation visits) "
-              f"per step")
+    sample = (f"per step: the first Jacobi sweep of the build over every {stride}-th row of the full graph "
+              f"({rows} rows, {visits} edge-simulation visits)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(vals),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic", "config": config(prob, args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "recorded_whole_run": golden_record(args.workload)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def config(prob, args):
     g = prob.graph
-    return {"workload": "R-MAT scale 20, edge factor 16 (a,b,c,d = .57,.19,.19,.05), weighted cascade",
+    return {"workload": WORKLOADS[args.workload], "name": args.workload,
             "n": g.n, "m": g.m, "R": prob.R, "K": prob.K, "eps_g": prob.eps_g, "eps_l": prob.eps_l,
             "eps_c": prob.eps_c, "seed": prob.seed, "parallelism": f"replicas{args.gpus}",
-            "l2": "flushed between steps (256 MiB write); registers 2 x 256 MiB exceed L2"}
+            "l2": f"flushed between steps (256 MiB write); registers 2 x {g.n * prob.R >> 20} MiB exceed L2"}
 
 
 def run_ours(args, world, rank, local):
@@ -188,7 +219,7 @@ def run_ours(args, world, rank, local):
     from paper_2105_04023_gb300 import build as b
 
     b.build()
-    prob = load_workload()
+    prob = load_workload(args.workload)
     if args.k:
         prob.K = args.k
     g = prob.graph
@@ -260,7 +291,8 @@ def run_ours(args, world, rank, local):
         with open(tpath) as f:
             traffic = json.load(f).get("bytes_per_launch")
     if rank == 0:
-        cpu_v, cpu_visits, cpu_dt = oracle_sample(prob)
+        stride = ORACLE_STRIDE[args.workload]
+        cpu_v, cpu_visits, cpu_dt, cpu_rows = oracle_sample(prob, stride)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
@@ -275,8 +307,9 @@ def run_ours(args, world, rank, local):
                          "bytes_per_launch": prop_bytes / max(prop_launches, 1),
                          "launches": prop_launches, "ms": prop_ms},
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first Jacobi sweep of the build on the full graph ({cpu_visits} visits, "
-                                       f"{cpu_dt:.1f} s)"},
+                             "sample": f"first Jacobi sweep of the build over every {stride}-th row of the full "
+                                       f"graph ({cpu_rows} rows, {cpu_visits} visits, {cpu_dt:.1f} s)",
+                             "recorded_whole_run": golden_record(args.workload)},
             "e2e": {"value": e2e_all / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(g.xadj.nbytes + g.adj.nbytes), "d2h_bytes_per_step": 4 * prob.K + 8,
                     "ms_per_step": 1000 * e2e_s / max(1, args.steps)},
@@ -298,7 +331,7 @@ def run_build(args, local):
 
     torch.cuda.set_device(local)
     b.build()
-    prob = load_workload()
+    prob = load_workload(args.workload)
     g = prob.graph
     graph = im.Graph.from_synth(g, prob.model, prob.p, device=f"cuda:{local}")
     prm = im.params(R=prob.R, seed=prob.seed)
@@ -337,7 +370,7 @@ def run_mc(args, local):
 
     torch.cuda.set_device(local)
     b.build()
-    prob = load_workload()
+    prob = load_workload(args.workload)
     g = prob.graph
     graph = im.Graph.from_synth(g, prob.model, prob.p, device=f"cuda:{local}")
     ctx = im.Context(local)
@@ -518,6 +551,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chunglu22_ic", choices=sorted(WORKLOADS))
     ap.add_argument("--mode", default="select", choices=["select", "build", "batch", "serve", "mc"],
                     help="build: sketch builds only (for profiling); batch: the 256-graph batched workload; "
                          "serve: the query stream on a resident graph pool; mc: the Monte-Carlo influence scorer")

@@ -249,18 +249,20 @@ im_status im_server_cancel(im_server *srv, uint64_t ticket);
  * It returns what im_estimate returns without sigma: *est_out = 2^(g / R) / 0.77351 (Eq. 2), where g (also stored
  * in *gsum_out when it is not NULL) is the sum over the R simulations of the largest register of the k seeds
  * (Eq. 3).  The caller passes the data and owns it:
- *   registers: DEVICE pointer (device of ctx) to an n x R uint8 register matrix, row-major (row v = the R registers
- *              of vertex v), for example the output of im_sketch_registers copied to the device;
- *   seeds:     DEVICE pointer to k vertex ids;
+ *   registers: DEVICE pointer (device of ctx), 4-byte aligned, to an n x R uint8 register matrix, row-major (row v =
+ *              the R registers of vertex v), for example the output of im_sketch_registers copied to the device.
+ *              Any byte values are accepted (the library's own registers are at most 32);
+ *   seeds:     DEVICE pointer, 4-byte aligned, to k vertex ids;
  *   est_out, gsum_out: HOST pointers, written only on IM_OK.
- * Limits: R is 64, 128, 256, 512 or 1024; 1 <= k <= IM_STATIC_MAX_SEEDS; n >= 1.  Other values return IM_EINVAL,
- * and so does a seed id outside [0, n) (checked on the device, the row is then not read).
+ * Limits: R is 64, 128, 256, 512 or 1024; 1 <= k <= IM_STATIC_MAX_SEEDS; n >= 1.  Other values, and unaligned
+ * pointers, return IM_EINVAL, and so does a seed id outside [0, n) (checked on the device, the row is then not read).
  * Scratch: one static device array of about 64 KiB defined in the library, which every device that runs this
  * call keeps until the process exits.  The first call on a device looks up the array's address (once per device,
  * with that device current); make that first call before any stream capture on the device.  All calls share the
  * array and each call clears what it needs cleared, so calls that overlap on the GPU (from several threads or
- * streams) race and can return wrong results: serialise them.  Work runs on the context's stream and the call
- * returns after it completes.
+ * streams) race and can return wrong results: serialise them.  Work runs on the context's stream with the
+ * context's device current; the calling thread's current device is restored before the call returns, which is
+ * after the work completes.
  */
 im_status im_estimate_static(im_ctx *ctx, const uint8_t *registers, int64_t n, int32_t R, const int32_t *seeds,
                              int32_t k, double *est_out, uint64_t *gsum_out);

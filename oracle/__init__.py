@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
             "or_splitmix64": (_u64, [_u64, _u64]),
             "or_sim_words": (None, [_u64, _i32, _ptr, _ptr]),
             "or_edge_hash": (_u32, [_i64, _i64, _i64]),
+            "or_edge_hash_dir": (_u32, [_i64, _i64, _i64, _i32]),
             "or_clz32": (_i32, [_u32]),
             "or_init_rank": (_i32, [_i64, _u32]),
             "or_threshold_from_p": (_i32, [_dbl, _ptr]),
@@ -77,15 +78,15 @@ def lib() -> ctypes.CDLL:
             "or_edge_thresholds": (_i32, [_i64, _i64, _ptr, _ptr, _i32, _dbl, _ptr, _ptr, _ptr]),
             "or_init_registers": (None, [_i64, _i32, _ptr, _ptr, _ptr]),
             "or_simulate": (_i32, [_i64, _ptr, _ptr, _ptr, _ptr, _i32, _ptr, _ptr, _ptr, _dbl, _i64, _ptr, _ptr,
-                                   _ptr, _i64]),
-            "or_reach_add": (_i64, [_i64, _ptr, _ptr, _ptr, _ptr, _i32, _ptr, _i64, _ptr]),
+                                   _ptr, _i64, _i32]),
+            "or_reach_add": (_i64, [_i64, _ptr, _ptr, _ptr, _ptr, _i32, _ptr, _i64, _ptr, _i32]),
             "or_estimate_from_sum": (_dbl, [_u64, _i32]),
             "or_build": (_i32, [_i64, _i64, _ptr, _ptr, _i32, _dbl, _ptr, _i32, _u64, _dbl, _ptr, _ptr, _ptr, _ptr,
-                                _i64]),
+                                _i64, _i32]),
             "or_select_seeds": (_i32, [_i64, _i64, _ptr, _ptr, _i32, _dbl, _ptr, _i32, _i32, _dbl, _dbl, _dbl, _u64,
-                                       _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr]),
+                                       _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _i32, _i32]),
             "or_estimate_set": (_dbl, [_i64, _i32, _ptr, _ptr, _i32, _ptr]),
-            "or_register_at": (_i32, [_i64, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _i64, _i32, _ptr, _ptr]),
+            "or_register_at": (_i32, [_i64, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _i64, _i32, _ptr, _ptr, _i32]),
             "or_mt_outputs": (None, [_u32, _i64, _ptr]),
             "or_mc_stream_seed": (_u32, [_u64, _i64, _i64, _i64]),
             "or_mc_live": (_i32, [_i64, _ptr, _ptr, _u64, _i64, _ptr]),
@@ -126,6 +127,11 @@ def edge_hash(u: int, v: int, n: int) -> int:
     return int(lib().or_edge_hash(u, v, n))
 
 
+def edge_hash_dir(u: int, v: int, n: int, undirected: bool) -> int:
+    """Reading R16: an undirected input's edge hashes by its ordered key, the same in both directions."""
+    return int(lib().or_edge_hash_dir(u, v, n, 1 if undirected else 0))
+
+
 def clz32(x: int) -> int:
     return int(lib().or_clz32(x))
 
@@ -164,7 +170,8 @@ def init_registers(n, R, Y, blocked=None):
     return M
 
 
-def simulate(n, xadj, adj, T, possible, R, X, M, blocked=None, eps_c=0.0, max_sweeps=0, log_cap=4096):
+def simulate(n, xadj, adj, T, possible, R, X, M, blocked=None, eps_c=0.0, max_sweeps=0, log_cap=4096,
+             undirected=False):
     """Runs Algorithm 2 in place on M; returns (sweeps, visits, frontier sizes at the start of each sweep)."""
     xadj, adj = _csr(xadj, adj)
     assert M.flags.c_contiguous and M.dtype == np.uint8
@@ -176,20 +183,21 @@ def simulate(n, xadj, adj, T, possible, R, X, M, blocked=None, eps_c=0.0, max_sw
     vi = np.zeros(1, np.uint64)
     log = np.zeros(log_cap, np.int64)
     rc = lib().or_simulate(n, _p(xadj), _p(adj), _p(T), _p(possible), R, _p(X), _p(b), _p(M), eps_c, max_sweeps,
-                           _p(sw), _p(vi), _p(log), log_cap)
+                           _p(sw), _p(vi), _p(log), log_cap, 1 if undirected else 0)
     if rc != 0:
         raise RuntimeError(f"or_simulate rc={rc}")
     s = int(sw[0])
     return s, int(vi[0]), log[: min(s, log_cap)].copy()
 
 
-def reach_add(n, xadj, adj, T, possible, R, X, s, reached):
+def reach_add(n, xadj, adj, T, possible, R, X, s, reached, undirected=False):
     xadj, adj = _csr(xadj, adj)
     T = np.ascontiguousarray(T, dtype=np.uint32)
     possible = np.ascontiguousarray(possible, dtype=np.uint8)
     X = np.ascontiguousarray(X, dtype=np.uint32)
     assert reached.flags.c_contiguous and reached.dtype == np.uint8
-    r = lib().or_reach_add(n, _p(xadj), _p(adj), _p(T), _p(possible), R, _p(X), s, _p(reached))
+    r = lib().or_reach_add(n, _p(xadj), _p(adj), _p(T), _p(possible), R, _p(X), s, _p(reached),
+                           1 if undirected else 0)
     if r < 0:
         raise MemoryError
     return int(r)
@@ -199,7 +207,7 @@ def estimate_from_sum(g: int, R: int) -> float:
     return float(lib().or_estimate_from_sum(g, R))
 
 
-def build_sketch(n, xadj, adj, model, p, R, seed, p_edge=None, eps_c=0.0, log_cap=4096):
+def build_sketch(n, xadj, adj, model, p, R, seed, p_edge=None, eps_c=0.0, log_cap=4096, undirected=False):
     """Registers after a fresh build; returns (M[n, R], sweeps, visits, frontier log)."""
     xadj, adj = _csr(xadj, adj)
     M = np.zeros((n, R), np.uint8)
@@ -208,15 +216,17 @@ def build_sketch(n, xadj, adj, model, p, R, seed, p_edge=None, eps_c=0.0, log_ca
     vi = np.zeros(1, np.uint64)
     log = np.zeros(log_cap, np.int64)
     rc = lib().or_build(n, adj.shape[0], _p(xadj), _p(adj), model, p, _p(pe), R, seed, eps_c, _p(M), _p(sw), _p(vi),
-                        _p(log), log_cap)
+                        _p(log), log_cap, 1 if undirected else 0)
     if rc != 0:
         raise RuntimeError(f"or_build rc={rc}")
     s = int(sw[0])
     return M, s, int(vi[0]), log[: min(s, log_cap)].copy()
 
 
-def select_seeds(n, xadj, adj, model, p, R, K, eps_g, eps_l=0.3, eps_c=0.0, seed=1, p_edge=None):
-    """Algorithm 1; returns a dict of per-step arrays and run totals."""
+def select_seeds(n, xadj, adj, model, p, R, K, eps_g, eps_l=0.3, eps_c=0.0, seed=1, p_edge=None, literal=False,
+                 undirected=False):
+    """Algorithm 1; returns a dict of per-step arrays and run totals.  literal: blocked registers as Algorithms 1 and
+    2 print them (reading R17); undirected: reading R16."""
     xadj, adj = _csr(xadj, adj)
     pe = None if p_edge is None else np.ascontiguousarray(p_edge, dtype=np.float32)
     seeds = np.zeros(K, np.int32)
@@ -228,7 +238,8 @@ def select_seeds(n, xadj, adj, model, p, R, K, eps_g, eps_l=0.3, eps_c=0.0, seed
     sw = np.zeros(1, np.int64)
     nb = np.zeros(1, np.int32)
     rc = lib().or_select_seeds(n, adj.shape[0], _p(xadj), _p(adj), model, p, _p(pe), R, K, eps_g, eps_l, eps_c, seed,
-                               _p(seeds), _p(sigma), _p(est), _p(gsum), _p(rebuilt), _p(vis), _p(sw), _p(nb))
+                               _p(seeds), _p(sigma), _p(est), _p(gsum), _p(rebuilt), _p(vis), _p(sw), _p(nb),
+                               1 if literal else 0, 1 if undirected else 0)
     if rc != 0:
         raise RuntimeError(f"or_select_seeds rc={rc}")
     return dict(seeds=seeds, sigma=sigma, est=est, gsum=gsum, rebuilt=rebuilt, visits=int(vis[0]), sweeps=int(sw[0]),
@@ -246,8 +257,9 @@ def estimate_set(M: np.ndarray, S) -> tuple[float, int]:
 class RegisterProbe:
     """Evaluates single registers M_v[j] by breadth-first search (for sampled checks on large graphs)."""
 
-    def __init__(self, n, xadj, adj, model, p, R, seed, p_edge=None):
+    def __init__(self, n, xadj, adj, model, p, R, seed, p_edge=None, undirected=False):
         self.n = n
+        self.undirected = 1 if undirected else 0
         self.xadj, self.adj = _csr(xadj, adj)
         self.T, self.ok = edge_thresholds(n, self.xadj, self.adj, model, p=p, p_edge=p_edge)
         self.X, self.Y = sim_words(seed, R)
@@ -256,7 +268,7 @@ class RegisterProbe:
 
     def __call__(self, v: int, j: int) -> int:
         return int(lib().or_register_at(self.n, _p(self.xadj), _p(self.adj), _p(self.T), _p(self.ok), _p(self.X),
-                                        _p(self.Y), v, j, _p(self.seen), _p(self.queue)))
+                                        _p(self.Y), v, j, _p(self.seen), _p(self.queue), self.undirected))
 
     def reach_total(self, seeds) -> int:
         """|{(v, j): v reachable from the seed set in sample j}| summed over the R samples."""
@@ -264,7 +276,8 @@ class RegisterProbe:
         reached = np.zeros((self.n, R), np.uint8)
         total = 0
         for s in seeds:
-            total += reach_add(self.n, self.xadj, self.adj, self.T, self.ok, R, self.X, int(s), reached)
+            total += reach_add(self.n, self.xadj, self.adj, self.T, self.ok, R, self.X, int(s), reached,
+                               self.undirected)
         return total
 
 

@@ -20,12 +20,13 @@
  *      the MurmurHash3 finaliser (Eq. 4 names Murmur3); h_max = 2^32.
  *   R3 per-simulation words: the splitmix64 sequence (Steele, Lea & Flood 2014) seeded with the run seed; X_r is the
  *      high half of output 2r, Y_r (the "hash(j)" of the initialisation) the high half of output 2r+1.
- *   R4 live test: T = ceil(p * 2^32) - 1 and the edge is live iff (h XOR X_r) <= T, which is Eq. 5's "P < w"
- *      with P = (h XOR X_r) / 2^32; p <= 0 never samples the edge.  Weighted cascade uses p = 1/indeg(v) exactly:
- *      T = floor((2^32 - 1) / indeg(v)).
+ *   R4 live test: T = ceil(p * 2^32) - 1 and the edge is live iff (h XOR X_r) <= T, which is Eq. 5's comparison
+ *      of the draw with the edge weight, P < w, with P = (h XOR X_r) / 2^32; p <= 0 never samples the edge.
+ *      Weighted cascade uses p = 1/indeg(v) exactly: T = floor((2^32 - 1) / indeg(v)).
  *   R5 initial rank: rank(v, j) = clz32(fmix32(v XOR 0x9E3779B9) XOR Y_j), clz32(0) = 32.
  *   R6 blocked registers: on a rebuild every (v, j) with v in R_{G_j}(S) is set to 0 and never updated, so the
- *      rebuilt sketch is the sketch of the residual sample (Section 3.2.1: "remaining, unblocked vertices").
+ *      rebuilt sketch is the sketch of the residual sample (Section 3.2.1: the rebuild covers only the vertices
+ *      S has not reached).
  *   R7 eps_c: the diffusion stops after the first sweep with |L'| <= eps_c * |V| (Section 3.2).
  *   R8 thresholds: eps_g and eps_l are separate; a step keeps the sketch iff err_l < eps_l or err_g < eps_g;
  *      delta = 0 gives err_l = +infinity.
@@ -89,6 +90,17 @@ uint32_t or_edge_hash(int64_t u, int64_t v, int64_t n)
 {
     uint64_t key = (uint64_t)u * (uint64_t)n + (uint64_t)v;
     return or_fmix32((uint32_t)key ^ or_fmix32((uint32_t)(key >> 32)));
+}
+
+/*
+ * Reading R16 (undirected inputs, Section 4's undirected graphs stored with both directions): the two directions of
+ * an undirected edge are one edge of the influence graph, so both take the hash of the ordered key (min, max) and
+ * are live in the same simulations; a sampled undirected graph then reaches exactly the connected component.
+ */
+uint32_t or_edge_hash_dir(int64_t u, int64_t v, int64_t n, int32_t undirected)
+{
+    if (undirected && v < u) return or_edge_hash(v, u, n);
+    return or_edge_hash(u, v, n);
 }
 
 int32_t or_clz32(uint32_t x)
@@ -177,7 +189,8 @@ void or_init_registers(int64_t n, int32_t R, const uint32_t *Y, const uint8_t *b
  */
 int32_t or_simulate(int64_t n, const int64_t *xadj, const int32_t *adj, const uint32_t *T, const uint8_t *possible,
                     int32_t R, const uint32_t *X, const uint8_t *blocked, uint8_t *M, double eps_c, int64_t max_sweeps,
-                    int64_t *sweeps_out, uint64_t *visits_out, int64_t *frontier_log, int64_t log_cap)
+                    int64_t *sweeps_out, uint64_t *visits_out, int64_t *frontier_log, int64_t log_cap,
+                    int32_t undirected)
 {
     int64_t sweeps = 0;
     uint64_t visits = 0;
@@ -209,7 +222,7 @@ int32_t or_simulate(int64_t n, const int64_t *xadj, const int32_t *adj, const ui
                 int64_t v = adj[e];
                 if (!inL[v]) continue;
                 visits += (uint64_t)R;
-                uint32_t h = or_edge_hash(u, v, n);
+                uint32_t h = or_edge_hash_dir(u, v, n, undirected);
                 for (int32_t j = 0; j < R; ++j) {
                     size_t at = (size_t)u * (size_t)R + (size_t)j;
                     if (!or_is_live(h, X[j], T[e], possible[e])) continue;
@@ -243,12 +256,12 @@ int32_t or_simulate(int64_t n, const int64_t *xadj, const int32_t *adj, const ui
 }
 
 /*
- * Adds seed s to the reach sets (Algorithm 1: "reachability set of S, for all simulations"): for every simulation
+ * Adds seed s to the reach sets (Algorithm 1: the set S reaches, in every simulation): for every simulation
  * j a breadth-first search from s over the edges sampled in j, not entering vertices already in R_{G_j}(S).
  * `reached` holds one byte per (v, j).  Returns how many (v, j) pairs were newly reached.
  */
 int64_t or_reach_add(int64_t n, const int64_t *xadj, const int32_t *adj, const uint32_t *T, const uint8_t *possible,
-                     int32_t R, const uint32_t *X, int64_t s, uint8_t *reached)
+                     int32_t R, const uint32_t *X, int64_t s, uint8_t *reached, int32_t undirected)
 {
     int64_t added = 0;
     int64_t *queue = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
@@ -265,7 +278,7 @@ int64_t or_reach_add(int64_t n, const int64_t *xadj, const int32_t *adj, const u
                 int64_t v = adj[e];
                 size_t at = (size_t)v * (size_t)R + (size_t)j;
                 if (reached[at]) continue;
-                if (!or_is_live(or_edge_hash(u, v, n), X[j], T[e], possible[e])) continue;
+                if (!or_is_live(or_edge_hash_dir(u, v, n, undirected), X[j], T[e], possible[e])) continue;
                 reached[at] = 1;
                 queue[tail++] = v;
                 ++added;
@@ -285,7 +298,7 @@ double or_estimate_from_sum(uint64_t g, int32_t R)
 /* Registers after a fresh build: initialisation then Simulate with no blocked set. */
 int32_t or_build(int64_t n, int64_t m, const int64_t *xadj, const int32_t *adj, int32_t model, double p,
                  const float *p_edge, int32_t R, uint64_t seed, double eps_c, uint8_t *M, int64_t *sweeps_out,
-                 uint64_t *visits_out, int64_t *frontier_log, int64_t log_cap)
+                 uint64_t *visits_out, int64_t *frontier_log, int64_t log_cap, int32_t undirected)
 {
     uint32_t *X = (uint32_t *)malloc((size_t)R * 4), *Y = (uint32_t *)malloc((size_t)R * 4);
     uint32_t *T = (uint32_t *)malloc((size_t)(m > 0 ? m : 1) * 4);
@@ -297,7 +310,7 @@ int32_t or_build(int64_t n, int64_t m, const int64_t *xadj, const int32_t *adj, 
         if (rc == OR_OK) {
             or_init_registers(n, R, Y, NULL, M);
             rc = or_simulate(n, xadj, adj, T, possible, R, X, NULL, M, eps_c, 0, sweeps_out, visits_out, frontier_log,
-                             log_cap);
+                             log_cap, undirected);
         }
     }
     free(X);
@@ -312,11 +325,15 @@ int32_t or_build(int64_t n, int64_t m, const int64_t *xadj, const int32_t *adj, 
  * reach of S over the R samples), e (the sketch estimate of the gain since the last rebuild), the integer register
  * sum behind e, and whether the error check asked for a rebuild.  Totals: edge-simulation visits and sweeps over all
  * diffusions, and the number of diffusions run.
+ * literal: the rebuild as Algorithms 1 and 2 print it (reading R17): every register is re-initialised to its rank
+ * and Simulate only leaves the blocked (u, j) un-updated, so a blocked vertex keeps its rank and still passes it to
+ * unblocked in-neighbours; otherwise (reading R6) blocked registers are 0.  undirected: reading R16.
  */
 int32_t or_select_seeds(int64_t n, int64_t m, const int64_t *xadj, const int32_t *adj, int32_t model, double p,
                         const float *p_edge, int32_t R, int32_t K, double eps_g, double eps_l, double eps_c,
                         uint64_t seed, int32_t *seeds, double *sigma_out, double *est_out, uint64_t *gsum_out,
-                        uint8_t *rebuilt_out, uint64_t *visits_total, int64_t *sweeps_total, int32_t *builds_out)
+                        uint8_t *rebuilt_out, uint64_t *visits_total, int64_t *sweeps_total, int32_t *builds_out,
+                        int32_t literal, int32_t undirected)
 {
     if (n <= 0 || K < 1 || K > n || R < 1) return OR_EINVAL;
     size_t bytes = (size_t)n * (size_t)R;
@@ -341,7 +358,7 @@ int32_t or_select_seeds(int64_t n, int64_t m, const int64_t *xadj, const int32_t
     {
         int64_t sw;
         uint64_t vi;
-        rc = or_simulate(n, xadj, adj, T, possible, R, X, NULL, M, eps_c, 0, &sw, &vi, NULL, 0);
+        rc = or_simulate(n, xadj, adj, T, possible, R, X, NULL, M, eps_c, 0, &sw, &vi, NULL, 0, undirected);
         if (rc != OR_OK) goto done;
         sweeps += sw;
         visits += vi;
@@ -369,7 +386,7 @@ int32_t or_select_seeds(int64_t n, int64_t m, const int64_t *xadj, const int32_t
         /* e <- Estimate(Merge(M_S', M_s)) */
         double e = or_estimate_from_sum(best_g, R);
         /* R_G(S) and the Monte-Carlo influence sigma over the same R samples */
-        int64_t added = or_reach_add(n, xadj, adj, T, possible, R, X, s, reached);
+        int64_t added = or_reach_add(n, xadj, adj, T, possible, R, X, s, reached, undirected);
         if (added < 0) {
             rc = OR_ENOMEM;
             goto done;
@@ -394,8 +411,8 @@ int32_t or_select_seeds(int64_t n, int64_t m, const int64_t *xadj, const int32_t
                 /* re-initialise with R_G(S) blocked, M <- Simulate(G, M, J, R_G(S)) */
                 int64_t sw;
                 uint64_t vi;
-                or_init_registers(n, R, Y, reached, M);
-                rc = or_simulate(n, xadj, adj, T, possible, R, X, reached, M, eps_c, 0, &sw, &vi, NULL, 0);
+                or_init_registers(n, R, Y, literal ? NULL : reached, M);
+                rc = or_simulate(n, xadj, adj, T, possible, R, X, reached, M, eps_c, 0, &sw, &vi, NULL, 0, undirected);
                 if (rc != OR_OK) goto done;
                 sweeps += sw;
                 visits += vi;
@@ -444,7 +461,8 @@ double or_estimate_set(int64_t n, int32_t R, const uint8_t *M, const int32_t *S,
  * scratch of n bytes, all zero on entry and returned all zero; `queue` holds n entries.
  */
 int32_t or_register_at(int64_t n, const int64_t *xadj, const int32_t *adj, const uint32_t *T, const uint8_t *possible,
-                       const uint32_t *X, const uint32_t *Y, int64_t v, int32_t j, uint8_t *seen, int64_t *queue)
+                       const uint32_t *X, const uint32_t *Y, int64_t v, int32_t j, uint8_t *seen, int64_t *queue,
+                       int32_t undirected)
 {
     int64_t head = 0, tail = 0;
     int32_t best = 0;
@@ -457,7 +475,7 @@ int32_t or_register_at(int64_t n, const int64_t *xadj, const int32_t *adj, const
         for (int64_t e = xadj[u]; e < xadj[u + 1]; ++e) {
             int64_t w = adj[e];
             if (seen[w]) continue;
-            if (!or_is_live(or_edge_hash(u, w, n), X[j], T[e], possible[e])) continue;
+            if (!or_is_live(or_edge_hash_dir(u, w, n, undirected), X[j], T[e], possible[e])) continue;
             seen[w] = 1;
             queue[tail++] = w;
         }

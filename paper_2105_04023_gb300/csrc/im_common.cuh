@@ -20,6 +20,7 @@ __host__ __device__ constexpr int bfs_task_edges(int W) { return W <= 8 ? 8 : (W
 constexpr int kPushChunk = 1024;     // a changed vertex pushes its in-edges in units of at most this many
 constexpr int kMcChunk = 8192;      // edges per generator stream of the Monte-Carlo influence scorer
 constexpr int kCasLimit = 1024;      // compare-and-swap tries of one register-word update before it counts as a fault
+                                     // (the default of DevProb::cas_limit)
 
 enum Model : int32_t { kIC = 0, kWC = 1, kPerEdge = 2 };
 
@@ -43,6 +44,7 @@ struct GridBar {
     unsigned int tail;   // blocks of a frontier launch that finished: the last one ends the sweep or level
 };
 constexpr uint32_t kBarrierLimit = 1u << 20;  // polls of one barrier wait (under a second in all) before giving up
+                                              // (the default limit the persistent search is launched with)
 
 // Counters of one problem, written by the kernels and read back by the host after each engine tick.
 struct DevCtr {
@@ -65,9 +67,13 @@ struct DevCtr {
     unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total
     unsigned long long sweeps_total;  // sweeps, running total
     // greedy step (Algorithm 1) --------------------------------------------------------------------------------
-    unsigned long long best_key;      // max over candidates of (gsum << 32 | ~v)
+    unsigned long long best_key;      // max over candidates of (gain << 32 | ~v), gain = gsum - gms
+    unsigned long long cand_key;      // lazy scan: max over candidates of (stale gain << 32 | ~v)
+    unsigned long long tau_key;       // lazy scan: exact key of that candidate (the bound the others must beat)
     uint32_t s;          // seed chosen by the last step
     uint32_t gsum;       // sum_j max(M_S'[j], M_s[j]) of that seed
+    uint32_t gms;        // sum_j M_S'[j] (the register sum every candidate's gsum is compared over)
+    uint32_t pad_c;
     // reachability search ---------------------------------------------------------------------------------------
     uint32_t lvl;        // level of the current search
     uint32_t bdone;      // 1 once the search found no new vertex
@@ -110,6 +116,8 @@ struct DevProb {
     uint8_t *part;             // n_tasks x R partial maxima of heavy-row tasks
     uint32_t *part_any;        // bit per task: the task merged at least one neighbour
     uint32_t *Lb0, *Lb1;       // frontier bits: vertices changed in the previous sweep
+    uint16_t *dmask;           // n x R/16: per 16-simulation chunk of row v, the registers the previous sweep changed
+                               // (written by the frontier pass for the rows it copies, read by the next push sweep)
     int32_t *chg_list;         // compacted changed vertices with at most kPushChunk in-edges
     uint64_t *chg_hc;          // (chunk << 32) | v for the changed vertices with more in-edges
     uint32_t *live;            // m x W: edge e is live in simulation j (Eq. 4-5 evaluated once per run)
@@ -135,12 +143,15 @@ struct DevProb {
     uint32_t pull_sweeps;      // sweeps 0 .. pull_sweeps-1 pull into every row, later ones push
 
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
+    uint32_t *rany;            // bit per vertex: reached by S in some simulation (set at a rebuild; NULL: no search)
     uint32_t *del[3];          // n x W: bits newly reached at the previous level, by level mod 3
     uint32_t *lstamp;          // per vertex: 1 + the last level that listed it
     int4 *T[2];                // search tasks by level parity: {first edge (lo, hi), vertex, edge count}
     int32_t *V[3];             // frontier vertices by level mod 3
     uint32_t *inS;             // bit per vertex: in the seed set
     uint8_t *MS;               // R bytes: M_S'
+    uint32_t *gst;             // n: a candidate's last evaluated gain sum_j max(M_S'[j], M_v[j]) - sum_j M_S'[j]; an
+                               // upper bound of its gain until the sketch is rebuilt (M_S' only grows)
     DevCtr *ctr;
     uint32_t stop_thr;         // diffusion stops when |L'| <= stop_thr
     uint32_t max_sweeps;       // sweep / level limit
@@ -149,6 +160,8 @@ struct DevProb {
     uint32_t *step_seed;       // per greedy step k: seed (device trace)
     uint32_t *step_gsum;
     unsigned long long *step_reached;
+    uint32_t cas_limit;        // compare-and-swap tries of one register-word update before the fault flag is raised
+    uint32_t pad1;
 };
 
 // ------------------------------------------------------------------------------------------------------------

@@ -68,6 +68,12 @@ struct im_ctx {
     // run whole searches in one cooperative launch (IM_PERSISTENT=1); measured no faster than level-by-level
     // launches on the R-MAT workloads, whose levels are dominated by their own dependent loads, so off by default
     bool persistent = false;
+    // wait limits of the device-side waits; lowered only by the failure-detection tests (IM_TEST_CAS_LIMIT,
+    // IM_TEST_BARRIER_LIMIT) to make a wait run out without any fault
+    // lazy (CELF) argmax for greedy steps that keep the sketch (IM_CELF=0: a full scan every step; same results)
+    bool celf = true;
+    uint32_t cas_limit = kCasLimit;
+    uint32_t barrier_limit = kBarrierLimit;
 };
 
 namespace {
@@ -313,6 +319,7 @@ void alloc_bfs(Prob &P) {
     for (auto &d : P.dp.del) d = mem.alloc<uint32_t>(n * W, true);
     P.dp.lstamp = mem.alloc<uint32_t>(n, true);
     P.dp.inS = mem.alloc<uint32_t>(words, true);
+    P.dp.rany = mem.alloc<uint32_t>(words, true);
     // tasks of a level: at most one per vertex plus one per kBfsTaskEdgesMin out-edges
     const size_t ntask = static_cast<size_t>(n + P.G->m / kBfsTaskEdgesMin + 1);
     for (auto &t : P.dp.T) t = mem.alloc<int4>(ntask);
@@ -355,6 +362,9 @@ void sample_edges(im_ctx *ctx, Prob &P) {
         d.vdesc = vd0;
         d.ipofs = pofs;
         d.idofs = dofs;
+        // the first sweep of every diffusion visits every row through its descriptor (no pairs, no dense edges)
+        launch_unit_desc(d, rdesc, tdesc, s);
+        ctx->launches += 1;
         return;
     }
     launch_live_masks(d, s);
@@ -479,6 +489,7 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     d.T_vert = g.T_vert;
     d.T_edge = g.T_edge;
     d.ok_edge = g.ok_edge;
+    d.cas_limit = ctx->cas_limit;
     uint32_t *X = mem.alloc<uint32_t>(R);
     uint32_t *Y = mem.alloc<uint32_t>(R);
     launch_words(prm.seed, R, X, Y, ctx->stream);
@@ -492,6 +503,7 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     const int64_t words = (n + 31) / 32;
     d.Lb0 = mem.alloc<uint32_t>(words, true);
     d.Lb1 = mem.alloc<uint32_t>(words, true);
+    d.dmask = mem.alloc<uint16_t>(static_cast<size_t>(n) * (R / 16));
     d.chg_list = mem.alloc<int32_t>(n);
     // chunks of changed vertices with more than kPushChunk in-edges: ceil(d / 1024) <= d / 512 for d > 1024
     d.chg_hc = mem.alloc<uint64_t>(static_cast<size_t>(g.m / 512 + 1));
@@ -514,6 +526,7 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     }
     if (greedy) {
         alloc_bfs(*P);
+        d.gst = mem.alloc<uint32_t>(static_cast<size_t>(n));
         d.step_seed = mem.alloc<uint32_t>(prm.K);
         d.step_gsum = mem.alloc<uint32_t>(prm.K);
     }
@@ -606,14 +619,18 @@ struct Engine {
             b = get_event();
             ck(cudaEventRecord(a, s), "event");
         }
-        for (auto &rl : byR) launch_prop(rl.first, d_probs, dptr(rl.second), rl.second.count, combine, s);
-        if (combine)
+        int64_t nl = 0;
+        for (auto &rl : byR)
+            nl += launch_prop(rl.first, d_probs, dptr(rl.second), rl.second.count, combine, ctx->pull_sweeps > 1, s);
+        if (combine) {
             for (auto &rl : byR) launch_combine(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
+            nl += 2 * static_cast<int64_t>(byR.size());  // the two combine kernels
+        }
         if (ctx->timing) {
             ck(cudaEventRecord(b, s), "event");
             ctx->prop_ev.emplace_back(a, b);
         }
-        ctx->launches += (combine ? 3 : 1) * static_cast<int64_t>(byR.size());  // sweep kernel, two combine kernels
+        ctx->launches += nl;
         ctx->prop_launches += static_cast<int64_t>(byR.size());
     }
 
@@ -682,7 +699,8 @@ struct Engine {
                 if (ctx->persistent) {
                     size_t done = 0;
                     for (auto &rl : byR) {
-                        if (!launch_bfs_run(rl.first, d_probs, dptr(rl.second), rl.second.count, ctx->d_gbar, s))
+                        if (!launch_bfs_run(rl.first, d_probs, dptr(rl.second), rl.second.count, ctx->d_gbar,
+                                            ctx->barrier_limit, s))
                             break;
                         ++done;
                     }
@@ -699,25 +717,32 @@ struct Engine {
         });
     }
 
+    // The argmax of a greedy step: a full scan for the first step after a (re)build, the lazy scan (k_celf_*) for
+    // a step whose sketch was kept (the gains of its previous scans still bound the current ones).
     void enqueue_scan(const std::vector<int32_t> &ids) {
         if (ids.empty()) return;
         cudaStream_t s = ctx->stream;
-        std::vector<std::pair<int, List>> byR;
+        std::vector<std::pair<int, List>> full, lazy;
         for (int R : {64, 128, 256, 512, 1024}) {
-            std::vector<int32_t> sub;
-            for (int32_t i : ids)
-                if (probs[i]->prm.R == R) sub.push_back(i);
-            if (!sub.empty()) byR.emplace_back(R, add_list(sub));
+            std::vector<int32_t> fsub, lsub;
+            for (int32_t i : ids) {
+                if (probs[i]->prm.R != R) continue;
+                (ctx->celf && probs[i]->merge_pending ? lsub : fsub).push_back(i);
+            }
+            if (!fsub.empty()) full.emplace_back(R, add_list(fsub));
+            if (!lsub.empty()) lazy.emplace_back(R, add_list(lsub));
         }
         // one choose launch per problem: each records its own step index
         std::vector<std::pair<List, int>> chooses;
         for (int32_t i : ids) chooses.emplace_back(add_list({i}), probs[i]->step);
-        pending.push_back([this, byR, chooses, s]() {
+        pending.push_back([this, full, lazy, chooses, s]() {
+            int64_t nl = 0;
             phase(1, [&]() {
-                for (auto &rl : byR) launch_scan(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
+                for (auto &rl : full) launch_scan(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
+                for (auto &rl : lazy) nl += launch_celf(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
                 for (auto &c : chooses) launch_choose(d_probs, dptr(c.first), 1, c.second, s);
             });
-            ctx->launches += static_cast<int64_t>(byR.size() + chooses.size());
+            ctx->launches += nl + static_cast<int64_t>(full.size() + chooses.size());
         });
     }
 
@@ -1005,6 +1030,10 @@ im_status im_ctx_create(int device, void *cuda_stream, im_ctx **out) {
     if (const char *v = std::getenv("IM_LEVEL_CHUNK")) ctx->level_chunk = std::max(1, std::atoi(v));
     if (const char *v = std::getenv("IM_PERSISTENT")) ctx->persistent = std::atoi(v) != 0;
     if (const char *v = std::getenv("IM_PULL_SWEEPS")) ctx->pull_sweeps = std::max(1, std::min(8, std::atoi(v)));
+    if (const char *v = std::getenv("IM_CELF")) ctx->celf = std::atoi(v) != 0;
+    if (const char *v = std::getenv("IM_TEST_CAS_LIMIT")) ctx->cas_limit = static_cast<uint32_t>(std::atol(v));
+    if (const char *v = std::getenv("IM_TEST_BARRIER_LIMIT"))
+        ctx->barrier_limit = static_cast<uint32_t>(std::atol(v));
     // every pulling sweep of a diffusion falls in the tick that starts it (split rows are combined only there)
     ctx->pull_sweeps = std::min(ctx->pull_sweeps, ctx->sweep_chunk);
     if (cudaMalloc(&ctx->d_gbar, sizeof(GridBar)) != cudaSuccess ||
@@ -1299,9 +1328,12 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     b += r(n * R) * 2;                                       // register buffers
     b += r(nt * R) + r(4 * (static_cast<uint64_t>(g.n_tasks) / 32 + 1));  // partial rows, their bits
     b += r(4 * words) * 2;                                   // L bits
+    b += r(n * R / 8);                                       // changed-register masks of the push sweeps
     b += r(4 * n) + r(8 * (static_cast<uint64_t>(g.m) / 512 + 1));  // changed lists
     b += r(R) + r(8 * 4096);                                 // M_S', frontier log
-    b += r(4 * n * W) * 4 + r(4 * words) + r(4 * n) * 4;  // reach and delta bits, seed-set bits, stamps, frontiers
+    b += r(4 * n * W) * 4 + r(4 * words) * 2 + r(4 * n) * 4;  // reach and delta bits, seed-set and reached-vertex
+                                                                 // bits, stamps, frontiers
+    b += r(4 * n);                                           // bounds of the lazy argmax
     b += r(sizeof(int4) * (n + static_cast<uint64_t>(g.m) / kBfsTaskEdgesMin + 1)) * 2;  // search tasks
     const uint64_t m1 = std::max<uint64_t>(static_cast<uint64_t>(g.m), 1);
     b += r(4 * W * m1);                                      // live-simulation masks of the edges

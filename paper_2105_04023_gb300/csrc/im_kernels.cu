@@ -7,9 +7,12 @@
 //
 // Paper map:
 //   k_init        Algorithm 1, register initialisation (and its re-initialisation with R_G(S) blocked)
-//   k_propg       Algorithm 2, one sweep that pulls into every row (sweep 0); the sampling of Eq. 4-5 is
-//                 evaluated once per run (k_live_masks) and kept as (target, simulation) pairs for edges live in
-//                 few simulations (k_pair_counts, k_pair_fill) and as live masks for the others
+//   k_first       Algorithm 1's initialisation fused into Algorithm 2's first sweep (L = V): every register it
+//                 reads is an initial rank, computed from (v, j); it writes every row of both register buffers.
+//                 The sampling of Eq. 4-5 is evaluated once per run (k_live_masks) and kept as (target,
+//                 simulation) pairs for edges live in few simulations (k_pair_counts, k_pair_fill) and as live
+//                 masks for the others
+//   k_propg       Algorithm 2, a later sweep that pulls into every row (when more than one sweep pulls)
 //   k_push        Algorithm 2, the later sweeps, pushed from the vertices L that changed in the previous one
 //   k_combine     Algorithm 2, sweep 0 for rows split over several warps
 //   k_frontier    Algorithm 2, the live sets L and L' (and the copy a push sweep needs); its last block applies
@@ -152,6 +155,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *m, uint32_t parity
 // Orders this warp's earlier generic reads of a buffer before bulk copies that overwrite it.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Bit k set where byte k of a and b differ (four bits): one byte-compare, then the low bit of each byte moved to
+// bit 24 + k by one multiply (the shifted copies land on distinct bits, so nothing carries into bits 24..27).
+__device__ __forceinline__ uint32_t ne_bits4(uint32_t a, uint32_t b) {
+    return (((__vcmpne4(a, b) & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
+}
+// Sixteen registers (one 16-byte chunk): bit k set where register k of the chunk differs.
+__device__ __forceinline__ uint32_t ne_bits16(const uint4 &a, const uint4 &b) {
+    return ne_bits4(a.x, b.x) | (ne_bits4(a.y, b.y) << 4) | (ne_bits4(a.z, b.z) << 8) | (ne_bits4(a.w, b.w) << 12);
+}
+
 // Byte masks of four simulations from four live bits (the low nibble of n): bit k is moved to bit 8k + 7 by one
 // multiply (the shifted copies never overlap, so nothing carries) and prmt replicates each byte's top bit.
 __device__ __forceinline__ uint32_t nibble_bytes(uint32_t n) { return sign_bytes(n * 0x10204080u, 0u, 0xBA98u); }
@@ -164,13 +177,68 @@ __device__ __forceinline__ unsigned tile_mask(int g) {
     return Geo<R>::G == 32 ? kFull : (((1u << Geo<R>::G) - 1u) << (g * Geo<R>::G));
 }
 
+// The first sweep of a diffusion reads every register before any sweep has changed it, so every register it
+// reads is an initial rank (Algorithm 1's initialisation), which is computed from (v, j) instead of loaded:
+// M_v[j] = clz(hash(v) XOR Y_j), or 0 where v is in R_{G_j}(S) (a rebuild).  P.rany marks the vertices reached in
+// some simulation (their blocked bits are then read from vis); it is NULL when there is no seed set.
+__device__ __forceinline__ uint32_t blocked16(const DevProb &P, int64_t v, int ch) {
+    if (!P.rany || !test_bit(P.rany, v)) return 0u;
+    return (__ldg(&P.vis[static_cast<size_t>(v) * P.W + (ch >> 1)]) >> (16 * (ch & 1))) & 0xFFFFu;
+}
+
+// Initial registers of the 16 simulations of chunk ch (four bytes a word) of a vertex with hash hv, zero where
+// blk (bit k: simulation 16 ch + k) is set.  Y: the problem's initialisation words (global, or a shared copy).
+__device__ __forceinline__ uint4 init_chunk(const uint32_t *Y, uint32_t hv, int ch, uint32_t blk) {
+    const uint4 *y = reinterpret_cast<const uint4 *>(Y) + 4 * ch;
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint4 q = y[k];
+        const uint32_t x = __clz(hv ^ q.x) | (__clz(hv ^ q.y) << 8) | (__clz(hv ^ q.z) << 16) |
+                           (__clz(hv ^ q.w) << 24);
+        w[k] = x & ~nibble_bytes((blk >> (4 * k)) & 0xFu);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Shared-memory slot of simulation j in a per-simulation word array (a tile's accumulators, the staged Y words):
+// the four 16-byte words of each 16-simulation chunk are stored rotated by the chunk index plus rot, so that when
+// lane li reads word w of its own chunk (a 64-byte stride between lanes) the lanes spread over all banks instead of
+// two (a 16-way conflict without the rotation).
+__device__ __forceinline__ uint32_t sw_slot(uint32_t j, uint32_t rot) {
+    return (j & ~15u) | ((((j >> 2) + (j >> 4) + rot) & 3u) << 2) | (j & 3u);
+}
+
+// init_chunk over Y words staged in shared memory with sw_slot(j, 0).
+__device__ __forceinline__ uint4 init_chunk_sw(const uint32_t *Ysw, uint32_t hv, int ch, uint32_t blk) {
+    const uint4 *y = reinterpret_cast<const uint4 *>(Ysw + 16 * ch);
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint4 q = y[(k + ch) & 3];
+        const uint32_t x = __clz(hv ^ q.x) | (__clz(hv ^ q.y) << 8) | (__clz(hv ^ q.z) << 16) |
+                           (__clz(hv ^ q.w) << 24);
+        w[k] = x & ~nibble_bytes((blk >> (4 * k)) & 0xFu);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Initial register of (v, j), 0 if v is in R_{G_j}(S).  Ysw: the Y words staged with sw_slot(j, 0).
+__device__ __forceinline__ uint32_t init_reg(const DevProb &P, const uint32_t *Ysw, int32_t v, uint32_t j) {
+    const uint32_t r = __clz(vertex_hash(static_cast<uint32_t>(v)) ^ Ysw[sw_slot(j, 0)]);
+    if (P.rany && test_bit(P.rany, v) && ((__ldg(&P.vis[static_cast<size_t>(v) * P.W + (j >> 5)]) >> (j & 31)) & 1u))
+        return 0u;
+    return r;
+}
+
 // Dense edges dlist[d0, d1) of the tile's unit (edges live in many simulations), merged with whole register rows:
 // the tile loads two neighbour rows per round (16 bytes per lane and chunk) when their v is in L, and max-merges
-// them into acc through the edges' live masks (Eq. 4-5, sampled once per run).  Returns the merged rows.
-template <int R>
+// them into acc through the edges' live masks (Eq. 4-5, sampled once per run).  Returns the merged rows.  In the
+// first sweep (INIT) the rows are the neighbours' initial registers, computed.
+template <int R, bool INIT>
 __device__ __forceinline__ uint32_t dense_tile(const DevProb &P, int64_t d0, int64_t d1, bool allL,
                                                const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
-                                               uint32_t (&acc)[Geo<R>::CPL][4], int li) {
+                                               const uint32_t *Ys, uint32_t (&acc)[Geo<R>::CPL][4], int li) {
     using Gm = Geo<R>;
     constexpr int W = R / 32;
     uint32_t taken = 0;
@@ -188,11 +256,15 @@ __device__ __forceinline__ uint32_t dense_tile(const DevProb &P, int64_t d0, int
                 v = __ldg(&P.adj[e]);
                 in[r] = allL || test_bit(Lcur, v);
             }
+            const uint32_t hv = INIT ? vertex_hash(static_cast<uint32_t>(v)) : 0u;
 #pragma unroll
             for (int c = 0; c < Gm::CPL; ++c) {
                 const int ch = li + Gm::G * c;  // 16-simulation chunk: half (ch & 1) of mask word ch / 2
-                row[r][c] = in[r] ? __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(v) * R) + ch)
-                                  : make_uint4(0, 0, 0, 0);
+                if (INIT)
+                    row[r][c] = in[r] ? init_chunk_sw(Ys, hv, ch, blocked16(P, v, ch)) : make_uint4(0, 0, 0, 0);
+                else
+                    row[r][c] = in[r] ? __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(v) * R) + ch)
+                                      : make_uint4(0, 0, 0, 0);
                 msk[r][c] = in[r] ? (__ldg(&P.live[static_cast<size_t>(e) * W + (ch >> 1)]) >> (16 * (ch & 1))) : 0u;
             }
         }
@@ -215,12 +287,14 @@ __device__ __forceinline__ uint32_t dense_tile(const DevProb &P, int64_t d0, int
 // Sparse pairs [p0, p1) of the tile's unit: for every pair (v, j) with v in L, acc32[j] = max(acc32[j], M_v[j])
 // (the max-merge of Algorithm 2 for one sampled simulation).  Lanes take pairs four at a time, and a pair's
 // register is loaded together with its L bit (and dropped if v is not in L), so one round of dependent loads
-// serves 4 G pairs.  Returns the number of pairs this lane merged.
-template <int R>
+// serves 4 G pairs (in the first sweep, INIT, the registers are initial ranks, computed).  Returns the number of
+// pairs this lane merged.
+template <int R, bool INIT>
 __device__ __forceinline__ uint32_t sparse_tile(const DevProb &P, int64_t p0, int64_t p1, bool allL,
                                                 const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
-                                                uint32_t *acc32, int li) {
+                                                const uint32_t *Ys, uint32_t *acc32, int li) {
     constexpr int G = Geo<R>::G;
+    const uint32_t g = static_cast<uint32_t>((threadIdx.x & 31) / G);  // the tile: rotation of its slots
     uint32_t taken = 0;
     for (int64_t p = p0 + li; p < p1; p += 4 * G) {
         int32_t v[4];
@@ -236,14 +310,17 @@ __device__ __forceinline__ uint32_t sparse_tile(const DevProb &P, int64_t p0, in
         uint32_t x[4], lw[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            x[k] = ok[k] ? __ldg(&Mcur[static_cast<size_t>(v[k]) * R + j[k]]) : 0u;
+            if (INIT)
+                x[k] = ok[k] ? init_reg(P, Ys, v[k], j[k]) : 0u;
+            else
+                x[k] = ok[k] ? __ldg(&Mcur[static_cast<size_t>(v[k]) * R + j[k]]) : 0u;
             lw[k] = (ok[k] && !allL) ? Lcur[v[k] >> 5] : 0xFFFFFFFFu;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const bool in = ok[k] && ((lw[k] >> (v[k] & 31)) & 1u);
             taken += in ? 1u : 0u;
-            if (in && x[k]) atomicMax(&acc32[j[k]], x[k]);
+            if (in && x[k]) atomicMax(&acc32[sw_slot(j[k], g)], x[k]);
         }
     }
     return taken;
@@ -253,13 +330,15 @@ __device__ __forceinline__ uint32_t sparse_tile(const DevProb &P, int64_t p0, in
 template <int R>
 __device__ __forceinline__ void fold_tile(uint32_t (&acc)[Geo<R>::CPL][4], uint32_t *acc32, unsigned tm, int li) {
     using Gm = Geo<R>;
+    const int g = (threadIdx.x & 31) / Gm::G;
     __syncwarp(tm);
 #pragma unroll
     for (int c = 0; c < Gm::CPL; ++c) {
-        const uint4 *a = reinterpret_cast<const uint4 *>(acc32 + 16 * (li + Gm::G * c));
+        const int ch = li + Gm::G * c;
+        const uint4 *a = reinterpret_cast<const uint4 *>(acc32 + 16 * ch);
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            const uint4 q = a[w];
+            const uint4 q = a[(w + ch + g) & 3];  // slots laid out by sw_slot(j, g)
             acc[c][w] = vmax4(acc[c][w], q.x | (q.y << 8) | (q.z << 16) | (q.w << 24));
         }
     }
@@ -270,14 +349,15 @@ __device__ __forceinline__ void fold_tile(uint32_t (&acc)[Geo<R>::CPL][4], uint3
 }
 
 // Row u's new registers max(M_u, acc) for a tile (every lane holds its chunks of acc and of the row's own
-// registers in own): written to the next buffer if they changed or the row is in L, and u joins L'.
+// registers in own): written to the next buffer if they changed or the row is in L, and u joins L'.  With Mother
+// (the first sweep) the row is written to both buffers whatever it holds: nothing else initialises them.
 template <int R>
 __device__ __forceinline__ void finalize_tile(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4],
                                               bool anyTaken, bool sync, const uint4 (&own)[Geo<R>::CPL],
-                                              uint8_t *__restrict__ Mnext, uint32_t *__restrict__ Lnext,
-                                              unsigned tm, int li, Stats &st) {
+                                              uint8_t *__restrict__ Mnext, uint8_t *__restrict__ Mother,
+                                              uint32_t *__restrict__ Lnext, unsigned tm, int li, Stats &st) {
     using Gm = Geo<R>;
-    if (!anyTaken && !sync) return;
+    if (!anyTaken && !sync && !Mother) return;
     bool diff = false;
     uint4 nw[Gm::CPL];
 #pragma unroll
@@ -288,22 +368,27 @@ __device__ __forceinline__ void finalize_tile(const DevProb &P, int64_t u, uint3
         diff |= (nw[c].x != o.x) | (nw[c].y != o.y) | (nw[c].z != o.z) | (nw[c].w != o.w);
     }
     const bool changed = __any_sync(tm, diff);
-    if (changed || sync) {
+    if (changed || sync || Mother) {
         uint4 *dst = reinterpret_cast<uint4 *>(Mnext + static_cast<size_t>(u) * R);
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
     }
+    if (Mother) {
+        uint4 *dst = reinterpret_cast<uint4 *>(Mother + static_cast<size_t>(u) * R);
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
+    }
     if (changed && li == 0) set_bit(Lnext, u);
-    st.bytes += R + ((changed || sync) ? R : 0);
+    st.bytes += Mother ? 2 * R : R + ((changed || sync) ? R : 0);
 }
 
 template <int R>
 __device__ __forceinline__ void finalize_row_r(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4],
                                                bool anyTaken, bool sync, const uint4 (&own)[Geo<R>::CPL],
-                                               uint8_t *__restrict__ Mnext, uint32_t *__restrict__ Lnext, int lane,
-                                               int g, int li, Stats &st) {
+                                               uint8_t *__restrict__ Mnext, uint8_t *__restrict__ Mother,
+                                               uint32_t *__restrict__ Lnext, int lane, int g, int li, Stats &st) {
     using Gm = Geo<R>;
-    if (!anyTaken && !sync) return;
+    if (!anyTaken && !sync && !Mother) return;
     bool diff = false;
     uint4 nw[Gm::CPL];
     if (g == 0) {
@@ -316,26 +401,37 @@ __device__ __forceinline__ void finalize_row_r(const DevProb &P, int64_t u, uint
         }
     }
     const bool changed = __any_sync(kFull, diff);
-    if (g == 0 && (changed || sync)) {
+    if (g == 0 && (changed || sync || Mother)) {
         uint4 *dst = reinterpret_cast<uint4 *>(Mnext + static_cast<size_t>(u) * R);
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
     }
+    if (g == 0 && Mother) {
+        uint4 *dst = reinterpret_cast<uint4 *>(Mother + static_cast<size_t>(u) * R);
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
+    }
     if (changed && lane == 0) set_bit(Lnext, u);
-    st.bytes += R + ((changed || sync) ? R : 0);
+    st.bytes += Mother ? 2 * R : R + ((changed || sync) ? R : 0);
 }
 
+// finalize_row_r with the row's own registers read from ownp, or, in the first sweep of a diffusion (init), formed
+// as initial ranks and written to both buffers (Mother).
 template <int R>
 __device__ __forceinline__ void finalize_row_g(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4],
-                                               bool anyTaken, bool sync, const uint4 *ownp,
-                                               uint8_t *__restrict__ Mnext, uint32_t *__restrict__ Lnext, int lane,
-                                               int g, int li, Stats &st) {
+                                               bool anyTaken, bool sync, const uint4 *ownp, bool init,
+                                               uint8_t *__restrict__ Mnext, uint8_t *__restrict__ Mother,
+                                               uint32_t *__restrict__ Lnext, int lane, int g, int li, Stats &st) {
     using Gm = Geo<R>;
-    if (!anyTaken && !sync) return;
+    if (!anyTaken && !sync && !init) return;
     uint4 own[Gm::CPL];
+    const uint32_t hv = vertex_hash(static_cast<uint32_t>(u));
 #pragma unroll
-    for (int c = 0; c < Gm::CPL; ++c) own[c] = g == 0 ? ownp[li + Gm::G * c] : make_uint4(0, 0, 0, 0);
-    finalize_row_r<R>(P, u, acc, anyTaken, sync, own, Mnext, Lnext, lane, g, li, st);
+    for (int c = 0; c < Gm::CPL; ++c) {
+        const int ch = li + Gm::G * c;
+        own[c] = g != 0 ? make_uint4(0, 0, 0, 0) : (init ? init_chunk(P.Y, hv, ch, blocked16(P, u, ch)) : ownp[ch]);
+    }
+    finalize_row_r<R>(P, u, acc, anyTaken, sync, own, Mnext, init ? Mother : nullptr, Lnext, lane, g, li, st);
 }
 
 // Work of a full sweep: every light row that has out-edges (static list) and every task of every split row.
@@ -352,18 +448,33 @@ __device__ __forceinline__ SweepWork sweep_work(const DevProb &P) {
     return w;
 }
 
-// Index of sweep unit l in the descriptor arrays: a row id (l < nlight) or a task id.
-__device__ __forceinline__ int64_t unit_id(const SweepWork &W, uint64_t l) {
-    return l < W.nlight ? static_cast<int64_t>(W.rows[l]) : static_cast<int64_t>(l - W.nlight);
+// The first sweep of a diffusion covers every row (those without out-edges too: it writes every row of both
+// buffers) and every task; split rows are finished by the combine kernels.
+__device__ __forceinline__ SweepWork sweep_work_init(const DevProb &P) {
+    SweepWork w;
+    w.nlight = static_cast<uint64_t>(P.n);
+    w.ntask = static_cast<uint64_t>(P.n_tasks);
+    w.rows = nullptr;
+    return w;
 }
 
-template <int R>
+// Index of sweep unit l in the descriptor arrays: a row id (l < nlight) or a task id.
+__device__ __forceinline__ int64_t unit_id(const SweepWork &W, uint64_t l) {
+    return l < W.nlight ? (W.rows ? static_cast<int64_t>(W.rows[l]) : static_cast<int64_t>(l))
+                        : static_cast<int64_t>(l - W.nlight);
+}
+
+// A pulling sweep of one problem over this tile's units.  INIT: the first sweep of a diffusion (t = 0), which
+// forms the initial registers itself (Algorithm 1's initialisation fused into the first Simulate sweep) and writes
+// every row to both register buffers.
+template <int R, bool INIT>
 __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W, uint64_t cnt, uint64_t first,
-                               uint64_t nworkers, unsigned tm, int li, uint32_t *acc32) {
+                               uint64_t nworkers, unsigned tm, int li, uint32_t *acc32, const uint32_t *Ys) {
     using Gm = Geo<R>;
     const bool par = t & 1u;
     const uint8_t *Mcur = par ? P.M1 : P.M0;
     uint8_t *Mnext = par ? P.M0 : P.M1;
+    uint8_t *Mother = INIT ? (par ? P.M1 : P.M0) : nullptr;
     const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
     uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
     const bool allL = (t == 0);
@@ -386,28 +497,44 @@ __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W,
         }
         if (l + 2 * nworkers < cnt) id_next = unit_id(W, l + 2 * nworkers);
         const bool is_row = l < W.nlight;
+        if (INIT && is_row && cur.u < 0) {  // a split row: its tasks and the combine kernels finish it
+            cur = nxt;
+            continue;
+        }
         const int64_t u = cur.u;
         uint4 own[Gm::CPL];
+        const uint32_t hu = INIT ? vertex_hash(static_cast<uint32_t>(u)) : 0u;
 #pragma unroll
-        for (int c = 0; c < Gm::CPL; ++c)
-            own[c] = is_row ? __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R) + li +
-                                    Gm::G * c)
-                            : make_uint4(0, 0, 0, 0);
+        for (int c = 0; c < Gm::CPL; ++c) {
+            const int ch = li + Gm::G * c;
+            if (INIT)
+                own[c] = is_row ? init_chunk_sw(Ys, hu, ch, blocked16(P, u, ch)) : make_uint4(0, 0, 0, 0);
+            else
+                own[c] = is_row ? __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R) + ch)
+                                : make_uint4(0, 0, 0, 0);
+        }
         uint32_t acc[Gm::CPL][4];
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c)
 #pragma unroll
             for (int w = 0; w < 4; ++w) acc[c][w] = 0;
-        uint32_t nPairs = sparse_tile<R>(P, cur.p0, cur.p0 + cur.np, allL, Lcur, Mcur, acc32, li);
-        const uint32_t nTaken = cur.nd > 0 ? dense_tile<R>(P, cur.d0, cur.d0 + cur.nd, allL, Lcur, Mcur, acc, li) : 0u;
-        nPairs = __reduce_add_sync(tm, nPairs);
-        fold_tile<R>(acc, acc32, tm, li);
+        uint32_t nPairs = 0;
+        if (cur.np > 0) {
+            nPairs = sparse_tile<R, INIT>(P, cur.p0, cur.p0 + cur.np, allL, Lcur, Mcur, Ys, acc32, li);
+            nPairs = __reduce_add_sync(tm, nPairs);
+            fold_tile<R>(acc, acc32, tm, li);
+        }
+        const uint32_t nTaken =
+            cur.nd > 0 ? dense_tile<R, INIT>(P, cur.d0, cur.d0 + cur.nd, allL, Lcur, Mcur, Ys, acc, li) : 0u;
+        // modelled bytes: descriptor, pair records, the registers pairs read (computed in the first sweep), dense
+        // edges (id, target, threshold) and their rows (masks only in the first sweep)
         if (li == 0)
-            st.bytes += 32 + 6 * static_cast<uint64_t>(cur.np) + nPairs + (8 + tb) * static_cast<uint64_t>(cur.nd) +
-                        static_cast<uint64_t>(nTaken) * R;
+            st.bytes += 32 + 6 * static_cast<uint64_t>(cur.np) + (INIT ? 0u : nPairs) +
+                        (8 + tb + (INIT ? R / 8 : 0)) * static_cast<uint64_t>(cur.nd) +
+                        (INIT ? 0u : static_cast<uint64_t>(nTaken) * R);
         const bool any = nPairs + nTaken > 0;
         if (is_row) {
-            finalize_tile<R>(P, u, acc, any, test_bit(Lcur, u), own, Mnext, Lnext, tm, li, st);
+            finalize_tile<R>(P, u, acc, any, !INIT && test_bit(Lcur, u), own, Mnext, Mother, Lnext, tm, li, st);
         } else if (any) {
             const int64_t task = cur.pad;
             uint4 *dst = reinterpret_cast<uint4 *>(P.part + static_cast<size_t>(task) * R);
@@ -482,9 +609,10 @@ __device__ __forceinline__ uint64_t heavy_count(const DevProb &P, const DevCtr &
 
 // Bytewise max-merge of cand into the register word at w, lock-free, starting from the value old read there:
 // returns whether the word grew.  A failed compare-and-swap means another thread grew the word first; words only
-// grow (four registers of at most 33 values), so the retries are few; after kCasLimit the fault flag is raised.
-__device__ __forceinline__ bool word_max(uint32_t *w, uint32_t old, uint32_t cand, unsigned int *fault) {
-    for (int it = 0; it < kCasLimit; ++it) {
+// grow (four registers of at most 33 values), so the retries are few; after `limit` tries the fault flag is raised.
+__device__ __forceinline__ bool word_max(uint32_t *w, uint32_t old, uint32_t cand, unsigned int *fault,
+                                         uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         const uint32_t nw = vmax4(old, cand);
         if (nw == old) return false;
         const uint32_t prev = atomicCAS(w, old, nw);
@@ -516,7 +644,9 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
     uint8_t *Mnext = par ? P.M0 : P.M1;
     uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
     uint8_t *srow = reinterpret_cast<uint8_t *>(warp_smem);
+    uint16_t *sdel = reinterpret_cast<uint16_t *>(warp_smem + R / 4);  // M_v's changed registers, per chunk
     unsigned int *fault = &P.ctr->fault;
+    const uint32_t lim = P.cas_limit;
     const uint64_t nl = P.ctr->npush_l;
     Stats st;
     for (uint64_t l = first; l < cnt; l += nworkers) {
@@ -539,12 +669,28 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
             d0 = __ldg(&P.idofs[k0]);
             d1 = __ldg(&P.idofs[k1]);
         }
+        // Stage M_v and the registers of v that the previous sweep changed: only those can raise an in-neighbour
+        // (M_u[j] >= the previous sweep's M_v[j] holds for every live (u, v) after the first sweep), so pairs of
+        // other simulations are skipped.  After the first sweep they are the registers above v's initial rank.
         const uint4 *vrow = reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(v) * R);
-        for (int c = lane; c < Gm::CH; c += 32) reinterpret_cast<uint4 *>(srow)[c] = __ldg(vrow + c);
+        if (t == 1) {
+            const uint32_t hv = vertex_hash(static_cast<uint32_t>(v));
+            for (int c = lane; c < Gm::CH; c += 32) {
+                const uint4 x = __ldg(vrow + c);
+                reinterpret_cast<uint4 *>(srow)[c] = x;
+                sdel[c] = static_cast<uint16_t>(ne_bits16(x, init_chunk(P.Y, hv, c, blocked16(P, v, c))));
+            }
+        } else {
+            for (int c = lane; c < Gm::CH; c += 32) {
+                reinterpret_cast<uint4 *>(srow)[c] = __ldg(vrow + c);
+                sdel[c] = __ldg(&P.dmask[static_cast<size_t>(v) * Gm::CH + c]);
+            }
+        }
         uint4 rowc[Gm::CPL];
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) rowc[c] = __ldg(vrow + li + G * c);
         __syncwarp();
+        uint32_t nproc = 0;  // pairs of changed registers (the others cost only their record)
         for (int64_t p = p0 + lane; p < p1; p += 128) {
             uint32_t *addr[4];
             uint32_t cand[4], old[4];
@@ -556,15 +702,18 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
                 if (q < p1) {
                     const int64_t u = __ldg(&P.iu[q]);
                     const uint32_t j = __ldg(&P.ij[q]);
-                    cand[k] = static_cast<uint32_t>(srow[j]) << (8 * (j & 3));
-                    addr[k] = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u) * R + (j & ~3u));
+                    if ((sdel[j >> 4] >> (j & 15)) & 1u) {
+                        cand[k] = static_cast<uint32_t>(srow[j]) << (8 * (j & 3));
+                        addr[k] = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u) * R + (j & ~3u));
+                        ++nproc;
+                    }
                 }
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) old[k] = cand[k] ? __ldcg(addr[k]) : 0u;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (cand[k] && word_max(addr[k], old[k], cand[k], fault))
+                if (cand[k] && word_max(addr[k], old[k], cand[k], fault, lim))
                     set_bit(Lnext, (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R);
             }
         }
@@ -591,11 +740,12 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
 #pragma unroll
                     for (int c = 0; c < Gm::CPL; ++c) {
                         const int ch = li + G * c;
-                        m[r][c] = ok[r] ? (__ldg(&P.live[static_cast<size_t>(e) * W + (ch >> 1)]) >> (16 * (ch & 1)))
+                        m[r][c] = ok[r] ? (__ldg(&P.live[static_cast<size_t>(e) * W + (ch >> 1)]) >> (16 * (ch & 1))) &
+                                              sdel[ch]
                                         : 0u;
-                        o[r][c] = ok[r] ? __ldcg(reinterpret_cast<const uint4 *>(Mnext + static_cast<size_t>(u[r]) * R) +
-                                                 ch)
-                                        : make_uint4(0, 0, 0, 0);
+                        o[r][c] = m[r][c] ? __ldcg(reinterpret_cast<const uint4 *>(Mnext + static_cast<size_t>(u[r]) * R) +
+                                                   ch)
+                                          : make_uint4(0, 0, 0, 0);
                     }
                 }
 #pragma unroll
@@ -606,27 +756,79 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
                             uint32_t *dst = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u[r]) * R) +
                                             4 * (li + G * c);
                             const uint32_t mm = m[r][c];
-                            grew[r] |= word_max(dst + 0, o[r][c].x, rowc[c].x & nibble_bytes(mm & 0xFu), fault);
-                            grew[r] |= word_max(dst + 1, o[r][c].y, rowc[c].y & nibble_bytes((mm >> 4) & 0xFu), fault);
-                            grew[r] |= word_max(dst + 2, o[r][c].z, rowc[c].z & nibble_bytes((mm >> 8) & 0xFu), fault);
-                            grew[r] |= word_max(dst + 3, o[r][c].w, rowc[c].w & nibble_bytes((mm >> 12) & 0xFu), fault);
+                            grew[r] |= word_max(dst + 0, o[r][c].x, rowc[c].x & nibble_bytes(mm & 0xFu), fault,
+                                                lim);
+                            grew[r] |= word_max(dst + 1, o[r][c].y, rowc[c].y & nibble_bytes((mm >> 4) & 0xFu), fault,
+                                                lim);
+                            grew[r] |= word_max(dst + 2, o[r][c].z, rowc[c].z & nibble_bytes((mm >> 8) & 0xFu), fault,
+                                                lim);
+                            grew[r] |= word_max(dst + 3, o[r][c].w, rowc[c].w & nibble_bytes((mm >> 12) & 0xFu), fault,
+                                                lim);
                         }
                     }
                     if (__any_sync(tm, grew[r]) && li == 0) set_bit(Lnext, u[r]);
                 }
             }
         }
+        nproc = __reduce_add_sync(kFull, nproc);
+        // modelled bytes: M_v and its change mask, descriptor, pair records, the register word of each pair of a
+        // changed register, and per dense in-edge its ids, live mask and target row
         if (lane == 0)
-            st.bytes += R + 32 + 10 * static_cast<uint64_t>(p1 - p0) + (12 + W * 4 + R) * static_cast<uint64_t>(d1 - d0);
+            st.bytes += R + R / 8 + 32 + 6 * static_cast<uint64_t>(p1 - p0) + 4 * static_cast<uint64_t>(nproc) +
+                        (12 + W * 4 + R) * static_cast<uint64_t>(d1 - d0);
         __syncwarp();
     }
     // the staged rows shared the sparse accumulators, which a pulling unit of another problem in the same launch
     // expects to find zero
-    for (int k = lane; k < R / 16; k += 32) reinterpret_cast<uint4 *>(srow)[k] = make_uint4(0, 0, 0, 0);
+    for (int k = lane; k < R / 4 + R / 32; k += 32) warp_smem[k] = 0u;
     __syncwarp();
     if (st.bytes) atomicAdd(&P.ctr->bytes, st.bytes);
 }
 
+// Per-tile shared-memory accumulators of the pulling sweep kernels: one 32-bit slot per simulation and tile.
+template <int R>
+__device__ __forceinline__ uint32_t *tile_acc(uint4 *smem, int wib, int g, int li) {
+    using Gm = Geo<R>;
+    uint32_t *acc32 = reinterpret_cast<uint32_t *>(smem) + (static_cast<size_t>(wib) * Gm::NG + g) * R;
+    for (int k = li; k < R; k += Gm::G) acc32[k] = 0;
+    return acc32;
+}
+
+// The first sweep of every listed problem that starts a diffusion (Algorithm 1's initialisation fused into
+// Algorithm 2's first sweep, L = V): tiles of G lanes take rows and tasks; problems at other sweeps are left to the
+// sweep kernel launched beside this one.
+template <int R, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_first(const DevProb *__restrict__ probs,
+                                                        const int32_t *__restrict__ act, int nact) {
+    using Gm = Geo<R>;
+    extern __shared__ __align__(16) uint4 gather_smem[];
+    __shared__ __align__(16) uint32_t sY[R];  // the problem's initialisation words Y_j (slots sw_slot(j, 0))
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int g = lane / Gm::G, li = lane % Gm::G;
+    const unsigned tm = tile_mask<R>(g);
+    uint32_t *acc32 = tile_acc<R>(gather_smem, wib, g, li);
+    __syncwarp(tm);
+    const uint64_t worker = (static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib) * Gm::NG + g;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock * Gm::NG;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        if (C.done || !C.full || C.t != 0) continue;  // the same for every thread of the block
+        __syncthreads();  // the previous problem's use of sY is over
+        for (int k = threadIdx.x; k < R; k += blockDim.x) sY[sw_slot(k, 0)] = __ldg(&P.Y[k]);
+        __syncthreads();
+        const SweepWork W = sweep_work_init(P);
+        const uint64_t cnt = W.nlight + W.ntask;
+        const uint64_t first = first_owned(worker, nworkers, base);
+        base += cnt;
+        if (first >= cnt) continue;
+        prop_problem_t<R, true>(P, 0, W, cnt, first, nworkers, tm, li, acc32, sY);
+    }
+}
+
+// A later sweep that pulls into every row (sweeps 1 .. pull_sweeps - 1), or pushes, for every listed problem that
+// is not in its first sweep.
 template <int R, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restrict__ probs,
                                                         const int32_t *__restrict__ act, int nact) {
@@ -635,8 +837,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restric
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int g = lane / Gm::G, li = lane % Gm::G;
     const unsigned tm = tile_mask<R>(g);
-    uint32_t *acc32 = reinterpret_cast<uint32_t *>(gather_smem) + (static_cast<size_t>(wib) * Gm::NG + g) * R;
-    for (int k = li; k < R; k += Gm::G) acc32[k] = 0;
+    uint32_t *acc32 = tile_acc<R>(gather_smem, wib, g, li);
     __syncwarp(tm);
     const uint64_t wworker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
     const uint64_t nwworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
@@ -646,14 +847,14 @@ __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restric
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
-        if (C.done) continue;
+        if (C.done || (C.full && C.t == 0)) continue;
         const SweepWork W = sweep_work(P);
         const uint64_t cnt = C.full ? W.nlight + W.ntask : static_cast<uint64_t>(C.npush_l) + C.npush_h;
         const uint64_t first = C.full ? first_owned(worker, nworkers, base) : first_owned(wworker, nwworkers, base);
         base += cnt;
         if (first >= cnt) continue;
         if (C.full)
-            prop_problem_t<R>(P, C.t, W, cnt, first, nworkers, tm, li, acc32);
+            prop_problem_t<R, false>(P, C.t, W, cnt, first, nworkers, tm, li, acc32, P.Y);
         else
             push_problem_w<R>(P, C.t, cnt, first, nwworkers, lane,
                               reinterpret_cast<uint32_t *>(gather_smem) + static_cast<size_t>(wib) * Gm::NG * R);
@@ -663,11 +864,13 @@ __global__ void __launch_bounds__(kBlock, MINB) k_propg(const DevProb *__restric
 constexpr int kPushMinBlocks = 4;  // resident blocks an SM the push kernel's register budget is set for
 
 // A sweep in which every listed problem pushes (only the first pull_sweeps sweeps of a diffusion pull): the push
-// path alone, with its own register budget and R bytes of shared memory a warp for the staged row.
+// path alone, with its own register budget and R bytes of shared memory a warp for the staged row.  skip_full:
+// problems in their first sweep are pulled by k_first in the same sweep.
 template <int R, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_push(const DevProb *__restrict__ probs,
-                                                       const int32_t *__restrict__ act, int nact) {
-    __shared__ __align__(16) uint32_t srow[kWarpsPerBlock][R / 4];
+                                                       const int32_t *__restrict__ act, int nact, int skip_full) {
+    // per warp: M_v, then its change mask (padded to whole 16-byte words so every warp's row stays aligned)
+    __shared__ __align__(16) uint32_t srow[kWarpsPerBlock][R / 4 + ((R / 32 + 3) & ~3)];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t wworker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
     const uint64_t nwworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
@@ -676,8 +879,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(const DevProb *__restrict
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
         if (C.done) continue;
-        if (C.full) {  // a pulling sweep here would be a scheduling error: flag it rather than skip the rows
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&P.ctr->fault, 8u);
+        if (C.full) {  // pulled by k_first launched beside this kernel; otherwise a scheduling error, flagged
+            if (!skip_full && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&P.ctr->fault, 8u);
             continue;
         }
         const uint64_t cnt = static_cast<uint64_t>(C.npush_l) + C.npush_h;
@@ -715,8 +918,10 @@ __global__ void __launch_bounds__(kBlock) k_combine(const DevProb *__restrict__ 
         base += cnt;
         if (first >= cnt) continue;
         const bool par = C.t & 1u;
+        const bool init = C.t == 0;  // the first sweep: own registers are initial ranks, both buffers written
         const uint8_t *Mcur = par ? P.M1 : P.M0;
         uint8_t *Mnext = par ? P.M0 : P.M1;
+        uint8_t *Mother = par ? P.M1 : P.M0;
         const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
         uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
         Stats st;
@@ -731,9 +936,9 @@ __global__ void __launch_bounds__(kBlock) k_combine(const DevProb *__restrict__ 
                                                li, stage[wib], buf, st, phase, aborted);
             reduce_groups<R>(acc);
             if (lane == 0) st.bytes += 16;
-            finalize_row_g<R>(P, u, acc, any, test_bit(Lcur, u),
-                              reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R), Mnext, Lnext, lane,
-                              g, li, st);
+            finalize_row_g<R>(P, u, acc, any, !init && test_bit(Lcur, u),
+                              reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R), init, Mnext,
+                              Mother, Lnext, lane, g, li, st);
             __syncwarp();
         }
         flush_stats(P.ctr, st, lane);
@@ -768,8 +973,10 @@ __global__ void __launch_bounds__(kBlock) k_combine_big(const DevProb *__restric
         base += cnt;
         if (first >= cnt) continue;
         const bool par = C.t & 1u;
+        const bool init = C.t == 0;
         const uint8_t *Mcur = par ? P.M1 : P.M0;
         uint8_t *Mnext = par ? P.M0 : P.M1;
+        uint8_t *Mother = par ? P.M1 : P.M0;
         const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
         uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
         Stats st;
@@ -806,9 +1013,9 @@ __global__ void __launch_bounds__(kBlock) k_combine_big(const DevProb *__restric
                     }
                 }
                 if (lane == 0) st.bytes += 16;
-                finalize_row_g<R>(P, u, acc, all_any, test_bit(Lcur, u),
-                                  reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R), Mnext, Lnext,
-                                  lane, g, li, st);
+                finalize_row_g<R>(P, u, acc, all_any, !init && test_bit(Lcur, u),
+                                  reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R), init, Mnext,
+                                  Mother, Lnext, lane, g, li, st);
             }
             __syncthreads();
         }
@@ -902,6 +1109,8 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
         const DevCtr &C = *P.ctr;
         if (C.done) continue;
         const bool push_next = next_is_push(P, C);
+        // the first sweep of a diffusion wrote every row to both buffers: nothing to copy after it
+        const bool copy = C.t != 0;
         const bool par = C.t & 1u;
         uint32_t *Lold = par ? P.Lb1 : P.Lb0;
         const uint32_t *Lnew = par ? P.Lb0 : P.Lb1;
@@ -935,7 +1144,14 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
                         light[k] = false;
                         const uint4 *src = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R);
                         uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R);
-                        for (int c = 0; c < P.R / 16; ++c) dst[c] = src[c];
+                        if (copy) {
+                            const int CH = P.R / 16;
+                            for (int c = 0; c < CH; ++c) {
+                                const uint4 a = src[c];
+                                P.dmask[static_cast<size_t>(v) * CH + c] = static_cast<uint16_t>(ne_bits16(a, dst[c]));
+                                dst[c] = a;
+                            }
+                        }
                         const uint32_t nt = static_cast<uint32_t>((d + kPushChunk - 1) / kPushChunk);
                         const uint32_t at = atomicAdd(&P.ctr->nchg_hc, nt);
                         for (uint32_t c = 0; c < nt; ++c)
@@ -981,13 +1197,17 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
                 }
             }
             __syncthreads();
-            // consecutive threads on consecutive 16-byte chunks of the listed rows
+            if (!copy) continue;
+            // consecutive threads on consecutive 16-byte chunks of the listed rows; the chunks' changed registers
+            // (Mw against the previous sweep's Mr) go to dmask for the push sweep
             const uint32_t CH = static_cast<uint32_t>(P.R / 16);
 #pragma unroll 4
             for (uint32_t x = threadIdx.x; x < sn * CH; x += blockDim.x) {
                 const int64_t v = s_v[x / CH];
-                reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R)[x % CH] =
-                    reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R)[x % CH];
+                uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R) + x % CH;
+                const uint4 a = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R)[x % CH];
+                P.dmask[static_cast<size_t>(v) * CH + x % CH] = static_cast<uint16_t>(ne_bits16(a, *dst));
+                *dst = a;
             }
         }
 #pragma unroll
@@ -1032,8 +1252,10 @@ __device__ __forceinline__ void advance_one(const DevProb &P) {
     C.t = t + 1;
 }
 
-// Algorithm 1's initialisation: M_v[j] = clz(hash(v) XOR Y_j), 0 where v is in R_{G_j}(S) (a rebuild), written to
-// both register buffers; resets the diffusion state and M_S'.
+// Start of a diffusion (Algorithm 1's initialisation; the initial registers themselves are formed by the first
+// sweep, which writes both register buffers): clears the frontier and task bits, resets the diffusion counters and
+// M_S', and on a rebuild marks in rany the vertices R_G(S) reached in some simulation (their blocked registers are
+// 0 in the rebuilt sketch).
 __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
                                                  int nact) {
     const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -1041,38 +1263,37 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
-        const int CH = P.R / 16;
-        const uint64_t nchunks = static_cast<uint64_t>(P.n) * CH;
         const int64_t words = (P.n + 31) >> 5;
         const int64_t twords = (P.n_tasks + 31) >> 5;
-        // units: register chunks, then L bits (2 x words), task bits, counters
-        const uint64_t cnt = nchunks + 2 * static_cast<uint64_t>(words) + static_cast<uint64_t>(twords) + 1;
+        const uint64_t rwords = P.rany ? static_cast<uint64_t>(words) : 0u;
+        // units: L bits (2 x words), task bits, rany words, counters
+        const uint64_t cnt = 2 * static_cast<uint64_t>(words) + static_cast<uint64_t>(twords) + rwords + 1;
         const uint64_t first = first_owned(tid, nthreads, base);
         base += cnt;
+        // no search has run yet (levels count on over the searches of a problem): nothing is reached
+        const bool searched = P.rany && P.ctr->lvl != 0;
         for (uint64_t l = first; l < cnt; l += nthreads) {
-            if (l < nchunks) {
-                const uint32_t v = static_cast<uint32_t>(l / CH);
-                const int c = static_cast<int>(l % CH);
-                const uint32_t hv = vertex_hash(v);
-                uint32_t blocked = 0;
-                if (P.vis) blocked = (P.vis[static_cast<size_t>(v) * P.W + (c >> 1)] >> (16 * (c & 1))) & 0xFFFFu;
-                const uint4 *y = reinterpret_cast<const uint4 *>(P.Y) + 4 * c;  // Y_j of this chunk, 4 at a time
-                uint32_t w[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint4 q = __ldg(y + k);
-                    const uint32_t x = __clz(hv ^ q.x) | (__clz(hv ^ q.y) << 8) | (__clz(hv ^ q.z) << 16) |
-                                       (__clz(hv ^ q.w) << 24);
-                    w[k] = x & ~nibble_bytes((blocked >> (4 * k)) & 0xFu);
-                }
-                const uint4 val = make_uint4(w[0], w[1], w[2], w[3]);
-                reinterpret_cast<uint4 *>(P.M0)[l] = val;
-                reinterpret_cast<uint4 *>(P.M1)[l] = val;
-            } else if (l < nchunks + 2 * static_cast<uint64_t>(words)) {
-                const uint64_t k = l - nchunks;
-                (k < static_cast<uint64_t>(words) ? P.Lb0 : P.Lb1)[k % words] = 0;
+            if (l < 2 * static_cast<uint64_t>(words)) {
+                (l < static_cast<uint64_t>(words) ? P.Lb0 : P.Lb1)[l % words] = 0;
+            } else if (l < 2 * static_cast<uint64_t>(words) + twords) {
+                P.part_any[l - 2 * static_cast<uint64_t>(words)] = 0;
             } else if (l < cnt - 1) {
-                P.part_any[l - nchunks - 2 * static_cast<uint64_t>(words)] = 0;
+                const int64_t wi = static_cast<int64_t>(l - 2 * static_cast<uint64_t>(words) - twords);
+                uint32_t bits = 0;
+                if (searched) {
+                    for (int b = 0; b < 32; ++b) {
+                        const int64_t v = wi * 32 + b;
+                        if (v >= P.n) break;
+                        const uint2 *row = reinterpret_cast<const uint2 *>(P.vis + static_cast<size_t>(v) * P.W);
+                        uint32_t any = 0;
+                        for (int k = 0; k < P.W / 2; ++k) {
+                            const uint2 x = row[k];
+                            any |= x.x | x.y;
+                        }
+                        bits |= (any != 0 ? 1u : 0u) << b;
+                    }
+                }
+                P.rany[wi] = bits;
             } else {
                 DevCtr &C = *P.ctr;
                 C.t = 0;
@@ -1086,6 +1307,8 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 C.npush_l = 0;
                 C.npush_h = 0;
                 C.chg_indeg = 0;
+                C.gms = 0;  // M_S' is cleared below
+                C.cand_key = 0;
                 if (P.flog_cap > 0) P.flog[0] = P.n;
                 C.visits += static_cast<unsigned long long>(P.m) * static_cast<unsigned long long>(P.R);  // L_0 = V
                 for (int j = 0; j < P.R; ++j) P.MS[j] = 0;
@@ -1101,6 +1324,7 @@ __device__ void scan_problem(const DevProb &P, uint64_t cnt, uint64_t first, uin
     using Gm = Geo<R>;
     const int g = lane / Gm::G, li = lane % Gm::G;
     const uint8_t *M = P.ctr->res_par ? P.M1 : P.M0;
+    const uint32_t gms = P.ctr->gms;
     uint32_t ms[Gm::CPL][4];
     {
         const uint4 *p = reinterpret_cast<const uint4 *>(P.MS);
@@ -1144,8 +1368,10 @@ __device__ void scan_problem(const DevProb &P, uint64_t cnt, uint64_t first, uin
 #pragma unroll
             for (int off = 1; off < Gm::G; off <<= 1) s += __shfl_xor_sync(kFull, s, off);
             if (ok[u]) {
+                const uint32_t gain = s - gms;  // s >= sum_j M_S'[j]
+                if (li == 0 && P.gst) P.gst[v[u]] = gain;
                 const unsigned long long key =
-                    (static_cast<unsigned long long>(s) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(v[u]));
+                    (static_cast<unsigned long long>(gain) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(v[u]));
                 best = key > best ? key : best;
             }
         }
@@ -1161,7 +1387,8 @@ __device__ void scan_problem(const DevProb &P, uint64_t cnt, uint64_t first, uin
 }  // namespace
 
 // Algorithm 1's argmax: for every v not in S, gsum_v = sum_j max(M_S'[j], M_v[j]) (Merge, Eq. 3; Estimate, Eq. 2 is
-// increasing in it); the maximum of (gsum_v << 32 | ~v) picks the largest sum, ties to the smallest id.
+// increasing in it); the maximum of (gain_v << 32 | ~v), gain_v = gsum_v - sum_j M_S'[j], picks the largest sum,
+// ties to the smallest id.  Every gain is also kept in gst for the lazy scans of the next steps.
 template <int R>
 __global__ void __launch_bounds__(kBlock) k_scan(const DevProb *__restrict__ probs, const int32_t *__restrict__ act,
                                                  int nact) {
@@ -1176,6 +1403,130 @@ __global__ void __launch_bounds__(kBlock) k_scan(const DevProb *__restrict__ pro
         base += cnt;
         if (first >= cnt) continue;
         scan_problem<R>(P, cnt, first, nworkers, lane);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Lazy (CELF-style) argmax for the greedy steps that keep the sketch.  Between two builds M_S' only grows, so a
+// candidate's gain gain_v = sum_j max(M_S'[j], M_v[j]) - sum_j M_S'[j] = sum_j (M_v[j] - M_S'[j])^+ only shrinks,
+// and the gain last evaluated for v (gst[v]) bounds its current gain from above.  A step then
+//   1. finds the candidate v1 with the largest bound key (gst[v] << 32 | ~v)            (k_celf_max),
+//   2. evaluates v1 exactly: its exact key tau                                           (k_celf_tau),
+//   3. evaluates exactly every other candidate whose bound key exceeds tau, and keeps the largest exact key
+//                                                                                        (k_celf_eval).
+// Every candidate left out has exact key <= bound key <= tau <= the result, so the result is the full argmax
+// (largest gain, ties to the smallest id), with far fewer register rows read.
+
+__global__ void __launch_bounds__(kBlock) k_celf_max(const DevProb *__restrict__ probs,
+                                                     const int32_t *__restrict__ act, int nact) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const uint64_t cnt = (static_cast<uint64_t>(P.n) + 31) & ~31ull;  // whole warps per 32 vertices
+        const uint64_t first = first_owned(tid, nthreads, base);
+        base += cnt;
+        unsigned long long best = 0;
+        for (uint64_t v = first; v < cnt; v += nthreads) {
+            if (v < static_cast<uint64_t>(P.n) && !test_bit(P.inS, static_cast<int64_t>(v))) {
+                const unsigned long long key = (static_cast<unsigned long long>(__ldg(&P.gst[v])) << 32) |
+                                               (0xFFFFFFFFu - static_cast<uint32_t>(v));
+                best = key > best ? key : best;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kFull, best, off);
+            best = o > best ? o : best;
+        }
+        if (lane == 0 && best) atomicMax(&P.ctr->cand_key, best);
+    }
+}
+
+// The exact key of the best-bounded candidate (one block per problem); it also starts the step's best key.
+__global__ void k_celf_tau(const DevProb *__restrict__ probs, const int32_t *__restrict__ act, int nact) {
+    const int q = blockIdx.x;
+    if (q >= nact) return;
+    const DevProb &P = probs[act[q]];
+    DevCtr &C = *P.ctr;
+    const unsigned long long ck = C.cand_key;
+    __shared__ uint32_t s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
+    if (ck == 0) {  // no candidate left: every vertex is a seed
+        if (threadIdx.x == 0) C.tau_key = C.best_key = 0;
+        return;
+    }
+    const uint32_t v = 0xFFFFFFFFu - static_cast<uint32_t>(ck & 0xFFFFFFFFull);
+    const uint8_t *M = C.res_par ? P.M1 : P.M0;
+    const uint32_t *row = reinterpret_cast<const uint32_t *>(M + static_cast<size_t>(v) * P.R);
+    const uint32_t *ms = reinterpret_cast<const uint32_t *>(P.MS);
+    uint32_t part = 0;
+    for (int i = threadIdx.x; i < P.R / 4; i += blockDim.x) part = __dp4a(vmax4(row[i], ms[i]), 0x01010101u, part);
+    atomicAdd(&s_sum, part);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t gain = s_sum - C.gms;
+        const unsigned long long key = (static_cast<unsigned long long>(gain) << 32) | (0xFFFFFFFFu - v);
+        P.gst[v] = gain;
+        C.tau_key = key;
+        C.best_key = key;
+        C.cand_key = 0;
+    }
+}
+
+// Exact evaluation of every candidate whose bound key exceeds tau: a warp takes 32 consecutive vertices, a lane
+// tests one bound, and the warp evaluates the surviving rows one after the other (R / 4 register words over its
+// lanes), storing each exact gain back into gst.
+template <int R>
+__global__ void __launch_bounds__(kBlock) k_celf_eval(const DevProb *__restrict__ probs,
+                                                      const int32_t *__restrict__ act, int nact) {
+    constexpr int WPL = R / 4 >= 32 ? R / 128 : 1;  // register words a lane holds
+    constexpr int LANES = R / 4 >= 32 ? 32 : R / 4;   // lanes that hold words
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        const DevCtr &C = *P.ctr;
+        const uint64_t cnt = (static_cast<uint64_t>(P.n) + 31) / 32;
+        const uint64_t first = first_owned(worker, nworkers, base);
+        base += cnt;
+        if (first >= cnt) continue;
+        const unsigned long long tau = C.tau_key;
+        const uint32_t gms = C.gms;
+        const uint8_t *M = C.res_par ? P.M1 : P.M0;
+        uint32_t ms[WPL];
+#pragma unroll
+        for (int k = 0; k < WPL; ++k)
+            ms[k] = lane < LANES ? reinterpret_cast<const uint32_t *>(P.MS)[lane + LANES * k] : 0u;
+        unsigned long long best = 0;
+        for (uint64_t l = first; l < cnt; l += nworkers) {
+            const uint64_t v = l * 32 + lane;
+            bool cand = false;
+            if (v < static_cast<uint64_t>(P.n) && !test_bit(P.inS, static_cast<int64_t>(v))) {
+                const unsigned long long key = (static_cast<unsigned long long>(__ldg(&P.gst[v])) << 32) |
+                                               (0xFFFFFFFFu - static_cast<uint32_t>(v));
+                cand = key > tau;
+            }
+            for (unsigned m = __ballot_sync(kFull, cand); m; m &= m - 1u) {
+                const uint32_t u = static_cast<uint32_t>(l * 32 + (__ffs(m) - 1));
+                const uint32_t *row = reinterpret_cast<const uint32_t *>(M + static_cast<size_t>(u) * R);
+                uint32_t sum = 0;
+#pragma unroll
+                for (int k = 0; k < WPL; ++k)
+                    if (lane < LANES) sum = __dp4a(vmax4(__ldg(row + lane + LANES * k), ms[k]), 0x01010101u, sum);
+                sum = __reduce_add_sync(kFull, sum);
+                const uint32_t gain = sum - gms;
+                if (lane == 0) P.gst[u] = gain;
+                const unsigned long long key = (static_cast<unsigned long long>(gain) << 32) | (0xFFFFFFFFu - u);
+                best = key > best ? key : best;
+            }
+        }
+        if (lane == 0 && best) atomicMax(&P.ctr->best_key, best);
     }
 }
 
@@ -1225,7 +1576,7 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
     const int lane = threadIdx.x;
     const unsigned long long key = C.best_key;
     const uint32_t s = 0xFFFFFFFFu - static_cast<uint32_t>(key & 0xFFFFFFFFull);
-    const uint32_t gsum = static_cast<uint32_t>(key >> 32);
+    const uint32_t gsum = static_cast<uint32_t>(key >> 32) + C.gms;
     if (key == 0 || s >= static_cast<uint64_t>(P.n)) {  // no candidate was scanned: nothing to search
         if (lane == 0) {
             C.bdone = 1;
@@ -1256,7 +1607,6 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
         C.nVl[L % 3u] = 1;
         C.nVl[(L + 1u) % 3u] = 0;
         P.V[L % 3u][0] = static_cast<int32_t>(s);
-        bfs_tasks(P.T[L & 1u], &C.nT[L & 1u], s, P.xadj, bfs_task_edges(P.W));
         C.lvl0 = L;
         C.bdone = added ? 0u : 1u;
         C.btimeout = 0;
@@ -1265,6 +1615,13 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
             P.step_gsum[step] = gsum;
         }
     }
+    // the seed's search tasks for the first level, written by the whole warp (a hub seed has many); the task
+    // lists of this level were empty, so they start at 0
+    const int te = bfs_task_edges(P.W);
+    const int64_t e = P.xadj[s], deg = P.xadj[s + 1] - e;
+    const uint32_t nt = bfs_ntasks(deg, te);
+    for (uint32_t c = lane; c < nt; c += 32) P.T[L & 1u][c] = bfs_task(s, e, deg, c, te);
+    if (lane == 0) C.nT[L & 1u] = nt;
 }
 
 // Starts a reachability search from a whole seed set (for an exact sigma of a given set).
@@ -1555,7 +1912,7 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
 // Grid-wide barrier for a cooperatively launched kernel (every block resident).  Each wait is bounded: a block that
 // gives up raises gb->fail, and every block leaves the kernel at its next barrier (returns false) instead of waiting
 // again, so a lost block cannot hang the device.
-__device__ __forceinline__ bool grid_sync(GridBar *gb) {
+__device__ __forceinline__ bool grid_sync(GridBar *gb, uint32_t limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1570,7 +1927,7 @@ __device__ __forceinline__ bool grid_sync(GridBar *gb) {
             } else {
                 // spin first (a barrier normally opens within microseconds), then poll with short sleeps
                 for (uint32_t it = 0; ld_acquire(&gb->gen) == gen; ++it) {
-                    if (it >= kBarrierLimit || ld_acquire(&gb->fail)) {
+                    if (it >= limit || ld_acquire(&gb->fail)) {
                         atomicExch(&gb->fail, 1u);
                         ok = 0;
                         break;
@@ -1598,14 +1955,15 @@ constexpr int kRunBlock = 1024;  // threads per block of the persistent kernels 
 
 template <int R>
 __global__ void __launch_bounds__(kRunBlock) k_bfs_run(const DevProb *__restrict__ probs,
-                                                       const int32_t *__restrict__ act, int nact, GridBar *gb) {
+                                                       const int32_t *__restrict__ act, int nact, GridBar *gb,
+                                                       uint32_t barrier_limit) {
     __shared__ int32_t stage[(kRunBlock / 32) * kStage];
     for (;;) {
         bfs_level_phase<R>(probs, act, nact, stage + (threadIdx.x >> 5) * kStage);
-        if (!grid_sync(gb)) return barrier_lost(probs, act, nact);
+        if (!grid_sync(gb, barrier_limit)) return barrier_lost(probs, act, nact);
         if (blockIdx.x == 0)
             for (int q = threadIdx.x; q < nact; q += blockDim.x) bfs_advance_one(probs, act, q);
-        if (!grid_sync(gb)) return barrier_lost(probs, act, nact);
+        if (!grid_sync(gb, barrier_limit)) return barrier_lost(probs, act, nact);
         bool all = true;
         for (int q = 0; q < nact && all; ++q) all = __ldcg(&probs[act[q]].ctr->bdone) != 0;
         if (all) return;
@@ -1621,7 +1979,18 @@ __global__ void k_merge(const DevProb *__restrict__ probs, const int32_t *__rest
     const uint8_t *M = C.res_par ? P.M1 : P.M0;
     const uint32_t *row = reinterpret_cast<const uint32_t *>(M + static_cast<size_t>(C.s) * P.R);
     uint32_t *ms = reinterpret_cast<uint32_t *>(P.MS);
-    for (int i = threadIdx.x; i < P.R / 4; i += blockDim.x) ms[i] = vmax4(ms[i], row[i]);
+    __shared__ uint32_t s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
+    uint32_t part = 0;
+    for (int i = threadIdx.x; i < P.R / 4; i += blockDim.x) {
+        const uint32_t x = vmax4(ms[i], row[i]);
+        ms[i] = x;
+        part = __dp4a(x, 0x01010101u, part);
+    }
+    atomicAdd(&s_sum, part);
+    __syncthreads();
+    if (threadIdx.x == 0) P.ctr->gms = s_sum;  // sum_j M_S'[j] after the merge
 }
 
 // Merge of the registers of k seeds and their byte sum (Eq. 3 then the sum behind Eq. 2).
@@ -1765,6 +2134,8 @@ __global__ void __launch_bounds__(kBlock) k_unit_desc(const DevProb P, UnitD *rd
         d.nd = static_cast<uint32_t>(P.dofs[e1] - d.d0);
         d.u = static_cast<int32_t>(u);
         d.pad = 0;
+        // a split row's own descriptor is only read by the first sweep, which leaves the row to its tasks
+        if (i < P.n && e1 - e0 > kHeavyDeg) d.u = -1;
         (i < P.n ? rdesc[i] : tdesc[i - P.n]) = d;
     }
 }
@@ -2113,28 +2484,29 @@ cudaError_t configure(int device) {
     return cudaSuccess;
 }
 
-template <int R, int MINB>
+template <int R, int MINB, bool FIRST>
 static void launch_gather(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     static int grid = 0;
     const int smem = kWarpsPerBlock * GSlots<R>::kPropBytesPerWarp;
+    auto kern = FIRST ? k_first<R, MINB> : k_propg<R, MINB>;
     if (grid == 0) {
-        cudaFuncSetAttribute(k_propg<R, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_propg<R, MINB>, kBlock, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, smem);
         grid = g_sms * (occ > 0 ? occ : 1);
     }
-    k_propg<R, MINB><<<grid, kBlock, smem, s>>>(probs, act, nact);
+    kern<<<grid, kBlock, smem, s>>>(probs, act, nact);
 }
 
 template <int R, int MINB>
-static void launch_push(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+static void launch_push(const DevProb *probs, const int32_t *act, int nact, bool skip_full, cudaStream_t s) {
     static int grid = 0;
     if (grid == 0) {
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push<R, MINB>, kBlock, 0);
         grid = g_sms * (occ > 0 ? occ : 1);
     }
-    k_push<R, MINB><<<grid, kBlock, 0, s>>>(probs, act, nact);
+    k_push<R, MINB><<<grid, kBlock, 0, s>>>(probs, act, nact, skip_full ? 1 : 0);
 }
 
 template <int R>
@@ -2164,18 +2536,27 @@ static void launch_combines(const DevProb *probs, const int32_t *act, int nact, 
         default: break;                                      \
     }
 
-// Minimum resident blocks per SM of the propagation kernel (register budget); IM_PROP_VARIANT selects 3 or 6
-// instead of the default 4 (all exact alike).
-void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, bool pulls, cudaStream_t s) {
+// One sweep's propagation launches.  pulls: some listed problem may start a diffusion, whose first sweep k_first
+// runs; the others run in k_push, or in k_propg when later sweeps pull too (pull_more).  Returns the launches.
+// Minimum resident blocks per SM of the pulling kernels (register budget); IM_PROP_VARIANT selects 3 or 6 instead
+// of the default 4 (all exact alike).
+int launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, bool pulls, bool pull_more,
+                cudaStream_t s) {
     if (!pulls) {
-        IMK_R_SWITCH(R, (launch_push<RR, kPushMinBlocks>(probs, act, nact, s)));
-        return;
+        IMK_R_SWITCH(R, (launch_push<RR, kPushMinBlocks>(probs, act, nact, false, s)));
+        return 1;
     }
     switch (g_variant) {
-        case 3: IMK_R_SWITCH(R, (launch_gather<RR, 3>(probs, act, nact, s))); return;
-        case 6: IMK_R_SWITCH(R, (launch_gather<RR, 6>(probs, act, nact, s))); return;
-        default: IMK_R_SWITCH(R, (launch_gather<RR, 4>(probs, act, nact, s))); return;
+        case 3: IMK_R_SWITCH(R, (launch_gather<RR, 3, true>(probs, act, nact, s))); break;
+        case 6: IMK_R_SWITCH(R, (launch_gather<RR, 6, true>(probs, act, nact, s))); break;
+        default: IMK_R_SWITCH(R, (launch_gather<RR, 4, true>(probs, act, nact, s))); break;
     }
+    if (pull_more) {
+        IMK_R_SWITCH(R, (launch_gather<RR, 4, false>(probs, act, nact, s)));
+    } else {
+        IMK_R_SWITCH(R, (launch_push<RR, kPushMinBlocks>(probs, act, nact, true, s)));
+    }
+    return 2;
 }
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     IMK_R_SWITCH(R, (launch_combines<RR>(probs, act, nact, s)));
@@ -2189,6 +2570,12 @@ void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_
 }
 void launch_scan(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     IMK_R_SWITCH(R, (k_scan<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
+}
+int launch_celf(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    k_celf_max<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
+    k_celf_tau<<<nact, 128, 0, s>>>(probs, act, nact);
+    IMK_R_SWITCH(R, (k_celf_eval<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
+    return 3;
 }
 void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t step, cudaStream_t s) {
     k_choose<<<nact, 32, 0, s>>>(probs, act, nact, step);
@@ -2210,7 +2597,8 @@ void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact,
     IMK_R_SWITCH(R, (launch_bfs_level_r<RR>(probs, act, nact, gb, s)));
 }
 template <int R>
-static bool launch_bfs_run_r(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
+static bool launch_bfs_run_r(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, uint32_t limit,
+                             cudaStream_t s) {
     static int grid = -1;
     if (grid < 0) {
         int coop = 0, occ = 0;
@@ -2219,7 +2607,7 @@ static bool launch_bfs_run_r(const DevProb *probs, const int32_t *act, int nact,
         grid = (coop && occ > 0) ? g_sms * std::min(occ, 2) : 0;
     }
     if (grid == 0) return false;
-    void *args[] = {const_cast<DevProb **>(&probs), const_cast<int32_t **>(&act), &nact, &gb};
+    void *args[] = {const_cast<DevProb **>(&probs), const_cast<int32_t **>(&act), &nact, &gb, &limit};
     if (cudaMemsetAsync(gb, 0, sizeof(GridBar), s) != cudaSuccess) return false;
     if (cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_bfs_run<R>), dim3(grid), dim3(kRunBlock), args,
                                     0, s) != cudaSuccess) {
@@ -2228,9 +2616,10 @@ static bool launch_bfs_run_r(const DevProb *probs, const int32_t *act, int nact,
     }
     return true;
 }
-bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
+bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, uint32_t barrier_limit,
+                    cudaStream_t s) {
     bool ok = false;
-    IMK_R_SWITCH(R, (ok = launch_bfs_run_r<RR>(probs, act, nact, gb, s)));
+    IMK_R_SWITCH(R, (ok = launch_bfs_run_r<RR>(probs, act, nact, gb, barrier_limit, s)));
     return ok;
 }
 void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {

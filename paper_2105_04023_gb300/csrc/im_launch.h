@@ -13,18 +13,27 @@ cudaError_t configure(int device);
 int grid_warp();
 
 void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
-// One sweep: the pull-and-push kernel when a listed problem may pull (pulls), else the push-only kernel.
-void launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, bool pulls, cudaStream_t s);
+// One sweep: when a listed problem may start a diffusion (pulls), the fused first-sweep kernel and beside it the
+// push kernel (or, with pull_more, the kernel that also pulls later sweeps); else the push-only kernel.  Returns the
+// number of kernels launched.
+int launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, bool pulls, bool pull_more,
+                cudaStream_t s);
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 // Ends a sweep: frontier lists and row copies, then (last block) the stop test and counter resets.
 void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
 void launch_scan(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+// The lazy argmax of a greedy step that keeps the sketch (bound pass, exact key of the best bound, exact pass over
+// the candidates whose bound beats it); every listed problem must have had a full scan since its last build.
+// Returns the kernels launched.
+int launch_celf(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t step, cudaStream_t s);
 void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cudaStream_t s);
 // One search level of each listed problem; its last block ends the level (stop test, counter resets).
 void launch_bfs_level(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
 // A whole search in one cooperative launch; false if the device cannot run it (the caller then steps levels).
-bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
+// barrier_limit: polls of one grid-barrier wait before the kernel gives up (kBarrierLimit unless a test lowers it).
+bool launch_bfs_run(int R, const DevProb *probs, const int32_t *act, int nact, GridBar *gb, uint32_t barrier_limit,
+                    cudaStream_t s);
 void launch_merge(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 // Influence scorer: live masks of samples s0 .. s0 + R - 1 (those at or past nvalid left dead) into prob->live,
 // and per-sample reach counts of prob->vis added into counts[R].

@@ -36,12 +36,9 @@ struct StaticScratch {
 
 static __device__ __align__(256) StaticScratch g_scratch;
 
-// Bytewise max of register words (registers are <= 32, so no byte of the difference borrows).
-__device__ __forceinline__ uint32_t bytemax(uint32_t a, uint32_t b) {
-    uint32_t ge;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(ge) : "r"(a + 0x80808080u - b), "r"(0u), "r"(0xBA98u));
-    return (a & ge) | (b & ~ge);
-}
+// Bytewise unsigned max of register words, exact for every byte value (a caller's matrix need not come from this
+// library, so its bytes are not assumed to be small).
+__device__ __forceinline__ uint32_t bytemax(uint32_t a, uint32_t b) { return __vmaxu4(a, b); }
 
 // Block b merges seeds [64 b, 64 b + 64) into partial[b]; thread w owns register word w.
 __global__ void k_estimate_partial(StaticScratch *sc, const uint8_t *__restrict__ M, int64_t n, int R,
@@ -117,10 +114,18 @@ extern "C" im_status im_estimate_static(im_ctx *ctx, const uint8_t *registers, i
         imh::ctx_set_error(ctx, "n must be >= 1");
         return IM_EINVAL;
     }
+    // rows are read as 32-bit words
+    if ((reinterpret_cast<uintptr_t>(registers) & 3u) != 0 || (reinterpret_cast<uintptr_t>(seeds) & 3u) != 0) {
+        imh::ctx_set_error(ctx, "registers and seeds must be 4-byte aligned");
+        return IM_EINVAL;
+    }
     const int device = imh::ctx_device(ctx);
     cudaStream_t s = imh::ctx_stream(ctx);
     StaticScratch *sc = nullptr;
-    cudaError_t e = cudaSetDevice(device);
+    // the call runs with the context's device current and gives the calling thread its own current device back
+    int prev = -1;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess) e = cudaSetDevice(device);
     if (e == cudaSuccess) e = scratch_address(device, &sc);
     if (e == cudaSuccess) e = cudaMemsetAsync(&sc->bad_seed, 0, sizeof(unsigned int), s);
     const int nblocks = (k + kSeedsPerBlock - 1) / kSeedsPerBlock;
@@ -134,6 +139,10 @@ extern "C" im_status im_estimate_static(im_ctx *ctx, const uint8_t *registers, i
     if (e == cudaSuccess) e = cudaMemcpyAsync(&g, &sc->gsum, sizeof(g), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, &sc->bad_seed, sizeof(bad), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (prev >= 0 && prev != device) {
+        const cudaError_t r = cudaSetDevice(prev);
+        if (e == cudaSuccess) e = r;
+    }
     if (e != cudaSuccess) {
         imh::ctx_set_error(ctx, cudaGetErrorString(e));
         cudaGetLastError();

@@ -46,9 +46,10 @@ def rmat20_wc(cache: bool = False) -> Problem:
     return Problem(g, WC, 0.0, R=256, K=50, eps_g=0.01, seed=2, name="rmat_s20_ef16_wc_R256_K50")
 
 
-def chunglu22_ic() -> Problem:
+def chunglu22_ic(cache: bool = False) -> Problem:
     """Directed Chung-Lu n=2^22, mean degree 16, exponent 2.1, IC p=0.01, R=512, K=100, eps_g=0.02."""
-    g = graphs.chung_lu(1 << 22, 16.0, 2.1, seed=3)
+    g = (graphs.cached(lambda: graphs.chung_lu(1 << 22, 16.0, 2.1, seed=3), "chunglu_n22_d16_g2.1_seed3") if cache
+         else graphs.chung_lu(1 << 22, 16.0, 2.1, seed=3))
     return Problem(g, IC, 0.01, R=512, K=100, eps_g=0.02, seed=3, name="chunglu_n4M_d16_ic0.01_R512_K100")
 
 

@@ -10,46 +10,57 @@ from collections import deque
 import numpy as np
 
 
-def live_matrix(orc, n, xadj, adj, T, possible, X):
-    """live[e, j] for every edge e and simulation j, from the oracle's pinned live test."""
+def live_matrix(orc, n, xadj, adj, T, possible, X, undirected=False):
+    """live[e, j] for every edge e and simulation j, from the oracle's pinned live test.  undirected: both directions
+    of an edge take the hash of the key (min, max)."""
     m = adj.shape[0]
     R = X.shape[0]
     src = np.repeat(np.arange(n), np.diff(xadj))
     L = np.zeros((m, R), dtype=bool)
     for e in range(m):
-        h = orc.edge_hash(int(src[e]), int(adj[e]), n)
+        a, b = int(src[e]), int(adj[e])
+        if undirected and b < a:
+            a, b = b, a
+        h = orc.edge_hash(a, b, n)
         for j in range(R):
             L[e, j] = orc.is_live(h, int(X[j]), int(T[e]), int(possible[e]))
     return L
 
 
-def reach_set(n, xadj, adj, live, j, start, blocked=None):
-    """Vertices reachable from `start` over edges live in simulation j, never entering blocked (v, j)."""
+def reach_set(n, xadj, adj, live, j, start, blocked=None, enter_blocked=False):
+    """Vertices reachable from `start` over edges live in simulation j, never entering blocked (v, j); with
+    enter_blocked a blocked vertex is entered but not left (a path ends there)."""
     seen = {start}
     q = deque([start])
     while q:
         u = q.popleft()
+        if blocked is not None and blocked[u, j] and u != start:
+            continue
         for e in range(xadj[u], xadj[u + 1]):
             v = int(adj[e])
             if v in seen or not live[e, j]:
                 continue
-            if blocked is not None and blocked[v, j]:
+            if blocked is not None and blocked[v, j] and not enter_blocked:
                 continue
             seen.add(v)
             q.append(v)
     return seen
 
 
-def registers(orc, n, xadj, adj, live, Y, blocked=None):
-    """M[v, j] = max initial rank over the reach set of v in sample j (0 for blocked registers)."""
+def registers(orc, n, xadj, adj, live, Y, blocked=None, literal=False):
+    """M[v, j] = max initial rank over the reach set of v in sample j.  Residual blocking: blocked registers are 0
+    and blocked vertices are not entered.  Literal blocking (Algorithms 1 and 2 as printed): a blocked register keeps
+    its initial rank, and an unblocked v takes the max over the vertices it reaches by paths on which only the last
+    vertex may be blocked."""
     R = Y.shape[0]
     M = np.zeros((n, R), np.uint8)
     rank = np.array([[orc.init_rank(v, int(Y[j])) for j in range(R)] for v in range(n)], dtype=np.int64)
     for v in range(n):
         for j in range(R):
             if blocked is not None and blocked[v, j]:
+                M[v, j] = rank[v, j] if literal else 0
                 continue
-            M[v, j] = max(rank[x, j] for x in reach_set(n, xadj, adj, live, j, v, blocked))
+            M[v, j] = max(rank[x, j] for x in reach_set(n, xadj, adj, live, j, v, blocked, enter_blocked=literal))
     return M
 
 
@@ -63,7 +74,7 @@ def reached_by(n, xadj, adj, live, S, R):
     return out
 
 
-def greedy(orc, n, xadj, adj, live, Y, K, eps_g, eps_l):
+def greedy(orc, n, xadj, adj, live, Y, K, eps_g, eps_l, literal=False):
     """Algorithm 1 with every sketch formed by brute force (no diffusion), sigma by brute-force reach sets."""
     R = Y.shape[0]
     M = registers(orc, n, xadj, adj, live, Y)
@@ -95,7 +106,7 @@ def greedy(orc, n, xadj, adj, live, Y, K, eps_g, eps_l):
             out["rebuilt"].append(0)
         else:
             out["rebuilt"].append(1)
-            M = registers(orc, n, xadj, adj, live, Y, blocked=reached.astype(bool))
+            M = registers(orc, n, xadj, adj, live, Y, blocked=reached.astype(bool), literal=literal)
             MS = np.zeros(R, np.int64)
             varsigma = sigma
     return out

@@ -1,11 +1,13 @@
 """Parity at full workload sizes, in the configuration the benchmark times.
 
-The R-MAT scale-20 weighted-cascade workload (n = 2^20, m = 16.1M, R = 256, K = 50) is compared with a golden file
-the CPU oracle wrote (``tests/golden/make_golden.py rmat20_wc``, about an hour of CPU): the SHA-256 of all n*R
-registers, the sweep count, the edge-simulation visits and the frontier size of every sweep of the first diffusion,
-and the whole greedy trace.  The Chung-Lu n = 2^22 workload (R = 512) is checked on sampled registers, each of
-which the oracle evaluates alone by a search in one sample (Eq. 6: M_v[j] is the largest initial rank over the
-vertices v reaches in sample j).
+Both full-size workloads are compared with golden files the CPU oracle wrote (``tests/golden/make_golden.py``):
+  chunglu22_ic: Chung-Lu n = 2^22, mean degree 16, exponent 2.1, IC p = 0.01, R = 512, K = 100, eps_g = 0.02
+      (the benchmark's default workload);
+  rmat20_wc: R-MAT scale 20, edge factor 16, weighted cascade, R = 256, K = 50, eps_g = 0.01.
+Each golden file holds the SHA-256 of all n*R registers of the first diffusion, its sweep count, edge-simulation
+visits and the frontier size of every sweep, and the whole greedy trace (seeds, sigma, estimates, register sums,
+rebuild decisions, run totals).  Some registers are also re-derived one at a time by the oracle's search in one
+sample (M_v[j] is the largest initial rank over the vertices v reaches in sample j).
 """
 from __future__ import annotations
 
@@ -24,6 +26,7 @@ import paper_2105_04023_gb300 as im
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+WORKLOADS = ["chunglu22_ic", "rmat20_wc"]
 
 
 @pytest.fixture(scope="module")
@@ -36,22 +39,32 @@ def ctx():
     c.close()
 
 
-@pytest.fixture(scope="module")
-def rmat20():
-    with open(os.path.join(HERE, "golden", "rmat20_wc.json")) as f:
-        gold = json.load(f)
-    prob = workloads.rmat20_wc(cache=True)
-    assert (prob.graph.n, prob.graph.m, prob.R, prob.K, prob.seed) == (gold["n"], gold["m"], gold["R"], gold["K"],
-                                                                       gold["seed"])
-    return prob, gold
+_cache: dict = {}
+
+
+def _workload(name):
+    if name not in _cache:
+        with open(os.path.join(HERE, "golden", f"{name}.json")) as f:
+            gold = json.load(f)
+        prob = getattr(workloads, name)(cache=True)
+        assert (prob.graph.n, prob.graph.m, prob.R, prob.K, prob.seed) == (gold["n"], gold["m"], gold["R"],
+                                                                           gold["K"], gold["seed"])
+        _cache.clear()  # one full-size graph at a time in host memory
+        _cache[name] = (prob, gold)
+    return _cache[name]
 
 
 def _graph(prob, device="cuda"):
     return im.Graph.from_synth(prob.graph, prob.model, prob.p, p_edge=prob.p_edge, device=device)
 
 
-def test_rmat20_build_matches_golden(ctx, rmat20):
-    prob, gold = rmat20
+def _params(prob):
+    return im.params(R=prob.R, K=prob.K, eps_g=prob.eps_g, eps_l=prob.eps_l, eps_c=prob.eps_c, seed=prob.seed)
+
+
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_build_matches_golden(ctx, name):
+    prob, gold = _workload(name)
     sk = ctx.im_build_sketches(_graph(prob), im.params(R=prob.R, seed=prob.seed, eps_c=prob.eps_c))
     M = sk.im_sketch_registers()
     sweeps, visits, log = sk.im_sketch_info()
@@ -64,17 +77,18 @@ def test_rmat20_build_matches_golden(ctx, rmat20):
     probe = oracle.RegisterProbe(g.n, g.xadj, g.adj, prob.model, prob.p, prob.R, prob.seed)
     deg = np.diff(g.xadj)
     rng = np.random.default_rng(5)
-    vs = np.concatenate([np.argsort(deg)[-8:], rng.integers(0, g.n, 24)])
+    vs = np.concatenate([np.argsort(deg)[-8:], rng.integers(0, g.n, 24), [0, g.n - 1]])
     for v in vs:
-        for j in (0, 1, 127, 255):
+        for j in (0, 1, 31, 32, prob.R // 2 - 1, prob.R - 1):
             assert int(M[v, j]) == probe(int(v), j), (int(v), j)
+    assert int(M.max()) <= 32  # a register is a leading-zero count of a 32-bit word
     sk.close()
 
 
-def test_rmat20_select_matches_golden(ctx, rmat20):
-    prob, gold = rmat20
-    out = ctx.im_select_seeds(_graph(prob), im.params(R=prob.R, K=prob.K, eps_g=prob.eps_g, eps_l=prob.eps_l,
-                                                      eps_c=prob.eps_c, seed=prob.seed))
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_select_matches_golden(ctx, name):
+    prob, gold = _workload(name)
+    out = ctx.im_select_seeds(_graph(prob), _params(prob))
     sel = gold["select"]
     assert out["seeds"].tolist() == sel["seeds"]
     assert out["gsum"].tolist() == sel["gsum"]
@@ -86,29 +100,9 @@ def test_rmat20_select_matches_golden(ctx, rmat20):
     assert (st["visits"], st["sweeps"], st["builds"]) == (sel["visits"], sel["sweeps"], sel["builds"])
 
 
-def test_rmat20_select_host_buffers_match_golden(ctx, rmat20):
-    prob, gold = rmat20
-    out = ctx.im_select_seeds(_graph(prob, device=None), im.params(R=prob.R, K=prob.K, eps_g=prob.eps_g,
-                                                                   eps_l=prob.eps_l, eps_c=prob.eps_c,
-                                                                   seed=prob.seed), trace=False)
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_select_host_buffers_match_golden(ctx, name):
+    prob, gold = _workload(name)
+    out = ctx.im_select_seeds(_graph(prob, device=None), _params(prob), trace=False)
     assert out["seeds"].tolist() == gold["select"]["seeds"]
     assert out["sigma_final"] == gold["select"]["sigma"][-1]
-
-
-def test_chunglu22_sampled_registers(ctx):
-    prob = workloads.chunglu22_ic()
-    g = prob.graph
-    sk = ctx.im_build_sketches(_graph(prob), im.params(R=prob.R, seed=prob.seed))
-    M = sk.im_sketch_registers()
-    assert M.shape == (g.n, prob.R)
-    probe = oracle.RegisterProbe(g.n, g.xadj, g.adj, prob.model, prob.p, prob.R, prob.seed)
-    deg = np.diff(g.xadj)
-    rng = np.random.default_rng(9)
-    vs = np.concatenate([np.argsort(deg)[-16:], rng.integers(0, g.n, 48), [0, g.n - 1]])
-    js = (0, 31, 32, 255, 256, 511)
-    for v in vs:
-        for j in js:
-            assert int(M[v, j]) == probe(int(v), j), (int(v), j)
-    # a register is a leading-zero count of a 32-bit word (Eq. 5)
-    assert int(M.max()) <= 32
-    sk.close()

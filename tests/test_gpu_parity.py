@@ -100,6 +100,34 @@ def test_select_rmat_scale13_wc(ctx):
     assert_select_parity(ctx, g, WC, 0.0, 256, K=12, eps_g=0.01, seed=2, device="cuda")
 
 
+@pytest.mark.parametrize("gname,model,p,R", [("rmat10", WC, 0.0, 64), ("er300", IC, 0.05, 128),
+                                             ("hub1500", IC, 0.3, 256), ("ragged97", IC, 0.2, 512)])
+def test_lazy_argmax_equals_full_scan(monkeypatch, gname, model, p, R):
+    """The lazy argmax of the steps that keep the sketch (bounds from earlier scans, exact evaluation of the
+    candidates whose bound beats the best exact gain) picks the full scan's seed every step, ties to the smallest
+    id included; eps = +inf keeps the sketch for every step after the first."""
+    g = SMALL[gname]
+    K = min(20, g.n)
+    graph = im.Graph.from_synth(g, model, p)
+    prm = im.params(R=R, K=K, eps_g=math.inf, eps_l=math.inf, seed=13)
+    monkeypatch.setenv("IM_CELF", "0")
+    c0 = im.Context(0)
+    monkeypatch.delenv("IM_CELF")
+    try:
+        full = c0.im_select_seeds(graph, prm)
+    finally:
+        c0.close()
+    c1 = im.Context(0)
+    try:
+        lazy = c1.im_select_seeds(graph, prm)
+    finally:
+        c1.close()
+    for k in ("seeds", "gsum", "rebuilt", "sigma"):
+        assert lazy[k].tolist() == full[k].tolist(), k
+    ref = oracle.select_seeds(g.n, g.xadj, g.adj, model, p, R, K, math.inf, math.inf, 0.0, 13)
+    assert lazy["seeds"].tolist() == ref["seeds"].tolist()
+
+
 # --- edge cases -------------------------------------------------------------------------------------------------
 
 def test_single_vertex(ctx):

@@ -56,14 +56,21 @@ MUTATIONS = {
                    "if ((double)sizeL <= (double)n * eps_c + 1.0) break;"),
     # Algorithm 1's reach: an edge's liveness taken from the next simulation's word (a search that re-entered reached
     # vertices would overrun its queue instead)
-    "reach_wrong_simulation": ("if (!or_is_live(or_edge_hash(u, v, n), X[j], T[e], possible[e])) continue;",
-                               "if (!or_is_live(or_edge_hash(u, v, n), X[(j + 1) % R], T[e], possible[e])) continue;"),
+    "reach_wrong_simulation": ("if (!or_is_live(or_edge_hash_dir(u, v, n, undirected), X[j], T[e], possible[e])) continue;",
+                               "if (!or_is_live(or_edge_hash_dir(u, v, n, undirected), X[(j + 1) % R], T[e], possible[e])) "
+                               "continue;"),
     # Eq. 2: the FM correction factor
     "phi": ("static const double OR_PHI = 0.77351;", "static const double OR_PHI = 0.7735;"),
     # Eq. 3: M_S' merged with a min instead of a max
     "merge_min": ("if (row[j] > MS[j]) MS[j] = row[j];", "if (row[j] < MS[j]) MS[j] = row[j];"),
     # Section 3.2.1: the rebuild without the reached registers blocked
-    "rebuild_unblocked": ("or_init_registers(n, R, Y, reached, M);", "or_init_registers(n, R, Y, NULL, M);"),
+    "rebuild_unblocked": ("or_init_registers(n, R, Y, literal ? NULL : reached, M);",
+                          "or_init_registers(n, R, Y, NULL, M);"),
+    # reading R17: the literal rebuild zeroing the blocked registers as the residual one does
+    "literal_zeroes": ("or_init_registers(n, R, Y, literal ? NULL : reached, M);",
+                       "or_init_registers(n, R, Y, reached, M);"),
+    # reading R16: an undirected edge hashed by its direction
+    "undirected_key": ("if (undirected && v < u) return or_edge_hash(v, u, n);", "if (0) return or_edge_hash(v, u, n);"),
     # reading R8: the sketch kept only when both errors are small
     "keep_rule_and": ("if (err_l < eps_l || err_g < eps_g) {", "if (err_l < eps_l && err_g < eps_g) {"),
     # reading R9: seeds already in S scanned again

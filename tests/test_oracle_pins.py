@@ -512,3 +512,98 @@ def test_influence_mc_star_expectation(orc):
     assert reach.min() >= 1 and reach.max() <= L + 1
     # a leaf as the only seed reaches itself alone
     assert orc.influence_mc(g.n, g.xadj, g.adj, IC, p, [5], 64, seed=3)[0] == 64
+
+
+# --- literal blocking (reading R17) and undirected inputs (reading R16) ------------------------------------------
+
+@pytest.mark.parametrize("eps", [(0.0, 0.0), (0.01, 0.3), (0.2, 0.9)], ids=["always", "paper", "loose"])
+@pytest.mark.parametrize("gseed", [61, 63])
+def test_literal_blocking_greedy_equals_bruteforce(orc, eps, gseed):
+    # Algorithms 1 and 2 as printed: a rebuild re-initialises every register and Simulate skips only the blocked
+    # (u, j), so a blocked vertex keeps its rank and still passes it to unblocked in-neighbours
+    g = graphs.random_small(12, 30, gseed)
+    T, ok, X, Y = _problem(orc, g, IC, 0.5, 64, gseed)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X)
+    ref = bf.greedy(orc, g.n, g.xadj, g.adj, live, Y, 4, eps[0], eps[1], literal=True)
+    out = orc.select_seeds(g.n, g.xadj, g.adj, IC, 0.5, 64, 4, eps[0], eps[1], seed=gseed, literal=True)
+    assert out["seeds"].tolist() == ref["seeds"]
+    assert out["gsum"].tolist() == ref["gsum"]
+    assert out["rebuilt"].tolist() == ref["rebuilt"]
+    assert np.array_equal(out["sigma"], np.array(ref["sigma"]))
+
+
+def test_literal_blocking_registers_keep_their_rank(orc):
+    # after blocking, a literal rebuild's blocked registers are exactly the initial ranks, the residual ones 0
+    g = graphs.random_small(30, 120, 67)
+    R = 64
+    T, ok, X, Y = _problem(orc, g, IC, 0.4, R, 9)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X)
+    blocked = bf.reached_by(g.n, g.xadj, g.adj, live, [0, 5], R).astype(bool)
+    assert blocked.any() and not blocked.all()
+    init = orc.init_registers(g.n, R, Y)
+    lit = init.copy()
+    orc.simulate(g.n, g.xadj, g.adj, T, ok, R, X, lit, blocked=blocked.astype(np.uint8))
+    assert np.array_equal(lit[blocked], init[blocked])
+    assert np.array_equal(lit, bf.registers(orc, g.n, g.xadj, g.adj, live, Y, blocked=blocked, literal=True))
+    res = orc.init_registers(g.n, R, Y, blocked=blocked.astype(np.uint8))
+    orc.simulate(g.n, g.xadj, g.adj, T, ok, R, X, res, blocked=blocked.astype(np.uint8))
+    assert np.array_equal(res, bf.registers(orc, g.n, g.xadj, g.adj, live, Y, blocked=blocked))
+    assert not np.array_equal(lit, res)
+
+
+def _symmetric(n, m, seed):
+    g = graphs.random_small(n, m, seed)
+    src, dst = g.edges()
+    return graphs.csr_from_edges(n, np.concatenate([src, dst]), np.concatenate([dst, src]))
+
+
+def test_undirected_edge_key_is_symmetric(orc):
+    n = 1000
+    for u, v in [(0, 1), (3, 999), (512, 17), (998, 999)]:
+        h = orc.edge_hash(min(u, v), max(u, v), n)
+        assert orc.edge_hash_dir(u, v, n, True) == h == orc.edge_hash_dir(v, u, n, True)
+        assert orc.edge_hash_dir(u, v, n, False) == orc.edge_hash(u, v, n)
+
+
+def test_undirected_weighted_cascade_equals_bruteforce(orc):
+    # weighted cascade keeps a threshold per direction (1 / indeg of the target), so the shared key couples the two
+    # directions without making them equal; registers are still the brute-force reach-set maxima
+    g = _symmetric(40, 60, 82)
+    M, _, _, _ = orc.build_sketch(g.n, g.xadj, g.adj, WC, 0.0, 64, seed=5, undirected=True)
+    T, ok, X, Y = _problem(orc, g, WC, 0.0, 64, 5)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X, undirected=True)
+    assert np.array_equal(M, bf.registers(orc, g.n, g.xadj, g.adj, live, Y))
+
+
+@pytest.mark.parametrize("model,p", [(IC, 0.25), (IC, 0.6)])
+def test_undirected_registers_are_component_maxima(orc, model, p):
+    # with one probability for both directions, an edge is live in both directions together, so the reach set of v
+    # in a sample is its connected component: every register is the largest rank over the component (scipy's
+    # components, independent of the oracle)
+    g = _symmetric(40, 60, 81)
+    R = 64
+    M, sweeps, visits, _ = orc.build_sketch(g.n, g.xadj, g.adj, model, p, R, seed=5, undirected=True)
+    T, ok, X, Y = _problem(orc, g, model, p, R, 5)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X, undirected=True)
+    src = np.repeat(np.arange(g.n), np.diff(g.xadj))
+    rank = np.array([[orc.init_rank(v, int(Y[j])) for j in range(R)] for v in range(g.n)])
+    for j in range(R):
+        e = live[:, j]
+        A = sp.coo_matrix((np.ones(int(e.sum())), (src[e], g.adj[e])), shape=(g.n, g.n)).tocsr()
+        assert (A != A.T).nnz == 0  # the live sample is symmetric
+        _, comp = csg.connected_components(A, directed=False)
+        for c in np.unique(comp):
+            members = comp == c
+            assert np.all(M[members, j] == rank[members, j].max())
+    assert np.array_equal(M, bf.registers(orc, g.n, g.xadj, g.adj, live, Y))
+
+
+def test_undirected_greedy_equals_bruteforce(orc):
+    g = _symmetric(14, 20, 83)
+    T, ok, X, Y = _problem(orc, g, IC, 0.4, 64, 6)
+    live = bf.live_matrix(orc, g.n, g.xadj, g.adj, T, ok, X, undirected=True)
+    ref = bf.greedy(orc, g.n, g.xadj, g.adj, live, Y, 4, 0.01, 0.3)
+    out = orc.select_seeds(g.n, g.xadj, g.adj, IC, 0.4, 64, 4, 0.01, 0.3, seed=6, undirected=True)
+    assert out["seeds"].tolist() == ref["seeds"]
+    assert out["gsum"].tolist() == ref["gsum"]
+    assert np.array_equal(out["sigma"], np.array(ref["sigma"]))

@@ -231,6 +231,8 @@ def run_ours(args, world, rank, local):
     host_graph = im.Graph(g.n, hx.numpy(), ha.numpy(), prob.model, prob.p)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     ctx = im.Context(local)
+    # set-up (untimed): the autotuner picks this graph class's launch shapes (results do not depend on them)
+    tuning = ctx.im_autotune(dev_graph, prm) if not args.no_autotune else None
 
     seeds_ref = None
     for _ in range(args.warmup):
@@ -245,6 +247,8 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     dev_ms, visits, launches, prop_ms, prop_bytes, prop_launches, wall = [], 0, 0, 0.0, 0, 0, []
+    pairs = first_bytes = first_launches = 0
+    first_ms = 0.0
     phases = {"sweep_ms": 0.0, "scan_ms": 0.0, "bfs_ms": 0.0, "init_ms": 0.0}
     for _ in range(args.steps):
         flush.fill_(1)
@@ -259,6 +263,10 @@ def run_ours(args, world, rank, local):
         prop_ms += st["prop_ms"]
         prop_bytes += st["prop_bytes"]
         prop_launches += st["prop_launches"]
+        pairs += st["live_pairs"]
+        first_bytes += st["first_bytes"]
+        first_ms += st["first_ms"]
+        first_launches += st["first_launches"]
         for k in phases:
             phases[k] += st[k]
         if seeds_ref is not None:
@@ -284,12 +292,14 @@ def run_ours(args, world, rank, local):
     e2e_s, e2e_all = aggregate(sum(e2e_ms) / 1000.0, float(e2e_visits), world)
 
     hbm, peak_kind = peaks()
-    achieved = prop_bytes / (prop_ms / 1000.0) / 1e9 if prop_ms > 0 else None
+    # the dominant kernel: the first sweep of every diffusion (k_first), timed by CUDA events around its launches
+    achieved = first_bytes / (first_ms / 1000.0) / 1e9 if first_ms > 0 else None
+    sweeps_achieved = prop_bytes / (prop_ms / 1000.0) / 1e9 if prop_ms > 0 else None
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "prop_traffic.json")
+    tpath = os.path.join(ROOT, "profiles", f"k_first_{args.workload}_traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
-            traffic = json.load(f).get("bytes_per_launch")
+            traffic = json.load(f).get("dram_bytes_per_launch")
     if rank == 0:
         stride = ORACLE_STRIDE[args.workload]
         cpu_v, cpu_visits, cpu_dt, cpu_rows = oracle_sample(prob, stride)
@@ -303,9 +313,14 @@ def run_ours(args, world, rank, local):
             "visits_per_step": visits // args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                         "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "k_propg / k_push (one sweep: sweep 0 pulls every row in k_propg, later sweeps push from L in k_push)",
-                         "bytes_per_launch": prop_bytes / max(prop_launches, 1),
-                         "launches": prop_launches, "ms": prop_ms},
+                         "peak_kind": f"{peak_kind} copy bandwidth (sustained copy; of measured)",
+                         "kernel": "k_first: the first sweep of every diffusion (initial registers formed in the "
+                                   "kernel, every sparse pair merged, every row written to both buffers)",
+                         "bytes_per_launch": first_bytes / max(first_launches, 1),
+                         "launches": first_launches, "ms": first_ms,
+                         "all_sweep_kernels": {"achieved": sweeps_achieved,
+                                               "frac": (sweeps_achieved / hbm) if sweeps_achieved else None,
+                                               "bytes": prop_bytes, "ms": prop_ms, "launches": prop_launches}},
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"first Jacobi sweep of the build over every {stride}-th row of the full "
                                        f"graph ({cpu_rows} rows, {cpu_visits} visits, {cpu_dt:.1f} s)",
@@ -315,6 +330,13 @@ def run_ours(args, world, rank, local):
                     "ms_per_step": 1000 * e2e_s / max(1, args.steps)},
             "gpu_launches": launches,
             "clocks": clk,
+            "tuning": tuning,
+            "executed": {"live_pairs_per_step": pairs // args.steps,
+                         "live_pairs_per_s": pairs / (sum(dev_ms) / 1000.0),
+                         "modelled_sweep_bytes_per_s": achieved * 1e9 if achieved else None,
+                         "note": "value counts the Jacobi edge-simulation visits of Algorithm 2 (every edge into L "
+                                 "times R); the kernels touch only the live (edge, simulation) pairs, counted here, "
+                                 "and move the modelled bytes of roofline.achieved"},
             "wall_ms_per_step": 1000 * sum(wall) / len(wall),
             "phase_ms_per_step": {k: v / args.steps for k, v in phases.items()},
         }
@@ -382,6 +404,8 @@ def run_mc(args, local):
         ctx.im_influence_mc(graph, seeds, N, 77)
     ctx.set_timing(True)
     times, sig = [], None
+    clocks = ClockSampler(local)
+    clocks.start()
     for i in range(args.steps):
         a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -390,6 +414,7 @@ def run_mc(args, local):
         c.record()
         torch.cuda.synchronize()
         times.append(a.elapsed_time(c) / 1000.0)
+    clk = clocks.stop()
     st = ctx.stats()
     t = sum(times) / len(times)
     import oracle
@@ -397,7 +422,7 @@ def run_mc(args, local):
     t0 = time.perf_counter()
     _, one = oracle.influence_mc(g.n, g.xadj, g.adj, prob.model, prob.p, seeds, 1, 77)
     t_cpu = time.perf_counter() - t0
-    out = {"mode": "mc", "workload": "R-MAT scale 20, edge factor 16, weighted cascade (the 50 seeds of the select)",
+    out = {"mode": "mc", "workload": f"{WORKLOADS[args.workload]} (the {prob.K} seeds of the select)", "clocks": clk,
            "samples": N, "steps": args.steps, "s_per_call": t, "samples_per_s": N / t,
            "edge_draws_per_s": g.m * N / t, "sigma_mc": sig, "sigma_sketch_samples": sel["sigma_final"],
            "mc_stderr": float(np.std(reach.astype(np.float64), ddof=1) / np.sqrt(N)),
@@ -429,8 +454,18 @@ def run_batch(args, local):
     gs = [im.Graph.from_synth(p.graph, p.model, p.p, device=f"cuda:{local}") for p in probs]
     prms = [im.params(R=p.R, K=p.K, eps_g=p.eps_g, eps_l=p.eps_l, seed=p.seed) for p in probs]
     ctx = im.Context(local)
+    # autotuning: one graph of every (R, degree class) times the candidate launch shapes (untimed set-up)
+    t_tune = time.perf_counter()
+    classes = {}
+    for p, g, prm in zip(probs, gs, prms):
+        dc = 0 if p.graph.m < p.graph.n else int(np.log2(p.graph.m // p.graph.n)) + 1
+        classes.setdefault((p.R, dc), (g, prm))
+    tuning = {f"R{k[0]}_d{k[1]}": ctx.im_autotune(g, prm) for k, (g, prm) in sorted(classes.items())}
+    t_tune = time.perf_counter() - t_tune
     ctx.im_select_seeds_batch(gs[:8], prms[:8])  # warm-up
     torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
     t = time.perf_counter()
     batch = ctx.im_select_seeds_batch(gs, prms)
     t_batch = time.perf_counter() - t
@@ -442,6 +477,7 @@ def run_batch(args, local):
         plain.append(ctx.im_select_seeds(g, prm, trace=False))
         visits_plain += ctx.stats()["visits"]
     t_plain = time.perf_counter() - t
+    clk = clocks.stop()
     same = all(a["seeds"].tolist() == c["seeds"].tolist() and a["sigma_final"] == c["sigma_final"]
                for a, c in zip(batch, plain))
     m_total = sum(p.graph.m for p in probs)
@@ -449,16 +485,20 @@ def run_batch(args, local):
            "batched_s": t_batch, "plain_s": t_plain, "speedup": t_plain / t_batch,
            "batched_graphs_per_s": len(probs) / t_batch, "plain_graphs_per_s": len(probs) / t_plain,
            "batched_visits_per_s": st_b["visits"] / t_batch, "plain_visits_per_s": visits_plain / t_plain,
-           "identical_seed_sets": same, "batched_kernel_launches": st_b["kernel_launches"]}
+           "identical_seed_sets": same, "batched_kernel_launches": st_b["kernel_launches"], "clocks": clk,
+           "autotune_s": t_tune, "tuning": {k: (v["first_sweep_blocks"], v["stream_push"]) for k, v in tuning.items()}}
     print(json.dumps(out), flush=True)
     ctx.close()
 
 
 def run_serve(args, local):
-    """The served workload: a resident pool of 64 R-MAT graphs (weighted cascade) and a Poisson stream of queries
-    (K uniform in 5..100, R in {64, 256}); admission by a 120 GB HBM budget; continuous batching.  The arrival rate
-    is 0.8 x the saturation rate measured by a closed-loop pre-run.  Reported: p50/p99 latency and queries/s, and
-    the same queries answered one at a time through im_select_seeds."""
+    """The served workload: a resident pool of 64 R-MAT graphs (scale 12 + i mod 9, edge factor 16, weighted
+    cascade) and a Poisson stream of queries (K uniform in 5..100, R in {64, 256}, graph uniform over the pool, each
+    query with its own run seed unless --serve-shared-seed); admission by a 120 GB HBM budget; continuous batching.
+    The arrival rate is 0.8 x the saturation rate measured by a closed-loop pre-run.  Reported with the clocks of
+    the timed stream: p50/p99 latency, queries/s, the share of queries started from a kept first diffusion, and, on
+    a sample of the same queries answered one at a time through im_select_seeds, the sequential queries/s and
+    whether every sampled result is identical."""
     import torch
 
     import paper_2105_04023_gb300 as im
@@ -471,50 +511,47 @@ def run_serve(args, local):
     for i in range(64):
         scale = min(12 + (i % 9), args.serve_max_scale)
         pool.append(graphs.cached(lambda: graphs.rmat(scale, 16, seed=2000 + i), f"rmat_s{scale}_ef16_seed{2000 + i}"))
-    Q = workloads.serve_queries(count=args.serve_queries, pool=64, seed=5)
+    Q = workloads.serve_queries(count=args.serve_queries + args.serve_saturation, pool=64, seed=5)
     ctx = im.Context(local)
     srv = im.Server(ctx, hbm_budget_bytes=120 << 30, max_active=256)
     gdev = [im.Graph.from_synth(g, im.IM_WC, device=f"cuda:{local}") for g in pool]
     gids = [srv.im_server_add_graph(g) for g in gdev]
 
-    def prm(q):
-        return im.params(R=int(q[2]), K=int(q[1]), eps_g=0.01, eps_l=0.3, seed=7)
+    def prm(k):
+        q = Q[k]
+        seed = 7 if args.serve_shared_seed else 100000 + k
+        return im.params(R=int(q[2]), K=int(q[1]), eps_g=0.01, eps_l=0.3, seed=seed)
 
-    def drain(tickets, arrivals=None):
-        done, lat = {}, []
+    def drain(tickets):
         while tickets:
             srv.im_server_step()
-            now = time.perf_counter()
             for tk in list(tickets):
-                r = srv.im_server_poll(tk)
-                if r is not None:
-                    done[tk] = r
-                    if arrivals is not None:
-                        lat.append(now - arrivals[tk])
+                if srv.im_server_poll(tk) is not None:
                     tickets.discard(tk)
-        return done, lat
 
-    # closed loop: everything submitted at once gives the saturation rate
-    n_sat = min(100, len(Q) // 4)
+    # closed loop: the first queries submitted at once give the saturation rate
+    n_sat = args.serve_saturation
     t0 = time.perf_counter()
-    tk = {srv.im_server_submit(gids[int(q[0])], prm(q)) for q in Q[:n_sat]}
-    drain(tk)
+    drain({srv.im_server_submit(gids[int(Q[k, 0])], prm(k)) for k in range(n_sat)})
     qps_sat = n_sat / (time.perf_counter() - t0)
+    hits0 = srv.im_server_info()["build_hits"]
     lam = 0.8 * qps_sat
     # open loop: Poisson arrivals at lam
-    rest = Q[n_sat:]
-    arrive = np.cumsum(rest[:, 3]) / lam
+    ks = list(range(n_sat, len(Q)))
+    arrive = np.cumsum(Q[n_sat:, 3]) / lam
+    clocks = ClockSampler(local)
+    clocks.start()
     t0 = time.perf_counter()
     pending, arrivals, results, lat = set(), {}, {}, []
-    k = 0
-    while k < len(rest) or pending:
+    i = 0
+    while i < len(ks) or pending:
         now = time.perf_counter() - t0
-        while k < len(rest) and arrive[k] <= now:
-            t = srv.im_server_submit(gids[int(rest[k, 0])], prm(rest[k]))
-            arrivals[t] = t0 + arrive[k]
+        while i < len(ks) and arrive[i] <= now:
+            t = srv.im_server_submit(gids[int(Q[ks[i], 0])], prm(ks[i]))
+            arrivals[t] = t0 + arrive[i]
             pending.add(t)
-            results[t] = k
-            k += 1
+            results[t] = ks[i]
+            i += 1
         if pending:
             srv.im_server_step()
             now2 = time.perf_counter()
@@ -524,22 +561,27 @@ def run_serve(args, local):
                     lat.append(now2 - arrivals[t])
                     results[t] = (results[t], r)
                     pending.discard(t)
-        elif k < len(rest):
-            time.sleep(max(0.0, min(0.001, arrive[k] - (time.perf_counter() - t0))))
+        elif i < len(ks):
+            time.sleep(max(0.0, min(0.001, arrive[i] - (time.perf_counter() - t0))))
     span = time.perf_counter() - t0
-    # the same queries one at a time through the plain call
+    clk = clocks.stop()
+    hits = srv.im_server_info()["build_hits"] - hits0
+    # a sample of the same queries one at a time through the plain call
+    sample = list(results.items())[: args.serve_sequential]
     t1 = time.perf_counter()
     same = True
-    for t, (k_i, r) in results.items():
-        q = rest[k_i]
-        alone = ctx.im_select_seeds(gdev[int(q[0])], prm(q), trace=False)
-        same = same and alone["seeds"].tolist() == r["seeds"].tolist()
+    for t, (k, r) in sample:
+        alone = ctx.im_select_seeds(gdev[int(Q[k, 0])], prm(k), trace=False)
+        same = same and alone["seeds"].tolist() == r["seeds"].tolist() and alone["sigma_final"] == r["sigma_final"]
     t_seq = time.perf_counter() - t1
     lat_ms = np.array(lat) * 1000
-    out = {"mode": "serve", "queries": len(rest), "pool_graphs": 64, "pool_max_scale": args.serve_max_scale,
-           "saturation_qps": qps_sat, "lambda_qps": lam, "served_qps": len(rest) / span,
+    out = {"mode": "serve", "queries": len(ks), "pool_graphs": 64, "pool_max_scale": args.serve_max_scale,
+           "seeds": "shared (one run seed)" if args.serve_shared_seed else "one run seed per query",
+           "saturation_queries": n_sat, "saturation_qps": qps_sat, "lambda_qps": lam, "served_qps": len(ks) / span,
            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-           "sequential_qps": len(rest) / t_seq, "identical_seed_sets": same, "hbm_budget_gb": 120}
+           "kept_diffusion_hit_rate": hits / len(ks),
+           "sequential_sample": len(sample), "sequential_qps": len(sample) / t_seq,
+           "identical_seed_sets": same, "hbm_budget_gb": 120, "clocks": clk}
     print(json.dumps(out), flush=True)
     srv.close()
     ctx.close()
@@ -557,10 +599,14 @@ def main():
                          "serve: the query stream on a resident graph pool; mc: the Monte-Carlo influence scorer")
     ap.add_argument("--mc-samples", type=int, default=1024)
     ap.add_argument("--k", type=int, default=0, help="override the workload's K (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--batch-graphs", type=int, default=256)
     ap.add_argument("--batch-max-scale", type=int, default=18)
-    ap.add_argument("--serve-queries", type=int, default=400)
-    ap.add_argument("--serve-max-scale", type=int, default=16)
+    ap.add_argument("--serve-queries", type=int, default=10000)
+    ap.add_argument("--serve-saturation", type=int, default=200, help="queries of the closed-loop pre-run")
+    ap.add_argument("--serve-sequential", type=int, default=200, help="queries re-run one at a time")
+    ap.add_argument("--serve-max-scale", type=int, default=20)
+    ap.add_argument("--serve-shared-seed", action="store_true", help="one run seed for every query")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.mode == "build":

@@ -63,6 +63,11 @@ typedef enum {
  * Requirements (checked, IM_EINVAL otherwise): n >= 1, xadj[0] = 0, xadj non-decreasing, xadj[n] = m, every target
  * in [0, n), n < 2^31.  Self-loops and parallel edges should be merged beforehand (Section 2.1); they are accepted
  * and treated as ordinary edges.
+ * undirected = 1 marks an undirected input (six of the paper's graphs, Section 4) stored with both directions of
+ * every edge: each row sorted by target and every (u, v) matched by (v, u) (checked, IM_EINVAL otherwise).  Both
+ * directions then take the hash of the key (min(u, v), max(u, v)) and are sampled in the same simulations, so with
+ * one probability for both directions a sampled graph reaches exactly a connected component; the weighted cascade
+ * keeps 1/indeg of the target per direction.  im_influence_mc does not take undirected inputs.
  */
 typedef struct {
     int64_t n;             /* vertices */
@@ -73,7 +78,16 @@ typedef struct {
     double p;              /* IM_IC_CONST: the edge probability, in [0, 1] */
     const float *p_edge;   /* IM_PER_EDGE: m probabilities in [0, 1]; NULL otherwise */
     im_memory memory;
+    int32_t undirected;    /* 0: directed; 1: undirected input stored with both directions (see above) */
 } im_graph;
+
+typedef enum {
+    IM_BLOCK_RESIDUAL = 0, /* a rebuild sketches the residual samples: registers of vertices S reaches are 0 and never
+                              updated (Section 3.2.1) */
+    IM_BLOCK_LITERAL = 1   /* Algorithms 1 and 2 as printed: a rebuild re-initialises every register and Simulate
+                              never updates a blocked (u, j), which keeps its rank and passes it to unblocked
+                              in-neighbours */
+} im_blocking;
 
 /*
  * Parameters of one influence-maximisation run (Algorithm 1).
@@ -86,6 +100,7 @@ typedef struct {
  * seed: run seed of the per-simulation words.
  * max_sweeps: limit on sweeps of one diffusion and levels of one reachability search; 0 means n + 2 (always
  *   enough for a fixpoint).  Exceeding it returns IM_ETIMEOUT.
+ * blocking: an im_blocking value, how a rebuild treats the registers of vertices S reaches (default residual).
  */
 typedef struct {
     int32_t R;
@@ -95,6 +110,7 @@ typedef struct {
     double eps_c;
     uint64_t seed;
     int64_t max_sweeps;
+    int32_t blocking;
 } im_params;
 
 /* Per-step record of a seed selection (Algorithm 1); every array has K entries and may be NULL. */
@@ -125,6 +141,12 @@ typedef struct {
     double scan_ms;           /* with timing enabled: gain scans and seed choice */
     double bfs_ms;            /* with timing enabled: reachability-search levels */
     double init_ms;           /* with timing enabled: register (re)initialisation and M_S' merges */
+    uint64_t live_pairs;      /* sparse (edge, simulation) pairs the propagation kernels examined: the live pairs
+                                 behind `visits` that the sweeps actually touch (edges live in many simulations,
+                                 merged as whole rows, are not counted) */
+    uint64_t first_bytes;     /* of prop_bytes, those of the first sweep of every diffusion (its own kernel) */
+    double first_ms;          /* with timing enabled: CUDA-event time of the first-sweep kernel's launches */
+    int64_t first_launches;   /* its launches */
 } im_stats;
 
 typedef struct im_ctx im_ctx;
@@ -137,6 +159,25 @@ im_status im_ctx_destroy(im_ctx *ctx);
 
 /* Last error message of the context (never NULL); valid until the next call on the context. */
 const char *im_last_error(const im_ctx *ctx);
+
+/*
+ * Autotuning of launch shapes (no counterpart in the paper; the results never depend on it).  For the graph's
+ * shape class (R and the mean out-degree class floor(log2(m / n)) + 1, or 0 when m < n) the call times the first
+ * diffusion of `graph` with `params` under each candidate configuration (the register budget of the first-sweep
+ * kernel, 3, 4 or 6 resident blocks per SM, and whether push sweeps over a large frontier stream every in-pair),
+ * checks that every candidate reaches the same registers, sweeps and visits (IM_ECUDA otherwise), and keeps the
+ * fastest for all later calls on the context with graphs of that class.  out (nullable) receives the choice.
+ */
+typedef struct {
+    int32_t first_sweep_blocks; /* chosen register budget of the first-sweep kernel (resident blocks per SM) */
+    int32_t stream_push;        /* 1: push sweeps over a large frontier stream every in-pair */
+    int32_t candidates;         /* configurations timed */
+    int32_t degree_class;
+    double best_ms;             /* diffusion time under the chosen configuration (best of two) */
+    double default_ms;          /* and under the default one */
+} im_tuning;
+
+im_status im_autotune(im_ctx *ctx, const im_graph *graph, const im_params *params, im_tuning *out);
 
 /* Enables (1) or disables (0) per-launch CUDA-event timing of the propagation kernel, reported in im_stats. */
 im_status im_ctx_set_timing(im_ctx *ctx, int enable);
@@ -169,6 +210,52 @@ im_status im_sketch_info(im_ctx *ctx, const im_sketch *sketch, int64_t *sweeps, 
                          int64_t *frontier_log, int64_t log_cap);
 
 im_status im_sketch_destroy(im_sketch *sketch);
+
+/*
+ * Export and import of a built sketch, so that one build serves later runs with the same (graph, R, seed, eps_c,
+ * max_sweeps) outside a server (Section 3's sketch is a pure function of them).  The exported bytes are an
+ * im_sketch_header, then the R sampling words X_r and the R initialisation words Y_r (uint32 each), then the n*R
+ * registers, row-major.  The header carries the parameters, the diffusion's sweep and visit counts, and a 64-bit
+ * fingerprint of the graph (its edges and per-edge thresholds) that an import must match.
+ */
+#define IM_SKETCH_MAGIC 0x314354454B534D49ull /* the bytes "IMSKETC1" */
+typedef struct {
+    uint64_t magic;      /* IM_SKETCH_MAGIC */
+    int64_t n, m;
+    int32_t R;
+    int32_t model;       /* im_model */
+    double p;            /* the graph's p */
+    uint64_t seed;
+    double eps_c;
+    int64_t max_sweeps;
+    int64_t sweeps;      /* sweeps of the diffusion */
+    uint64_t visits;     /* its edge-simulation visits */
+    uint64_t graph_hash;
+    int32_t undirected;
+    int32_t reserved;
+} im_sketch_header;
+
+/* Writes the sketch to host_buf (HOST pointer, capacity cap bytes) and its size to *size_out; with host_buf NULL only
+ * the size is reported.  IM_EINVAL if cap is too small. */
+im_status im_sketch_export(im_ctx *ctx, const im_sketch *sketch, void *host_buf, uint64_t cap, uint64_t *size_out);
+
+/*
+ * Recreates a sketch from exported bytes (HOST pointer, size bytes) on `graph`, which must be the graph it was built
+ * on (same n, m, model, p, undirected flag and fingerprint; IM_EINVAL otherwise).  The sampling of the graph is
+ * redone (it is deterministic) and its words must equal the exported ones.  The imported sketch answers
+ * im_estimate, im_sketch_registers and im_select_seeds_from like the original; im_sketch_info reports its sweep
+ * and visit counts but no frontier sizes (zeros).
+ */
+im_status im_sketch_import(im_ctx *ctx, const im_graph *graph, const void *host_buf, uint64_t size,
+                           im_sketch **out);
+
+/*
+ * im_select_seeds starting from a built (or imported) sketch instead of running the first diffusion: params must
+ * have the sketch's R, seed, eps_c and max_sweeps (IM_EINVAL otherwise); K, eps_g, eps_l and blocking are free.
+ * The results are those of im_select_seeds with the same graph and parameters.  The sketch is not modified.
+ */
+im_status im_select_seeds_from(im_ctx *ctx, const im_sketch *sketch, const im_params *params, int32_t *seeds_out,
+                               double *sigma_out, int32_t *rebuilds_out, im_trace *trace);
 
 /*
  * Selects K seeds with Algorithm 1: build, then K greedy steps; each step picks the argmax of the merged-sketch

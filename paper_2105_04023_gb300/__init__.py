@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _lib
-from ._lib import IM_IC_CONST, IM_PER_EDGE, IM_WC  # noqa: F401
+from ._lib import IM_BLOCK_LITERAL, IM_BLOCK_RESIDUAL, IM_IC_CONST, IM_PER_EDGE, IM_WC  # noqa: F401
 
 
 class ImError(RuntimeError):
@@ -41,6 +41,7 @@ class Graph:
     model: int = IM_IC_CONST
     p: float = 0.0
     p_edge: object = None  # float32[m] for IM_PER_EDGE
+    undirected: bool = False  # both directions of every edge stored, rows sorted
 
     def c(self) -> _lib.im_graph:
         dev = not isinstance(self.xadj, np.ndarray)
@@ -60,25 +61,28 @@ class Graph:
             assert self.xadj.is_contiguous() and self.adj.is_contiguous()
         m = int(self.adj.shape[0])
         return _lib.im_graph(n=self.n, m=m, xadj=_addr(self.xadj), adj=_addr(self.adj), model=self.model, p=self.p,
-                             p_edge=_addr(self.p_edge), memory=_lib.IM_MEM_DEVICE if dev else _lib.IM_MEM_HOST)
+                             p_edge=_addr(self.p_edge), memory=_lib.IM_MEM_DEVICE if dev else _lib.IM_MEM_HOST,
+                             undirected=1 if self.undirected else 0)
 
     @staticmethod
-    def from_synth(g, model: int, p: float = 0.0, p_edge=None, device: str | None = None) -> "Graph":
+    def from_synth(g, model: int, p: float = 0.0, p_edge=None, device: str | None = None,
+                   undirected: bool = False) -> "Graph":
         """Wraps a ``synth.graphs.Graph``; with ``device='cuda'`` the arrays are uploaded as torch tensors."""
         if device is None:
             pe = None if p_edge is None else np.ascontiguousarray(p_edge, dtype=np.float32)
             return Graph(g.n, np.ascontiguousarray(g.xadj, np.int64), np.ascontiguousarray(g.adj, np.int32), model, p,
-                         pe)
+                         pe, undirected)
         import torch
 
         pe = None if p_edge is None else torch.as_tensor(np.asarray(p_edge, np.float32), device=device)
         return Graph(g.n, torch.as_tensor(g.xadj, device=device), torch.as_tensor(g.adj, device=device), model, p,
-                     pe)
+                     pe, undirected)
 
 
 def params(R: int, K: int = 1, eps_g: float = 0.01, eps_l: float = 0.3, eps_c: float = 0.0, seed: int = 1,
-           max_sweeps: int = 0) -> _lib.im_params:
-    return _lib.im_params(R=R, K=K, eps_g=eps_g, eps_l=eps_l, eps_c=eps_c, seed=seed, max_sweeps=max_sweeps)
+           max_sweeps: int = 0, blocking: int = IM_BLOCK_RESIDUAL) -> _lib.im_params:
+    return _lib.im_params(R=R, K=K, eps_g=eps_g, eps_l=eps_l, eps_c=eps_c, seed=seed, max_sweeps=max_sweeps,
+                          blocking=blocking)
 
 
 def _sync_torch():
@@ -128,6 +132,14 @@ class Context:
         self._check(self._L.im_ctx_stats(self.h, ctypes.byref(s)))
         return {k: getattr(s, k) for k, _ in _lib.im_stats._fields_}
 
+    def im_autotune(self, graph: Graph, prm: _lib.im_params) -> dict:
+        """Times the candidate launch shapes on the graph's first diffusion and keeps the fastest for its class."""
+        _sync_torch()
+        g = graph.c()
+        t = _lib.im_tuning()
+        self._check(self._L.im_autotune(self.h, ctypes.byref(g), ctypes.byref(prm), ctypes.byref(t)))
+        return {k: getattr(t, k) for k, _ in _lib.im_tuning._fields_}
+
     # --- the C calls, same names --------------------------------------------------------------------------------
     def im_build_sketches(self, graph: Graph, prm: _lib.im_params) -> "Sketch":
         _sync_torch()
@@ -135,6 +147,39 @@ class Context:
         out = ctypes.c_void_p()
         self._check(self._L.im_build_sketches(self.h, ctypes.byref(g), ctypes.byref(prm), ctypes.byref(out)))
         return Sketch(self, out, graph.n, prm.R)
+
+    def _select_out(self, K: int, trace: bool):
+        seeds = np.zeros(K, np.int32)
+        arrs = {}
+        tr = None
+        if trace:
+            arrs = dict(seeds=np.zeros(K, np.int32), sigma=np.zeros(K, np.float64), estimate=np.zeros(K, np.float64),
+                        gsum=np.zeros(K, np.uint64), rebuilt=np.zeros(K, np.uint8))
+            tr = _lib.im_trace(**{k: v.ctypes.data for k, v in arrs.items()})
+        return seeds, arrs, tr
+
+    def im_select_seeds_from(self, sketch: "Sketch", prm: _lib.im_params, trace: bool = True) -> dict:
+        """im_select_seeds starting from a built or imported sketch (same R, seed, eps_c and max_sweeps)."""
+        _sync_torch()
+        seeds, arrs, tr = self._select_out(prm.K, trace)
+        sigma = ctypes.c_double()
+        reb = ctypes.c_int32()
+        self._check(self._L.im_select_seeds_from(self.h, sketch.h, ctypes.byref(prm), seeds.ctypes.data,
+                                                 ctypes.addressof(sigma), ctypes.addressof(reb),
+                                                 ctypes.byref(tr) if tr is not None else None))
+        out = dict(seeds=seeds, sigma_final=sigma.value, rebuilds=reb.value)
+        out.update(arrs)
+        return out
+
+    def im_sketch_import(self, graph: Graph, data: bytes) -> "Sketch":
+        """A sketch recreated from im_sketch_export's bytes on the graph it was built on."""
+        _sync_torch()
+        g = graph.c()
+        buf = np.frombuffer(data, dtype=np.uint8)
+        h = ctypes.c_void_p()
+        self._check(self._L.im_sketch_import(self.h, ctypes.byref(g), buf.ctypes.data, int(buf.size), ctypes.byref(h)))
+        R = int(np.frombuffer(data[24:28], dtype=np.int32)[0])
+        return Sketch(self, h, graph.n, R)
 
     def im_select_seeds(self, graph: Graph, prm: _lib.im_params, trace: bool = True) -> dict:
         _sync_torch()
@@ -292,6 +337,15 @@ class Sketch:
             self.close()
         except Exception:
             pass
+
+    def im_sketch_export(self) -> bytes:
+        """The sketch as bytes: an im_sketch_header, the X and Y words, then the n*R registers."""
+        size = ctypes.c_uint64()
+        self.ctx._check(self.ctx._L.im_sketch_export(self.ctx.h, self.h, None, 0, ctypes.addressof(size)))
+        buf = np.zeros(size.value, np.uint8)
+        self.ctx._check(self.ctx._L.im_sketch_export(self.ctx.h, self.h, buf.ctypes.data, size.value,
+                                                     ctypes.addressof(size)))
+        return buf.tobytes()
 
     def im_sketch_registers(self) -> np.ndarray:
         M = np.zeros((self.n, self.R), np.uint8)

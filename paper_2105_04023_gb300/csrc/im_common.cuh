@@ -59,12 +59,16 @@ struct DevCtr {
     uint32_t nchg_hc;    // entries written to chg_hc (chunks of the changed vertices with more)
     uint32_t npush_l;    // chg_list / chg_hc entries the current push sweep works on
     uint32_t npush_h;
+    uint32_t stream;     // the current push sweep streams every in-pair (its L is large)
+    uint32_t pad_s;
     uint32_t fault;      // bit 0: a bulk copy did not complete in time; bit 1: a register update kept failing;
                          // bit 2: a grid barrier of a persistent kernel was not reached in time;
                          // bit 3: a pulling sweep reached the push-only kernel
     unsigned long long chg_indeg;     // in-edges into the vertices changed in the current sweep
     unsigned long long visits;        // edge-simulation visits, running total
     unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total
+    unsigned long long pairs;         // sparse (edge, simulation) pairs the propagation kernels examined
+    unsigned long long first_bytes;   // of `bytes`, those of the first-sweep kernel
     unsigned long long sweeps_total;  // sweeps, running total
     // greedy step (Algorithm 1) --------------------------------------------------------------------------------
     unsigned long long best_key;      // max over candidates of (gain << 32 | ~v), gain = gsum - gms
@@ -106,7 +110,7 @@ struct DevProb {
     int32_t W;                 // R / 32: words per row of a bit array over simulations
     uint32_t T_const;          // IC threshold
     int32_t ic_ok;             // IC: p > 0
-    int32_t pad0;
+    int32_t undirected;        // both directions of an edge share one hash key (min, max): an undirected input
     const uint32_t *T_vert;    // WC: threshold per target vertex
     const uint32_t *T_edge;    // per-edge model: threshold per edge
     const uint8_t *ok_edge;    // per-edge model: p > 0
@@ -128,11 +132,14 @@ struct DevProb {
     const int64_t *dofs;       // m+1: dense edges before each edge
     const int32_t *pv;         // per pair: target vertex
     const uint16_t *pj;        // per pair: simulation
+    const uint8_t *pr;         // per pair: the initial rank of (target, simulation), read by the first sweep
+    const uint32_t *iop;       // per in-pair: the index of the same pair in out-CSR order
     const uint32_t *dlist;     // dense edge ids, in edge order
     // the same pairs and dense edges by target: per in-edge of the in-CSR
     const int64_t *ipofs;      // m+1: in-pairs before each in-edge
     const int64_t *idofs;      // m+1: dense in-edges before each in-edge
     const int32_t *iu;         // per in-pair: source vertex
+    const int32_t *iv;         // per in-pair: target vertex (the in-CSR row holding it), for streamed push sweeps
     const uint16_t *ij;        // per in-pair: simulation
     const int32_t *idu;        // per dense in-edge, in in-CSR order: source vertex
     const uint32_t *ide;       //   and out-CSR edge id
@@ -141,9 +148,14 @@ struct DevProb {
     const UnitD *tdesc;        // n_tasks: sweep unit of each task
     int32_t dense_min;
     uint32_t pull_sweeps;      // sweeps 0 .. pull_sweeps-1 pull into every row, later ones push
+    unsigned long long stream_min;  // a push sweep whose L has at least this many in-edges streams every in-pair
+                                    // instead of taking L's vertices one by one (~0: never)
 
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
     uint32_t *rany;            // bit per vertex: reached by S in some simulation (set at a rebuild; NULL: no search)
+    uint8_t *prb;              // residual blocking: this problem's copy of pr with the pairs of blocked (v, j) at 0
+    uint32_t *vis_done;        // n x W: the blocked bits already applied to prb
+    uint32_t *rnew;            // bit per vertex: has bits in vis not yet in vis_done (set by k_init)
     uint32_t *del[3];          // n x W: bits newly reached at the previous level, by level mod 3
     uint32_t *lstamp;          // per vertex: 1 + the last level that listed it
     int4 *T[2];                // search tasks by level parity: {first edge (lo, hi), vertex, edge count}
@@ -161,7 +173,8 @@ struct DevProb {
     uint32_t *step_gsum;
     unsigned long long *step_reached;
     uint32_t cas_limit;        // compare-and-swap tries of one register-word update before the fault flag is raised
-    uint32_t pad1;
+    int32_t literal;           // blocked registers as Algorithms 1 and 2 print them: they keep their initial rank and
+                               // are never updated (otherwise they are 0 in a rebuilt sketch)
 };
 
 // ------------------------------------------------------------------------------------------------------------
@@ -177,8 +190,14 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t x) {
     return x;
 }
 
-// Eq. 4: hash of edge (u, v) from the 64-bit key u * n + v.
-__device__ __forceinline__ uint32_t edge_hash(uint64_t u, uint64_t v, uint64_t n) {
+// Eq. 4: hash of edge (u, v) from the 64-bit key u * n + v; an undirected input hashes both directions of an edge
+// by the key of (min, max), so they are live in the same simulations.
+__device__ __forceinline__ uint32_t edge_hash(uint64_t u, uint64_t v, uint64_t n, bool undirected) {
+    if (undirected && v < u) {
+        const uint64_t t = u;
+        u = v;
+        v = t;
+    }
     const uint64_t key = u * n + v;
     return fmix32(static_cast<uint32_t>(key) ^ fmix32(static_cast<uint32_t>(key >> 32)));
 }

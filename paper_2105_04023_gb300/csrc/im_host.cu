@@ -52,6 +52,8 @@ struct im_ctx {
     bool timing = false;
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prop_ev;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> first_ev;  // the first-sweep kernel's launches
+    int64_t first_launches = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> phase_ev[4];  // sweeps, scans, searches, inits
     int64_t launches = 0;
     int64_t prop_launches = 0;
@@ -72,6 +74,10 @@ struct im_ctx {
     // IM_TEST_BARRIER_LIMIT) to make a wait run out without any fault
     // lazy (CELF) argmax for greedy steps that keep the sketch (IM_CELF=0: a full scan every step; same results)
     bool celf = true;
+    // launch shapes chosen by im_autotune per (R, degree class): (first-sweep register budget, streamed pushes)
+    std::map<std::pair<int, int>, std::pair<int, bool>> tuned;
+    // push sweeps over a large L stream every in-pair (IM_STREAM=0: always vertex by vertex; same results)
+    bool stream_push = true;
     uint32_t cas_limit = kCasLimit;
     uint32_t barrier_limit = kBarrierLimit;
 };
@@ -135,6 +141,7 @@ struct GraphDev {
     const int32_t *adj = nullptr;
     const float *p_edge = nullptr;
     int32_t model = 0;
+    int32_t undirected = 0;
     uint32_t T_const = 0;
     int32_t ic_ok = 0;
     int64_t *xadj_in = nullptr;
@@ -159,6 +166,8 @@ void launch_validate(const int64_t *xadj, const int32_t *adj, int64_t n, int64_t
                      cudaStream_t s);
 void launch_edge_thresholds(const float *p, int64_t m, uint32_t *T, uint8_t *ok, unsigned int *flags,
                             cudaStream_t s);
+void launch_validate_undirected(const int64_t *xadj, const int32_t *adj, int64_t n, unsigned int *flags,
+                                cudaStream_t s);
 }  // namespace imk
 
 namespace {
@@ -173,6 +182,8 @@ void check_params(const im_params *pr, int64_t n, bool need_k) {
         fail(IM_EINVAL, "eps_g and eps_l must be >= 0");
     if (!(pr->eps_c >= 0.0 && pr->eps_c < 1.0)) fail(IM_EINVAL, "eps_c must be in [0, 1)");
     if (pr->max_sweeps < 0) fail(IM_EINVAL, "max_sweeps must be >= 0");
+    if (pr->blocking != IM_BLOCK_RESIDUAL && pr->blocking != IM_BLOCK_LITERAL)
+        fail(IM_EINVAL, "blocking must be IM_BLOCK_RESIDUAL or IM_BLOCK_LITERAL");
 }
 
 std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
@@ -184,6 +195,7 @@ std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
     if (g->model == IM_IC_CONST && !(g->p >= 0.0 && g->p <= 1.0)) fail(IM_EINVAL, "p must be in [0, 1]");
     if (g->model == IM_PER_EDGE && g->m > 0 && !g->p_edge) fail(IM_EINVAL, "p_edge is NULL");
     if (g->memory != IM_MEM_DEVICE && g->memory != IM_MEM_HOST) fail(IM_EINVAL, "unknown memory kind");
+    if (g->undirected != 0 && g->undirected != 1) fail(IM_EINVAL, "undirected must be 0 or 1");
     cudaStream_t s = ctx->stream;
     auto G = std::make_shared<GraphDev>();
     G->mem = std::make_unique<DevMem>(s);
@@ -191,6 +203,7 @@ std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
     G->n = g->n;
     G->m = g->m;
     G->model = g->model;
+    G->undirected = g->undirected;
     const int64_t n = g->n, m = g->m;
     if (g->memory == IM_MEM_HOST) {
         if (g->xadj[0] != 0 || g->xadj[n] != m) fail(IM_EINVAL, "xadj[0] must be 0 and xadj[n] must be m");
@@ -212,16 +225,25 @@ std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
     }
     // validation on the device: xadj[0] = 0, xadj[n] = m, non-decreasing, every target in [0, n)
     // (checked before any kernel indexes memory with these values)
-    unsigned int *flags = mem.alloc<unsigned int>(4, true);
+    unsigned int *flags = mem.alloc<unsigned int>(8, true);
     launch_validate(G->xadj, G->adj, n, m, flags, s);
     ctx->launches += 1;
     {
-        unsigned int f[4] = {0, 0, 0, 0};
+        unsigned int f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         ck(cudaMemcpyAsync(f, flags, sizeof(f), cudaMemcpyDeviceToHost, s), "read flags");
         ck(cudaStreamSynchronize(s), "sync");
         if (f[0]) fail(IM_EINVAL, "xadj[0] must be 0 and xadj[n] must be m");
         if (f[1]) fail(IM_EINVAL, "xadj must be non-decreasing");
         if (f[2]) fail(IM_EINVAL, "adj holds a vertex id outside [0, n)");
+    }
+    if (g->undirected) {  // (checked only once the offsets and ids are known to be in range)
+        launch_validate_undirected(G->xadj, G->adj, n, flags, s);
+        ctx->launches += 1;
+        unsigned int f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        ck(cudaMemcpyAsync(f, flags, sizeof(f), cudaMemcpyDeviceToHost, s), "read flags");
+        ck(cudaStreamSynchronize(s), "sync");
+        if (f[4]) fail(IM_EINVAL, "an undirected graph needs every row sorted by target without repeats");
+        if (f[5]) fail(IM_EINVAL, "an undirected graph needs (v, u) for every edge (u, v)");
     }
     // in-degree, in-CSR
     int32_t *indeg = mem.alloc<int32_t>(n, true);
@@ -254,7 +276,7 @@ std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
     // in-CSR, with the split-row task holding each in-edge
     G->adj_in = mem.alloc<int32_t>(m);
     G->ein = mem.alloc<uint32_t>(m);
-    launch_transpose_fill(G->xadj, G->adj, n, cursor, G->adj_in, G->ein, s);
+    launch_transpose_fill(G->xadj, G->adj, n, m, cursor, G->adj_in, G->ein, s);
     ctx->launches += 2;
     int64_t h_tasks = 0;
     unsigned int h_flags[4] = {0, 0, 0, 0};
@@ -306,7 +328,16 @@ struct Prob {
     int64_t npairs = 0, ndense = 0;  // sparse pairs and dense edges of the sampled graph
     im_status status = IM_OK;  // failure of this problem when the engine keeps going (serving)
     std::string error;
+    int variant = 0;  // register budget of the first-sweep kernel (resident blocks per SM; 0: default)
 };
+
+// Shape class of a graph for the autotuner: floor(log2(mean out-degree)) + 1, 0 below one edge per vertex.
+int degree_class(int64_t n, int64_t m) {
+    if (m < n || n <= 0) return 0;
+    int c = 1;
+    for (int64_t d = m / n; d > 1; d >>= 1) ++c;
+    return c;
+}
 
 // Buffers of the reachability searches (the per-edge live-simulation masks they read come from the sampling).
 // The descriptor must be complete apart from its counters.
@@ -354,8 +385,10 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     d.rdesc = rdesc;
     d.tdesc = tdesc;
     if (m == 0) {
-        d.pv = d.iu = mem.alloc<int32_t>(1);
+        d.pv = d.iu = d.iv = mem.alloc<int32_t>(1);
+        d.stream_min = ~0ull;
         d.pj = d.ij = mem.alloc<uint16_t>(1);
+        d.pr = mem.alloc<uint8_t>(1);
         d.dlist = d.ide = mem.alloc<uint32_t>(1);
         d.idu = mem.alloc<int32_t>(1);
         UnitD *vd0 = mem.alloc<UnitD>(static_cast<size_t>(std::max<int64_t>(P.G->n, 1)), true);
@@ -383,12 +416,14 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     mem.release(bsums);
     int32_t *pv = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
     uint16_t *pj = mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
+    uint8_t *pr = mem.alloc<uint8_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
     uint32_t *dlist = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
-    launch_pair_fill(d, pv, pj, dlist, s);
+    launch_pair_fill(d, pv, pj, pr, dlist, s);
     launch_unit_desc(d, rdesc, tdesc, s);
     ctx->launches += 2;
     d.pv = pv;
     d.pj = pj;
+    d.pr = pr;
     d.dlist = dlist;
     P.npairs = tot[0];
     P.ndense = tot[1];
@@ -408,9 +443,21 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     d.idofs = idofs;
     int32_t *iu = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
     uint16_t *ij = mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
+    // in-pair -> out-pair index (32-bit), for residual blocking in a problem's copy of the pair ranks
+    uint32_t *iop = tot[0] < (int64_t(1) << 32)
+                        ? mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)))
+                        : nullptr;
     int32_t *idu = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
     uint32_t *ide = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
-    launch_inpair_fill(d, iu, ij, idu, ide, s);
+    launch_inpair_fill(d, iu, ij, iop, idu, ide, s);
+    d.iop = iop;
+    int32_t *iv = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
+    launch_inpair_targets(d, iv, s);
+    ctx->launches += 1;
+    d.iv = iv;
+    // push sweeps over a large L stream every in-pair (only without dense edges, which the stream leaves out)
+    d.stream_min = (tot[1] == 0 && ctx->stream_push) ? static_cast<unsigned long long>(std::max<int64_t>(m / 2, 1))
+                                                      : ~0ull;
     UnitD *vdesc = mem.alloc<UnitD>(static_cast<size_t>(std::max<int64_t>(P.G->n, 1)));
     launch_vertex_desc(d, vdesc, s);
     ctx->launches += 2;
@@ -432,10 +479,14 @@ void copy_sample_fields(DevProb &d, const DevProb &src) {
     d.tdesc = src.tdesc;
     d.pv = src.pv;
     d.pj = src.pj;
+    d.pr = src.pr;
     d.dlist = src.dlist;
     d.ipofs = src.ipofs;
     d.idofs = src.idofs;
     d.iu = src.iu;
+    d.iv = src.iv;
+    d.iop = src.iop;
+    d.stream_min = src.stream_min;
     d.ij = src.ij;
     d.idu = src.idu;
     d.ide = src.ide;
@@ -490,6 +541,8 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     d.T_edge = g.T_edge;
     d.ok_edge = g.ok_edge;
     d.cas_limit = ctx->cas_limit;
+    d.undirected = g.undirected;
+    d.literal = prm.blocking == IM_BLOCK_LITERAL ? 1 : 0;
     uint32_t *X = mem.alloc<uint32_t>(R);
     uint32_t *Y = mem.alloc<uint32_t>(R);
     launch_words(prm.seed, R, X, Y, ctx->stream);
@@ -524,9 +577,23 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     } else {
         sample_edges(ctx, *P);
     }
+    // the autotuner's choice for this shape class, if any (the stream needs a sampled graph without dense edges)
+    auto tn = ctx->tuned.find({R, degree_class(n, g.m)});
+    if (tn != ctx->tuned.end()) {
+        P->variant = tn->second.first;
+        if (!tn->second.second) d.stream_min = ~0ull;
+    }
     if (greedy) {
         alloc_bfs(*P);
         d.gst = mem.alloc<uint32_t>(static_cast<size_t>(n));
+        // residual blocking applied to a copy of the pair ranks at each rebuild (the first sweep then tests nothing)
+        if (d.iop && prm.blocking == IM_BLOCK_RESIDUAL && P->npairs > 0) {
+            d.prb = mem.alloc<uint8_t>(static_cast<size_t>(P->npairs));
+            ck(cudaMemcpyAsync(d.prb, d.pr, static_cast<size_t>(P->npairs), cudaMemcpyDeviceToDevice, ctx->stream),
+               "copy pair ranks");
+            d.vis_done = mem.alloc<uint32_t>(static_cast<size_t>(n) * (R / 32), true);
+            d.rnew = mem.alloc<uint32_t>(words, true);
+        }
         d.step_seed = mem.alloc<uint32_t>(prm.K);
         d.step_gsum = mem.alloc<uint32_t>(prm.K);
     }
@@ -611,7 +678,7 @@ struct Engine {
 
     // One sweep's propagation launches (k_prop, then for a sweep that pulls into every row, k_combine for the split
     // rows), optionally between two events.
-    void timed_prop(const std::vector<std::pair<int, List>> &byR, bool combine) {
+    void timed_prop(const std::vector<std::pair<int, List>> &byR, const std::vector<int> &variants, bool combine) {
         cudaStream_t s = ctx->stream;
         cudaEvent_t a = nullptr, b = nullptr;
         if (ctx->timing) {
@@ -620,8 +687,24 @@ struct Engine {
             ck(cudaEventRecord(a, s), "event");
         }
         int64_t nl = 0;
-        for (auto &rl : byR)
-            nl += launch_prop(rl.first, d_probs, dptr(rl.second), rl.second.count, combine, ctx->pull_sweeps > 1, s);
+        if (combine) {  // the first-sweep kernel, timed on its own as well
+            cudaEvent_t fa = nullptr, fb = nullptr;
+            if (ctx->timing) {
+                fa = get_event();
+                fb = get_event();
+                ck(cudaEventRecord(fa, s), "event");
+            }
+            for (size_t i = 0; i < byR.size(); ++i)
+                nl += launch_first(byR[i].first, d_probs, dptr(byR[i].second), byR[i].second.count, variants[i], s);
+            if (ctx->timing) {
+                ck(cudaEventRecord(fb, s), "event");
+                ctx->first_ev.emplace_back(fa, fb);
+            }
+            ctx->first_launches += static_cast<int64_t>(byR.size());
+        }
+        for (size_t i = 0; i < byR.size(); ++i)
+            nl += launch_prop(byR[i].first, d_probs, dptr(byR[i].second), byR[i].second.count, combine,
+                              ctx->pull_sweeps > 1, s);
         if (combine) {
             for (auto &rl : byR) launch_combine(rl.first, d_probs, dptr(rl.second), rl.second.count, s);
             nl += 2 * static_cast<int64_t>(byR.size());  // the two combine kernels
@@ -665,17 +748,21 @@ struct Engine {
         if (ids.empty()) return;
         cudaStream_t s = ctx->stream;
         std::vector<std::pair<int, List>> byR;
+        std::vector<int> variants;  // the first-sweep kernel's shape: that of the group's first problem
         for (int R : {64, 128, 256, 512, 1024}) {
             std::vector<int32_t> sub;
             for (int32_t i : ids)
                 if (probs[i]->prm.R == R) sub.push_back(i);
-            if (!sub.empty()) byR.emplace_back(R, add_list(sub));
+            if (!sub.empty()) {
+                byR.emplace_back(R, add_list(sub));
+                variants.push_back(probs[sub[0]]->variant);
+            }
         }
         const List all = add_list(ids);
-        pending.push_back([this, byR, all, chunk, first_full, s]() {
+        pending.push_back([this, byR, variants, all, chunk, first_full, s]() {
             phase(0, [&]() {
                 for (int c = 0; c < chunk; ++c) {
-                    timed_prop(byR, first_full && c < ctx->pull_sweeps);
+                    timed_prop(byR, variants, first_full && c < ctx->pull_sweeps);
                     launch_frontier(d_probs, dptr(all), all.count, ctx->d_gbar, s);
                     ctx->launches += 1;
                 }
@@ -837,8 +924,9 @@ struct Engine {
         if (!init.empty()) {
             const List l = add_list(init);
             pending.push_back([this, l, s]() {
-                phase(3, [&]() { launch_init(d_probs, dptr(l), l.count, s); });
-                ctx->launches += 1;
+                int nl = 0;
+                phase(3, [&]() { nl = launch_init(d_probs, dptr(l), l.count, s); });
+                ctx->launches += nl;
             });
         }
         enqueue_sweeps(sweep, ctx->sweep_chunk, !init.empty());
@@ -914,6 +1002,12 @@ void begin_call(im_ctx *ctx) {
         ctx->ev_free.push_back(pe.second);
     }
     ctx->prop_ev.clear();
+    for (auto &pe : ctx->first_ev) {
+        ctx->ev_free.push_back(pe.first);
+        ctx->ev_free.push_back(pe.second);
+    }
+    ctx->first_ev.clear();
+    ctx->first_launches = 0;
     for (auto &v : ctx->phase_ev) {
         for (auto &pe : v) {
             ctx->ev_free.push_back(pe.first);
@@ -928,6 +1022,8 @@ void end_call(im_ctx *ctx, const std::vector<Prob *> &probs, cudaEvent_t t0, cud
     for (Prob *P : probs) {
         st.visits += P->last.visits;
         st.prop_bytes += P->last.bytes;
+        st.live_pairs += P->last.pairs;
+        st.first_bytes += P->last.first_bytes;
         st.sweeps += static_cast<int64_t>(P->last.sweeps_total);
         st.bfs_levels += static_cast<int64_t>(P->last.levels_total);
         st.builds += P->builds;
@@ -944,6 +1040,14 @@ void end_call(im_ctx *ctx, const std::vector<Prob *> &probs, cudaEvent_t t0, cud
         pm += x;
     }
     st.prop_ms = pm;
+    double fm = 0.0;
+    for (auto &pe : ctx->first_ev) {
+        float x = 0.f;
+        ck(cudaEventElapsedTime(&x, pe.first, pe.second), "elapsed");
+        fm += x;
+    }
+    st.first_ms = fm;
+    st.first_launches = ctx->first_launches;
     double ph[4] = {0, 0, 0, 0};
     for (int k = 0; k < 4; ++k)
         for (auto &pe : ctx->phase_ev[k]) {
@@ -981,6 +1085,7 @@ struct CallTimer {
 struct im_sketch {
     std::unique_ptr<Prob> P;
     im_ctx *ctx = nullptr;
+    double p = 0.0;  // the graph's p (recorded in exports)
 };
 
 // Context accessors for the allocation-free entry point (im_static.cu).
@@ -1031,6 +1136,7 @@ im_status im_ctx_create(int device, void *cuda_stream, im_ctx **out) {
     if (const char *v = std::getenv("IM_PERSISTENT")) ctx->persistent = std::atoi(v) != 0;
     if (const char *v = std::getenv("IM_PULL_SWEEPS")) ctx->pull_sweeps = std::max(1, std::min(8, std::atoi(v)));
     if (const char *v = std::getenv("IM_CELF")) ctx->celf = std::atoi(v) != 0;
+    if (const char *v = std::getenv("IM_STREAM")) ctx->stream_push = std::atoi(v) != 0;
     if (const char *v = std::getenv("IM_TEST_CAS_LIMIT")) ctx->cas_limit = static_cast<uint32_t>(std::atol(v));
     if (const char *v = std::getenv("IM_TEST_BARRIER_LIMIT"))
         ctx->barrier_limit = static_cast<uint32_t>(std::atol(v));
@@ -1095,6 +1201,7 @@ im_status im_build_sketches(im_ctx *ctx, const im_graph *graph, const im_params 
         auto G = prepare_graph(ctx, graph);
         auto sk = std::make_unique<im_sketch>();
         sk->ctx = ctx;
+        sk->p = graph->p;
         sk->P = make_prob(ctx, G, *params, false);
         Engine eng(ctx, {sk->P.get()});
         eng.run();
@@ -1142,6 +1249,7 @@ im_status im_influence_mc(im_ctx *ctx, const im_graph *graph, const int32_t *see
     return guarded(ctx, [&]() {
         if (!graph || !seeds || !sigma_out) fail(IM_EINVAL, "graph / seeds / sigma_out is NULL");
         if (k < 1) fail(IM_EINVAL, "k must be >= 1");
+        if (graph->undirected) fail(IM_EINVAL, "the Monte-Carlo scorer draws per directed edge: no undirected input");
         if (nsamples < 64 || nsamples % 64 != 0 || nsamples > (int64_t{1} << 24))
             fail(IM_EINVAL, "nsamples must be a multiple of 64 in [64, 2^24]");
         for (int32_t i = 0; i < k; ++i)
@@ -1334,6 +1442,7 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     b += r(4 * n * W) * 4 + r(4 * words) * 2 + r(4 * n) * 4;  // reach and delta bits, seed-set and reached-vertex
                                                                  // bits, stamps, frontiers
     b += r(4 * n);                                           // bounds of the lazy argmax
+    b += r(4 * n * W) + r(4 * words);                        // blocked bits applied to the pair ranks, new ones
     b += r(sizeof(int4) * (n + static_cast<uint64_t>(g.m) / kBfsTaskEdgesMin + 1)) * 2;  // search tasks
     const uint64_t m1 = std::max<uint64_t>(static_cast<uint64_t>(g.m), 1);
     b += r(4 * W * m1);                                      // live-simulation masks of the edges
@@ -1342,7 +1451,8 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     // pairs: at most dense_min per edge (6 bytes each), dense edges 4 bytes; the counts and scan sums of the
     // preparation are freed before the pairs are allocated, and are smaller
     const uint64_t pmax = m1 * static_cast<uint64_t>(dense_min_for(prm.R));
-    b += (r(4 * pmax) + r(2 * pmax)) * 2 + r(4 * m1) * 3;  // pairs both ways, dense edges (ids; u and e)
+    b += (r(4 * pmax) + r(2 * pmax)) * 2 + r(pmax) * 2 + r(4 * pmax) * 2 + r(4 * m1) * 3;  // pairs both ways with
+        // the out-pairs' ranks (and the query's copy), the in-pairs' targets and out-pair indices, dense edges
     b += r(sizeof(UnitD) * std::max<uint64_t>(n, 1));       // push-unit descriptors
     b += r(4 * static_cast<uint64_t>(prm.K)) * 2;            // step records
     return b;
@@ -1469,6 +1579,26 @@ static void select_many(im_ctx *ctx, int32_t nq, const im_graph *graphs, const i
     eng.run();
 }
 
+static void write_select_outputs(const Prob &P, int K, int32_t *seeds_out, double *sigma_out, int32_t *rebuilds_out,
+                                 im_trace *trace) {
+    std::copy(P.seeds.begin(), P.seeds.end(), seeds_out);
+    if (sigma_out) *sigma_out = P.sigma.back();
+    if (rebuilds_out) {
+        int32_t r = 0;
+        for (uint8_t b : P.rebuilt) r += b;
+        *rebuilds_out = r;
+    }
+    if (trace) {
+        for (int k = 0; k < K; ++k) {
+            if (trace->seeds) trace->seeds[k] = P.seeds[k];
+            if (trace->sigma) trace->sigma[k] = P.sigma[k];
+            if (trace->estimate) trace->estimate[k] = P.est[k];
+            if (trace->gsum) trace->gsum[k] = P.gsum[k];
+            if (trace->rebuilt) trace->rebuilt[k] = P.rebuilt[k];
+        }
+    }
+}
+
 im_status im_select_seeds(im_ctx *ctx, const im_graph *graph, const im_params *params, int32_t *seeds_out,
                           double *sigma_out, int32_t *rebuilds_out, im_trace *trace) {
     if (!ctx) return IM_EINVAL;
@@ -1482,23 +1612,229 @@ im_status im_select_seeds(im_ctx *ctx, const im_graph *graph, const im_params *p
         Prob &P = *probs[0];
         std::vector<Prob *> raw{&P};
         end_call(ctx, raw, tm.a, tm.b);
-        const int K = params->K;
-        std::copy(P.seeds.begin(), P.seeds.end(), seeds_out);
-        if (sigma_out) *sigma_out = P.sigma.back();
-        if (rebuilds_out) {
-            int32_t r = 0;
-            for (uint8_t b : P.rebuilt) r += b;
-            *rebuilds_out = r;
-        }
-        if (trace) {
-            for (int k = 0; k < K; ++k) {
-                if (trace->seeds) trace->seeds[k] = P.seeds[k];
-                if (trace->sigma) trace->sigma[k] = P.sigma[k];
-                if (trace->estimate) trace->estimate[k] = P.est[k];
-                if (trace->gsum) trace->gsum[k] = P.gsum[k];
-                if (trace->rebuilt) trace->rebuilt[k] = P.rebuilt[k];
+        write_select_outputs(P, params->K, seeds_out, sigma_out, rebuilds_out, trace);
+    });
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Autotuning of launch shapes: every candidate runs the same first diffusion (bit-identical results, checked) and
+// the fastest is kept for the graph's (R, degree class).
+
+im_status im_autotune(im_ctx *ctx, const im_graph *graph, const im_params *params, im_tuning *out) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!graph || !params) fail(IM_EINVAL, "graph / params is NULL");
+        check_params(params, graph->n, false);
+        begin_call(ctx);
+        auto G = prepare_graph(ctx, graph);
+        const std::pair<int, int> key{params->R, degree_class(G->n, G->m)};
+        ctx->tuned.erase(key);  // the base problem samples with the defaults
+        auto base = make_prob(ctx, G, *params, false);
+        const bool can_stream = base->dp.stream_min != ~0ull;
+        struct Cand {
+            int variant;
+            bool stream;
+            double ms;
+        };
+        std::vector<Cand> cands;
+        for (int v : {4, 3, 6})
+            for (int st = can_stream ? 1 : 0; st >= 0; --st) cands.push_back({v, st != 0, 1e30});
+        const size_t regs = static_cast<size_t>(G->n) * params->R;
+        DevMem tmp(ctx->stream);
+        unsigned long long *d_sum = tmp.alloc<unsigned long long>(1);
+        bool have_ref = false;
+        DevCtr ref{};
+        unsigned long long ref_sum = 0;
+        for (int trial = 0; trial < 2; ++trial)
+            for (Cand &c : cands) {
+                auto P = make_prob(ctx, G, *params, false, base.get());
+                P->variant = c.variant;
+                P->dp.stream_min = c.stream ? base->dp.stream_min : ~0ull;
+                Engine eng(ctx, {P.get()});
+                cudaEvent_t a = eng.get_event(), b = eng.get_event();
+                ck(cudaEventRecord(a, ctx->stream), "event");
+                eng.run();
+                ck(cudaEventRecord(b, ctx->stream), "event");
+                ck(cudaEventSynchronize(b), "event");
+                float ms = 0.f;
+                ck(cudaEventElapsedTime(&ms, a, b), "elapsed");
+                ctx->ev_free.push_back(a);
+                ctx->ev_free.push_back(b);
+                c.ms = std::min(c.ms, static_cast<double>(ms));
+                ck(cudaMemsetAsync(d_sum, 0, sizeof(unsigned long long), ctx->stream), "memset");
+                launch_checksum(P->last.res_par ? P->dp.M1 : P->dp.M0, regs, d_sum, ctx->stream);
+                unsigned long long sum = 0;
+                ck(cudaMemcpyAsync(&sum, d_sum, sizeof(sum), cudaMemcpyDeviceToHost, ctx->stream), "read sum");
+                ck(cudaStreamSynchronize(ctx->stream), "sync");
+                if (P->last.timeout) fail(IM_ETIMEOUT, "diffusion exceeded max_sweeps");
+                if (!have_ref) {
+                    have_ref = true;
+                    ref = P->last;
+                    ref_sum = sum;
+                } else if (sum != ref_sum || P->last.sweeps_total != ref.sweeps_total || P->last.visits != ref.visits) {
+                    fail(IM_ECUDA, "autotuning candidates reached different registers");
+                }
             }
+        const Cand *best = &cands[0];
+        for (const Cand &c : cands)
+            if (c.ms < best->ms) best = &c;
+        ctx->tuned[key] = {best->variant, best->stream};
+        if (out) {
+            out->first_sweep_blocks = best->variant;
+            out->stream_push = best->stream ? 1 : 0;
+            out->candidates = static_cast<int32_t>(cands.size());
+            out->degree_class = key.second;
+            out->best_ms = best->ms;
+            out->default_ms = cands[0].ms;
         }
+    });
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Sketch export / import and selections that start from a built sketch.
+
+namespace {
+
+uint64_t graph_fingerprint(im_ctx *ctx, const GraphDev &g) {
+    DevMem tmp(ctx->stream);
+    unsigned long long *d = tmp.alloc<unsigned long long>(1, true);
+    launch_graph_hash(g.xadj, g.adj, g.n, g.T_edge, d, ctx->stream);
+    ctx->launches += 1;
+    unsigned long long h = 0;
+    ck(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "read fingerprint");
+    ck(cudaStreamSynchronize(ctx->stream), "sync");
+    return h;
+}
+
+uint64_t export_size(int64_t n, int32_t R) {
+    return sizeof(im_sketch_header) + 8ull * static_cast<uint64_t>(R) + static_cast<uint64_t>(n) * R;
+}
+
+}  // namespace
+
+im_status im_sketch_export(im_ctx *ctx, const im_sketch *sketch, void *host_buf, uint64_t cap, uint64_t *size_out) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!sketch || !size_out) fail(IM_EINVAL, "sketch / size_out is NULL");
+        const Prob &P = *sketch->P;
+        const int64_t n = P.G->n;
+        const int32_t R = P.prm.R;
+        const uint64_t size = export_size(n, R);
+        *size_out = size;
+        if (!host_buf) return;
+        if (cap < size) fail(IM_EINVAL, "the buffer is smaller than the exported sketch");
+        begin_call(ctx);
+        im_sketch_header h{};
+        h.magic = IM_SKETCH_MAGIC;
+        h.n = n;
+        h.m = P.G->m;
+        h.R = R;
+        h.model = P.G->model;
+        h.p = sketch->p;
+        h.seed = P.prm.seed;
+        h.eps_c = P.prm.eps_c;
+        h.max_sweeps = P.prm.max_sweeps;
+        h.sweeps = static_cast<int64_t>(P.last.sweeps_total);
+        h.visits = P.last.visits;
+        h.graph_hash = graph_fingerprint(ctx, *P.G);
+        h.undirected = P.G->undirected;
+        uint8_t *out = static_cast<uint8_t *>(host_buf);
+        std::memcpy(out, &h, sizeof(h));
+        cudaStream_t s = ctx->stream;
+        ck(cudaMemcpyAsync(out + sizeof(h), P.dp.X, 4ull * R, cudaMemcpyDeviceToHost, s), "copy X");
+        ck(cudaMemcpyAsync(out + sizeof(h) + 4ull * R, P.dp.Y, 4ull * R, cudaMemcpyDeviceToHost, s), "copy Y");
+        ck(cudaMemcpyAsync(out + sizeof(h) + 8ull * R, P.last.res_par ? P.dp.M1 : P.dp.M0,
+                           static_cast<size_t>(n) * R, cudaMemcpyDeviceToHost, s),
+           "copy registers");
+        ck(cudaStreamSynchronize(s), "sync");
+    });
+}
+
+im_status im_sketch_import(im_ctx *ctx, const im_graph *graph, const void *host_buf, uint64_t size,
+                           im_sketch **out) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!graph || !host_buf || !out) fail(IM_EINVAL, "graph / host_buf / out is NULL");
+        if (size < sizeof(im_sketch_header)) fail(IM_EINVAL, "too few bytes for a sketch");
+        im_sketch_header h;
+        std::memcpy(&h, host_buf, sizeof(h));
+        if (h.magic != IM_SKETCH_MAGIC) fail(IM_EINVAL, "not an exported sketch");
+        im_params prm{};
+        prm.R = h.R;
+        prm.K = 1;
+        prm.eps_g = 0.01;
+        prm.eps_l = 0.3;
+        prm.eps_c = h.eps_c;
+        prm.seed = h.seed;
+        prm.max_sweeps = h.max_sweeps;
+        check_params(&prm, graph->n, false);
+        if (h.n != graph->n || h.m != graph->m) fail(IM_EINVAL, "the sketch was built on another graph (n, m)");
+        if (size != export_size(h.n, h.R)) fail(IM_EINVAL, "the byte count does not match the header");
+        if (h.model != graph->model || h.undirected != graph->undirected ||
+            (graph->model == IM_IC_CONST && std::memcmp(&h.p, &graph->p, sizeof(double)) != 0))
+            fail(IM_EINVAL, "the sketch was built with another diffusion model, probability or edge kind");
+        begin_call(ctx);
+        CallTimer tm(ctx);
+        auto G = prepare_graph(ctx, graph);
+        if (graph_fingerprint(ctx, *G) != h.graph_hash) fail(IM_EINVAL, "the sketch was built on another graph");
+        auto sk = std::make_unique<im_sketch>();
+        sk->ctx = ctx;
+        sk->p = graph->p;
+        sk->P = make_prob(ctx, G, prm, false);
+        Prob &P = *sk->P;
+        cudaStream_t s = ctx->stream;
+        const uint8_t *in = static_cast<const uint8_t *>(host_buf);
+        std::vector<uint32_t> xy(2 * static_cast<size_t>(h.R));
+        ck(cudaMemcpyAsync(xy.data(), P.dp.X, 4ull * h.R, cudaMemcpyDeviceToHost, s), "read X");
+        ck(cudaMemcpyAsync(xy.data() + h.R, P.dp.Y, 4ull * h.R, cudaMemcpyDeviceToHost, s), "read Y");
+        ck(cudaMemcpyAsync(P.dp.M0, in + sizeof(h) + 8ull * h.R, static_cast<size_t>(h.n) * h.R,
+                           cudaMemcpyHostToDevice, s),
+           "copy registers");
+        ck(cudaStreamSynchronize(s), "sync");
+        if (std::memcmp(xy.data(), in + sizeof(h), 8ull * h.R) != 0)
+            fail(IM_EINVAL, "the sketch's simulation words differ from this library's for its seed");
+        P.last = DevCtr{};
+        P.last.done = 1;
+        P.last.res_par = 0;
+        P.last.sweeps_total = static_cast<unsigned long long>(h.sweeps);
+        P.last.visits = h.visits;
+        P.builds = 1;
+        tm.stop();
+        end_call(ctx, {&P}, tm.a, tm.b);
+        *out = sk.release();
+    });
+}
+
+im_status im_select_seeds_from(im_ctx *ctx, const im_sketch *sketch, const im_params *params, int32_t *seeds_out,
+                               double *sigma_out, int32_t *rebuilds_out, im_trace *trace) {
+    if (!ctx) return IM_EINVAL;
+    return guarded(ctx, [&]() {
+        if (!sketch || !params || !seeds_out) fail(IM_EINVAL, "sketch / params / seeds_out is NULL");
+        const Prob &S = *sketch->P;
+        check_params(params, S.G->n, true);
+        if (params->R != S.prm.R || params->seed != S.prm.seed || params->eps_c != S.prm.eps_c ||
+            params->max_sweeps != S.prm.max_sweeps)
+            fail(IM_EINVAL, "params must have the sketch's R, seed, eps_c and max_sweeps");
+        begin_call(ctx);
+        CallTimer tm(ctx);
+        // share the sketch's sampled graph, start from a copy of its registers at the first greedy step
+        auto P = make_prob(ctx, S.G, *params, true, &S);
+        ck(cudaMemcpyAsync(S.last.res_par ? P->dp.M1 : P->dp.M0, S.last.res_par ? S.dp.M1 : S.dp.M0,
+                           static_cast<size_t>(S.G->n) * S.prm.R, cudaMemcpyDeviceToDevice, ctx->stream),
+           "copy registers");
+        std::vector<DevCtr> c0(1);
+        c0[0].res_par = S.last.res_par;
+        c0[0].done = 1;
+        c0[0].sweeps_total = S.last.sweeps_total;
+        c0[0].visits = S.last.visits;
+        c0[0].bytes = S.last.bytes;
+        Engine eng(ctx, {P.get()}, &c0);
+        P->phase = Prob::kScan;
+        P->builds = 1;
+        eng.run();
+        tm.stop();
+        end_call(ctx, {P.get()}, tm.a, tm.b);
+        write_select_outputs(*P, params->K, seeds_out, sigma_out, rebuilds_out, trace);
     });
 }
 

@@ -82,11 +82,13 @@ __device__ __forceinline__ uint64_t in_degree(const DevProb &P, int64_t v) {
 
 struct Stats {
     unsigned long long bytes = 0;
+    unsigned long long pairs = 0;  // sparse (edge, simulation) pairs examined
 };
 
 __device__ __forceinline__ void flush_stats(DevCtr *C, Stats &st, int lane) {
     if (lane == 0) {
         if (st.bytes) atomicAdd(&C->bytes, st.bytes);
+        if (st.pairs) atomicAdd(&C->pairs, st.pairs);
     }
     st = Stats();
 }
@@ -223,12 +225,27 @@ __device__ __forceinline__ uint4 init_chunk_sw(const uint32_t *Ysw, uint32_t hv,
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Initial register of (v, j), 0 if v is in R_{G_j}(S).  Ysw: the Y words staged with sw_slot(j, 0).
+// Initial register of (v, j), 0 if v is in R_{G_j}(S) (unless literal blocking keeps it).  Ysw: the Y words
+// staged with sw_slot(j, 0).
 __device__ __forceinline__ uint32_t init_reg(const DevProb &P, const uint32_t *Ysw, int32_t v, uint32_t j) {
     const uint32_t r = __clz(vertex_hash(static_cast<uint32_t>(v)) ^ Ysw[sw_slot(j, 0)]);
-    if (P.rany && test_bit(P.rany, v) && ((__ldg(&P.vis[static_cast<size_t>(v) * P.W + (j >> 5)]) >> (j & 31)) & 1u))
+    if (!P.literal && P.rany && test_bit(P.rany, v) &&
+        ((__ldg(&P.vis[static_cast<size_t>(v) * P.W + (j >> 5)]) >> (j & 31)) & 1u))
         return 0u;
     return r;
+}
+
+// Blocked bits of an initial row: those of v under residual blocking (its registers there are 0), none under
+// literal blocking (a blocked register keeps its rank).
+__device__ __forceinline__ uint32_t init_blocked16(const DevProb &P, int64_t v, int ch) {
+    return P.literal ? 0u : blocked16(P, v, ch);
+}
+
+// Whether (u, j) is blocked under literal blocking, where such a register is never updated.  Under residual
+// blocking nothing needs this test: a blocked (u, j) has only blocked live successors, whose registers are 0.
+__device__ __forceinline__ bool literal_blocked(const DevProb &P, int64_t u, uint32_t j) {
+    return P.literal && P.rany && test_bit(P.rany, u) &&
+           ((__ldg(&P.vis[static_cast<size_t>(u) * P.W + (j >> 5)]) >> (j & 31)) & 1u);
 }
 
 // Dense edges dlist[d0, d1) of the tile's unit (edges live in many simulations), merged with whole register rows:
@@ -238,7 +255,8 @@ __device__ __forceinline__ uint32_t init_reg(const DevProb &P, const uint32_t *Y
 template <int R, bool INIT>
 __device__ __forceinline__ uint32_t dense_tile(const DevProb &P, int64_t d0, int64_t d1, bool allL,
                                                const uint32_t *__restrict__ Lcur, const uint8_t *__restrict__ Mcur,
-                                               const uint32_t *Ys, uint32_t (&acc)[Geo<R>::CPL][4], int li) {
+                                               const uint32_t *Ys, bool chk, uint32_t (&acc)[Geo<R>::CPL][4],
+                                               int li) {
     using Gm = Geo<R>;
     constexpr int W = R / 32;
     uint32_t taken = 0;
@@ -261,7 +279,8 @@ __device__ __forceinline__ uint32_t dense_tile(const DevProb &P, int64_t d0, int
             for (int c = 0; c < Gm::CPL; ++c) {
                 const int ch = li + Gm::G * c;  // 16-simulation chunk: half (ch & 1) of mask word ch / 2
                 if (INIT)
-                    row[r][c] = in[r] ? init_chunk_sw(Ys, hv, ch, blocked16(P, v, ch)) : make_uint4(0, 0, 0, 0);
+                    row[r][c] = in[r] ? init_chunk_sw(Ys, hv, ch, chk ? init_blocked16(P, v, ch) : 0u)
+                                      : make_uint4(0, 0, 0, 0);
                 else
                     row[r][c] = in[r] ? __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(v) * R) + ch)
                                       : make_uint4(0, 0, 0, 0);
@@ -326,6 +345,43 @@ __device__ __forceinline__ uint32_t sparse_tile(const DevProb &P, int64_t p0, in
     return taken;
 }
 
+// The first sweep's sparse pairs [p0, p1): each pair's candidate is the initial rank of (v, j), kept per pair since
+// sampling (pr, or the problem's copy prb whose blocked pairs k_block_pairs set to 0), so only (j, rank) are read;
+// a rank of 0 changes nothing.  Without prb, a rebuild (chk) reads the pair's v too and a blocked (v, j) gives 0
+// (residual blocking; literal blocking keeps the rank).
+template <int R>
+__device__ __forceinline__ void sparse_tile_init(const DevProb &P, int64_t p0, int64_t p1, bool chk,
+                                                 uint32_t *acc32, int li) {
+    constexpr int G = Geo<R>::G;
+    const uint32_t g = static_cast<uint32_t>((threadIdx.x & 31) / G);
+    // the problem's own ranks, with blocked pairs already 0, when it keeps them; else the sampled graph's, tested
+    const uint8_t *rk = P.prb ? P.prb : P.pr;
+    const bool test = chk && !P.literal && !P.prb;
+    for (int64_t p = p0 + li; p < p1; p += 4 * G) {
+        uint32_t j[4], x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t q = p + G * k;
+            const bool ok = q < p1;
+            j[k] = ok ? __ldg(&P.pj[q]) : 0u;
+            x[k] = ok ? __ldg(&rk[q]) : 0u;
+        }
+        if (test) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (x[k]) {
+                    const int32_t v = __ldg(&P.pv[p + G * k]);
+                    if (test_bit(P.rany, v) &&
+                        ((__ldg(&P.vis[static_cast<size_t>(v) * P.W + (j[k] >> 5)]) >> (j[k] & 31)) & 1u))
+                        x[k] = 0;
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (x[k]) atomicMax(&acc32[sw_slot(j[k], g)], x[k]);
+    }
+}
+
 // Adds the tile's sparse accumulators into acc and clears them.
 template <int R>
 __device__ __forceinline__ void fold_tile(uint32_t (&acc)[Geo<R>::CPL][4], uint32_t *acc32, unsigned tm, int li) {
@@ -346,6 +402,18 @@ __device__ __forceinline__ void fold_tile(uint32_t (&acc)[Geo<R>::CPL][4], uint3
     uint4 *z = reinterpret_cast<uint4 *>(acc32);
     for (int k = li; k < R / 4; k += Gm::G) z[k] = make_uint4(0, 0, 0, 0);
     __syncwarp(tm);
+}
+
+// Literal blocking: a blocked (u, j) is never updated, so the merged registers lose u's blocked simulations.
+template <int R>
+__device__ __forceinline__ void drop_blocked(const DevProb &P, int64_t u, uint32_t (&acc)[Geo<R>::CPL][4], int li) {
+    if (!P.literal || !P.rany || !test_bit(P.rany, u)) return;
+#pragma unroll
+    for (int c = 0; c < Geo<R>::CPL; ++c) {
+        const uint32_t blk = blocked16(P, u, li + Geo<R>::G * c);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[c][w] &= ~nibble_bytes((blk >> (4 * w)) & 0xFu);
+    }
 }
 
 // Row u's new registers max(M_u, acc) for a tile (every lane holds its chunks of acc and of the row's own
@@ -373,13 +441,17 @@ __device__ __forceinline__ void finalize_tile(const DevProb &P, int64_t u, uint3
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
     }
-    if (Mother) {
+    if (Mother) {  // the first sweep also records which registers it raised, for the push of the next sweep
         uint4 *dst = reinterpret_cast<uint4 *>(Mother + static_cast<size_t>(u) * R);
 #pragma unroll
-        for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
+        for (int c = 0; c < Gm::CPL; ++c) {
+            dst[li + Gm::G * c] = nw[c];
+            P.dmask[static_cast<size_t>(u) * Gm::CH + li + Gm::G * c] =
+                static_cast<uint16_t>(ne_bits16(nw[c], own[c]));
+        }
     }
     if (changed && li == 0) set_bit(Lnext, u);
-    st.bytes += Mother ? 2 * R : R + ((changed || sync) ? R : 0);
+    st.bytes += Mother ? 2 * R + R / 8 : R + ((changed || sync) ? R : 0);
 }
 
 template <int R>
@@ -409,10 +481,14 @@ __device__ __forceinline__ void finalize_row_r(const DevProb &P, int64_t u, uint
     if (g == 0 && Mother) {
         uint4 *dst = reinterpret_cast<uint4 *>(Mother + static_cast<size_t>(u) * R);
 #pragma unroll
-        for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
+        for (int c = 0; c < Gm::CPL; ++c) {
+            dst[li + Gm::G * c] = nw[c];
+            P.dmask[static_cast<size_t>(u) * Gm::CH + li + Gm::G * c] =
+                static_cast<uint16_t>(ne_bits16(nw[c], own[c]));
+        }
     }
     if (changed && lane == 0) set_bit(Lnext, u);
-    st.bytes += Mother ? 2 * R : R + ((changed || sync) ? R : 0);
+    st.bytes += Mother ? 2 * R + R / 8 : R + ((changed || sync) ? R : 0);
 }
 
 // finalize_row_r with the row's own registers read from ownp, or, in the first sweep of a diffusion (init), formed
@@ -429,8 +505,9 @@ __device__ __forceinline__ void finalize_row_g(const DevProb &P, int64_t u, uint
 #pragma unroll
     for (int c = 0; c < Gm::CPL; ++c) {
         const int ch = li + Gm::G * c;
-        own[c] = g != 0 ? make_uint4(0, 0, 0, 0) : (init ? init_chunk(P.Y, hv, ch, blocked16(P, u, ch)) : ownp[ch]);
+        own[c] = g != 0 ? make_uint4(0, 0, 0, 0) : (init ? init_chunk(P.Y, hv, ch, init_blocked16(P, u, ch)) : ownp[ch]);
     }
+    drop_blocked<R>(P, u, acc, li);
     finalize_row_r<R>(P, u, acc, anyTaken, sync, own, Mnext, init ? Mother : nullptr, Lnext, lane, g, li, st);
 }
 
@@ -508,7 +585,7 @@ __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W,
         for (int c = 0; c < Gm::CPL; ++c) {
             const int ch = li + Gm::G * c;
             if (INIT)
-                own[c] = is_row ? init_chunk_sw(Ys, hu, ch, blocked16(P, u, ch)) : make_uint4(0, 0, 0, 0);
+                own[c] = is_row ? init_chunk_sw(Ys, hu, ch, init_blocked16(P, u, ch)) : make_uint4(0, 0, 0, 0);
             else
                 own[c] = is_row ? __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(u) * R) + ch)
                                 : make_uint4(0, 0, 0, 0);
@@ -518,22 +595,32 @@ __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W,
         for (int c = 0; c < Gm::CPL; ++c)
 #pragma unroll
             for (int w = 0; w < 4; ++w) acc[c][w] = 0;
+        // the first sweep of a rebuild tests its pairs' neighbours for blocked simulations (none before a search)
+        const bool chk = INIT && P.rany && P.ctr->lvl != 0;
         uint32_t nPairs = 0;
         if (cur.np > 0) {
-            nPairs = sparse_tile<R, INIT>(P, cur.p0, cur.p0 + cur.np, allL, Lcur, Mcur, Ys, acc32, li);
-            nPairs = __reduce_add_sync(tm, nPairs);
+            if (INIT) {
+                sparse_tile_init<R>(P, cur.p0, cur.p0 + cur.np, chk, acc32, li);
+                nPairs = cur.np;
+            } else {
+                nPairs = sparse_tile<R, INIT>(P, cur.p0, cur.p0 + cur.np, allL, Lcur, Mcur, Ys, acc32, li);
+                nPairs = __reduce_add_sync(tm, nPairs);
+            }
             fold_tile<R>(acc, acc32, tm, li);
         }
         const uint32_t nTaken =
-            cur.nd > 0 ? dense_tile<R, INIT>(P, cur.d0, cur.d0 + cur.nd, allL, Lcur, Mcur, Ys, acc, li) : 0u;
+            cur.nd > 0 ? dense_tile<R, INIT>(P, cur.d0, cur.d0 + cur.nd, allL, Lcur, Mcur, Ys, chk, acc, li) : 0u;
         // modelled bytes: descriptor, pair records, the registers pairs read (computed in the first sweep), dense
         // edges (id, target, threshold) and their rows (masks only in the first sweep)
+        if (li == 0)
+            st.pairs += cur.np;
         if (li == 0)
             st.bytes += 32 + 6 * static_cast<uint64_t>(cur.np) + (INIT ? 0u : nPairs) +
                         (8 + tb + (INIT ? R / 8 : 0)) * static_cast<uint64_t>(cur.nd) +
                         (INIT ? 0u : static_cast<uint64_t>(nTaken) * R);
         const bool any = nPairs + nTaken > 0;
         if (is_row) {
+            drop_blocked<R>(P, u, acc, li);
             finalize_tile<R>(P, u, acc, any, !INIT && test_bit(Lcur, u), own, Mnext, Mother, Lnext, tm, li, st);
         } else if (any) {
             const int64_t task = cur.pad;
@@ -548,6 +635,148 @@ __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W,
         }
         cur = nxt;
     }
+    flush_stats(P.ctr, st, li);
+}
+
+// The first sweep of one problem over this tile's units (every row, then every task), software-pipelined: while a
+// unit is processed, the pair records and ranks of the next unit's first 4 G pairs and the descriptor of the unit
+// after it are already in flight, so the chain descriptor -> pairs -> merge of one unit overlaps the previous one.
+// The descriptors wait in a per-tile ring of three in shared memory (ring: 3 x 8 words), loaded a word a lane, and
+// each prefetched pair is one word (simulation | rank << 16), to keep the registers few.
+template <int R>
+__device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, uint64_t nworkers, unsigned tm,
+                                int li, uint32_t *acc32, const uint32_t *Ys, uint32_t *ring) {
+    using Gm = Geo<R>;
+    constexpr int G = Gm::G;
+    constexpr int DW = sizeof(UnitD) / 4;  // descriptor words
+    static_assert(DW == 8, "descriptor of 8 words");
+    const uint64_t n = static_cast<uint64_t>(P.n);
+    uint8_t *Mnext = P.M1;  // sweep 0 writes buffer 1, and buffer 0 too (both start as its result)
+    uint8_t *Mother = P.M0;
+    uint32_t *Lnext = P.Lb1;
+    const uint64_t tb = thr_bytes(P.model);
+    const uint8_t *rk = P.prb ? P.prb : P.pr;
+    const bool rebuild = P.rany && P.ctr->lvl != 0;  // some vertices are blocked
+    // a rebuild without the problem's own blocked ranks tests each pair's neighbour (residual blocking only)
+    const bool test = rebuild && !P.prb && !P.literal;
+    const uint32_t g = static_cast<uint32_t>((threadIdx.x & 31) / G);
+    Stats st;
+    // this lane's words (li, li + G, ...) of descriptor l (zeros past the end)
+    auto load_desc = [&](uint64_t l, uint32_t (&w)[(DW + G - 1) / G]) {
+        const uint32_t *src = l < cnt ? reinterpret_cast<const uint32_t *>(l < n ? P.rdesc + l : P.tdesc + (l - n))
+                                      : nullptr;
+#pragma unroll
+        for (int k = 0; k < (DW + G - 1) / G; ++k) {
+            const int wi = li + G * k;
+            w[k] = (src && wi < DW) ? __ldg(src + wi) : 0u;
+        }
+    };
+    auto store_desc = [&](int slot, const uint32_t (&w)[(DW + G - 1) / G]) {
+#pragma unroll
+        for (int k = 0; k < (DW + G - 1) / G; ++k) {
+            const int wi = li + G * k;
+            if (wi < DW) ring[slot * DW + wi] = w[k];
+        }
+    };
+    struct D {
+        int64_t p0, d0;
+        uint32_t np, nd;
+        int32_t u;
+    };
+    auto read_desc = [&](int slot) {
+        const uint32_t *r = ring + slot * DW;
+        D d;
+        d.p0 = static_cast<int64_t>((static_cast<uint64_t>(r[1]) << 32) | r[0]);
+        d.d0 = static_cast<int64_t>((static_cast<uint64_t>(r[3]) << 32) | r[2]);
+        d.np = r[4];
+        d.nd = r[5];
+        d.u = static_cast<int32_t>(r[6]);
+        return d;
+    };
+    // the first 4 G pairs of unit d, this lane's share: simulation | rank << 16 (rank 0 past the unit's end)
+    auto batch = [&](const D &d, uint32_t (&b)[4]) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t o = li + G * k;
+            b[k] = o < d.np ? (static_cast<uint32_t>(__ldg(&P.pj[d.p0 + o])) |
+                               (static_cast<uint32_t>(__ldg(&rk[d.p0 + o])) << 16))
+                            : 0u;
+        }
+    };
+    {
+        uint32_t w[(DW + G - 1) / G];
+        load_desc(first, w);
+        store_desc(0, w);
+        load_desc(first + nworkers, w);
+        store_desc(1, w);
+    }
+    __syncwarp(tm);
+    int slot = 0;  // ring slot of the current unit; slot + 1 holds the next one
+    uint32_t cb[4];
+    batch(read_desc(0), cb);
+    for (uint64_t l = first; l < cnt; l += nworkers) {
+        const int s1 = slot == 2 ? 0 : slot + 1, s2 = s1 == 2 ? 0 : s1 + 1;
+        const D cur = read_desc(slot);
+        uint32_t nb[4];
+        batch(read_desc(s1), nb);                 // the next unit's first pairs
+        uint32_t wn[(DW + G - 1) / G];
+        load_desc(l + 2 * nworkers, wn);          // and the descriptor after it
+        const bool is_row = l < n;
+        if (!(is_row && cur.u < 0)) {  // a split row is left to its tasks and the combine kernels
+            const int64_t u = cur.u;
+            uint4 own[Gm::CPL];
+            const uint32_t hu = vertex_hash(static_cast<uint32_t>(u));
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c)
+                own[c] = is_row ? init_chunk_sw(Ys, hu, li + G * c, init_blocked16(P, u, li + G * c))
+                                : make_uint4(0, 0, 0, 0);
+            uint32_t acc[Gm::CPL][4];
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[c][w] = 0;
+            if (cur.np > 0) {
+                if (test) {
+                    sparse_tile_init<R>(P, cur.p0, cur.p0 + cur.np, true, acc32, li);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (cb[k] >> 16) atomicMax(&acc32[sw_slot(cb[k] & 0xFFFFu, g)], cb[k] >> 16);
+                    if (cur.np > 4 * G) sparse_tile_init<R>(P, cur.p0 + 4 * G, cur.p0 + cur.np, false, acc32, li);
+                }
+                fold_tile<R>(acc, acc32, tm, li);
+            }
+            const uint32_t nTaken = cur.nd > 0 ? dense_tile<R, true>(P, cur.d0, cur.d0 + cur.nd, true, nullptr,
+                                                                     nullptr, Ys, rebuild, acc, li)
+                                               : 0u;
+            // modelled bytes: descriptor, pair records (simulation, rank), dense edges (id, target, threshold,
+            // mask); the rows' writes are counted by finalize_tile
+            if (li == 0) {
+                st.pairs += cur.np;
+                st.bytes += 32 + 3 * static_cast<uint64_t>(cur.np) + (8 + tb + R / 8) * static_cast<uint64_t>(cur.nd);
+            }
+            if (is_row) {
+                drop_blocked<R>(P, u, acc, li);
+                finalize_tile<R>(P, u, acc, true, false, own, Mnext, Mother, Lnext, tm, li, st);
+            } else if (cur.np + nTaken > 0) {
+                const int64_t task = static_cast<int64_t>(l - n);
+                uint4 *dst = reinterpret_cast<uint4 *>(P.part + static_cast<size_t>(task) * R);
+#pragma unroll
+                for (int c = 0; c < Gm::CPL; ++c)
+                    dst[li + G * c] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+                if (li == 0) {
+                    set_bit(P.part_any, task);
+                    st.bytes += R;
+                }
+            }
+        }
+        store_desc(s2, wn);  // the unit after next goes to the free slot (read as the next unit from next round)
+        __syncwarp(tm);
+        slot = s1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cb[k] = nb[k];
+    }
+    if (li == 0 && st.bytes) atomicAdd(&P.ctr->first_bytes, st.bytes);
     flush_stats(P.ctr, st, li);
 }
 
@@ -649,15 +878,22 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
     const uint32_t lim = P.cas_limit;
     const uint64_t nl = P.ctr->npush_l;
     Stats st;
+    // the vertex and descriptor of a light unit are loaded one unit ahead, so that the next unit's dependent loads
+    // overlap this unit's work
+    int64_t vn = 0;
+    UnitD dn{};
+    if (first < cnt && first < nl) {
+        vn = P.chg_list[first];
+        dn = P.vdesc[vn];
+    }
     for (uint64_t l = first; l < cnt; l += nworkers) {
         int64_t v, p0, p1, d0, d1;
         if (l < nl) {
-            v = P.chg_list[l];
-            const UnitD dv = P.vdesc[v];
-            p0 = dv.p0;
-            p1 = dv.p0 + dv.np;
-            d0 = dv.d0;
-            d1 = dv.d0 + dv.nd;
+            v = vn;
+            p0 = dn.p0;
+            p1 = dn.p0 + dn.np;
+            d0 = dn.d0;
+            d1 = dn.d0 + dn.nd;
         } else {
             const uint64_t h = P.chg_hc[l - nl];
             v = static_cast<int64_t>(static_cast<uint32_t>(h));
@@ -669,51 +905,50 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
             d0 = __ldg(&P.idofs[k0]);
             d1 = __ldg(&P.idofs[k1]);
         }
-        // Stage M_v and the registers of v that the previous sweep changed: only those can raise an in-neighbour
-        // (M_u[j] >= the previous sweep's M_v[j] holds for every live (u, v) after the first sweep), so pairs of
-        // other simulations are skipped.  After the first sweep they are the registers above v's initial rank.
-        const uint4 *vrow = reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(v) * R);
-        if (t == 1) {
-            const uint32_t hv = vertex_hash(static_cast<uint32_t>(v));
-            for (int c = lane; c < Gm::CH; c += 32) {
-                const uint4 x = __ldg(vrow + c);
-                reinterpret_cast<uint4 *>(srow)[c] = x;
-                sdel[c] = static_cast<uint16_t>(ne_bits16(x, init_chunk(P.Y, hv, c, blocked16(P, v, c))));
-            }
-        } else {
-            for (int c = lane; c < Gm::CH; c += 32) {
-                reinterpret_cast<uint4 *>(srow)[c] = __ldg(vrow + c);
-                sdel[c] = __ldg(&P.dmask[static_cast<size_t>(v) * Gm::CH + c]);
-            }
+        if (l + nworkers < cnt && l + nworkers < nl) {
+            vn = P.chg_list[l + nworkers];
+            dn = P.vdesc[vn];
         }
-        uint4 rowc[Gm::CPL];
+        // Stage the registers of v that the previous sweep changed (recorded by that sweep's first pass, or by the
+        // frontier pass that copied the row): only those can raise an in-neighbour (M_u[j] >= the previous sweep's
+        // M_v[j] holds for every live (u, v) after the first sweep), so pairs of other simulations are skipped and
+        // a pair of a changed one reads M_v[j] itself.
+        const uint8_t *vbytes = Mcur + static_cast<size_t>(v) * R;
+        const uint4 *vrow = reinterpret_cast<const uint4 *>(vbytes);
+        for (int c = lane; c < Gm::CH; c += 32) sdel[c] = __ldg(&P.dmask[static_cast<size_t>(v) * Gm::CH + c]);
+        uint4 rowc[Gm::CPL];  // this lane's chunks of M_v, for the dense in-edges
+        const bool dense = d1 > d0;
 #pragma unroll
-        for (int c = 0; c < Gm::CPL; ++c) rowc[c] = __ldg(vrow + li + G * c);
+        for (int c = 0; c < Gm::CPL; ++c) rowc[c] = dense ? __ldg(vrow + li + G * c) : make_uint4(0, 0, 0, 0);
         __syncwarp();
         uint32_t nproc = 0;  // pairs of changed registers (the others cost only their record)
         for (int64_t p = p0 + lane; p < p1; p += 128) {
             uint32_t *addr[4];
-            uint32_t cand[4], old[4];
+            uint32_t jj[4], old[4], x[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int64_t q = p + 32 * k;
-                cand[k] = 0;
                 addr[k] = nullptr;
+                jj[k] = 0;
                 if (q < p1) {
                     const int64_t u = __ldg(&P.iu[q]);
                     const uint32_t j = __ldg(&P.ij[q]);
-                    if ((sdel[j >> 4] >> (j & 15)) & 1u) {
-                        cand[k] = static_cast<uint32_t>(srow[j]) << (8 * (j & 3));
+                    if (((sdel[j >> 4] >> (j & 15)) & 1u) && !literal_blocked(P, u, j)) {
+                        jj[k] = j;
                         addr[k] = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u) * R + (j & ~3u));
                         ++nproc;
                     }
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) old[k] = cand[k] ? __ldcg(addr[k]) : 0u;
+            for (int k = 0; k < 4; ++k) {  // the candidate register and the target word, loaded together
+                x[k] = addr[k] ? __ldg(vbytes + jj[k]) : 0u;
+                old[k] = addr[k] ? __ldcg(addr[k]) : 0u;
+            }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (cand[k] && word_max(addr[k], old[k], cand[k], fault, lim))
+                const uint32_t cand = x[k] << (8 * (jj[k] & 3));
+                if (cand && word_max(addr[k], old[k], cand, fault, lim))
                     set_bit(Lnext, (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R);
             }
         }
@@ -743,6 +978,7 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
                         m[r][c] = ok[r] ? (__ldg(&P.live[static_cast<size_t>(e) * W + (ch >> 1)]) >> (16 * (ch & 1))) &
                                               sdel[ch]
                                         : 0u;
+                        if (m[r][c] && P.literal) m[r][c] &= ~blocked16(P, u[r], ch);
                         o[r][c] = m[r][c] ? __ldcg(reinterpret_cast<const uint4 *>(Mnext + static_cast<size_t>(u[r]) * R) +
                                                    ch)
                                           : make_uint4(0, 0, 0, 0);
@@ -771,11 +1007,13 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
             }
         }
         nproc = __reduce_add_sync(kFull, nproc);
-        // modelled bytes: M_v and its change mask, descriptor, pair records, the register word of each pair of a
-        // changed register, and per dense in-edge its ids, live mask and target row
+        // modelled bytes: list entry and descriptor, the change mask, pair records, per pair of a changed register
+        // the register and the target word, and with dense in-edges M_v plus per edge its ids, mask and target row
         if (lane == 0)
-            st.bytes += R + R / 8 + 32 + 6 * static_cast<uint64_t>(p1 - p0) + 4 * static_cast<uint64_t>(nproc) +
-                        (12 + W * 4 + R) * static_cast<uint64_t>(d1 - d0);
+            st.pairs += static_cast<uint64_t>(p1 - p0);
+        if (lane == 0)
+            st.bytes += 36 + R / 8 + 6 * static_cast<uint64_t>(p1 - p0) + 5 * static_cast<uint64_t>(nproc) +
+                        (dense ? R : 0) + (12 + W * 4 + R) * static_cast<uint64_t>(d1 - d0);
         __syncwarp();
     }
     // the staged rows shared the sparse accumulators, which a pulling unit of another problem in the same launch
@@ -783,6 +1021,96 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
     for (int k = lane; k < R / 4 + R / 32; k += 32) warp_smem[k] = 0u;
     __syncwarp();
     if (st.bytes) atomicAdd(&P.ctr->bytes, st.bytes);
+    if (st.pairs) atomicAdd(&P.ctr->pairs, st.pairs);
+}
+
+// A push sweep over a large L as one stream of in-pairs (sampled graphs without dense edges): every in-pair
+// (u, v, j) in in-CSR order, 128 a warp at a time, merges M_v[j] into the next buffer's M_u[j] when v is in L and
+// the previous sweep changed (v, j) (the same skip as push_problem_w; dmask of every listed v, or of every row after
+// the first sweep, is current); the pair records and the change masks of consecutive pairs are coalesced, and
+// only pairs of changed registers touch a register row.
+template <int R>
+__device__ void push_stream_w(const DevProb &P, uint32_t t, uint64_t cnt, uint64_t first, uint64_t nworkers,
+                              int lane) {
+    constexpr int CH = R / 16;
+    const bool par = t & 1u;
+    const uint8_t *Mcur = par ? P.M1 : P.M0;
+    uint8_t *Mnext = par ? P.M0 : P.M1;
+    const uint32_t *Lcur = par ? P.Lb1 : P.Lb0;
+    uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
+    unsigned int *fault = &P.ctr->fault;
+    const uint32_t lim = P.cas_limit;
+    const uint64_t npairs = static_cast<uint64_t>(P.ipofs[P.m]);
+    uint32_t nproc = 0, nrec = 0;
+    // the records of the next item are loaded while this one is processed (the loop is a chain of dependent loads:
+    // record -> change mask -> register and target word -> compare-and-swap)
+    int32_t nv[4], nu[4];
+    uint32_t nj[4];
+    auto fetch = [&](uint64_t l) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t q = l * 128 + 32 * k + lane;
+            const bool ok = l < cnt && q < npairs;
+            nv[k] = ok ? __ldg(&P.iv[q]) : -1;
+            nj[k] = ok ? __ldg(&P.ij[q]) : 0u;
+            nu[k] = ok ? __ldg(&P.iu[q]) : 0;
+        }
+    };
+    fetch(first);
+    for (uint64_t l = first; l < cnt; l += nworkers) {
+        int32_t cv[4], cu[4];
+        uint32_t cj[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            cv[k] = nv[k];
+            cu[k] = nu[k];
+            cj[k] = nj[k];
+        }
+        fetch(l + nworkers);
+        uint32_t *addr[4];
+        uint32_t jj[4], old[4], x[4];
+        const uint8_t *vb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            addr[k] = nullptr;
+            jj[k] = 0;
+            vb[k] = Mcur;
+            if (cv[k] >= 0) {
+                ++nrec;
+                const int32_t v = cv[k];
+                const uint32_t j = cj[k];
+                const bool inL = t == 1 || test_bit(Lcur, v);
+                if (inL && ((__ldg(&P.dmask[static_cast<size_t>(v) * CH + (j >> 4)]) >> (j & 15)) & 1u)) {
+                    const int32_t u = cu[k];
+                    if (!literal_blocked(P, u, j)) {
+                        jj[k] = j;
+                        vb[k] = Mcur + static_cast<size_t>(v) * R;
+                        addr[k] = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u) * R + (j & ~3u));
+                        ++nproc;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            x[k] = addr[k] ? __ldg(vb[k] + jj[k]) : 0u;
+            old[k] = addr[k] ? __ldcg(addr[k]) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t cand = x[k] << (8 * (jj[k] & 3));
+            if (cand && word_max(addr[k], old[k], cand, fault, lim))
+                set_bit(Lnext, (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R);
+        }
+    }
+    // modelled bytes: per pair its record (target, source, simulation: 10 bytes) and change-mask word (2), and per
+    // pair of a changed register the register and the target word (5)
+    nproc = __reduce_add_sync(kFull, nproc);
+    nrec = __reduce_add_sync(kFull, nrec);
+    if (lane == 0 && nrec) {
+        atomicAdd(&P.ctr->bytes, 12ull * nrec + 5ull * nproc);
+        atomicAdd(&P.ctr->pairs, static_cast<unsigned long long>(nrec));
+    }
 }
 
 // Per-tile shared-memory accumulators of the pulling sweep kernels: one 32-bit slot per simulation and tile.
@@ -803,6 +1131,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_first(const DevProb *__restric
     using Gm = Geo<R>;
     extern __shared__ __align__(16) uint4 gather_smem[];
     __shared__ __align__(16) uint32_t sY[R];  // the problem's initialisation words Y_j (slots sw_slot(j, 0))
+    __shared__ uint32_t sring[kWarpsPerBlock * Geo<R>::NG][3 * 8];  // per tile: three unit descriptors
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int g = lane / Gm::G, li = lane % Gm::G;
     const unsigned tm = tile_mask<R>(g);
@@ -818,12 +1147,11 @@ __global__ void __launch_bounds__(kBlock, MINB) k_first(const DevProb *__restric
         __syncthreads();  // the previous problem's use of sY is over
         for (int k = threadIdx.x; k < R; k += blockDim.x) sY[sw_slot(k, 0)] = __ldg(&P.Y[k]);
         __syncthreads();
-        const SweepWork W = sweep_work_init(P);
-        const uint64_t cnt = W.nlight + W.ntask;
+        const uint64_t cnt = static_cast<uint64_t>(P.n) + static_cast<uint64_t>(P.n_tasks);
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
         if (first >= cnt) continue;
-        prop_problem_t<R, true>(P, 0, W, cnt, first, nworkers, tm, li, acc32, sY);
+        first_problem_t<R>(P, cnt, first, nworkers, tm, li, acc32, sY, sring[wib * Geo<R>::NG + g]);
     }
 }
 
@@ -881,6 +1209,14 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(const DevProb *__restrict
         if (C.done) continue;
         if (C.full) {  // pulled by k_first launched beside this kernel; otherwise a scheduling error, flagged
             if (!skip_full && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&P.ctr->fault, 8u);
+            continue;
+        }
+        if (C.stream) {  // a large L: every in-pair, 128 a warp item
+            const uint64_t cnt = (static_cast<uint64_t>(P.ipofs[P.m]) + 127) / 128;
+            const uint64_t first = first_owned(wworker, nwworkers, base);
+            base += cnt;
+            if (first >= cnt) continue;
+            push_stream_w<R>(P, C.t, cnt, first, nwworkers, lane);
             continue;
         }
         const uint64_t cnt = static_cast<uint64_t>(C.npush_l) + C.npush_h;
@@ -1243,6 +1579,7 @@ __device__ __forceinline__ void advance_one(const DevProb &P) {
     // visits of the next sweep (Algorithm 2's work count): every edge (u, v) with v in L_{t+1}, in every simulation
     if (!C.done) C.visits += __ldcg(&C.chg_indeg) * static_cast<unsigned long long>(P.R);
     C.full = next_is_push(P, C) ? 0u : 1u;
+    C.stream = (!C.full && __ldcg(&C.chg_indeg) >= P.stream_min) ? 1u : 0u;
     C.npush_l = C.full ? 0u : __ldcg(&C.nchg_list);
     C.npush_h = C.full ? 0u : __ldcg(&C.nchg_hc);
     C.nchg = 0;
@@ -1260,40 +1597,58 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                                                  int nact) {
     const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    // rany / rnew words: a warp per 32 vertices, a lane per vertex row
+    {
+        const uint64_t worker = tid >> 5, nworkers = nthreads >> 5;
+        uint64_t base = 0;
+        for (int q = 0; q < nact; ++q) {
+            const DevProb &P = probs[act[q]];
+            if (!P.rany) continue;
+            const uint64_t words = (static_cast<uint64_t>(P.n) + 31) >> 5;
+            const uint64_t first = first_owned(worker, nworkers, base);
+            base += words;
+            // no search has run yet (levels count on over the searches of a problem): nothing is reached
+            const bool searched = P.ctr->lvl != 0;
+            for (uint64_t wi = first; wi < words; wi += nworkers) {
+                const int64_t v = static_cast<int64_t>(wi) * 32 + lane;
+                uint32_t any = 0, nw = 0;
+                if (searched && v < P.n) {
+                    const uint2 *row = reinterpret_cast<const uint2 *>(P.vis + static_cast<size_t>(v) * P.W);
+                    const uint2 *done =
+                        P.prb ? reinterpret_cast<const uint2 *>(P.vis_done + static_cast<size_t>(v) * P.W) : nullptr;
+                    for (int k = 0; k < P.W / 2; ++k) {
+                        const uint2 x = row[k];
+                        any |= x.x | x.y;
+                        if (done) {
+                            const uint2 y = done[k];
+                            nw |= (x.x & ~y.x) | (x.y & ~y.y);
+                        }
+                    }
+                }
+                const uint32_t bits = __ballot_sync(kFull, any != 0);
+                const uint32_t fresh = __ballot_sync(kFull, nw != 0);
+                if (lane == 0) {
+                    P.rany[wi] = bits;
+                    if (P.prb) P.rnew[wi] = fresh;  // vertices with blocked bits not yet in the pair ranks
+                }
+            }
+        }
+    }
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
         const int64_t words = (P.n + 31) >> 5;
         const int64_t twords = (P.n_tasks + 31) >> 5;
-        const uint64_t rwords = P.rany ? static_cast<uint64_t>(words) : 0u;
-        // units: L bits (2 x words), task bits, rany words, counters
-        const uint64_t cnt = 2 * static_cast<uint64_t>(words) + static_cast<uint64_t>(twords) + rwords + 1;
+        // units: L bits (2 x words), task bits, counters
+        const uint64_t cnt = 2 * static_cast<uint64_t>(words) + static_cast<uint64_t>(twords) + 1;
         const uint64_t first = first_owned(tid, nthreads, base);
         base += cnt;
-        // no search has run yet (levels count on over the searches of a problem): nothing is reached
-        const bool searched = P.rany && P.ctr->lvl != 0;
         for (uint64_t l = first; l < cnt; l += nthreads) {
             if (l < 2 * static_cast<uint64_t>(words)) {
                 (l < static_cast<uint64_t>(words) ? P.Lb0 : P.Lb1)[l % words] = 0;
-            } else if (l < 2 * static_cast<uint64_t>(words) + twords) {
-                P.part_any[l - 2 * static_cast<uint64_t>(words)] = 0;
             } else if (l < cnt - 1) {
-                const int64_t wi = static_cast<int64_t>(l - 2 * static_cast<uint64_t>(words) - twords);
-                uint32_t bits = 0;
-                if (searched) {
-                    for (int b = 0; b < 32; ++b) {
-                        const int64_t v = wi * 32 + b;
-                        if (v >= P.n) break;
-                        const uint2 *row = reinterpret_cast<const uint2 *>(P.vis + static_cast<size_t>(v) * P.W);
-                        uint32_t any = 0;
-                        for (int k = 0; k < P.W / 2; ++k) {
-                            const uint2 x = row[k];
-                            any |= x.x | x.y;
-                        }
-                        bits |= (any != 0 ? 1u : 0u) << b;
-                    }
-                }
-                P.rany[wi] = bits;
+                P.part_any[l - 2 * static_cast<uint64_t>(words)] = 0;
             } else {
                 DevCtr &C = *P.ctr;
                 C.t = 0;
@@ -1306,6 +1661,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 C.nchg_hc = 0;
                 C.npush_l = 0;
                 C.npush_h = 0;
+                C.stream = 0;
                 C.chg_indeg = 0;
                 C.gms = 0;  // M_S' is cleared below
                 C.cand_key = 0;
@@ -2045,7 +2401,8 @@ __global__ void __launch_bounds__(kBlock) k_live_masks(const DevProb P) {
             if (e < e1) {
                 const int32_t v = __ldg(&P.adj[e]);
                 edge_threshold(P, e, v, T, ok);
-                h = edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n));
+                h = edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n),
+                              P.undirected != 0);
             }
             const int cnt_e = e1 - base < 32 ? static_cast<int>(e1 - base) : 32;
             for (int j = 0; j < cnt_e; ++j) {
@@ -2075,8 +2432,8 @@ __global__ void __launch_bounds__(kBlock) k_inpair_counts(const DevProb P, int32
 }
 
 // In-pairs (source u, simulation j) of every sparse in-edge at ipofs[k], and the dense in-edges (u, e).
-__global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t *iu, uint16_t *ij, int32_t *idu,
-                                                        uint32_t *ide) {
+__global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t *iu, uint16_t *ij, uint32_t *iop,
+                                                        int32_t *idu, uint32_t *ide) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < P.m; k += stride) {
         const int64_t d0 = P.idofs[k];
@@ -2091,8 +2448,79 @@ __global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t
         for (int64_t p = P.pofs[e]; p < P.pofs[e + 1]; ++p) {
             iu[at] = u;
             ij[at] = P.pj[p];
+            if (iop) iop[at] = static_cast<uint32_t>(p);  // the same pair in out-CSR order
             ++at;
         }
+    }
+}
+
+// Residual blocking in the pair ranks of a rebuild: every in-pair (u, v, j) whose (v, j) S reached since the last
+// rebuild (set in vis, not yet in vis_done) gets rank 0 in the problem's copy of the out-pair ranks, so the first
+// sweep needs no test.  A stream over the in-pairs, four a thread in flight; rnew (set by k_init) marks the vertices
+// with new bits, so the pairs of other vertices cost their target id and one cached bit.
+__global__ void __launch_bounds__(kBlock) k_block_pairs(const DevProb *__restrict__ probs,
+                                                        const int32_t *__restrict__ act, int nact) {
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        if (!P.prb || P.ctr->lvl == 0) continue;
+        const uint64_t npairs = static_cast<uint64_t>(P.ipofs[P.m]);
+        // items of four pairs nthreads apart, in whole rounds of nthreads items (round r: pairs 4 r nthreads ..)
+        const uint64_t cnt = (npairs + 4 * nthreads - 1) / (4 * nthreads) * nthreads;
+        const uint64_t first = first_owned(tid, nthreads, base);
+        base += cnt;
+        for (uint64_t it = first; it < cnt; it += nthreads) {
+            const uint64_t blk = it - it % nthreads;  // the four pairs of this item lie nthreads apart
+            int32_t v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint64_t kk = blk * 4 + static_cast<uint64_t>(k) * nthreads + (it - blk);
+                v[k] = kk < npairs ? __ldg(&P.iv[kk]) : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (v[k] < 0 || !test_bit(P.rnew, v[k])) continue;
+                const uint64_t kk = blk * 4 + static_cast<uint64_t>(k) * nthreads + (it - blk);
+                const uint32_t j = __ldg(&P.ij[kk]);
+                const size_t w = static_cast<size_t>(v[k]) * P.W + (j >> 5);
+                if (((P.vis[w] & ~P.vis_done[w]) >> (j & 31)) & 1u) P.prb[__ldg(&P.iop[kk])] = 0;
+            }
+        }
+    }
+}
+
+// After k_block_pairs: the blocked bits now applied to the pair ranks (vis_done = vis for the rows with new bits).
+// A warp per 32 vertices; most words of rnew are zero.
+__global__ void __launch_bounds__(kBlock) k_block_done(const DevProb *__restrict__ probs,
+                                                       const int32_t *__restrict__ act, int nact) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    uint64_t base = 0;
+    for (int q = 0; q < nact; ++q) {
+        const DevProb &P = probs[act[q]];
+        if (!P.prb || P.ctr->lvl == 0) continue;
+        const uint64_t cnt = (static_cast<uint64_t>(P.n) + 31) / 32;
+        const uint64_t first = first_owned(worker, nworkers, base);
+        base += cnt;
+        for (uint64_t l = first; l < cnt; l += nworkers)
+            for (uint32_t m = P.rnew[l]; m; m &= m - 1u) {
+                const size_t row = (l * 32 + (__ffs(m) - 1)) * static_cast<size_t>(P.W);
+                for (int k = lane; k < P.W; k += 32) P.vis_done[row + k] = P.vis[row + k];
+            }
+    }
+}
+
+// Target vertex of every in-pair (the in-CSR row v of the in-edge holding it): a warp per vertex.
+__global__ void __launch_bounds__(kBlock) k_inpair_targets(const DevProb P, int32_t *iv) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t v = warp; v < P.n; v += nwarps) {
+        const int64_t q0 = P.ipofs[P.xadj_in[v]], q1 = P.ipofs[P.xadj_in[v + 1]];
+        for (int64_t q = q0 + lane; q < q1; q += 32) iv[q] = static_cast<int32_t>(v);
     }
 }
 
@@ -2155,7 +2583,8 @@ __global__ void __launch_bounds__(kBlock) k_pair_counts(const DevProb P, int32_t
 }
 
 // Writes the pairs of every sparse edge at pofs[e] (simulations in increasing order) and the dense edge ids.
-__global__ void __launch_bounds__(kBlock) k_pair_fill(const DevProb P, int32_t *pv, uint16_t *pj, uint32_t *dlist) {
+__global__ void __launch_bounds__(kBlock) k_pair_fill(const DevProb P, int32_t *pv, uint16_t *pj, uint8_t *pr,
+                                                      uint32_t *dlist) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < P.m; e += stride) {
         const int64_t d0 = P.dofs[e];
@@ -2165,11 +2594,14 @@ __global__ void __launch_bounds__(kBlock) k_pair_fill(const DevProb P, int32_t *
         }
         int64_t at = P.pofs[e];
         const int32_t v = P.adj[e];
+        const uint32_t hv = vertex_hash(static_cast<uint32_t>(v));
         const uint32_t *lv = P.live + static_cast<size_t>(e) * P.W;
         for (int k = 0; k < P.W; ++k) {
             for (uint32_t w = lv[k]; w; w &= w - 1) {
+                const uint32_t j = 32 * k + __ffs(w) - 1;
                 pv[at] = v;
-                pj[at] = static_cast<uint16_t>(32 * k + __ffs(w) - 1);
+                pj[at] = static_cast<uint16_t>(j);
+                pr[at] = static_cast<uint8_t>(__clz(hv ^ __ldg(&P.Y[j])));  // the initial rank of (v, j)
                 ++at;
             }
         }
@@ -2289,18 +2721,83 @@ __global__ void k_wc_thresholds(const int32_t *__restrict__ indeg, int64_t n, ui
     }
 }
 
-__global__ void k_transpose_fill(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj, int64_t n,
-                                 unsigned long long *__restrict__ cursor, int32_t *__restrict__ adj_in,
-                                 uint32_t *__restrict__ ein) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t u = warp; u < n; u += nwarps)
-        for (int64_t e = xadj[u] + lane; e < xadj[u + 1]; e += 32) {
-            const unsigned long long at = atomicAdd(&cursor[adj[e]], 1ull);
-            adj_in[at] = static_cast<int32_t>(u);
+// In-CSR fill: every edge e = (u, v) takes the next free place among v's in-edges.  A block takes kTrChunk
+// consecutive edges and first counts them per target in a shared-memory hash table, so a target that many of them
+// share (a hub) costs one returned global atomic per block instead of one per edge; the edges then take their
+// places from the block's reservation.  (The order of a vertex's in-edges is free: nothing depends on it.)
+constexpr int kTrChunk = 1024;
+constexpr int kTrSlots = 2048;  // hash slots (twice the edges of a chunk)
+__global__ void __launch_bounds__(kBlock) k_transpose_fill(const int64_t *__restrict__ xadj,
+                                                           const int32_t *__restrict__ adj, int64_t n, int64_t m,
+                                                           unsigned long long *__restrict__ cursor,
+                                                           int32_t *__restrict__ adj_in, uint32_t *__restrict__ ein) {
+    __shared__ int32_t s_key[kTrSlots];
+    __shared__ uint32_t s_cnt[kTrSlots];
+    __shared__ unsigned long long s_base[kTrSlots];
+    __shared__ int64_t s_u0, s_u1;
+    constexpr int PER = kTrChunk / kBlock;  // edges a thread
+    const uint64_t chunks = (static_cast<uint64_t>(m) + kTrChunk - 1) / kTrChunk;
+    for (uint64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+        const int64_t e0 = static_cast<int64_t>(c) * kTrChunk;
+        const int64_t e1 = e0 + kTrChunk < m ? e0 + kTrChunk : m;
+        for (int k = threadIdx.x; k < kTrSlots; k += blockDim.x) {
+            s_key[k] = -1;
+            s_cnt[k] = 0;
+        }
+        if (threadIdx.x == 0) {  // the rows holding edges e0 and e1 - 1 (the last u with xadj[u] <= e)
+            int64_t lo = 0, hi = n - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (xadj[mid] <= e0) lo = mid; else hi = mid - 1;
+            }
+            s_u0 = lo;
+            hi = n - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (xadj[mid] <= e1 - 1) lo = mid; else hi = mid - 1;
+            }
+            s_u1 = lo;
+        }
+        __syncthreads();
+        int32_t slot[PER];
+        uint32_t rank[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int64_t e = e0 + threadIdx.x + static_cast<int64_t>(i) * kBlock;
+            slot[i] = -1;
+            rank[i] = 0;
+            if (e < e1) {
+                const int32_t v = adj[e];
+                uint32_t h = (static_cast<uint32_t>(v) * 0x9E3779B1u) >> 21;  // 11 bits: kTrSlots
+                for (;;) {  // linear probing; the table has twice the chunk's edges, so a free slot exists
+                    const int32_t k = atomicCAS(&s_key[h], -1, v);
+                    if (k == -1 || k == v) break;
+                    h = (h + 1) & (kTrSlots - 1);
+                }
+                slot[i] = static_cast<int32_t>(h);
+                rank[i] = atomicAdd(&s_cnt[h], 1u);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < kTrSlots; k += blockDim.x)
+            if (s_cnt[k]) s_base[k] = atomicAdd(&cursor[s_key[k]], static_cast<unsigned long long>(s_cnt[k]));
+        __syncthreads();
+        const int64_t u0 = s_u0, u1 = s_u1;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            if (slot[i] < 0) continue;
+            const int64_t e = e0 + threadIdx.x + static_cast<int64_t>(i) * kBlock;
+            int64_t lo = u0, hi = u1;  // the row of e among the chunk's rows
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(&xadj[mid]) <= e) lo = mid; else hi = mid - 1;
+            }
+            const unsigned long long at = s_base[slot[i]] + rank[i];
+            adj_in[at] = static_cast<int32_t>(lo);
             ein[at] = static_cast<uint32_t>(e);
         }
+        __syncthreads();  // the table is reset for the next chunk
+    }
 }
 
 __global__ void k_row_tasks(const int64_t *__restrict__ xadj, int64_t n, int32_t *__restrict__ ntask,
@@ -2446,6 +2943,61 @@ __global__ void k_validate(const int64_t *__restrict__ xadj, const int32_t *__re
     }
 }
 
+// Order-free 64-bit fingerprint of a graph for exported sketches: the wrapping sum over edges of a splitmix64-style
+// mix of (edge index, source, target, per-edge threshold).  A warp per row.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__global__ void k_graph_hash(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj, int64_t n,
+                             const uint32_t *__restrict__ T_edge, unsigned long long *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    unsigned long long acc = 0;
+    for (int64_t u = warp; u < n; u += nwarps)
+        for (int64_t e = xadj[u] + lane; e < xadj[u + 1]; e += 32) {
+            const unsigned long long t = T_edge ? T_edge[e] : 0u;
+            acc += mix64(static_cast<unsigned long long>(e) * 0x9E3779B97F4A7C15ull ^
+                         (static_cast<unsigned long long>(u) << 32) ^ static_cast<uint32_t>(adj[e]) ^ (t << 17));
+        }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+    if (lane == 0 && acc) atomicAdd(out, acc);
+}
+
+// Order-free checksum of a byte array (8-byte words; bytes a multiple of 8): the wrapping sum of mix64(index, word).
+__global__ void k_checksum(const unsigned long long *__restrict__ x, uint64_t words, unsigned long long *out) {
+    unsigned long long acc = 0;
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < words;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        acc += mix64(i * 0x9E3779B97F4A7C15ull ^ __ldg(&x[i]));
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+// Checks of an undirected input: every row strictly increasing (flag 4) and every (u, v) matched by (v, u) (flag 5,
+// found by binary search in the sorted row of v).  A warp per row.
+__global__ void k_validate_undirected(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj, int64_t n,
+                                      unsigned int *flags) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
+        const int64_t e0 = xadj[u], e1 = xadj[u + 1];
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int32_t v = adj[e];
+            if (e > e0 && adj[e - 1] >= v) flags[4] = 1;
+            int64_t lo = xadj[v], hi = xadj[v + 1];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (adj[mid] < u) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= xadj[v + 1] || adj[lo] != u) flags[5] = 1;
+        }
+    }
+}
+
 // Per-edge thresholds of Eq. 5: T = ceil(p * 2^32) - 1 in double (exact for float p), never live for p <= 0.
 __global__ void k_edge_thresholds(const float *__restrict__ p, int64_t m, uint32_t *__restrict__ T,
                                   uint8_t *__restrict__ ok, unsigned int *flags) {
@@ -2464,7 +3016,7 @@ __global__ void k_edge_thresholds(const float *__restrict__ p, int64_t m, uint32
 
 static int g_sms = 0;
 static int g_device = 0;
-static int g_variant = 0;     // propagation launch shape (IM_PROP_VARIANT)
+static int g_variant = 0;     // default register budget of the first-sweep kernel (IM_PROP_VARIANT)
 static int g_grid_warp = 0;   // blocks for warp-striped kernels
 static int g_grid_block = 0;  // blocks for block-striped kernels
 
@@ -2473,12 +3025,12 @@ cudaError_t configure(int device) {
     cudaError_t e = cudaGetDeviceProperties(&prop, device);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan<256>, kBlock, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_init, kBlock, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     g_sms = prop.multiProcessorCount;
     g_device = device;
-    g_grid_warp = prop.multiProcessorCount * occ;
+    g_grid_warp = prop.multiProcessorCount * occ;  // grid-stride kernels: one wave of 256-thread blocks
     g_grid_block = prop.multiProcessorCount * 4;
     if (const char *v = getenv("IM_PROP_VARIANT")) g_variant = atoi(v);
     return cudaSuccess;
@@ -2536,27 +3088,30 @@ static void launch_combines(const DevProb *probs, const int32_t *act, int nact, 
         default: break;                                      \
     }
 
-// One sweep's propagation launches.  pulls: some listed problem may start a diffusion, whose first sweep k_first
-// runs; the others run in k_push, or in k_propg when later sweeps pull too (pull_more).  Returns the launches.
-// Minimum resident blocks per SM of the pulling kernels (register budget); IM_PROP_VARIANT selects 3 or 6 instead
-// of the default 4 (all exact alike).
+// The first sweep of the listed problems that start a diffusion.  variant: resident blocks per SM the kernel's
+// register budget targets (3, 4 or 6; 0: the default, 4, or IM_PROP_VARIANT); every variant gives the same
+// registers.  Then one sweep of the others (launch_prop): in k_push, or in k_propg when later sweeps pull too
+// (pull_more); pulls says that launch_first ran for this sweep.  Each returns the launches.
+int launch_first(int R, const DevProb *probs, const int32_t *act, int nact, int variant, cudaStream_t s) {
+    switch (variant > 0 ? variant : g_variant) {
+        case 3: IMK_R_SWITCH(R, (launch_gather<RR, 3, true>(probs, act, nact, s))); break;
+        case 6: IMK_R_SWITCH(R, (launch_gather<RR, 6, true>(probs, act, nact, s))); break;
+        default: IMK_R_SWITCH(R, (launch_gather<RR, 4, true>(probs, act, nact, s))); break;
+    }
+    return 1;
+}
 int launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, bool pulls, bool pull_more,
                 cudaStream_t s) {
     if (!pulls) {
         IMK_R_SWITCH(R, (launch_push<RR, kPushMinBlocks>(probs, act, nact, false, s)));
         return 1;
     }
-    switch (g_variant) {
-        case 3: IMK_R_SWITCH(R, (launch_gather<RR, 3, true>(probs, act, nact, s))); break;
-        case 6: IMK_R_SWITCH(R, (launch_gather<RR, 6, true>(probs, act, nact, s))); break;
-        default: IMK_R_SWITCH(R, (launch_gather<RR, 4, true>(probs, act, nact, s))); break;
-    }
     if (pull_more) {
         IMK_R_SWITCH(R, (launch_gather<RR, 4, false>(probs, act, nact, s)));
     } else {
         IMK_R_SWITCH(R, (launch_push<RR, kPushMinBlocks>(probs, act, nact, true, s)));
     }
-    return 2;
+    return 1;
 }
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     IMK_R_SWITCH(R, (launch_combines<RR>(probs, act, nact, s)));
@@ -2565,11 +3120,24 @@ void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, c
 void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s) {
     k_frontier<<<g_sms * 3, kBlock, 0, s>>>(probs, act, nact, gb);  // 3 blocks an SM at its register count
 }
-void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+int launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_init<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
+    k_block_pairs<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);
+    k_block_done<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
+    return 3;
+}
+template <int R>
+static void launch_scan_r(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
+    static int grid = 0;  // one wave of this R's scan kernel (its register count sets the blocks per SM)
+    if (grid == 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scan<R>, kBlock, 0);
+        grid = g_sms * (occ > 0 ? occ : 1);
+    }
+    k_scan<R><<<grid, kBlock, 0, s>>>(probs, act, nact);
 }
 void launch_scan(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
-    IMK_R_SWITCH(R, (k_scan<RR><<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact)));
+    IMK_R_SWITCH(R, (launch_scan_r<RR>(probs, act, nact, s)));
 }
 int launch_celf(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_celf_max<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
@@ -2632,6 +3200,17 @@ void launch_validate(const int64_t *xadj, const int32_t *adj, int64_t n, int64_t
                      cudaStream_t s) {
     k_validate<<<g_grid_block, kBlock, 0, s>>>(xadj, adj, n, m, flags);
 }
+void launch_checksum(const void *x, uint64_t bytes, unsigned long long *out, cudaStream_t s) {
+    k_checksum<<<g_grid_block, kBlock, 0, s>>>(static_cast<const unsigned long long *>(x), bytes / 8, out);
+}
+void launch_graph_hash(const int64_t *xadj, const int32_t *adj, int64_t n, const uint32_t *T_edge,
+                       unsigned long long *out, cudaStream_t s) {
+    k_graph_hash<<<g_grid_warp, kBlock, 0, s>>>(xadj, adj, n, T_edge, out);
+}
+void launch_validate_undirected(const int64_t *xadj, const int32_t *adj, int64_t n, unsigned int *flags,
+                                cudaStream_t s) {
+    k_validate_undirected<<<g_grid_warp, kBlock, 0, s>>>(xadj, adj, n, flags);
+}
 void launch_edge_thresholds(const float *p, int64_t m, uint32_t *T, uint8_t *ok, unsigned int *flags,
                             cudaStream_t s) {
     if (m > 0) k_edge_thresholds<<<g_grid_block, kBlock, 0, s>>>(p, m, T, ok, flags);
@@ -2642,14 +3221,18 @@ void launch_live_masks(const DevProb &P, cudaStream_t s) {
 void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
     k_pair_counts<<<g_grid_block, kBlock, 0, s>>>(P, npairs, ndense);
 }
-void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint32_t *dlist, cudaStream_t s) {
-    k_pair_fill<<<g_grid_block, kBlock, 0, s>>>(P, pv, pj, dlist);
+void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint8_t *pr, uint32_t *dlist, cudaStream_t s) {
+    k_pair_fill<<<g_grid_block, kBlock, 0, s>>>(P, pv, pj, pr, dlist);
 }
 void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
     k_inpair_counts<<<g_grid_block, kBlock, 0, s>>>(P, npairs, ndense);
 }
-void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, int32_t *idu, uint32_t *ide, cudaStream_t s) {
-    k_inpair_fill<<<g_grid_block, kBlock, 0, s>>>(P, iu, ij, idu, ide);
+void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *iop, int32_t *idu, uint32_t *ide,
+                        cudaStream_t s) {
+    k_inpair_fill<<<g_grid_block, kBlock, 0, s>>>(P, iu, ij, iop, idu, ide);
+}
+void launch_inpair_targets(const DevProb &P, int32_t *iv, cudaStream_t s) {
+    k_inpair_targets<<<g_grid_warp, kBlock, 0, s>>>(P, iv);
 }
 void launch_vertex_desc(const DevProb &P, UnitD *vdesc, cudaStream_t s) {
     k_vertex_desc<<<g_grid_block, kBlock, 0, s>>>(P, vdesc);
@@ -2676,9 +3259,9 @@ void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s)
 void launch_wc_thresholds(const int32_t *indeg, int64_t n, uint32_t *T, cudaStream_t s) {
     k_wc_thresholds<<<g_grid_block, kBlock, 0, s>>>(indeg, n, T);
 }
-void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, unsigned long long *cursor,
+void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, int64_t m, unsigned long long *cursor,
                            int32_t *adj_in, uint32_t *ein, cudaStream_t s) {
-    k_transpose_fill<<<g_grid_warp, kBlock, 0, s>>>(xadj, adj, n, cursor, adj_in, ein);
+    if (m > 0) k_transpose_fill<<<g_sms * 4, kBlock, 0, s>>>(xadj, adj, n, m, cursor, adj_in, ein);
 }
 void launch_row_tasks(const int64_t *xadj, int64_t n, int32_t *ntask, uint32_t *heavy, cudaStream_t s) {
     k_row_tasks<<<g_grid_block, kBlock, 0, s>>>(xadj, n, ntask, heavy);

@@ -12,12 +12,17 @@ namespace imk {
 cudaError_t configure(int device);
 int grid_warp();
 
-void launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
-// One sweep: when a listed problem may start a diffusion (pulls), the fused first-sweep kernel and beside it the
-// push kernel (or, with pull_more, the kernel that also pulls later sweeps); else the push-only kernel.  Returns the
-// number of kernels launched.
+// Start of a diffusion (counters, bits, the vertices S reached, residual blocking in the problem's pair ranks).
+// Returns the launches.
+int launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
+// One sweep: when a listed problem may start a diffusion, launch_first (the fused first-sweep kernel) and then
+// launch_prop with pulls (the push kernel beside it, or with pull_more the kernel that also pulls later sweeps);
+// else launch_prop alone (the push-only kernel).  Each returns the number of kernels launched.
+int launch_first(int R, const DevProb *probs, const int32_t *act, int nact, int variant, cudaStream_t s);
 int launch_prop(int R, const DevProb *probs, const int32_t *act, int nact, bool pulls, bool pull_more,
                 cudaStream_t s);
+// Adds an order-free checksum of `bytes` bytes (a multiple of 8) at x to *out.
+void launch_checksum(const void *x, uint64_t bytes, unsigned long long *out, cudaStream_t s);
 void launch_combine(int R, const DevProb *probs, const int32_t *act, int nact, cudaStream_t s);
 // Ends a sweep: frontier lists and row copies, then (last block) the stop test and counter resets.
 void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar *gb, cudaStream_t s);
@@ -44,15 +49,20 @@ void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned 
 
 void launch_live_masks(const DevProb &P, cudaStream_t s);
 void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
-void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint32_t *dlist, cudaStream_t s);
+void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint8_t *pr, uint32_t *dlist, cudaStream_t s);
 void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
-void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, int32_t *idu, uint32_t *ide, cudaStream_t s);
+void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *iop, int32_t *idu, uint32_t *ide,
+                        cudaStream_t s);
 void launch_vertex_desc(const DevProb &P, UnitD *vdesc, cudaStream_t s);
+void launch_inpair_targets(const DevProb &P, int32_t *iv, cudaStream_t s);
 void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s);
 void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, cudaStream_t s);
+// Adds the graph's 64-bit fingerprint (edges and per-edge thresholds, if any) to *out.
+void launch_graph_hash(const int64_t *xadj, const int32_t *adj, int64_t n, const uint32_t *T_edge,
+                       unsigned long long *out, cudaStream_t s);
 void launch_indeg(const int32_t *adj, int64_t m, int32_t *indeg, cudaStream_t s);
 void launch_wc_thresholds(const int32_t *indeg, int64_t n, uint32_t *T, cudaStream_t s);
-void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, unsigned long long *cursor,
+void launch_transpose_fill(const int64_t *xadj, const int32_t *adj, int64_t n, int64_t m, unsigned long long *cursor,
                            int32_t *adj_in, uint32_t *ein, cudaStream_t s);
 void launch_row_tasks(const int64_t *xadj, int64_t n, int32_t *ntask, uint32_t *heavy, cudaStream_t s);
 void launch_classes(const int64_t *xadj, const int64_t *task_off, int64_t n, int32_t *task_row, int32_t *light,

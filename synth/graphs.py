@@ -135,6 +135,12 @@ def chung_lu(n: int, mean_degree: float, gamma: float, seed: int) -> Graph:
     return csr_from_edges(n, src, dst, name=f"chunglu_n{n}_d{mean_degree}_g{gamma}_s{seed}")
 
 
+def symmetrized(g: Graph) -> Graph:
+    """The undirected graph of g stored with both directions of every edge (rows sorted, repeats merged)."""
+    src, dst = g.edges()
+    return csr_from_edges(g.n, np.concatenate([src, dst]), np.concatenate([dst, src]), name=g.name + "_sym")
+
+
 def chain(n: int) -> Graph:
     """Directed path 0 -> 1 -> ... -> n-1."""
     return csr_from_edges(n, np.arange(n - 1), np.arange(1, n), name=f"chain{n}")

@@ -50,7 +50,7 @@ def test_structs_match_header_layout():
 
     text = open(os.path.join(ROOT, "include", "im.h")).read()
     for cname, py in [("im_graph", _lib.im_graph), ("im_params", _lib.im_params), ("im_trace", _lib.im_trace),
-                      ("im_stats", _lib.im_stats)]:
+                      ("im_stats", _lib.im_stats), ("im_tuning", _lib.im_tuning)]:
         plain = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + ";", plain).group(1)
         fields = re.findall(r"(\w+)\s*;", body)

@@ -128,6 +128,95 @@ def test_lazy_argmax_equals_full_scan(monkeypatch, gname, model, p, R):
     assert lazy["seeds"].tolist() == ref["seeds"].tolist()
 
 
+@pytest.mark.parametrize("gname,p,R", [("er2000", 0.03, 512), ("rmat12", 0.02, 256), ("rmat12", 0.01, 1024)])
+def test_streamed_push_equals_vertex_push(monkeypatch, gname, p, R):
+    """Push sweeps over a large L stream every in-pair when the sampled graph has no dense edges (small p, large R);
+    registers, sweeps, visits, frontiers and a whole selection equal the vertex-by-vertex push and the oracle."""
+    g = graphs.erdos_renyi(2000, 24000, seed=57) if gname == "er2000" else graphs.rmat(12, 16, seed=58)
+    graph = im.Graph.from_synth(g, IC, p)
+    outs = []
+    for env in ("0", "1"):
+        monkeypatch.setenv("IM_STREAM", env)
+        c = im.Context(0)
+        monkeypatch.delenv("IM_STREAM")
+        try:
+            sk = c.im_build_sketches(graph, im.params(R=R, seed=4))
+            info = sk.im_sketch_info()
+            outs.append((sk.im_sketch_registers(), info[0], info[1], info[2].tolist(),
+                         c.im_select_seeds(graph, im.params(R=R, K=6, eps_g=0.01, seed=4))))
+            sk.close()
+        finally:
+            c.close()
+    (M0, s0, v0, l0, sel0), (M1, s1, v1, l1, sel1) = outs
+    assert np.array_equal(M0, M1) and (s0, v0, l0) == (s1, v1, l1)
+    for k in ("seeds", "gsum", "rebuilt", "sigma"):
+        assert sel0[k].tolist() == sel1[k].tolist(), k
+    Mo, so, vo, lo = oracle.build_sketch(g.n, g.xadj, g.adj, IC, p, R, 4)
+    assert np.array_equal(M1, Mo) and (s1, v1) == (so, vo)
+
+
+@pytest.mark.parametrize("model,p,R", [(IC, 0.02, 256), (WC, 0.0, 128)])
+def test_autotuned_shapes_give_the_same_selection(model, p, R):
+    """The autotuner times every candidate launch shape on the first diffusion (it checks they agree) and keeps the
+    fastest for the graph's class; a selection under the chosen shape equals the oracle's."""
+    g = graphs.rmat(12, 16, seed=59)
+    graph = im.Graph.from_synth(g, model, p)
+    c = im.Context(0)
+    try:
+        t = c.im_autotune(graph, im.params(R=R, seed=4))
+        assert t["first_sweep_blocks"] in (3, 4, 6) and t["candidates"] >= 3
+        assert 0 < t["best_ms"] <= t["default_ms"]
+        out = c.im_select_seeds(graph, im.params(R=R, K=6, eps_g=0.01, seed=4))
+    finally:
+        c.close()
+    ref = oracle.select_seeds(g.n, g.xadj, g.adj, model, p, R, 6, 0.01, 0.3, 0.0, 4)
+    assert out["seeds"].tolist() == ref["seeds"].tolist()
+    assert out["sigma"].tolist() == ref["sigma"].tolist()
+
+
+# --- literal blocking and undirected inputs ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("eps", [(0.0, 0.0), (0.01, 0.3)], ids=["always", "paper"])
+@pytest.mark.parametrize("gname,model,p,R", [("er300", IC, 0.05, 256), ("rmat10", WC, 0.0, 128),
+                                             ("hub1500", IC, 0.3, 64), ("er300", IC, 0.05, 512)])
+def test_select_literal_blocking(ctx, eps, gname, model, p, R):
+    """Algorithms 1 and 2 as printed: blocked registers keep their rank and are never updated (reading R17)."""
+    g = SMALL[gname]
+    assert_select_parity(ctx, g, model, p, R, K=8, eps_g=eps[0], eps_l=eps[1], seed=21, literal=True)
+
+
+def test_select_literal_heavy_rows(ctx):
+    g = graphs.rmat(12, 16, seed=43)
+    assert_select_parity(ctx, g, WC, 0.0, 256, K=10, eps_g=0.0, eps_l=0.0, seed=4, literal=True, device="cuda")
+
+
+UNDIRECTED = {
+    "rmat11s": graphs.symmetrized(graphs.rmat(11, 8, seed=51)),
+    "er500s": graphs.symmetrized(graphs.erdos_renyi(500, 2000, seed=52)),
+    "hub1500s": graphs.symmetrized(graphs.star_hub(1500, seed=5)),
+}
+
+
+@pytest.mark.parametrize("R", [64, 256, 512])
+@pytest.mark.parametrize("gname,model,p", [("rmat11s", IC, 0.05), ("er500s", IC, 0.2), ("hub1500s", WC, 0.0)])
+def test_registers_undirected(ctx, R, gname, model, p):
+    """Undirected inputs: both directions share the hash key (min, max) (reading R16)."""
+    assert_build_parity(ctx, UNDIRECTED[gname], model, p, R, seed=9 + R, undirected=True)
+
+
+@pytest.mark.parametrize("gname,model,p,R", [("rmat11s", IC, 0.05, 128), ("er500s", IC, 0.1, 256),
+                                             ("hub1500s", WC, 0.0, 64)])
+def test_select_undirected(ctx, gname, model, p, R):
+    assert_select_parity(ctx, UNDIRECTED[gname], model, p, R, K=8, eps_g=0.01, seed=3, undirected=True)
+
+
+def test_undirected_input_must_be_symmetric(ctx):
+    g = graphs.rmat(9, 8, seed=53)  # directed: some (u, v) has no (v, u)
+    with pytest.raises(im.ImError) as err:
+        ctx.im_build_sketches(im.Graph.from_synth(g, IC, 0.1, undirected=True), im.params(R=64))
+    assert err.value.status == 1 and "(v, u)" in str(err.value)
+
+
 # --- edge cases -------------------------------------------------------------------------------------------------
 
 def test_single_vertex(ctx):

@@ -1,9 +1,11 @@
-"""Serving loop: queries answered in a continuously batched mix give exactly what they give alone."""
+"""Serving loop: queries answered in a continuously batched mix give exactly what they give alone, and what the
+CPU oracle's Algorithm 1 gives for the same graph and parameters."""
 from __future__ import annotations
 
 import numpy as np
 import pytest
 
+import oracle
 from synth import graphs
 
 import paper_2105_04023_gb300 as im
@@ -25,7 +27,8 @@ def ctx():
 
 POOL = [(graphs.rmat(10, 12, seed=71), WC, 0.0), (graphs.rmat(11, 8, seed=72), IC, 0.05),
         (graphs.erdos_renyi(700, 5000, seed=73), IC, 0.1), (graphs.star_hub(800, seed=74), WC, 0.0)]
-QUERIES = [(i % 4, 3 + (i * 5) % 9, (64, 256, 128)[i % 3], 100 + i) for i in range(14)]
+# (graph, K, R, seed, literal blocking)
+QUERIES = [(i % 4, 3 + (i * 5) % 9, (64, 256, 128)[i % 3], 100 + i, i % 5 == 4) for i in range(14)]
 
 
 def _graph(i):
@@ -33,8 +36,30 @@ def _graph(i):
     return im.Graph.from_synth(g, model, p)
 
 
-def _alone(ctx, gid, K, R, seed):
-    return ctx.im_select_seeds(_graph(gid), im.params(R=R, K=K, eps_g=0.01, eps_l=0.3, seed=seed), trace=False)
+def _prm(K, R, seed, literal=False):
+    return im.params(R=R, K=K, eps_g=0.01, eps_l=0.3, seed=seed,
+                     blocking=im.IM_BLOCK_LITERAL if literal else im.IM_BLOCK_RESIDUAL)
+
+
+def _alone(ctx, gid, K, R, seed, literal=False):
+    return ctx.im_select_seeds(_graph(gid), _prm(K, R, seed, literal), trace=False)
+
+
+def _oracle(gid, K, R, seed, literal=False):
+    g, model, p = POOL[gid]
+    return oracle.select_seeds(g.n, g.xadj, g.adj, model, p, R, K, 0.01, 0.3, 0.0, seed, literal=literal)
+
+
+def _check(res, q, ctx):
+    """A served result equals the same query alone on the GPU and the oracle's selection."""
+    alone = _alone(ctx, *q)
+    assert res["seeds"].tolist() == alone["seeds"].tolist(), q
+    assert res["sigma_final"] == alone["sigma_final"]
+    assert res["rebuilds"] == alone["rebuilds"]
+    ref = _oracle(*q)
+    assert res["seeds"].tolist() == ref["seeds"].tolist(), q
+    assert res["sigma_final"] == float(ref["sigma"][-1])
+    assert res["rebuilds"] == int(ref["rebuilt"].sum())
 
 
 def _drain(srv, tickets, max_steps=100000):
@@ -57,18 +82,15 @@ def test_mix_equals_alone_with_late_arrivals(ctx):
     tickets = {}
     first = QUERIES[: len(QUERIES) // 2]
     for q in first:
-        tickets[srv.im_server_submit(gids[q[0]], im.params(R=q[2], K=q[1], eps_g=0.01, seed=q[3]))] = q
+        tickets[srv.im_server_submit(gids[q[0]], _prm(*q[1:]))] = q
     # a few ticks with the first half running, then the rest arrive and join the batch
     for _ in range(5):
         srv.im_server_step()
     for q in QUERIES[len(QUERIES) // 2:]:
-        tickets[srv.im_server_submit(gids[q[0]], im.params(R=q[2], K=q[1], eps_g=0.01, seed=q[3]))] = q
+        tickets[srv.im_server_submit(gids[q[0]], _prm(*q[1:]))] = q
     res = _drain(srv, set(tickets))
     for t, q in tickets.items():
-        alone = _alone(ctx, *q)
-        assert res[t]["seeds"].tolist() == alone["seeds"].tolist(), q
-        assert res[t]["sigma_final"] == alone["sigma_final"]
-        assert res[t]["rebuilds"] == alone["rebuilds"]
+        _check(res[t], q, ctx)
     srv.close()
 
 
@@ -95,7 +117,7 @@ def test_budget_limits_admission(ctx):
             break
     assert max(seen_active) == 1
     for t, s in tickets.items():
-        assert res[t]["seeds"].tolist() == _alone(ctx, 0, 4, 256, s)["seeds"].tolist()
+        _check(res[t], (0, 4, 256, s), ctx)
     srv.close()
 
 
@@ -107,8 +129,8 @@ def test_cancel_and_over_budget(ctx):
     t3 = srv.im_server_submit(gid, im.params(R=64, K=3, eps_g=0.01, seed=7))
     srv.im_server_cancel(t2)  # still queued
     res = _drain(srv, {t1, t3})
-    assert res[t1]["seeds"].tolist() == _alone(ctx, 1, 3, 64, 5)["seeds"].tolist()
-    assert res[t3]["seeds"].tolist() == _alone(ctx, 1, 3, 64, 7)["seeds"].tolist()
+    _check(res[t1], (1, 3, 64, 5), ctx)
+    _check(res[t3], (1, 3, 64, 7), ctx)
     with pytest.raises(im.ImError) as ei:
         srv.im_server_poll(t2)
     assert ei.value.status == im._lib.IM_ECANCELED
@@ -128,7 +150,7 @@ def test_cancel_running_query_frees_its_slot(ctx):
     assert active == 1 and queued == 1
     srv.im_server_cancel(t1)
     res = _drain(srv, {t2})
-    assert res[t2]["seeds"].tolist() == _alone(ctx, 0, 2, 64, 10)["seeds"].tolist()
+    _check(res[t2], (0, 2, 64, 10), ctx)
     srv.close()
 
 
@@ -137,11 +159,12 @@ def test_repeated_first_diffusions_are_reused(ctx):
     # answer alone; a different seed or R does not hit
     srv = im.Server(ctx, hbm_budget_bytes=8 << 30, max_active=4)
     gids = [srv.im_server_add_graph(_graph(i)) for i in range(2)]
-    first = [(0, 6, 256, 31), (1, 4, 64, 32)]
-    rest = [(0, 9, 256, 31), (0, 3, 256, 31), (1, 7, 64, 32), (0, 5, 128, 31), (1, 2, 64, 33), (0, 8, 256, 31)]
+    first = [(0, 6, 256, 31, False), (1, 4, 64, 32, False)]
+    rest = [(0, 9, 256, 31, False), (0, 3, 256, 31, True), (1, 7, 64, 32, False), (0, 5, 128, 31, False),
+            (1, 2, 64, 33, False), (0, 8, 256, 31, False)]
     res, tickets = {}, {}
     for batch in (first, rest):
-        ts = {srv.im_server_submit(gids[q[0]], im.params(R=q[2], K=q[1], eps_g=0.01, seed=q[3])): q for q in batch}
+        ts = {srv.im_server_submit(gids[q[0]], _prm(*q[1:])): q for q in batch}
         res.update(_drain(srv, set(ts)))
         tickets.update(ts)
     info = srv.im_server_info()
@@ -149,8 +172,5 @@ def test_repeated_first_diffusions_are_reused(ctx):
     assert info["kept_builds"] == 4, info  # one per distinct (graph, R, seed)
     assert info["used_bytes"] > 0
     for t, q in tickets.items():
-        alone = _alone(ctx, *q)
-        assert res[t]["seeds"].tolist() == alone["seeds"].tolist(), q
-        assert res[t]["sigma_final"] == alone["sigma_final"]
-        assert res[t]["rebuilds"] == alone["rebuilds"]
+        _check(res[t], q, ctx)
     srv.close()

@@ -132,7 +132,8 @@ struct DevProb {
     const int64_t *dofs;       // m+1: dense edges before each edge
     const int32_t *pv;         // per pair: target vertex
     const uint16_t *pj;        // per pair: simulation
-    const uint8_t *pr;         // per pair: the initial rank of (target, simulation), read by the first sweep
+    const uint16_t *pq;        // per pair, for the first sweep: sw_slot(simulation, 0) | initial rank of (target,
+                               // simulation) << 10 (R <= 1024, ranks <= 32)
     const uint32_t *iop;       // per in-pair: the index of the same pair in out-CSR order
     const uint32_t *dlist;     // dense edge ids, in edge order
     // the same pairs and dense edges by target: per in-edge of the in-CSR
@@ -153,7 +154,7 @@ struct DevProb {
 
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
     uint32_t *rany;            // bit per vertex: reached by S in some simulation (set at a rebuild; NULL: no search)
-    uint8_t *prb;              // residual blocking: this problem's copy of pr with the pairs of blocked (v, j) at 0
+    uint16_t *pqb;             // residual blocking: this problem's copy of pq with the ranks of blocked (v, j) at 0
     uint32_t *vis_done;        // n x W: the blocked bits already applied to prb
     uint32_t *rnew;            // bit per vertex: has bits in vis not yet in vis_done (set by k_init)
     uint32_t *del[3];          // n x W: bits newly reached at the previous level, by level mod 3

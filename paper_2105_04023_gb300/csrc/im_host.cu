@@ -388,7 +388,7 @@ void sample_edges(im_ctx *ctx, Prob &P) {
         d.pv = d.iu = d.iv = mem.alloc<int32_t>(1);
         d.stream_min = ~0ull;
         d.pj = d.ij = mem.alloc<uint16_t>(1);
-        d.pr = mem.alloc<uint8_t>(1);
+        d.pq = mem.alloc<uint16_t>(1);
         d.dlist = d.ide = mem.alloc<uint32_t>(1);
         d.idu = mem.alloc<int32_t>(1);
         UnitD *vd0 = mem.alloc<UnitD>(static_cast<size_t>(std::max<int64_t>(P.G->n, 1)), true);
@@ -416,14 +416,14 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     mem.release(bsums);
     int32_t *pv = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
     uint16_t *pj = mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
-    uint8_t *pr = mem.alloc<uint8_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
+    uint16_t *pq = mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
     uint32_t *dlist = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
-    launch_pair_fill(d, pv, pj, pr, dlist, s);
+    launch_pair_fill(d, pv, pj, pq, dlist, s);
     launch_unit_desc(d, rdesc, tdesc, s);
     ctx->launches += 2;
     d.pv = pv;
     d.pj = pj;
-    d.pr = pr;
+    d.pq = pq;
     d.dlist = dlist;
     P.npairs = tot[0];
     P.ndense = tot[1];
@@ -479,7 +479,7 @@ void copy_sample_fields(DevProb &d, const DevProb &src) {
     d.tdesc = src.tdesc;
     d.pv = src.pv;
     d.pj = src.pj;
-    d.pr = src.pr;
+    d.pq = src.pq;
     d.dlist = src.dlist;
     d.ipofs = src.ipofs;
     d.idofs = src.idofs;
@@ -588,9 +588,10 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
         d.gst = mem.alloc<uint32_t>(static_cast<size_t>(n));
         // residual blocking applied to a copy of the pair ranks at each rebuild (the first sweep then tests nothing)
         if (d.iop && prm.blocking == IM_BLOCK_RESIDUAL && P->npairs > 0) {
-            d.prb = mem.alloc<uint8_t>(static_cast<size_t>(P->npairs));
-            ck(cudaMemcpyAsync(d.prb, d.pr, static_cast<size_t>(P->npairs), cudaMemcpyDeviceToDevice, ctx->stream),
-               "copy pair ranks");
+            d.pqb = mem.alloc<uint16_t>(static_cast<size_t>(P->npairs));
+            ck(cudaMemcpyAsync(d.pqb, d.pq, static_cast<size_t>(P->npairs) * sizeof(uint16_t), cudaMemcpyDeviceToDevice,
+                               ctx->stream),
+               "copy pair words");
             d.vis_done = mem.alloc<uint32_t>(static_cast<size_t>(n) * (R / 32), true);
             d.rnew = mem.alloc<uint32_t>(words, true);
         }
@@ -1442,7 +1443,7 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     b += r(4 * n * W) * 4 + r(4 * words) * 2 + r(4 * n) * 4;  // reach and delta bits, seed-set and reached-vertex
                                                                  // bits, stamps, frontiers
     b += r(4 * n);                                           // bounds of the lazy argmax
-    b += r(4 * n * W) + r(4 * words);                        // blocked bits applied to the pair ranks, new ones
+    b += r(4 * n * W) + r(4 * words);                        // blocked bits applied to the pair words, new ones
     b += r(sizeof(int4) * (n + static_cast<uint64_t>(g.m) / kBfsTaskEdgesMin + 1)) * 2;  // search tasks
     const uint64_t m1 = std::max<uint64_t>(static_cast<uint64_t>(g.m), 1);
     b += r(4 * W * m1);                                      // live-simulation masks of the edges
@@ -1451,8 +1452,9 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     // pairs: at most dense_min per edge (6 bytes each), dense edges 4 bytes; the counts and scan sums of the
     // preparation are freed before the pairs are allocated, and are smaller
     const uint64_t pmax = m1 * static_cast<uint64_t>(dense_min_for(prm.R));
-    b += (r(4 * pmax) + r(2 * pmax)) * 2 + r(pmax) * 2 + r(4 * pmax) * 2 + r(4 * m1) * 3;  // pairs both ways with
-        // the out-pairs' ranks (and the query's copy), the in-pairs' targets and out-pair indices, dense edges
+    b += (r(4 * pmax) + r(2 * pmax)) * 2 + r(2 * pmax) * 2 + r(4 * pmax) * 2 + r(4 * m1) * 3;  // pairs both ways
+        // with the out-pairs' first-sweep words (and the query's copy), the in-pairs' targets and out-pair indices,
+        // dense edges
     b += r(sizeof(UnitD) * std::max<uint64_t>(n, 1));       // push-unit descriptors
     b += r(4 * static_cast<uint64_t>(prm.K)) * 2;            // step records
     return b;

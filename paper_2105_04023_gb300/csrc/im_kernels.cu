@@ -204,23 +204,30 @@ __device__ __forceinline__ uint4 init_chunk(const uint32_t *Y, uint32_t hv, int 
 }
 
 // Shared-memory slot of simulation j in a per-simulation word array (a tile's accumulators, the staged Y words):
-// the four 16-byte words of each 16-simulation chunk are stored rotated by the chunk index plus rot, so that when
-// lane li reads word w of its own chunk (a 64-byte stride between lanes) the lanes spread over all banks instead of
-// two (a 16-way conflict without the rotation).
+// the four 16-byte words of each 16-simulation chunk ch are permuted by XOR with (ch / 2 XOR 2 rot) mod 4.  A 16-byte
+// load is served eight lanes at a time, and eight lanes reading word w of chunks ch .. ch + 7 (a 64-byte stride)
+// then cover the eight 16-byte bank groups once each: ch mod 2 picks the half of the 128 bytes, the permutation the
+// group within it (without it the eight lanes fall on two groups, a 4-way conflict).  2 rot separates the two
+// 4-lane tiles that share a load when a tile is 4 lanes wide (R = 64).  The map is its own inverse, and
+// sw_slot(j, rot) = sw_slot(j, 0) XOR sw_tile(rot).
+__device__ __forceinline__ uint32_t sw_tile(uint32_t rot) { return ((2u * rot) & 3u) << 2; }
 __device__ __forceinline__ uint32_t sw_slot(uint32_t j, uint32_t rot) {
-    return (j & ~15u) | ((((j >> 2) + (j >> 4) + rot) & 3u) << 2) | (j & 3u);
+    return j ^ (((j >> 5) & 3u) << 2) ^ sw_tile(rot);
 }
+// Position of word w of chunk ch among the chunk's four 16-byte words under sw_slot(., rot).
+__device__ __forceinline__ int sw_pos(int w, int ch, int rot) { return (w ^ (ch >> 1) ^ (2 * rot)) & 3; }
 
-// init_chunk over Y words staged in shared memory with sw_slot(j, 0).
+// init_chunk over Y words staged in shared memory with sw_slot(j, 0); without BLK nothing is blocked (blk unused).
+template <bool BLK = true>
 __device__ __forceinline__ uint4 init_chunk_sw(const uint32_t *Ysw, uint32_t hv, int ch, uint32_t blk) {
     const uint4 *y = reinterpret_cast<const uint4 *>(Ysw + 16 * ch);
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const uint4 q = y[(k + ch) & 3];
+        const uint4 q = y[sw_pos(k, ch, 0)];
         const uint32_t x = __clz(hv ^ q.x) | (__clz(hv ^ q.y) << 8) | (__clz(hv ^ q.z) << 16) |
                            (__clz(hv ^ q.w) << 24);
-        w[k] = x & ~nibble_bytes((blk >> (4 * k)) & 0xFu);
+        w[k] = BLK ? x & ~nibble_bytes((blk >> (4 * k)) & 0xFu) : x;
     }
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
@@ -346,44 +353,44 @@ __device__ __forceinline__ uint32_t sparse_tile(const DevProb &P, int64_t p0, in
 }
 
 // The first sweep's sparse pairs [p0, p1): each pair's candidate is the initial rank of (v, j), kept per pair since
-// sampling (pr, or the problem's copy prb whose blocked pairs k_block_pairs set to 0), so only (j, rank) are read;
-// a rank of 0 changes nothing.  Without prb, a rebuild (chk) reads the pair's v too and a blocked (v, j) gives 0
-// (residual blocking; literal blocking keeps the rank).
+// sampling in one 16-bit word with the simulation's accumulator slot (pq, or the problem's copy pqb whose blocked
+// pairs k_block_pairs set to rank 0), so one load serves a pair; a rank of 0 changes nothing.  Without pqb, a
+// rebuild (chk) reads the pair's v too and a blocked (v, j) gives 0 (residual blocking; literal blocking keeps the
+// rank).
 template <int R>
 __device__ __forceinline__ void sparse_tile_init(const DevProb &P, int64_t p0, int64_t p1, bool chk,
                                                  uint32_t *acc32, int li) {
     constexpr int G = Geo<R>::G;
-    const uint32_t g = static_cast<uint32_t>((threadIdx.x & 31) / G);
-    // the problem's own ranks, with blocked pairs already 0, when it keeps them; else the sampled graph's, tested
-    const uint8_t *rk = P.prb ? P.prb : P.pr;
-    const bool test = chk && !P.literal && !P.prb;
+    const uint32_t tx = sw_tile(static_cast<uint32_t>((threadIdx.x & 31) / G));
+    const uint16_t *pq = P.pqb ? P.pqb : P.pq;
+    const bool test = chk && !P.literal && !P.pqb;
     for (int64_t p = p0 + li; p < p1; p += 4 * G) {
-        uint32_t j[4], x[4];
+        uint32_t x[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int64_t q = p + G * k;
-            const bool ok = q < p1;
-            j[k] = ok ? __ldg(&P.pj[q]) : 0u;
-            x[k] = ok ? __ldg(&rk[q]) : 0u;
+            x[k] = q < p1 ? __ldg(&pq[q]) : 0u;
         }
         if (test) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (x[k]) {
+                if (x[k] >> 10) {
                     const int32_t v = __ldg(&P.pv[p + G * k]);
-                    if (test_bit(P.rany, v) &&
-                        ((__ldg(&P.vis[static_cast<size_t>(v) * P.W + (j[k] >> 5)]) >> (j[k] & 31)) & 1u))
+                    const uint32_t j = sw_slot(x[k] & 0x3FFu, 0);  // the slot map is its own inverse
+                    if (test_bit(P.rany, v) && ((__ldg(&P.vis[static_cast<size_t>(v) * P.W + (j >> 5)]) >> (j & 31)) & 1u))
                         x[k] = 0;
                 }
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (x[k]) atomicMax(&acc32[sw_slot(j[k], g)], x[k]);
+            if (x[k] >> 10) atomicMax(&acc32[(x[k] & 0x3FFu) ^ tx], x[k] >> 10);
     }
 }
 
-// Adds the tile's sparse accumulators into acc and clears them.
-template <int R>
+// Adds the tile's sparse accumulators into acc (ASSIGN: acc is still zero, so they are copied) and clears them:
+// each lane clears exactly the chunks it read, so one barrier before (the tile's atomics are done) and one after
+// (the zeros land before the next unit's atomics) suffice.
+template <int R, bool ASSIGN = false>
 __device__ __forceinline__ void fold_tile(uint32_t (&acc)[Geo<R>::CPL][4], uint32_t *acc32, unsigned tm, int li) {
     using Gm = Geo<R>;
     const int g = (threadIdx.x & 31) / Gm::G;
@@ -391,16 +398,16 @@ __device__ __forceinline__ void fold_tile(uint32_t (&acc)[Geo<R>::CPL][4], uint3
 #pragma unroll
     for (int c = 0; c < Gm::CPL; ++c) {
         const int ch = li + Gm::G * c;
-        const uint4 *a = reinterpret_cast<const uint4 *>(acc32 + 16 * ch);
+        uint4 *a = reinterpret_cast<uint4 *>(acc32 + 16 * ch);
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            const uint4 q = a[(w + ch + g) & 3];  // slots laid out by sw_slot(j, g)
-            acc[c][w] = vmax4(acc[c][w], q.x | (q.y << 8) | (q.z << 16) | (q.w << 24));
+            const int pos = sw_pos(w, ch, g);  // slots laid out by sw_slot(j, g)
+            const uint4 q = a[pos];
+            const uint32_t x = q.x | (q.y << 8) | (q.z << 16) | (q.w << 24);
+            acc[c][w] = ASSIGN ? x : vmax4(acc[c][w], x);
+            a[pos] = make_uint4(0, 0, 0, 0);
         }
     }
-    __syncwarp(tm);
-    uint4 *z = reinterpret_cast<uint4 *>(acc32);
-    for (int k = li; k < R / 4; k += Gm::G) z[k] = make_uint4(0, 0, 0, 0);
     __syncwarp(tm);
 }
 
@@ -606,7 +613,7 @@ __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W,
                 nPairs = sparse_tile<R, INIT>(P, cur.p0, cur.p0 + cur.np, allL, Lcur, Mcur, Ys, acc32, li);
                 nPairs = __reduce_add_sync(tm, nPairs);
             }
-            fold_tile<R>(acc, acc32, tm, li);
+            fold_tile<R, true>(acc, acc32, tm, li);
         }
         const uint32_t nTaken =
             cur.nd > 0 ? dense_tile<R, INIT>(P, cur.d0, cur.d0 + cur.nd, allL, Lcur, Mcur, Ys, chk, acc, li) : 0u;
@@ -638,42 +645,74 @@ __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W,
     flush_stats(P.ctr, st, li);
 }
 
+// Row u of the first sweep: M_u = max(initial ranks own, merged acc), written to both register buffers, with its
+// change mask (the registers raised above their initial rank, which the next sweep pushes); u joins L' if any
+// register rose.  Per byte, own + 128 - acc has bit 7 set exactly where own >= acc (every register is <= 32, so no
+// byte borrows): one word gives both the max and the change bits.
+template <int R>
+__device__ __forceinline__ void finalize_first(const DevProb &P, int64_t u, const uint32_t (&acc)[Geo<R>::CPL][4],
+                                               const uint4 (&own)[Geo<R>::CPL], uint32_t *__restrict__ Lnext,
+                                               unsigned tm, int li) {
+    using Gm = Geo<R>;
+    uint32_t any = 0;
+#pragma unroll
+    for (int c = 0; c < Gm::CPL; ++c) {
+        const int ch = li + Gm::G * c;
+        const uint32_t o[4] = {own[c].x, own[c].y, own[c].z, own[c].w};
+        uint32_t nw[4], bits = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint32_t x = o[w] + 0x80808080u - acc[c][w];
+            const uint32_t ge = sign_bytes(x, 0u, 0xBA98u);
+            nw[w] = (o[w] & ge) | (acc[c][w] & ~ge);
+            bits |= ((((~x >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * w);
+        }
+        const uint4 v = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+        reinterpret_cast<uint4 *>(P.M1 + static_cast<size_t>(u) * R)[ch] = v;
+        reinterpret_cast<uint4 *>(P.M0 + static_cast<size_t>(u) * R)[ch] = v;
+        P.dmask[static_cast<size_t>(u) * Gm::CH + ch] = static_cast<uint16_t>(bits);
+        any |= bits;
+    }
+    if (__any_sync(tm, any != 0u) && li == 0) set_bit(Lnext, u);
+}
+
 // The first sweep of one problem over this tile's units (every row, then every task), software-pipelined: while a
 // unit is processed, the pair records and ranks of the next unit's first 4 G pairs and the descriptor of the unit
 // after it are already in flight, so the chain descriptor -> pairs -> merge of one unit overlaps the previous one.
-// The descriptors wait in a per-tile ring of three in shared memory (ring: 3 x 8 words), loaded a word a lane, and
-// each prefetched pair is one word (simulation | rank << 16), to keep the registers few.
+// The descriptors wait in a per-tile ring of three in shared memory (ring: 3 x 8 words, 16-byte aligned), loaded a
+// word a lane, and each prefetched pair is one word (simulation | rank << 16), to keep the registers few.  A row's
+// own initial ranks are formed after its merges, when fewer registers are live.
 template <int R>
 __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, uint64_t nworkers, unsigned tm,
                                 int li, uint32_t *acc32, const uint32_t *Ys, uint32_t *ring) {
     using Gm = Geo<R>;
     constexpr int G = Gm::G;
     constexpr int DW = sizeof(UnitD) / 4;  // descriptor words
+    constexpr int NW = (DW + G - 1) / G;   // descriptor words a lane moves
     static_assert(DW == 8, "descriptor of 8 words");
     const uint64_t n = static_cast<uint64_t>(P.n);
-    uint8_t *Mnext = P.M1;  // sweep 0 writes buffer 1, and buffer 0 too (both start as its result)
-    uint8_t *Mother = P.M0;
-    uint32_t *Lnext = P.Lb1;
     const uint64_t tb = thr_bytes(P.model);
-    const uint8_t *rk = P.prb ? P.prb : P.pr;
+    const uint16_t *pq = P.pqb ? P.pqb : P.pq;
     const bool rebuild = P.rany && P.ctr->lvl != 0;  // some vertices are blocked
     // a rebuild without the problem's own blocked ranks tests each pair's neighbour (residual blocking only)
-    const bool test = rebuild && !P.prb && !P.literal;
-    const uint32_t g = static_cast<uint32_t>((threadIdx.x & 31) / G);
-    Stats st;
+    const bool test = rebuild && !P.pqb && !P.literal;
+    const bool zero_own = rebuild && !P.literal;  // residual blocking: a blocked register of the row is 0
+    const bool keep_own = rebuild && P.literal;   // literal blocking: a blocked register is never raised
+    const uint32_t tx = sw_tile(static_cast<uint32_t>((threadIdx.x & 31) / G));  // this tile's slot permutation
+    unsigned long long pairs = 0, bytes = 0;  // counted by lane 0 of the tile
     // this lane's words (li, li + G, ...) of descriptor l (zeros past the end)
-    auto load_desc = [&](uint64_t l, uint32_t (&w)[(DW + G - 1) / G]) {
+    auto load_desc = [&](uint64_t l, uint32_t (&w)[NW]) {
         const uint32_t *src = l < cnt ? reinterpret_cast<const uint32_t *>(l < n ? P.rdesc + l : P.tdesc + (l - n))
                                       : nullptr;
 #pragma unroll
-        for (int k = 0; k < (DW + G - 1) / G; ++k) {
+        for (int k = 0; k < NW; ++k) {
             const int wi = li + G * k;
             w[k] = (src && wi < DW) ? __ldg(src + wi) : 0u;
         }
     };
-    auto store_desc = [&](int slot, const uint32_t (&w)[(DW + G - 1) / G]) {
+    auto store_desc = [&](int slot, const uint32_t (&w)[NW]) {
 #pragma unroll
-        for (int k = 0; k < (DW + G - 1) / G; ++k) {
+        for (int k = 0; k < NW; ++k) {
             const int wi = li + G * k;
             if (wi < DW) ring[slot * DW + wi] = w[k];
         }
@@ -684,27 +723,26 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
         int32_t u;
     };
     auto read_desc = [&](int slot) {
-        const uint32_t *r = ring + slot * DW;
+        const uint4 *r = reinterpret_cast<const uint4 *>(ring + slot * DW);
+        const uint4 a = r[0], b = r[1];
         D d;
-        d.p0 = static_cast<int64_t>((static_cast<uint64_t>(r[1]) << 32) | r[0]);
-        d.d0 = static_cast<int64_t>((static_cast<uint64_t>(r[3]) << 32) | r[2]);
-        d.np = r[4];
-        d.nd = r[5];
-        d.u = static_cast<int32_t>(r[6]);
+        d.p0 = static_cast<int64_t>((static_cast<uint64_t>(a.y) << 32) | a.x);
+        d.d0 = static_cast<int64_t>((static_cast<uint64_t>(a.w) << 32) | a.z);
+        d.np = b.x;
+        d.nd = b.y;
+        d.u = static_cast<int32_t>(b.z);
         return d;
     };
-    // the first 4 G pairs of unit d, this lane's share: simulation | rank << 16 (rank 0 past the unit's end)
+    // the first 4 G pair words of unit d, this lane's share (rank 0 past the unit's end)
     auto batch = [&](const D &d, uint32_t (&b)[4]) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const uint32_t o = li + G * k;
-            b[k] = o < d.np ? (static_cast<uint32_t>(__ldg(&P.pj[d.p0 + o])) |
-                               (static_cast<uint32_t>(__ldg(&rk[d.p0 + o])) << 16))
-                            : 0u;
+            b[k] = o < d.np ? static_cast<uint32_t>(__ldg(&pq[d.p0 + o])) : 0u;
         }
     };
     {
-        uint32_t w[(DW + G - 1) / G];
+        uint32_t w[NW];
         load_desc(first, w);
         store_desc(0, w);
         load_desc(first + nworkers, w);
@@ -719,17 +757,10 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
         const D cur = read_desc(slot);
         uint32_t nb[4];
         batch(read_desc(s1), nb);                 // the next unit's first pairs
-        uint32_t wn[(DW + G - 1) / G];
+        uint32_t wn[NW];
         load_desc(l + 2 * nworkers, wn);          // and the descriptor after it
         const bool is_row = l < n;
         if (!(is_row && cur.u < 0)) {  // a split row is left to its tasks and the combine kernels
-            const int64_t u = cur.u;
-            uint4 own[Gm::CPL];
-            const uint32_t hu = vertex_hash(static_cast<uint32_t>(u));
-#pragma unroll
-            for (int c = 0; c < Gm::CPL; ++c)
-                own[c] = is_row ? init_chunk_sw(Ys, hu, li + G * c, init_blocked16(P, u, li + G * c))
-                                : make_uint4(0, 0, 0, 0);
             uint32_t acc[Gm::CPL][4];
 #pragma unroll
             for (int c = 0; c < Gm::CPL; ++c)
@@ -741,33 +772,37 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
                 } else {
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        if (cb[k] >> 16) atomicMax(&acc32[sw_slot(cb[k] & 0xFFFFu, g)], cb[k] >> 16);
+                        if (cb[k] >> 10) atomicMax(&acc32[(cb[k] & 0x3FFu) ^ tx], cb[k] >> 10);
                     if (cur.np > 4 * G) sparse_tile_init<R>(P, cur.p0 + 4 * G, cur.p0 + cur.np, false, acc32, li);
                 }
-                fold_tile<R>(acc, acc32, tm, li);
+                fold_tile<R, true>(acc, acc32, tm, li);
             }
-            const uint32_t nTaken = cur.nd > 0 ? dense_tile<R, true>(P, cur.d0, cur.d0 + cur.nd, true, nullptr,
-                                                                     nullptr, Ys, rebuild, acc, li)
-                                               : 0u;
-            // modelled bytes: descriptor, pair records (simulation, rank), dense edges (id, target, threshold,
-            // mask); the rows' writes are counted by finalize_tile
+            if (cur.nd > 0)
+                dense_tile<R, true>(P, cur.d0, cur.d0 + cur.nd, true, nullptr, nullptr, Ys, rebuild, acc, li);
+            // modelled bytes: descriptor, pair words (slot, rank), dense edges (id, target, threshold, mask), and
+            // the row written to both buffers with its change mask (or a task's partial row)
             if (li == 0) {
-                st.pairs += cur.np;
-                st.bytes += 32 + 3 * static_cast<uint64_t>(cur.np) + (8 + tb + R / 8) * static_cast<uint64_t>(cur.nd);
+                pairs += cur.np;
+                bytes += 32 + 2 * static_cast<uint64_t>(cur.np) + (8 + tb + R / 8) * static_cast<uint64_t>(cur.nd) +
+                         (is_row ? 2 * R + R / 8 : (cur.np + cur.nd > 0 ? R : 0));
             }
             if (is_row) {
-                drop_blocked<R>(P, u, acc, li);
-                finalize_tile<R>(P, u, acc, true, false, own, Mnext, Mother, Lnext, tm, li, st);
-            } else if (cur.np + nTaken > 0) {
+                const int64_t u = cur.u;
+                const uint32_t hu = vertex_hash(static_cast<uint32_t>(u));
+                uint4 own[Gm::CPL];
+#pragma unroll
+                for (int c = 0; c < Gm::CPL; ++c)
+                    own[c] = zero_own ? init_chunk_sw<true>(Ys, hu, li + G * c, blocked16(P, u, li + G * c))
+                                      : init_chunk_sw<false>(Ys, hu, li + G * c, 0u);
+                if (keep_own) drop_blocked<R>(P, u, acc, li);
+                finalize_first<R>(P, u, acc, own, P.Lb1, tm, li);
+            } else if (cur.np + cur.nd > 0) {
                 const int64_t task = static_cast<int64_t>(l - n);
                 uint4 *dst = reinterpret_cast<uint4 *>(P.part + static_cast<size_t>(task) * R);
 #pragma unroll
                 for (int c = 0; c < Gm::CPL; ++c)
                     dst[li + G * c] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
-                if (li == 0) {
-                    set_bit(P.part_any, task);
-                    st.bytes += R;
-                }
+                if (li == 0) set_bit(P.part_any, task);
             }
         }
         store_desc(s2, wn);  // the unit after next goes to the free slot (read as the next unit from next round)
@@ -776,8 +811,11 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
 #pragma unroll
         for (int k = 0; k < 4; ++k) cb[k] = nb[k];
     }
-    if (li == 0 && st.bytes) atomicAdd(&P.ctr->first_bytes, st.bytes);
-    flush_stats(P.ctr, st, li);
+    if (li == 0 && bytes) {
+        atomicAdd(&P.ctr->first_bytes, bytes);
+        atomicAdd(&P.ctr->bytes, bytes);
+        atomicAdd(&P.ctr->pairs, pairs);
+    }
 }
 
 // The partial rows of tasks [a, b) (b - a <= 32) that merged something: their part_any bits are consumed and the
@@ -1131,7 +1169,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_first(const DevProb *__restric
     using Gm = Geo<R>;
     extern __shared__ __align__(16) uint4 gather_smem[];
     __shared__ __align__(16) uint32_t sY[R];  // the problem's initialisation words Y_j (slots sw_slot(j, 0))
-    __shared__ uint32_t sring[kWarpsPerBlock * Geo<R>::NG][3 * 8];  // per tile: three unit descriptors
+    __shared__ __align__(16) uint32_t sring[kWarpsPerBlock * Geo<R>::NG][3 * 8];  // per tile: three unit descriptors
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int g = lane / Gm::G, li = lane % Gm::G;
     const unsigned tm = tile_mask<R>(g);
@@ -1616,7 +1654,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 if (searched && v < P.n) {
                     const uint2 *row = reinterpret_cast<const uint2 *>(P.vis + static_cast<size_t>(v) * P.W);
                     const uint2 *done =
-                        P.prb ? reinterpret_cast<const uint2 *>(P.vis_done + static_cast<size_t>(v) * P.W) : nullptr;
+                        P.pqb ? reinterpret_cast<const uint2 *>(P.vis_done + static_cast<size_t>(v) * P.W) : nullptr;
                     for (int k = 0; k < P.W / 2; ++k) {
                         const uint2 x = row[k];
                         any |= x.x | x.y;
@@ -1630,7 +1668,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 const uint32_t fresh = __ballot_sync(kFull, nw != 0);
                 if (lane == 0) {
                     P.rany[wi] = bits;
-                    if (P.prb) P.rnew[wi] = fresh;  // vertices with blocked bits not yet in the pair ranks
+                    if (P.pqb) P.rnew[wi] = fresh;  // vertices with blocked bits not yet in the pair ranks
                 }
             }
         }
@@ -2456,36 +2494,66 @@ __global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t
 
 // Residual blocking in the pair ranks of a rebuild: every in-pair (u, v, j) whose (v, j) S reached since the last
 // rebuild (set in vis, not yet in vis_done) gets rank 0 in the problem's copy of the out-pair ranks, so the first
-// sweep needs no test.  A stream over the in-pairs, four a thread in flight; rnew (set by k_init) marks the vertices
-// with new bits, so the pairs of other vertices cost their target id and one cached bit.
-__global__ void __launch_bounds__(kBlock) k_block_pairs(const DevProb *__restrict__ probs,
+// sweep needs no test.  rnew (set by k_init) marks the vertices with new bits, usually few.  The in-pairs are in
+// in-CSR order, sorted by target, so a group of kBlkGroup consecutive in-pairs has its targets in
+// [iv[first], iv[last]]: a lane tests that span's rnew bits (two loads and one or a few cached words) for one group,
+// 32 groups a warp at once, and the warp then visits only the groups whose span has a marked vertex, four pairs a
+// lane.  A span longer than kBlkSpanWords words (targets without in-pairs in between) is visited without the test.
+constexpr int kBlkGroup = 128;
+constexpr uint32_t kBlkSpanWords = 8;
+
+__global__ void __launch_bounds__(kBlock, 4) k_block_pairs(const DevProb *__restrict__ probs,
                                                         const int32_t *__restrict__ act, int nact) {
-    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
-        if (!P.prb || P.ctr->lvl == 0) continue;
+        if (!P.pqb || P.ctr->lvl == 0) continue;
         const uint64_t npairs = static_cast<uint64_t>(P.ipofs[P.m]);
-        // items of four pairs nthreads apart, in whole rounds of nthreads items (round r: pairs 4 r nthreads ..)
-        const uint64_t cnt = (npairs + 4 * nthreads - 1) / (4 * nthreads) * nthreads;
-        const uint64_t first = first_owned(tid, nthreads, base);
+        const uint64_t ngroups = (npairs + kBlkGroup - 1) / kBlkGroup;
+        const uint64_t cnt = (ngroups + 31) / 32;  // warp items of 32 groups
+        const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
-        for (uint64_t it = first; it < cnt; it += nthreads) {
-            const uint64_t blk = it - it % nthreads;  // the four pairs of this item lie nthreads apart
-            int32_t v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint64_t kk = blk * 4 + static_cast<uint64_t>(k) * nthreads + (it - blk);
-                v[k] = kk < npairs ? __ldg(&P.iv[kk]) : -1;
+        for (uint64_t it = first; it < cnt; it += nworkers) {
+            const uint64_t gi = it * 32 + lane;
+            bool hit = false;
+            if (gi < ngroups) {
+                const uint64_t ga = gi * kBlkGroup;
+                const uint64_t gb = (ga + kBlkGroup < npairs ? ga + kBlkGroup : npairs) - 1;
+                const uint32_t va = static_cast<uint32_t>(__ldg(&P.iv[ga]));
+                const uint32_t vb = static_cast<uint32_t>(__ldg(&P.iv[gb]));
+                const uint32_t wa = va >> 5, wb = vb >> 5;
+                if (wb - wa >= kBlkSpanWords) {
+                    hit = true;
+                } else {
+                    for (uint32_t w = wa; w <= wb && !hit; ++w) {
+                        uint32_t m = P.rnew[w];
+                        if (w == wa) m &= ~0u << (va & 31);
+                        if (w == wb) m &= ~0u >> (31 - (vb & 31));
+                        hit = m != 0u;
+                    }
+                }
             }
+            for (unsigned hits = __ballot_sync(kFull, hit); hits; hits &= hits - 1u) {
+                const uint64_t ga = (it * 32 + static_cast<uint64_t>(__ffs(hits) - 1)) * kBlkGroup;
+                int32_t v[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (v[k] < 0 || !test_bit(P.rnew, v[k])) continue;
-                const uint64_t kk = blk * 4 + static_cast<uint64_t>(k) * nthreads + (it - blk);
-                const uint32_t j = __ldg(&P.ij[kk]);
-                const size_t w = static_cast<size_t>(v[k]) * P.W + (j >> 5);
-                if (((P.vis[w] & ~P.vis_done[w]) >> (j & 31)) & 1u) P.prb[__ldg(&P.iop[kk])] = 0;
+                for (int k = 0; k < 4; ++k) {
+                    const uint64_t kk = ga + lane + 32 * k;
+                    v[k] = (kk < npairs && kk < ga + kBlkGroup) ? __ldg(&P.iv[kk]) : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (v[k] >= 0 && test_bit(P.rnew, v[k])) {
+                        const uint64_t kk = ga + lane + 32 * k;
+                        const uint32_t j = __ldg(&P.ij[kk]);
+                        const size_t w = static_cast<size_t>(v[k]) * P.W + (j >> 5);
+                        if (((P.vis[w] & ~P.vis_done[w]) >> (j & 31)) & 1u)
+                            P.pqb[__ldg(&P.iop[kk])] = static_cast<uint16_t>(sw_slot(j, 0));  // rank 0
+                    }
+                }
             }
         }
     }
@@ -2501,7 +2569,7 @@ __global__ void __launch_bounds__(kBlock) k_block_done(const DevProb *__restrict
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
-        if (!P.prb || P.ctr->lvl == 0) continue;
+        if (!P.pqb || P.ctr->lvl == 0) continue;
         const uint64_t cnt = (static_cast<uint64_t>(P.n) + 31) / 32;
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
@@ -2583,7 +2651,7 @@ __global__ void __launch_bounds__(kBlock) k_pair_counts(const DevProb P, int32_t
 }
 
 // Writes the pairs of every sparse edge at pofs[e] (simulations in increasing order) and the dense edge ids.
-__global__ void __launch_bounds__(kBlock) k_pair_fill(const DevProb P, int32_t *pv, uint16_t *pj, uint8_t *pr,
+__global__ void __launch_bounds__(kBlock) k_pair_fill(const DevProb P, int32_t *pv, uint16_t *pj, uint16_t *pq,
                                                       uint32_t *dlist) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < P.m; e += stride) {
@@ -2601,7 +2669,8 @@ __global__ void __launch_bounds__(kBlock) k_pair_fill(const DevProb P, int32_t *
                 const uint32_t j = 32 * k + __ffs(w) - 1;
                 pv[at] = v;
                 pj[at] = static_cast<uint16_t>(j);
-                pr[at] = static_cast<uint8_t>(__clz(hv ^ __ldg(&P.Y[j])));  // the initial rank of (v, j)
+                // the first sweep's word: accumulator slot and the initial rank of (v, j)
+                pq[at] = static_cast<uint16_t>(sw_slot(j, 0) | (static_cast<uint32_t>(__clz(hv ^ __ldg(&P.Y[j]))) << 10));
                 ++at;
             }
         }
@@ -3122,7 +3191,7 @@ void launch_frontier(const DevProb *probs, const int32_t *act, int nact, GridBar
 }
 int launch_init(const DevProb *probs, const int32_t *act, int nact, cudaStream_t s) {
     k_init<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
-    k_block_pairs<<<g_grid_block, kBlock, 0, s>>>(probs, act, nact);
+    k_block_pairs<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
     k_block_done<<<g_grid_warp, kBlock, 0, s>>>(probs, act, nact);
     return 3;
 }
@@ -3221,8 +3290,8 @@ void launch_live_masks(const DevProb &P, cudaStream_t s) {
 void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
     k_pair_counts<<<g_grid_block, kBlock, 0, s>>>(P, npairs, ndense);
 }
-void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint8_t *pr, uint32_t *dlist, cudaStream_t s) {
-    k_pair_fill<<<g_grid_block, kBlock, 0, s>>>(P, pv, pj, pr, dlist);
+void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint16_t *pq, uint32_t *dlist, cudaStream_t s) {
+    k_pair_fill<<<g_grid_block, kBlock, 0, s>>>(P, pv, pj, pq, dlist);
 }
 void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
     k_inpair_counts<<<g_grid_block, kBlock, 0, s>>>(P, npairs, ndense);

@@ -49,7 +49,7 @@ void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned 
 
 void launch_live_masks(const DevProb &P, cudaStream_t s);
 void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
-void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint8_t *pr, uint32_t *dlist, cudaStream_t s);
+void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint16_t *pq, uint32_t *dlist, cudaStream_t s);
 void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
 void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *iop, int32_t *idu, uint32_t *ide,
                         cudaStream_t s);

@@ -25,14 +25,15 @@ constexpr int kCasLimit = 1024;      // compare-and-swap tries of one register-w
 enum Model : int32_t { kIC = 0, kWC = 1, kPerEdge = 2 };
 
 // Work of one sweep unit (a light row, or a task of kTaskEdges edges of a split row): its sparse pairs
-// [p0, p0 + np) and its dense edges dlist[d0, d0 + nd).
+// [p0, p0 + np) and its dense edges dlist[d0, d0 + nd); hu is vertex_hash(u), the first sweep's seed of u's initial
+// ranks (0 in push-unit descriptors).
 struct UnitD {
     int64_t p0;
     int64_t d0;
     uint32_t np;
     uint32_t nd;
     int32_t u;
-    int32_t pad;
+    uint32_t hu;
 };
 
 // Grid-wide barrier of the persistent (cooperatively launched) kernels: arrivals and a generation count; and the
@@ -130,8 +131,9 @@ struct DevProb {
     // merged with whole register rows.
     const int64_t *pofs;       // m+1: pairs before each edge
     const int64_t *dofs;       // m+1: dense edges before each edge
-    const int32_t *pv;         // per pair: target vertex
-    const uint16_t *pj;        // per pair: simulation
+    const int32_t *pv;         // per pair: target vertex (NULL unless pulling sweeps follow the first, or a rebuild
+                               // tests each pair's target: more than 2^32 pairs)
+    const uint16_t *pj;        // per pair: simulation (NULL with pv)
     const uint16_t *pq;        // per pair, for the first sweep: sw_slot(simulation, 0) | initial rank of (target,
                                // simulation) << 10 (R <= 1024, ranks <= 32)
     const uint32_t *iop;       // per in-pair: the index of the same pair in out-CSR order

@@ -400,22 +400,34 @@ void sample_edges(im_ctx *ctx, Prob &P) {
         ctx->launches += 1;
         return;
     }
-    launch_live_masks(d, s);
     int32_t *np = mem.alloc<int32_t>(m);
     int32_t *nd = mem.alloc<int32_t>(m);
     int64_t *bsums = mem.alloc<int64_t>(scan_block_count(m) + 1);
-    launch_pair_counts(d, np, nd, s);
-    ctx->launches += 2 + launch_exclusive_scan(np, m, pofs, bsums, s);
+    launch_live_masks(d, np, nd, s);
+    ctx->launches += 1 + launch_exclusive_scan(np, m, pofs, bsums, s);
     ctx->launches += launch_exclusive_scan(nd, m, dofs, bsums, s);
+    // the same classes in in-CSR order (gathered from the out-edges'), for the pairs and dense edges of push sweeps
+    int64_t *ipofs = mem.alloc<int64_t>(m + 1);
+    int64_t *idofs = mem.alloc<int64_t>(m + 1);
+    int32_t *inp = mem.alloc<int32_t>(m);
+    int32_t *ind = mem.alloc<int32_t>(m);
+    launch_inpair_counts(d, np, nd, inp, ind, s);
+    ctx->launches += 1 + launch_exclusive_scan(inp, m, ipofs, bsums, s);
+    ctx->launches += launch_exclusive_scan(ind, m, idofs, bsums, s);
     int64_t tot[2] = {0, 0};
     ck(cudaMemcpyAsync(&tot[0], pofs + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
     ck(cudaMemcpyAsync(&tot[1], dofs + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
     ck(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    mem.release(inp);
+    mem.release(ind);
     mem.release(np);
     mem.release(nd);
     mem.release(bsums);
-    int32_t *pv = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
-    uint16_t *pj = mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
+    // targets and simulations of the out-pairs are read only by pulling sweeps after the first and by a rebuild
+    // without the problem's own pair words (more than 2^32 pairs, no 32-bit in-pair -> out-pair index)
+    const bool need_pv = ctx->pull_sweeps > 1 || tot[0] >= (int64_t(1) << 32);
+    int32_t *pv = need_pv ? mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1))) : nullptr;
+    uint16_t *pj = need_pv ? mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1))) : nullptr;
     uint16_t *pq = mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
     uint32_t *dlist = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
     launch_pair_fill(d, pv, pj, pq, dlist, s);
@@ -427,40 +439,27 @@ void sample_edges(im_ctx *ctx, Prob &P) {
     d.dlist = dlist;
     P.npairs = tot[0];
     P.ndense = tot[1];
-    // the same pairs and dense edges in in-CSR order, for push sweeps
-    int64_t *ipofs = mem.alloc<int64_t>(m + 1);
-    int64_t *idofs = mem.alloc<int64_t>(m + 1);
-    np = mem.alloc<int32_t>(m);
-    nd = mem.alloc<int32_t>(m);
-    bsums = mem.alloc<int64_t>(scan_block_count(m) + 1);
-    launch_inpair_counts(d, np, nd, s);
-    ctx->launches += 1 + launch_exclusive_scan(np, m, ipofs, bsums, s);
-    ctx->launches += launch_exclusive_scan(nd, m, idofs, bsums, s);
-    mem.release(np);
-    mem.release(nd);
-    mem.release(bsums);
     d.ipofs = ipofs;
     d.idofs = idofs;
     int32_t *iu = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
     uint16_t *ij = mem.alloc<uint16_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
-    // in-pair -> out-pair index (32-bit), for residual blocking in a problem's copy of the pair ranks
+    int32_t *iv = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
+    // in-pair -> out-pair index (32-bit), for residual blocking in a problem's copy of the pair words
     uint32_t *iop = tot[0] < (int64_t(1) << 32)
                         ? mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)))
                         : nullptr;
     int32_t *idu = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
     uint32_t *ide = mem.alloc<uint32_t>(static_cast<size_t>(std::max<int64_t>(tot[1], 1)));
-    launch_inpair_fill(d, iu, ij, iop, idu, ide, s);
-    d.iop = iop;
-    int32_t *iv = mem.alloc<int32_t>(static_cast<size_t>(std::max<int64_t>(tot[0], 1)));
-    launch_inpair_targets(d, iv, s);
+    launch_inpair_fill(d, iu, ij, iop, iv, idu, ide, s);
     ctx->launches += 1;
+    d.iop = iop;
     d.iv = iv;
     // push sweeps over a large L stream every in-pair (only without dense edges, which the stream leaves out)
     d.stream_min = (tot[1] == 0 && ctx->stream_push) ? static_cast<unsigned long long>(std::max<int64_t>(m / 2, 1))
                                                       : ~0ull;
     UnitD *vdesc = mem.alloc<UnitD>(static_cast<size_t>(std::max<int64_t>(P.G->n, 1)));
     launch_vertex_desc(d, vdesc, s);
-    ctx->launches += 2;
+    ctx->launches += 1;
     d.iu = iu;
     d.ij = ij;
     d.idu = idu;
@@ -1449,8 +1448,8 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     b += r(4 * W * m1);                                      // live-simulation masks of the edges
     b += r(8 * (m1 + 1)) * 4;                                // pair and dense-edge offsets, out- and in-CSR order
     b += r(sizeof(UnitD) * std::max<uint64_t>(n, 1)) + r(sizeof(UnitD) * nt);  // sweep-unit descriptors
-    // pairs: at most dense_min per edge (6 bytes each), dense edges 4 bytes; the counts and scan sums of the
-    // preparation are freed before the pairs are allocated, and are smaller
+    // pairs: at most dense_min per edge, dense edges 4 bytes; the per-edge counts (out- and in-CSR order) and the
+    // scan sums of the preparation are freed before the pairs are allocated, and are smaller
     const uint64_t pmax = m1 * static_cast<uint64_t>(dense_min_for(prm.R));
     b += (r(4 * pmax) + r(2 * pmax)) * 2 + r(2 * pmax) * 2 + r(4 * pmax) * 2 + r(4 * m1) * 3;  // pairs both ways
         // with the out-pairs' first-sweep words (and the query's copy), the in-pairs' targets and out-pair indices,

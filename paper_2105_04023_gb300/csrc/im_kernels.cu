@@ -10,8 +10,8 @@
 //   k_first       Algorithm 1's initialisation fused into Algorithm 2's first sweep (L = V): every register it
 //                 reads is an initial rank, computed from (v, j); it writes every row of both register buffers.
 //                 The sampling of Eq. 4-5 is evaluated once per run (k_live_masks) and kept as (target,
-//                 simulation) pairs for edges live in few simulations (k_pair_counts, k_pair_fill) and as live
-//                 masks for the others
+//                 simulation) pairs for edges live in few simulations (k_pair_fill, and in in-CSR order
+//                 k_inpair_fill) and as live masks for the others
 //   k_propg       Algorithm 2, a later sweep that pulls into every row (when more than one sweep pulls)
 //   k_push        Algorithm 2, the later sweeps, pushed from the vertices L that changed in the previous one
 //   k_combine     Algorithm 2, sweep 0 for rows split over several warps
@@ -568,21 +568,20 @@ __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W,
     // are loaded while the current unit is processed
     int64_t id_next = first + nworkers < cnt ? unit_id(W, first + nworkers) : 0;
     UnitD cur{};
+    int64_t cur_id = 0;
     if (first < cnt) {
-        const int64_t id0 = unit_id(W, first);
-        cur = first < W.nlight ? P.rdesc[id0] : P.tdesc[id0];
-        cur.pad = static_cast<int32_t>(id0);
+        cur_id = unit_id(W, first);
+        cur = first < W.nlight ? P.rdesc[cur_id] : P.tdesc[cur_id];
     }
     for (uint64_t l = first; l < cnt; l += nworkers) {
         UnitD nxt{};
-        if (l + nworkers < cnt) {
-            nxt = l + nworkers < W.nlight ? P.rdesc[id_next] : P.tdesc[id_next];
-            nxt.pad = static_cast<int32_t>(id_next);
-        }
+        const int64_t nxt_id = id_next;
+        if (l + nworkers < cnt) nxt = l + nworkers < W.nlight ? P.rdesc[id_next] : P.tdesc[id_next];
         if (l + 2 * nworkers < cnt) id_next = unit_id(W, l + 2 * nworkers);
         const bool is_row = l < W.nlight;
         if (INIT && is_row && cur.u < 0) {  // a split row: its tasks and the combine kernels finish it
             cur = nxt;
+            cur_id = nxt_id;
             continue;
         }
         const int64_t u = cur.u;
@@ -630,7 +629,7 @@ __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W,
             drop_blocked<R>(P, u, acc, li);
             finalize_tile<R>(P, u, acc, any, !INIT && test_bit(Lcur, u), own, Mnext, Mother, Lnext, tm, li, st);
         } else if (any) {
-            const int64_t task = cur.pad;
+            const int64_t task = cur_id;
             uint4 *dst = reinterpret_cast<uint4 *>(P.part + static_cast<size_t>(task) * R);
 #pragma unroll
             for (int c = 0; c < Gm::CPL; ++c)
@@ -641,6 +640,7 @@ __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W,
             }
         }
         cur = nxt;
+        cur_id = nxt_id;
     }
     flush_stats(P.ctr, st, li);
 }
@@ -721,6 +721,7 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
         int64_t p0, d0;
         uint32_t np, nd;
         int32_t u;
+        uint32_t hu;
     };
     auto read_desc = [&](int slot) {
         const uint4 *r = reinterpret_cast<const uint4 *>(ring + slot * DW);
@@ -731,6 +732,7 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
         d.np = b.x;
         d.nd = b.y;
         d.u = static_cast<int32_t>(b.z);
+        d.hu = b.w;
         return d;
     };
     // the first 4 G pair words of unit d, this lane's share (rank 0 past the unit's end)
@@ -788,12 +790,11 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
             }
             if (is_row) {
                 const int64_t u = cur.u;
-                const uint32_t hu = vertex_hash(static_cast<uint32_t>(u));
                 uint4 own[Gm::CPL];
 #pragma unroll
                 for (int c = 0; c < Gm::CPL; ++c)
-                    own[c] = zero_own ? init_chunk_sw<true>(Ys, hu, li + G * c, blocked16(P, u, li + G * c))
-                                      : init_chunk_sw<false>(Ys, hu, li + G * c, 0u);
+                    own[c] = zero_own ? init_chunk_sw<true>(Ys, cur.hu, li + G * c, blocked16(P, u, li + G * c))
+                                      : init_chunk_sw<false>(Ys, cur.hu, li + G * c, 0u);
                 if (keep_own) drop_blocked<R>(P, u, acc, li);
                 finalize_first<R>(P, u, acc, own, P.Lb1, tm, li);
             } else if (cur.np + cur.nd > 0) {
@@ -1065,8 +1066,8 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
 // A push sweep over a large L as one stream of in-pairs (sampled graphs without dense edges): every in-pair
 // (u, v, j) in in-CSR order, 128 a warp at a time, merges M_v[j] into the next buffer's M_u[j] when v is in L and
 // the previous sweep changed (v, j) (the same skip as push_problem_w; dmask of every listed v, or of every row after
-// the first sweep, is current); the pair records and the change masks of consecutive pairs are coalesced, and
-// only pairs of changed registers touch a register row.
+// the first sweep, is current); the pair records and the change masks of consecutive pairs are coalesced, and only
+// pairs of changed registers read their source u and touch a register row.
 template <int R>
 __device__ void push_stream_w(const DevProb &P, uint32_t t, uint64_t cnt, uint64_t first, uint64_t nworkers,
                               int lane) {
@@ -1081,8 +1082,8 @@ __device__ void push_stream_w(const DevProb &P, uint32_t t, uint64_t cnt, uint64
     const uint64_t npairs = static_cast<uint64_t>(P.ipofs[P.m]);
     uint32_t nproc = 0, nrec = 0;
     // the records of the next item are loaded while this one is processed (the loop is a chain of dependent loads:
-    // record -> change mask -> register and target word -> compare-and-swap)
-    int32_t nv[4], nu[4];
+    // record -> change mask -> source, register and target word -> compare-and-swap)
+    int32_t nv[4];
     uint32_t nj[4];
     auto fetch = [&](uint64_t l) {
 #pragma unroll
@@ -1091,62 +1092,61 @@ __device__ void push_stream_w(const DevProb &P, uint32_t t, uint64_t cnt, uint64
             const bool ok = l < cnt && q < npairs;
             nv[k] = ok ? __ldg(&P.iv[q]) : -1;
             nj[k] = ok ? __ldg(&P.ij[q]) : 0u;
-            nu[k] = ok ? __ldg(&P.iu[q]) : 0;
         }
     };
     fetch(first);
     for (uint64_t l = first; l < cnt; l += nworkers) {
-        int32_t cv[4], cu[4];
+        int32_t cv[4];
         uint32_t cj[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             cv[k] = nv[k];
-            cu[k] = nu[k];
             cj[k] = nj[k];
         }
         fetch(l + nworkers);
-        uint32_t *addr[4];
-        uint32_t jj[4], old[4], x[4];
-        const uint8_t *vb[4];
+        bool go[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            addr[k] = nullptr;
-            jj[k] = 0;
-            vb[k] = Mcur;
+            go[k] = false;
             if (cv[k] >= 0) {
                 ++nrec;
                 const int32_t v = cv[k];
                 const uint32_t j = cj[k];
                 const bool inL = t == 1 || test_bit(Lcur, v);
-                if (inL && ((__ldg(&P.dmask[static_cast<size_t>(v) * CH + (j >> 4)]) >> (j & 15)) & 1u)) {
-                    const int32_t u = cu[k];
-                    if (!literal_blocked(P, u, j)) {
-                        jj[k] = j;
-                        vb[k] = Mcur + static_cast<size_t>(v) * R;
-                        addr[k] = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u) * R + (j & ~3u));
-                        ++nproc;
-                    }
-                }
+                go[k] = inL && ((__ldg(&P.dmask[static_cast<size_t>(v) * CH + (j >> 4)]) >> (j & 15)) & 1u);
+            }
+        }
+        int32_t cu[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cu[k] = go[k] ? __ldg(&P.iu[l * 128 + 32 * k + lane]) : 0;
+        uint32_t *addr[4];
+        uint32_t old[4], x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            addr[k] = nullptr;
+            if (go[k] && !literal_blocked(P, cu[k], cj[k])) {
+                addr[k] = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(cu[k]) * R + (cj[k] & ~3u));
+                ++nproc;
             }
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            x[k] = addr[k] ? __ldg(vb[k] + jj[k]) : 0u;
+            x[k] = addr[k] ? __ldg(Mcur + static_cast<size_t>(cv[k]) * R + cj[k]) : 0u;
             old[k] = addr[k] ? __ldcg(addr[k]) : 0u;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const uint32_t cand = x[k] << (8 * (jj[k] & 3));
+            const uint32_t cand = x[k] << (8 * (cj[k] & 3));
             if (cand && word_max(addr[k], old[k], cand, fault, lim))
                 set_bit(Lnext, (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R);
         }
     }
-    // modelled bytes: per pair its record (target, source, simulation: 10 bytes) and change-mask word (2), and per
-    // pair of a changed register the register and the target word (5)
+    // modelled bytes: per pair its target and simulation (6 bytes) and change-mask word (2), and per pair of a
+    // changed register its source (4), the register and the target word (5)
     nproc = __reduce_add_sync(kFull, nproc);
     nrec = __reduce_add_sync(kFull, nrec);
     if (lane == 0 && nrec) {
-        atomicAdd(&P.ctr->bytes, 12ull * nrec + 5ull * nproc);
+        atomicAdd(&P.ctr->bytes, 8ull * nrec + 9ull * nproc);
         atomicAdd(&P.ctr->pairs, static_cast<unsigned long long>(nrec));
     }
 }
@@ -2407,152 +2407,255 @@ __global__ void k_estimate(const DevProb *__restrict__ prob, const int32_t *__re
     if (threadIdx.x == 0) *gsum_out = s_sum;
 }
 
-// Live-simulation masks for the reachability searches (Eq. 4-5 evaluated once per edge and simulation): bit j of
-// live[e] is set iff edge e is sampled in simulation j.  One warp per light row or split-row task; lanes stage 32
-// edges, then for each edge every lane tests one simulation of each 32-simulation word and a ballot forms the word.
+// Live-simulation masks (Eq. 4-5 evaluated once per edge and simulation): bit j of live[e] is set iff edge e is
+// sampled in simulation j; with them each edge's class, npairs[e] (live in at most dense_min simulations: its pair
+// count) or ndense[e] = 1.  A thread per edge, in chunks of kLiveChunk consecutive edges a block (each edge's row
+// found by a binary search among the chunk's rows).  The test (h XOR X_j) <= T can only pass where the top byte
+// of h XOR X_j is at most T's top byte tb, so the block groups the simulations by the top byte of X_j, and an edge
+// visits only the groups whose top byte is (h's top byte) XOR t, t = 0 .. tb: for t < tb every simulation of the
+// group passes (its h XOR X_j is below tb * 2^24 <= T), for t = tb each is compared in full.  An edge with tb >= 128
+// (p >= 1/2) tests every simulation.  A warp forms its 32 edges' masks in shared memory and writes them as one
+// contiguous block.
+constexpr int kLiveChunk = 2048;
+
 template <int R>
-__global__ void __launch_bounds__(kBlock) k_live_masks(const DevProb P) {
+__global__ void __launch_bounds__(kBlock) k_live_masks(const DevProb P, int32_t *npairs, int32_t *ndense) {
     constexpr int W = R / 32;
+    constexpr int SW = W + 1;  // words a staged row (odd, so the lanes' rows start in different banks)
+    __shared__ uint32_t sX[R];
+    __shared__ uint16_t sSim[R];     // simulations grouped by the top byte of X_j
+    __shared__ uint32_t sOfs[257];   // group g: sSim[sOfs[g] .. sOfs[g + 1])
+    __shared__ uint32_t sCur[256];
+    __shared__ uint32_t sM[kWarpsPerBlock][32 * SW];
+    __shared__ int64_t s_u0, s_u1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < 257; k += blockDim.x) sOfs[k] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < R; j += blockDim.x) {
+        const uint32_t x = __ldg(&P.X[j]);
+        sX[j] = x;
+        atomicAdd(&sOfs[(x >> 24) + 1], 1u);
+    }
+    __syncthreads();
+    if (wib == 0) {  // inclusive scan of the 256 group sizes: sOfs[g + 1] = end of group g
+        uint32_t c[8], sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            c[i] = sOfs[1 + 8 * lane + i];
+            sum += c[i];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += y;
+        }
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            sCur[8 * lane + i] = run;
+            run += c[i];
+            sOfs[1 + 8 * lane + i] = run;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < R; j += blockDim.x) sSim[atomicAdd(&sCur[sX[j] >> 24], 1u)] = static_cast<uint16_t>(j);
+    __syncthreads();
+    const int64_t m = P.m, n = P.n;
+    const uint64_t chunks = (static_cast<uint64_t>(m) + kLiveChunk - 1) / kLiveChunk;
+    uint32_t *row = &sM[wib][lane * SW];
+    for (uint64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+        const int64_t e0 = static_cast<int64_t>(c) * kLiveChunk;
+        const int64_t e1 = e0 + kLiveChunk < m ? e0 + kLiveChunk : m;
+        if (threadIdx.x == 0) {  // the rows holding edges e0 and e1 - 1 (the last u with xadj[u] <= e)
+            int64_t lo = 0, hi = n - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(&P.xadj[mid]) <= e0) lo = mid; else hi = mid - 1;
+            }
+            s_u0 = lo;
+            hi = n - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(&P.xadj[mid]) <= e1 - 1) lo = mid; else hi = mid - 1;
+            }
+            s_u1 = lo;
+        }
+        __syncthreads();
+        const int64_t u0 = s_u0, u1 = s_u1;
+        for (int64_t eb = e0 + 32 * wib; eb < e1; eb += kBlock) {  // this warp's 32 edges
+#pragma unroll
+            for (int k = 0; k < W; ++k) row[k] = 0u;
+            const int64_t e = eb + lane;
+            uint32_t cnt = 0;
+            if (e < e1) {
+                int64_t lo = u0, hi = u1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi + 1) >> 1;
+                    if (__ldg(&P.xadj[mid]) <= e) lo = mid; else hi = mid - 1;
+                }
+                const int32_t v = __ldg(&P.adj[e]);
+                uint32_t T = 0;
+                bool ok = false;
+                edge_threshold(P, e, v, T, ok);
+                if (ok) {
+                    const uint32_t h = edge_hash(static_cast<uint64_t>(lo), static_cast<uint64_t>(v),
+                                                 static_cast<uint64_t>(n), P.undirected != 0);
+                    const uint32_t tb = T >> 24;
+                    if (tb >= 128) {
+                        for (int k = 0; k < W; ++k) {
+                            uint32_t w = 0;
+#pragma unroll 8
+                            for (int b = 0; b < 32; ++b) w |= ((h ^ sX[32 * k + b]) <= T ? 1u : 0u) << b;
+                            row[k] = w;
+                            cnt += __popc(w);
+                        }
+                    } else {
+                        const uint32_t ht = h >> 24;
+                        for (uint32_t t = 0; t <= tb; ++t) {
+                            const uint32_t grp = ht ^ t;
+                            const uint32_t i1 = sOfs[grp + 1];
+                            for (uint32_t i = sOfs[grp]; i < i1; ++i) {
+                                const uint32_t j = sSim[i];
+                                if (t < tb || (h ^ sX[j]) <= T) {
+                                    row[j >> 5] |= 1u << (j & 31);
+                                    ++cnt;
+                                }
+                            }
+                        }
+                    }
+                }
+                const bool dense = cnt > static_cast<uint32_t>(P.dense_min);
+                npairs[e] = dense ? 0 : static_cast<int32_t>(cnt);
+                ndense[e] = dense ? 1 : 0;
+            }
+            __syncwarp();
+            const int ne = e1 - eb < 32 ? static_cast<int>(e1 - eb) : 32;
+            uint32_t *out = P.live + static_cast<size_t>(eb) * W;
+            for (int q = lane; q < ne * W; q += 32) out[q] = sM[wib][(q / W) * SW + q % W];
+            __syncwarp();
+        }
+        __syncthreads();  // the chunk's rows are read before the next chunk's replace them
+    }
+}
+
+// The same classification per in-edge k (edge ein[k]), gathered from the out-edges' counts.
+__global__ void __launch_bounds__(kBlock) k_inpair_counts(const DevProb P, const int32_t *__restrict__ np_out,
+                                                          const int32_t *__restrict__ nd_out, int32_t *npairs,
+                                                          int32_t *ndense) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < P.m; k += stride) {
+        const int64_t e = __ldg(&P.ein[k]);
+        npairs[k] = __ldg(&np_out[e]);
+        ndense[k] = __ldg(&nd_out[e]);
+    }
+}
+
+// The pairs and dense in-edges in in-CSR order: in-edge k (out-CSR edge e = ein[k], source u) gets e's out-pairs
+// at ipofs[k] as (u, simulation, out-pair index) with its target v in iv, or one dense entry (u, e).  A thread per
+// in-edge; a warp takes chunks of kInChunk consecutive in-edges, 32 at a time, and finds the target row of each from
+// the row of the previous 32 (a binary search at the chunk's start, then a short forward walk).
+constexpr int kInChunk = 1024;
+
+__global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t *iu, uint16_t *ij, uint32_t *iop,
+                                                        int32_t *iv, int32_t *idu, uint32_t *ide) {
     const int lane = threadIdx.x & 31;
     const uint64_t worker = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nworkers = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-    uint32_t xr[W < 8 ? W : 8];
-#pragma unroll
-    for (int k = 0; k < (W < 8 ? W : 8); ++k) xr[k] = __ldg(&P.X[32 * k + lane]);
-    const uint64_t cnt = static_cast<uint64_t>(P.n_light) + static_cast<uint64_t>(P.n_tasks);
-    for (uint64_t l = worker; l < cnt; l += nworkers) {
-        int64_t u, e0, e1;
-        if (l < static_cast<uint64_t>(P.n_light)) {
-            u = P.light_list[l];
-            e0 = P.xadj[u];
-            e1 = P.xadj[u + 1];
-        } else {
-            const int64_t task = static_cast<int64_t>(l - P.n_light);
-            u = P.task_row[task];
-            e0 = P.xadj[u] + (task - P.task_off[u]) * kTaskEdges;
-            e1 = min(e0 + kTaskEdges, P.xadj[u + 1]);
-        }
-        for (int64_t base = e0; base < e1; base += 32) {
-            const int64_t e = base + lane;
-            uint32_t h = 0, T = 0;
-            bool ok = false;
-            if (e < e1) {
-                const int32_t v = __ldg(&P.adj[e]);
-                edge_threshold(P, e, v, T, ok);
-                h = edge_hash(static_cast<uint64_t>(u), static_cast<uint64_t>(v), static_cast<uint64_t>(P.n),
-                              P.undirected != 0);
+    const int64_t m = P.m, n = P.n;
+    const uint64_t chunks = (static_cast<uint64_t>(m) + kInChunk - 1) / kInChunk;
+    for (uint64_t c = worker; c < chunks; c += nworkers) {
+        const int64_t k0 = static_cast<int64_t>(c) * kInChunk;
+        const int64_t k1 = k0 + kInChunk < m ? k0 + kInChunk : m;
+        int64_t vb = 0;  // the in-CSR row holding in-edge k0 (the last v with xadj_in[v] <= k0)
+        {
+            int64_t lo = 0, hi = n - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(&P.xadj_in[mid]) <= k0) lo = mid; else hi = mid - 1;
             }
-            const int cnt_e = e1 - base < 32 ? static_cast<int>(e1 - base) : 32;
-            for (int j = 0; j < cnt_e; ++j) {
-                const uint32_t hj = __shfl_sync(kFull, h, j);
-                const uint32_t Tj = __shfl_sync(kFull, T, j);
-                const bool okj = __shfl_sync(kFull, ok, j);
-                uint32_t *out = P.live + static_cast<size_t>(base + j) * W;
-#pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    const uint32_t x = k < 8 ? xr[k < 8 ? k : 0] : __ldg(&P.X[32 * k + lane]);
-                    const uint32_t m = __ballot_sync(kFull, okj && ((hj ^ x) <= Tj));
-                    if (lane == (k & 31)) out[k] = m;
+            vb = lo;
+        }
+        for (int64_t kb = k0; kb < k1; kb += 32) {
+            const int64_t k = kb + lane;
+            int64_t v = vb;
+            if (k < k1) {
+                while (__ldg(&P.xadj_in[v + 1]) <= k) ++v;  // ends at the row holding k (k < xadj_in[n])
+                const int64_t e = __ldg(&P.ein[k]);
+                const int32_t u = __ldg(&P.adj_in[k]);
+                const int64_t dd = __ldg(&P.idofs[k]);
+                if (__ldg(&P.idofs[k + 1]) != dd) {
+                    idu[dd] = u;
+                    ide[dd] = static_cast<uint32_t>(e);
+                } else {
+                    const int64_t p0 = __ldg(&P.pofs[e]), p1 = __ldg(&P.pofs[e + 1]);
+                    int64_t at = __ldg(&P.ipofs[k]);
+                    for (int64_t p = p0; p < p1; ++p, ++at) {
+                        iu[at] = u;
+                        ij[at] = static_cast<uint16_t>(sw_slot(__ldg(&P.pq[p]) & 0x3FFu, 0));  // the slot map inverts itself
+                        iv[at] = static_cast<int32_t>(v);
+                        if (iop) iop[at] = static_cast<uint32_t>(p);  // the same pair in out-CSR order
+                    }
                 }
             }
+            vb = __shfl_sync(kFull, v, 31);  // the last lane's row (lanes past k1 keep vb: the loop ends anyway)
         }
     }
 }
 
-// The same classification per in-edge k (edge ein[k]): in-pair counts and dense in-edge flags.
-__global__ void __launch_bounds__(kBlock) k_inpair_counts(const DevProb P, int32_t *npairs, int32_t *ndense) {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < P.m; k += stride) {
-        const int64_t e = P.ein[k];
-        npairs[k] = static_cast<int32_t>(P.pofs[e + 1] - P.pofs[e]);
-        ndense[k] = P.dofs[e + 1] != P.dofs[e] ? 1 : 0;
-    }
-}
-
-// In-pairs (source u, simulation j) of every sparse in-edge at ipofs[k], and the dense in-edges (u, e).
-__global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t *iu, uint16_t *ij, uint32_t *iop,
-                                                        int32_t *idu, uint32_t *ide) {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < P.m; k += stride) {
-        const int64_t d0 = P.idofs[k];
-        if (P.idofs[k + 1] != d0) {
-            idu[d0] = P.adj_in[k];
-            ide[d0] = P.ein[k];
-            continue;
-        }
-        const int64_t e = P.ein[k];
-        const int32_t u = P.adj_in[k];
-        int64_t at = P.ipofs[k];
-        for (int64_t p = P.pofs[e]; p < P.pofs[e + 1]; ++p) {
-            iu[at] = u;
-            ij[at] = P.pj[p];
-            if (iop) iop[at] = static_cast<uint32_t>(p);  // the same pair in out-CSR order
-            ++at;
-        }
-    }
-}
-
-// Residual blocking in the pair ranks of a rebuild: every in-pair (u, v, j) whose (v, j) S reached since the last
-// rebuild (set in vis, not yet in vis_done) gets rank 0 in the problem's copy of the out-pair ranks, so the first
-// sweep needs no test.  rnew (set by k_init) marks the vertices with new bits, usually few.  The in-pairs are in
-// in-CSR order, sorted by target, so a group of kBlkGroup consecutive in-pairs has its targets in
-// [iv[first], iv[last]]: a lane tests that span's rnew bits (two loads and one or a few cached words) for one group,
-// 32 groups a warp at once, and the warp then visits only the groups whose span has a marked vertex, four pairs a
-// lane.  A span longer than kBlkSpanWords words (targets without in-pairs in between) is visited without the test.
-constexpr int kBlkGroup = 128;
-constexpr uint32_t kBlkSpanWords = 8;
-
-__global__ void __launch_bounds__(kBlock, 4) k_block_pairs(const DevProb *__restrict__ probs,
+// Residual blocking in the pair words of a rebuild: every in-pair (u, v, j) whose (v, j) S reached since the last
+// rebuild (set in vis, not yet in vis_done) gets rank 0 in the problem's copy of the out-pair words, so the first
+// sweep needs no test.  rnew (set by k_init) marks the vertices with such bits.  A thread takes 8 consecutive
+// in-pairs (targets and simulations loaded as 16-byte vectors, a warp reading 1 KB of targets at once) and tests
+// the blocked bits only of pairs whose target is marked; consecutive in-pairs mostly share their target (in-CSR
+// order), so those tests hit the same cached words.
+__global__ void __launch_bounds__(kBlock) k_block_pairs(const DevProb *__restrict__ probs,
                                                         const int32_t *__restrict__ act, int nact) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const uint64_t worker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
-    const uint64_t nworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
         if (!P.pqb || P.ctr->lvl == 0) continue;
         const uint64_t npairs = static_cast<uint64_t>(P.ipofs[P.m]);
-        const uint64_t ngroups = (npairs + kBlkGroup - 1) / kBlkGroup;
-        const uint64_t cnt = (ngroups + 31) / 32;  // warp items of 32 groups
-        const uint64_t first = first_owned(worker, nworkers, base);
+        const uint64_t cnt = (npairs + 7) / 8;  // octets of in-pairs
+        const uint64_t first = first_owned(tid, nthreads, base);
         base += cnt;
-        for (uint64_t it = first; it < cnt; it += nworkers) {
-            const uint64_t gi = it * 32 + lane;
-            bool hit = false;
-            if (gi < ngroups) {
-                const uint64_t ga = gi * kBlkGroup;
-                const uint64_t gb = (ga + kBlkGroup < npairs ? ga + kBlkGroup : npairs) - 1;
-                const uint32_t va = static_cast<uint32_t>(__ldg(&P.iv[ga]));
-                const uint32_t vb = static_cast<uint32_t>(__ldg(&P.iv[gb]));
-                const uint32_t wa = va >> 5, wb = vb >> 5;
-                if (wb - wa >= kBlkSpanWords) {
-                    hit = true;
-                } else {
-                    for (uint32_t w = wa; w <= wb && !hit; ++w) {
-                        uint32_t m = P.rnew[w];
-                        if (w == wa) m &= ~0u << (va & 31);
-                        if (w == wb) m &= ~0u >> (31 - (vb & 31));
-                        hit = m != 0u;
-                    }
+        // vector loads need 16-byte aligned octets (the device allocator aligns far more; checked, not assumed)
+        const bool vec = ((reinterpret_cast<uintptr_t>(P.iv) | reinterpret_cast<uintptr_t>(P.ij)) & 15u) == 0;
+        for (uint64_t o = first; o < cnt; o += nthreads) {
+            const uint64_t q0 = o * 8;
+            int32_t v[8];
+            uint32_t j[8];
+            if (vec && q0 + 8 <= npairs) {
+                const int4 a = __ldg(reinterpret_cast<const int4 *>(P.iv + q0));
+                const int4 b = __ldg(reinterpret_cast<const int4 *>(P.iv + q0) + 1);
+                const uint4 c = __ldg(reinterpret_cast<const uint4 *>(P.ij + q0));
+                v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+                const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    j[2 * i] = cw[i] & 0xFFFFu;
+                    j[2 * i + 1] = cw[i] >> 16;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    v[i] = q0 + i < npairs ? __ldg(&P.iv[q0 + i]) : -1;
+                    j[i] = q0 + i < npairs ? __ldg(&P.ij[q0 + i]) : 0u;
                 }
             }
-            for (unsigned hits = __ballot_sync(kFull, hit); hits; hits &= hits - 1u) {
-                const uint64_t ga = (it * 32 + static_cast<uint64_t>(__ffs(hits) - 1)) * kBlkGroup;
-                int32_t v[4];
+            uint32_t marked = 0;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint64_t kk = ga + lane + 32 * k;
-                    v[k] = (kk < npairs && kk < ga + kBlkGroup) ? __ldg(&P.iv[kk]) : -1;
-                }
+            for (int i = 0; i < 8; ++i)
+                if (v[i] >= 0 && test_bit(P.rnew, v[i])) marked |= 1u << i;
+            if (!marked) continue;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (v[k] >= 0 && test_bit(P.rnew, v[k])) {
-                        const uint64_t kk = ga + lane + 32 * k;
-                        const uint32_t j = __ldg(&P.ij[kk]);
-                        const size_t w = static_cast<size_t>(v[k]) * P.W + (j >> 5);
-                        if (((P.vis[w] & ~P.vis_done[w]) >> (j & 31)) & 1u)
-                            P.pqb[__ldg(&P.iop[kk])] = static_cast<uint16_t>(sw_slot(j, 0));  // rank 0
-                    }
+            for (int i = 0; i < 8; ++i) {
+                if ((marked >> i) & 1u) {
+                    const size_t w = static_cast<size_t>(v[i]) * P.W + (j[i] >> 5);
+                    if (((P.vis[w] & ~P.vis_done[w]) >> (j[i] & 31)) & 1u)
+                        P.pqb[__ldg(&P.iop[q0 + i])] = static_cast<uint16_t>(sw_slot(j[i], 0));  // rank 0
                 }
             }
         }
@@ -2581,17 +2684,6 @@ __global__ void __launch_bounds__(kBlock) k_block_done(const DevProb *__restrict
     }
 }
 
-// Target vertex of every in-pair (the in-CSR row v of the in-edge holding it): a warp per vertex.
-__global__ void __launch_bounds__(kBlock) k_inpair_targets(const DevProb P, int32_t *iv) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t v = warp; v < P.n; v += nwarps) {
-        const int64_t q0 = P.ipofs[P.xadj_in[v]], q1 = P.ipofs[P.xadj_in[v + 1]];
-        for (int64_t q = q0 + lane; q < q1; q += 32) iv[q] = static_cast<int32_t>(v);
-    }
-}
-
 // Push-unit descriptor of every vertex (its in-pairs and dense in-edges).
 __global__ void __launch_bounds__(kBlock) k_vertex_desc(const DevProb P, UnitD *vdesc) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -2603,7 +2695,7 @@ __global__ void __launch_bounds__(kBlock) k_vertex_desc(const DevProb P, UnitD *
         d.np = static_cast<uint32_t>(P.ipofs[k1] - d.p0);
         d.nd = static_cast<uint32_t>(P.idofs[k1] - d.d0);
         d.u = static_cast<int32_t>(v);
-        d.pad = 0;
+        d.hu = 0;
         vdesc[v] = d;
     }
 }
@@ -2629,48 +2721,49 @@ __global__ void __launch_bounds__(kBlock) k_unit_desc(const DevProb P, UnitD *rd
         d.np = static_cast<uint32_t>(P.pofs[e1] - d.p0);
         d.nd = static_cast<uint32_t>(P.dofs[e1] - d.d0);
         d.u = static_cast<int32_t>(u);
-        d.pad = 0;
+        d.hu = vertex_hash(static_cast<uint32_t>(u));
         // a split row's own descriptor is only read by the first sweep, which leaves the row to its tasks
         if (i < P.n && e1 - e0 > kHeavyDeg) d.u = -1;
         (i < P.n ? rdesc[i] : tdesc[i - P.n]) = d;
     }
 }
 
-// Per edge: its number of live simulations.  An edge live in at most dense_min of them contributes that many
-// pairs, any other edge one entry of the dense list.
-__global__ void __launch_bounds__(kBlock) k_pair_counts(const DevProb P, int32_t *npairs, int32_t *ndense) {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < P.m; e += stride) {
-        const uint32_t *lv = P.live + static_cast<size_t>(e) * P.W;
-        int c = 0;
-        for (int k = 0; k < P.W; ++k) c += __popc(lv[k]);
-        const bool dense = c > P.dense_min;
-        npairs[e] = dense ? 0 : c;
-        ndense[e] = dense ? 1 : 0;
-    }
-}
-
-// Writes the pairs of every sparse edge at pofs[e] (simulations in increasing order) and the dense edge ids.
+// Writes the pairs of every sparse edge at pofs[e] (simulations in increasing order) and the dense edge ids: the
+// first sweep's word of every pair, and its target and simulation when pv is given (pulling sweeps after the first,
+// or a rebuild that tests each pair's target).  A thread per edge: its live mask is loaded with 16-byte loads, Y
+// staged in shared memory.
+template <int R>
 __global__ void __launch_bounds__(kBlock) k_pair_fill(const DevProb P, int32_t *pv, uint16_t *pj, uint16_t *pq,
                                                       uint32_t *dlist) {
+    constexpr int W = R / 32;
+    constexpr int VW = W < 4 ? W : 4;
+    __shared__ uint32_t sY[R];
+    for (int j = threadIdx.x; j < R; j += blockDim.x) sY[j] = __ldg(&P.Y[j]);
+    __syncthreads();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < P.m; e += stride) {
-        const int64_t d0 = P.dofs[e];
-        if (P.dofs[e + 1] != d0) {
+        const int64_t d0 = __ldg(&P.dofs[e]);
+        if (__ldg(&P.dofs[e + 1]) != d0) {
             dlist[d0] = static_cast<uint32_t>(e);
             continue;
         }
-        int64_t at = P.pofs[e];
-        const int32_t v = P.adj[e];
+        int64_t at = __ldg(&P.pofs[e]);
+        if (__ldg(&P.pofs[e + 1]) == at) continue;
+        uint32_t w[W];
+#pragma unroll
+        for (int c = 0; c < W; c += VW) ldg_words<VW>(P.live + static_cast<size_t>(e) * W + c, w + c);
+        const int32_t v = __ldg(&P.adj[e]);
         const uint32_t hv = vertex_hash(static_cast<uint32_t>(v));
-        const uint32_t *lv = P.live + static_cast<size_t>(e) * P.W;
-        for (int k = 0; k < P.W; ++k) {
-            for (uint32_t w = lv[k]; w; w &= w - 1) {
-                const uint32_t j = 32 * k + __ffs(w) - 1;
-                pv[at] = v;
-                pj[at] = static_cast<uint16_t>(j);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            for (uint32_t b = w[k]; b; b &= b - 1u) {
+                const uint32_t j = 32u * k + __ffs(b) - 1u;
+                if (pv) {
+                    pv[at] = v;
+                    pj[at] = static_cast<uint16_t>(j);
+                }
                 // the first sweep's word: accumulator slot and the initial rank of (v, j)
-                pq[at] = static_cast<uint16_t>(sw_slot(j, 0) | (static_cast<uint32_t>(__clz(hv ^ __ldg(&P.Y[j]))) << 10));
+                pq[at] = static_cast<uint16_t>(sw_slot(j, 0) | (static_cast<uint32_t>(__clz(hv ^ sY[j])) << 10));
                 ++at;
             }
         }
@@ -3284,24 +3377,29 @@ void launch_edge_thresholds(const float *p, int64_t m, uint32_t *T, uint8_t *ok,
                             cudaStream_t s) {
     if (m > 0) k_edge_thresholds<<<g_grid_block, kBlock, 0, s>>>(p, m, T, ok, flags);
 }
-void launch_live_masks(const DevProb &P, cudaStream_t s) {
-    IMK_R_SWITCH(P.R, (k_live_masks<RR><<<g_grid_warp, kBlock, 0, s>>>(P)));
+template <int R>
+static void launch_live_masks_r(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
+    static int grid = 0;
+    if (grid == 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_live_masks<R>, kBlock, 0);
+        grid = g_sms * (occ > 0 ? occ : 1);
+    }
+    k_live_masks<R><<<grid, kBlock, 0, s>>>(P, npairs, ndense);
 }
-void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
-    k_pair_counts<<<g_grid_block, kBlock, 0, s>>>(P, npairs, ndense);
+void launch_live_masks(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
+    IMK_R_SWITCH(P.R, (launch_live_masks_r<RR>(P, npairs, ndense, s)));
 }
 void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint16_t *pq, uint32_t *dlist, cudaStream_t s) {
-    k_pair_fill<<<g_grid_block, kBlock, 0, s>>>(P, pv, pj, pq, dlist);
+    IMK_R_SWITCH(P.R, (k_pair_fill<RR><<<g_grid_warp, kBlock, 0, s>>>(P, pv, pj, pq, dlist)));
 }
-void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
-    k_inpair_counts<<<g_grid_block, kBlock, 0, s>>>(P, npairs, ndense);
+void launch_inpair_counts(const DevProb &P, const int32_t *np_out, const int32_t *nd_out, int32_t *npairs,
+                          int32_t *ndense, cudaStream_t s) {
+    k_inpair_counts<<<g_grid_block, kBlock, 0, s>>>(P, np_out, nd_out, npairs, ndense);
 }
-void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *iop, int32_t *idu, uint32_t *ide,
-                        cudaStream_t s) {
-    k_inpair_fill<<<g_grid_block, kBlock, 0, s>>>(P, iu, ij, iop, idu, ide);
-}
-void launch_inpair_targets(const DevProb &P, int32_t *iv, cudaStream_t s) {
-    k_inpair_targets<<<g_grid_warp, kBlock, 0, s>>>(P, iv);
+void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *iop, int32_t *iv, int32_t *idu,
+                        uint32_t *ide, cudaStream_t s) {
+    k_inpair_fill<<<g_grid_warp, kBlock, 0, s>>>(P, iu, ij, iop, iv, idu, ide);
 }
 void launch_vertex_desc(const DevProb &P, UnitD *vdesc, cudaStream_t s) {
     k_vertex_desc<<<g_grid_block, kBlock, 0, s>>>(P, vdesc);

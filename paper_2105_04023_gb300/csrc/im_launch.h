@@ -47,14 +47,13 @@ void launch_mc_live(int R, const DevProb *prob, uint64_t seed, int64_t s0, int64
 void launch_sample_counts(int R, const DevProb *prob, unsigned long long *counts, cudaStream_t s);
 void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned long long *gsum, cudaStream_t s);
 
-void launch_live_masks(const DevProb &P, cudaStream_t s);
-void launch_pair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
+void launch_live_masks(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
 void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint16_t *pq, uint32_t *dlist, cudaStream_t s);
-void launch_inpair_counts(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
-void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *iop, int32_t *idu, uint32_t *ide,
-                        cudaStream_t s);
+void launch_inpair_counts(const DevProb &P, const int32_t *np_out, const int32_t *nd_out, int32_t *npairs,
+                          int32_t *ndense, cudaStream_t s);
+void launch_inpair_fill(const DevProb &P, int32_t *iu, uint16_t *ij, uint32_t *iop, int32_t *iv, int32_t *idu,
+                        uint32_t *ide, cudaStream_t s);
 void launch_vertex_desc(const DevProb &P, UnitD *vdesc, cudaStream_t s);
-void launch_inpair_targets(const DevProb &P, int32_t *iv, cudaStream_t s);
 void launch_unit_desc(const DevProb &P, UnitD *rdesc, UnitD *tdesc, cudaStream_t s);
 void launch_words(uint64_t seed, int R, uint32_t *X, uint32_t *Y, cudaStream_t s);
 // Adds the graph's 64-bit fingerprint (edges and per-edge thresholds, if any) to *out.

@@ -155,6 +155,32 @@ def test_streamed_push_equals_vertex_push(monkeypatch, gname, p, R):
     assert np.array_equal(M1, Mo) and (s1, v1) == (so, vo)
 
 
+@pytest.mark.parametrize("pulls,gname,model,p,R", [(2, "rmat10", WC, 0.0, 256), (3, "er300", IC, 0.05, 64),
+                                                   (2, "hub1500", IC, 0.3, 512)])
+def test_pulled_later_sweeps_equal_the_oracle(monkeypatch, pulls, gname, model, p, R):
+    """With IM_PULL_SWEEPS the first sweeps after the first also pull into every row (they read the out-pairs'
+    targets and simulations, kept only then); registers, sweeps, visits and a selection with rebuilds still equal the
+    oracle's."""
+    g = SMALL[gname]
+    graph = im.Graph.from_synth(g, model, p)
+    monkeypatch.setenv("IM_PULL_SWEEPS", str(pulls))
+    c = im.Context(0)
+    monkeypatch.delenv("IM_PULL_SWEEPS")
+    try:
+        sk = c.im_build_sketches(graph, im.params(R=R, seed=8))
+        M, sweeps, visits = sk.im_sketch_registers(), *sk.im_sketch_info()[:2]
+        sk.close()
+        K = min(8, g.n)
+        sel = c.im_select_seeds(graph, im.params(R=R, K=K, eps_g=0.0, eps_l=0.0, seed=8))
+    finally:
+        c.close()
+    Mo, so, vo, _ = oracle.build_sketch(g.n, g.xadj, g.adj, model, p, R, 8)
+    assert np.array_equal(M, Mo) and (sweeps, visits) == (so, vo)
+    ref = oracle.select_seeds(g.n, g.xadj, g.adj, model, p, R, K, 0.0, 0.0, 0.0, 8)
+    assert sel["seeds"].tolist() == ref["seeds"].tolist()
+    assert sel["gsum"].tolist() == ref["gsum"].tolist()
+
+
 @pytest.mark.parametrize("model,p,R", [(IC, 0.02, 256), (WC, 0.0, 128)])
 def test_autotuned_shapes_give_the_same_selection(model, p, R):
     """The autotuner times every candidate launch shape on the first diffusion (it checks they agree) and keeps the

@@ -2553,8 +2553,10 @@ __global__ void __launch_bounds__(kBlock) k_inpair_counts(const DevProb P, const
 
 // The pairs and dense in-edges in in-CSR order: in-edge k (out-CSR edge e = ein[k], source u) gets e's out-pairs
 // at ipofs[k] as (u, simulation, out-pair index) with its target v in iv, or one dense entry (u, e).  A thread per
-// in-edge; a warp takes chunks of kInChunk consecutive in-edges, 32 at a time, and finds the target row of each from
-// the row of the previous 32 (a binary search at the chunk's start, then a short forward walk).
+// in-pair q, so every store is coalesced: a warp takes kInChunk consecutive in-pairs, 32 at a time; the in-edge k
+// holding q (the last k with ipofs[k] <= q) and its row v are found by binary searches at the chunk's start and
+// then by short forward walks from the previous 32's (consecutive in-pairs mostly share their in-edge).  The dense
+// in-edges follow, a thread per in-edge.
 constexpr int kInChunk = 1024;
 
 __global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t *iu, uint16_t *ij, uint32_t *iop,
@@ -2563,42 +2565,50 @@ __global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t
     const uint64_t worker = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nworkers = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
     const int64_t m = P.m, n = P.n;
-    const uint64_t chunks = (static_cast<uint64_t>(m) + kInChunk - 1) / kInChunk;
+    const int64_t npairs = P.ipofs[m];
+    const uint64_t chunks = (static_cast<uint64_t>(npairs) + kInChunk - 1) / kInChunk;
     for (uint64_t c = worker; c < chunks; c += nworkers) {
-        const int64_t k0 = static_cast<int64_t>(c) * kInChunk;
-        const int64_t k1 = k0 + kInChunk < m ? k0 + kInChunk : m;
-        int64_t vb = 0;  // the in-CSR row holding in-edge k0 (the last v with xadj_in[v] <= k0)
+        const int64_t q0 = static_cast<int64_t>(c) * kInChunk;
+        const int64_t q1 = q0 + kInChunk < npairs ? q0 + kInChunk : npairs;
+        int64_t kb = 0, vb = 0;  // the in-edge holding q0 and its in-CSR row
         {
-            int64_t lo = 0, hi = n - 1;
+            int64_t lo = 0, hi = m - 1;
             while (lo < hi) {
                 const int64_t mid = (lo + hi + 1) >> 1;
-                if (__ldg(&P.xadj_in[mid]) <= k0) lo = mid; else hi = mid - 1;
+                if (__ldg(&P.ipofs[mid]) <= q0) lo = mid; else hi = mid - 1;
+            }
+            kb = lo;
+            lo = 0;
+            hi = n - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(&P.xadj_in[mid]) <= kb) lo = mid; else hi = mid - 1;
             }
             vb = lo;
         }
-        for (int64_t kb = k0; kb < k1; kb += 32) {
-            const int64_t k = kb + lane;
-            int64_t v = vb;
-            if (k < k1) {
-                while (__ldg(&P.xadj_in[v + 1]) <= k) ++v;  // ends at the row holding k (k < xadj_in[n])
+        for (int64_t qb = q0; qb < q1; qb += 32) {
+            const int64_t q = qb + lane;
+            int64_t k = kb, v = vb;
+            if (q < q1) {
+                while (__ldg(&P.ipofs[k + 1]) <= q) ++k;      // ends at the in-edge holding q
+                while (__ldg(&P.xadj_in[v + 1]) <= k) ++v;    // and at its row
                 const int64_t e = __ldg(&P.ein[k]);
-                const int32_t u = __ldg(&P.adj_in[k]);
-                const int64_t dd = __ldg(&P.idofs[k]);
-                if (__ldg(&P.idofs[k + 1]) != dd) {
-                    idu[dd] = u;
-                    ide[dd] = static_cast<uint32_t>(e);
-                } else {
-                    const int64_t p0 = __ldg(&P.pofs[e]), p1 = __ldg(&P.pofs[e + 1]);
-                    int64_t at = __ldg(&P.ipofs[k]);
-                    for (int64_t p = p0; p < p1; ++p, ++at) {
-                        iu[at] = u;
-                        ij[at] = static_cast<uint16_t>(sw_slot(__ldg(&P.pq[p]) & 0x3FFu, 0));  // the slot map inverts itself
-                        iv[at] = static_cast<int32_t>(v);
-                        if (iop) iop[at] = static_cast<uint32_t>(p);  // the same pair in out-CSR order
-                    }
-                }
+                const int64_t pp = __ldg(&P.pofs[e]) + (q - __ldg(&P.ipofs[k]));
+                iu[q] = __ldg(&P.adj_in[k]);
+                ij[q] = static_cast<uint16_t>(sw_slot(__ldg(&P.pq[pp]) & 0x3FFu, 0));  // the slot map inverts itself
+                iv[q] = static_cast<int32_t>(v);
+                if (iop) iop[q] = static_cast<uint32_t>(pp);  // the same pair in out-CSR order
             }
-            vb = __shfl_sync(kFull, v, 31);  // the last lane's row (lanes past k1 keep vb: the loop ends anyway)
+            kb = __shfl_sync(kFull, k, 31);  // the last lane's (lanes past q1 keep theirs: the loop ends anyway)
+            vb = __shfl_sync(kFull, v, 31);
+        }
+    }
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < m; k += stride) {
+        const int64_t dd = __ldg(&P.idofs[k]);
+        if (__ldg(&P.idofs[k + 1]) != dd) {
+            idu[dd] = __ldg(&P.adj_in[k]);
+            ide[dd] = __ldg(&P.ein[k]);
         }
     }
 }
@@ -2730,43 +2740,70 @@ __global__ void __launch_bounds__(kBlock) k_unit_desc(const DevProb P, UnitD *rd
 
 // Writes the pairs of every sparse edge at pofs[e] (simulations in increasing order) and the dense edge ids: the
 // first sweep's word of every pair, and its target and simulation when pv is given (pulling sweeps after the first,
-// or a rebuild that tests each pair's target).  A thread per edge: its live mask is loaded with 16-byte loads, Y
-// staged in shared memory.
+// or a rebuild that tests each pair's target).  A warp takes 32 consecutive edges, a lane each (its live mask loaded
+// with 16-byte loads, Y staged in shared memory): the lanes write their pair words into a per-warp stage in shared
+// memory at their offsets within the 32 edges' pairs, which are contiguous, and the warp then copies the stage out
+// with coalesced stores (edges with more pairs than the stage holds write directly).
+constexpr int kPairStage = 2048;  // pair words a warp stages (32 edges of at most 64 pairs each)
+
 template <int R>
 __global__ void __launch_bounds__(kBlock) k_pair_fill(const DevProb P, int32_t *pv, uint16_t *pj, uint16_t *pq,
                                                       uint32_t *dlist) {
     constexpr int W = R / 32;
     constexpr int VW = W < 4 ? W : 4;
     __shared__ uint32_t sY[R];
+    __shared__ uint16_t sP[kWarpsPerBlock][kPairStage];
     for (int j = threadIdx.x; j < R; j += blockDim.x) sY[j] = __ldg(&P.Y[j]);
     __syncthreads();
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < P.m; e += stride) {
-        const int64_t d0 = __ldg(&P.dofs[e]);
-        if (__ldg(&P.dofs[e + 1]) != d0) {
-            dlist[d0] = static_cast<uint32_t>(e);
-            continue;
-        }
-        int64_t at = __ldg(&P.pofs[e]);
-        if (__ldg(&P.pofs[e + 1]) == at) continue;
-        uint32_t w[W];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t worker = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nworkers = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int64_t m = P.m;
+    uint16_t *stage = sP[wib];
+    for (uint64_t it = worker; it < (static_cast<uint64_t>(m) + 31) / 32; it += nworkers) {
+        const int64_t e0 = static_cast<int64_t>(it) * 32;
+        const int64_t e1 = e0 + 32 < m ? e0 + 32 : m;
+        const int64_t pb = __ldg(&P.pofs[e0]), pe = __ldg(&P.pofs[e1]);
+        const bool staged = pe - pb <= kPairStage;
+        const int64_t e = e0 + lane;
+        if (e < e1) {
+            const int64_t d0 = __ldg(&P.dofs[e]);
+            if (__ldg(&P.dofs[e + 1]) != d0) {
+                dlist[d0] = static_cast<uint32_t>(e);
+            } else {
+                const int64_t p0 = __ldg(&P.pofs[e]);
+                if (__ldg(&P.pofs[e + 1]) != p0) {
+                    uint32_t w[W];
 #pragma unroll
-        for (int c = 0; c < W; c += VW) ldg_words<VW>(P.live + static_cast<size_t>(e) * W + c, w + c);
-        const int32_t v = __ldg(&P.adj[e]);
-        const uint32_t hv = vertex_hash(static_cast<uint32_t>(v));
+                    for (int c = 0; c < W; c += VW) ldg_words<VW>(P.live + static_cast<size_t>(e) * W + c, w + c);
+                    const int32_t v = __ldg(&P.adj[e]);
+                    const uint32_t hv = vertex_hash(static_cast<uint32_t>(v));
+                    int64_t at = p0;
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            for (uint32_t b = w[k]; b; b &= b - 1u) {
-                const uint32_t j = 32u * k + __ffs(b) - 1u;
-                if (pv) {
-                    pv[at] = v;
-                    pj[at] = static_cast<uint16_t>(j);
+                    for (int k = 0; k < W; ++k) {
+                        for (uint32_t b = w[k]; b; b &= b - 1u) {
+                            const uint32_t j = 32u * k + __ffs(b) - 1u;
+                            if (pv) {
+                                pv[at] = v;
+                                pj[at] = static_cast<uint16_t>(j);
+                            }
+                            // the first sweep's word: accumulator slot and the initial rank of (v, j)
+                            const uint16_t word = static_cast<uint16_t>(
+                                sw_slot(j, 0) | (static_cast<uint32_t>(__clz(hv ^ sY[j])) << 10));
+                            if (staged)
+                                stage[at - pb] = word;
+                            else
+                                pq[at] = word;
+                            ++at;
+                        }
+                    }
                 }
-                // the first sweep's word: accumulator slot and the initial rank of (v, j)
-                pq[at] = static_cast<uint16_t>(sw_slot(j, 0) | (static_cast<uint32_t>(__clz(hv ^ sY[j])) << 10));
-                ++at;
             }
         }
+        if (!staged) continue;  // the same for the whole warp
+        __syncwarp();
+        for (int64_t i = lane; i < pe - pb; i += 32) pq[pb + i] = stage[i];
+        __syncwarp();
     }
 }
 

@@ -34,9 +34,10 @@ UNIT = "edge-sim visits/s"
 WORKLOADS = {
     "chunglu22_ic": "Chung-Lu n=2^22, mean degree 16, degree exponent 2.1, independent cascade p=0.01",
     "rmat20_wc": "R-MAT scale 20, edge factor 16 (a,b,c,d = .57,.19,.19,.05), weighted cascade",
+    "chunglu20_ic": "Chung-Lu n=2^20, mean degree 16, degree exponent 2.1, independent cascade p=0.01 (profiling case)",
 }
 # the oracle sample of one step: the first Jacobi sweep over every ORACLE_STRIDE-th row
-ORACLE_STRIDE = {"chunglu22_ic": 32, "rmat20_wc": 1}
+ORACLE_STRIDE = {"chunglu22_ic": 32, "rmat20_wc": 1, "chunglu20_ic": 8}
 
 
 def load_workload(name: str):
@@ -372,7 +373,11 @@ def run_build(args, local):
     prop_bytes = sum(r["prop_bytes"] for r in rows)
     visits = sum(r["visits"] for r in rows)
     total_ms = sum(r["total_ms"] for r in rows)
-    out = {"mode": "build", "variant": os.environ.get("IM_PROP_VARIANT", "0"), "steps": args.steps,
+    first_ms = sum(r["first_ms"] for r in rows)
+    first_bytes = sum(r["first_bytes"] for r in rows)
+    out = {"mode": "build", "workload": WORKLOADS[args.workload], "variant": os.environ.get("IM_PROP_VARIANT", "0"),
+           "steps": args.steps, "first_ms": first_ms / args.steps, "first_bytes": first_bytes // args.steps,
+           "first_GBps": first_bytes / first_ms / 1e6 if first_ms > 0 else None,
            "build_ms": total_ms / args.steps, "prop_ms": prop_ms / args.steps, "sweeps": rows[0]["sweeps"],
            "visits": visits // args.steps, "prop_GBps": prop_bytes / prop_ms / 1e6,
            "frac": prop_bytes / prop_ms / 1e6 / hbm, "visits_per_s": visits / (total_ms / 1000),

@@ -53,6 +53,14 @@ def chunglu22_ic(cache: bool = False) -> Problem:
     return Problem(g, IC, 0.01, R=512, K=100, eps_g=0.02, seed=3, name="chunglu_n4M_d16_ic0.01_R512_K100")
 
 
+def chunglu20_ic(cache: bool = False) -> Problem:
+    """The Chung-Lu recipe at n=2^20 (mean degree 16, exponent 2.1, IC p=0.01, R=512): the profiling case of the
+    n=2^22 workload, small enough for multi-pass profiler captures."""
+    g = (graphs.cached(lambda: graphs.chung_lu(1 << 20, 16.0, 2.1, seed=3), "chunglu_n20_d16_g2.1_seed3") if cache
+         else graphs.chung_lu(1 << 20, 16.0, 2.1, seed=3))
+    return Problem(g, IC, 0.01, R=512, K=100, eps_g=0.02, seed=3, name="chunglu_n1M_d16_ic0.01_R512_K100")
+
+
 _BATCH_MODELS = ((IC, 0.005), (IC, 0.01), (IC, 0.05), (WC, 0.0))
 _BATCH_R = (64, 128, 256)
 

@@ -329,6 +329,9 @@ struct Prob {
     im_status status = IM_OK;  // failure of this problem when the engine keeps going (serving)
     std::string error;
     int variant = 0;  // register budget of the first-sweep kernel (resident blocks per SM; 0: default)
+    // search levels: the counter at the start of the current search, and the length of the last finished one
+    uint64_t levels_at_start = 0;
+    uint32_t last_search_levels = 0;
 };
 
 // Shape class of a graph for the autotuner: floor(log2(mean out-degree)) + 1, 0 below one edge per vertex.
@@ -907,6 +910,7 @@ struct Engine {
                     if (P.merge_pending) merge.push_back(i);
                     scan.push_back(i);
                     bfs.push_back(i);
+                    P.levels_at_start = P.last.levels_total;  // this step's search starts in this tick
                     any = true;
                     break;
                 case Prob::kBfs: bfs.push_back(i); any = true; break;
@@ -931,7 +935,14 @@ struct Engine {
         }
         enqueue_sweeps(sweep, ctx->sweep_chunk, !init.empty());
         enqueue_scan(scan);
-        enqueue_bfs(bfs, ctx->level_chunk);
+        // a search takes about as many levels as the problem's previous one (seeds of one selection reach alike), so
+        // a tick enqueues that many and two more, up to level_chunk; a longer search takes another tick
+        int lchunk = 0;
+        for (int32_t i : bfs) {
+            const Prob &P = *probs[i];
+            lchunk = std::max(lchunk, P.last_search_levels ? static_cast<int>(P.last_search_levels) + 2 : ctx->level_chunk);
+        }
+        enqueue_bfs(bfs, std::min(std::max(lchunk, 1), ctx->level_chunk));
         flush();
         read_counters();
         for (int32_t i : init) {
@@ -955,6 +966,7 @@ struct Engine {
                 else
                     P.phase = P.greedy ? Prob::kScan : Prob::kDone;
             } else if (P.phase == Prob::kBfs && P.last.bdone) {
+                P.last_search_levels = static_cast<uint32_t>(P.last.levels_total - P.levels_at_start);
                 if (P.last.btimeout)
                     problem_error(P, IM_ETIMEOUT, "reachability search exceeded max_sweeps levels");
                 else

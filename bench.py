@@ -208,7 +208,7 @@ def config(prob, args):
     return {"workload": WORKLOADS[args.workload], "name": args.workload,
             "n": g.n, "m": g.m, "R": prob.R, "K": prob.K, "eps_g": prob.eps_g, "eps_l": prob.eps_l,
             "eps_c": prob.eps_c, "seed": prob.seed, "parallelism": f"replicas{args.gpus}",
-            "l2": f"flushed between steps (256 MiB write); registers 2 x {g.n * prob.R >> 20} MiB exceed L2"}
+            "l2": f"flushed between steps (256 MiB write); registers 3 x {g.n * prob.R >> 20} MiB exceed L2"}
 
 
 def run_ours(args, world, rank, local):
@@ -315,8 +315,8 @@ def run_ours(args, world, rank, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth (sustained copy; of measured)",
-                         "kernel": "k_first: the first sweep of every diffusion (initial registers formed in the "
-                                   "kernel, every sparse pair merged, every row written to both buffers)",
+                         "kernel": "k_first: the first sweep of every diffusion (initial registers read from the "
+                                   "problem's table, every sparse pair merged, every row written to both buffers)",
                          "bytes_per_launch": first_bytes / max(first_launches, 1),
                          "launches": first_launches, "ms": first_ms,
                          "all_sweep_kernels": {"achieved": sweeps_achieved,

@@ -157,7 +157,9 @@ struct DevProb {
     uint32_t *vis;             // n x W: v in R_{G_j}(S)
     uint32_t *rany;            // bit per vertex: reached by S in some simulation (set at a rebuild; NULL: no search)
     uint16_t *pqb;             // residual blocking: this problem's copy of pq with the ranks of blocked (v, j) at 0
-    uint32_t *vis_done;        // n x W: the blocked bits already applied to prb
+    uint8_t *Mi;               // n x R: the initial registers (Algorithm 1's initialisation) the first sweep of a
+                               // diffusion reads, with the blocked (v, j) at 0 under residual blocking
+    uint32_t *vis_done;        // n x W: the blocked bits already applied to Mi and pqb
     uint32_t *rnew;            // bit per vertex: has bits in vis not yet in vis_done (set by k_init)
     uint32_t *del[3];          // n x W: bits newly reached at the previous level, by level mod 3
     uint32_t *lstamp;          // per vertex: 1 + the last level that listed it

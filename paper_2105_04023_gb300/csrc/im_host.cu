@@ -553,6 +553,12 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     d.Y = Y;
     d.M0 = mem.alloc<uint8_t>(static_cast<size_t>(n) * R);
     d.M1 = mem.alloc<uint8_t>(static_cast<size_t>(n) * R);
+    // the initial registers the first sweep of every diffusion reads (rebuilds zero the blocked ones in place)
+    d.Mi = mem.alloc<uint8_t>(static_cast<size_t>(std::max<int64_t>(n, 1)) * R);
+    if (n > 0) {
+        launch_init_table(d, ctx->stream);
+        ctx->launches += 1;
+    }
     d.part = mem.alloc<uint8_t>(static_cast<size_t>(std::max<int64_t>(g.n_tasks, 1)) * R);
     d.part_any = mem.alloc<uint32_t>((g.n_tasks + 31) / 32 + 1, true);
     const int64_t words = (n + 31) / 32;
@@ -588,14 +594,17 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     if (greedy) {
         alloc_bfs(*P);
         d.gst = mem.alloc<uint32_t>(static_cast<size_t>(n));
-        // residual blocking applied to a copy of the pair ranks at each rebuild (the first sweep then tests nothing)
-        if (d.iop && prm.blocking == IM_BLOCK_RESIDUAL && P->npairs > 0) {
-            d.pqb = mem.alloc<uint16_t>(static_cast<size_t>(P->npairs));
-            ck(cudaMemcpyAsync(d.pqb, d.pq, static_cast<size_t>(P->npairs) * sizeof(uint16_t), cudaMemcpyDeviceToDevice,
-                               ctx->stream),
-               "copy pair words");
+        // residual blocking applied at each rebuild to the initial registers and to a copy of the pair ranks (the
+        // first sweep then tests nothing)
+        if (prm.blocking == IM_BLOCK_RESIDUAL) {
             d.vis_done = mem.alloc<uint32_t>(static_cast<size_t>(n) * (R / 32), true);
             d.rnew = mem.alloc<uint32_t>(words, true);
+            if (d.iop && P->npairs > 0) {
+                d.pqb = mem.alloc<uint16_t>(static_cast<size_t>(P->npairs));
+                ck(cudaMemcpyAsync(d.pqb, d.pq, static_cast<size_t>(P->npairs) * sizeof(uint16_t),
+                                   cudaMemcpyDeviceToDevice, ctx->stream),
+                   "copy pair words");
+            }
         }
         d.step_seed = mem.alloc<uint32_t>(prm.K);
         d.step_gsum = mem.alloc<uint32_t>(prm.K);
@@ -1445,7 +1454,7 @@ uint64_t query_footprint(const GraphDev &g, const im_params &prm) {
     const uint64_t words = (n + 31) / 32, nt = std::max<int64_t>(g.n_tasks, 1);
     uint64_t b = 0;
     b += r(4 * R) * 2;                                       // X, Y
-    b += r(n * R) * 2;                                       // register buffers
+    b += r(n * R) * 3;                                       // register buffers, initial registers
     b += r(nt * R) + r(4 * (static_cast<uint64_t>(g.n_tasks) / 32 + 1));  // partial rows, their bits
     b += r(4 * words) * 2;                                   // L bits
     b += r(n * R / 8);                                       // changed-register masks of the push sweeps

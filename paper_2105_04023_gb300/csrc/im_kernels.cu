@@ -8,7 +8,10 @@
 // Paper map:
 //   k_init        Algorithm 1, register initialisation (and its re-initialisation with R_G(S) blocked)
 //   k_first       Algorithm 1's initialisation fused into Algorithm 2's first sweep (L = V): every register it
-//                 reads is an initial rank, computed from (v, j); it writes every row of both register buffers.
+//                 reads is an initial rank (the pair words carry their neighbour's, the problem's table Mi the
+//                 row's own and the dense neighbours'); it writes every row of both register buffers.
+//   k_init_table  the table Mi of initial ranks, once per problem (rebuilds zero its blocked entries in
+//                 k_block_done)
 //                 The sampling of Eq. 4-5 is evaluated once per run (k_live_masks) and kept as (target,
 //                 simulation) pairs for edges live in few simulations (k_pair_fill, and in in-CSR order
 //                 k_inpair_fill) and as live masks for the others
@@ -180,9 +183,9 @@ __device__ __forceinline__ unsigned tile_mask(int g) {
 }
 
 // The first sweep of a diffusion reads every register before any sweep has changed it, so every register it
-// reads is an initial rank (Algorithm 1's initialisation), which is computed from (v, j) instead of loaded:
-// M_v[j] = clz(hash(v) XOR Y_j), or 0 where v is in R_{G_j}(S) (a rebuild).  P.rany marks the vertices reached in
-// some simulation (their blocked bits are then read from vis); it is NULL when there is no seed set.
+// reads is an initial rank (Algorithm 1's initialisation): M_v[j] = clz(hash(v) XOR Y_j), or 0 where v is in
+// R_{G_j}(S) (a rebuild).  P.rany marks the vertices reached in some simulation (their blocked bits are then read
+// from vis); it is NULL when there is no seed set.
 __device__ __forceinline__ uint32_t blocked16(const DevProb &P, int64_t v, int ch) {
     if (!P.rany || !test_bit(P.rany, v)) return 0u;
     return (__ldg(&P.vis[static_cast<size_t>(v) * P.W + (ch >> 1)]) >> (16 * (ch & 1))) & 0xFFFFu;
@@ -281,12 +284,11 @@ __device__ __forceinline__ uint32_t dense_tile(const DevProb &P, int64_t d0, int
                 v = __ldg(&P.adj[e]);
                 in[r] = allL || test_bit(Lcur, v);
             }
-            const uint32_t hv = INIT ? vertex_hash(static_cast<uint32_t>(v)) : 0u;
 #pragma unroll
             for (int c = 0; c < Gm::CPL; ++c) {
                 const int ch = li + Gm::G * c;  // 16-simulation chunk: half (ch & 1) of mask word ch / 2
-                if (INIT)
-                    row[r][c] = in[r] ? init_chunk_sw(Ys, hv, ch, chk ? init_blocked16(P, v, ch) : 0u)
+                if (INIT)  // the neighbour's initial registers (blocked ones 0 under residual blocking)
+                    row[r][c] = in[r] ? __ldg(reinterpret_cast<const uint4 *>(P.Mi + static_cast<size_t>(v) * R) + ch)
                                       : make_uint4(0, 0, 0, 0);
                 else
                     row[r][c] = in[r] ? __ldg(reinterpret_cast<const uint4 *>(Mcur + static_cast<size_t>(v) * R) + ch)
@@ -680,11 +682,11 @@ __device__ __forceinline__ void finalize_first(const DevProb &P, int64_t u, cons
 // unit is processed, the pair records and ranks of the next unit's first 4 G pairs and the descriptor of the unit
 // after it are already in flight, so the chain descriptor -> pairs -> merge of one unit overlaps the previous one.
 // The descriptors wait in a per-tile ring of three in shared memory (ring: 3 x 8 words, 16-byte aligned), loaded a
-// word a lane, and each prefetched pair is one word (simulation | rank << 16), to keep the registers few.  A row's
-// own initial ranks are formed after its merges, when fewer registers are live.
+// word a lane, and each prefetched pair is its 16-bit word (slot, rank), to keep the registers few.  A row's own
+// initial registers come from the problem's table Mi (loaded before the merges, used after them).
 template <int R>
 __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, uint64_t nworkers, unsigned tm,
-                                int li, uint32_t *acc32, const uint32_t *Ys, uint32_t *ring) {
+                                int li, uint32_t *acc32, uint32_t *ring) {
     using Gm = Geo<R>;
     constexpr int G = Gm::G;
     constexpr int DW = sizeof(UnitD) / 4;  // descriptor words
@@ -696,8 +698,7 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
     const bool rebuild = P.rany && P.ctr->lvl != 0;  // some vertices are blocked
     // a rebuild without the problem's own blocked ranks tests each pair's neighbour (residual blocking only)
     const bool test = rebuild && !P.pqb && !P.literal;
-    const bool zero_own = rebuild && !P.literal;  // residual blocking: a blocked register of the row is 0
-    const bool keep_own = rebuild && P.literal;   // literal blocking: a blocked register is never raised
+    const bool keep_own = rebuild && P.literal;  // literal blocking: a blocked register is never raised
     const uint32_t tx = sw_tile(static_cast<uint32_t>((threadIdx.x & 31) / G));  // this tile's slot permutation
     unsigned long long pairs = 0, bytes = 0;  // counted by lane 0 of the tile
     // this lane's words (li, li + G, ...) of descriptor l (zeros past the end)
@@ -763,6 +764,12 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
         load_desc(l + 2 * nworkers, wn);          // and the descriptor after it
         const bool is_row = l < n;
         if (!(is_row && cur.u < 0)) {  // a split row is left to its tasks and the combine kernels
+            // the row's initial registers (blocked ones 0 under residual blocking), loaded before the merges
+            uint4 own[Gm::CPL];
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c)
+                own[c] = is_row ? __ldg(reinterpret_cast<const uint4 *>(P.Mi + static_cast<size_t>(cur.u) * R) + li + G * c)
+                                : make_uint4(0, 0, 0, 0);
             uint32_t acc[Gm::CPL][4];
 #pragma unroll
             for (int c = 0; c < Gm::CPL; ++c)
@@ -780,21 +787,17 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
                 fold_tile<R, true>(acc, acc32, tm, li);
             }
             if (cur.nd > 0)
-                dense_tile<R, true>(P, cur.d0, cur.d0 + cur.nd, true, nullptr, nullptr, Ys, rebuild, acc, li);
-            // modelled bytes: descriptor, pair words (slot, rank), dense edges (id, target, threshold, mask), and
-            // the row written to both buffers with its change mask (or a task's partial row)
+                dense_tile<R, true>(P, cur.d0, cur.d0 + cur.nd, true, nullptr, nullptr, nullptr, rebuild, acc, li);
+            // modelled bytes: descriptor, pair words (slot, rank), dense edges (id, target, threshold, mask, the
+            // neighbour's initial row), and the row's initial registers read and the row written to both buffers
+            // with its change mask (or a task's partial row)
             if (li == 0) {
                 pairs += cur.np;
-                bytes += 32 + 2 * static_cast<uint64_t>(cur.np) + (8 + tb + R / 8) * static_cast<uint64_t>(cur.nd) +
-                         (is_row ? 2 * R + R / 8 : (cur.np + cur.nd > 0 ? R : 0));
+                bytes += 32 + 2 * static_cast<uint64_t>(cur.np) + (8 + tb + R / 8 + R) * static_cast<uint64_t>(cur.nd) +
+                         (is_row ? 3 * R + R / 8 : (cur.np + cur.nd > 0 ? R : 0));
             }
             if (is_row) {
                 const int64_t u = cur.u;
-                uint4 own[Gm::CPL];
-#pragma unroll
-                for (int c = 0; c < Gm::CPL; ++c)
-                    own[c] = zero_own ? init_chunk_sw<true>(Ys, cur.hu, li + G * c, blocked16(P, u, li + G * c))
-                                      : init_chunk_sw<false>(Ys, cur.hu, li + G * c, 0u);
                 if (keep_own) drop_blocked<R>(P, u, acc, li);
                 finalize_first<R>(P, u, acc, own, P.Lb1, tm, li);
             } else if (cur.np + cur.nd > 0) {
@@ -1168,7 +1171,6 @@ __global__ void __launch_bounds__(kBlock, MINB) k_first(const DevProb *__restric
                                                         const int32_t *__restrict__ act, int nact) {
     using Gm = Geo<R>;
     extern __shared__ __align__(16) uint4 gather_smem[];
-    __shared__ __align__(16) uint32_t sY[R];  // the problem's initialisation words Y_j (slots sw_slot(j, 0))
     __shared__ __align__(16) uint32_t sring[kWarpsPerBlock * Geo<R>::NG][3 * 8];  // per tile: three unit descriptors
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int g = lane / Gm::G, li = lane % Gm::G;
@@ -1182,14 +1184,11 @@ __global__ void __launch_bounds__(kBlock, MINB) k_first(const DevProb *__restric
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
         if (C.done || !C.full || C.t != 0) continue;  // the same for every thread of the block
-        __syncthreads();  // the previous problem's use of sY is over
-        for (int k = threadIdx.x; k < R; k += blockDim.x) sY[sw_slot(k, 0)] = __ldg(&P.Y[k]);
-        __syncthreads();
         const uint64_t cnt = static_cast<uint64_t>(P.n) + static_cast<uint64_t>(P.n_tasks);
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
         if (first >= cnt) continue;
-        first_problem_t<R>(P, cnt, first, nworkers, tm, li, acc32, sY, sring[wib * Geo<R>::NG + g]);
+        first_problem_t<R>(P, cnt, first, nworkers, tm, li, acc32, sring[wib * Geo<R>::NG + g]);
     }
 }
 
@@ -1654,7 +1653,8 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 if (searched && v < P.n) {
                     const uint2 *row = reinterpret_cast<const uint2 *>(P.vis + static_cast<size_t>(v) * P.W);
                     const uint2 *done =
-                        P.pqb ? reinterpret_cast<const uint2 *>(P.vis_done + static_cast<size_t>(v) * P.W) : nullptr;
+                        P.vis_done ? reinterpret_cast<const uint2 *>(P.vis_done + static_cast<size_t>(v) * P.W)
+                                   : nullptr;
                     for (int k = 0; k < P.W / 2; ++k) {
                         const uint2 x = row[k];
                         any |= x.x | x.y;
@@ -1668,7 +1668,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 const uint32_t fresh = __ballot_sync(kFull, nw != 0);
                 if (lane == 0) {
                     P.rany[wi] = bits;
-                    if (P.pqb) P.rnew[wi] = fresh;  // vertices with blocked bits not yet in the pair ranks
+                    if (P.rnew) P.rnew[wi] = fresh;  // vertices with blocked bits not yet applied
                 }
             }
         }
@@ -2672,8 +2672,9 @@ __global__ void __launch_bounds__(kBlock) k_block_pairs(const DevProb *__restric
     }
 }
 
-// After k_block_pairs: the blocked bits now applied to the pair ranks (vis_done = vis for the rows with new bits).
-// A warp per 32 vertices; most words of rnew are zero.
+// After k_block_pairs: the newly blocked (v, j) (set in vis, not yet in vis_done) become 0 in the problem's initial
+// registers Mi (residual blocking), and vis_done takes vis for the rows with new bits.  A warp per 32 vertices
+// (most words of rnew are zero), a lane per 32-simulation word of a marked row.
 __global__ void __launch_bounds__(kBlock) k_block_done(const DevProb *__restrict__ probs,
                                                        const int32_t *__restrict__ act, int nact) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -2682,14 +2683,20 @@ __global__ void __launch_bounds__(kBlock) k_block_done(const DevProb *__restrict
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
-        if (!P.pqb || P.ctr->lvl == 0) continue;
+        if (!P.vis_done || P.ctr->lvl == 0) continue;
         const uint64_t cnt = (static_cast<uint64_t>(P.n) + 31) / 32;
         const uint64_t first = first_owned(worker, nworkers, base);
         base += cnt;
         for (uint64_t l = first; l < cnt; l += nworkers)
             for (uint32_t m = P.rnew[l]; m; m &= m - 1u) {
-                const size_t row = (l * 32 + (__ffs(m) - 1)) * static_cast<size_t>(P.W);
-                for (int k = lane; k < P.W; k += 32) P.vis_done[row + k] = P.vis[row + k];
+                const uint64_t v = l * 32 + (__ffs(m) - 1);
+                const size_t row = v * static_cast<size_t>(P.W);
+                for (int k = lane; k < P.W; k += 32) {
+                    const uint32_t x = P.vis[row + k];
+                    for (uint32_t nb = x & ~P.vis_done[row + k]; nb; nb &= nb - 1u)
+                        P.Mi[v * P.R + 32u * k + (__ffs(nb) - 1)] = 0;
+                    P.vis_done[row + k] = x;
+                }
             }
     }
 }
@@ -2735,6 +2742,23 @@ __global__ void __launch_bounds__(kBlock) k_unit_desc(const DevProb P, UnitD *rd
         // a split row's own descriptor is only read by the first sweep, which leaves the row to its tasks
         if (i < P.n && e1 - e0 > kHeavyDeg) d.u = -1;
         (i < P.n ? rdesc[i] : tdesc[i - P.n]) = d;
+    }
+}
+
+// The initial registers of every (v, j): Mi[v][j] = clz(vertex_hash(v) XOR Y_j) (Algorithm 1's initialisation, no
+// seed set yet).  A thread per 16-register chunk, Y staged in shared memory.
+template <int R>
+__global__ void __launch_bounds__(kBlock) k_init_table(const DevProb P) {
+    constexpr int CH = R / 16;
+    __shared__ __align__(16) uint32_t sY[R];
+    for (int j = threadIdx.x; j < R; j += blockDim.x) sY[j] = __ldg(&P.Y[j]);
+    __syncthreads();
+    const uint64_t items = static_cast<uint64_t>(P.n) * CH;
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < items;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t v = static_cast<uint32_t>(i / CH);
+        const int ch = static_cast<int>(i % CH);
+        reinterpret_cast<uint4 *>(P.Mi)[i] = init_chunk(sY, vertex_hash(v), ch, 0u);
     }
 }
 
@@ -3426,6 +3450,9 @@ static void launch_live_masks_r(const DevProb &P, int32_t *npairs, int32_t *nden
 }
 void launch_live_masks(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s) {
     IMK_R_SWITCH(P.R, (launch_live_masks_r<RR>(P, npairs, ndense, s)));
+}
+void launch_init_table(const DevProb &P, cudaStream_t s) {
+    IMK_R_SWITCH(P.R, (k_init_table<RR><<<g_grid_block, kBlock, 0, s>>>(P)));
 }
 void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint16_t *pq, uint32_t *dlist, cudaStream_t s) {
     IMK_R_SWITCH(P.R, (k_pair_fill<RR><<<g_grid_warp, kBlock, 0, s>>>(P, pv, pj, pq, dlist)));

@@ -48,6 +48,7 @@ void launch_sample_counts(int R, const DevProb *prob, unsigned long long *counts
 void launch_estimate(const DevProb *prob, const int32_t *seeds, int k, unsigned long long *gsum, cudaStream_t s);
 
 void launch_live_masks(const DevProb &P, int32_t *npairs, int32_t *ndense, cudaStream_t s);
+void launch_init_table(const DevProb &P, cudaStream_t s);
 void launch_pair_fill(const DevProb &P, int32_t *pv, uint16_t *pj, uint16_t *pq, uint32_t *dlist, cudaStream_t s);
 void launch_inpair_counts(const DevProb &P, const int32_t *np_out, const int32_t *nd_out, int32_t *npairs,
                           int32_t *ndense, cudaStream_t s);

@@ -122,7 +122,7 @@ def test_budget_limits_admission(ctx):
 
 
 def test_cancel_and_over_budget(ctx):
-    srv = im.Server(ctx, hbm_budget_bytes=4 << 20, max_active=1)
+    srv = im.Server(ctx, hbm_budget_bytes=8 << 20, max_active=1)
     gid = srv.im_server_add_graph(_graph(1))
     t1 = srv.im_server_submit(gid, im.params(R=64, K=3, eps_g=0.01, seed=5))
     t2 = srv.im_server_submit(gid, im.params(R=64, K=3, eps_g=0.01, seed=6))

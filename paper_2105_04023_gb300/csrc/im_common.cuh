@@ -10,9 +10,21 @@ namespace imk {
 
 constexpr int kBlock = 256;          // threads per block of every kernel
 constexpr int kWarpsPerBlock = kBlock / 32;
-constexpr int kHeavyDeg = 64;        // rows with more out-edges are split into tasks of kTaskEdges edges
+constexpr int kHeavyDeg = 64;        // rows with more out-edges are split into tasks (task_edges)
 constexpr int kTaskEdges = 64;
 constexpr int kBigTasks = 32;        // split rows with more tasks are merged by a whole block
+constexpr int kMaxTaskEdges = 1024;
+
+// Edges of each task of a split row with d out-edges: kTaskEdges, or for hubs (d > kTaskEdges * kBigTasks) a
+// multiple of kTaskEdges near d / 512, at most kMaxTaskEdges, so that a hub has about 512 partial rows to merge
+// (more only past 512 kMaxTaskEdges edges): the one block that merges a hub's partials was the critical path for
+// hubs of 10^5 to 10^6 edges in 64-edge tasks.  The first sweep hands tasks out dynamically, so their unequal
+// lengths do not unbalance it.
+__host__ __device__ __forceinline__ int64_t task_edges(int64_t d) {
+    if (d <= static_cast<int64_t>(kTaskEdges) * kBigTasks) return kTaskEdges;
+    const int64_t t = ((d + 511) / 512 + kTaskEdges - 1) / kTaskEdges * kTaskEdges;
+    return t < kMaxTaskEdges ? t : kMaxTaskEdges;
+}
 constexpr int kBfsTaskEdges = 32;    // out-edges per search task with R = 1024 (one warp, one edge a lane)
 constexpr int kBfsTaskEdgesMin = 8;  // out-edges per search task with R <= 256 (four tasks a warp)
 // Out-edges per search task for rows of W words: a group of that many lanes holds the task's delta row.
@@ -24,7 +36,7 @@ constexpr int kCasLimit = 1024;      // compare-and-swap tries of one register-w
 
 enum Model : int32_t { kIC = 0, kWC = 1, kPerEdge = 2 };
 
-// Work of one sweep unit (a light row, or a task of kTaskEdges edges of a split row): its sparse pairs
+// Work of one sweep unit (a light row, or a task of task_edges(deg) edges of a split row): its sparse pairs
 // [p0, p0 + np) and its dense edges dlist[d0, d0 + nd); hu is vertex_hash(u), the first sweep's seed of u's initial
 // ranks (0 in push-unit descriptors).
 struct UnitD {
@@ -61,10 +73,11 @@ struct DevCtr {
     uint32_t npush_l;    // chg_list / chg_hc entries the current push sweep works on
     uint32_t npush_h;
     uint32_t stream;     // the current push sweep streams every in-pair (its L is large)
-    uint32_t pad_s;
+    uint32_t task_next;  // first sweep: tasks handed out so far (the tiles that finished their rows take the next)
     uint32_t fault;      // bit 0: a bulk copy did not complete in time; bit 1: a register update kept failing;
                          // bit 2: a grid barrier of a persistent kernel was not reached in time;
-                         // bit 3: a pulling sweep reached the push-only kernel
+                         // bit 3: a pulling sweep reached the push-only kernel;
+                         // bit 4: a row's kept register sum disagreed with its registers (check_sums only)
     unsigned long long chg_indeg;     // in-edges into the vertices changed in the current sweep
     unsigned long long visits;        // edge-simulation visits, running total
     unsigned long long bytes;         // algorithmic bytes of the propagation kernels, running total
@@ -178,6 +191,7 @@ struct DevProb {
     uint32_t *step_gsum;
     unsigned long long *step_reached;
     uint32_t cas_limit;        // compare-and-swap tries of one register-word update before the fault flag is raised
+    uint32_t check_sums;       // the full scan checks that gst holds every row's register sum while M_S' is empty
     int32_t literal;           // blocked registers as Algorithms 1 and 2 print them: they keep their initial rank and
                                // are never updated (otherwise they are 0 in a rebuilt sketch)
 };

@@ -74,6 +74,9 @@ struct im_ctx {
     // IM_TEST_BARRIER_LIMIT) to make a wait run out without any fault
     // lazy (CELF) argmax for greedy steps that keep the sketch (IM_CELF=0: a full scan every step; same results)
     bool celf = true;
+    // the first step after a build scans every row and checks the register sums the sweeps kept
+    // (IM_TEST_CHECK_SUMS=1); otherwise that step's argmax starts from those sums
+    bool check_sums = false;
     // launch shapes chosen by im_autotune per (R, degree class): (first-sweep register budget, streamed pushes)
     std::map<std::pair<int, int>, std::pair<int, bool>> tuned;
     // push sweeps over a large L stream every in-pair (IM_STREAM=0: always vertex by vertex; same results)
@@ -284,6 +287,8 @@ std::shared_ptr<GraphDev> prepare_graph(im_ctx *ctx, const im_graph *g) {
     ck(cudaMemcpyAsync(h_flags, flags, sizeof(h_flags), cudaMemcpyDeviceToHost, s), "read flags");
     ck(cudaStreamSynchronize(s), "sync");
     if (h_flags[3]) fail(IM_EINVAL, "p_edge holds a value outside [0, 1]");
+    if (n + h_tasks >= static_cast<int64_t>(0xFFFFFFFFll))  // the first sweep numbers rows and tasks in 32 bits
+        fail(IM_EINVAL, "graph too large: vertices plus split-row tasks must stay below 2^32 - 1");
     G->n_tasks = h_tasks;
     G->task_row = mem.alloc<int32_t>(std::max<int64_t>(h_tasks, 1));
     G->light_list = mem.alloc<int32_t>(n);
@@ -316,6 +321,7 @@ struct Prob {
     // engine state
     enum Phase { kInit, kSweep, kScan, kBfs, kDone } phase = kInit;
     bool merge_pending = false;
+    bool sums = false;  // gst holds every row's register sum, kept by the sweeps of the last build
     int step = 0;
     double varsigma = 0.0;
     std::vector<int32_t> seeds;
@@ -543,6 +549,7 @@ std::unique_ptr<Prob> make_prob(im_ctx *ctx, std::shared_ptr<GraphDev> G, const 
     d.T_edge = g.T_edge;
     d.ok_edge = g.ok_edge;
     d.cas_limit = ctx->cas_limit;
+    d.check_sums = ctx->check_sums ? 1u : 0u;
     d.undirected = g.undirected;
     d.literal = prm.blocking == IM_BLOCK_LITERAL ? 1 : 0;
     uint32_t *X = mem.alloc<uint32_t>(R);
@@ -816,8 +823,10 @@ struct Engine {
         });
     }
 
-    // The argmax of a greedy step: a full scan for the first step after a (re)build, the lazy scan (k_celf_*) for
-    // a step whose sketch was kept (the gains of its previous scans still bound the current ones).
+    // The argmax of a greedy step: the lazy scan (k_celf_*) for a step whose sketch was kept (the gains of its
+    // previous scans still bound the current ones) and for the first step after a build, whose gains (M_S' is
+    // empty) are the row sums the sweeps kept in gst; a full scan otherwise (an imported sketch, IM_CELF=0, or
+    // IM_TEST_CHECK_SUMS, whose scan also checks those sums).
     void enqueue_scan(const std::vector<int32_t> &ids) {
         if (ids.empty()) return;
         cudaStream_t s = ctx->stream;
@@ -826,7 +835,7 @@ struct Engine {
             std::vector<int32_t> fsub, lsub;
             for (int32_t i : ids) {
                 if (probs[i]->prm.R != R) continue;
-                (ctx->celf && probs[i]->merge_pending ? lsub : fsub).push_back(i);
+                (ctx->celf && (probs[i]->merge_pending || probs[i]->sums) ? lsub : fsub).push_back(i);
             }
             if (!fsub.empty()) full.emplace_back(R, add_list(fsub));
             if (!lsub.empty()) lazy.emplace_back(R, add_list(lsub));
@@ -957,6 +966,7 @@ struct Engine {
         for (int32_t i : init) {
             probs[i]->phase = Prob::kSweep;
             probs[i]->builds += 1;
+            probs[i]->sums = probs[i]->dp.gst != nullptr && !ctx->check_sums;
         }
         for (int32_t i : merge) probs[i]->merge_pending = false;
         for (int32_t i : scan) probs[i]->phase = Prob::kBfs;
@@ -968,6 +978,7 @@ struct Engine {
                 problem_error(P, IM_ECUDA, (P.last.fault & 1u)   ? "a bulk copy into shared memory did not complete"
                                            : (P.last.fault & 2u) ? "a register update did not settle"
                                            : (P.last.fault & 4u) ? "a grid barrier was not reached in time"
+                                           : (P.last.fault & 16u) ? "a kept register row sum disagreed with the row"
                                                                  : "a pulling sweep was launched as a push sweep");
             } else if (P.phase == Prob::kSweep && P.last.done) {
                 if (P.last.timeout)
@@ -1157,6 +1168,7 @@ im_status im_ctx_create(int device, void *cuda_stream, im_ctx **out) {
     if (const char *v = std::getenv("IM_PERSISTENT")) ctx->persistent = std::atoi(v) != 0;
     if (const char *v = std::getenv("IM_PULL_SWEEPS")) ctx->pull_sweeps = std::max(1, std::min(8, std::atoi(v)));
     if (const char *v = std::getenv("IM_CELF")) ctx->celf = std::atoi(v) != 0;
+    if (const char *v = std::getenv("IM_TEST_CHECK_SUMS")) ctx->check_sums = std::atoi(v) != 0;
     if (const char *v = std::getenv("IM_STREAM")) ctx->stream_push = std::atoi(v) != 0;
     if (const char *v = std::getenv("IM_TEST_CAS_LIMIT")) ctx->cas_limit = static_cast<uint32_t>(std::atol(v));
     if (const char *v = std::getenv("IM_TEST_BARRIER_LIMIT"))

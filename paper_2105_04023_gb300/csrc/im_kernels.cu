@@ -170,6 +170,11 @@ __device__ __forceinline__ uint32_t ne_bits16(const uint4 &a, const uint4 &b) {
     return ne_bits4(a.x, b.x) | (ne_bits4(a.y, b.y) << 4) | (ne_bits4(a.z, b.z) << 8) | (ne_bits4(a.w, b.w) << 12);
 }
 
+// Sum of the 16 registers (bytes) of a chunk.
+__device__ __forceinline__ uint32_t byte_sum16(const uint4 &a) {
+    return __dp4a(a.x, 0x01010101u, __dp4a(a.y, 0x01010101u, __dp4a(a.z, 0x01010101u, __dp4a(a.w, 0x01010101u, 0u))));
+}
+
 // Byte masks of four simulations from four live bits (the low nibble of n): bit k is moved to bit 8k + 7 by one
 // multiply (the shifted copies never overlap, so nothing carries) and prmt replicates each byte's top bit.
 __device__ __forceinline__ uint32_t nibble_bytes(uint32_t n) { return sign_bytes(n * 0x10204080u, 0u, 0xBA98u); }
@@ -450,6 +455,13 @@ __device__ __forceinline__ void finalize_tile(const DevProb &P, int64_t u, uint3
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
     }
+    if (P.gst && (changed || Mother)) {  // the row's register sum (its gain while M_S' is empty)
+        uint32_t sum = 0;
+#pragma unroll
+        for (int c = 0; c < Gm::CPL; ++c) sum += byte_sum16(nw[c]);
+        sum = __reduce_add_sync(tm, sum);
+        if (li == 0) P.gst[u] = sum;
+    }
     if (Mother) {  // the first sweep also records which registers it raised, for the push of the next sweep
         uint4 *dst = reinterpret_cast<uint4 *>(Mother + static_cast<size_t>(u) * R);
 #pragma unroll
@@ -486,6 +498,15 @@ __device__ __forceinline__ void finalize_row_r(const DevProb &P, int64_t u, uint
         uint4 *dst = reinterpret_cast<uint4 *>(Mnext + static_cast<size_t>(u) * R);
 #pragma unroll
         for (int c = 0; c < Gm::CPL; ++c) dst[li + Gm::G * c] = nw[c];
+    }
+    if (P.gst && (changed || Mother)) {  // the row's register sum (its gain while M_S' is empty)
+        uint32_t sum = 0;
+        if (g == 0) {
+#pragma unroll
+            for (int c = 0; c < Gm::CPL; ++c) sum += byte_sum16(nw[c]);
+        }
+        sum = __reduce_add_sync(kFull, sum);
+        if (lane == 0) P.gst[u] = sum;
     }
     if (g == 0 && Mother) {
         uint4 *dst = reinterpret_cast<uint4 *>(Mother + static_cast<size_t>(u) * R);
@@ -654,9 +675,9 @@ __device__ void prop_problem_t(const DevProb &P, uint32_t t, const SweepWork &W,
 template <int R>
 __device__ __forceinline__ void finalize_first(const DevProb &P, int64_t u, const uint32_t (&acc)[Geo<R>::CPL][4],
                                                const uint4 (&own)[Geo<R>::CPL], uint32_t *__restrict__ Lnext,
-                                               unsigned tm, int li) {
+                                               uint32_t *__restrict__ gst, unsigned tm, int li) {
     using Gm = Geo<R>;
-    uint32_t any = 0;
+    uint32_t any = 0, sum = 0;
 #pragma unroll
     for (int c = 0; c < Gm::CPL; ++c) {
         const int ch = li + Gm::G * c;
@@ -674,37 +695,76 @@ __device__ __forceinline__ void finalize_first(const DevProb &P, int64_t u, cons
         reinterpret_cast<uint4 *>(P.M0 + static_cast<size_t>(u) * R)[ch] = v;
         P.dmask[static_cast<size_t>(u) * Gm::CH + ch] = static_cast<uint16_t>(bits);
         any |= bits;
+        sum += byte_sum16(v);
     }
     if (__any_sync(tm, any != 0u) && li == 0) set_bit(Lnext, u);
+    if (gst) {  // the row's register sum (its gain while M_S' is empty)
+        sum = __reduce_add_sync(tm, sum);
+        if (li == 0) gst[u] = sum;
+    }
 }
 
-// The first sweep of one problem over this tile's units (every row, then every task), software-pipelined: while a
-// unit is processed, the pair records and ranks of the next unit's first 4 G pairs and the descriptor of the unit
-// after it are already in flight, so the chain descriptor -> pairs -> merge of one unit overlaps the previous one.
-// The descriptors wait in a per-tile ring of three in shared memory (ring: 3 x 8 words, 16-byte aligned), loaded a
-// word a lane, and each prefetched pair is its 16-bit word (slot, rank), to keep the registers few.  A row's own
-// initial registers come from the problem's table Mi (loaded before the merges, used after them).
+// The first sweep of one problem over this tile's units, software-pipelined: while a unit is processed, the pair
+// records and ranks of the next unit's first 4 G pairs and the descriptor of the unit after it are already in
+// flight, so the chain descriptor -> pairs -> merge of one unit overlaps the previous one.  The tile takes the rows
+// first, dealt round-robin from row `first` on (rows have at most kHeavyDeg out-edges, so the deal is even), then
+// tasks from the problem's shared counter until none is left: tasks differ in length (a hub's tasks are up to
+// kMaxTaskEdges edges), and whichever tile is free takes the next one.  The counter is read one unit ahead of the
+// descriptor load it feeds.  The descriptors wait in a per-tile ring of three in shared memory (ring: 3 x 8 words,
+// 16-byte aligned), loaded a word a lane, and each prefetched pair is its 16-bit word (slot, rank), to keep the
+// registers few.  A row's own initial registers come from the problem's table Mi (loaded before the merges, used
+// after them).
 template <int R>
-__device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, uint64_t nworkers, unsigned tm,
-                                int li, uint32_t *acc32, uint32_t *ring) {
+__device__ void first_problem_t(const DevProb &P, uint64_t first, uint64_t nworkers, unsigned tm, int li,
+                                uint32_t *acc32, uint32_t *ring) {
     using Gm = Geo<R>;
     constexpr int G = Gm::G;
     constexpr int DW = sizeof(UnitD) / 4;  // descriptor words
     constexpr int NW = (DW + G - 1) / G;   // descriptor words a lane moves
     static_assert(DW == 8, "descriptor of 8 words");
     const uint64_t n = static_cast<uint64_t>(P.n);
+    const uint64_t nt = static_cast<uint64_t>(P.n_tasks);
+    // unit ids: x < n row x, n <= x < n + nt task x - n, kEnd none left (n + nt < 2^32 - 1, checked at graph set-up)
+    constexpr uint32_t kEnd = 0xFFFFFFFFu;
+    const int lead = static_cast<int>(threadIdx.x & 31) - li;  // the tile's first lane
+    // the tile's unit sequence: the next row of its deal, then the counter's next task (its atomic issued by
+    // issue(), its value read by resolve() one unit later)
+    uint32_t sx = static_cast<uint32_t>(first);
+    bool ended = false, dyn = false;
+    uint32_t pend = 0;  // the issued unit: a row id, or (dyn) the counter's value in the tile's first lane
+    auto issue = [&]() {
+        dyn = false;
+        pend = kEnd;
+        if (sx < n) {
+            pend = sx;
+            sx += static_cast<uint32_t>(nworkers);
+        } else if (!ended) {
+            dyn = true;
+            if (li == 0) pend = atomicAdd(&P.ctr->task_next, 1u);
+        }
+    };
+    auto resolve = [&]() -> uint32_t {
+        if (!dyn) return pend;
+        const uint32_t k = __shfl_sync(tm, pend, lead);
+        if (k >= nt) {
+            ended = true;
+            return kEnd;
+        }
+        return static_cast<uint32_t>(n) + k;
+    };
     const uint64_t tb = thr_bytes(P.model);
     const uint16_t *pq = P.pqb ? P.pqb : P.pq;
+    uint32_t *const gst = P.gst;
     const bool rebuild = P.rany && P.ctr->lvl != 0;  // some vertices are blocked
     // a rebuild without the problem's own blocked ranks tests each pair's neighbour (residual blocking only)
     const bool test = rebuild && !P.pqb && !P.literal;
     const bool keep_own = rebuild && P.literal;  // literal blocking: a blocked register is never raised
     const uint32_t tx = sw_tile(static_cast<uint32_t>((threadIdx.x & 31) / G));  // this tile's slot permutation
     unsigned long long pairs = 0, bytes = 0;  // counted by lane 0 of the tile
-    // this lane's words (li, li + G, ...) of descriptor l (zeros past the end)
-    auto load_desc = [&](uint64_t l, uint32_t (&w)[NW]) {
-        const uint32_t *src = l < cnt ? reinterpret_cast<const uint32_t *>(l < n ? P.rdesc + l : P.tdesc + (l - n))
-                                      : nullptr;
+    // this lane's words (li, li + G, ...) of the descriptor of unit x (zeros for kEnd)
+    auto load_desc = [&](uint32_t x, uint32_t (&w)[NW]) {
+        const uint32_t *src = x != kEnd ? reinterpret_cast<const uint32_t *>(x < n ? P.rdesc + x : P.tdesc + (x - n))
+                                        : nullptr;
 #pragma unroll
         for (int k = 0; k < NW; ++k) {
             const int wi = li + G * k;
@@ -744,25 +804,33 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
             b[k] = o < d.np ? static_cast<uint32_t>(__ldg(&pq[d.p0 + o])) : 0u;
         }
     };
+    issue();
+    uint32_t x0 = resolve();  // the current unit (row `first`)
+    issue();
+    uint32_t x1 = resolve();  // the next one
+    issue();
+    uint32_t x2 = resolve();  // the one after it
+    issue();                  // and the one after that, resolved at the end of the first round
     {
         uint32_t w[NW];
-        load_desc(first, w);
+        load_desc(x0, w);
         store_desc(0, w);
-        load_desc(first + nworkers, w);
+        load_desc(x1, w);
         store_desc(1, w);
     }
     __syncwarp(tm);
     int slot = 0;  // ring slot of the current unit; slot + 1 holds the next one
     uint32_t cb[4];
     batch(read_desc(0), cb);
-    for (uint64_t l = first; l < cnt; l += nworkers) {
+    while (x0 != kEnd) {
         const int s1 = slot == 2 ? 0 : slot + 1, s2 = s1 == 2 ? 0 : s1 + 1;
         const D cur = read_desc(slot);
         uint32_t nb[4];
         batch(read_desc(s1), nb);                 // the next unit's first pairs
         uint32_t wn[NW];
-        load_desc(l + 2 * nworkers, wn);          // and the descriptor after it
-        const bool is_row = l < n;
+        load_desc(x2, wn);                        // and the descriptor after it
+        const uint32_t x = x0;
+        const bool is_row = x < n;
         if (!(is_row && cur.u < 0)) {  // a split row is left to its tasks and the combine kernels
             // the row's initial registers (blocked ones 0 under residual blocking), loaded before the merges
             uint4 own[Gm::CPL];
@@ -799,9 +867,9 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
             if (is_row) {
                 const int64_t u = cur.u;
                 if (keep_own) drop_blocked<R>(P, u, acc, li);
-                finalize_first<R>(P, u, acc, own, P.Lb1, tm, li);
+                finalize_first<R>(P, u, acc, own, P.Lb1, gst, tm, li);
             } else if (cur.np + cur.nd > 0) {
-                const int64_t task = static_cast<int64_t>(l - n);
+                const int64_t task = static_cast<int64_t>(x - n);
                 uint4 *dst = reinterpret_cast<uint4 *>(P.part + static_cast<size_t>(task) * R);
 #pragma unroll
                 for (int c = 0; c < Gm::CPL; ++c)
@@ -814,6 +882,10 @@ __device__ void first_problem_t(const DevProb &P, uint64_t cnt, uint64_t first, 
         slot = s1;
 #pragma unroll
         for (int k = 0; k < 4; ++k) cb[k] = nb[k];
+        x0 = x1;
+        x1 = x2;
+        x2 = resolve();
+        issue();
     }
     if (li == 0 && bytes) {
         atomicAdd(&P.ctr->first_bytes, bytes);
@@ -1069,11 +1141,16 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
 // A push sweep over a large L as one stream of in-pairs (sampled graphs without dense edges): every in-pair
 // (u, v, j) in in-CSR order, 128 a warp at a time, merges M_v[j] into the next buffer's M_u[j] when v is in L and
 // the previous sweep changed (v, j) (the same skip as push_problem_w; dmask of every listed v, or of every row after
-// the first sweep, is current); the pair records and the change masks of consecutive pairs are coalesced, and only
-// pairs of changed registers read their source u and touch a register row.
+// the first sweep, is current).  The pair records and the change masks of consecutive pairs are coalesced, and
+// consecutive pairs share v, so M_v[j] is read from a row the warp just touched.  Few pairs pass (a few percent in
+// sweep 1), so each passing pair (u, j, M_v[j]) goes to a per-warp queue in shared memory, and the warp updates the
+// target words 32 at a time, one a lane: the random read and compare-and-swap of each target word then run with
+// the whole warp's in flight instead of one or two lanes' per item.
+constexpr int kPushQueue = 64;  // queue entries a warp (at most 31 left over plus 32 of one record slot)
+
 template <int R>
 __device__ void push_stream_w(const DevProb &P, uint32_t t, uint64_t cnt, uint64_t first, uint64_t nworkers,
-                              int lane) {
+                              int lane, uint2 *queue) {
     constexpr int CH = R / 16;
     const bool par = t & 1u;
     const uint8_t *Mcur = par ? P.M1 : P.M0;
@@ -1083,9 +1160,27 @@ __device__ void push_stream_w(const DevProb &P, uint32_t t, uint64_t cnt, uint64
     unsigned int *fault = &P.ctr->fault;
     const uint32_t lim = P.cas_limit;
     const uint64_t npairs = static_cast<uint64_t>(P.ipofs[P.m]);
+    const uint32_t lt = (1u << lane) - 1u;
     uint32_t nproc = 0, nrec = 0;
-    // the records of the next item are loaded while this one is processed (the loop is a chain of dependent loads:
-    // record -> change mask -> source, register and target word -> compare-and-swap)
+    uint32_t head = 0, count = 0;  // the queue's first entry and length (the same in every lane)
+    // the 32 queued entries from head on, one a lane (or the first n of them): target word max-merge
+    auto drain = [&](uint32_t n) {
+        __syncwarp();
+        if (static_cast<uint32_t>(lane) < n) {
+            const uint2 e = queue[(head + lane) % kPushQueue];
+            const int32_t u = static_cast<int32_t>(e.x);
+            const uint32_t j = e.y & 0xFFFFu, x = e.y >> 16;
+            if (!literal_blocked(P, u, j)) {
+                ++nproc;
+                uint32_t *addr = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(u) * R + (j & ~3u));
+                if (word_max(addr, __ldcg(addr), x << (8 * (j & 3)), fault, lim)) set_bit(Lnext, u);
+            }
+        }
+        head = (head + n) % kPushQueue;
+        count -= n;
+        __syncwarp();
+    };
+    // the records of the next item are loaded while this one is processed
     int32_t nv[4];
     uint32_t nj[4];
     auto fetch = [&](uint64_t l) {
@@ -1119,31 +1214,22 @@ __device__ void push_stream_w(const DevProb &P, uint32_t t, uint64_t cnt, uint64
                 go[k] = inL && ((__ldg(&P.dmask[static_cast<size_t>(v) * CH + (j >> 4)]) >> (j & 15)) & 1u);
             }
         }
-        int32_t cu[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) cu[k] = go[k] ? __ldg(&P.iu[l * 128 + 32 * k + lane]) : 0;
-        uint32_t *addr[4];
-        uint32_t old[4], x[4];
+        // a passing pair's source u and candidate register M_v[j] (a changed register is never 0)
+        uint32_t cu[4], cx[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            addr[k] = nullptr;
-            if (go[k] && !literal_blocked(P, cu[k], cj[k])) {
-                addr[k] = reinterpret_cast<uint32_t *>(Mnext + static_cast<size_t>(cu[k]) * R + (cj[k] & ~3u));
-                ++nproc;
-            }
+            cu[k] = go[k] ? static_cast<uint32_t>(__ldg(&P.iu[l * 128 + 32 * k + lane])) : 0u;
+            cx[k] = go[k] ? static_cast<uint32_t>(__ldg(Mcur + static_cast<size_t>(cv[k]) * R + cj[k])) : 0u;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            x[k] = addr[k] ? __ldg(Mcur + static_cast<size_t>(cv[k]) * R + cj[k]) : 0u;
-            old[k] = addr[k] ? __ldcg(addr[k]) : 0u;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t cand = x[k] << (8 * (cj[k] & 3));
-            if (cand && word_max(addr[k], old[k], cand, fault, lim))
-                set_bit(Lnext, (reinterpret_cast<uint8_t *>(addr[k]) - Mnext) / R);
+            const unsigned m = __ballot_sync(kFull, go[k]);
+            if (go[k]) queue[(head + count + __popc(m & lt)) % kPushQueue] = make_uint2(cu[k], cj[k] | (cx[k] << 16));
+            count += __popc(m);
+            if (count >= 32) drain(32);
         }
     }
+    if (count) drain(count);
     // modelled bytes: per pair its target and simulation (6 bytes) and change-mask word (2), and per pair of a
     // changed register its source (4), the register and the target word (5)
     nproc = __reduce_add_sync(kFull, nproc);
@@ -1184,11 +1270,11 @@ __global__ void __launch_bounds__(kBlock, MINB) k_first(const DevProb *__restric
         const DevProb &P = probs[act[q]];
         const DevCtr &C = *P.ctr;
         if (C.done || !C.full || C.t != 0) continue;  // the same for every thread of the block
-        const uint64_t cnt = static_cast<uint64_t>(P.n) + static_cast<uint64_t>(P.n_tasks);
+        // rows are dealt over the tiles; the tiles that got a row also share the problem's tasks
         const uint64_t first = first_owned(worker, nworkers, base);
-        base += cnt;
-        if (first >= cnt) continue;
-        first_problem_t<R>(P, cnt, first, nworkers, tm, li, acc32, sring[wib * Geo<R>::NG + g]);
+        base += static_cast<uint64_t>(P.n);
+        if (first >= static_cast<uint64_t>(P.n)) continue;
+        first_problem_t<R>(P, first, nworkers, tm, li, acc32, sring[wib * Geo<R>::NG + g]);
     }
 }
 
@@ -1236,6 +1322,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(const DevProb *__restrict
                                                        const int32_t *__restrict__ act, int nact, int skip_full) {
     // per warp: M_v, then its change mask (padded to whole 16-byte words so every warp's row stays aligned)
     __shared__ __align__(16) uint32_t srow[kWarpsPerBlock][R / 4 + ((R / 32 + 3) & ~3)];
+    __shared__ uint2 squeue[kWarpsPerBlock][kPushQueue];  // the streamed push's queue of passing pairs
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t wworker = static_cast<uint64_t>(blockIdx.x) * kWarpsPerBlock + wib;
     const uint64_t nwworkers = static_cast<uint64_t>(gridDim.x) * kWarpsPerBlock;
@@ -1253,7 +1340,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_push(const DevProb *__restrict
             const uint64_t first = first_owned(wworker, nwworkers, base);
             base += cnt;
             if (first >= cnt) continue;
-            push_stream_w<R>(P, C.t, cnt, first, nwworkers, lane);
+            push_stream_w<R>(P, C.t, cnt, first, nwworkers, lane, squeue[wib]);
             continue;
         }
         const uint64_t cnt = static_cast<uint64_t>(C.npush_l) + C.npush_h;
@@ -1484,6 +1571,8 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
         const bool push_next = next_is_push(P, C);
         // the first sweep of a diffusion wrote every row to both buffers: nothing to copy after it
         const bool copy = C.t != 0;
+        // after a push sweep the copies also raise the rows' register sums (a pulling sweep stored them itself)
+        const bool rsum = P.gst && !C.full;
         const bool par = C.t & 1u;
         uint32_t *Lold = par ? P.Lb1 : P.Lb0;
         const uint32_t *Lnew = par ? P.Lb0 : P.Lb1;
@@ -1519,11 +1608,14 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
                         uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R);
                         if (copy) {
                             const int CH = P.R / 16;
+                            uint32_t rise = 0;  // how much sweep t raised the row's register sum
                             for (int c = 0; c < CH; ++c) {
-                                const uint4 a = src[c];
-                                P.dmask[static_cast<size_t>(v) * CH + c] = static_cast<uint16_t>(ne_bits16(a, dst[c]));
+                                const uint4 a = src[c], b = dst[c];
+                                P.dmask[static_cast<size_t>(v) * CH + c] = static_cast<uint16_t>(ne_bits16(a, b));
+                                rise += byte_sum16(a) - byte_sum16(b);
                                 dst[c] = a;
                             }
+                            if (rsum && rise) atomicAdd(&P.gst[v], rise);
                         }
                         const uint32_t nt = static_cast<uint32_t>((d + kPushChunk - 1) / kPushChunk);
                         const uint32_t at = atomicAdd(&P.ctr->nchg_hc, nt);
@@ -1573,14 +1665,29 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
             if (!copy) continue;
             // consecutive threads on consecutive 16-byte chunks of the listed rows; the chunks' changed registers
             // (Mw against the previous sweep's Mr) go to dmask for the push sweep
+            // and each row's register sum rises by what sweep t added (one atomic per row and warp: a row's CH
+            // chunks are CH consecutive lanes, CH-aligned, when CH divides 32, or whole warps when 32 divides CH)
             const uint32_t CH = static_cast<uint32_t>(P.R / 16);
+            const uint32_t seg = CH < 32 ? CH : 32;
+            const uint32_t xend = (sn * CH + 31) & ~31u;  // whole warps, so that the sums' shuffles converge
 #pragma unroll 4
-            for (uint32_t x = threadIdx.x; x < sn * CH; x += blockDim.x) {
-                const int64_t v = s_v[x / CH];
-                uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R) + x % CH;
-                const uint4 a = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R)[x % CH];
-                P.dmask[static_cast<size_t>(v) * CH + x % CH] = static_cast<uint16_t>(ne_bits16(a, *dst));
-                *dst = a;
+            for (uint32_t x = threadIdx.x; x < xend; x += blockDim.x) {
+                const bool in = x < sn * CH;
+                const int64_t v = in ? s_v[x / CH] : 0;
+                uint32_t rise = 0;
+                if (in) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R) + x % CH;
+                    const uint4 a = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R)[x % CH];
+                    const uint4 b = *dst;
+                    P.dmask[static_cast<size_t>(v) * CH + x % CH] = static_cast<uint16_t>(ne_bits16(a, b));
+                    rise = byte_sum16(a) - byte_sum16(b);
+                    *dst = a;
+                }
+                if (rsum) {
+                    const unsigned segmask = (seg == 32 ? kFull : (1u << seg) - 1u) << (lane & ~(seg - 1));
+                    rise = __reduce_add_sync(segmask, rise);
+                    if (in && (lane & (seg - 1)) == 0 && rise) atomicAdd(&P.gst[v], rise);
+                }
             }
         }
 #pragma unroll
@@ -1700,6 +1807,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const DevProb *__restrict__ pro
                 C.npush_l = 0;
                 C.npush_h = 0;
                 C.stream = 0;
+                C.task_next = 0;
                 C.chg_indeg = 0;
                 C.gms = 0;  // M_S' is cleared below
                 C.cand_key = 0;
@@ -1763,7 +1871,11 @@ __device__ void scan_problem(const DevProb &P, uint64_t cnt, uint64_t first, uin
             for (int off = 1; off < Gm::G; off <<= 1) s += __shfl_xor_sync(kFull, s, off);
             if (ok[u]) {
                 const uint32_t gain = s - gms;  // s >= sum_j M_S'[j]
-                if (li == 0 && P.gst) P.gst[v[u]] = gain;
+                if (li == 0 && P.gst) {
+                    // with M_S' empty every gain is the row's register sum, which the sweeps kept in gst
+                    if (P.check_sums && gms == 0 && P.gst[v[u]] != gain) atomicOr(&P.ctr->fault, 16u);
+                    P.gst[v[u]] = gain;
+                }
                 const unsigned long long key =
                     (static_cast<unsigned long long>(gain) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(v[u]));
                 best = key > best ? key : best;
@@ -1979,18 +2091,21 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
         return;
     }
     const uint32_t L = C.lvl;
+    __syncthreads();  // every thread has read the counters before warp 0 updates them
     uint32_t *d0 = P.del[L % 3u];
     uint32_t added = 0;
-    for (int k = lane; k < P.W; k += 32) {
-        const size_t at = static_cast<size_t>(s) * P.W + k;
-        const uint32_t nb = ~P.vis[at];
-        P.vis[at] = 0xFFFFFFFFu;
-        d0[at] = nb;
-        added += __popc(nb);
-    }
+    if (lane < 32) {
+        for (int k = lane; k < P.W; k += 32) {
+            const size_t at = static_cast<size_t>(s) * P.W + k;
+            const uint32_t nb = ~P.vis[at];
+            P.vis[at] = 0xFFFFFFFFu;
+            d0[at] = nb;
+            added += __popc(nb);
+        }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
-    __syncwarp();
+        for (int off = 16; off > 0; off >>= 1) added += __shfl_xor_sync(kFull, added, off);
+        __syncwarp();
+    }
     if (lane == 0) {
         C.s = s;
         C.gsum = gsum;
@@ -2009,12 +2124,12 @@ __global__ void k_choose(const DevProb *__restrict__ probs, const int32_t *__res
             P.step_gsum[step] = gsum;
         }
     }
-    // the seed's search tasks for the first level, written by the whole warp (a hub seed has many); the task
-    // lists of this level were empty, so they start at 0
+    // the seed's search tasks for the first level, written by the whole block (a hub seed has 10^5 of them); the
+    // task lists of this level were empty, so they start at 0
     const int te = bfs_task_edges(P.W);
     const int64_t e = P.xadj[s], deg = P.xadj[s + 1] - e;
     const uint32_t nt = bfs_ntasks(deg, te);
-    for (uint32_t c = lane; c < nt; c += 32) P.T[L & 1u][c] = bfs_task(s, e, deg, c, te);
+    for (uint32_t c = lane; c < nt; c += blockDim.x) P.T[L & 1u][c] = bfs_task(s, e, deg, c, te);
     if (lane == 0) C.nT[L & 1u] = nt;
 }
 
@@ -2717,7 +2832,7 @@ __global__ void __launch_bounds__(kBlock) k_vertex_desc(const DevProb P, UnitD *
     }
 }
 
-// Sweep-unit descriptors of every row (its whole edge range) and every task (its kTaskEdges-edge slice).
+// Sweep-unit descriptors of every row (its whole edge range) and every task (its task_edges(deg)-edge slice).
 __global__ void __launch_bounds__(kBlock) k_unit_desc(const DevProb P, UnitD *rdesc, UnitD *tdesc) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n + P.n_tasks; i += stride) {
@@ -2729,8 +2844,9 @@ __global__ void __launch_bounds__(kBlock) k_unit_desc(const DevProb P, UnitD *rd
         } else {
             const int64_t task = i - P.n;
             u = P.task_row[task];
-            e0 = P.xadj[u] + (task - P.task_off[u]) * kTaskEdges;
-            e1 = min(e0 + kTaskEdges, P.xadj[u + 1]);
+            const int64_t te = task_edges(P.xadj[u + 1] - P.xadj[u]);
+            e0 = P.xadj[u] + (task - P.task_off[u]) * te;
+            e1 = min(e0 + te, P.xadj[u + 1]);
         }
         UnitD d;
         d.p0 = P.pofs[e0];
@@ -3029,7 +3145,8 @@ __global__ void k_row_tasks(const int64_t *__restrict__ xadj, int64_t n, int32_t
          u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t d = xadj[u + 1] - xadj[u];
         const bool h = d > kHeavyDeg;
-        ntask[u] = h ? static_cast<int32_t>((d + kTaskEdges - 1) / kTaskEdges) : 0;
+        const int64_t te = task_edges(d);
+        ntask[u] = h ? static_cast<int32_t>((d + te - 1) / te) : 0;
         if (h) set_bit(heavy, u);
     }
 }
@@ -3369,7 +3486,7 @@ int launch_celf(int R, const DevProb *probs, const int32_t *act, int nact, cudaS
     return 3;
 }
 void launch_choose(const DevProb *probs, const int32_t *act, int nact, int32_t step, cudaStream_t s) {
-    k_choose<<<nact, 32, 0, s>>>(probs, act, nact, step);
+    k_choose<<<nact, kBlock, 0, s>>>(probs, act, nact, step);
 }
 void launch_seed_set(const DevProb *prob, const int32_t *seeds, int k, int W, cudaStream_t s) {
     k_seed_set<<<(k * W + 255) / 256, 256, 0, s>>>(prob, seeds, k);

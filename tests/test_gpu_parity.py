@@ -181,6 +181,37 @@ def test_pulled_later_sweeps_equal_the_oracle(monkeypatch, pulls, gname, model, 
     assert sel["gsum"].tolist() == ref["gsum"].tolist()
 
 
+@pytest.mark.parametrize("env,gname,model,p,R,literal",
+                         [({}, "rmat10", WC, 0.0, 64, False), ({}, "hub1500", IC, 0.3, 1024, False),
+                          ({"IM_PULL_SWEEPS": "2"}, "er300", IC, 0.05, 256, False),
+                          ({"IM_STREAM": "0"}, "ragged97", IC, 0.2, 512, False),
+                          ({}, "er300", IC, 0.05, 128, True)])
+def test_kept_row_sums_equal_the_registers(monkeypatch, env, gname, model, p, R, literal):
+    """The sweeps keep every row's register sum (the first sweep and pulling sweeps store it, the copies after a push
+    sweep add what the sweep raised), and the first greedy step after each build starts its argmax from those sums.
+    Under IM_TEST_CHECK_SUMS that step scans every row instead and raises a fault if a kept sum differs from the
+    row's registers: none may, and the selection equals the oracle's, rebuilds included."""
+    g = SMALL[gname]
+    K = min(10, g.n)
+    graph = im.Graph.from_synth(g, model, p)
+    blocking = im.IM_BLOCK_LITERAL if literal else im.IM_BLOCK_RESIDUAL
+    prm = im.params(R=R, K=K, eps_g=0.0, eps_l=0.0, seed=17, blocking=blocking)
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    monkeypatch.setenv("IM_TEST_CHECK_SUMS", "1")
+    c = im.Context(0)
+    for k in list(env) + ["IM_TEST_CHECK_SUMS"]:
+        monkeypatch.delenv(k)
+    try:
+        checked = c.im_select_seeds(graph, prm)
+    finally:
+        c.close()
+    ref = oracle.select_seeds(g.n, g.xadj, g.adj, model, p, R, K, 0.0, 0.0, 0.0, 17, literal=literal)
+    assert checked["seeds"].tolist() == ref["seeds"].tolist()
+    assert checked["gsum"].tolist() == ref["gsum"].tolist()
+    assert int(np.sum(checked["rebuilt"])) >= 2
+
+
 @pytest.mark.parametrize("model,p,R", [(IC, 0.02, 256), (WC, 0.0, 128)])
 def test_autotuned_shapes_give_the_same_selection(model, p, R):
     """The autotuner times every candidate launch shape on the first diffusion (it checks they agree) and keeps the

@@ -364,23 +364,23 @@ __device__ __forceinline__ uint32_t sparse_tile(const DevProb &P, int64_t p0, in
 // pairs k_block_pairs set to rank 0), so one load serves a pair; a rank of 0 changes nothing.  Without pqb, a
 // rebuild (chk) reads the pair's v too and a blocked (v, j) gives 0 (residual blocking; literal blocking keeps the
 // rank).
-template <int R>
+template <int R, int NB = 4>
 __device__ __forceinline__ void sparse_tile_init(const DevProb &P, int64_t p0, int64_t p1, bool chk,
                                                  uint32_t *acc32, int li) {
     constexpr int G = Geo<R>::G;
     const uint32_t tx = sw_tile(static_cast<uint32_t>((threadIdx.x & 31) / G));
     const uint16_t *pq = P.pqb ? P.pqb : P.pq;
     const bool test = chk && !P.literal && !P.pqb;
-    for (int64_t p = p0 + li; p < p1; p += 4 * G) {
-        uint32_t x[4];
+    for (int64_t p = p0 + li; p < p1; p += NB * G) {  // NB pair words a lane per round
+        uint32_t x[NB];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < NB; ++k) {
             const int64_t q = p + G * k;
             x[k] = q < p1 ? __ldg(&pq[q]) : 0u;
         }
         if (test) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < NB; ++k)
                 if (x[k] >> 10) {
                     const int32_t v = __ldg(&P.pv[p + G * k]);
                     const uint32_t j = sw_slot(x[k] & 0x3FFu, 0);  // the slot map is its own inverse
@@ -389,7 +389,7 @@ __device__ __forceinline__ void sparse_tile_init(const DevProb &P, int64_t p0, i
                 }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < NB; ++k)
             if (x[k] >> 10) atomicMax(&acc32[(x[k] & 0x3FFu) ^ tx], x[k] >> 10);
     }
 }
@@ -844,13 +844,15 @@ __device__ void first_problem_t(const DevProb &P, uint64_t first, uint64_t nwork
 #pragma unroll
                 for (int w = 0; w < 4; ++w) acc[c][w] = 0;
             if (cur.np > 0) {
+                // a unit's pairs past its first 4 G take 8 words a lane per round: hub tasks of hundreds of pairs
+                // then wait for fewer rounds of loads
                 if (test) {
-                    sparse_tile_init<R>(P, cur.p0, cur.p0 + cur.np, true, acc32, li);
+                    sparse_tile_init<R, 8>(P, cur.p0, cur.p0 + cur.np, true, acc32, li);
                 } else {
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         if (cb[k] >> 10) atomicMax(&acc32[(cb[k] & 0x3FFu) ^ tx], cb[k] >> 10);
-                    if (cur.np > 4 * G) sparse_tile_init<R>(P, cur.p0 + 4 * G, cur.p0 + cur.np, false, acc32, li);
+                    if (cur.np > 4 * G) sparse_tile_init<R, 8>(P, cur.p0 + 4 * G, cur.p0 + cur.np, false, acc32, li);
                 }
                 fold_tile<R, true>(acc, acc32, tm, li);
             }
@@ -858,11 +860,11 @@ __device__ void first_problem_t(const DevProb &P, uint64_t first, uint64_t nwork
                 dense_tile<R, true>(P, cur.d0, cur.d0 + cur.nd, true, nullptr, nullptr, nullptr, rebuild, acc, li);
             // modelled bytes: descriptor, pair words (slot, rank), dense edges (id, target, threshold, mask, the
             // neighbour's initial row), and the row's initial registers read and the row written to both buffers
-            // with its change mask (or a task's partial row)
+            // with its change mask and register sum (or a task's partial row)
             if (li == 0) {
                 pairs += cur.np;
                 bytes += 32 + 2 * static_cast<uint64_t>(cur.np) + (8 + tb + R / 8 + R) * static_cast<uint64_t>(cur.nd) +
-                         (is_row ? 3 * R + R / 8 : (cur.np + cur.nd > 0 ? R : 0));
+                         (is_row ? 3 * R + R / 8 + (gst ? 4 : 0) : (cur.np + cur.nd > 0 ? R : 0));
             }
             if (is_row) {
                 const int64_t u = cur.u;
@@ -1554,6 +1556,7 @@ __device__ __forceinline__ bool last_block(GridBar *gb) {
 }
 
 constexpr int kFrontChunk = 4 * kBlock;  // vertices of L_{t+1} a frontier block takes at a time (4 a thread)
+constexpr int kFrontSuper = kBlock / 32;  // chunks a frontier block checks at once: one a warp, a word a lane
 static_assert(4 * kWarpsPerBlock == 32, "one warp scans the frontier chunk's per-warp counts");
 
 __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__ probs,
@@ -1561,6 +1564,7 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
     __shared__ uint32_t s_cnt[4 * kWarpsPerBlock];  // light vertices listed by (k, warp), then their offsets
     __shared__ uint32_t s_base, s_n;
     __shared__ int32_t s_v[kFrontChunk];            // the chunk's listed vertices, for the row copies
+    __shared__ int s_nz[kFrontSuper];               // which of the block's current chunks have a bit of L_{t+1}
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     uint64_t base = 0;
@@ -1584,111 +1588,133 @@ __global__ void __launch_bounds__(kBlock) k_frontier(const DevProb *__restrict__
         base += chunks;
         unsigned long long indeg = 0;  // in-edges into L': the next sweep's work count
         uint32_t nchg = 0;             // |L'| (this thread's bits)
-        for (uint64_t ch = first; ch < chunks; ch += gridDim.x) {
-            // vertex ch * kFrontChunk + k * kBlock + threadIdx.x: word (ch * 4 + k) * kWarpsPerBlock + wib, bit lane
-            bool light[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t wi = (static_cast<int64_t>(ch) * 4 + k) * kWarpsPerBlock + wib;
+        // the block's chunks first, first + grid, ...: kFrontSuper of them at a time, warp w loading chunk w's 32
+        // words of L_{t+1} (and clearing its words of L_t); a chunk without any bit costs nothing more, so a later
+        // sweep's small L skips most chunks after one load and one barrier
+        for (uint64_t cg = first; cg < chunks; cg += kFrontSuper * static_cast<uint64_t>(gridDim.x)) {
+            {
+                const uint64_t chw = cg + static_cast<uint64_t>(wib) * gridDim.x;  // this warp's chunk
+                const int64_t wi = static_cast<int64_t>(chw) * 32 + lane;
                 uint32_t w = 0;
-                if (wi < words) {
+                if (chw < chunks && wi < words) {
                     w = Lnew[wi];
-                    if (lane == 0) Lold[wi] = 0;
+                    Lold[wi] = 0;
                 }
-                light[k] = false;
-                nchg += (w >> lane) & 1u;
-                if ((w >> lane) & 1u) {
-                    const int64_t v = wi * 32 + lane;
-                    const uint64_t d = in_degree(P, v);
-                    indeg += d;
-                    light[k] = true;
-                    if (push_next && d > kPushChunk) {
-                        light[k] = false;
-                        const uint4 *src = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R);
-                        uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R);
-                        if (copy) {
-                            const int CH = P.R / 16;
-                            uint32_t rise = 0;  // how much sweep t raised the row's register sum
-                            for (int c = 0; c < CH; ++c) {
-                                const uint4 a = src[c], b = dst[c];
-                                P.dmask[static_cast<size_t>(v) * CH + c] = static_cast<uint16_t>(ne_bits16(a, b));
-                                rise += byte_sum16(a) - byte_sum16(b);
-                                dst[c] = a;
+                const bool nz = __any_sync(kFull, w != 0u);
+                if (lane == 0) s_nz[wib] = nz ? 1 : 0;
+                if (!__syncthreads_or(nz)) continue;  // also orders s_nz before its reads
+            }
+            for (int sub = 0; sub < kFrontSuper; ++sub) {
+                const uint64_t ch = cg + static_cast<uint64_t>(sub) * gridDim.x;
+                if (ch >= chunks) break;
+                if (!s_nz[sub]) continue;
+                // vertex ch * kFrontChunk + k * kBlock + threadIdx.x: word (ch * 4 + k) * kWarpsPerBlock + wib,
+                // bit lane
+                bool light[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int64_t wi = (static_cast<int64_t>(ch) * 4 + k) * kWarpsPerBlock + wib;
+                    uint32_t w = 0;
+                    if (wi < words) {
+                        w = Lnew[wi];
+                        if (lane == 0) Lold[wi] = 0;
+                    }
+                    light[k] = false;
+                    nchg += (w >> lane) & 1u;
+                    if ((w >> lane) & 1u) {
+                        const int64_t v = wi * 32 + lane;
+                        const uint64_t d = in_degree(P, v);
+                        indeg += d;
+                        light[k] = true;
+                        if (push_next && d > kPushChunk) {
+                            light[k] = false;
+                            const uint4 *src = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R);
+                            uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R);
+                            if (copy) {
+                                const int CH = P.R / 16;
+                                uint32_t rise = 0;  // how much sweep t raised the row's register sum
+                                for (int c = 0; c < CH; ++c) {
+                                    const uint4 a = src[c], b = dst[c];
+                                    P.dmask[static_cast<size_t>(v) * CH + c] = static_cast<uint16_t>(ne_bits16(a, b));
+                                    rise += byte_sum16(a) - byte_sum16(b);
+                                    dst[c] = a;
+                                }
+                                if (rsum && rise) atomicAdd(&P.gst[v], rise);
                             }
-                            if (rsum && rise) atomicAdd(&P.gst[v], rise);
+                            const uint32_t nt = static_cast<uint32_t>((d + kPushChunk - 1) / kPushChunk);
+                            const uint32_t at = atomicAdd(&P.ctr->nchg_hc, nt);
+                            for (uint32_t c = 0; c < nt; ++c)
+                                P.chg_hc[at + c] = (static_cast<uint64_t>(c) << 32) | static_cast<uint32_t>(v);
                         }
-                        const uint32_t nt = static_cast<uint32_t>((d + kPushChunk - 1) / kPushChunk);
-                        const uint32_t at = atomicAdd(&P.ctr->nchg_hc, nt);
-                        for (uint32_t c = 0; c < nt; ++c)
-                            P.chg_hc[at + c] = (static_cast<uint64_t>(c) << 32) | static_cast<uint32_t>(v);
+                    }
+                }
+                if (!push_next) continue;  // the next sweep pulls into every row: no list, no copies
+                // list the chunk's light vertices (one reservation) and copy their rows into the next sweep's buffer.
+                // This barrier also ends the previous chunk's use of the shared arrays.
+                if (!__syncthreads_or(light[0] | light[1] | light[2] | light[3])) continue;
+                unsigned mk[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    mk[k] = __ballot_sync(kFull, light[k]);
+                    if (lane == 0) s_cnt[k * kWarpsPerBlock + wib] = __popc(mk[k]);
+                }
+                __syncthreads();
+                if (wib == 0) {
+                    const uint32_t c = s_cnt[lane];
+                    uint32_t incl = c;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint32_t y = __shfl_up_sync(kFull, incl, off);
+                        if (lane >= off) incl += y;
+                    }
+                    s_cnt[lane] = incl - c;
+                    if (lane == 31) {
+                        s_n = incl;
+                        s_base = incl ? atomicAdd(&P.ctr->nchg_list, incl) : 0u;
+                    }
+                }
+                __syncthreads();
+                const uint32_t sn = s_n, sb = s_base;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (light[k]) {
+                        const uint32_t at = s_cnt[k * kWarpsPerBlock + wib] + __popc(mk[k] & lt);
+                        const int32_t v = static_cast<int32_t>(
+                            ((static_cast<int64_t>(ch) * 4 + k) * kWarpsPerBlock + wib) * 32 + lane);
+                        P.chg_list[sb + at] = v;
+                        s_v[at] = v;
+                    }
+                }
+                __syncthreads();
+                if (!copy) continue;
+                // consecutive threads on consecutive 16-byte chunks of the listed rows; the chunks' changed registers
+                // (Mw against the previous sweep's Mr) go to dmask for the push sweep
+                // and each row's register sum rises by what sweep t added (one atomic per row and warp: a row's CH
+                // chunks are CH consecutive lanes, CH-aligned, when CH divides 32, or whole warps when 32 divides CH)
+                const uint32_t CH = static_cast<uint32_t>(P.R / 16);
+                const uint32_t seg = CH < 32 ? CH : 32;
+                const uint32_t xend = (sn * CH + 31) & ~31u;  // whole warps, so that the sums' shuffles converge
+#pragma unroll 4
+                for (uint32_t x = threadIdx.x; x < xend; x += blockDim.x) {
+                    const bool in = x < sn * CH;
+                    const int64_t v = in ? s_v[x / CH] : 0;
+                    uint32_t rise = 0;
+                    if (in) {
+                        uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R) + x % CH;
+                        const uint4 a = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R)[x % CH];
+                        const uint4 b = *dst;
+                        P.dmask[static_cast<size_t>(v) * CH + x % CH] = static_cast<uint16_t>(ne_bits16(a, b));
+                        rise = byte_sum16(a) - byte_sum16(b);
+                        *dst = a;
+                    }
+                    if (rsum) {
+                        const unsigned segmask = (seg == 32 ? kFull : (1u << seg) - 1u) << (lane & ~(seg - 1));
+                        rise = __reduce_add_sync(segmask, rise);
+                        if (in && (lane & (seg - 1)) == 0 && rise) atomicAdd(&P.gst[v], rise);
                     }
                 }
             }
-            if (!push_next) continue;  // the next sweep pulls into every row: no list, no copies
-            // list the chunk's light vertices (one reservation) and copy their rows into the next sweep's buffer.
-            // This barrier also ends the previous chunk's use of the shared arrays.
-            if (!__syncthreads_or(light[0] | light[1] | light[2] | light[3])) continue;
-            unsigned mk[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                mk[k] = __ballot_sync(kFull, light[k]);
-                if (lane == 0) s_cnt[k * kWarpsPerBlock + wib] = __popc(mk[k]);
-            }
-            __syncthreads();
-            if (wib == 0) {
-                const uint32_t c = s_cnt[lane];
-                uint32_t incl = c;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t y = __shfl_up_sync(kFull, incl, off);
-                    if (lane >= off) incl += y;
-                }
-                s_cnt[lane] = incl - c;
-                if (lane == 31) {
-                    s_n = incl;
-                    s_base = incl ? atomicAdd(&P.ctr->nchg_list, incl) : 0u;
-                }
-            }
-            __syncthreads();
-            const uint32_t sn = s_n, sb = s_base;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (light[k]) {
-                    const uint32_t at = s_cnt[k * kWarpsPerBlock + wib] + __popc(mk[k] & lt);
-                    const int32_t v = static_cast<int32_t>(
-                        ((static_cast<int64_t>(ch) * 4 + k) * kWarpsPerBlock + wib) * 32 + lane);
-                    P.chg_list[sb + at] = v;
-                    s_v[at] = v;
-                }
-            }
-            __syncthreads();
-            if (!copy) continue;
-            // consecutive threads on consecutive 16-byte chunks of the listed rows; the chunks' changed registers
-            // (Mw against the previous sweep's Mr) go to dmask for the push sweep
-            // and each row's register sum rises by what sweep t added (one atomic per row and warp: a row's CH
-            // chunks are CH consecutive lanes, CH-aligned, when CH divides 32, or whole warps when 32 divides CH)
-            const uint32_t CH = static_cast<uint32_t>(P.R / 16);
-            const uint32_t seg = CH < 32 ? CH : 32;
-            const uint32_t xend = (sn * CH + 31) & ~31u;  // whole warps, so that the sums' shuffles converge
-#pragma unroll 4
-            for (uint32_t x = threadIdx.x; x < xend; x += blockDim.x) {
-                const bool in = x < sn * CH;
-                const int64_t v = in ? s_v[x / CH] : 0;
-                uint32_t rise = 0;
-                if (in) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(Mr + static_cast<size_t>(v) * P.R) + x % CH;
-                    const uint4 a = reinterpret_cast<const uint4 *>(Mw + static_cast<size_t>(v) * P.R)[x % CH];
-                    const uint4 b = *dst;
-                    P.dmask[static_cast<size_t>(v) * CH + x % CH] = static_cast<uint16_t>(ne_bits16(a, b));
-                    rise = byte_sum16(a) - byte_sum16(b);
-                    *dst = a;
-                }
-                if (rsum) {
-                    const unsigned segmask = (seg == 32 ? kFull : (1u << seg) - 1u) << (lane & ~(seg - 1));
-                    rise = __reduce_add_sync(segmask, rise);
-                    if (in && (lane & (seg - 1)) == 0 && rise) atomicAdd(&P.gst[v], rise);
-                }
-            }
+            __syncthreads();  // the chunks are done with s_nz before the next group writes it
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -1912,10 +1938,34 @@ __global__ void __launch_bounds__(kBlock) k_scan(const DevProb *__restrict__ pro
     }
 }
 
+// The block's largest key, added to *dst by one atomic (every thread of the block calls it with its own key).
+__device__ __forceinline__ void block_max_key(unsigned long long key, unsigned long long *dst) {
+    __shared__ unsigned long long s_key[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, key, off);
+        key = o > key ? o : key;
+    }
+    if (lane == 0) s_key[wib] = key;
+    __syncthreads();
+    if (wib == 0) {
+        key = lane < kWarpsPerBlock ? s_key[lane] : 0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kFull, key, off);
+            key = o > key ? o : key;
+        }
+        if (lane == 0 && key) atomicMax(dst, key);
+    }
+    __syncthreads();  // s_key is free again
+}
+
 // ------------------------------------------------------------------------------------------------------------
 // Lazy (CELF-style) argmax for the greedy steps that keep the sketch.  Between two builds M_S' only grows, so a
 // candidate's gain gain_v = sum_j max(M_S'[j], M_v[j]) - sum_j M_S'[j] = sum_j (M_v[j] - M_S'[j])^+ only shrinks,
-// and the gain last evaluated for v (gst[v]) bounds its current gain from above.  A step then
+// and the gain last evaluated for v (gst[v]; right after a build, the row's register sum kept by the sweeps, which
+// is its exact gain since M_S' is empty) bounds its current gain from above.  A step then
 //   1. finds the candidate v1 with the largest bound key (gst[v] << 32 | ~v)            (k_celf_max),
 //   2. evaluates v1 exactly: its exact key tau                                           (k_celf_tau),
 //   3. evaluates exactly every other candidate whose bound key exceeds tau, and keeps the largest exact key
@@ -1923,31 +1973,40 @@ __global__ void __launch_bounds__(kBlock) k_scan(const DevProb *__restrict__ pro
 // Every candidate left out has exact key <= bound key <= tau <= the result, so the result is the full argmax
 // (largest gain, ties to the smallest id), with far fewer register rows read.
 
+// A thread takes four consecutive candidates at a time (one 16-byte load of their bounds, one word of seed bits).
 __global__ void __launch_bounds__(kBlock) k_celf_max(const DevProb *__restrict__ probs,
                                                      const int32_t *__restrict__ act, int nact) {
-    const int lane = threadIdx.x & 31;
     const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     uint64_t base = 0;
     for (int q = 0; q < nact; ++q) {
         const DevProb &P = probs[act[q]];
-        const uint64_t cnt = (static_cast<uint64_t>(P.n) + 31) & ~31ull;  // whole warps per 32 vertices
+        const uint64_t n = static_cast<uint64_t>(P.n);
+        const uint64_t cnt = (n + 3) / 4;
         const uint64_t first = first_owned(tid, nthreads, base);
         base += cnt;
         unsigned long long best = 0;
-        for (uint64_t v = first; v < cnt; v += nthreads) {
-            if (v < static_cast<uint64_t>(P.n) && !test_bit(P.inS, static_cast<int64_t>(v))) {
-                const unsigned long long key = (static_cast<unsigned long long>(__ldg(&P.gst[v])) << 32) |
-                                               (0xFFFFFFFFu - static_cast<uint32_t>(v));
-                best = key > best ? key : best;
+        for (uint64_t g = first; g < cnt; g += nthreads) {
+            const uint64_t v0 = g * 4;
+            uint32_t b[4];
+            if (v0 + 4 <= n) {
+                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(P.gst) + g);
+                b[0] = x.x, b[1] = x.y, b[2] = x.z, b[3] = x.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) b[i] = v0 + i < n ? __ldg(&P.gst[v0 + i]) : 0u;
+            }
+            const uint32_t sb = __ldg(&P.inS[v0 >> 5]) >> (v0 & 31);  // the four candidates' seed bits
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (v0 + i < n && !((sb >> i) & 1u)) {
+                    const unsigned long long key = (static_cast<unsigned long long>(b[i]) << 32) |
+                                                   (0xFFFFFFFFu - static_cast<uint32_t>(v0 + i));
+                    best = key > best ? key : best;
+                }
             }
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(kFull, best, off);
-            best = o > best ? o : best;
-        }
-        if (lane == 0 && best) atomicMax(&P.ctr->cand_key, best);
+        block_max_key(best, &P.ctr->cand_key);
     }
 }
 
@@ -2667,12 +2726,13 @@ __global__ void __launch_bounds__(kBlock) k_inpair_counts(const DevProb P, const
 }
 
 // The pairs and dense in-edges in in-CSR order: in-edge k (out-CSR edge e = ein[k], source u) gets e's out-pairs
-// at ipofs[k] as (u, simulation, out-pair index) with its target v in iv, or one dense entry (u, e).  A thread per
-// in-pair q, so every store is coalesced: a warp takes kInChunk consecutive in-pairs, 32 at a time; the in-edge k
-// holding q (the last k with ipofs[k] <= q) and its row v are found by binary searches at the chunk's start and
-// then by short forward walks from the previous 32's (consecutive in-pairs mostly share their in-edge).  The dense
-// in-edges follow, a thread per in-edge.
-constexpr int kInChunk = 1024;
+// at ipofs[k] as (u, simulation, out-pair index) with its target v in iv, or one dense entry (u, e).  A warp takes
+// kInEdgeChunk consecutive in-edges, 32 at a time: lane t loads in-edge t's source, out-CSR pair offset and row
+// (a short forward walk from the previous group's row), so the dependent loads ein -> pofs of 32 in-edges are in
+// flight together; then the warp writes the group's pairs 32 at a time, lane i pair i, finding the in-edge that holds
+// it by a binary search over the lanes' pair offsets (shuffles), so every store is coalesced.  The dense in-edges
+// follow, a thread per in-edge.
+constexpr int kInEdgeChunk = 1024;
 
 __global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t *iu, uint16_t *ij, uint32_t *iop,
                                                         int32_t *iv, int32_t *idu, uint32_t *ide) {
@@ -2680,42 +2740,58 @@ __global__ void __launch_bounds__(kBlock) k_inpair_fill(const DevProb P, int32_t
     const uint64_t worker = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nworkers = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
     const int64_t m = P.m, n = P.n;
-    const int64_t npairs = P.ipofs[m];
-    const uint64_t chunks = (static_cast<uint64_t>(npairs) + kInChunk - 1) / kInChunk;
+    const uint64_t chunks = (static_cast<uint64_t>(m) + kInEdgeChunk - 1) / kInEdgeChunk;
     for (uint64_t c = worker; c < chunks; c += nworkers) {
-        const int64_t q0 = static_cast<int64_t>(c) * kInChunk;
-        const int64_t q1 = q0 + kInChunk < npairs ? q0 + kInChunk : npairs;
-        int64_t kb = 0, vb = 0;  // the in-edge holding q0 and its in-CSR row
+        const int64_t k0 = static_cast<int64_t>(c) * kInEdgeChunk;
+        const int64_t k1 = k0 + kInEdgeChunk < m ? k0 + kInEdgeChunk : m;
+        int32_t vb = 0;  // the in-CSR row holding in-edge k0 (the last v with xadj_in[v] <= k0)
         {
-            int64_t lo = 0, hi = m - 1;
+            int64_t lo = 0, hi = n - 1;
             while (lo < hi) {
                 const int64_t mid = (lo + hi + 1) >> 1;
-                if (__ldg(&P.ipofs[mid]) <= q0) lo = mid; else hi = mid - 1;
+                if (__ldg(&P.xadj_in[mid]) <= k0) lo = mid; else hi = mid - 1;
             }
-            kb = lo;
-            lo = 0;
-            hi = n - 1;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi + 1) >> 1;
-                if (__ldg(&P.xadj_in[mid]) <= kb) lo = mid; else hi = mid - 1;
-            }
-            vb = lo;
+            vb = static_cast<int32_t>(lo);
         }
-        for (int64_t qb = q0; qb < q1; qb += 32) {
-            const int64_t q = qb + lane;
-            int64_t k = kb, v = vb;
-            if (q < q1) {
-                while (__ldg(&P.ipofs[k + 1]) <= q) ++k;      // ends at the in-edge holding q
-                while (__ldg(&P.xadj_in[v + 1]) <= k) ++v;    // and at its row
+        for (int64_t kb = k0; kb < k1; kb += 32) {
+            const int64_t k = kb + lane;
+            const int64_t kend = kb + 32 < k1 ? kb + 32 : k1;
+            const int64_t Q0 = __ldg(&P.ipofs[kb]);
+            const uint32_t np = static_cast<uint32_t>(__ldg(&P.ipofs[kend]) - Q0);  // the group's pairs
+            int32_t v = vb, u = 0;
+            uint32_t a = 0xFFFFFFFFu;  // this in-edge's first pair, from Q0 (past the group: after every pair)
+            int64_t pp0 = 0;
+            if (k < kend) {
+                while (__ldg(&P.xadj_in[v + 1]) <= k) ++v;
                 const int64_t e = __ldg(&P.ein[k]);
-                const int64_t pp = __ldg(&P.pofs[e]) + (q - __ldg(&P.ipofs[k]));
-                iu[q] = __ldg(&P.adj_in[k]);
-                ij[q] = static_cast<uint16_t>(sw_slot(__ldg(&P.pq[pp]) & 0x3FFu, 0));  // the slot map inverts itself
-                iv[q] = static_cast<int32_t>(v);
-                if (iop) iop[q] = static_cast<uint32_t>(pp);  // the same pair in out-CSR order
+                a = static_cast<uint32_t>(__ldg(&P.ipofs[k]) - Q0);
+                u = __ldg(&P.adj_in[k]);
+                pp0 = __ldg(&P.pofs[e]);
             }
-            kb = __shfl_sync(kFull, k, 31);  // the last lane's (lanes past q1 keep theirs: the loop ends anyway)
-            vb = __shfl_sync(kFull, v, 31);
+            vb = __shfl_sync(kFull, v, 31);  // the last lane's row (a later group starts at or after it)
+            for (uint32_t r = 0; r < np; r += 32) {
+                const uint32_t qo = r + lane;
+                // the in-edge holding pair qo: the last lane t with a_t <= qo (a is non-decreasing over the lanes)
+                int t = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t at = __shfl_sync(kFull, a, t + step);
+                    if (at <= qo) t += step;
+                }
+                const uint32_t at = __shfl_sync(kFull, a, t);
+                const int64_t pt = __shfl_sync(kFull, pp0, t);
+                const int32_t ut = __shfl_sync(kFull, u, t);
+                const int32_t vt = __shfl_sync(kFull, v, t);
+                if (qo < np) {
+                    const int64_t q = Q0 + qo;
+                    const int64_t pp = pt + (qo - at);
+                    iu[q] = ut;
+                    // the slot map inverts itself
+                    ij[q] = static_cast<uint16_t>(sw_slot(__ldg(&P.pq[pp]) & 0x3FFu, 0));
+                    iv[q] = vt;
+                    if (iop) iop[q] = static_cast<uint32_t>(pp);  // the same pair in out-CSR order
+                }
+            }
         }
     }
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;

@@ -555,16 +555,6 @@ __device__ __forceinline__ SweepWork sweep_work(const DevProb &P) {
     return w;
 }
 
-// The first sweep of a diffusion covers every row (those without out-edges too: it writes every row of both
-// buffers) and every task; split rows are finished by the combine kernels.
-__device__ __forceinline__ SweepWork sweep_work_init(const DevProb &P) {
-    SweepWork w;
-    w.nlight = static_cast<uint64_t>(P.n);
-    w.ntask = static_cast<uint64_t>(P.n_tasks);
-    w.rows = nullptr;
-    return w;
-}
-
 // Index of sweep unit l in the descriptor arrays: a row id (l < nlight) or a task id.
 __device__ __forceinline__ int64_t unit_id(const SweepWork &W, uint64_t l) {
     return l < W.nlight ? (W.rows ? static_cast<int64_t>(W.rows[l]) : static_cast<int64_t>(l))
@@ -974,8 +964,10 @@ __device__ __forceinline__ bool word_max(uint32_t *w, uint32_t old, uint32_t can
 // holds M_u for every row (rows of L were copied after the previous sweep), so it is updated in place with
 // compare-and-swap; reads come from the current buffer only (Jacobi).  A whole warp takes one unit, a changed
 // vertex or a chunk of kPushChunk in-edges of one with more (tiles of one warp busy with units of different shapes
-// would run their divergent paths one after the other); its row M_v is staged in shared memory.  Pairs take all 32
-// lanes, four per lane in flight; dense in-edges are merged by the warp's NG lane groups, two per group a round.
+// would run their divergent paths one after the other); the change mask of v is staged in shared memory (after R
+// bytes of the warp's area, which this path leaves unused), and a lane holds its chunks of M_v in registers for the
+// dense in-edges.  Pairs take all 32 lanes, four per lane in flight; dense in-edges are merged by the warp's NG lane
+// groups, two per group a round.
 template <int R>
 __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint64_t first, uint64_t nworkers,
                                int lane, uint32_t *warp_smem) {
@@ -988,7 +980,6 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
     const uint8_t *Mcur = par ? P.M1 : P.M0;
     uint8_t *Mnext = par ? P.M0 : P.M1;
     uint32_t *Lnext = par ? P.Lb0 : P.Lb1;
-    uint8_t *srow = reinterpret_cast<uint8_t *>(warp_smem);
     uint16_t *sdel = reinterpret_cast<uint16_t *>(warp_smem + R / 4);  // M_v's changed registers, per chunk
     unsigned int *fault = &P.ctr->fault;
     const uint32_t lim = P.cas_limit;
@@ -1132,8 +1123,8 @@ __device__ void push_problem_w(const DevProb &P, uint32_t t, uint64_t cnt, uint6
                         (dense ? R : 0) + (12 + W * 4 + R) * static_cast<uint64_t>(d1 - d0);
         __syncwarp();
     }
-    // the staged rows shared the sparse accumulators, which a pulling unit of another problem in the same launch
-    // expects to find zero
+    // the staged masks may share the sparse accumulators, which a pulling unit of another problem in the same
+    // launch expects to find zero
     for (int k = lane; k < R / 4 + R / 32; k += 32) warp_smem[k] = 0u;
     __syncwarp();
     if (st.bytes) atomicAdd(&P.ctr->bytes, st.bytes);
@@ -1322,7 +1313,7 @@ constexpr int kPushMinBlocks = 4;  // resident blocks an SM the push kernel's re
 template <int R, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_push(const DevProb *__restrict__ probs,
                                                        const int32_t *__restrict__ act, int nact, int skip_full) {
-    // per warp: M_v, then its change mask (padded to whole 16-byte words so every warp's row stays aligned)
+    // per warp: R bytes the push leaves unused, then v's change mask (padded to whole 16-byte words)
     __shared__ __align__(16) uint32_t srow[kWarpsPerBlock][R / 4 + ((R / 32 + 3) & ~3)];
     __shared__ uint2 squeue[kWarpsPerBlock][kPushQueue];  // the streamed push's queue of passing pairs
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;

@@ -316,7 +316,8 @@ def run_ours(args, world, rank, local):
                          "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth (sustained copy; of measured)",
                          "kernel": "k_first: the first sweep of every diffusion (initial registers read from the "
-                                   "problem's table, every sparse pair merged, every row written to both buffers)",
+                                   "problem's table, every sparse pair merged, every row written to both buffers "
+                                   "with its change mask and register sum)",
                          "bytes_per_launch": first_bytes / max(first_launches, 1),
                          "launches": first_launches, "ms": first_ms,
                          "all_sweep_kernels": {"achieved": sweeps_achieved,
